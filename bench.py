@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the smoothed-circulant-embedding MLMC hot path.
+
+One step = one MLMC sweep of the oscillatory workload (workloads.OSCILLATORY):
+for every level l = 0..5 (n = 16..512), N_l samples of Algorithm 2 --
+Philox normals -> sqrt(Lambda~)-scaled spectrum -> 2D FFT -> Hartley -> exp,
+the fine and the coarse Darcy solve (multigrid-preconditioned CG with FP64
+iterative refinement), the QoI and the level differences Y_l -- and the level
+sums, through mlmc_level_estimate of the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 32|64]
+    python bench.py --impl reference ...      # the FP64 CPU oracle, bounded sample
+
+Prints one JSON line (rank 0).  value = fine-level samples (Y_l samples, each a
+field + fine + coarse solve) per second over all ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "fine-level samples/s (field+Darcy solve)"
+UNIT = "samples/s"
+L2_BYTES = 129 * 1024 * 1024
+# oracle sample sizes per level for the CPU baseline (bounded: ~10-30 s of CPU work)
+CPU_SAMPLES = [24, 12, 8, 4, 2, 1]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="multiply the per-level sample counts (tests only)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline)
+_ORACLE_LEVELS = None
+
+
+def _oracle_init(wl_name):
+    import numpy as np  # noqa: F401
+    from oracle import embedding as oem
+    global _ORACLE_LEVELS
+    wl = getattr(workloads, wl_name)
+    levels = {}
+    L = len(wl.N) - 1
+    for (l, n, _) in wl.levels:
+        e = oem.setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n, wl.pad_mode)
+        kf, kc = workloads.keep_counts(e.P, l == L, wl.smoothing)
+        mf = oem.smoothing_mask(e.Lam, kf)
+        mc = oem.smoothing_mask(e.Lam, kc)
+        levels[l] = (e, mf, mc)
+    _ORACLE_LEVELS = (wl, levels)
+
+
+def _oracle_task(task):
+    from oracle import mlmc as omlmc
+    wl, levels = _ORACLE_LEVELS
+    l, sample = task
+    e, mf, mc = levels[l]
+    t0 = time.perf_counter()
+    omlmc.level_estimate(e, mf, mc, wl.seed, l, sample, 1, qoi_index=wl.qoi, f=wl.f,
+                         precision=64)
+    return l, time.perf_counter() - t0
+
+
+def oracle_pool(wl):
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    env_threads = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+    os.environ.update(env_threads)
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(cores, initializer=_oracle_init, initargs=(wl.name,))
+    return pool, cores
+
+
+def oracle_measure(pool, cores, wl, step):
+    """Times one bounded sample of the workload on the oracle (all cores, one
+    sample per task, single-threaded BLAS).  Returns (samples/s of the N_l mix,
+    wall seconds, per-level mean seconds)."""
+    tasks = [(l, 10_000_000 + step * 1000 + i) for (l, n, N) in wl.levels
+             for i in range(CPU_SAMPLES[l])]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_task, tasks, chunksize=1)
+    wall = time.perf_counter() - t0
+    per = {}
+    for l, t in res:
+        per.setdefault(l, []).append(t)
+    mean = {l: sum(v) / len(v) for l, v in per.items()}
+    Ntot = sum(N for (_, _, N) in wl.levels)
+    sec_per_sample = sum(N * mean[l] for (l, _, N) in wl.levels) / Ntot
+    return cores / sec_per_sample, wall, mean
+
+
+def cpu_sample_text(wl, cores):
+    return (f"oracle (numpy/scipy FP64) on {cores} host cores, one sample per task with "
+            f"single-threaded BLAS; {'/'.join(map(str, CPU_SAMPLES))} samples on levels 0..5, "
+            f"per-sample times scaled to the N_l mix {'/'.join(map(str, wl.N))}")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workloads.OSCILLATORY
+    pool, cores = oracle_pool(wl)
+    try:
+        for w in range(args.warmup):
+            oracle_measure(pool, cores, wl, 1000 + w)
+        vals, walls = [], []
+        for s in range(args.steps):
+            v, wall, _ = oracle_measure(pool, cores, wl, s)
+            vals.append(v)
+            walls.append(wall)
+    finally:
+        pool.close()
+        pool.join()
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * statistics.mean(walls), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.describe()},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": cpu_sample_text(wl, cores)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_pool = None
+    wl = workloads.OSCILLATORY
+    if args.scale != 1.0:
+        wl = workloads.MLMCWorkload(**{**wl.__dict__, "N": [max(1, int(N * args.scale)) for N in wl.N]})
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if want_cpu:   # spawn the oracle pool before the first GPU call
+        cpu_pool, cpu_cores = oracle_pool(wl)
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    sce.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    prec = args.precision
+    L = len(wl.N) - 1
+
+    embs = []
+    for (l, n, N) in wl.levels:
+        P = 4 * n if wl.pad_mode == 2 else None
+        e0 = sce.ce_setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n, pad_mode=wl.pad_mode)
+        kf, kc = workloads.keep_counts(e0.P, l == L, wl.smoothing)
+        e0.close()
+        embs.append(sce.ce_setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n,
+                                           pad_mode=wl.pad_mode, keep_fine=kf, keep_coarse=kc))
+    Ybuf = [torch.empty(N, dtype=torch.float64, device=dev) for (_, _, N) in wl.levels]
+    Yhost = [torch.empty(N, dtype=torch.float64, pin_memory=True) for (_, _, N) in wl.levels]
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    sums_acc = np.zeros((len(wl.N), 5))
+    iters_max = [0] * len(wl.N)
+
+    def step(i, copy_y=False, record=True):
+        sums = torch.zeros(len(wl.N), 5, dtype=torch.float64)
+        for (l, n, N) in wl.levels:
+            first = (i * world + rank) * N
+            out, _ = sce.mlmc_level_estimate(embs[l], wl.seed, l, first, N, qoi_index=wl.qoi,
+                                             f=wl.f, rtol=wl.rtol, maxit=2000, precision=prec,
+                                             Y=Ybuf[l], stream=stream.cuda_stream,
+                                             allow_not_converged=True)
+            sums[l] = torch.tensor([out.N, out.sumY, out.sumY2, out.sumQf, out.sumQf2])
+            iters_max[l] = max(iters_max[l], out.max_iters)
+            if copy_y:
+                Yhost[l].copy_(Ybuf[l], non_blocking=True)
+        if world > 1:
+            import torch.distributed as dist
+            t = sums.to(dev)
+            dist.all_reduce(t)
+            sums = t.cpu()
+        if copy_y:
+            stream.synchronize()
+        if record:
+            sums_acc[:] += sums.numpy()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for w in range(args.warmup):
+        step(10_000 + w, record=False)
+
+    # device-timed steps (inputs resident; L2 flushed before each step)
+    clocks = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ
+                          else os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local])
+    clocks.start()
+    total_ms = 0.0
+    for i in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(i)
+        e1.record(stream)
+        barrier()
+        total_ms += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    Ntot = sum(wl.N)
+    value = world * Ntot / (ms_per_step / 1000.0)
+
+    # end to end: public API from the host, per-sample Y read back to pinned host memory
+    e2e_steps = max(1, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        step(100 + i, copy_y=True, record=False)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * Ntot / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * Ntot + 56 * len(wl.N),
+           "note": "inputs are the scalar sample ranges (normals are drawn on the device); "
+                   "per-sample Y and the level sums are read back every step"}
+
+    # roofline: one extra step with the launch profiler on
+    barrier()
+    sce.sce_profile_enable(1)
+    step(200, record=False)
+    barrier()
+    prof = sce.sce_profile_read()
+    sce.sce_profile_enable(0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else None
+    roof = None
+    kernels = {}
+    prof_total = sum(v[0] for v in prof.values()) if prof else 0.0
+    for name, (ms, by, nl) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        kernels[name] = {"ms": round(ms, 3), "launches": nl, "share": round(ms / prof_total, 4),
+                         "GBps": round(by / (ms * 1e6), 1) if ms > 0 else None}
+    if top:
+        name, (ms, by, nl) = top
+        ach = by / (ms * 1e6)
+        roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+                "peak_source": peak_src, "avg_launch_us": round(1000 * ms / nl, 2)}
+
+    # level statistics of the timed steps
+    per_level = []
+    for (l, n, N) in wl.levels:
+        Nn, s1, s2, q1, q2 = sums_acc[l]
+        mean = s1 / Nn
+        var = (s2 - Nn * mean * mean) / (Nn - 1)
+        qm = q1 / Nn
+        qv = (q2 - Nn * qm * qm) / (Nn - 1)
+        per_level.append({"level": l, "n": n, "N": N, "mean_Y": mean, "var_Y": var,
+                          "var_Qf": qv, "max_iters": iters_max[l]})
+
+    # plain FP64 per-sample path (batch 1, FP64 field and solver), bounded sample
+    fp64 = None
+    if not args.no_fp64_path:
+        per = []
+        for (l, n, N) in wl.levels:
+            k = max(1, CPU_SAMPLES[l] // 4)
+            barrier()
+            t0 = time.perf_counter()
+            for i in range(k):
+                sce.mlmc_level_estimate(embs[l], wl.seed, l, 50_000_000 + i, 1, qoi_index=wl.qoi,
+                                        f=wl.f, rtol=wl.rtol, maxit=2000, precision=64,
+                                        stream=stream.cuda_stream, allow_not_converged=True)
+            barrier()
+            per.append((time.perf_counter() - t0) / k)
+        sec = sum(N * per[l] for (l, _, N) in wl.levels) / Ntot
+        fp64 = {"value": 1.0 / sec, "unit": UNIT, "speedup": value / world * sec,
+                "sample": "batch-1 FP64 calls, " + "/".join(
+                    str(max(1, c // 4)) for c in CPU_SAMPLES) + " samples on levels 0..5, "
+                "scaled to the N_l mix"}
+
+    cpu = None
+    if want_cpu:
+        try:
+            v, wall, mean = oracle_measure(cpu_pool, cpu_cores, wl, 0)
+            cpu = {"value": v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle",
+                   "sample": cpu_sample_text(wl, cpu_cores), "wall_s": round(wall, 2)}
+        finally:
+            cpu_pool.close()
+            cpu_pool.join()
+
+    for e in embs:
+        e.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == 32 else "f64", "data": "synthetic",
+            "config": {"workload": wl.describe(), "precision": prec,
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": f"dp{world} (samples sharded, level sums all-reduced)"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(v[2] for v in prof.values())),
+            "roofline": roof, "kernels": kernels, "per_level": per_level,
+            "fp64_per_sample_path": fp64, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,227 @@
+/*
+ * sce.h -- C ABI of the GB300 (sm_103a) smoothed-circulant-embedding MLMC library.
+ *
+ * Method: Istratuca & Teckentrup, "Smoothed Circulant Embedding with
+ * Applications to Multilevel Monte Carlo Methods for PDEs with Random
+ * Coefficients".  Citations below name the paper's sections, equations and
+ * algorithms.
+ *
+ * Conventions for every entry point
+ *   - Return value: CE_OK (0) or a negative CE_ERR_* code.  No call throws,
+ *     aborts or exits; ce_status_string() names a code.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it unless stated otherwise.
+ *   - Array arguments marked "device" are caller-owned device memory
+ *     (e.g. a torch tensor's data_ptr) on the current CUDA device; the library
+ *     never frees them.  "host" arrays are caller-owned host memory.
+ *   - Grids: an n-cell grid has (n+1) x (n+1) vertices x_p = p/n on [0,1]^2,
+ *     stored row-major x-fastest: vertex (i, j) at index j*(n+1) + i (the
+ *     lexicographic order of §2.1.2).  n must be a power of two, 4 <= n <= 4096.
+ *   - Embedding side P = 2(n + J) is a power of two, 8 <= P <= 8192.
+ *   - Handles are immutable after set-up: one handle may serve concurrent
+ *     calls on several streams.
+ */
+#ifndef SCE_H
+#define SCE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CE_OK = 0,
+    CE_ERR_INVALID_ARG = -1,   /* bad size, NULL pointer, unsupported option   */
+    CE_ERR_NOT_PSD = -2,       /* embedding not positive semi-definite          */
+    CE_ERR_OOM = -3,           /* device or host allocation failed              */
+    CE_ERR_CUDA = -4,          /* a CUDA runtime call failed                    */
+    CE_ERR_NOT_CONVERGED = -5, /* at least one sample missed the tolerance      */
+    CE_ERR_TIMEOUT = -6,       /* a bounded device wait gave up                 */
+    CE_ERR_NONFINITE = -7      /* a non-finite value reached a result           */
+};
+
+enum { CE_COV_MATERN = 0, CE_COV_SEP_EXP = 1 };
+enum { CE_PAD_NONE = 0, CE_PAD_DOUBLING = 1, CE_PAD_SMOOTH = 2 };
+
+/* Covariance, §2.1: kind CE_COV_MATERN = Eq. (2.2) (nu in {0.5, 1.5, 2.5});
+ * CE_COV_SEP_EXP = Eq. (2.3) with p = 1 (nu ignored). */
+typedef struct {
+    int kind;
+    double nu, lambda, sigma2;
+} ce_cov;
+
+/* Padding, Algorithm 1 step 3(b) and §2.2.  mode CE_PAD_NONE: J as given,
+ * CE_ERR_NOT_PSD if the check fails.  CE_PAD_DOUBLING: classical padding
+ * (the covariance itself at the padded lags), P doubled until the check
+ * passes.  CE_PAD_SMOOTH: smooth periodisation C_ext of Eq. (2.7) with
+ * l = 1 + J/n, P doubled until the check passes.  J < 0 selects the default
+ * (0 for NONE/DOUBLING, n for SMOOTH).  max_P bounds the search (<= 8192). */
+typedef struct {
+    int mode;
+    int J;
+    int max_P;
+} ce_pad;
+
+/* Smoothing, §2.4 and Algorithm 2 step 4(b): keep the `keep` largest
+ * eigenvalues (keep < 0: all).  keep_fine shapes the fine field, keep_coarse
+ * the coarse field of an MLMC level (read at every second vertex).  A tie
+ * group (eigenvalues within tie_rel_tol relative of the cut value) that
+ * straddles the cut is dropped whole.  tie_rel_tol <= 0 selects 1e-10. */
+typedef struct {
+    long long keep_fine, keep_coarse;
+    double tie_rel_tol;
+} ce_smoothing;
+
+typedef struct {
+    int n, P, J;
+    long long s;                              /* P*P                             */
+    long long keep_eff_fine, keep_eff_coarse; /* eigenvalues kept after ties     */
+    double lambda_min, lambda_max;            /* before clipping negatives to 0  */
+    double max_imag;                          /* max |Im Lambda| (round-off)     */
+} ce_embedding_info;
+
+typedef struct ce_embedding_s *ce_embedding_t;
+
+/*
+ * ce_setup_embedding -- Algorithm 1 steps 1-3 (+ Algorithm 2 step 4(b)).
+ * Builds the first column of the block-circulant embedding (§2.1.2, §2.2),
+ * its eigenvalues Lambda = sqrt(s) F s by an FP64 2D FFT on the device
+ * (Eq. (2.6) sign +i), checks min Lambda >= -1e-12 max Lambda (entries in
+ * [-1e-12 max, 0) are clipped to 0), pads as `pad` says, and builds the
+ * smoothing masks and the resident sqrt(Lambda~) tables (FP64 and FP32).
+ *   cov, pad, sm : host structs (sm may be NULL = no smoothing)
+ *   n            : cells per side of the field grid
+ *   out          : host; receives a handle owning its device tables
+ *   info         : host, may be NULL
+ * Synchronises `stream` (reads back scalars).  Errors: CE_ERR_INVALID_ARG,
+ * CE_ERR_NOT_PSD, CE_ERR_OOM, CE_ERR_CUDA.
+ */
+int ce_setup_embedding(const ce_cov *cov, int n, const ce_pad *pad, const ce_smoothing *sm,
+                       void *stream, ce_embedding_t *out, ce_embedding_info *info);
+
+/* Copies the P*P eigenvalues (after clipping, unmasked; index k1 + P*k2) to
+ * dst (device if dst_on_device, else host; host copies synchronise). */
+int ce_get_eigenvalues(ce_embedding_t e, double *dst, int dst_on_device, void *stream);
+
+/* Copies the P*P fine (which = 0) or coarse (which = 1) keep-mask as bytes
+ * (1 = kept) to host memory.  Synchronises. */
+int ce_get_mask(ce_embedding_t e, int which, unsigned char *dst_host);
+
+/*
+ * ce_normals -- the normal generator of Algorithm 1 step 4(a) on its own:
+ * out[c*len + j] = xi_j of sample first_sample + c, j < len (len a multiple
+ * of 4).  Philox4x32-10 (Salmon et al., SC'11) with key (seed lo, seed hi),
+ * counter (j/4, sample lo, sample hi, level); Box-Muller with the library's
+ * IEEE-only ln/sin/cos.  precision 64: double out, u = (x + 0.5) 2^-32;
+ * precision 32: float out, u = (float(x) + 0.5f) 2^-32.  out: device.
+ */
+int ce_normals(uint64_t seed, uint32_t level, uint64_t first_sample, int count, long long len,
+               int precision, void *out, void *stream);
+
+/*
+ * ce_sample_batch -- Algorithm 1 step 4(a)-(f) (Algorithm 2 with masks) for
+ * `count` samples first_sample .. first_sample+count-1 of MLMC level `level`:
+ * xi (in registers) -> w = sqrt(Lambda~) xi -> v = F w (2D FFT, +i, unitary)
+ * -> u = Re v + Im v -> Z = u on the (n+1)^2 grid -> k = exp(Z).
+ *   precision 64: k arrays are double; 32: float (FP32 normals, FFT and exp).
+ *   k_fine   : device, count*(n+1)^2, or NULL
+ *   k_coarse : device, count*(n/2+1)^2, or NULL; the coarse field of the
+ *              level (coarse mask), read at the even vertices of the grid
+ * Errors: CE_ERR_INVALID_ARG, CE_ERR_OOM, CE_ERR_CUDA.
+ */
+int ce_sample_batch(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,
+                    int count, int precision, void *k_fine, void *k_coarse, void *stream);
+
+/* Darcy problem of §3.1, Eq. (3.1), on the n-cell grid:
+ *   -div(k grad u) = f, u = 1 at x1 = 0, u = 0 at x1 = 1, zero flux at x2 = 0, 1;
+ * P1 elements with nodal quadrature (§3.2; each cell split by the diagonal
+ * (i,j)-(i+1,j+1), k averaged over each triangle's vertices).
+ *   rtol      : relative residual target ||r|| <= rtol ||r_0|| (r_0 at u = lifting)
+ *   maxit     : bound on preconditioned iterations (all inner iterations)
+ *   precision : 64 = all-FP64 multigrid-preconditioned CG;
+ *               32 = FP64 residual and solution with FP32 multigrid-CG
+ *                    corrections (iterative refinement). */
+typedef struct {
+    int n;
+    double f;
+    double rtol;
+    int maxit;
+    int precision;
+} darcy_problem;
+
+/*
+ * darcy_solve_batch -- solves the problem for `count` coefficient fields.
+ *   k      : device, count*(n+1)^2, double if precision == 64 else float
+ *   qoi    : device, count*3 doubles: [outflow through x1 = 1 (consistent
+ *            flux), u(7/15, 7/15) (P1 interpolant), ||u_h||_L2 (P1 mass)]
+ *   iters  : device int[count] or NULL: iterations used per sample
+ *   status : device int[count] or NULL: 0 ok, CE_ERR_NOT_CONVERGED,
+ *            CE_ERR_NONFINITE per sample
+ *   u_out  : device double[count*(n+1)^2] or NULL: nodal solution
+ * Returns CE_ERR_NOT_CONVERGED if any sample missed rtol (results are still
+ * written).  Synchronises `stream` (reads back convergence counts).
+ */
+int darcy_solve_batch(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
+                      int *status, double *u_out, void *stream);
+
+/* Level sums of Algorithm 1/2 for one MLMC level (Eq. (3.5)). */
+typedef struct {
+    long long N;
+    double sumY, sumY2, sumQf, sumQf2;
+    int n_failed;
+    int max_iters;
+} mlmc_level_sums;
+
+/*
+ * mlmc_level_estimate -- Algorithm 1 (Algorithm 2 with a smoothed handle):
+ * for samples first_sample .. first_sample+count-1 of `level`, fields by
+ * ce_sample_batch, Darcy solves on the fine grid and (level > 0) on the
+ * coarse grid, QoI number qoi_index (0 outflow, 1 point value, 2 L2 norm),
+ * Y = Q_f - Q_c (Y = Q_f on level 0), and the level sums (fixed-order
+ * reduction on the device).  p->n must equal the handle's n; p->precision
+ * selects the field and solver precision.
+ *   out  : host, the level sums
+ *   Y    : device double[count] or NULL
+ *   qoi_f, qoi_c : device double[count*3] or NULL
+ * Synchronises `stream`.  Returns CE_ERR_NOT_CONVERGED if any solve missed
+ * rtol (sums still written; out->n_failed counts the samples).
+ */
+int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uint64_t seed, uint32_t level,
+                        uint64_t first_sample, int count, int qoi_index, mlmc_level_sums *out,
+                        double *Y, double *qoi_f, double *qoi_c, void *stream);
+
+/* Eq. (3.6): N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)),
+ * l = 0..L.  V, C, N: host arrays of length L+1 (C > 0, V >= 0). */
+int mlmc_optimal_samples(int L_plus_1, const double *V, const double *C, double eps, long long *N);
+
+/* Releases a handle and its device tables (synchronises the device). */
+void ce_destroy(ce_embedding_t e);
+
+const char *ce_status_string(int status);
+
+/* Text of the last CUDA runtime failure seen by the calling thread. */
+const char *sce_last_error(void);
+
+/*
+ * Launch profiler -- instrumentation of this library, not a step of the
+ * paper's method.  sce_profile_enable(1) clears the totals and records a CUDA
+ * event pair around every subsequent kernel launch (on the launching stream),
+ * per kernel family, together with the algorithmic bytes the library
+ * attributes to that launch; sce_profile_enable(0) stops recording.
+ * sce_profile_read waits for the recorded events and returns the family's
+ * total elapsed milliseconds, algorithmic bytes and launch count (any
+ * pointer may be NULL).  Families are numbered 0 .. sce_profile_count()-1
+ * and named by sce_profile_name.  Not thread-safe against concurrent
+ * enable/read calls.
+ */
+void sce_profile_enable(int on);
+int sce_profile_read(int kernel, double *ms, double *bytes, long long *launches);
+int sce_profile_count(void);
+const char *sce_profile_name(int kernel);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCE_H */

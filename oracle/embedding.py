@@ -67,13 +67,13 @@ def dft2_naive(a):
     return D @ a @ D.T
 
 
-NAIVE_DFT_MAX_P = 2048
+NAIVE_DFT_MAX_P = 1024
 
 
 def eigenvalues(c):
     """Algorithm 1 step 3: Lambda = sqrt(s) F s (complex; the caller checks Im).
 
-    Naive DFT up to P = 2048; above that numpy's FFT serves as the same
+    Naive DFT up to P = 1024; above that numpy's FFT serves as the same
     unnormalised +i transform (ifft2 * s), pinned against the naive DFT at
     smaller P by the tests.
     """

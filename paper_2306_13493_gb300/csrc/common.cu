@@ -1,0 +1,162 @@
+// Library-wide helpers: error text, stream-ordered allocation, twiddle tables,
+// status strings.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "sce_internal.cuh"
+
+static thread_local char g_last_error[512];
+
+void sce_set_last_cuda_error(cudaError_t err, const char *what, const char *file, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what,
+             cudaGetErrorString(err), file, line);
+    if (getenv("SCE_VERBOSE")) fprintf(stderr, "[sce] %s\n", g_last_error);
+}
+
+extern "C" const char *sce_last_error(void) { return g_last_error; }
+
+static std::mutex g_pool_mu;
+static bool g_pool_configured[64];
+
+int sce_alloc(void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (bytes == 0) return CE_OK;
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (dev >= 0 && dev < 64 && !g_pool_configured[dev]) {
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t thr = UINT64_MAX;   // keep freed blocks cached in the pool
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+            g_pool_configured[dev] = true;
+        }
+    }
+    SCE_CUDA(cudaMallocAsync(p, bytes, st));
+    return CE_OK;
+}
+
+int sce_free(void *p, cudaStream_t st) {
+    if (p) SCE_CUDA(cudaFreeAsync(p, st));
+    return CE_OK;
+}
+
+// exp(+2 pi i k / P) for k = 0..P-1, evaluated in FP64 on the host from the
+// octant-reduced angle (cos and sin of pi k'/ (P/2) with k' <= P/8 and the
+// symmetries of the circle), so every entry is within an ulp or two.
+static void host_twiddles(int P, std::vector<double> &re, std::vector<double> &im) {
+    re.resize(P);
+    im.resize(P);
+    const double two_pi_over_P = 2.0 * M_PI / P;
+    for (int k = 0; k < P; ++k) {
+        // angle = 2 pi k / P = oct * pi/4 + 2 pi kr / P with kr in [0, P/8)
+        const int oct = (int)((8LL * k) / P);
+        const int kr = k - (int)((long long)oct * P / 8);
+        double c, s;
+        if (P % 8 == 0) {
+            double a;
+            if (oct & 1) a = two_pi_over_P * (double)(P / 8 - kr);   // mirrored
+            else a = two_pi_over_P * (double)kr;
+            double ca = std::cos(a), sa = std::sin(a);
+            // angle = oct*pi/4 + kr*2pi/P; express via symmetry
+            switch (oct) {
+                case 0: c = ca; s = sa; break;           // [0, pi/4)
+                case 1: c = sa; s = ca; break;           // [pi/4, pi/2): pi/2 - a
+                case 2: c = -sa; s = ca; break;          // pi/2 + a
+                case 3: c = -ca; s = sa; break;          // pi - a
+                case 4: c = -ca; s = -sa; break;         // pi + a
+                case 5: c = -sa; s = -ca; break;         // 3pi/2 - a
+                case 6: c = sa; s = -ca; break;          // 3pi/2 + a
+                default: c = ca; s = -sa; break;         // 2pi - a
+            }
+        } else {
+            c = std::cos(two_pi_over_P * k);
+            s = std::sin(two_pi_over_P * k);
+        }
+        re[k] = c;
+        im[k] = s;
+    }
+}
+
+struct TwKey {
+    int dev, P;
+    bool operator<(const TwKey &o) const { return dev != o.dev ? dev < o.dev : P < o.P; }
+};
+static std::mutex g_tw_mu;
+static std::map<TwKey, std::pair<double2 *, float2 *>> g_tw;
+
+static int twiddles(int P, double2 **d64, float2 **d32) {
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto it = g_tw.find({dev, P});
+    if (it != g_tw.end()) {
+        *d64 = it->second.first;
+        *d32 = it->second.second;
+        return CE_OK;
+    }
+    std::vector<double> re, im;
+    host_twiddles(P, re, im);
+    std::vector<double2> h64(P);
+    std::vector<float2> h32(P);
+    for (int k = 0; k < P; ++k) {
+        h64[k] = make_double2(re[k], im[k]);
+        h32[k] = make_float2((float)re[k], (float)im[k]);
+    }
+    double2 *a = nullptr;
+    float2 *b = nullptr;
+    SCE_CUDA(cudaMalloc(&a, P * sizeof(double2)));
+    SCE_CUDA(cudaMalloc(&b, P * sizeof(float2)));
+    SCE_CUDA(cudaMemcpy(a, h64.data(), P * sizeof(double2), cudaMemcpyHostToDevice));
+    SCE_CUDA(cudaMemcpy(b, h32.data(), P * sizeof(float2), cudaMemcpyHostToDevice));
+    g_tw[{dev, P}] = {a, b};
+    *d64 = a;
+    *d32 = b;
+    return CE_OK;
+}
+
+const double2 *sce_twiddles64(int P, int *status) {
+    double2 *a = nullptr;
+    float2 *b = nullptr;
+    *status = twiddles(P, &a, &b);
+    return a;
+}
+
+const float2 *sce_twiddles32(int P, int *status) {
+    double2 *a = nullptr;
+    float2 *b = nullptr;
+    *status = twiddles(P, &a, &b);
+    return b;
+}
+
+extern "C" const char *ce_status_string(int status) {
+    switch (status) {
+        case CE_OK: return "ok";
+        case CE_ERR_INVALID_ARG: return "invalid argument";
+        case CE_ERR_NOT_PSD: return "embedding not positive semi-definite";
+        case CE_ERR_OOM: return "out of memory";
+        case CE_ERR_CUDA: return "CUDA runtime error";
+        case CE_ERR_NOT_CONVERGED: return "solver did not converge";
+        case CE_ERR_TIMEOUT: return "device wait timed out";
+        case CE_ERR_NONFINITE: return "non-finite value";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int mlmc_optimal_samples(int L_plus_1, const double *V, const double *C, double eps,
+                                    long long *N) {
+    if (L_plus_1 <= 0 || !V || !C || !N || !(eps > 0)) return CE_ERR_INVALID_ARG;
+    double total = 0.0;
+    for (int l = 0; l < L_plus_1; ++l) {
+        if (!(C[l] > 0) || !(V[l] >= 0)) return CE_ERR_INVALID_ARG;
+        total += std::sqrt(C[l] * V[l]);
+    }
+    for (int l = 0; l < L_plus_1; ++l)
+        N[l] = (long long)std::ceil(2.0 / (eps * eps) * total * std::sqrt(V[l] / C[l]));
+    return CE_OK;
+}

@@ -1,0 +1,831 @@
+// Batched Darcy solver: Eq. (3.1) with P1 elements and nodal quadrature (§3.2).
+//
+// Discrete operator.  Each cell [a,a+1]x[b,b+1] of the n-cell grid is split by
+// the diagonal (a,b)-(a+1,b+1) into T1 = {(a,b),(a+1,b),(a+1,b+1)} and
+// T2 = {(a,b),(a,b+1),(a+1,b+1)}; k is averaged over each triangle's vertices.
+// On these right triangles the P1 stiffness couples only the two legs, each
+// with weight -1/2 kbar_T (the hypotenuse coupling vanishes), so the matrix is
+// the five-point graph Laplacian with edge conductances
+//   cx(i,j) = 1/2 [kbar_T1(i,j) + kbar_T2(i,j-1)]   edge (i,j)-(i+1,j)
+//   cy(i,j) = 1/2 [kbar_T2(i,j) + kbar_T1(i-1,j)]   edge (i,j)-(i,j+1)
+// (terms of triangles outside the grid dropped) and the load is
+// F = f h^2/6 * (number of triangles at the vertex).  Dirichlet columns
+// i = 0 (u = 1) and i = n (u = 0) are kept in the arrays and never updated.
+//
+// Solver.  u (FP64, nodal, Dirichlet values included) is improved by
+// iterative refinement: r = F - A u in FP64; the correction equation A d = r
+// is solved by CG preconditioned with one symmetric multigrid V(1,1) cycle
+// (red-black Gauss-Seidel, full-weighting restriction = transpose of bilinear
+// prolongation, coarse conductances by series/parallel edge averaging, exact
+// tridiagonal solve on the 2-cell grid), in FP32 (precision 32) or FP64
+// (precision 64); u += d.  Batched over samples: grid.y = sample, every
+// kernel skips samples whose flag is clear, and all reductions are
+// two-stage in a fixed order (bit-reproducible).
+//
+// QoIs: outflow = sum_j cx(n-1,j) u(n-1,j) + f h/2 (the consistent flux
+// -sum (A u - F) over x1 = 1); u(7/15,7/15) from the P1 interpolant;
+// ||u_h||_L2^2 = sum_T |T|/12 [(u_a+u_b+u_c)^2 + u_a^2 + u_b^2 + u_c^2].
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sce_internal.cuh"
+
+namespace {
+
+constexpr int MAXLEV = 14;
+
+struct Launch {
+    int tpb, vpt, epb, nblk;
+    long long V;
+};
+
+static Launch launch_for(int n) {
+    Launch L;
+    L.V = (long long)(n + 1) * (n + 1);
+    long long e = 1;
+    while (e < L.V && e < 1024) e <<= 1;
+    L.epb = (int)e;
+    L.tpb = std::min(256, L.epb);
+    L.vpt = L.epb / L.tpb;
+    L.nblk = (int)((L.V + L.epb - 1) / L.epb);
+    return L;
+}
+
+// vertex loop of one block: v = blockIdx.x*epb + threadIdx.x + e*blockDim.x
+#define FOR_VERT(V, vpt)                                                               \
+    for (int e_ = 0, v = blockIdx.x * (blockDim.x * (vpt)) + threadIdx.x; e_ < (vpt);  \
+         ++e_, v += blockDim.x)                                                        \
+        if (v < (V))
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T val, T *sh) {
+    // fixed-order tree: warp shuffles then warp partials in order
+    for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = val;
+    __syncthreads();
+    T tot = T(0);
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < nw; ++i) tot += sh[i];
+    }
+    return tot;   // valid in thread 0
+}
+
+// ---------------------------------------------------------------- operator
+template <typename Tk, typename T>
+__global__ void cond_kernel(const Tk *__restrict__ k, int n, int vpt, T *__restrict__ cx,
+                            T *__restrict__ cy, double *__restrict__ cx64,
+                            double *__restrict__ cy64) {
+    const int s = blockIdx.y;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const Tk *ks = k + s * V;
+    const int w = n + 1;
+    FOR_VERT(V, vpt) {
+        const int j = v / w, i = v - j * w;
+        auto K = [&](int a, int b) { return (double)ks[b * w + a]; };
+        double gx = 0.0, gy = 0.0;
+        if (i < n) {
+            if (j < n) gx += (K(i, j) + K(i + 1, j) + K(i + 1, j + 1)) / 3.0;        // T1(i,j)
+            if (j > 0) gx += (K(i, j - 1) + K(i, j) + K(i + 1, j)) / 3.0;            // T2(i,j-1)
+            gx *= 0.5;
+        }
+        if (j < n) {
+            if (i < n) gy += (K(i, j) + K(i, j + 1) + K(i + 1, j + 1)) / 3.0;        // T2(i,j)
+            if (i > 0) gy += (K(i - 1, j) + K(i, j) + K(i, j + 1)) / 3.0;            // T1(i-1,j)
+            gy *= 0.5;
+        }
+        cx[s * V + v] = (T)gx;
+        cy[s * V + v] = (T)gy;
+        if (cx64) {
+            cx64[s * V + v] = gx;
+            cy64[s * V + v] = gy;
+        }
+    }
+}
+
+__device__ __forceinline__ double series(double a, double b) {
+    const double t = a + b;
+    return t > 0.0 ? a * b / t : 0.0;
+}
+
+// Coarse conductances: a coarse horizontal edge spans two fine edges in
+// series; it stands for the fine rows 2J (weight 1) and 2J +- 1 (weight 1/2).
+template <typename T>
+__global__ void coarsen_kernel(const T *__restrict__ cxf, const T *__restrict__ cyf, int nf,
+                               int vpt, T *__restrict__ cxc, T *__restrict__ cyc) {
+    const int s = blockIdx.y;
+    const int nc = nf / 2;
+    const long long Vf = (long long)(nf + 1) * (nf + 1), Vc = (long long)(nc + 1) * (nc + 1);
+    const T *ax = cxf + s * Vf, *ay = cyf + s * Vf;
+    const int wf = nf + 1, wc = nc + 1;
+    FOR_VERT(Vc, vpt) {
+        const int J = v / wc, I = v - J * wc;
+        double gx = 0.0, gy = 0.0;
+        if (I < nc) {
+            auto S = [&](int j) { return series((double)ax[j * wf + 2 * I], (double)ax[j * wf + 2 * I + 1]); };
+            gx = S(2 * J);
+            if (J > 0) gx += 0.5 * S(2 * J - 1);
+            if (J < nc) gx += 0.5 * S(2 * J + 1);
+        }
+        if (J < nc) {
+            auto Sy = [&](int i) { return series((double)ay[(2 * J) * wf + i], (double)ay[(2 * J + 1) * wf + i]); };
+            gy = Sy(2 * I);
+            if (I > 0) gy += 0.5 * Sy(2 * I - 1);
+            if (I < nc) gy += 0.5 * Sy(2 * I + 1);
+        }
+        cxc[s * Vc + v] = (T)gx;
+        cyc[s * Vc + v] = (T)gy;
+    }
+}
+
+// ---------------------------------------------------------------- multigrid
+template <typename T>
+__global__ void smooth_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
+                              const T *__restrict__ b, T *__restrict__ z, int n, int vpt,
+                              int color, const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const int w = n + 1;
+    const T *ax = cx + s * V, *ay = cy + s * V, *bs = b + s * V;
+    T *zs = z + s * V;
+    FOR_VERT(V, vpt) {
+        const int j = v / w, i = v - j * w;
+        if (i == 0 || i == n || ((i + j) & 1) != color) continue;
+        const T cw = ax[v - 1], ce = ax[v];
+        const T cs = j > 0 ? ay[v - w] : T(0), cn = j < n ? ay[v] : T(0);
+        T acc = bs[v] + cw * zs[v - 1] + ce * zs[v + 1];
+        if (j > 0) acc += cs * zs[v - w];
+        if (j < n) acc += cn * zs[v + w];
+        zs[v] = acc / (cw + ce + cs + cn);
+    }
+}
+
+// fine residual r = b - A z at an unknown vertex (i in 1..n-1)
+template <typename T>
+__device__ __forceinline__ T resid_at(const T *ax, const T *ay, const T *bs, const T *zs, int i,
+                                      int j, int n) {
+    const int w = n + 1, v = j * w + i;
+    const T zc = zs[v];
+    T Az = ax[v - 1] * (zc - zs[v - 1]) + ax[v] * (zc - zs[v + 1]);
+    if (j > 0) Az += ay[v - w] * (zc - zs[v - w]);
+    if (j < n) Az += ay[v] * (zc - zs[v + w]);
+    return bs[v] - Az;
+}
+
+template <typename T>
+__global__ void restrict_kernel(const T *__restrict__ cxf, const T *__restrict__ cyf,
+                                const T *__restrict__ bf, const T *__restrict__ zf, int nf,
+                                int vpt, T *__restrict__ bc, T *__restrict__ zc,
+                                const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int nc = nf / 2;
+    const long long Vf = (long long)(nf + 1) * (nf + 1), Vc = (long long)(nc + 1) * (nc + 1);
+    const T *ax = cxf + s * Vf, *ay = cyf + s * Vf, *bs = bf + s * Vf, *zs = zf + s * Vf;
+    const int wc = nc + 1;
+    FOR_VERT(Vc, vpt) {
+        const int J = v / wc, I = v - J * wc;
+        T acc = T(0);
+        if (I > 0 && I < nc) {
+            for (int dj = -1; dj <= 1; ++dj) {
+                const int j = 2 * J + dj;
+                if (j < 0 || j > nf) continue;
+                const T wy = dj == 0 ? T(1) : T(0.5);
+                for (int di = -1; di <= 1; ++di) {
+                    const T wx = di == 0 ? T(1) : T(0.5);
+                    acc += wx * wy * resid_at(ax, ay, bs, zs, 2 * I + di, j, nf);
+                }
+            }
+        }
+        bc[s * Vc + v] = acc;
+        zc[s * Vc + v] = T(0);
+    }
+}
+
+template <typename T>
+__global__ void prolong_kernel(const T *__restrict__ zc, int nc, T *__restrict__ zf, int vpt,
+                               const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int nf = 2 * nc;
+    const long long Vf = (long long)(nf + 1) * (nf + 1), Vc = (long long)(nc + 1) * (nc + 1);
+    const T *c = zc + s * Vc;
+    T *f = zf + s * Vf;
+    const int wf = nf + 1, wc = nc + 1;
+    FOR_VERT(Vf, vpt) {
+        const int j = v / wf, i = v - j * wf;
+        if (i == 0 || i == nf) continue;
+        const int I = i >> 1, J = j >> 1;
+        T val;
+        if (!(i & 1) && !(j & 1)) val = c[J * wc + I];
+        else if ((i & 1) && !(j & 1)) val = T(0.5) * (c[J * wc + I] + c[J * wc + I + 1]);
+        else if (!(i & 1) && (j & 1)) val = T(0.5) * (c[J * wc + I] + c[(J + 1) * wc + I]);
+        else
+            val = T(0.25) * (c[J * wc + I] + c[J * wc + I + 1] + c[(J + 1) * wc + I] +
+                             c[(J + 1) * wc + I + 1]);
+        f[v] += val;
+    }
+}
+
+// exact solve on the 2-cell grid: unknowns (1, j), j = 0..2, tridiagonal in j
+template <typename T>
+__global__ void coarsest_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
+                                const T *__restrict__ b, T *__restrict__ z, int count,
+                                const int *__restrict__ act) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= count || !act[s]) return;
+    const T *ax = cx + s * 9, *ay = cy + s * 9, *bs = b + s * 9;
+    T *zs = z + s * 9;
+    double d[3], o[2], r[3];
+    for (int j = 0; j < 3; ++j) {
+        const int v = j * 3 + 1;
+        d[j] = (double)ax[v - 1] + (double)ax[v] + (j > 0 ? (double)ay[v - 3] : 0.0) +
+               (j < 2 ? (double)ay[v] : 0.0);
+        r[j] = (double)bs[v];
+    }
+    o[0] = -(double)ay[1];
+    o[1] = -(double)ay[4];
+    // Thomas algorithm
+    double c0 = o[0] / d[0];
+    double r0 = r[0] / d[0];
+    double den1 = d[1] - o[0] * c0;
+    double c1 = o[1] / den1;
+    double r1 = (r[1] - o[0] * r0) / den1;
+    double den2 = d[2] - o[1] * c1;
+    double x2 = (r[2] - o[1] * r1) / den2;
+    double x1 = r1 - c1 * x2;
+    double x0 = r0 - c0 * x1;
+    zs[1] = (T)x0;
+    zs[4] = (T)x1;
+    zs[7] = (T)x2;
+}
+
+// ---------------------------------------------------------------- Krylov pieces
+template <typename T>
+__global__ void spmv_dot_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
+                                const T *__restrict__ p, T *__restrict__ q, int n, int vpt,
+                                double *__restrict__ part, int nblk, const int *__restrict__ act) {
+    __shared__ T sh[32];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const int w = n + 1;
+    const T *ax = cx + s * V, *ay = cy + s * V, *ps = p + s * V;
+    T *qs = q + s * V;
+    T acc = T(0);
+    FOR_VERT(V, vpt) {
+        const int j = v / w, i = v - j * w;
+        T val = T(0);
+        if (i > 0 && i < n) {
+            const T pc = ps[v];
+            val = ax[v - 1] * (pc - ps[v - 1]) + ax[v] * (pc - ps[v + 1]);
+            if (j > 0) val += ay[v - w] * (pc - ps[v - w]);
+            if (j < n) val += ay[v] * (pc - ps[v + w]);
+            acc += pc * val;
+        }
+        qs[v] = val;
+    }
+    const T tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
+}
+
+template <typename T>
+__global__ void axpy2_kernel(T *__restrict__ d, T *__restrict__ r, const T *__restrict__ p,
+                             const T *__restrict__ q, const double *__restrict__ alpha, int n,
+                             int vpt, double *__restrict__ part, int nblk,
+                             const int *__restrict__ act) {
+    __shared__ T sh[32];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const T a = (T)alpha[s];
+    T acc = T(0);
+    FOR_VERT(V, vpt) {
+        const long long g = s * V + v;
+        d[g] += a * p[g];
+        const T rv = r[g] - a * q[g];
+        r[g] = rv;
+        acc += rv * rv;
+    }
+    const T tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
+}
+
+template <typename T>
+__global__ void dot_kernel(const T *__restrict__ a, const T *__restrict__ b, int n, int vpt,
+                           double *__restrict__ part, int nblk, const int *__restrict__ act) {
+    __shared__ T sh[32];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    T acc = T(0);
+    FOR_VERT(V, vpt) acc += a[s * V + v] * b[s * V + v];
+    const T tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
+}
+
+template <typename T>
+__global__ void pupdate_kernel(T *__restrict__ p, const T *__restrict__ z,
+                               const double *__restrict__ beta, int n, int vpt,
+                               const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const T bt = (T)beta[s];
+    FOR_VERT(V, vpt) {
+        const long long g = s * V + v;
+        p[g] = z[g] + bt * p[g];
+    }
+}
+
+template <typename T>
+__global__ void copy_kernel(T *__restrict__ dst, const T *__restrict__ src, int n, int vpt,
+                            const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    FOR_VERT(V, vpt) dst[s * V + v] = src[s * V + v];
+}
+
+// Per-sample scalar state.
+struct Scal {
+    double *rz, *pq, *rr, *rr0, *alpha, *beta, *orr, *orr0, *thr;
+    int *act_out, *act_in, *iters, *counter;
+};
+
+enum { RED_ALPHA = 0, RED_RR = 1, RED_BETA = 2, RED_RZ0 = 3, RED_ORR = 4, RED_ORR0 = 5 };
+
+// one warp per sample: fixed-order sum of the block partials, then the
+// scalar update of `mode`.
+__global__ void reduce_kernel(const double *__restrict__ part, int nblk, int count, int mode,
+                              Scal sc, const int *__restrict__ act, double rtol2,
+                              double in_rel2) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= count) return;
+    const int s = warp;
+    if (act && !act[s]) return;
+    double v = 0.0;
+    for (int i = lane; i < nblk; i += 32) v += part[(long long)s * nblk + i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane != 0) return;
+    switch (mode) {
+        case RED_ALPHA:
+            sc.pq[s] = v;
+            sc.alpha[s] = v > 0.0 ? sc.rz[s] / v : 0.0;
+            break;
+        case RED_RR: {
+            sc.rr[s] = v;
+            sc.iters[s] += 1;
+            const bool more = v > sc.thr[s];
+            if (!more) sc.act_in[s] = 0;
+            else atomicAdd(sc.counter, 1);
+            break;
+        }
+        case RED_BETA:
+            sc.beta[s] = sc.rz[s] > 0.0 ? v / sc.rz[s] : 0.0;
+            sc.rz[s] = v;
+            break;
+        case RED_RZ0:
+            sc.rz[s] = v;
+            break;
+        case RED_ORR:
+        case RED_ORR0: {
+            sc.orr[s] = v;
+            if (mode == RED_ORR0) sc.orr0[s] = v;
+            const bool more = v > rtol2 * sc.orr0[s] && v == v;
+            sc.act_out[s] = more ? 1 : 0;
+            sc.act_in[s] = sc.act_out[s];
+            // inner target: relative drop in_rel2, but never below what the
+            // outer tolerance needs (a quarter of it, squared: 1/16)
+            sc.thr[s] = fmax(in_rel2 * v, 0.0625 * rtol2 * sc.orr0[s]);
+            if (more) atomicAdd(sc.counter, 1);
+            break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- FP64 outer
+__global__ void lift_kernel(double *__restrict__ u, int n, int vpt) {
+    const int s = blockIdx.y;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const int w = n + 1;
+    FOR_VERT(V, vpt) {
+        const int i = v % w;
+        u[s * V + v] = i == 0 ? 1.0 : 0.0;
+    }
+}
+
+// r64 = F - A u (unknowns; 0 on Dirichlet columns), rin = (T) r64, partial |r64|^2
+template <typename T>
+__global__ void outer_residual_kernel(const double *__restrict__ cx, const double *__restrict__ cy,
+                                      const double *__restrict__ u, double f, int n, int vpt,
+                                      double *__restrict__ r64, T *__restrict__ rin,
+                                      double *__restrict__ part, int nblk,
+                                      const int *__restrict__ act) {
+    __shared__ double sh[32];
+    const int s = blockIdx.y;
+    if (act && !act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const int w = n + 1;
+    const double *ax = cx + s * V, *ay = cy + s * V, *us = u + s * V;
+    const double h2_6 = f / (6.0 * (double)n * (double)n);
+    double acc = 0.0;
+    FOR_VERT(V, vpt) {
+        const int j = v / w, i = v - j * w;
+        double r = 0.0;
+        if (i > 0 && i < n) {
+            const double uc = us[v];
+            double Au = ax[v - 1] * (uc - us[v - 1]) + ax[v] * (uc - us[v + 1]);
+            if (j > 0) Au += ay[v - w] * (uc - us[v - w]);
+            if (j < n) Au += ay[v] * (uc - us[v + w]);
+            const double F = h2_6 * ((j == 0 || j == n) ? 3.0 : 6.0);
+            r = F - Au;
+            acc += r * r;
+        }
+        r64[s * V + v] = r;
+        rin[s * V + v] = (T)r;
+    }
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void outer_update_kernel(double *__restrict__ u, const T *__restrict__ d, int n,
+                                    int vpt, const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    FOR_VERT(V, vpt) u[s * V + v] += (double)d[s * V + v];
+}
+
+// QoI partials: outflow (vertices i = n-1) and the P1 mass norm (cells).
+__global__ void qoi_partial_kernel(const double *__restrict__ cx, const double *__restrict__ u,
+                                   int n, int vpt, double *__restrict__ part_out,
+                                   double *__restrict__ part_l2, int nblk) {
+    __shared__ double sh[32];
+    const int s = blockIdx.y;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const int w = n + 1;
+    const double *us = u + s * V, *ax = cx + s * V;
+    double qo = 0.0, l2 = 0.0;
+    FOR_VERT(V, vpt) {
+        const int j = v / w, i = v - j * w;
+        if (i == n - 1) qo += ax[v] * us[v];
+        if (i < n && j < n) {
+            const double a = us[v], b = us[v + 1], c = us[v + w + 1], d = us[v + w];
+            const double s1 = a + b + c, s2 = a + d + c;
+            l2 += s1 * s1 + a * a + b * b + c * c + s2 * s2 + a * a + d * d + c * c;
+        }
+    }
+    double t = block_sum(qo, sh);
+    if (threadIdx.x == 0) part_out[(long long)s * nblk + blockIdx.x] = t;
+    t = block_sum(l2, sh);
+    if (threadIdx.x == 0) part_l2[(long long)s * nblk + blockIdx.x] = t;
+}
+
+__global__ void qoi_final_kernel(const double *__restrict__ part_out,
+                                 const double *__restrict__ part_l2, int nblk, int count,
+                                 const double *__restrict__ u, int n, double f,
+                                 const Scal sc, double rtol2, double *__restrict__ qoi,
+                                 int *__restrict__ iters_out, int *__restrict__ status_out,
+                                 int *__restrict__ nfail) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= count) return;
+    const int s = warp;
+    double a = 0.0, b = 0.0;
+    for (int i = lane; i < nblk; i += 32) {
+        a += part_out[(long long)s * nblk + i];
+        b += part_l2[(long long)s * nblk + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane != 0) return;
+    const double h = 1.0 / (double)n;
+    const double q_out = a + f * h * 0.5;
+    const double q_l2 = sqrt(b * h * h / 24.0);
+    // point value at (7/15, 7/15): cell (ca, cb), local (xi, eta)
+    const double xs = 7.0 / 15.0 * (double)n, ys = 7.0 / 15.0 * (double)n;
+    const int ca = min((int)floor(xs), n - 1), cb = min((int)floor(ys), n - 1);
+    const double xi = xs - ca, et = ys - cb;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const double *us = u + s * V;
+    const int w = n + 1;
+    const double uab = us[cb * w + ca], ua1b = us[cb * w + ca + 1];
+    const double uab1 = us[(cb + 1) * w + ca], ua1b1 = us[(cb + 1) * w + ca + 1];
+    double q_pt;
+    if (xi >= et) q_pt = uab + xi * (ua1b - uab) + et * (ua1b1 - ua1b);   // T1
+    else q_pt = uab + et * (uab1 - uab) + xi * (ua1b1 - uab1);             // T2
+    qoi[3 * s + 0] = q_out;
+    qoi[3 * s + 1] = q_pt;
+    qoi[3 * s + 2] = q_l2;
+    int st = 0;
+    if (!(fabs(q_out) < 1e300 && fabs(q_pt) < 1e300 && fabs(q_l2) < 1e300)) st = CE_ERR_NONFINITE;
+    else if (!(sc.orr[s] <= rtol2 * sc.orr0[s])) st = CE_ERR_NOT_CONVERGED;
+    if (status_out) status_out[s] = st;
+    if (iters_out) iters_out[s] = sc.iters[s];
+    if (st != 0) atomicAdd(nfail, 1);
+}
+
+__global__ void max_int_kernel(const int *__restrict__ a, int count, int *__restrict__ out) {
+    int m = 0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) m = max(m, a[i]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ int sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (blockDim.x + 31) / 32; ++i) m = max(m, sh[i]);
+        *out = m;
+    }
+}
+
+// ---------------------------------------------------------------- host driver
+template <typename T>
+struct Solver {
+    int count = 0, nlev = 0;
+    int n[MAXLEV];
+    Launch ln[MAXLEV];
+    T *cx[MAXLEV], *cy[MAXLEV], *b[MAXLEV], *z[MAXLEV];
+    T *d = nullptr, *p = nullptr, *q = nullptr;
+    double *u64 = nullptr, *r64 = nullptr, *cx64 = nullptr, *cy64 = nullptr;
+    double *part = nullptr, *part2 = nullptr;
+    Scal sc{};
+    int *misc = nullptr;   // [0] counter, [1] nfail, [2] max iters
+    std::vector<void *> owned;
+    cudaStream_t st = nullptr;
+
+    template <typename U> int alloc(U **ptr, size_t cnt) {
+        int rc = sce_alloc_t(ptr, cnt, st);
+        if (rc == CE_OK) owned.push_back((void *)*ptr);
+        return rc;
+    }
+    ~Solver() {
+        for (void *ptr : owned) sce_free(ptr, st);
+    }
+
+    dim3 grid(int L) const { return dim3(ln[L].nblk, count); }
+
+    double vb(int L, double per_vertex_T, double extra_bytes = 0.0) const {
+        return (double)count * (double)ln[L].V * (per_vertex_T * sizeof(T) + extra_bytes);
+    }
+
+    int smooth(int L, int color) {
+        SceProf pr(KP_SMOOTH, st, vb(L, 3.5));
+        smooth_kernel<T><<<grid(L), ln[L].tpb, 0, st>>>(cx[L], cy[L], b[L], z[L], n[L], ln[L].vpt,
+                                                        color, sc.act_in);
+        return CE_OK;
+    }
+
+    void vcycle(int L) {
+        if (n[L] == 2) {
+            SceProf pr(KP_COARSEST, st, vb(L, 4.0));
+            coarsest_kernel<T><<<(count + 127) / 128, 128, 0, st>>>(cx[L], cy[L], b[L], z[L], count,
+                                                                    sc.act_in);
+            return;
+        }
+        smooth(L, 0);
+        smooth(L, 1);
+        {
+            SceProf pr(KP_RESTRICT, st, vb(L, 4.0) + vb(L + 1, 2.0));
+            restrict_kernel<T><<<grid(L + 1), ln[L + 1].tpb, 0, st>>>(
+                cx[L], cy[L], b[L], z[L], n[L], ln[L + 1].vpt, b[L + 1], z[L + 1], sc.act_in);
+        }
+        vcycle(L + 1);
+        {
+            SceProf pr(KP_PROLONG, st, vb(L, 2.0) + vb(L + 1, 1.0));
+            prolong_kernel<T><<<grid(L), ln[L].tpb, 0, st>>>(z[L + 1], n[L + 1], z[L], ln[L].vpt,
+                                                             sc.act_in);
+        }
+        smooth(L, 1);
+        smooth(L, 0);
+    }
+
+    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0) {
+        const int threads = 256;
+        const int blocks = (count * 32 + threads - 1) / threads;
+        SceProf pr(KP_REDUCE, st, (double)count * ln[0].nblk * 8.0);
+        reduce_kernel<<<blocks, threads, 0, st>>>(part, ln[0].nblk, count, mode, sc, act, rtol2,
+                                                  in_rel2);
+    }
+
+    int read_counter(int *host) {
+        SCE_CUDA(cudaMemcpyAsync(host, sc.counter, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SCE_CUDA(cudaStreamSynchronize(st));
+        return CE_OK;
+    }
+};
+
+template <typename T, typename Tk>
+static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double *qoi, int *iters,
+                         int *status, double *u_out, cudaStream_t st, int *max_iters_out,
+                         int *n_failed_out) {
+    Solver<T> S;
+    S.st = st;
+    S.count = count;
+    const int n0 = p->n;
+    int lv = 0;
+    for (int nn = n0; nn >= 2; nn /= 2) {
+        S.n[lv] = nn;
+        S.ln[lv] = launch_for(nn);
+        ++lv;
+    }
+    S.nlev = lv;
+    const long long V0 = S.ln[0].V;
+    for (int L = 0; L < S.nlev; ++L) {
+        const size_t cnt = (size_t)count * S.ln[L].V;
+        SCE_TRY(S.alloc(&S.cx[L], cnt));
+        SCE_TRY(S.alloc(&S.cy[L], cnt));
+        SCE_TRY(S.alloc(&S.b[L], cnt));
+        SCE_TRY(S.alloc(&S.z[L], cnt));
+    }
+    const size_t c0 = (size_t)count * V0;
+    SCE_TRY(S.alloc(&S.d, c0));
+    SCE_TRY(S.alloc(&S.p, c0));
+    SCE_TRY(S.alloc(&S.q, c0));
+    SCE_TRY(S.alloc(&S.u64, c0));
+    SCE_TRY(S.alloc(&S.r64, c0));
+    const bool same64 = sizeof(T) == sizeof(double);
+    if (same64) {
+        S.cx64 = (double *)S.cx[0];
+        S.cy64 = (double *)S.cy[0];
+    } else {
+        SCE_TRY(S.alloc(&S.cx64, c0));
+        SCE_TRY(S.alloc(&S.cy64, c0));
+    }
+    SCE_TRY(S.alloc(&S.part, (size_t)count * S.ln[0].nblk));
+    SCE_TRY(S.alloc(&S.part2, (size_t)count * S.ln[0].nblk));
+    double *scal = nullptr;
+    SCE_TRY(S.alloc(&scal, (size_t)count * 9));
+    S.sc.rz = scal;
+    S.sc.pq = scal + count;
+    S.sc.rr = scal + 2 * count;
+    S.sc.rr0 = scal + 3 * count;
+    S.sc.alpha = scal + 4 * count;
+    S.sc.beta = scal + 5 * count;
+    S.sc.orr = scal + 6 * count;
+    S.sc.orr0 = scal + 7 * count;
+    S.sc.thr = scal + 8 * count;
+    int *ints = nullptr;
+    SCE_TRY(S.alloc(&ints, (size_t)count * 3 + 4));
+    S.sc.act_out = ints;
+    S.sc.act_in = ints + count;
+    S.sc.iters = ints + 2 * count;
+    S.misc = ints + 3 * count;
+    S.sc.counter = S.misc;
+    SCE_CUDA(cudaMemsetAsync(ints, 0, ((size_t)count * 3 + 4) * sizeof(int), st));
+
+    const Launch &l0 = S.ln[0];
+    const dim3 g0 = S.grid(0);
+    // operator and hierarchy
+    {
+        SceProf pr(KP_COND, st, S.vb(0, 2.0, sizeof(Tk) + (same64 ? 0.0 : 16.0)));
+        cond_kernel<Tk, T><<<g0, l0.tpb, 0, st>>>(k, n0, l0.vpt, S.cx[0], S.cy[0],
+                                                  same64 ? nullptr : S.cx64, same64 ? nullptr : S.cy64);
+    }
+    SCE_CUDA(cudaGetLastError());
+    for (int L = 1; L < S.nlev; ++L) {
+        SceProf pr(KP_COARSEN, st, S.vb(L - 1, 2.0) + S.vb(L, 2.0));
+        coarsen_kernel<T><<<S.grid(L), S.ln[L].tpb, 0, st>>>(S.cx[L - 1], S.cy[L - 1], S.n[L - 1],
+                                                             S.ln[L].vpt, S.cx[L], S.cy[L]);
+    }
+    SCE_CUDA(cudaGetLastError());
+    {
+        SceProf pr(KP_OUTER_UPD, st, S.vb(0, 0.0, 8.0));
+        lift_kernel<<<g0, l0.tpb, 0, st>>>(S.u64, n0, l0.vpt);
+    }
+
+    const double rtol2 = p->rtol * p->rtol;
+    const double in_rel = sizeof(T) == 4 ? 1e-5 : 0.0;
+    const double in_rel2 = in_rel * in_rel;
+    const int maxit = p->maxit > 0 ? p->maxit : 1000;
+    const int inner_max = sizeof(T) == 4 ? 40 : maxit;
+    const int check_every = 4;
+
+    // initial residual
+    {
+        SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 32.0));
+        outer_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx64, S.cy64, S.u64, p->f, n0, l0.vpt,
+                                                        S.r64, S.b[0], S.part, l0.nblk, nullptr);
+    }
+    SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
+    S.reduce(RED_ORR0, nullptr, rtol2, in_rel2);
+    SCE_CUDA(cudaGetLastError());
+    int n_act = 0;
+    SCE_TRY(S.read_counter(&n_act));
+    int total_inner = 0;
+    for (int outer = 0; outer < 64 && n_act > 0 && total_inner < maxit; ++outer) {
+        // inner PCG on the correction equation, samples with act_in set
+        SCE_CUDA(cudaMemsetAsync(S.d, 0, c0 * sizeof(T), st));
+        SCE_CUDA(cudaMemsetAsync(S.z[0], 0, c0 * sizeof(T), st));
+        S.vcycle(0);
+        {
+            SceProf pr(KP_COPY, st, S.vb(0, 2.0));
+            copy_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], n0, l0.vpt, S.sc.act_in);
+        }
+        {
+            SceProf pr(KP_DOT, st, S.vb(0, 2.0));
+            dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.z[0], n0, l0.vpt, S.part, l0.nblk,
+                                                 S.sc.act_in);
+        }
+        S.reduce(RED_RZ0, S.sc.act_in);
+        int in_act = n_act;
+        for (int it = 0; it < inner_max && in_act > 0 && total_inner < maxit; ++it) {
+            {
+                SceProf pr(KP_SPMV, st, S.vb(0, 4.0));
+                spmv_dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.p, S.q, n0, l0.vpt,
+                                                          S.part, l0.nblk, S.sc.act_in);
+            }
+            S.reduce(RED_ALPHA, S.sc.act_in);
+            {
+                SceProf pr(KP_AXPY, st, S.vb(0, 6.0));
+                axpy2_kernel<T><<<g0, l0.tpb, 0, st>>>(S.d, S.b[0], S.p, S.q, S.sc.alpha, n0,
+                                                       l0.vpt, S.part, l0.nblk, S.sc.act_in);
+            }
+            SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
+            S.reduce(RED_RR, S.sc.act_in);
+            ++total_inner;
+            if ((it + 1) % check_every == 0) {
+                SCE_TRY(S.read_counter(&in_act));
+                if (in_act == 0) break;
+            }
+            SCE_CUDA(cudaMemsetAsync(S.z[0], 0, c0 * sizeof(T), st));
+            S.vcycle(0);
+            {
+                SceProf pr(KP_DOT, st, S.vb(0, 2.0));
+                dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.z[0], n0, l0.vpt, S.part, l0.nblk,
+                                                     S.sc.act_in);
+            }
+            S.reduce(RED_BETA, S.sc.act_in);
+            {
+                SceProf pr(KP_PUPDATE, st, S.vb(0, 3.0));
+                pupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], S.sc.beta, n0, l0.vpt,
+                                                         S.sc.act_in);
+            }
+        }
+        SCE_CUDA(cudaGetLastError());
+        {
+            SceProf pr(KP_OUTER_UPD, st, S.vb(0, 1.0, 16.0));
+            outer_update_kernel<T><<<g0, l0.tpb, 0, st>>>(S.u64, S.d, n0, l0.vpt, S.sc.act_out);
+        }
+        {
+            SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 32.0));
+            outer_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx64, S.cy64, S.u64, p->f, n0,
+                                                            l0.vpt, S.r64, S.b[0], S.part, l0.nblk,
+                                                            S.sc.act_out);
+        }
+        SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
+        S.reduce(RED_ORR, S.sc.act_out, rtol2, in_rel2);
+        SCE_CUDA(cudaGetLastError());
+        SCE_TRY(S.read_counter(&n_act));
+    }
+
+    // QoIs
+    {
+        SceProf pr(KP_QOI, st, S.vb(0, 0.0, 16.0));
+        qoi_partial_kernel<<<g0, l0.tpb, 0, st>>>(S.cx64, S.u64, n0, l0.vpt, S.part, S.part2,
+                                                  l0.nblk);
+    }
+    SCE_CUDA(cudaMemsetAsync(S.misc + 1, 0, sizeof(int), st));
+    qoi_final_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(
+        S.part, S.part2, l0.nblk, count, S.u64, n0, p->f, S.sc, rtol2, qoi, iters, status,
+        S.misc + 1);
+    max_int_kernel<<<1, 256, 0, st>>>(S.sc.iters, count, S.misc + 2);
+    SCE_CUDA(cudaGetLastError());
+    if (u_out)
+        SCE_CUDA(cudaMemcpyAsync(u_out, S.u64, c0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int hm[2] = {0, 0};
+    SCE_CUDA(cudaMemcpyAsync(hm, S.misc + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCE_CUDA(cudaStreamSynchronize(st));
+    if (n_failed_out) *n_failed_out = hm[0];
+    if (max_iters_out) *max_iters_out = hm[1];
+    return hm[0] > 0 ? CE_ERR_NOT_CONVERGED : CE_OK;
+}
+
+}  // namespace
+
+int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
+                         int *status, double *u_out, cudaStream_t st, int *max_iters_out,
+                         int *n_failed_out) {
+    if (!p || !k || !qoi || count < 0) return CE_ERR_INVALID_ARG;
+    if (!is_pow2(p->n) || p->n < 4 || p->n > 4096) return CE_ERR_INVALID_ARG;
+    if (p->precision != 32 && p->precision != 64) return CE_ERR_INVALID_ARG;
+    if (!(p->rtol > 0) || count > 65535) return CE_ERR_INVALID_ARG;
+    if (count == 0) return CE_OK;
+    if (p->precision == 64)
+        return darcy_solve_t<double, double>(p, (const double *)k, count, qoi, iters, status,
+                                             u_out, st, max_iters_out, n_failed_out);
+    return darcy_solve_t<float, float>(p, (const float *)k, count, qoi, iters, status, u_out, st,
+                                       max_iters_out, n_failed_out);
+}
+
+extern "C" int darcy_solve_batch(const darcy_problem *p, const void *k, int count, double *qoi,
+                                 int *iters, int *status, double *u_out, void *stream) {
+    return sce_darcy_solve_impl(p, k, count, qoi, iters, status, u_out, as_stream(stream), nullptr,
+                                nullptr);
+}

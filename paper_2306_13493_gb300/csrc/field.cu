@@ -1,0 +1,661 @@
+// Circulant-embedding set-up and per-sample field generation.
+//
+// Set-up (Algorithm 1 steps 1-3, §2.1-2.2; Algorithm 2 step 4(b)):
+//   first column c[i2][i1] = C_pad(d(i1)/n, d(i2)/n), d(i) = min(i, P-i), on
+//   the device in FP64; Lambda = unnormalised +i 2D DFT of c by the library's
+//   FP64 shared-memory FFT; FP64 positivity check; doubling of P while the
+//   check fails; smoothing masks on the host (selection of the keep-th largest
+//   eigenvalue, tie groups dropped whole); resident sqrt(Lambda~) tables.
+//
+// Sampling (Algorithm 1 step 4(a)-(f)), two kernels per batch:
+//   row pass   : xi generated in registers (Philox), w = sqrt(Lambda~) xi,
+//                real-input DFT along x of two real lines packed as one
+//                complex line (two rows of w, or the fine- and coarse-masked
+//                copies of one row), outputs x = 0..n kept, transposed to
+//                Y[x][k2] so the column pass reads contiguous lines;
+//   column pass: DFT along y, outputs y = 0..n kept, u = (Re v + Im v)/P
+//                (1/sqrt(s) = 1/P), k = exp(u) written x-fastest; the plain
+//                coarse field is the fine field at even vertices.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fft.cuh"
+#include "rng.cuh"
+#include "sce_internal.cuh"
+
+using namespace sce;
+
+// ------------------------------------------------------------------ covariance
+__device__ double cov_eval(int kind, double nu, double lam, double sigma2, double t1, double t2) {
+    if (kind == CE_COV_SEP_EXP) return sigma2 * exp(-(fabs(t1) + fabs(t2)) / lam);
+    const double r = sqrt(t1 * t1 + t2 * t2);
+    if (nu == 0.5) return sigma2 * exp(-r / lam);
+    if (nu == 1.5) {
+        const double z = sqrt(3.0) * r / lam;
+        return sigma2 * (1.0 + z) * exp(-z);
+    }
+    const double z = sqrt(5.0) * r / lam;   // nu == 2.5
+    return sigma2 * (1.0 + z + z * z / 3.0) * exp(-z);
+}
+
+__device__ double eta_fn(double x) { return x > 0.0 ? exp(-1.0 / x) : 0.0; }
+
+// cutoff phi of §2.2 (1 on [-1,1], 0 outside [-kappa, kappa])
+__device__ double phi_cut(double t, double kappa) {
+    const double a = fabs(t);
+    const double e1 = eta_fn((kappa - a) / (kappa - 1.0));
+    const double e2 = eta_fn((a - 1.0) / (kappa - 1.0));
+    return e1 / (e1 + e2);
+}
+
+// Eq. (2.7): sum over shifts n in {-2..2}^2 of (C phi_kappa)(x + 2 l n)
+__device__ double cov_ext(int kind, double nu, double lam, double sigma2, double x1, double x2,
+                          double ell) {
+    const double kappa = 2.0 * ell - 1.0;
+    double total = 0.0;
+    for (int n1 = -2; n1 <= 2; ++n1) {
+        for (int n2 = -2; n2 <= 2; ++n2) {
+            const double y1 = x1 + 2.0 * ell * n1;
+            const double y2 = x2 + 2.0 * ell * n2;
+            const double w = phi_cut(fmax(fabs(y1), fabs(y2)), kappa);
+            if (w > 0.0) total += cov_eval(kind, nu, lam, sigma2, y1, y2) * w;
+        }
+    }
+    return total;
+}
+
+__global__ void first_column_kernel(ce_cov cov, int n, int J, int P, int mode, double2 *c) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)P * P) return;
+    const int i1 = (int)(idx % P), i2 = (int)(idx / P);
+    const double t1 = (double)min(i1, P - i1) / (double)n;
+    const double t2 = (double)min(i2, P - i2) / (double)n;
+    double v;
+    if (mode == CE_PAD_SMOOTH)
+        v = cov_ext(cov.kind, cov.nu, cov.lambda, cov.sigma2, t1, t2, 1.0 + (double)J / (double)n);
+    else
+        v = cov_eval(cov.kind, cov.nu, cov.lambda, cov.sigma2, t1, t2);
+    c[idx] = make_double2(v, 0.0);
+}
+
+// One complex line per block, in place: data[line*line_stride + q*elem_stride].
+template <int MAXB>
+__global__ void fft_lines_f64_kernel(double2 *data, int logP, long long line_stride,
+                                     long long elem_stride, const double2 *tw) {
+    extern __shared__ double2 sm_lines[];
+    const int P = 1 << logP;
+    double2 *base = data + (long long)blockIdx.x * line_stride;
+    for (int q = threadIdx.x; q < P; q += blockDim.x) sm_lines[q] = base[q * elem_stride];
+    __syncthreads();
+    smem_fft<double, MAXB>(sm_lines, logP, tw, threadIdx.x, blockDim.x);
+    for (int q = threadIdx.x; q < P; q += blockDim.x) base[q * elem_stride] = sm_lines[q];
+}
+
+// min Re, max Re, max |Im| (one block, fixed-order tree).
+__global__ void spectrum_stats_kernel(const double2 *L, long long s, double *out3) {
+    __shared__ double smin[1024], smax[1024], simag[1024];
+    double mn = 1e300, mx = -1e300, im = 0.0;
+    for (long long i = threadIdx.x; i < s; i += blockDim.x) {
+        const double2 v = L[i];
+        mn = fmin(mn, v.x);
+        mx = fmax(mx, v.x);
+        im = fmax(im, fabs(v.y));
+    }
+    smin[threadIdx.x] = mn;
+    smax[threadIdx.x] = mx;
+    simag[threadIdx.x] = im;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + w]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+            simag[threadIdx.x] = fmax(simag[threadIdx.x], simag[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out3[0] = smin[0];
+        out3[1] = smax[0];
+        out3[2] = simag[0];
+    }
+}
+
+__global__ void clip_real_kernel(const double2 *L, long long s, double *lam) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < s) lam[i] = fmax(L[i].x, 0.0);
+}
+
+__global__ void sqrt_table_kernel(const double *lam, const unsigned char *mask, long long s,
+                                  double *sq64, float *sq32) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s) return;
+    const double v = (mask == nullptr || mask[i]) ? sqrt(lam[i]) : 0.0;
+    sq64[i] = v;
+    sq32[i] = (float)v;
+}
+
+// Keep-mask of §2.4 / Algorithm 2 step 4(b) with the tie rule: a = keep-th
+// largest, b = (keep+1)-th largest; if a - b > tol |a| keep Lambda >= a, else
+// keep Lambda > a + tol |a| (the straddling tie group is dropped whole).
+static long long keep_mask(const std::vector<double> &L, long long keep, double tol,
+                           std::vector<unsigned char> &mask) {
+    const long long s = (long long)L.size();
+    mask.assign(s, 1);
+    if (keep < 0 || keep >= s) return s;
+    if (keep == 0) {
+        std::fill(mask.begin(), mask.end(), 0);
+        return 0;
+    }
+    std::vector<double> v(L);
+    std::nth_element(v.begin(), v.begin() + (keep - 1), v.end(), std::greater<double>());
+    const double a = v[keep - 1];
+    const double b = *std::max_element(v.begin() + keep, v.end());
+    const double tabs = tol * std::fabs(a);
+    long long kept = 0;
+    if (a - b > tabs) {
+        for (long long i = 0; i < s; ++i) kept += (mask[i] = (L[i] >= a) ? 1 : 0);
+    } else {
+        const double thr = a + tabs;
+        for (long long i = 0; i < s; ++i) kept += (mask[i] = (L[i] > thr) ? 1 : 0);
+    }
+    return kept;
+}
+
+static int fft2_f64(double2 *d, int P, cudaStream_t st) {
+    int status = CE_OK;
+    const double2 *tw = sce_twiddles64(P, &status);
+    if (status != CE_OK) return status;
+    const int logP = ilog2(P);
+    const int nthr = std::max(1, std::min(256, P / 4));
+    const size_t smem = (size_t)P * sizeof(double2);
+    SCE_CUDA(cudaFuncSetAttribute(fft_lines_f64_kernel<8>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // rows (contiguous), then columns (stride P)
+    fft_lines_f64_kernel<8><<<P, nthr, smem, st>>>(d, logP, P, 1, tw);
+    SCE_CUDA(cudaGetLastError());
+    fft_lines_f64_kernel<8><<<P, nthr, smem, st>>>(d, logP, 1, P, tw);
+    SCE_CUDA(cudaGetLastError());
+    return CE_OK;
+}
+
+extern "C" int ce_setup_embedding(const ce_cov *cov, int n, const ce_pad *pad,
+                                  const ce_smoothing *sm, void *stream, ce_embedding_t *out,
+                                  ce_embedding_info *info) {
+    if (!cov || !pad || !out) return CE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!is_pow2(n) || n < 4 || n > 4096) return CE_ERR_INVALID_ARG;
+    if (!(cov->lambda > 0) || !(cov->sigma2 > 0)) return CE_ERR_INVALID_ARG;
+    if (cov->kind == CE_COV_MATERN) {
+        if (!(cov->nu == 0.5 || cov->nu == 1.5 || cov->nu == 2.5)) return CE_ERR_INVALID_ARG;
+    } else if (cov->kind != CE_COV_SEP_EXP) {
+        return CE_ERR_INVALID_ARG;
+    }
+    if (pad->mode < CE_PAD_NONE || pad->mode > CE_PAD_SMOOTH) return CE_ERR_INVALID_ARG;
+    const int max_P = pad->max_P > 0 ? std::min(pad->max_P, 8192) : 8192;
+    int J = pad->J >= 0 ? pad->J : (pad->mode == CE_PAD_SMOOTH ? n : 0);
+    if (pad->mode == CE_PAD_SMOOTH && J < 1) return CE_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+
+    double2 *Lc = nullptr;
+    double *dstats = nullptr;
+    int P = 0;
+    double stats[3] = {0, 0, 0};
+    for (;;) {
+        P = 2 * (n + J);
+        if (!is_pow2(P) || P < 8 || P > max_P) {
+            if (Lc) sce_free(Lc, st);
+            return P > max_P ? CE_ERR_NOT_PSD : CE_ERR_INVALID_ARG;
+        }
+        const long long s = (long long)P * P;
+        if (Lc) sce_free(Lc, st);
+        SCE_TRY(sce_alloc_t(&Lc, s, st));
+        if (!dstats) SCE_TRY(sce_alloc_t(&dstats, 3, st));
+        first_column_kernel<<<(unsigned)((s + 255) / 256), 256, 0, st>>>(*cov, n, J, P, pad->mode, Lc);
+        SCE_CUDA(cudaGetLastError());
+        SCE_TRY(fft2_f64(Lc, P, st));
+        spectrum_stats_kernel<<<1, 1024, 0, st>>>(Lc, s, dstats);
+        SCE_CUDA(cudaGetLastError());
+        SCE_CUDA(cudaMemcpyAsync(stats, dstats, sizeof(stats), cudaMemcpyDeviceToHost, st));
+        SCE_CUDA(cudaStreamSynchronize(st));
+        if (stats[0] >= -1e-12 * stats[1]) break;
+        if (pad->mode == CE_PAD_NONE || 2 * P > max_P) {
+            sce_free(Lc, st);
+            sce_free(dstats, st);
+            cudaStreamSynchronize(st);
+            return CE_ERR_NOT_PSD;
+        }
+        J = P - n;   // P -> 2P
+    }
+
+    ce_embedding_s *e = new ce_embedding_s();
+    cudaGetDevice(&e->device);
+    e->n = n;
+    e->P = P;
+    e->J = J;
+    e->mode = pad->mode;
+    e->cov = *cov;
+    e->s = (long long)P * P;
+    e->lambda_min = stats[0];
+    e->lambda_max = stats[1];
+    e->max_imag = stats[2];
+    const long long s = e->s;
+    int rc = CE_OK;
+    auto fail = [&](int code) {
+        ce_destroy(e);
+        sce_free(Lc, st);
+        sce_free(dstats, st);
+        cudaStreamSynchronize(st);
+        return code;
+    };
+    if (cudaMalloc(&e->lam, s * sizeof(double)) != cudaSuccess) return fail(CE_ERR_OOM);
+    clip_real_kernel<<<(unsigned)((s + 255) / 256), 256, 0, st>>>(Lc, s, e->lam);
+    if (cudaGetLastError() != cudaSuccess) return fail(CE_ERR_CUDA);
+
+    long long keep_f = sm ? sm->keep_fine : -1, keep_c = sm ? sm->keep_coarse : -1;
+    const double tol = (sm && sm->tie_rel_tol > 0) ? sm->tie_rel_tol : 1e-10;
+    const bool need_f = keep_f >= 0 && keep_f < s;
+    const bool need_c = keep_c >= 0 && keep_c < s;
+    std::vector<double> hl;
+    if (need_f || need_c) {
+        hl.resize(s);
+        if (cudaMemcpyAsync(hl.data(), e->lam, s * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return fail(CE_ERR_CUDA);
+    }
+    e->keep_eff_fine = need_f ? keep_mask(hl, keep_f, tol, e->mask_f) : s;
+    e->keep_eff_coarse = need_c ? keep_mask(hl, keep_c, tol, e->mask_c) : s;
+    if (!need_f) e->mask_f.assign(s, 1);
+    if (!need_c) e->mask_c.assign(s, 1);
+    e->coarse_distinct = e->mask_c != e->mask_f;
+
+    unsigned char *dmask = nullptr;
+    if ((rc = sce_alloc_t(&dmask, s, st)) != CE_OK) return fail(rc);
+    const unsigned blocks = (unsigned)((s + 255) / 256);
+    if (cudaMalloc(&e->sq64_f, s * sizeof(double)) != cudaSuccess) return fail(CE_ERR_OOM);
+    if (cudaMalloc(&e->sq32_f, s * sizeof(float)) != cudaSuccess) return fail(CE_ERR_OOM);
+    if (cudaMemcpyAsync(dmask, e->mask_f.data(), s, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(CE_ERR_CUDA);
+    sqrt_table_kernel<<<blocks, 256, 0, st>>>(e->lam, dmask, s, e->sq64_f, e->sq32_f);
+    if (e->coarse_distinct) {
+        if (cudaMalloc(&e->sq64_c, s * sizeof(double)) != cudaSuccess) return fail(CE_ERR_OOM);
+        if (cudaMalloc(&e->sq32_c, s * sizeof(float)) != cudaSuccess) return fail(CE_ERR_OOM);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CE_ERR_CUDA);
+        if (cudaMemcpyAsync(dmask, e->mask_c.data(), s, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return fail(CE_ERR_CUDA);
+        sqrt_table_kernel<<<blocks, 256, 0, st>>>(e->lam, dmask, s, e->sq64_c, e->sq32_c);
+    } else {
+        e->sq64_c = e->sq64_f;
+        e->sq32_c = e->sq32_f;
+    }
+    if (cudaGetLastError() != cudaSuccess) return fail(CE_ERR_CUDA);
+    sce_free(dmask, st);
+    sce_free(Lc, st);
+    sce_free(dstats, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        ce_destroy(e);
+        return CE_ERR_CUDA;
+    }
+    if (info) {
+        info->n = n;
+        info->P = P;
+        info->J = J;
+        info->s = s;
+        info->keep_eff_fine = e->keep_eff_fine;
+        info->keep_eff_coarse = e->keep_eff_coarse;
+        info->lambda_min = e->lambda_min;
+        info->lambda_max = e->lambda_max;
+        info->max_imag = e->max_imag;
+    }
+    *out = e;
+    return CE_OK;
+}
+
+extern "C" void ce_destroy(ce_embedding_t e) {
+    if (!e) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(e->device);
+    cudaDeviceSynchronize();
+    if (e->sq64_c && e->sq64_c != e->sq64_f) cudaFree(e->sq64_c);
+    if (e->sq32_c && e->sq32_c != e->sq32_f) cudaFree(e->sq32_c);
+    if (e->sq64_f) cudaFree(e->sq64_f);
+    if (e->sq32_f) cudaFree(e->sq32_f);
+    if (e->lam) cudaFree(e->lam);
+    cudaSetDevice(cur);
+    delete e;
+}
+
+extern "C" int ce_get_eigenvalues(ce_embedding_t e, double *dst, int dst_on_device, void *stream) {
+    if (!e || !dst) return CE_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    SCE_CUDA(cudaMemcpyAsync(dst, e->lam, e->s * sizeof(double),
+                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!dst_on_device) SCE_CUDA(cudaStreamSynchronize(st));
+    return CE_OK;
+}
+
+extern "C" int ce_get_mask(ce_embedding_t e, int which, unsigned char *dst_host) {
+    if (!e || !dst_host || which < 0 || which > 1) return CE_ERR_INVALID_ARG;
+    const std::vector<unsigned char> &m = which == 0 ? e->mask_f : e->mask_c;
+    std::memcpy(dst_host, m.data(), m.size());
+    return CE_OK;
+}
+
+// ------------------------------------------------------------------ normals
+template <typename R>
+__global__ void normals_kernel(uint64_t seed, uint32_t level, uint64_t first_sample, int count,
+                               long long len, R *out) {
+    const long long nq = len / 4;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nq * count) return;
+    const long long c = idx / nq, q = idx % nq;
+    R z[4];
+    Normals<R>::gen4(philox_block(seed, level, first_sample + (uint64_t)c, (uint32_t)q), z);
+    R *o = out + c * len + 4 * q;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) o[r] = z[r];
+}
+
+extern "C" int ce_normals(uint64_t seed, uint32_t level, uint64_t first_sample, int count,
+                          long long len, int precision, void *out, void *stream) {
+    if (!out || count < 0 || len < 0 || (len & 3) || len / 4 > (1LL << 32) ||
+        (precision != 32 && precision != 64))
+        return CE_ERR_INVALID_ARG;
+    if (count == 0 || len == 0) return CE_OK;
+    cudaStream_t st = as_stream(stream);
+    const long long total = (len / 4) * count;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (precision == 64)
+        normals_kernel<double><<<blocks, 256, 0, st>>>(seed, level, first_sample, count, len, (double *)out);
+    else
+        normals_kernel<float><<<blocks, 256, 0, st>>>(seed, level, first_sample, count, len, (float *)out);
+    SCE_CUDA(cudaGetLastError());
+    return CE_OK;
+}
+
+// ------------------------------------------------------------------ row pass
+// Block = F lines x tpf threads.  Plain mode (sq_c == nullptr): line u packs
+// rows 2u and 2u+1 as real and imaginary parts.  Masked mode: line u = row u
+// with the fine-masked w as real part and the coarse-masked w as imaginary part.
+template <typename R, int MAXB>
+__global__ void __launch_bounds__(256) ce_row_kernel(
+    const R *__restrict__ sq_f, const R *__restrict__ sq_c, const typename C2<R>::T *__restrict__ tw,
+    int P, int logP, int m, uint64_t seed, uint32_t level, uint64_t first_sample, int F, int tpf,
+    typename C2<R>::T *__restrict__ Yf, typename C2<R>::T *__restrict__ Yc) {
+    using R2 = typename C2<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R2 *sm = reinterpret_cast<R2 *>(smem_raw);
+    const int sl = blockIdx.y;
+    const uint64_t sample = first_sample + (uint64_t)sl;
+    const int f = threadIdx.x / tpf, t = threadIdx.x - f * tpf;
+    const bool masked = sq_c != nullptr;
+    const int units = masked ? P : P / 2;
+    const int u0 = blockIdx.x * F;
+    const int unit = u0 + f;
+    R2 *buf = sm + (size_t)f * P;
+    const int P4 = P >> 2;
+    if (unit < units) {
+        if (masked) {
+            const int k2 = unit;
+            const R *rf = sq_f + (size_t)k2 * P;
+            const R *rc = sq_c + (size_t)k2 * P;
+            for (int g = t; g < P4; g += tpf) {
+                R xi[4];
+                Normals<R>::gen4(philox_block(seed, level, sample, (uint32_t)(g + P4 * k2)), xi);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int k1 = 4 * g + r;
+                    buf[k1] = R2{rf[k1] * xi[r], rc[k1] * xi[r]};
+                }
+            }
+        } else {
+            const int ka = 2 * unit, kb = ka + 1;
+            const R *ra = sq_f + (size_t)ka * P;
+            const R *rb = sq_f + (size_t)kb * P;
+            for (int g = t; g < P4; g += tpf) {
+                R xa[4], xb[4];
+                Normals<R>::gen4(philox_block(seed, level, sample, (uint32_t)(g + P4 * ka)), xa);
+                Normals<R>::gen4(philox_block(seed, level, sample, (uint32_t)(g + P4 * kb)), xb);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int k1 = 4 * g + r;
+                    buf[k1] = R2{ra[k1] * xa[r], rb[k1] * xb[r]};
+                }
+            }
+        }
+    }
+    __syncthreads();
+    smem_fft<R, MAXB>(buf, logP, tw, t, tpf);
+    // split the packed transform: A = (Z[x] + conj Z[-x])/2, B = (Z[x] - conj Z[-x])/(2i)
+    const R half = R(0.5);
+    const int nthr = blockDim.x;
+    if (!masked) {
+        const int rows = 2 * F;
+        const int k2base = 2 * u0;
+        const long long total = (long long)(m + 1) * rows;
+        for (long long idx = threadIdx.x; idx < total; idx += nthr) {
+            const int x = (int)(idx / rows), rr = (int)(idx - (long long)x * rows);
+            const int ff = rr >> 1;
+            if (u0 + ff >= units) continue;
+            const R2 *b = sm + (size_t)ff * P;
+            const R2 z = b[x], zm = b[(P - x) & (P - 1)];
+            R2 o;
+            if ((rr & 1) == 0) o = R2{half * (z.x + zm.x), half * (z.y - zm.y)};
+            else o = R2{half * (z.y + zm.y), half * (zm.x - z.x)};
+            Yf[((size_t)sl * (m + 1) + x) * P + k2base + rr] = o;
+        }
+    } else {
+        const long long total = (long long)(m + 1) * F;
+        const int mc = m / 2;
+        for (long long idx = threadIdx.x; idx < total; idx += nthr) {
+            const int x = (int)(idx / F), ff = (int)(idx - (long long)x * F);
+            if (u0 + ff >= units) continue;
+            const R2 *b = sm + (size_t)ff * P;
+            const R2 z = b[x], zm = b[(P - x) & (P - 1)];
+            Yf[((size_t)sl * (m + 1) + x) * P + u0 + ff] = R2{half * (z.x + zm.x), half * (z.y - zm.y)};
+            if ((x & 1) == 0)
+                Yc[((size_t)sl * (mc + 1) + (x >> 1)) * P + u0 + ff] =
+                    R2{half * (z.y + zm.y), half * (zm.x - z.x)};
+        }
+    }
+}
+
+template <typename R> __device__ __forceinline__ R exp_r(R x);
+template <> __device__ __forceinline__ float exp_r<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double exp_r<double>(double x) { return exp(x); }
+
+// ------------------------------------------------------------------ column pass
+// coarse == 0: lines x = 0..m of Y (fine field), outputs y = 0..m -> kf, and
+//              (kc_plain != nullptr) kc_plain at even (x, y).
+// coarse == 1: lines xc = 0..m/2 of Y (coarse-masked), outputs y = 2 yc -> kout.
+template <typename R, int MAXB>
+__global__ void __launch_bounds__(256) ce_col_kernel(
+    const typename C2<R>::T *__restrict__ Y, int ncols, int P, int logP, int m, int F, int tpf,
+    const typename C2<R>::T *__restrict__ tw, int coarse, R *__restrict__ kout,
+    R *__restrict__ kc_plain) {
+    using R2 = typename C2<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R2 *sm = reinterpret_cast<R2 *>(smem_raw);
+    const int sl = blockIdx.y;
+    const int f = threadIdx.x / tpf, t = threadIdx.x - f * tpf;
+    const int x0 = blockIdx.x * F;
+    const int col = x0 + f;
+    R2 *buf = sm + (size_t)f * P;
+    if (col < ncols) {
+        const R2 *src = Y + ((size_t)sl * ncols + col) * P;
+        for (int q = t; q < P; q += tpf) buf[q] = src[q];
+    }
+    __syncthreads();
+    smem_fft<R, MAXB>(buf, logP, tw, t, tpf);
+    const R invP = R(1) / R(P);
+    const int mc = m / 2;
+    const int nthr = blockDim.x;
+    if (!coarse) {
+        const long long total = (long long)(m + 1) * F;
+        for (long long idx = threadIdx.x; idx < total; idx += nthr) {
+            const int y = (int)(idx / F), ff = (int)(idx - (long long)y * F);
+            const int x = x0 + ff;
+            if (x >= ncols) continue;
+            const R2 v = sm[(size_t)ff * P + y];
+            const R k = exp_r<R>((v.x + v.y) * invP);
+            kout[((size_t)sl * (m + 1) + y) * (m + 1) + x] = k;
+            if (kc_plain && ((x | y) & 1) == 0)
+                kc_plain[((size_t)sl * (mc + 1) + (y >> 1)) * (mc + 1) + (x >> 1)] = k;
+        }
+    } else {
+        const long long total = (long long)(mc + 1) * F;
+        for (long long idx = threadIdx.x; idx < total; idx += nthr) {
+            const int yc = (int)(idx / F), ff = (int)(idx - (long long)yc * F);
+            const int xc = x0 + ff;
+            if (xc >= ncols) continue;
+            const R2 v = sm[(size_t)ff * P + 2 * yc];
+            kout[((size_t)sl * (mc + 1) + yc) * (mc + 1) + xc] = exp_r<R>((v.x + v.y) * invP);
+        }
+    }
+}
+
+struct LineCfg {
+    int tpf, F, maxb;
+    size_t smem;
+};
+
+template <typename R>
+static LineCfg line_cfg(int P, int units) {
+    LineCfg c;
+    c.tpf = std::max(1, std::min(256, P / 16));
+    const int bpt = (P / 4 + c.tpf - 1) / c.tpf;
+    c.maxb = bpt <= 4 ? 4 : 8;
+    c.F = std::max(1, 256 / c.tpf);
+    const size_t line = (size_t)P * sizeof(typename C2<R>::T);
+    const size_t budget = 96 * 1024;
+    while (c.F > 1 && (size_t)c.F * line > budget) c.F >>= 1;
+    while (c.F > 1 && c.F / 2 >= units) c.F >>= 1;
+    c.smem = (size_t)c.F * line;
+    return c;
+}
+
+template <typename R, int MAXB>
+static int launch_row(const ce_embedding_s *e, bool masked, const typename C2<R>::T *tw,
+                      uint64_t seed, uint32_t level, uint64_t first, int count,
+                      typename C2<R>::T *Yf, typename C2<R>::T *Yc, const LineCfg &c,
+                      cudaStream_t st) {
+    const R *sqf, *sqc;
+    if constexpr (sizeof(R) == 8) {
+        sqf = (const R *)e->sq64_f;
+        sqc = (const R *)e->sq64_c;
+    } else {
+        sqf = (const R *)e->sq32_f;
+        sqc = (const R *)e->sq32_c;
+    }
+    const int units = masked ? e->P : e->P / 2;
+    SCE_CUDA(cudaFuncSetAttribute(ce_row_kernel<R, MAXB>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+    dim3 grid((units + c.F - 1) / c.F, count);
+    const int m = e->n;
+    SceProf pr(KP_ROW, st,
+               (double)e->s * sizeof(R) * (masked ? 2 : 1) +
+                   (double)count * (m + 1) * e->P * 2 * sizeof(R) * (masked ? 1.5 : 1.0));
+    ce_row_kernel<R, MAXB><<<grid, c.F * c.tpf, c.smem, st>>>(
+        sqf, masked ? sqc : nullptr, tw, e->P, ilog2(e->P), e->n, seed, level, first, c.F, c.tpf,
+        Yf, Yc);
+    SCE_CUDA(cudaGetLastError());
+    return CE_OK;
+}
+
+template <typename R, int MAXB>
+static int launch_col(const ce_embedding_s *e, const typename C2<R>::T *Y, int ncols, int coarse,
+                      const typename C2<R>::T *tw, int count, R *kout, R *kc_plain,
+                      const LineCfg &c, cudaStream_t st) {
+    SCE_CUDA(cudaFuncSetAttribute(ce_col_kernel<R, MAXB>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+    dim3 grid((ncols + c.F - 1) / c.F, count);
+    const double rows_out = coarse ? (e->n / 2 + 1) : (e->n + 1);
+    SceProf pr(KP_COL, st,
+               (double)count * ncols * e->P * 2 * sizeof(R) +
+                   (double)count * ncols * rows_out * sizeof(R) * (kc_plain ? 1.25 : 1.0));
+    ce_col_kernel<R, MAXB><<<grid, c.F * c.tpf, c.smem, st>>>(Y, ncols, e->P, ilog2(e->P), e->n,
+                                                               c.F, c.tpf, tw, coarse, kout,
+                                                               kc_plain);
+    SCE_CUDA(cudaGetLastError());
+    return CE_OK;
+}
+
+template <typename R>
+static int sample_batch_t(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first,
+                          int count, R *kf, R *kc, cudaStream_t st) {
+    using R2 = typename C2<R>::T;
+    int status = CE_OK;
+    const R2 *tw;
+    if constexpr (sizeof(R) == 8) tw = sce_twiddles64(e->P, &status);
+    else tw = sce_twiddles32(e->P, &status);
+    if (status != CE_OK) return status;
+    const int P = e->P, m = e->n, mc = m / 2;
+    const bool masked = e->coarse_distinct && kc != nullptr;
+    // fine field needed for kf, and (plain) for kc
+    const bool need_fine = kf != nullptr || (!masked && kc != nullptr);
+    // chunk so the intermediate stays below ~512 MB
+    const size_t per_sample = (size_t)(m + 1) * P * sizeof(R2) + (masked ? (size_t)(mc + 1) * P * sizeof(R2) : 0);
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)count, (512ull << 20) / per_sample));
+    chunk = std::min(chunk, 65535);
+    R2 *Yf = nullptr, *Yc = nullptr;
+    R *kf_tmp = nullptr;
+    SCE_TRY(sce_alloc_t(&Yf, (size_t)chunk * (m + 1) * P, st));
+    if (masked) SCE_TRY(sce_alloc_t(&Yc, (size_t)chunk * (mc + 1) * P, st));
+    if (need_fine && kf == nullptr) SCE_TRY(sce_alloc_t(&kf_tmp, (size_t)chunk * (m + 1) * (m + 1), st));
+    const LineCfg rc = line_cfg<R>(P, masked ? P : P / 2);
+    const LineCfg cc = line_cfg<R>(P, m + 1);
+    const LineCfg ccc = line_cfg<R>(P, mc + 1);
+    int rcode = CE_OK;
+    for (int c0 = 0; c0 < count && rcode == CE_OK; c0 += chunk) {
+        const int cn = std::min(chunk, count - c0);
+        R *kf_c = kf ? kf + (size_t)c0 * (m + 1) * (m + 1) : kf_tmp;
+        R *kc_c = kc ? kc + (size_t)c0 * (mc + 1) * (mc + 1) : nullptr;
+        if (rc.maxb == 4)
+            rcode = launch_row<R, 4>(e, masked, tw, seed, level, first + c0, cn, Yf, Yc, rc, st);
+        else
+            rcode = launch_row<R, 8>(e, masked, tw, seed, level, first + c0, cn, Yf, Yc, rc, st);
+        if (rcode != CE_OK) break;
+        if (need_fine) {
+            R *kcp = masked ? nullptr : kc_c;
+            if (cc.maxb == 4)
+                rcode = launch_col<R, 4>(e, Yf, m + 1, 0, tw, cn, kf_c, kcp, cc, st);
+            else
+                rcode = launch_col<R, 8>(e, Yf, m + 1, 0, tw, cn, kf_c, kcp, cc, st);
+            if (rcode != CE_OK) break;
+        }
+        if (masked) {
+            if (ccc.maxb == 4)
+                rcode = launch_col<R, 4>(e, Yc, mc + 1, 1, tw, cn, kc_c, nullptr, ccc, st);
+            else
+                rcode = launch_col<R, 8>(e, Yc, mc + 1, 1, tw, cn, kc_c, nullptr, ccc, st);
+        }
+    }
+    sce_free(Yf, st);
+    sce_free(Yc, st);
+    sce_free(kf_tmp, st);
+    return rcode;
+}
+
+int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,
+                          int count, int precision, void *k_fine, void *k_coarse, cudaStream_t st) {
+    if (!e || count < 0 || (precision != 32 && precision != 64)) return CE_ERR_INVALID_ARG;
+    if (count == 0 || (!k_fine && !k_coarse)) return CE_OK;
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    if (dev != e->device) return CE_ERR_INVALID_ARG;
+    if (precision == 64)
+        return sample_batch_t<double>(e, seed, level, first_sample, count, (double *)k_fine,
+                                      (double *)k_coarse, st);
+    return sample_batch_t<float>(e, seed, level, first_sample, count, (float *)k_fine,
+                                 (float *)k_coarse, st);
+}
+
+extern "C" int ce_sample_batch(ce_embedding_t e, uint64_t seed, uint32_t level,
+                               uint64_t first_sample, int count, int precision, void *k_fine,
+                               void *k_coarse, void *stream) {
+    return sce_sample_batch_impl(e, seed, level, first_sample, count, precision, k_fine, k_coarse,
+                                 as_stream(stream));
+}

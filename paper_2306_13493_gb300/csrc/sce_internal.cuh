@@ -1,0 +1,93 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "../../include/sce.h"
+
+#define SCE_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t err__ = (call);                                                     \
+        if (err__ != cudaSuccess) {                                                     \
+            sce_set_last_cuda_error(err__, #call, __FILE__, __LINE__);                  \
+            return err__ == cudaErrorMemoryAllocation ? CE_ERR_OOM : CE_ERR_CUDA;       \
+        }                                                                               \
+    } while (0)
+
+#define SCE_TRY(call)                   \
+    do {                                        \
+        int st__ = (call);                      \
+        if (st__ != CE_OK) return st__;         \
+    } while (0)
+
+void sce_set_last_cuda_error(cudaError_t err, const char *what, const char *file, int line);
+
+static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static inline bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+static inline int ilog2(long long v) {
+    int r = 0;
+    while ((1LL << r) < v) ++r;
+    return r;
+}
+
+// Stream-ordered device allocation from the device's default pool.
+int sce_alloc(void **p, size_t bytes, cudaStream_t st);
+int sce_free(void *p, cudaStream_t st);
+
+template <typename T>
+static inline int sce_alloc_t(T **p, size_t count, cudaStream_t st) {
+    return sce_alloc(reinterpret_cast<void **>(p), count * sizeof(T), st);
+}
+
+// Twiddle tables exp(+2 pi i k / P), k = 0..P-1, built once per P and device.
+const double2 *sce_twiddles64(int P, int *status);
+const float2 *sce_twiddles32(int P, int *status);
+
+struct ce_embedding_s {
+    int device;
+    int n, P, J, mode;
+    ce_cov cov;
+    long long s;
+    long long keep_eff_fine, keep_eff_coarse;
+    bool coarse_distinct;   // coarse mask differs from the fine mask
+    double lambda_min, lambda_max, max_imag;
+    double *lam;            // P*P eigenvalues (clipped), device
+    double *sq64_f;         // P*P sqrt(Lambda~_fine), device
+    double *sq64_c;         // P*P sqrt(Lambda~_coarse) (== sq64_f if !coarse_distinct)
+    float *sq32_f;
+    float *sq32_c;
+    std::vector<unsigned char> mask_f, mask_c;   // host copies
+};
+
+// ---------------------------------------------------------------- profiling
+// Kernel families timed by the optional launch profiler (sce_profile_*).
+enum SceKernel {
+    KP_ROW = 0, KP_COL, KP_COND, KP_COARSEN, KP_SMOOTH, KP_RESTRICT, KP_PROLONG, KP_COARSEST,
+    KP_SPMV, KP_AXPY, KP_DOT, KP_PUPDATE, KP_COPY, KP_REDUCE, KP_OUTER_RES, KP_OUTER_UPD, KP_QOI,
+    KP_SETUP, KP_NORMALS, KP_LEVEL, KP_COUNT_
+};
+
+bool sce_prof_on();
+// Records a start event (when profiling is on) and, on destruction, the end
+// event of the launch(es) enqueued in between; `bytes` = algorithmic bytes.
+struct SceProf {
+    int id = -1;
+    int slot = -1;
+    cudaStream_t st = nullptr;
+    SceProf(int kernel, cudaStream_t s, double bytes);
+    ~SceProf();
+};
+
+// Field path entry used by mlmc_level_estimate (same as ce_sample_batch).
+int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,
+                          int count, int precision, void *k_fine, void *k_coarse, cudaStream_t st);
+
+// Darcy solver entry used by mlmc_level_estimate.
+int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
+                         int *status, double *u_out, cudaStream_t st, int *max_iters_out,
+                         int *n_failed_out);

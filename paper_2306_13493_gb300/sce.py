@@ -1,0 +1,265 @@
+"""Python binding of the C ABI declared in include/sce.h (ctypes).
+
+Argument marshalling only: every step runs in the CUDA library libsce.so.
+Device arrays are passed as torch CUDA tensors (their data_ptr); the stream is
+the tensor's current torch stream unless one is given.  A missing library is
+an error -- there is no fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsce.so")
+
+CE_OK = 0
+CE_ERR_INVALID_ARG = -1
+CE_ERR_NOT_PSD = -2
+CE_ERR_OOM = -3
+CE_ERR_CUDA = -4
+CE_ERR_NOT_CONVERGED = -5
+CE_ERR_TIMEOUT = -6
+CE_ERR_NONFINITE = -7
+
+CE_COV_MATERN = 0
+CE_COV_SEP_EXP = 1
+CE_PAD_NONE = 0
+CE_PAD_DOUBLING = 1
+CE_PAD_SMOOTH = 2
+
+QOI_OUTFLOW = 0
+QOI_POINT = 1
+QOI_L2 = 2
+
+
+class ce_cov(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nu", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("sigma2", ctypes.c_double)]
+
+
+class ce_pad(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("J", ctypes.c_int), ("max_P", ctypes.c_int)]
+
+
+class ce_smoothing(ctypes.Structure):
+    _fields_ = [("keep_fine", ctypes.c_longlong), ("keep_coarse", ctypes.c_longlong),
+                ("tie_rel_tol", ctypes.c_double)]
+
+
+class ce_embedding_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("P", ctypes.c_int), ("J", ctypes.c_int),
+                ("s", ctypes.c_longlong), ("keep_eff_fine", ctypes.c_longlong),
+                ("keep_eff_coarse", ctypes.c_longlong), ("lambda_min", ctypes.c_double),
+                ("lambda_max", ctypes.c_double), ("max_imag", ctypes.c_double)]
+
+
+class darcy_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("f", ctypes.c_double), ("rtol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class mlmc_level_sums(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_longlong), ("sumY", ctypes.c_double), ("sumY2", ctypes.c_double),
+                ("sumQf", ctypes.c_double), ("sumQf2", ctypes.c_double),
+                ("n_failed", ctypes.c_int), ("max_iters", ctypes.c_int)]
+
+
+# name -> (restype, argtypes); the exported C ABI
+_P = ctypes.c_void_p
+_SIGS = {
+    "ce_setup_embedding": (ctypes.c_int, [ctypes.POINTER(ce_cov), ctypes.c_int,
+                                          ctypes.POINTER(ce_pad), ctypes.POINTER(ce_smoothing),
+                                          _P, ctypes.POINTER(_P),
+                                          ctypes.POINTER(ce_embedding_info)]),
+    "ce_get_eigenvalues": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "ce_get_mask": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "ce_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                                  ctypes.c_longlong, ctypes.c_int, _P, _P]),
+    "ce_sample_batch": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                       ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "darcy_solve_batch": (ctypes.c_int, [ctypes.POINTER(darcy_problem), _P, ctypes.c_int, _P, _P,
+                                         _P, _P, _P]),
+    "mlmc_level_estimate": (ctypes.c_int, [_P, ctypes.POINTER(darcy_problem), ctypes.c_uint64,
+                                           ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                                           ctypes.c_int, ctypes.POINTER(mlmc_level_sums), _P, _P,
+                                           _P, _P]),
+    "mlmc_optimal_samples": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_double, _P]),
+    "ce_destroy": (None, [_P]),
+    "ce_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "sce_last_error": (ctypes.c_char_p, []),
+    "sce_profile_enable": (None, [ctypes.c_int]),
+    "sce_profile_read": (ctypes.c_int, [ctypes.c_int, _P, _P, _P]),
+    "sce_profile_count": (ctypes.c_int, []),
+    "sce_profile_name": (ctypes.c_char_p, [ctypes.c_int]),
+}
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+
+
+class SceError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def load(path=None):
+    """Loads libsce.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libsce.so not built at {p}: run paper_2306_13493_gb300.build")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_string(status):
+    return load().ce_status_string(int(status)).decode()
+
+
+def last_error():
+    return load().sce_last_error().decode()
+
+
+def _check(status, what, allow=()):
+    if status != CE_OK and status not in allow:
+        raise SceError(status, what)
+    return status
+
+
+def _stream(stream, tensor=None):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    dev = tensor.device if tensor is not None and tensor.is_cuda else None
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Embedding:
+    """Owner of a ce_embedding_t handle (destroyed with the object)."""
+
+    def __init__(self, handle, info):
+        self.handle = handle
+        self.info = info
+
+    @property
+    def n(self):
+        return self.info.n
+
+    @property
+    def P(self):
+        return self.info.P
+
+    def close(self):
+        if self.handle:
+            load().ce_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ce_setup_embedding(kind, nu, lam, sigma2, n, pad_mode=CE_PAD_DOUBLING, J=-1, max_P=8192,
+                       keep_fine=-1, keep_coarse=-1, tie_rel_tol=1e-10, stream=None):
+    lib = load()
+    cov = ce_cov(kind, nu, lam, sigma2)
+    pad = ce_pad(pad_mode, J, max_P)
+    sm = ce_smoothing(keep_fine, keep_coarse, tie_rel_tol)
+    h = ctypes.c_void_p()
+    info = ce_embedding_info()
+    _check(lib.ce_setup_embedding(ctypes.byref(cov), n, ctypes.byref(pad), ctypes.byref(sm),
+                                  _stream(stream), ctypes.byref(h), ctypes.byref(info)),
+           "ce_setup_embedding")
+    return Embedding(h, info)
+
+
+def ce_get_eigenvalues(emb, out, stream=None):
+    """out: torch float64 tensor of P*P elements (device or host)."""
+    _check(load().ce_get_eigenvalues(emb.handle, _ptr(out), int(out.is_cuda), _stream(stream, out)),
+           "ce_get_eigenvalues")
+    return out
+
+
+def ce_get_mask(emb, which, out):
+    """out: contiguous host uint8 tensor/array of P*P elements."""
+    ptr = out.ctypes.data if hasattr(out, "ctypes") else out.data_ptr()
+    _check(load().ce_get_mask(emb.handle, which, ctypes.c_void_p(ptr)), "ce_get_mask")
+    return out
+
+
+def ce_normals(seed, level, first_sample, count, length, precision, out, stream=None):
+    _check(load().ce_normals(seed, level, first_sample, count, length, precision, _ptr(out),
+                             _stream(stream, out)), "ce_normals")
+    return out
+
+
+def ce_sample_batch(emb, seed, level, first_sample, count, precision, k_fine=None,
+                    k_coarse=None, stream=None):
+    t = k_fine if k_fine is not None else k_coarse
+    _check(load().ce_sample_batch(emb.handle, seed, level, first_sample, count, precision,
+                                  _ptr(k_fine), _ptr(k_coarse), _stream(stream, t)),
+           "ce_sample_batch")
+
+
+def darcy_solve_batch(n, k, count, qoi, f=0.0, rtol=1e-10, maxit=1000, precision=32, iters=None,
+                      status=None, u_out=None, stream=None, allow_not_converged=False):
+    prob = darcy_problem(n, f, rtol, maxit, precision)
+    allow = (CE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    return _check(load().darcy_solve_batch(ctypes.byref(prob), _ptr(k), count, _ptr(qoi),
+                                           _ptr(iters), _ptr(status), _ptr(u_out),
+                                           _stream(stream, k)), "darcy_solve_batch", allow)
+
+
+def mlmc_level_estimate(emb, seed, level, first_sample, count, qoi_index=QOI_OUTFLOW, f=0.0,
+                        rtol=1e-10, maxit=1000, precision=32, Y=None, qoi_f=None, qoi_c=None,
+                        stream=None, allow_not_converged=False):
+    prob = darcy_problem(emb.n, f, rtol, maxit, precision)
+    out = mlmc_level_sums()
+    allow = (CE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    st = _check(load().mlmc_level_estimate(emb.handle, ctypes.byref(prob), seed, level,
+                                           first_sample, count, qoi_index, ctypes.byref(out),
+                                           _ptr(Y), _ptr(qoi_f), _ptr(qoi_c), _stream(stream, Y)),
+                "mlmc_level_estimate", allow)
+    return out, st
+
+
+def sce_profile_enable(on):
+    load().sce_profile_enable(int(bool(on)))
+
+
+def sce_profile_read():
+    """{family name: (ms, algorithmic bytes, launches)} for families that ran."""
+    lib = load()
+    out = {}
+    for i in range(lib.sce_profile_count()):
+        ms, by, nl = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        _check(lib.sce_profile_read(i, ctypes.byref(ms), ctypes.byref(by), ctypes.byref(nl)),
+               "sce_profile_read")
+        if nl.value:
+            out[lib.sce_profile_name(i).decode()] = (ms.value, by.value, nl.value)
+    return out
+
+
+def mlmc_optimal_samples(V, C, eps):
+    import numpy as np
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    N = np.zeros(len(V), dtype=np.int64)
+    _check(load().mlmc_optimal_samples(len(V), ctypes.c_void_p(V.ctypes.data),
+                                       ctypes.c_void_p(C.ctypes.data), eps,
+                                       ctypes.c_void_p(N.ctypes.data)), "mlmc_optimal_samples")
+    return N

@@ -1,0 +1,63 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+entry point include/sce.h declares; host-only entry points agree with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import mlmc as omlmc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "sce.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    return sce.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("ce_setup_embedding", "ce_sample_batch", "darcy_solve_batch", "mlmc_level_estimate",
+              "ce_destroy", "ce_status_string", "ce_normals", "mlmc_optimal_samples"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2306_13493_gb300 import sce
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in sce.EXPORTED, name
+
+
+def test_status_strings(lib):
+    from paper_2306_13493_gb300 import sce
+    assert sce.status_string(0) == "ok"
+    assert "converge" in sce.status_string(sce.CE_ERR_NOT_CONVERGED)
+
+
+def test_optimal_samples_matches_oracle(lib):
+    from paper_2306_13493_gb300 import sce
+    V = np.array([3.1e-2, 4.0e-3, 9.0e-4, 1.7e-4])
+    C = np.array([1.0, 4.2, 17.0, 70.0])
+    for eps in (1e-2, 2.5e-3, 1e-3):
+        assert list(sce.mlmc_optimal_samples(V, C, eps)) == list(omlmc.optimal_samples(V, C, eps))
+    with pytest.raises(sce.SceError):
+        sce.mlmc_optimal_samples([1.0], [0.0], 1e-2)
+
+
+def test_struct_layouts_match_header():
+    from paper_2306_13493_gb300 import sce
+    assert ctypes.sizeof(sce.ce_cov) == 32
+    assert ctypes.sizeof(sce.ce_embedding_info) == 4 * 3 + 4 + 8 * 3 + 8 * 3
+    assert ctypes.sizeof(sce.mlmc_level_sums) == 8 * 5 + 8

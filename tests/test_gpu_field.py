@@ -1,0 +1,152 @@
+"""GPU parity of the field path (Algorithm 1 steps 1-3 and 4(a)-(f)) against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import covariance as ocv
+from oracle import embedding as oem
+from oracle import field as ofield
+from oracle import rng as orng
+from tests.gpu_common import TOL32, TOL64, lib, rel_err, torch_dtype
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sce():
+    return lib()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("seed,level,first", [(0, 0, 0), (3, 5, 17), ((1 << 40) + 7, 2, (1 << 33) + 5)])
+def test_normals_bit_exact(sce, precision, seed, level, first):
+    import torch
+    count, length = 3, 4 * 1000 + 4
+    out = torch.empty(count * length, dtype=torch_dtype(precision), device="cuda")
+    sce.ce_normals(seed, level, first, count, length, precision, out)
+    got = out.cpu().numpy().reshape(count, length)
+    for c in range(count):
+        want = orng.normals(seed, level, first + c, length, precision)
+        assert got[c].dtype == want.dtype
+        bad = np.nonzero(got[c].view(np.uint64 if precision == 64 else np.uint32)
+                         != want.view(np.uint64 if precision == 64 else np.uint32))[0]
+        assert bad.size == 0, (c, bad[:5], got[c][bad[:5]], want[bad[:5]])
+
+
+CASES = [
+    # kind, nu, lam, sigma2, n, pad mode
+    (ocv.MATERN, 0.5, 0.3, 1.0, 32, oem.PAD_DOUBLING),     # 33x33 grid, doubled to 128
+    (ocv.MATERN, 0.5, 0.02, 1.0, 16, oem.PAD_SMOOTH),      # oscillatory, smooth periodisation
+    (ocv.MATERN, 1.5, 0.05, 1.0, 64, oem.PAD_DOUBLING),
+    (ocv.MATERN, 2.5, 0.1, 3.0, 8, oem.PAD_DOUBLING),
+    (ocv.SEP_EXP, 0.0, 0.1, 1.0, 16, oem.PAD_NONE),
+    (ocv.MATERN, 0.5, 0.3, 1.0, 4, oem.PAD_DOUBLING),      # smallest grid
+]
+
+
+def _setup_both(sce, case, keep_f=-1, keep_c=-1):
+    kind, nu, lam, s2, n, mode = case
+    emb = sce.ce_setup_embedding(kind, nu, lam, s2, n, pad_mode=mode, keep_fine=keep_f,
+                                 keep_coarse=keep_c)
+    oe = oem.setup_embedding(kind, nu, lam, s2, n, mode)
+    return emb, oe
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_embedding_eigenvalues(sce, case):
+    import torch
+    emb, oe = _setup_both(sce, case)
+    assert (emb.info.P, emb.info.J) == (oe.P, oe.J)
+    lam = torch.empty(oe.P * oe.P, dtype=torch.float64)
+    sce.ce_get_eigenvalues(emb, lam)
+    got = lam.numpy().reshape(oe.P, oe.P)
+    assert np.max(np.abs(got - oe.Lam)) <= 1e-12 * oe.lambda_max
+    assert abs(emb.info.lambda_max - oe.lambda_max) <= 1e-12 * oe.lambda_max
+    assert abs(emb.info.lambda_min - oe.lambda_min) <= 1e-12 * oe.lambda_max
+    assert emb.info.max_imag <= 1e-11 * oe.lambda_max
+
+
+def test_not_psd_is_reported(sce):
+    with pytest.raises(sce.SceError) as ex:
+        sce.ce_setup_embedding(ocv.MATERN, 0.5, 0.3, 1.0, 32, pad_mode=oem.PAD_NONE)
+    assert ex.value.status == sce.CE_ERR_NOT_PSD
+
+
+def test_invalid_arguments(sce):
+    for args in [(ocv.MATERN, 0.7, 0.3, 1.0, 32), (ocv.MATERN, 0.5, 0.3, 1.0, 24),
+                 (ocv.MATERN, 0.5, -1.0, 1.0, 32)]:
+        with pytest.raises(sce.SceError) as ex:
+            sce.ce_setup_embedding(*args)
+        assert ex.value.status == sce.CE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1]])
+def test_smoothing_masks_match(sce, case):
+    emb0, oe = _setup_both(sce, case)
+    s, P = oe.s, oe.P
+    for keep_f, keep_c in [(s - P, s // 4 - P // 2), (1000, 37), (s // 2, -1)]:
+        emb, _ = _setup_both(sce, case, keep_f, keep_c)
+        for which, keep in ((0, keep_f), (1, keep_c)):
+            got = np.zeros(s, dtype=np.uint8)
+            sce.ce_get_mask(emb, which, got)
+            want = oem.smoothing_mask(oe.Lam, keep).ravel()
+            assert np.array_equal(got.astype(bool), want), (which, keep)
+        assert emb.info.keep_eff_fine == oem.smoothing_mask(oe.Lam, keep_f).sum()
+
+
+def _fields(sce, emb, precision, seed, level, first, count, coarse=True):
+    import torch
+    n = emb.n
+    dt = torch_dtype(precision)
+    kf = torch.empty(count, n + 1, n + 1, dtype=dt, device="cuda")
+    kc = torch.empty(count, n // 2 + 1, n // 2 + 1, dtype=dt, device="cuda") if coarse else None
+    sce.ce_sample_batch(emb, seed, level, first, count, precision, kf, kc)
+    torch.cuda.synchronize()
+    return kf.cpu().numpy(), (kc.cpu().numpy() if coarse else None)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("case", CASES)
+def test_fields_plain(sce, case, precision):
+    emb, oe = _setup_both(sce, case)
+    full = np.ones(oe.Lam.shape, dtype=bool)
+    count, seed, level, first = 5, 11, 1, 3        # ragged count, offset samples
+    kf, kc = _fields(sce, emb, precision, seed, level, first, count)
+    tol = TOL64 if precision == 64 else TOL32
+    for c in range(count):
+        okf, okc = ofield.sample_k(oe, full, full, seed, level, first + c, precision)
+        assert rel_err(kf[c], okf) < tol
+        assert rel_err(kc[c], okc) < tol
+        assert np.array_equal(kc[c], kf[c][::2, ::2])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[4]])
+def test_fields_smoothed(sce, case, precision):
+    emb0, oe = _setup_both(sce, case)
+    s, P = oe.s, oe.P
+    keep_f, keep_c = s - P, s // 4 - P // 2
+    emb, _ = _setup_both(sce, case, keep_f, keep_c)
+    mf = oem.smoothing_mask(oe.Lam, keep_f)
+    mc = oem.smoothing_mask(oe.Lam, keep_c)
+    count, seed, level, first = 3, 2, 4, 0
+    kf, kc = _fields(sce, emb, precision, seed, level, first, count)
+    tol = TOL64 if precision == 64 else TOL32
+    for c in range(count):
+        okf, okc = ofield.sample_k(oe, mf, mc, seed, level, first + c, precision)
+        assert rel_err(kf[c], okf) < tol
+        assert rel_err(kc[c], okc) < tol
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_fields_full_size_sampled(sce, precision):
+    """n = 512 with a 2048 x 2048 smooth-periodisation embedding (the finest
+    level of the oscillatory MLMC workload): two samples, all vertices."""
+    case = (ocv.MATERN, 0.5, 0.02, 1.0, 512, oem.PAD_SMOOTH)
+    emb, oe = _setup_both(sce, case)
+    assert oe.P == 2048
+    full = np.ones(oe.Lam.shape, dtype=bool)
+    kf, _ = _fields(sce, emb, precision, 2, 5, 40, 2, coarse=False)
+    tol = TOL64 if precision == 64 else TOL32
+    for c in range(2):
+        okf, _ = ofield.sample_k(oe, full, None, 2, 5, 40 + c, precision)
+        assert rel_err(kf[c], okf) < tol

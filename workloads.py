@@ -1,0 +1,61 @@
+"""Synthetic workload definitions shared by the benchmark, the tests and the
+CPU baseline.  Parameters only -- no arithmetic of the method lives here.
+
+The paper (§4) samples its random fields synthetically (no dataset); the
+workloads below follow its experiments: unit square, Matern covariance,
+levels h_l = 2^-l h_0 with the field sampled on the solve's grid.
+"""
+from dataclasses import dataclass, field
+from typing import List
+
+
+@dataclass
+class MLMCWorkload:
+    name: str
+    nu: float
+    lam: float
+    sigma2: float
+    n0: int                      # coarsest grid (cells per side)
+    N: List[int]                 # samples per level
+    pad_mode: int                # 1 = classical doubling, 2 = smooth periodisation
+    smoothing: bool              # MLMC-CES (tau_l = sqrt(s_l), finest level unsmoothed)
+    qoi: int                     # 0 outflow, 1 u(7/15, 7/15), 2 L2 norm
+    f: float
+    seed: int
+    rtol: float = 1e-10
+    kind: int = 0                # 0 Matern
+
+    @property
+    def levels(self):
+        return [(l, self.n0 << l, self.N[l]) for l in range(len(self.N))]
+
+    def describe(self):
+        ns = [self.n0 << l for l in range(len(self.N))]
+        return (f"{'MLMC-CES' if self.smoothing else 'MLMC'} Matern nu={self.nu} "
+                f"lambda={self.lam} sigma2={self.sigma2}; n={ns[0]}..{ns[-1]} "
+                f"(L={len(ns) - 1}); N_l={'/'.join(map(str, self.N))}; "
+                f"{'smooth periodisation J=n' if self.pad_mode == 2 else 'doubling'}; "
+                f"{'tau_l=sqrt(s_l), finest unsmoothed; ' if self.smoothing else ''}"
+                f"Q={['outflow', 'u(7/15,7/15)', 'L2 norm'][self.qoi]}, f={self.f}, "
+                f"rtol={self.rtol}")
+
+
+# Oscillatory field, smoothed vs plain CE MLMC (the headline workload).
+OSCILLATORY = MLMCWorkload(
+    name="mlmc_oscillatory", nu=0.5, lam=0.02, sigma2=1.0, n0=16,
+    N=[20000, 8000, 3000, 1000, 300, 100], pad_mode=2, smoothing=True, qoi=1, f=1.0, seed=2)
+
+# Plain method, small: 33 x 33 vertices, doubled embedding, outflow, f = 0.
+PLAIN_SMALL = MLMCWorkload(
+    name="plain_33x33", nu=0.5, lam=0.3, sigma2=1.0, n0=32, N=[256], pad_mode=1,
+    smoothing=False, qoi=0, f=0.0, seed=0)
+
+
+def keep_counts(P, finest, smoothing):
+    """(keep_fine, keep_coarse) for one level: tau = sqrt(s) dropped on the
+    fine field (none on the finest level), s/4 - sqrt(s/4) kept for the coarse
+    field; -1 = no truncation."""
+    if not smoothing:
+        return -1, -1
+    s = P * P
+    return (-1 if finest else s - P), (s // 4 - P // 2)
