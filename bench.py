@@ -243,7 +243,7 @@ def run_ours(args):
     def step(i, copy_y=False, record=True):
         sums = torch.zeros(len(wl.N), 5, dtype=torch.float64)
         for (l, n, N) in wl.levels:
-            first = (i * world + rank) * N
+            first = workloads.shard_first_sample(i, rank, world, N)
             out, _ = sce.mlmc_level_estimate(embs[l], wl.seed, l, first, N, qoi_index=wl.qoi,
                                              f=wl.f, rtol=wl.rtol, maxit=2000, precision=prec,
                                              Y=Ybuf[l], stream=stream.cuda_stream,

@@ -51,6 +51,13 @@ PLAIN_SMALL = MLMCWorkload(
     smoothing=False, qoi=0, f=0.0, seed=0)
 
 
+def shard_first_sample(step, rank, world, N):
+    """First sample index of `rank`'s block of N samples in step `step`: the
+    sample ranges of all (step, rank) pairs tile [0, inf) without overlap, so
+    a sharded run draws exactly the samples of a single-rank run."""
+    return (step * world + rank) * N
+
+
 def keep_counts(P, finest, smoothing):
     """(keep_fine, keep_coarse) for one level: tau = sqrt(s) dropped on the
     fine field (none on the finest level), s/4 - sqrt(s/4) kept for the coarse
