@@ -105,24 +105,27 @@ class ClockSampler:
 _ORACLE_LEVELS = None
 
 
-def _oracle_init(wl_name):
-    import numpy as np  # noqa: F401
-    from oracle import embedding as oem
+def _oracle_init(wl):
     global _ORACLE_LEVELS
-    wl = getattr(workloads, wl_name)
-    levels = {}
-    L = len(wl.N) - 1
-    for (l, n, _) in wl.levels:
-        e = oem.setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n, wl.pad_mode)
-        kf, kc = workloads.keep_counts(e.P, l == L, wl.smoothing)
-        mf = oem.smoothing_mask(e.Lam, kf)
-        mc = oem.smoothing_mask(e.Lam, kc)
-        levels[l] = (e, mf, mc)
-    _ORACLE_LEVELS = (wl, levels)
+    try:
+        from oracle import embedding as oem
+        levels = {}
+        L = len(wl.N) - 1
+        for (l, n, _) in wl.levels:
+            e = oem.setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n, wl.pad_mode)
+            kf, kc = workloads.keep_counts(e.P, l == L, wl.smoothing)
+            mf = oem.smoothing_mask(e.Lam, kf)
+            mc = oem.smoothing_mask(e.Lam, kc)
+            levels[l] = (e, mf, mc)
+        _ORACLE_LEVELS = (wl, levels)
+    except Exception as exc:  # reported by the first task instead of respawning workers
+        _ORACLE_LEVELS = exc
 
 
 def _oracle_task(task):
     from oracle import mlmc as omlmc
+    if isinstance(_ORACLE_LEVELS, Exception):
+        raise RuntimeError(f"oracle worker set-up failed: {_ORACLE_LEVELS!r}")
     wl, levels = _ORACLE_LEVELS
     l, sample = task
     e, mf, mc = levels[l]
@@ -138,7 +141,7 @@ def oracle_pool(wl):
     env_threads = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
     os.environ.update(env_threads)
     ctx = mp.get_context("spawn")
-    pool = ctx.Pool(cores, initializer=_oracle_init, initargs=(wl.name,))
+    pool = ctx.Pool(cores, initializer=_oracle_init, initargs=(wl,))
     return pool, cores
 
 

@@ -817,6 +817,9 @@ int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, doubl
     if (p->precision != 32 && p->precision != 64) return CE_ERR_INVALID_ARG;
     if (!(p->rtol > 0) || count > 65535) return CE_ERR_INVALID_ARG;
     if (count == 0) return CE_OK;
+    if (p->precision == 32 && p->n <= sce_small_max_n() && p->n <= 64)
+        return sce_darcy_small(p, (const float *)k, count, qoi, iters, status, u_out, st,
+                               max_iters_out, n_failed_out);
     if (p->precision == 64)
         return darcy_solve_t<double, double>(p, (const double *)k, count, qoi, iters, status,
                                              u_out, st, max_iters_out, n_failed_out);

@@ -1,0 +1,312 @@
+// One-block-per-sample Darcy solver for small grids (n <= 64), mixed precision.
+//
+// The same discrete problem and the same algorithm as the batched solver in
+// darcy.cu (FP64 iterative refinement around FP32 CG preconditioned with one
+// symmetric multigrid V(1,1) cycle), but the whole solve of one sample --
+// conductances, hierarchy, every CG iteration and V-cycle, the QoIs -- runs in
+// one thread block with all state in shared memory: the coefficient field is
+// read from HBM once and three doubles per sample are written back.  Many
+// independent samples in flight per SM hide the block barriers.
+#include <algorithm>
+
+#include "sce_internal.cuh"
+#include "stencil.cuh"
+
+using namespace sce;
+
+namespace {
+
+constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+template <int N> struct SmallLayout {
+    static constexpr int W = N + 1;
+    static constexpr int V = W * W;
+    static constexpr int NL = ilog2c(N);            // levels N, N/2, ..., 2
+    static constexpr int vof(int L) { return ((N >> L) + 1) * ((N >> L) + 1); }
+    static constexpr int coarse_floats() {
+        int t = 0;
+        for (int L = 1; L < NL; ++L) t += 4 * vof(L);
+        return t;
+    }
+    // doubles: u, cx64, cy64, reduction scratch (64)
+    static constexpr size_t bytes =
+        sizeof(double) * (3 * (size_t)V + 64) + sizeof(float) * (6 * (size_t)V + coarse_floats());
+};
+
+// Sum over the block, returned to every thread (fixed order).
+template <int NT>
+__device__ __forceinline__ double bsum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < NT / 32; ++i) t += sh[i];
+        sh[32] = t;
+    }
+    __syncthreads();
+    const double t = sh[32];
+    __syncthreads();
+    return t;
+}
+
+template <int N, int NT>
+__global__ void __launch_bounds__(NT) small_solve_kernel(
+    const float *__restrict__ kin, double f, double rtol2, double in_rel2, int maxit,
+    double *__restrict__ qoi, int *__restrict__ iters_out, int *__restrict__ status_out,
+    double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits) {
+    using Lay = SmallLayout<N>;
+    constexpr int W = Lay::W, V = Lay::V, NL = Lay::NL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *u = reinterpret_cast<double *>(smem_raw);
+    double *cx64 = u + V;
+    double *cy64 = cx64 + V;
+    double *sh = cy64 + V;
+    float *cx[NL], *cy[NL], *bb[NL], *zz[NL];
+    float *fp = reinterpret_cast<float *>(sh + 64);
+    cx[0] = fp;
+    cy[0] = fp + V;
+    float *d = fp + 2 * V;
+    bb[0] = fp + 3 * V;   // r (inner residual) = rhs of the level-0 cycle
+    zz[0] = fp + 4 * V;
+    float *p = fp + 5 * V;
+    float *q = fp + 6 * V;
+#pragma unroll
+    for (int L = 1; L < NL; ++L) {
+        const int VL = Lay::vof(L);
+        cx[L] = q;
+        cy[L] = q + VL;
+        bb[L] = q + 2 * VL;
+        zz[L] = q + 3 * VL;
+        q += 4 * VL;
+    }
+    float *r = bb[0], *z = zz[0];
+    const int s = blockIdx.x;
+    const int tid = threadIdx.x;
+    const float *ks = kin + (size_t)s * V;
+
+    // operator: FP64 conductances (outer residual, QoIs) and FP32 copies
+    for (int v = tid; v < V; v += NT) {
+        const int j = v / W, i = v - j * W;
+        double gx, gy;
+        cond_at(ks, i, j, N, &gx, &gy);
+        cx64[v] = gx;
+        cy64[v] = gy;
+        cx[0][v] = (float)gx;
+        cy[0][v] = (float)gy;
+        u[v] = i == 0 ? 1.0 : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int L = 1; L < NL; ++L) {
+        const int nL = N >> L, wL = nL + 1, VL = wL * wL;
+        for (int v = tid; v < VL; v += NT) {
+            const int J = v / wL, I = v - J * wL;
+            double gx, gy;
+            coarsen_at(cx[L - 1], cy[L - 1], 2 * nL, I, J, &gx, &gy);
+            cx[L][v] = (float)gx;
+            cy[L][v] = (float)gy;
+        }
+        __syncthreads();
+    }
+
+    const double h2_6 = f / (6.0 * (double)N * (double)N);
+    // FP64 residual r = F - A u into the FP32 rhs, returns |r|^2
+    auto outer_residual = [&]() {
+        double acc = 0.0;
+        for (int v = tid; v < V; v += NT) {
+            const int j = v / W, i = v - j * W;
+            double rv = 0.0;
+            if (i > 0 && i < N) {
+                rv = h2_6 * ((j == 0 || j == N) ? 3.0 : 6.0) - apply_at(cx64, cy64, u, i, j, N);
+                acc += rv * rv;
+            }
+            r[v] = (float)rv;
+        }
+        return bsum<NT>(acc, sh);
+    };
+
+    // one symmetric V(1,1) cycle: z[0] = M^-1 r
+    auto vcycle = [&]() {
+        for (int v = tid; v < V; v += NT) z[v] = 0.f;
+        __syncthreads();
+        for (int L = 0; L < NL - 1; ++L) {
+            const int nL = N >> L, wL = nL + 1, VL = wL * wL;
+            for (int c = 0; c < 2; ++c) {
+                for (int v = tid; v < VL; v += NT) {
+                    const int j = v / wL, i = v - j * wL;
+                    if (i > 0 && i < nL && ((i + j) & 1) == c) smooth_at(cx[L], cy[L], bb[L], zz[L], i, j, nL);
+                }
+                __syncthreads();
+            }
+            const int nc = nL / 2, wc = nc + 1, Vc = wc * wc;
+            for (int v = tid; v < Vc; v += NT) {
+                const int J = v / wc, I = v - J * wc;
+                bb[L + 1][v] = (I > 0 && I < nc) ? restrict_at(cx[L], cy[L], bb[L], zz[L], nL, I, J) : 0.f;
+                zz[L + 1][v] = 0.f;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) coarsest_solve(cx[NL - 1], cy[NL - 1], bb[NL - 1], zz[NL - 1]);
+        __syncthreads();
+        for (int L = NL - 2; L >= 0; --L) {
+            const int nL = N >> L, wL = nL + 1, VL = wL * wL;
+            for (int v = tid; v < VL; v += NT) {
+                const int j = v / wL, i = v - j * wL;
+                if (i > 0 && i < nL) zz[L][v] += prolong_at(zz[L + 1], nL / 2, i, j);
+            }
+            __syncthreads();
+            for (int c = 1; c >= 0; --c) {
+                for (int v = tid; v < VL; v += NT) {
+                    const int j = v / wL, i = v - j * wL;
+                    if (i > 0 && i < nL && ((i + j) & 1) == c) smooth_at(cx[L], cy[L], bb[L], zz[L], i, j, nL);
+                }
+                __syncthreads();
+            }
+        }
+    };
+
+    double orr = outer_residual();
+    const double orr0 = orr;
+    int its = 0;
+    for (int outer = 0; outer < 64 && orr > rtol2 * orr0 && its < maxit; ++outer) {
+        // inner CG (FP32) on A d = r
+        double rr0 = 0.0;
+        for (int v = tid; v < V; v += NT) {
+            d[v] = 0.f;
+            rr0 += (double)r[v] * (double)r[v];
+        }
+        rr0 = bsum<NT>(rr0, sh);
+        const double thr = fmax(in_rel2 * rr0, 0.0625 * rtol2 * orr0);
+        vcycle();
+        double rzl = 0.0;
+        for (int v = tid; v < V; v += NT) {
+            p[v] = z[v];
+            rzl += (double)r[v] * (double)z[v];
+        }
+        double rz = bsum<NT>(rzl, sh);
+        for (int it = 0; it < 40 && its < maxit; ++it) {
+            double pq = 0.0;
+            for (int v = tid; v < V; v += NT) {
+                const int j = v / W, i = v - j * W;
+                if (i > 0 && i < N) pq += (double)p[v] * (double)apply_at(cx[0], cy[0], p, i, j, N);
+            }
+            pq = bsum<NT>(pq, sh);
+            const float alpha = pq > 0.0 ? (float)(rz / pq) : 0.f;
+            double rr = 0.0;
+            for (int v = tid; v < V; v += NT) {
+                const int j = v / W, i = v - j * W;
+                if (i > 0 && i < N) {
+                    const float ap = apply_at(cx[0], cy[0], p, i, j, N);
+                    d[v] += alpha * p[v];
+                    const float rv = r[v] - alpha * ap;
+                    r[v] = rv;
+                    rr += (double)rv * (double)rv;
+                }
+            }
+            rr = bsum<NT>(rr, sh);
+            ++its;
+            if (rr <= thr) break;
+            vcycle();
+            double rzn = 0.0;
+            for (int v = tid; v < V; v += NT) rzn += (double)r[v] * (double)z[v];
+            rzn = bsum<NT>(rzn, sh);
+            const float beta = rz > 0.0 ? (float)(rzn / rz) : 0.f;
+            rz = rzn;
+            for (int v = tid; v < V; v += NT) p[v] = z[v] + beta * p[v];
+            __syncthreads();
+        }
+        for (int v = tid; v < V; v += NT) u[v] += (double)d[v];
+        __syncthreads();
+        orr = outer_residual();
+    }
+
+    // QoIs (FP64)
+    double qo = 0.0, l2 = 0.0;
+    for (int v = tid; v < V; v += NT) {
+        const int j = v / W, i = v - j * W;
+        if (i == N - 1) qo += cx64[v] * u[v];
+        if (i < N && j < N) {
+            const double a = u[v], b = u[v + 1], c = u[v + W + 1], e = u[v + W];
+            const double s1 = a + b + c, s2 = a + e + c;
+            l2 += s1 * s1 + a * a + b * b + c * c + s2 * s2 + a * a + e * e + c * c;
+        }
+        if (u_out) u_out[(size_t)s * V + v] = u[v];
+    }
+    qo = bsum<NT>(qo, sh);
+    l2 = bsum<NT>(l2, sh);
+    if (tid == 0) {
+        const double h = 1.0 / (double)N;
+        const double q_out = qo + f * h * 0.5;
+        const double q_l2 = sqrt(l2 * h * h / 24.0);
+        const double xs = 7.0 / 15.0 * (double)N, ys = 7.0 / 15.0 * (double)N;
+        const int ca = min((int)floor(xs), N - 1), cb = min((int)floor(ys), N - 1);
+        const double xi = xs - ca, et = ys - cb;
+        const double uab = u[cb * W + ca], ua1b = u[cb * W + ca + 1];
+        const double uab1 = u[(cb + 1) * W + ca], ua1b1 = u[(cb + 1) * W + ca + 1];
+        const double q_pt = xi >= et ? uab + xi * (ua1b - uab) + et * (ua1b1 - ua1b)
+                                     : uab + et * (uab1 - uab) + xi * (ua1b1 - uab1);
+        qoi[3 * s + 0] = q_out;
+        qoi[3 * s + 1] = q_pt;
+        qoi[3 * s + 2] = q_l2;
+        int st = 0;
+        if (!(fabs(q_out) < 1e300 && fabs(q_pt) < 1e300 && fabs(q_l2) < 1e300)) st = CE_ERR_NONFINITE;
+        else if (!(orr <= rtol2 * orr0)) st = CE_ERR_NOT_CONVERGED;
+        if (status_out) status_out[s] = st;
+        if (iters_out) iters_out[s] = its;
+        if (st) atomicAdd(nfail, 1);
+        atomicMax(maxits, its);
+    }
+}
+
+template <int N, int NT>
+int launch_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
+                 int *status, double *u_out, int *misc, cudaStream_t st) {
+    const size_t smem = SmallLayout<N>::bytes;
+    SCE_CUDA(cudaFuncSetAttribute(small_solve_kernel<N, NT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const double in_rel = 1e-5;
+    SceProf pr(KP_SMALL, st, (double)count * SmallLayout<N>::V * (sizeof(float) + 0.0) + 24.0 * count);
+    small_solve_kernel<N, NT><<<count, NT, smem, st>>>(k, p->f, p->rtol * p->rtol, in_rel * in_rel,
+                                                       p->maxit > 0 ? p->maxit : 1000, qoi, iters,
+                                                       status, u_out, misc, misc + 1);
+    SCE_CUDA(cudaGetLastError());
+    return CE_OK;
+}
+
+}  // namespace
+
+// Largest n solved one block per sample (SCE_SMALL_MAX_N overrides; 0 = never).
+int sce_small_max_n() {
+    const char *e = getenv("SCE_SMALL_MAX_N");
+    return e ? atoi(e) : 32;
+}
+
+int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
+                    int *status, double *u_out, cudaStream_t st, int *max_iters_out,
+                    int *n_failed_out) {
+    int *misc = nullptr;
+    SCE_TRY(sce_alloc_t(&misc, 2, st));
+    SCE_CUDA(cudaMemsetAsync(misc, 0, 2 * sizeof(int), st));
+    int rc = CE_ERR_INVALID_ARG;
+    switch (p->n) {
+        case 4: rc = launch_small<4, 32>(p, k, count, qoi, iters, status, u_out, misc, st); break;
+        case 8: rc = launch_small<8, 64>(p, k, count, qoi, iters, status, u_out, misc, st); break;
+        case 16: rc = launch_small<16, 128>(p, k, count, qoi, iters, status, u_out, misc, st); break;
+        case 32: rc = launch_small<32, 256>(p, k, count, qoi, iters, status, u_out, misc, st); break;
+        case 64: rc = launch_small<64, 512>(p, k, count, qoi, iters, status, u_out, misc, st); break;
+        default: break;
+    }
+    if (rc != CE_OK) {
+        sce_free(misc, st);
+        return rc;
+    }
+    int h[2] = {0, 0};
+    SCE_CUDA(cudaMemcpyAsync(h, misc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SCE_CUDA(cudaStreamSynchronize(st));
+    sce_free(misc, st);
+    if (n_failed_out) *n_failed_out = h[0];
+    if (max_iters_out) *max_iters_out = h[1];
+    return h[0] > 0 ? CE_ERR_NOT_CONVERGED : CE_OK;
+}

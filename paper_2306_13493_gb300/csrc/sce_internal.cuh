@@ -69,7 +69,7 @@ struct ce_embedding_s {
 enum SceKernel {
     KP_ROW = 0, KP_COL, KP_COND, KP_COARSEN, KP_SMOOTH, KP_RESTRICT, KP_PROLONG, KP_COARSEST,
     KP_SPMV, KP_AXPY, KP_DOT, KP_PUPDATE, KP_COPY, KP_REDUCE, KP_OUTER_RES, KP_OUTER_UPD, KP_QOI,
-    KP_SETUP, KP_NORMALS, KP_LEVEL, KP_COUNT_
+    KP_SETUP, KP_NORMALS, KP_LEVEL, KP_SMALL, KP_COUNT_
 };
 
 bool sce_prof_on();
@@ -86,6 +86,12 @@ struct SceProf {
 // Field path entry used by mlmc_level_estimate (same as ce_sample_batch).
 int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,
                           int count, int precision, void *k_fine, void *k_coarse, cudaStream_t st);
+
+// One-block-per-sample solver for small grids (mixed precision).
+int sce_small_max_n();
+int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
+                    int *status, double *u_out, cudaStream_t st, int *max_iters_out,
+                    int *n_failed_out);
 
 // Darcy solver entry used by mlmc_level_estimate.
 int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,

@@ -1,0 +1,151 @@
+// Per-vertex pieces of the five-point P1 operator and of the multigrid cycle,
+// shared by the grid-wide batched kernels and the one-block-per-sample solver.
+// All functions take the base pointer of one sample's array on an n-cell grid
+// (row-major, x-fastest, width n+1); they work on global or shared memory.
+#pragma once
+
+namespace sce {
+
+// Edge conductances at vertex (i, j) from the vertex values of k, in FP64:
+//   gx = cx(i,j) = 1/2 [kbar_T1(i,j) + kbar_T2(i,j-1)]   (0 if i == n)
+//   gy = cy(i,j) = 1/2 [kbar_T2(i,j) + kbar_T1(i-1,j)]   (0 if j == n)
+// T1(a,b) = {(a,b),(a+1,b),(a+1,b+1)}, T2(a,b) = {(a,b),(a,b+1),(a+1,b+1)}.
+template <typename Tk>
+__device__ __forceinline__ void cond_at(const Tk *ks, int i, int j, int n, double *gx,
+                                        double *gy) {
+    const int w = n + 1;
+    auto K = [&](int a, int b) { return (double)ks[b * w + a]; };
+    double x = 0.0, y = 0.0;
+    if (i < n) {
+        if (j < n) x += (K(i, j) + K(i + 1, j) + K(i + 1, j + 1)) / 3.0;
+        if (j > 0) x += (K(i, j - 1) + K(i, j) + K(i + 1, j)) / 3.0;
+        x *= 0.5;
+    }
+    if (j < n) {
+        if (i < n) y += (K(i, j) + K(i, j + 1) + K(i + 1, j + 1)) / 3.0;
+        if (i > 0) y += (K(i - 1, j) + K(i, j) + K(i, j + 1)) / 3.0;
+        y *= 0.5;
+    }
+    *gx = x;
+    *gy = y;
+}
+
+__device__ __forceinline__ double series_cond(double a, double b) {
+    const double t = a + b;
+    return t > 0.0 ? a * b / t : 0.0;
+}
+
+// Coarse conductances at coarse vertex (I, J): a coarse edge spans two fine
+// edges in series and stands for the fine lines 2J (weight 1), 2J +- 1 (1/2).
+template <typename T>
+__device__ __forceinline__ void coarsen_at(const T *ax, const T *ay, int nf, int I, int J,
+                                           double *gx, double *gy) {
+    const int nc = nf / 2, wf = nf + 1;
+    double x = 0.0, y = 0.0;
+    if (I < nc) {
+        auto S = [&](int j) {
+            return series_cond((double)ax[j * wf + 2 * I], (double)ax[j * wf + 2 * I + 1]);
+        };
+        x = S(2 * J);
+        if (J > 0) x += 0.5 * S(2 * J - 1);
+        if (J < nc) x += 0.5 * S(2 * J + 1);
+    }
+    if (J < nc) {
+        auto S = [&](int i) {
+            return series_cond((double)ay[(2 * J) * wf + i], (double)ay[(2 * J + 1) * wf + i]);
+        };
+        y = S(2 * I);
+        if (I > 0) y += 0.5 * S(2 * I - 1);
+        if (I < nc) y += 0.5 * S(2 * I + 1);
+    }
+    *gx = x;
+    *gy = y;
+}
+
+// (A p)(i,j) at an unknown vertex (1 <= i <= n-1).
+template <typename T>
+__device__ __forceinline__ T apply_at(const T *ax, const T *ay, const T *p, int i, int j, int n) {
+    const int w = n + 1, v = j * w + i;
+    const T pc = p[v];
+    T a = ax[v - 1] * (pc - p[v - 1]) + ax[v] * (pc - p[v + 1]);
+    if (j > 0) a += ay[v - w] * (pc - p[v - w]);
+    if (j < n) a += ay[v] * (pc - p[v + w]);
+    return a;
+}
+
+// b - A z at an unknown vertex.
+template <typename T>
+__device__ __forceinline__ T resid_at(const T *ax, const T *ay, const T *b, const T *z, int i,
+                                      int j, int n) {
+    return b[j * (n + 1) + i] - apply_at(ax, ay, z, i, j, n);
+}
+
+// Gauss-Seidel update of one unknown vertex.
+template <typename T>
+__device__ __forceinline__ void smooth_at(const T *ax, const T *ay, const T *b, T *z, int i, int j,
+                                          int n) {
+    const int w = n + 1, v = j * w + i;
+    const T cw = ax[v - 1], ce = ax[v];
+    const T cs = j > 0 ? ay[v - w] : T(0), cn = j < n ? ay[v] : T(0);
+    T acc = b[v] + cw * z[v - 1] + ce * z[v + 1];
+    if (j > 0) acc += cs * z[v - w];
+    if (j < n) acc += cn * z[v + w];
+    z[v] = acc / (cw + ce + cs + cn);
+}
+
+// Full-weighting restriction (transpose of bilinear prolongation) of the
+// fine residual to coarse unknown (I, J), 1 <= I <= nc-1.
+template <typename T>
+__device__ __forceinline__ T restrict_at(const T *ax, const T *ay, const T *b, const T *z, int nf,
+                                         int I, int J) {
+    T acc = T(0);
+    for (int dj = -1; dj <= 1; ++dj) {
+        const int j = 2 * J + dj;
+        if (j < 0 || j > nf) continue;
+        const T wy = dj == 0 ? T(1) : T(0.5);
+        for (int di = -1; di <= 1; ++di) {
+            const T wx = di == 0 ? T(1) : T(0.5);
+            acc += wx * wy * resid_at(ax, ay, b, z, 2 * I + di, j, nf);
+        }
+    }
+    return acc;
+}
+
+// Bilinear prolongation of the coarse correction to fine vertex (i, j).
+template <typename T>
+__device__ __forceinline__ T prolong_at(const T *c, int nc, int i, int j) {
+    const int wc = nc + 1;
+    const int I = i >> 1, J = j >> 1;
+    if (!(i & 1) && !(j & 1)) return c[J * wc + I];
+    if ((i & 1) && !(j & 1)) return T(0.5) * (c[J * wc + I] + c[J * wc + I + 1]);
+    if (!(i & 1) && (j & 1)) return T(0.5) * (c[J * wc + I] + c[(J + 1) * wc + I]);
+    return T(0.25) * (c[J * wc + I] + c[J * wc + I + 1] + c[(J + 1) * wc + I] +
+                      c[(J + 1) * wc + I + 1]);
+}
+
+// Exact solve on the 2-cell grid (unknowns (1, j), j = 0..2; tridiagonal in j).
+template <typename T>
+__device__ __forceinline__ void coarsest_solve(const T *ax, const T *ay, const T *b, T *z) {
+    double d[3], r[3];
+    for (int j = 0; j < 3; ++j) {
+        const int v = j * 3 + 1;
+        d[j] = (double)ax[v - 1] + (double)ax[v] + (j > 0 ? (double)ay[v - 3] : 0.0) +
+               (j < 2 ? (double)ay[v] : 0.0);
+        r[j] = (double)b[v];
+    }
+    const double o0 = -(double)ay[1], o1 = -(double)ay[4];
+    const double c0 = o0 / d[0];
+    const double r0 = r[0] / d[0];
+    const double den1 = d[1] - o0 * c0;
+    const double c1 = o1 / den1;
+    const double r1 = (r[1] - o0 * r0) / den1;
+    const double den2 = d[2] - o1 * c1;
+    const double x2 = (r[2] - o1 * r1) / den2;
+    const double x1 = r1 - c1 * x2;
+    const double x0 = r0 - c0 * x1;
+    z[1] = (T)x0;
+    z[4] = (T)x1;
+    z[7] = (T)x2;
+}
+
+}  // namespace sce

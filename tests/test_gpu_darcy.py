@@ -104,6 +104,24 @@ def test_not_converged_status(sce):
     assert np.all(it <= 1)
 
 
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64])
+def test_block_per_sample_solver_matches_batched_and_oracle(sce, n, monkeypatch):
+    """The one-block-per-sample solver (small grids) and the grid-wide batched
+    solver solve the same discrete problem: both match the oracle."""
+    k = _oracle_k(n, 5, lam=0.05, sigma2=2.0, seed=100 + n, precision=32)
+    monkeypatch.setenv("SCE_SMALL_MAX_N", "64")
+    rc1, q1, it1, st1, u1 = _solve(sce, k, 32, f=1.0)
+    monkeypatch.setenv("SCE_SMALL_MAX_N", "0")
+    rc2, q2, it2, st2, u2 = _solve(sce, k, 32, f=1.0)
+    assert rc1 == 0 and rc2 == 0 and np.all(st1 == 0) and np.all(st2 == 0)
+    for c in range(5):
+        ou, (A, F, M) = odarcy.solve(k[c].astype(np.float64), 1.0)
+        oq = odarcy.qois(ou, A, F, M)
+        for q, u in ((q1, u1), (q2, u2)):
+            assert np.max(np.abs(u[c] - ou)) < QOI_TOL
+            assert np.max(np.abs(q[c] - oq) / np.maximum(np.abs(oq), 1e-3)) < QOI_TOL
+
+
 def test_results_independent_of_batch_composition(sce):
     """A sample's result is bit-identical alone and inside a larger batch."""
     k = _oracle_k(32, 6, lam=0.05, seed=4, precision=32)
