@@ -133,6 +133,32 @@ int ce_normals(uint64_t seed, uint32_t level, uint64_t first_sample, int count, 
 int ce_sample_batch(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,
                     int count, int precision, void *k_fine, void *k_coarse, void *stream);
 
+/*
+ * ce_sample_batch_noalloc -- the same fields as ce_sample_batch, for callers
+ * that cannot allocate device memory per call: code that runs where
+ * cudaMalloc/cudaMallocAsync is not allowed or not wanted, such as inside a
+ * caller's own memory-pool or real-time budget, or a host framework that owns
+ * all device allocation.  (The paper has no counterpart: this is a property of
+ * the library, not of the method.)
+ *   - Allocates nothing: the row/column intermediate lives in one fixed
+ *     64 MiB device array inside the library (every device that loads the
+ *     library reserves it until the process exits).  Batches are processed in
+ *     chunks that fit the array; a single sample that does not fit
+ *     ((n+1)*P complex values, plus (n/2+1)*P with a distinct coarse mask, in
+ *     the chosen precision, must be <= 64 MiB) is rejected with
+ *     CE_ERR_INVALID_ARG and a message in sce_last_error().
+ *   - The first call on a device resolves the array's device address (a
+ *     cudaGetSymbolAddress call, no allocation); make that first call before
+ *     any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (other streams,
+ *     other threads) race on it and must be serialised by the caller.
+ *   - k_fine must not be NULL (k_coarse may be).  Other arguments, layouts and
+ *     errors as ce_sample_batch.
+ */
+int ce_sample_batch_noalloc(ce_embedding_t e, uint64_t seed, uint32_t level,
+                            uint64_t first_sample, int count, int precision, void *k_fine,
+                            void *k_coarse, void *stream);
+
 /* Darcy problem of §3.1, Eq. (3.1), on the n-cell grid:
  *   -div(k grad u) = f, u = 1 at x1 = 0, u = 0 at x1 = 1, zero flux at x2 = 0, 1;
  * P1 elements with nodal quadrature (§3.2; each cell split by the diagonal

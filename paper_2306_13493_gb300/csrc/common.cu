@@ -18,6 +18,11 @@ void sce_set_last_cuda_error(cudaError_t err, const char *what, const char *file
 
 extern "C" const char *sce_last_error(void) { return g_last_error; }
 
+void sce_set_last_error_text(const char *text) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s", text);
+    if (getenv("SCE_VERBOSE")) fprintf(stderr, "[sce] %s\n", g_last_error);
+}
+
 static std::mutex g_pool_mu;
 static bool g_pool_configured[64];
 
@@ -117,6 +122,19 @@ static int twiddles(int P, double2 **d64, float2 **d32) {
     g_tw[{dev, P}] = {a, b};
     *d64 = a;
     *d32 = b;
+    return CE_OK;
+}
+
+// Lookup only: the tables of P on the current device if they were built
+// (every embedding set-up builds its P's tables); never allocates.
+int sce_twiddles_lookup(int P, const double2 **d64, const float2 **d32) {
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto it = g_tw.find({dev, P});
+    if (it == g_tw.end()) return CE_ERR_INVALID_ARG;
+    *d64 = it->second.first;
+    *d32 = it->second.second;
     return CE_OK;
 }
 

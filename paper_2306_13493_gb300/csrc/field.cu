@@ -17,6 +17,7 @@
 //                (1/sqrt(s) = 1/P), k = exp(u) written x-fastest; the plain
 //                coarse field is the fine field at even vertices.
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -658,4 +659,109 @@ extern "C" int ce_sample_batch(ce_embedding_t e, uint64_t seed, uint32_t level,
                                void *k_coarse, void *stream) {
     return sce_sample_batch_impl(e, seed, level, first_sample, count, precision, k_fine, k_coarse,
                                  as_stream(stream));
+}
+
+// ------------------------------------------------------------------ no-allocation variant
+// The row/column intermediate of ce_sample_batch_noalloc lives in this fixed
+// device array instead of memory allocated per call.  Every device that loads
+// the library reserves it until the process exits.
+static constexpr size_t kStaticScratchBytes = 64ull << 20;
+static __device__ __align__(256) unsigned char g_field_scratch[kStaticScratchBytes];
+
+static std::mutex g_scratch_mu;
+static void *g_scratch_addr[128];
+
+// Device address of g_field_scratch on the current device, resolved once per
+// device (host code must not use the symbol itself as a pointer).
+static int static_scratch(void **out) {
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return CE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        SCE_CUDA(cudaGetSymbolAddress(&p, g_field_scratch));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return CE_OK;
+}
+
+template <typename R>
+static int sample_batch_static_t(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first,
+                                 int count, R *kf, R *kc, unsigned char *scratch,
+                                 cudaStream_t st) {
+    using R2 = typename C2<R>::T;
+    const double2 *tw64 = nullptr;
+    const float2 *tw32 = nullptr;
+    SCE_TRY(sce_twiddles_lookup(e->P, &tw64, &tw32));
+    const R2 *tw;
+    if constexpr (sizeof(R) == 8) tw = tw64;
+    else tw = tw32;
+    const int P = e->P, m = e->n, mc = m / 2;
+    const bool masked = e->coarse_distinct && kc != nullptr;
+    const size_t yf = (size_t)(m + 1) * P * sizeof(R2);
+    const size_t yc = masked ? (size_t)(mc + 1) * P * sizeof(R2) : 0;
+    const size_t per_sample = ((yf + 255) & ~(size_t)255) + ((yc + 255) & ~(size_t)255);
+    if (per_sample > kStaticScratchBytes) {
+        char msg[256];
+        snprintf(msg, sizeof(msg),
+                 "ce_sample_batch_noalloc: one sample needs %zu bytes of scratch (n=%d, P=%d, "
+                 "precision %d), above the fixed %zu-byte array",
+                 per_sample, m, P, (int)(8 * sizeof(R)), kStaticScratchBytes);
+        sce_set_last_error_text(msg);
+        return CE_ERR_INVALID_ARG;
+    }
+    const int chunk = (int)std::min<size_t>({(size_t)count, kStaticScratchBytes / per_sample,
+                                             (size_t)65535});
+    R2 *Yf = reinterpret_cast<R2 *>(scratch);
+    R2 *Yc = masked ? reinterpret_cast<R2 *>(scratch + (((size_t)chunk * yf + 255) & ~(size_t)255))
+                    : nullptr;
+    const LineCfg rc = line_cfg<R>(P, masked ? P : P / 2);
+    const LineCfg cc = line_cfg<R>(P, m + 1);
+    const LineCfg ccc = line_cfg<R>(P, mc + 1);
+    int rcode = CE_OK;
+    for (int c0 = 0; c0 < count && rcode == CE_OK; c0 += chunk) {
+        const int cn = std::min(chunk, count - c0);
+        R *kf_c = kf + (size_t)c0 * (m + 1) * (m + 1);
+        R *kc_c = kc ? kc + (size_t)c0 * (mc + 1) * (mc + 1) : nullptr;
+        if (rc.maxb == 4)
+            rcode = launch_row<R, 4>(e, masked, tw, seed, level, first + c0, cn, Yf, Yc, rc, st);
+        else
+            rcode = launch_row<R, 8>(e, masked, tw, seed, level, first + c0, cn, Yf, Yc, rc, st);
+        if (rcode != CE_OK) break;
+        R *kcp = masked ? nullptr : kc_c;
+        if (cc.maxb == 4)
+            rcode = launch_col<R, 4>(e, Yf, m + 1, 0, tw, cn, kf_c, kcp, cc, st);
+        else
+            rcode = launch_col<R, 8>(e, Yf, m + 1, 0, tw, cn, kf_c, kcp, cc, st);
+        if (rcode != CE_OK) break;
+        if (masked) {
+            if (ccc.maxb == 4)
+                rcode = launch_col<R, 4>(e, Yc, mc + 1, 1, tw, cn, kc_c, nullptr, ccc, st);
+            else
+                rcode = launch_col<R, 8>(e, Yc, mc + 1, 1, tw, cn, kc_c, nullptr, ccc, st);
+        }
+    }
+    return rcode;
+}
+
+extern "C" int ce_sample_batch_noalloc(ce_embedding_t e, uint64_t seed, uint32_t level,
+                                       uint64_t first_sample, int count, int precision,
+                                       void *k_fine, void *k_coarse, void *stream) {
+    if (!e || count < 0 || (precision != 32 && precision != 64) || !k_fine)
+        return CE_ERR_INVALID_ARG;
+    if (count == 0) return CE_OK;
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    if (dev != e->device) return CE_ERR_INVALID_ARG;
+    void *scratch = nullptr;
+    SCE_TRY(static_scratch(&scratch));
+    cudaStream_t st = as_stream(stream);
+    if (precision == 64)
+        return sample_batch_static_t<double>(e, seed, level, first_sample, count,
+                                             (double *)k_fine, (double *)k_coarse,
+                                             (unsigned char *)scratch, st);
+    return sample_batch_static_t<float>(e, seed, level, first_sample, count, (float *)k_fine,
+                                        (float *)k_coarse, (unsigned char *)scratch, st);
 }

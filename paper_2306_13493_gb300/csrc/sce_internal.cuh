@@ -47,6 +47,10 @@ static inline int sce_alloc_t(T **p, size_t count, cudaStream_t st) {
 // Twiddle tables exp(+2 pi i k / P), k = 0..P-1, built once per P and device.
 const double2 *sce_twiddles64(int P, int *status);
 const float2 *sce_twiddles32(int P, int *status);
+// Lookup of already built tables (never allocates); CE_ERR_INVALID_ARG if absent.
+int sce_twiddles_lookup(int P, const double2 **d64, const float2 **d32);
+// Sets the text returned by sce_last_error().
+void sce_set_last_error_text(const char *text);
 
 struct ce_embedding_s {
     int device;

@@ -76,6 +76,9 @@ _SIGS = {
                                   ctypes.c_longlong, ctypes.c_int, _P, _P]),
     "ce_sample_batch": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                        ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "ce_sample_batch_noalloc": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32,
+                                               ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _P,
+                                               _P, _P]),
     "darcy_solve_batch": (ctypes.c_int, [ctypes.POINTER(darcy_problem), _P, ctypes.c_int, _P, _P,
                                          _P, _P, _P]),
     "mlmc_level_estimate": (ctypes.c_int, [_P, ctypes.POINTER(darcy_problem), ctypes.c_uint64,
@@ -213,6 +216,14 @@ def ce_sample_batch(emb, seed, level, first_sample, count, precision, k_fine=Non
     _check(load().ce_sample_batch(emb.handle, seed, level, first_sample, count, precision,
                                   _ptr(k_fine), _ptr(k_coarse), _stream(stream, t)),
            "ce_sample_batch")
+
+
+def ce_sample_batch_noalloc(emb, seed, level, first_sample, count, precision, k_fine,
+                            k_coarse=None, stream=None):
+    """ce_sample_batch without any device allocation (fixed internal scratch)."""
+    _check(load().ce_sample_batch_noalloc(emb.handle, seed, level, first_sample, count,
+                                          precision, _ptr(k_fine), _ptr(k_coarse),
+                                          _stream(stream, k_fine)), "ce_sample_batch_noalloc")
 
 
 def darcy_solve_batch(n, k, count, qoi, f=0.0, rtol=1e-10, maxit=1000, precision=32, iters=None,
