@@ -47,7 +47,48 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="multiply the per-level sample counts (tests only)")
+    ap.add_argument("--case", default=None, choices=[None, "darcy", "field"],
+                    help="time one kernel family on one batch (profiling driver)")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--count", type=int, default=64)
     return ap.parse_args()
+
+
+def run_case(args):
+    """One batch of the oscillatory field at n cells: fields, then one Darcy
+    solve (the small, fixed launch sequence used for kernel captures)."""
+    import torch
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    sce.load()
+    wl = workloads.OSCILLATORY
+    n, count, prec = args.n, args.count, args.precision
+    emb = sce.ce_setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n, pad_mode=wl.pad_mode)
+    dt = torch.float32 if prec == 32 else torch.float64
+    k = torch.empty(count, n + 1, n + 1, dtype=dt, device="cuda")
+    qoi = torch.empty(count, 3, dtype=torch.float64, device="cuda")
+    iters = torch.empty(count, dtype=torch.int32, device="cuda")
+    times = []
+    for rep in range(1 + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if args.case == "field":
+            sce.ce_sample_batch(emb, wl.seed, 0, rep * count, count, prec, k)
+        else:
+            if rep == 0:
+                sce.ce_sample_batch(emb, wl.seed, 0, 0, count, prec, k)
+            sce.darcy_solve_batch(n, k, count, qoi, f=wl.f, rtol=wl.rtol, precision=prec,
+                                  iters=iters, allow_not_converged=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep > 0:
+            times.append(e0.elapsed_time(e1))
+    it = iters.cpu().numpy()
+    print(json.dumps({"case": args.case, "n": n, "count": count, "precision": prec,
+                      "ms": statistics.mean(times) if times else None,
+                      "iters_mean": float(it.mean()), "iters_max": int(it.max())}), flush=True)
+    emb.close()
+    return 0
 
 
 # ------------------------------------------------------------------ clocks
@@ -242,6 +283,8 @@ def run_ours(args):
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     sums_acc = np.zeros((len(wl.N), 5))
     iters_max = [0] * len(wl.N)
+    iters_tot = [0] * len(wl.N)
+    solves = [0] * len(wl.N)
 
     def step(i, copy_y=False, record=True):
         sums = torch.zeros(len(wl.N), 5, dtype=torch.float64)
@@ -253,6 +296,9 @@ def run_ours(args):
                                              allow_not_converged=True)
             sums[l] = torch.tensor([out.N, out.sumY, out.sumY2, out.sumQf, out.sumQf2])
             iters_max[l] = max(iters_max[l], out.max_iters)
+            if record:
+                iters_tot[l] += out.total_iters
+                solves[l] += N * (2 if l > 0 else 1)
             if copy_y:
                 Yhost[l].copy_(Ybuf[l], non_blocking=True)
         if world > 1:
@@ -354,7 +400,8 @@ def run_ours(args):
         qm = q1 / Nn
         qv = (q2 - Nn * qm * qm) / (Nn - 1)
         per_level.append({"level": l, "n": n, "N": N, "mean_Y": mean, "var_Y": var,
-                          "var_Qf": qv, "max_iters": iters_max[l]})
+                          "var_Qf": qv, "max_iters": iters_max[l],
+                          "mean_iters": round(iters_tot[l] / max(1, solves[l]), 2)})
 
     # plain FP64 per-sample path (batch 1, FP64 field and solver), bounded sample
     fp64 = None
@@ -410,6 +457,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

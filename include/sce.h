@@ -196,7 +196,8 @@ typedef struct {
     long long N;
     double sumY, sumY2, sumQf, sumQf2;
     int n_failed;
-    int max_iters;
+    int max_iters;          /* largest iteration count of one solve          */
+    long long total_iters;  /* iterations summed over all fine + coarse solves */
 } mlmc_level_sums;
 
 /*

@@ -29,11 +29,15 @@
 #include <cmath>
 #include <vector>
 
+#include "mg_tiles.cuh"
 #include "sce_internal.cuh"
+
+using namespace sce;
 
 namespace {
 
 constexpr int MAXLEV = 14;
+constexpr int TAIL_N = 32;   // levels with n <= TAIL_N run in one block per sample
 
 struct Launch {
     int tpb, vpt, epb, nblk;
@@ -85,18 +89,8 @@ __global__ void cond_kernel(const Tk *__restrict__ k, int n, int vpt, T *__restr
     const int w = n + 1;
     FOR_VERT(V, vpt) {
         const int j = v / w, i = v - j * w;
-        auto K = [&](int a, int b) { return (double)ks[b * w + a]; };
-        double gx = 0.0, gy = 0.0;
-        if (i < n) {
-            if (j < n) gx += (K(i, j) + K(i + 1, j) + K(i + 1, j + 1)) / 3.0;        // T1(i,j)
-            if (j > 0) gx += (K(i, j - 1) + K(i, j) + K(i + 1, j)) / 3.0;            // T2(i,j-1)
-            gx *= 0.5;
-        }
-        if (j < n) {
-            if (i < n) gy += (K(i, j) + K(i, j + 1) + K(i + 1, j + 1)) / 3.0;        // T2(i,j)
-            if (i > 0) gy += (K(i - 1, j) + K(i, j) + K(i, j + 1)) / 3.0;            // T1(i-1,j)
-            gy *= 0.5;
-        }
+        double gx, gy;
+        cond_at(ks, i, j, n, &gx, &gy);
         cx[s * V + v] = (T)gx;
         cy[s * V + v] = (T)gy;
         if (cx64) {
@@ -106,13 +100,6 @@ __global__ void cond_kernel(const Tk *__restrict__ k, int n, int vpt, T *__restr
     }
 }
 
-__device__ __forceinline__ double series(double a, double b) {
-    const double t = a + b;
-    return t > 0.0 ? a * b / t : 0.0;
-}
-
-// Coarse conductances: a coarse horizontal edge spans two fine edges in
-// series; it stands for the fine rows 2J (weight 1) and 2J +- 1 (weight 1/2).
 template <typename T>
 __global__ void coarsen_kernel(const T *__restrict__ cxf, const T *__restrict__ cyf, int nf,
                                int vpt, T *__restrict__ cxc, T *__restrict__ cyc) {
@@ -120,24 +107,13 @@ __global__ void coarsen_kernel(const T *__restrict__ cxf, const T *__restrict__ 
     const int nc = nf / 2;
     const long long Vf = (long long)(nf + 1) * (nf + 1), Vc = (long long)(nc + 1) * (nc + 1);
     const T *ax = cxf + s * Vf, *ay = cyf + s * Vf;
-    const int wf = nf + 1, wc = nc + 1;
+    const int wc = nc + 1;
     FOR_VERT(Vc, vpt) {
         const int J = v / wc, I = v - J * wc;
-        double gx = 0.0, gy = 0.0;
-        if (I < nc) {
-            auto S = [&](int j) { return series((double)ax[j * wf + 2 * I], (double)ax[j * wf + 2 * I + 1]); };
-            gx = S(2 * J);
-            if (J > 0) gx += 0.5 * S(2 * J - 1);
-            if (J < nc) gx += 0.5 * S(2 * J + 1);
-        }
-        if (J < nc) {
-            auto Sy = [&](int i) { return series((double)ay[(2 * J) * wf + i], (double)ay[(2 * J + 1) * wf + i]); };
-            gy = Sy(2 * I);
-            if (I > 0) gy += 0.5 * Sy(2 * I - 1);
-            if (I < nc) gy += 0.5 * Sy(2 * I + 1);
-        }
-        cxc[s * Vc + v] = (T)gx;
-        cyc[s * Vc + v] = (T)gy;
+        T gx, gy;
+        coarsen_at(ax, ay, nf, I, J, &gx, &gy);
+        cxc[s * Vc + v] = gx;
+        cyc[s * Vc + v] = gy;
     }
 }
 
@@ -162,18 +138,6 @@ __global__ void smooth_kernel(const T *__restrict__ cx, const T *__restrict__ cy
         if (j < n) acc += cn * zs[v + w];
         zs[v] = acc / (cw + ce + cs + cn);
     }
-}
-
-// fine residual r = b - A z at an unknown vertex (i in 1..n-1)
-template <typename T>
-__device__ __forceinline__ T resid_at(const T *ax, const T *ay, const T *bs, const T *zs, int i,
-                                      int j, int n) {
-    const int w = n + 1, v = j * w + i;
-    const T zc = zs[v];
-    T Az = ax[v - 1] * (zc - zs[v - 1]) + ax[v] * (zc - zs[v + 1]);
-    if (j > 0) Az += ay[v - w] * (zc - zs[v - w]);
-    if (j < n) Az += ay[v] * (zc - zs[v + w]);
-    return bs[v] - Az;
 }
 
 template <typename T>
@@ -532,16 +496,32 @@ __global__ void qoi_final_kernel(const double *__restrict__ part_out,
     if (st != 0) atomicAdd(nfail, 1);
 }
 
+// out[0] = max, out[1] = sum of a[0..count)
 __global__ void max_int_kernel(const int *__restrict__ a, int count, int *__restrict__ out) {
-    int m = 0;
-    for (int i = threadIdx.x; i < count; i += blockDim.x) m = max(m, a[i]);
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
-    __shared__ int sh[32];
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    int m = 0, t = 0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        m = max(m, a[i]);
+        t += a[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+        t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    __shared__ int sh[32], sh2[32];
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5] = m;
+        sh2[threadIdx.x >> 5] = t;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 0; i < (blockDim.x + 31) / 32; ++i) m = max(m, sh[i]);
-        *out = m;
+        m = 0;
+        t = 0;
+        for (int i = 0; i < (blockDim.x + 31) / 32; ++i) {
+            m = max(m, sh[i]);
+            t += sh2[i];
+        }
+        out[0] = m;
+        out[1] = t;
     }
 }
 
@@ -606,11 +586,77 @@ struct Solver {
         smooth(L, 0);
     }
 
-    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0) {
+    // ---- fused cycle: tiled down/up kernels above the tail, one block per
+    // sample for the levels n <= TAIL_N
+    bool fused = true;
+    bool tile_attr_set = false;
+    int Lt = 0;                 // first level of the tail
+    int tiles_x[MAXLEV], tiles_n[MAXLEV];
+
+    void plan_fused() {
+        Lt = 0;
+        while (n[Lt] > TAIL_N) ++Lt;
+        for (int L = 0; L < Lt; ++L) {
+            const int nc1 = n[L] / 2 + 1;
+            tiles_x[L] = (nc1 + MG_CW - 1) / MG_CW;
+            tiles_n[L] = tiles_x[L] * ((nc1 + MG_CH - 1) / MG_CH);
+        }
+    }
+
+    // partial-sum slots per sample written by vcycle_fused(want_rz = true)
+    int rz_blocks() const { return Lt == 0 ? 1 : tiles_n[0]; }
+
+    template <int NTN, int NTHR>
+    void tail_launch(bool want_rz) {
+        TailPtrs tp{};
+        for (int i = 0; Lt + i < nlev && i < 8; ++i) {
+            tp.cx[i] = cx[Lt + i];
+            tp.cy[i] = cy[Lt + i];
+        }
+        constexpr size_t smem = tail_smem_bytes<T, NTN>();
+        cudaFuncSetAttribute(mg_tail_kernel<T, NTN, NTHR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        SceProf pr(KP_MG_TAIL, st, (double)count * (smem + 2 * sizeof(T) * ln[Lt].V));
+        mg_tail_kernel<T, NTN, NTHR><<<count, NTHR, smem, st>>>(tp, b[Lt], z[Lt], sc.act_in,
+                                                                want_rz ? part : nullptr);
+    }
+
+    // z[0] = M^{-1} b[0]; with want_rz the partial sums of b[0] . z[0] go to part
+    void vcycle_fused(bool want_rz) {
+        constexpr size_t smem = mg_tile_smem_bytes<T>();
+        if (!tile_attr_set) {
+            cudaFuncSetAttribute(mg_down_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            cudaFuncSetAttribute(mg_up_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            tile_attr_set = true;
+        }
+        for (int L = 0; L < Lt; ++L) {
+            SceProf pr(KP_MG_DOWN, st, vb(L, 4.0) + vb(L + 1, 1.0));
+            mg_down_kernel<T><<<dim3(tiles_n[L], count), MG_THREADS, smem, st>>>(
+                cx[L], cy[L], b[L], z[L], n[L], b[L + 1], tiles_x[L], sc.act_in);
+        }
+        const bool rz_tail = want_rz && Lt == 0;
+        switch (n[Lt]) {
+            case 32: tail_launch<32, 256>(rz_tail); break;
+            case 16: tail_launch<16, 128>(rz_tail); break;
+            case 8: tail_launch<8, 64>(rz_tail); break;
+            default: tail_launch<4, 32>(rz_tail); break;
+        }
+        for (int L = Lt - 1; L >= 0; --L) {
+            SceProf pr(KP_MG_UP, st, vb(L, 5.0) + vb(L + 1, 1.0));
+            mg_up_kernel<T><<<dim3(tiles_n[L], count), MG_THREADS, smem, st>>>(
+                cx[L], cy[L], b[L], z[L], n[L], z[L + 1], tiles_x[L], sc.act_in,
+                (want_rz && L == 0) ? part : nullptr, tiles_n[0]);
+        }
+    }
+
+    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0, int nblk = -1) {
         const int threads = 256;
         const int blocks = (count * 32 + threads - 1) / threads;
-        SceProf pr(KP_REDUCE, st, (double)count * ln[0].nblk * 8.0);
-        reduce_kernel<<<blocks, threads, 0, st>>>(part, ln[0].nblk, count, mode, sc, act, rtol2,
+        if (nblk < 0) nblk = ln[0].nblk;
+        SceProf pr(KP_REDUCE, st, (double)count * nblk * 8.0);
+        reduce_kernel<<<blocks, threads, 0, st>>>(part, nblk, count, mode, sc, act, rtol2,
                                                   in_rel2);
     }
 
@@ -658,8 +704,14 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         SCE_TRY(S.alloc(&S.cx64, c0));
         SCE_TRY(S.alloc(&S.cy64, c0));
     }
-    SCE_TRY(S.alloc(&S.part, (size_t)count * S.ln[0].nblk));
-    SCE_TRY(S.alloc(&S.part2, (size_t)count * S.ln[0].nblk));
+    {
+        const char *e = getenv("SCE_MG_FUSED");
+        S.fused = !(e && atoi(e) == 0);
+    }
+    S.plan_fused();
+    const int nblk_part = std::max(S.ln[0].nblk, S.rz_blocks());
+    SCE_TRY(S.alloc(&S.part, (size_t)count * nblk_part));
+    SCE_TRY(S.alloc(&S.part2, (size_t)count * nblk_part));
     double *scal = nullptr;
     SCE_TRY(S.alloc(&scal, (size_t)count * 9));
     S.sc.rz = scal;
@@ -722,18 +774,20 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     for (int outer = 0; outer < 64 && n_act > 0 && total_inner < maxit; ++outer) {
         // inner PCG on the correction equation, samples with act_in set
         SCE_CUDA(cudaMemsetAsync(S.d, 0, c0 * sizeof(T), st));
-        SCE_CUDA(cudaMemsetAsync(S.z[0], 0, c0 * sizeof(T), st));
-        S.vcycle(0);
-        {
-            SceProf pr(KP_COPY, st, S.vb(0, 2.0));
-            copy_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], n0, l0.vpt, S.sc.act_in);
-        }
-        {
+        if (S.fused) {
+            S.vcycle_fused(true);
+        } else {
+            SCE_CUDA(cudaMemsetAsync(S.z[0], 0, c0 * sizeof(T), st));
+            S.vcycle(0);
             SceProf pr(KP_DOT, st, S.vb(0, 2.0));
             dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.z[0], n0, l0.vpt, S.part, l0.nblk,
                                                  S.sc.act_in);
         }
-        S.reduce(RED_RZ0, S.sc.act_in);
+        {
+            SceProf pr(KP_COPY, st, S.vb(0, 2.0));
+            copy_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], n0, l0.vpt, S.sc.act_in);
+        }
+        S.reduce(RED_RZ0, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
         int in_act = n_act;
         for (int it = 0; it < inner_max && in_act > 0 && total_inner < maxit; ++it) {
             {
@@ -754,14 +808,16 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
                 SCE_TRY(S.read_counter(&in_act));
                 if (in_act == 0) break;
             }
-            SCE_CUDA(cudaMemsetAsync(S.z[0], 0, c0 * sizeof(T), st));
-            S.vcycle(0);
-            {
+            if (S.fused) {
+                S.vcycle_fused(true);
+            } else {
+                SCE_CUDA(cudaMemsetAsync(S.z[0], 0, c0 * sizeof(T), st));
+                S.vcycle(0);
                 SceProf pr(KP_DOT, st, S.vb(0, 2.0));
                 dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.z[0], n0, l0.vpt, S.part, l0.nblk,
                                                      S.sc.act_in);
             }
-            S.reduce(RED_BETA, S.sc.act_in);
+            S.reduce(RED_BETA, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
             {
                 SceProf pr(KP_PUPDATE, st, S.vb(0, 3.0));
                 pupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], S.sc.beta, n0, l0.vpt,
@@ -799,11 +855,14 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     SCE_CUDA(cudaGetLastError());
     if (u_out)
         SCE_CUDA(cudaMemcpyAsync(u_out, S.u64, c0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    int hm[2] = {0, 0};
-    SCE_CUDA(cudaMemcpyAsync(hm, S.misc + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hm[3] = {0, 0, 0};
+    SCE_CUDA(cudaMemcpyAsync(hm, S.misc + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     SCE_CUDA(cudaStreamSynchronize(st));
     if (n_failed_out) *n_failed_out = hm[0];
-    if (max_iters_out) *max_iters_out = hm[1];
+    if (max_iters_out) {
+        max_iters_out[0] = hm[1];
+        max_iters_out[1] = hm[2];
+    }
     return hm[0] > 0 ? CE_ERR_NOT_CONVERGED : CE_OK;
 }
 

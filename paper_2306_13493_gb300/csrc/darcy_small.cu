@@ -9,6 +9,7 @@
 // independent samples in flight per SM hide the block barriers.
 #include <algorithm>
 
+#include "block_mg.cuh"
 #include "sce_internal.cuh"
 #include "stencil.cuh"
 
@@ -47,6 +48,24 @@ __device__ __forceinline__ double bsum(double v, double *sh) {
     }
     __syncthreads();
     const double t = sh[32];
+    __syncthreads();
+    return t;
+}
+
+// FP32 version (the inner Krylov scalars), fixed order, returned to all threads.
+template <int NT>
+__device__ __forceinline__ float bsumf(float v, float *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int i = 0; i < NT / 32; ++i) t += sh[i];
+        sh[31] = t;
+    }
+    __syncthreads();
+    const float t = sh[31];
     __syncthreads();
     return t;
 }
@@ -103,10 +122,10 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
         const int nL = N >> L, wL = nL + 1, VL = wL * wL;
         for (int v = tid; v < VL; v += NT) {
             const int J = v / wL, I = v - J * wL;
-            double gx, gy;
+            float gx, gy;
             coarsen_at(cx[L - 1], cy[L - 1], 2 * nL, I, J, &gx, &gy);
-            cx[L][v] = (float)gx;
-            cy[L][v] = (float)gy;
+            cx[L][v] = gx;
+            cy[L][v] = gy;
         }
         __syncthreads();
     }
@@ -128,73 +147,37 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
     };
 
     // one symmetric V(1,1) cycle: z[0] = M^-1 r
-    auto vcycle = [&]() {
-        for (int v = tid; v < V; v += NT) z[v] = 0.f;
-        __syncthreads();
-        for (int L = 0; L < NL - 1; ++L) {
-            const int nL = N >> L, wL = nL + 1, VL = wL * wL;
-            for (int c = 0; c < 2; ++c) {
-                for (int v = tid; v < VL; v += NT) {
-                    const int j = v / wL, i = v - j * wL;
-                    if (i > 0 && i < nL && ((i + j) & 1) == c) smooth_at(cx[L], cy[L], bb[L], zz[L], i, j, nL);
-                }
-                __syncthreads();
-            }
-            const int nc = nL / 2, wc = nc + 1, Vc = wc * wc;
-            for (int v = tid; v < Vc; v += NT) {
-                const int J = v / wc, I = v - J * wc;
-                bb[L + 1][v] = (I > 0 && I < nc) ? restrict_at(cx[L], cy[L], bb[L], zz[L], nL, I, J) : 0.f;
-                zz[L + 1][v] = 0.f;
-            }
-            __syncthreads();
-        }
-        if (tid == 0) coarsest_solve(cx[NL - 1], cy[NL - 1], bb[NL - 1], zz[NL - 1]);
-        __syncthreads();
-        for (int L = NL - 2; L >= 0; --L) {
-            const int nL = N >> L, wL = nL + 1, VL = wL * wL;
-            for (int v = tid; v < VL; v += NT) {
-                const int j = v / wL, i = v - j * wL;
-                if (i > 0 && i < nL) zz[L][v] += prolong_at(zz[L + 1], nL / 2, i, j);
-            }
-            __syncthreads();
-            for (int c = 1; c >= 0; --c) {
-                for (int v = tid; v < VL; v += NT) {
-                    const int j = v / wL, i = v - j * wL;
-                    if (i > 0 && i < nL && ((i + j) & 1) == c) smooth_at(cx[L], cy[L], bb[L], zz[L], i, j, nL);
-                }
-                __syncthreads();
-            }
-        }
-    };
+    auto vcycle = [&]() { block_vcycle<float, N, NT>(cx, cy, bb, zz, NL); };
 
     double orr = outer_residual();
     const double orr0 = orr;
+    float *shf = reinterpret_cast<float *>(sh + 48);
     int its = 0;
     for (int outer = 0; outer < 64 && orr > rtol2 * orr0 && its < maxit; ++outer) {
-        // inner CG (FP32) on A d = r
-        double rr0 = 0.0;
+        // inner CG on A d = r, entirely in FP32 (dot products included)
+        float rr0 = 0.f;
         for (int v = tid; v < V; v += NT) {
             d[v] = 0.f;
-            rr0 += (double)r[v] * (double)r[v];
+            rr0 += r[v] * r[v];
         }
-        rr0 = bsum<NT>(rr0, sh);
-        const double thr = fmax(in_rel2 * rr0, 0.0625 * rtol2 * orr0);
+        rr0 = bsumf<NT>(rr0, shf);
+        const float thr = (float)fmax(in_rel2 * (double)rr0, 0.0625 * rtol2 * orr0);
         vcycle();
-        double rzl = 0.0;
+        float rz = 0.f;
         for (int v = tid; v < V; v += NT) {
             p[v] = z[v];
-            rzl += (double)r[v] * (double)z[v];
+            rz += r[v] * z[v];
         }
-        double rz = bsum<NT>(rzl, sh);
+        rz = bsumf<NT>(rz, shf);
         for (int it = 0; it < 40 && its < maxit; ++it) {
-            double pq = 0.0;
+            float pq = 0.f;
             for (int v = tid; v < V; v += NT) {
                 const int j = v / W, i = v - j * W;
-                if (i > 0 && i < N) pq += (double)p[v] * (double)apply_at(cx[0], cy[0], p, i, j, N);
+                if (i > 0 && i < N) pq += p[v] * apply_at(cx[0], cy[0], p, i, j, N);
             }
-            pq = bsum<NT>(pq, sh);
-            const float alpha = pq > 0.0 ? (float)(rz / pq) : 0.f;
-            double rr = 0.0;
+            pq = bsumf<NT>(pq, shf);
+            const float alpha = pq > 0.f ? rz / pq : 0.f;
+            float rr = 0.f;
             for (int v = tid; v < V; v += NT) {
                 const int j = v / W, i = v - j * W;
                 if (i > 0 && i < N) {
@@ -202,17 +185,17 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
                     d[v] += alpha * p[v];
                     const float rv = r[v] - alpha * ap;
                     r[v] = rv;
-                    rr += (double)rv * (double)rv;
+                    rr += rv * rv;
                 }
             }
-            rr = bsum<NT>(rr, sh);
+            rr = bsumf<NT>(rr, shf);
             ++its;
             if (rr <= thr) break;
             vcycle();
-            double rzn = 0.0;
-            for (int v = tid; v < V; v += NT) rzn += (double)r[v] * (double)z[v];
-            rzn = bsum<NT>(rzn, sh);
-            const float beta = rz > 0.0 ? (float)(rzn / rz) : 0.f;
+            float rzn = 0.f;
+            for (int v = tid; v < V; v += NT) rzn += r[v] * z[v];
+            rzn = bsumf<NT>(rzn, shf);
+            const float beta = rz > 0.f ? rzn / rz : 0.f;
             rz = rzn;
             for (int v = tid; v < V; v += NT) p[v] = z[v] + beta * p[v];
             __syncthreads();
@@ -257,6 +240,7 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
         if (iters_out) iters_out[s] = its;
         if (st) atomicAdd(nfail, 1);
         atomicMax(maxits, its);
+        atomicAdd(maxits + 1, its);
     }
 }
 
@@ -286,9 +270,9 @@ int sce_small_max_n() {
 int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
                     int *status, double *u_out, cudaStream_t st, int *max_iters_out,
                     int *n_failed_out) {
-    int *misc = nullptr;
-    SCE_TRY(sce_alloc_t(&misc, 2, st));
-    SCE_CUDA(cudaMemsetAsync(misc, 0, 2 * sizeof(int), st));
+    int *misc = nullptr;   // [0] failed samples, [1] max iterations, [2] total iterations
+    SCE_TRY(sce_alloc_t(&misc, 3, st));
+    SCE_CUDA(cudaMemsetAsync(misc, 0, 3 * sizeof(int), st));
     int rc = CE_ERR_INVALID_ARG;
     switch (p->n) {
         case 4: rc = launch_small<4, 32>(p, k, count, qoi, iters, status, u_out, misc, st); break;
@@ -302,11 +286,14 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
         sce_free(misc, st);
         return rc;
     }
-    int h[2] = {0, 0};
+    int h[3] = {0, 0, 0};
     SCE_CUDA(cudaMemcpyAsync(h, misc, sizeof(h), cudaMemcpyDeviceToHost, st));
     SCE_CUDA(cudaStreamSynchronize(st));
     sce_free(misc, st);
     if (n_failed_out) *n_failed_out = h[0];
-    if (max_iters_out) *max_iters_out = h[1];
+    if (max_iters_out) {
+        max_iters_out[0] = h[1];
+        max_iters_out[1] = h[2];
+    }
     return h[0] > 0 ? CE_ERR_NOT_CONVERGED : CE_OK;
 }

@@ -83,6 +83,7 @@ extern "C" int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uin
     pc.n = nc;
     double acc[4] = {0, 0, 0, 0};
     int n_failed = 0, max_it = 0;
+    long long tot_it = 0;
     int result = CE_OK;
     for (int c0 = 0; c0 < count; c0 += chunk) {
         const int cn = std::min(chunk, count - c0);
@@ -92,18 +93,20 @@ extern "C" int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uin
         rc = sce_sample_batch_impl(e, seed, level, first_sample + (uint64_t)c0, cn, p->precision, kf,
                                    coarse ? kc : nullptr, st);
         if (rc != CE_OK) { cleanup(); return rc; }
-        int mi = 0, nf = 0;
-        rc = sce_darcy_solve_impl(p, kf, cn, qf_c, nullptr, nullptr, nullptr, st, &mi, &nf);
+        int mi[2] = {0, 0}, nf = 0;
+        rc = sce_darcy_solve_impl(p, kf, cn, qf_c, nullptr, nullptr, nullptr, st, mi, &nf);
         if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
         if (rc == CE_ERR_NOT_CONVERGED) result = rc;
         n_failed += nf;
-        max_it = std::max(max_it, mi);
+        max_it = std::max(max_it, mi[0]);
+        tot_it += mi[1];
         if (coarse) {
-            rc = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, nullptr, st, &mi, &nf);
+            rc = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, nullptr, st, mi, &nf);
             if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
             if (rc == CE_ERR_NOT_CONVERGED) result = rc;
             n_failed += nf;
-            max_it = std::max(max_it, mi);
+            max_it = std::max(max_it, mi[0]);
+            tot_it += mi[1];
         }
         level_diff_kernel<<<(cn + 255) / 256, 256, 0, st>>>(qf_c, qc_c, cn, qoi_index, Y_c);
         level_sums_kernel<<<1, 256, 0, st>>>(Y_c, qf_c, cn, qoi_index, sums);
@@ -124,5 +127,6 @@ extern "C" int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uin
     out->sumQf2 = acc[3];
     out->n_failed = n_failed;
     out->max_iters = max_it;
+    out->total_iters = tot_it;
     return result;
 }

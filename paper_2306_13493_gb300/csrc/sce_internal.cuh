@@ -73,7 +73,7 @@ struct ce_embedding_s {
 enum SceKernel {
     KP_ROW = 0, KP_COL, KP_COND, KP_COARSEN, KP_SMOOTH, KP_RESTRICT, KP_PROLONG, KP_COARSEST,
     KP_SPMV, KP_AXPY, KP_DOT, KP_PUPDATE, KP_COPY, KP_REDUCE, KP_OUTER_RES, KP_OUTER_UPD, KP_QOI,
-    KP_SETUP, KP_NORMALS, KP_LEVEL, KP_SMALL, KP_COUNT_
+    KP_SETUP, KP_NORMALS, KP_LEVEL, KP_SMALL, KP_MG_DOWN, KP_MG_UP, KP_MG_TAIL, KP_COUNT_
 };
 
 bool sce_prof_on();
@@ -97,7 +97,8 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
                     int *status, double *u_out, cudaStream_t st, int *max_iters_out,
                     int *n_failed_out);
 
-// Darcy solver entry used by mlmc_level_estimate.
+// Darcy solver entry used by mlmc_level_estimate.  max_iters_out, if not
+// NULL, points at int[2]: {max iterations over the samples, total iterations}.
 int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
                          int *n_failed_out);

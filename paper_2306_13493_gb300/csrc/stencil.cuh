@@ -10,6 +10,8 @@ namespace sce {
 //   gx = cx(i,j) = 1/2 [kbar_T1(i,j) + kbar_T2(i,j-1)]   (0 if i == n)
 //   gy = cy(i,j) = 1/2 [kbar_T2(i,j) + kbar_T1(i-1,j)]   (0 if j == n)
 // T1(a,b) = {(a,b),(a+1,b),(a+1,b+1)}, T2(a,b) = {(a,b),(a,b+1),(a+1,b+1)}.
+// The sums are of at most six vertex values (exact in FP64 for FP32 k) and
+// are scaled once by 1/6 (= 1/2 * 1/3): no FP64 division.
 template <typename Tk>
 __device__ __forceinline__ void cond_at(const Tk *ks, int i, int j, int n, double *gx,
                                         double *gy) {
@@ -17,46 +19,44 @@ __device__ __forceinline__ void cond_at(const Tk *ks, int i, int j, int n, doubl
     auto K = [&](int a, int b) { return (double)ks[b * w + a]; };
     double x = 0.0, y = 0.0;
     if (i < n) {
-        if (j < n) x += (K(i, j) + K(i + 1, j) + K(i + 1, j + 1)) / 3.0;
-        if (j > 0) x += (K(i, j - 1) + K(i, j) + K(i + 1, j)) / 3.0;
-        x *= 0.5;
+        if (j < n) x += K(i, j) + K(i + 1, j) + K(i + 1, j + 1);
+        if (j > 0) x += K(i, j - 1) + K(i, j) + K(i + 1, j);
+        x *= (1.0 / 6.0);
     }
     if (j < n) {
-        if (i < n) y += (K(i, j) + K(i, j + 1) + K(i + 1, j + 1)) / 3.0;
-        if (i > 0) y += (K(i - 1, j) + K(i, j) + K(i, j + 1)) / 3.0;
-        y *= 0.5;
+        if (i < n) y += K(i, j) + K(i, j + 1) + K(i + 1, j + 1);
+        if (i > 0) y += K(i - 1, j) + K(i, j) + K(i, j + 1);
+        y *= (1.0 / 6.0);
     }
     *gx = x;
     *gy = y;
 }
 
-__device__ __forceinline__ double series_cond(double a, double b) {
-    const double t = a + b;
-    return t > 0.0 ? a * b / t : 0.0;
+template <typename T>
+__device__ __forceinline__ T series_cond(T a, T b) {
+    const T t = a + b;
+    return t > T(0) ? a * b / t : T(0);
 }
 
 // Coarse conductances at coarse vertex (I, J): a coarse edge spans two fine
 // edges in series and stands for the fine lines 2J (weight 1), 2J +- 1 (1/2).
+// Computed in the working precision T of the hierarchy.
 template <typename T>
-__device__ __forceinline__ void coarsen_at(const T *ax, const T *ay, int nf, int I, int J,
-                                           double *gx, double *gy) {
+__device__ __forceinline__ void coarsen_at(const T *ax, const T *ay, int nf, int I, int J, T *gx,
+                                           T *gy) {
     const int nc = nf / 2, wf = nf + 1;
-    double x = 0.0, y = 0.0;
+    T x = T(0), y = T(0);
     if (I < nc) {
-        auto S = [&](int j) {
-            return series_cond((double)ax[j * wf + 2 * I], (double)ax[j * wf + 2 * I + 1]);
-        };
+        auto S = [&](int j) { return series_cond(ax[j * wf + 2 * I], ax[j * wf + 2 * I + 1]); };
         x = S(2 * J);
-        if (J > 0) x += 0.5 * S(2 * J - 1);
-        if (J < nc) x += 0.5 * S(2 * J + 1);
+        if (J > 0) x += T(0.5) * S(2 * J - 1);
+        if (J < nc) x += T(0.5) * S(2 * J + 1);
     }
     if (J < nc) {
-        auto S = [&](int i) {
-            return series_cond((double)ay[(2 * J) * wf + i], (double)ay[(2 * J + 1) * wf + i]);
-        };
+        auto S = [&](int i) { return series_cond(ay[(2 * J) * wf + i], ay[(2 * J + 1) * wf + i]); };
         y = S(2 * I);
-        if (I > 0) y += 0.5 * S(2 * I - 1);
-        if (I < nc) y += 0.5 * S(2 * I + 1);
+        if (I > 0) y += T(0.5) * S(2 * I - 1);
+        if (I < nc) y += T(0.5) * S(2 * I + 1);
     }
     *gx = x;
     *gy = y;

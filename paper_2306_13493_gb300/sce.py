@@ -60,7 +60,8 @@ class darcy_problem(ctypes.Structure):
 class mlmc_level_sums(ctypes.Structure):
     _fields_ = [("N", ctypes.c_longlong), ("sumY", ctypes.c_double), ("sumY2", ctypes.c_double),
                 ("sumQf", ctypes.c_double), ("sumQf2", ctypes.c_double),
-                ("n_failed", ctypes.c_int), ("max_iters", ctypes.c_int)]
+                ("n_failed", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("total_iters", ctypes.c_longlong)]
 
 
 # name -> (restype, argtypes); the exported C ABI

@@ -60,4 +60,4 @@ def test_struct_layouts_match_header():
     from paper_2306_13493_gb300 import sce
     assert ctypes.sizeof(sce.ce_cov) == 32
     assert ctypes.sizeof(sce.ce_embedding_info) == 4 * 3 + 4 + 8 * 3 + 8 * 3
-    assert ctypes.sizeof(sce.mlmc_level_sums) == 8 * 5 + 8
+    assert ctypes.sizeof(sce.mlmc_level_sums) == 8 * 5 + 8 + 8

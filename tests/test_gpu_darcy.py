@@ -122,6 +122,25 @@ def test_block_per_sample_solver_matches_batched_and_oracle(sce, n, monkeypatch)
             assert np.max(np.abs(q[c] - oq) / np.maximum(np.abs(oq), 1e-3)) < QOI_TOL
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("n", [16, 64, 128, 256])
+def test_fused_cycle_matches_level_by_level_cycle(sce, n, precision, monkeypatch):
+    """The tiled down/up kernels + one-block tail apply the same V(1,1) cycle as
+    the level-by-level kernels: same iteration counts (up to one, from rounding
+    order) and QoIs equal to solver accuracy; both match the oracle."""
+    k = _oracle_k(n, 3, lam=0.03, sigma2=2.0, seed=200 + n, precision=precision)
+    monkeypatch.setenv("SCE_SMALL_MAX_N", "0")
+    monkeypatch.setenv("SCE_MG_FUSED", "1")
+    rc1, q1, it1, st1, u1 = _solve(sce, k, precision, f=1.0)
+    monkeypatch.setenv("SCE_MG_FUSED", "0")
+    rc2, q2, it2, st2, u2 = _solve(sce, k, precision, f=1.0)
+    assert rc1 == 0 and rc2 == 0
+    assert np.max(np.abs(it1.astype(int) - it2.astype(int))) <= 1, (it1, it2)
+    assert np.max(np.abs(q1 - q2)) < 1e-10
+    oq = odarcy.solve_qois(k[0].astype(np.float64), 1.0)
+    assert np.max(np.abs(q1[0] - oq) / np.maximum(np.abs(oq), 1e-3)) < QOI_TOL
+
+
 def test_results_independent_of_batch_composition(sce):
     """A sample's result is bit-identical alone and inside a larger batch."""
     k = _oracle_k(32, 6, lam=0.05, seed=4, precision=32)
