@@ -1,60 +1,106 @@
 // Multigrid V(1,1) cycle executed by one thread block on one sample whose
 // level arrays are in shared memory (levels N, N/2, ..., 2).  Shared by the
 // one-block-per-sample solver and by the coarse-level tail of the batched
-// solver.
+// solver.  Level sizes and array offsets are compile-time constants (the
+// level recursion is unrolled; arrays are addressed as base + constant), and
+// each Gauss-Seidel half-sweep visits only the vertices of its colour.
 #pragma once
 
 #include "stencil.cuh"
 
 namespace sce {
 
-// z[0] = M^{-1} b[0] for the hierarchy (cx[L], cy[L], bb[L], zz[L]), L < NL,
-// level L having N >> L cells.  Symmetric: red-black Gauss-Seidel before the
-// restriction, black-red after the prolongation, exact solve on 2 cells.
-// All NT threads of the block must call it.
-template <typename T, int N, int NT>
-__device__ __forceinline__ void block_vcycle(T *const *cx, T *const *cy, T *const *bb, T *const *zz,
-                                             int NL) {
-    const int tid = threadIdx.x;
-    {
-        const int V = (N + 1) * (N + 1);
-        for (int v = tid; v < V; v += NT) zz[0][v] = T(0);
+constexpr int mg_levels(int n) { return n <= 2 ? 1 : 1 + mg_levels(n / 2); }
+constexpr int mg_vof(int n) { return (n + 1) * (n + 1); }
+
+// Array k (0 cx, 1 cy, 2 b, 3 z) of level L of an N-cell hierarchy, all levels
+// stored one after the other, each as [cx | cy | b | z].
+template <int N> struct MGPackedLayout {
+    static constexpr int off(int L, int k) {
+        int o = 0;
+        for (int l = 0; l < L; ++l) o += 4 * mg_vof(N >> l);
+        return o + k * mg_vof(N >> L);
     }
-    __syncthreads();
-    for (int L = 0; L < NL - 1; ++L) {
-        const int nL = N >> L, wL = nL + 1, VL = wL * wL;
-        for (int c = 0; c < 2; ++c) {
-            for (int v = tid; v < VL; v += NT) {
-                const int j = v / wL, i = v - j * wL;
-                if (i > 0 && i < nL && ((i + j) & 1) == c) smooth_at(cx[L], cy[L], bb[L], zz[L], i, j, nL);
-            }
-            __syncthreads();
-        }
-        const int nc = nL / 2, wc = nc + 1, Vc = wc * wc;
-        for (int v = tid; v < Vc; v += NT) {
+    static constexpr int total() { return off(mg_levels(N), 0); }
+};
+
+// One red-black half-sweep of colour c on level nL: vertex (i, j) with
+// (i + j) % 2 == c, 1 <= i <= nL-1.
+template <typename T, int nL, int NT>
+__device__ __forceinline__ void block_half_sweep(const T *cx, const T *cy, const T *b, T *z,
+                                                 int c) {
+    constexpr int W = nL + 1;
+    constexpr int HW = (nL + 2) / 2;   // colour vertices per row (upper bound)
+    for (int k = threadIdx.x; k < W * HW; k += NT) {
+        const int j = k / HW;
+        const int i = 2 * (k - j * HW) + ((j + c) & 1);
+        if (i >= 1 && i <= nL - 1) smooth_at(cx, cy, b, z, i, j, nL);
+    }
+}
+
+template <typename T, int N, int NT, class Lay, int L>
+__device__ __forceinline__ void block_vcycle_level(T *base) {
+    constexpr int NL = mg_levels(N);
+    constexpr int nL = N >> L;
+    T *cx = base + Lay::off(L, 0), *cy = base + Lay::off(L, 1);
+    T *b = base + Lay::off(L, 2), *z = base + Lay::off(L, 3);
+    if constexpr (L == NL - 1) {
+        if (threadIdx.x == 0) coarsest_solve(cx, cy, b, z);
+        __syncthreads();
+    } else {
+        constexpr int nc = nL / 2, wc = nc + 1, Vc = wc * wc, wL = nL + 1, VL = wL * wL;
+        T *bc = base + Lay::off(L + 1, 2), *zc = base + Lay::off(L + 1, 3);
+        block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
+        __syncthreads();
+        block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
+        __syncthreads();
+        for (int v = threadIdx.x; v < Vc; v += NT) {
             const int J = v / wc, I = v - J * wc;
-            bb[L + 1][v] = (I > 0 && I < nc) ? restrict_at(cx[L], cy[L], bb[L], zz[L], nL, I, J) : T(0);
-            zz[L + 1][v] = T(0);
+            bc[v] = (I > 0 && I < nc) ? restrict_at(cx, cy, b, z, nL, I, J) : T(0);
+            zc[v] = T(0);
         }
         __syncthreads();
-    }
-    if (tid == 0) coarsest_solve(cx[NL - 1], cy[NL - 1], bb[NL - 1], zz[NL - 1]);
-    __syncthreads();
-    for (int L = NL - 2; L >= 0; --L) {
-        const int nL = N >> L, wL = nL + 1, VL = wL * wL;
-        for (int v = tid; v < VL; v += NT) {
+        block_vcycle_level<T, N, NT, Lay, L + 1>(base);
+        for (int v = threadIdx.x; v < VL; v += NT) {
             const int j = v / wL, i = v - j * wL;
-            if (i > 0 && i < nL) zz[L][v] += prolong_at(zz[L + 1], nL / 2, i, j);
+            if (i > 0 && i < nL) z[v] += prolong_at(zc, nc, i, j);
         }
         __syncthreads();
-        for (int c = 1; c >= 0; --c) {
-            for (int v = tid; v < VL; v += NT) {
-                const int j = v / wL, i = v - j * wL;
-                if (i > 0 && i < nL && ((i + j) & 1) == c) smooth_at(cx[L], cy[L], bb[L], zz[L], i, j, nL);
-            }
-            __syncthreads();
-        }
+        block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
+        __syncthreads();
+        block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
+        __syncthreads();
     }
+}
+
+// Coarse conductances of levels L..NL-1 from level L-1 (call with L = 1).
+template <typename T, int N, int NT, class Lay, int L>
+__device__ __forceinline__ void block_coarsen(T *base) {
+    if constexpr (L < mg_levels(N)) {
+        constexpr int nL = N >> L, wL = nL + 1, VL = wL * wL;
+        const T *fx = base + Lay::off(L - 1, 0), *fy = base + Lay::off(L - 1, 1);
+        T *cx = base + Lay::off(L, 0), *cy = base + Lay::off(L, 1);
+        for (int v = threadIdx.x; v < VL; v += NT) {
+            const int J = v / wL, I = v - J * wL;
+            T gx, gy;
+            coarsen_at(fx, fy, 2 * nL, I, J, &gx, &gy);
+            cx[v] = gx;
+            cy[v] = gy;
+        }
+        __syncthreads();
+        block_coarsen<T, N, NT, Lay, L + 1>(base);
+    }
+}
+
+// z = M^{-1} b on level 0 of the hierarchy laid out by Lay from `base`.
+// Symmetric: red-black Gauss-Seidel before the restriction, black-red after
+// the prolongation, exact solve on 2 cells.  All NT threads must call it.
+template <typename T, int N, int NT, class Lay>
+__device__ __forceinline__ void block_vcycle(T *base) {
+    T *z = base + Lay::off(0, 3);
+    for (int v = threadIdx.x; v < mg_vof(N); v += NT) z[v] = T(0);
+    __syncthreads();
+    block_vcycle_level<T, N, NT, Lay, 0>(base);
 }
 
 }  // namespace sce

@@ -24,14 +24,10 @@ template <int N> struct SmallLayout {
     static constexpr int V = W * W;
     static constexpr int NL = ilog2c(N);            // levels N, N/2, ..., 2
     static constexpr int vof(int L) { return ((N >> L) + 1) * ((N >> L) + 1); }
-    static constexpr int coarse_floats() {
-        int t = 0;
-        for (int L = 1; L < NL; ++L) t += 4 * vof(L);
-        return t;
-    }
-    // doubles: u, cx64, cy64, reduction scratch (64)
-    static constexpr size_t bytes =
-        sizeof(double) * (3 * (size_t)V + 64) + sizeof(float) * (6 * (size_t)V + coarse_floats());
+    // doubles: u, cx64, cy64, reduction scratch (64); floats: the multigrid
+    // hierarchy, d, p
+    static constexpr size_t bytes = sizeof(double) * (3 * (size_t)V + 64) +
+                                    sizeof(float) * (MGPackedLayout<N>::total() + 2 * (size_t)V);
 };
 
 // Sum over the block, returned to every thread (fixed order).
@@ -76,31 +72,19 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
     double *__restrict__ qoi, int *__restrict__ iters_out, int *__restrict__ status_out,
     double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits) {
     using Lay = SmallLayout<N>;
+    using MG = MGPackedLayout<N>;
     constexpr int W = Lay::W, V = Lay::V, NL = Lay::NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *u = reinterpret_cast<double *>(smem_raw);
     double *cx64 = u + V;
     double *cy64 = cx64 + V;
     double *sh = cy64 + V;
-    float *cx[NL], *cy[NL], *bb[NL], *zz[NL];
-    float *fp = reinterpret_cast<float *>(sh + 64);
-    cx[0] = fp;
-    cy[0] = fp + V;
-    float *d = fp + 2 * V;
-    bb[0] = fp + 3 * V;   // r (inner residual) = rhs of the level-0 cycle
-    zz[0] = fp + 4 * V;
-    float *p = fp + 5 * V;
-    float *q = fp + 6 * V;
-#pragma unroll
-    for (int L = 1; L < NL; ++L) {
-        const int VL = Lay::vof(L);
-        cx[L] = q;
-        cy[L] = q + VL;
-        bb[L] = q + 2 * VL;
-        zz[L] = q + 3 * VL;
-        q += 4 * VL;
-    }
-    float *r = bb[0], *z = zz[0];
+    // FP32 region: the multigrid hierarchy (level 0 = [cx | cy | r | z]), then d, p
+    float *mg = reinterpret_cast<float *>(sh + 64);
+    float *cx0 = mg + MG::off(0, 0), *cy0 = mg + MG::off(0, 1);
+    float *r = mg + MG::off(0, 2), *z = mg + MG::off(0, 3);
+    float *d = mg + MG::total();
+    float *p = d + V;
     const int s = blockIdx.x;
     const int tid = threadIdx.x;
     const float *ks = kin + (size_t)s * V;
@@ -112,23 +96,12 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
         cond_at(ks, i, j, N, &gx, &gy);
         cx64[v] = gx;
         cy64[v] = gy;
-        cx[0][v] = (float)gx;
-        cy[0][v] = (float)gy;
+        cx0[v] = (float)gx;
+        cy0[v] = (float)gy;
         u[v] = i == 0 ? 1.0 : 0.0;
     }
     __syncthreads();
-#pragma unroll
-    for (int L = 1; L < NL; ++L) {
-        const int nL = N >> L, wL = nL + 1, VL = wL * wL;
-        for (int v = tid; v < VL; v += NT) {
-            const int J = v / wL, I = v - J * wL;
-            float gx, gy;
-            coarsen_at(cx[L - 1], cy[L - 1], 2 * nL, I, J, &gx, &gy);
-            cx[L][v] = gx;
-            cy[L][v] = gy;
-        }
-        __syncthreads();
-    }
+    block_coarsen<float, N, NT, MG, 1>(mg);
 
     const double h2_6 = f / (6.0 * (double)N * (double)N);
     // FP64 residual r = F - A u into the FP32 rhs, returns |r|^2
@@ -147,7 +120,8 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
     };
 
     // one symmetric V(1,1) cycle: z[0] = M^-1 r
-    auto vcycle = [&]() { block_vcycle<float, N, NT>(cx, cy, bb, zz, NL); };
+    static_assert(NL == mg_levels(N), "level count");
+    auto vcycle = [&]() { block_vcycle<float, N, NT, MG>(mg); };
 
     double orr = outer_residual();
     const double orr0 = orr;
@@ -173,7 +147,7 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
             float pq = 0.f;
             for (int v = tid; v < V; v += NT) {
                 const int j = v / W, i = v - j * W;
-                if (i > 0 && i < N) pq += p[v] * apply_at(cx[0], cy[0], p, i, j, N);
+                if (i > 0 && i < N) pq += p[v] * apply_at(cx0, cy0, p, i, j, N);
             }
             pq = bsumf<NT>(pq, shf);
             const float alpha = pq > 0.f ? rz / pq : 0.f;
@@ -181,7 +155,7 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
             for (int v = tid; v < V; v += NT) {
                 const int j = v / W, i = v - j * W;
                 if (i > 0 && i < N) {
-                    const float ap = apply_at(cx[0], cy[0], p, i, j, N);
+                    const float ap = apply_at(cx0, cy0, p, i, j, N);
                     d[v] += alpha * p[v];
                     const float rv = r[v] - alpha * ap;
                     r[v] = rv;

@@ -259,38 +259,35 @@ __global__ void __launch_bounds__(NTHR) mg_tail_kernel(TailPtrs tp, const T *__r
                                                        T *__restrict__ z,
                                                        const int *__restrict__ act,
                                                        double *__restrict__ part_rz) {
-    constexpr int NL = NT_N >= 32 ? 5 : NT_N >= 16 ? 4 : NT_N >= 8 ? 3 : 2;
+    using Lay = MGPackedLayout<NT_N>;
+    constexpr int NL = mg_levels(NT_N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T sred[32];
     const int s = blockIdx.x;
     if (!act[s]) return;
-    T *cx[NL], *cy[NL], *bb[NL], *zz[NL];
-    T *q = reinterpret_cast<T *>(smem_raw);
+    T *base = reinterpret_cast<T *>(smem_raw);
 #pragma unroll
     for (int L = 0; L < NL; ++L) {
-        const int nl = NT_N >> L, VL = (nl + 1) * (nl + 1);
-        cx[L] = q;
-        cy[L] = q + VL;
-        bb[L] = q + 2 * VL;
-        zz[L] = q + 3 * VL;
-        q += 4 * VL;
+        const int VL = mg_vof(NT_N >> L);
+        T *cx = base + Lay::off(L, 0), *cy = base + Lay::off(L, 1);
         const T *gx = reinterpret_cast<const T *>(tp.cx[L]) + (long long)s * VL;
         const T *gy = reinterpret_cast<const T *>(tp.cy[L]) + (long long)s * VL;
         for (int v = threadIdx.x; v < VL; v += NTHR) {
-            cx[L][v] = gx[v];
-            cy[L][v] = gy[v];
+            cx[v] = gx[v];
+            cy[v] = gy[v];
         }
     }
     constexpr int V0 = (NT_N + 1) * (NT_N + 1);
     const T *bs = b + (long long)s * V0;
-    for (int v = threadIdx.x; v < V0; v += NTHR) bb[0][v] = bs[v];
+    T *b0 = base + Lay::off(0, 2), *z0 = base + Lay::off(0, 3);
+    for (int v = threadIdx.x; v < V0; v += NTHR) b0[v] = bs[v];
     __syncthreads();
-    block_vcycle<T, NT_N, NTHR>(cx, cy, bb, zz, NL);
+    block_vcycle<T, NT_N, NTHR, Lay>(base);
     T *zs = z + (long long)s * V0;
     T rz = T(0);
     for (int v = threadIdx.x; v < V0; v += NTHR) {
-        zs[v] = zz[0][v];
-        rz += bb[0][v] * zz[0][v];
+        zs[v] = z0[v];
+        rz += b0[v] * z0[v];
     }
     if (part_rz) {
         const T tot = block_sum_t(rz, sred);
