@@ -210,7 +210,8 @@ typedef struct {
  * selects the field and solver precision.
  *   out  : host, the level sums
  *   Y    : device double[count] or NULL
- *   qoi_f, qoi_c : device double[count*3] or NULL
+ *   qoi_f, qoi_c : device double[count*3] or NULL; when given, all three
+ *          QoIs are computed for those solves, otherwise only qoi_index
  * Synchronises `stream`.  Returns CE_ERR_NOT_CONVERGED if any solve missed
  * rtol (sums still written; out->n_failed counts the samples).
  */

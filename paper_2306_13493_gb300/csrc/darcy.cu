@@ -417,6 +417,34 @@ __global__ void outer_residual_kernel(const double *__restrict__ cx, const doubl
     if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = tot;
 }
 
+// Residual of the lifting u0 (1 on x1 = 0, 0 elsewhere): A u0 is -cx(0, j) at
+// the vertices (1, j) and 0 at the other unknowns, so r0 = F + [i = 1] cx(0, j).
+template <typename T>
+__global__ void initial_residual_kernel(const double *__restrict__ cx, double f, int n, int vpt,
+                                        double *__restrict__ r64, T *__restrict__ rin,
+                                        double *__restrict__ part, int nblk) {
+    __shared__ double sh[32];
+    const int s = blockIdx.y;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const int w = n + 1;
+    const double *ax = cx + s * V;
+    const double h2_6 = f / (6.0 * (double)n * (double)n);
+    double acc = 0.0;
+    FOR_VERT(V, vpt) {
+        const int j = v / w, i = v - j * w;
+        double r = 0.0;
+        if (i > 0 && i < n) {
+            r = h2_6 * ((j == 0 || j == n) ? 3.0 : 6.0);
+            if (i == 1) r += ax[v - 1];
+            acc += r * r;
+        }
+        r64[s * V + v] = r;
+        rin[s * V + v] = (T)r;
+    }
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = tot;
+}
+
 template <typename T>
 __global__ void outer_update_kernel(double *__restrict__ u, const T *__restrict__ d, int n,
                                     int vpt, const int *__restrict__ act) {
@@ -426,20 +454,22 @@ __global__ void outer_update_kernel(double *__restrict__ u, const T *__restrict_
     FOR_VERT(V, vpt) u[s * V + v] += (double)d[s * V + v];
 }
 
-// QoI partials: outflow (vertices i = n-1) and the P1 mass norm (cells).
+// QoI partials: outflow (vertices i = n-1; bit 0 of qmask) and the P1 mass
+// norm (cells; bit 2).
 __global__ void qoi_partial_kernel(const double *__restrict__ cx, const double *__restrict__ u,
                                    int n, int vpt, double *__restrict__ part_out,
-                                   double *__restrict__ part_l2, int nblk) {
+                                   double *__restrict__ part_l2, int nblk, int qmask) {
     __shared__ double sh[32];
     const int s = blockIdx.y;
     const long long V = (long long)(n + 1) * (n + 1);
     const int w = n + 1;
     const double *us = u + s * V, *ax = cx + s * V;
+    const bool want_out = qmask & 1, want_l2 = qmask & 4;
     double qo = 0.0, l2 = 0.0;
     FOR_VERT(V, vpt) {
         const int j = v / w, i = v - j * w;
-        if (i == n - 1) qo += ax[v] * us[v];
-        if (i < n && j < n) {
+        if (want_out && i == n - 1) qo += ax[v] * us[v];
+        if (want_l2 && i < n && j < n) {
             const double a = us[v], b = us[v + 1], c = us[v + w + 1], d = us[v + w];
             const double s1 = a + b + c, s2 = a + d + c;
             l2 += s1 * s1 + a * a + b * b + c * c + s2 * s2 + a * a + d * d + c * c;
@@ -451,19 +481,23 @@ __global__ void qoi_partial_kernel(const double *__restrict__ cx, const double *
     if (threadIdx.x == 0) part_l2[(long long)s * nblk + blockIdx.x] = t;
 }
 
+// QoIs per sample (those of qmask; the others are written as 0), status,
+// iteration counts.  part_out / part_l2 may be NULL when qmask has neither.
 __global__ void qoi_final_kernel(const double *__restrict__ part_out,
                                  const double *__restrict__ part_l2, int nblk, int count,
                                  const double *__restrict__ u, int n, double f,
                                  const Scal sc, double rtol2, double *__restrict__ qoi,
                                  int *__restrict__ iters_out, int *__restrict__ status_out,
-                                 int *__restrict__ nfail) {
+                                 int *__restrict__ nfail, int qmask) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= count) return;
     const int s = warp;
     double a = 0.0, b = 0.0;
-    for (int i = lane; i < nblk; i += 32) {
-        a += part_out[(long long)s * nblk + i];
-        b += part_l2[(long long)s * nblk + i];
+    if (part_out) {
+        for (int i = lane; i < nblk; i += 32) {
+            a += part_out[(long long)s * nblk + i];
+            b += part_l2[(long long)s * nblk + i];
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
@@ -485,11 +519,12 @@ __global__ void qoi_final_kernel(const double *__restrict__ part_out,
     double q_pt;
     if (xi >= et) q_pt = uab + xi * (ua1b - uab) + et * (ua1b1 - ua1b);   // T1
     else q_pt = uab + et * (uab1 - uab) + xi * (ua1b1 - uab1);             // T2
-    qoi[3 * s + 0] = q_out;
-    qoi[3 * s + 1] = q_pt;
-    qoi[3 * s + 2] = q_l2;
+    qoi[3 * s + 0] = (qmask & 1) ? q_out : 0.0;
+    qoi[3 * s + 1] = (qmask & 2) ? q_pt : 0.0;
+    qoi[3 * s + 2] = (qmask & 4) ? q_l2 : 0.0;
     int st = 0;
-    if (!(fabs(q_out) < 1e300 && fabs(q_pt) < 1e300 && fabs(q_l2) < 1e300)) st = CE_ERR_NONFINITE;
+    if (!(fabs(qoi[3 * s]) < 1e300 && fabs(qoi[3 * s + 1]) < 1e300 && fabs(qoi[3 * s + 2]) < 1e300))
+        st = CE_ERR_NONFINITE;
     else if (!(sc.orr[s] <= rtol2 * sc.orr0[s])) st = CE_ERR_NOT_CONVERGED;
     if (status_out) status_out[s] = st;
     if (iters_out) iters_out[s] = sc.iters[s];
@@ -670,7 +705,7 @@ struct Solver {
 template <typename T, typename Tk>
 static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                         int *n_failed_out) {
+                         int *n_failed_out, int qmask) {
     Solver<T> S;
     S.st = st;
     S.count = count;
@@ -759,11 +794,11 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     const int inner_max = sizeof(T) == 4 ? 40 : maxit;
     const int check_every = 4;
 
-    // initial residual
+    // initial residual (of the lifting, in closed form)
     {
-        SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 32.0));
-        outer_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx64, S.cy64, S.u64, p->f, n0, l0.vpt,
-                                                        S.r64, S.b[0], S.part, l0.nblk, nullptr);
+        SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 16.0));
+        initial_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx64, p->f, n0, l0.vpt, S.r64, S.b[0],
+                                                          S.part, l0.nblk);
     }
     SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
     S.reduce(RED_ORR0, nullptr, rtol2, in_rel2);
@@ -841,16 +876,17 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         SCE_TRY(S.read_counter(&n_act));
     }
 
-    // QoIs
-    {
+    // QoIs (outflow and L2 norm need a pass over the grid; the point value not)
+    const bool grid_qoi = (qmask & 5) != 0;
+    if (grid_qoi) {
         SceProf pr(KP_QOI, st, S.vb(0, 0.0, 16.0));
         qoi_partial_kernel<<<g0, l0.tpb, 0, st>>>(S.cx64, S.u64, n0, l0.vpt, S.part, S.part2,
-                                                  l0.nblk);
+                                                  l0.nblk, qmask);
     }
     SCE_CUDA(cudaMemsetAsync(S.misc + 1, 0, sizeof(int), st));
     qoi_final_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(
-        S.part, S.part2, l0.nblk, count, S.u64, n0, p->f, S.sc, rtol2, qoi, iters, status,
-        S.misc + 1);
+        grid_qoi ? S.part : nullptr, grid_qoi ? S.part2 : nullptr, l0.nblk, count, S.u64, n0,
+        p->f, S.sc, rtol2, qoi, iters, status, S.misc + 1, qmask);
     max_int_kernel<<<1, 256, 0, st>>>(S.sc.iters, count, S.misc + 2);
     SCE_CUDA(cudaGetLastError());
     if (u_out)
@@ -870,24 +906,25 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
 
 int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                         int *n_failed_out) {
+                         int *n_failed_out, int qmask) {
     if (!p || !k || !qoi || count < 0) return CE_ERR_INVALID_ARG;
     if (!is_pow2(p->n) || p->n < 4 || p->n > 4096) return CE_ERR_INVALID_ARG;
     if (p->precision != 32 && p->precision != 64) return CE_ERR_INVALID_ARG;
     if (!(p->rtol > 0) || count > 65535) return CE_ERR_INVALID_ARG;
     if (count == 0) return CE_OK;
+    qmask &= 7;
     if (p->precision == 32 && p->n <= sce_small_max_n() && p->n <= 64)
         return sce_darcy_small(p, (const float *)k, count, qoi, iters, status, u_out, st,
-                               max_iters_out, n_failed_out);
+                               max_iters_out, n_failed_out, qmask);
     if (p->precision == 64)
         return darcy_solve_t<double, double>(p, (const double *)k, count, qoi, iters, status,
-                                             u_out, st, max_iters_out, n_failed_out);
+                                             u_out, st, max_iters_out, n_failed_out, qmask);
     return darcy_solve_t<float, float>(p, (const float *)k, count, qoi, iters, status, u_out, st,
-                                       max_iters_out, n_failed_out);
+                                       max_iters_out, n_failed_out, qmask);
 }
 
 extern "C" int darcy_solve_batch(const darcy_problem *p, const void *k, int count, double *qoi,
                                  int *iters, int *status, double *u_out, void *stream) {
     return sce_darcy_solve_impl(p, k, count, qoi, iters, status, u_out, as_stream(stream), nullptr,
-                                nullptr);
+                                nullptr, 7);
 }

@@ -70,7 +70,7 @@ template <int N, int NT>
 __global__ void __launch_bounds__(NT) small_solve_kernel(
     const float *__restrict__ kin, double f, double rtol2, double in_rel2, int maxit,
     double *__restrict__ qoi, int *__restrict__ iters_out, int *__restrict__ status_out,
-    double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits) {
+    double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits, int qmask) {
     using Lay = SmallLayout<N>;
     using MG = MGPackedLayout<N>;
     constexpr int W = Lay::W, V = Lay::V, NL = Lay::NL;
@@ -123,7 +123,22 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
     static_assert(NL == mg_levels(N), "level count");
     auto vcycle = [&]() { block_vcycle<float, N, NT, MG>(mg); };
 
-    double orr = outer_residual();
+    // residual of the lifting in closed form: r0 = F + [i = 1] cx(0, j)
+    double orr;
+    {
+        double acc = 0.0;
+        for (int v = tid; v < V; v += NT) {
+            const int j = v / W, i = v - j * W;
+            double rv = 0.0;
+            if (i > 0 && i < N) {
+                rv = h2_6 * ((j == 0 || j == N) ? 3.0 : 6.0);
+                if (i == 1) rv += cx64[v - 1];
+                acc += rv * rv;
+            }
+            r[v] = (float)rv;
+        }
+        orr = bsum<NT>(acc, sh);
+    }
     const double orr0 = orr;
     float *shf = reinterpret_cast<float *>(sh + 48);
     int its = 0;
@@ -179,31 +194,36 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
         orr = outer_residual();
     }
 
-    // QoIs (FP64)
+    // QoIs (FP64): the outflow (bit 0 of qmask) and L2 norm (bit 2) need a
+    // pass over the grid, the point value (bit 1) does not
     double qo = 0.0, l2 = 0.0;
-    for (int v = tid; v < V; v += NT) {
-        const int j = v / W, i = v - j * W;
-        if (i == N - 1) qo += cx64[v] * u[v];
-        if (i < N && j < N) {
-            const double a = u[v], b = u[v + 1], c = u[v + W + 1], e = u[v + W];
-            const double s1 = a + b + c, s2 = a + e + c;
-            l2 += s1 * s1 + a * a + b * b + c * c + s2 * s2 + a * a + e * e + c * c;
+    const bool want_out = qmask & 1, want_l2 = qmask & 4;
+    if (want_out || want_l2 || u_out) {
+        for (int v = tid; v < V; v += NT) {
+            const int j = v / W, i = v - j * W;
+            if (want_out && i == N - 1) qo += cx64[v] * u[v];
+            if (want_l2 && i < N && j < N) {
+                const double a = u[v], b = u[v + 1], c = u[v + W + 1], e = u[v + W];
+                const double s1 = a + b + c, s2 = a + e + c;
+                l2 += s1 * s1 + a * a + b * b + c * c + s2 * s2 + a * a + e * e + c * c;
+            }
+            if (u_out) u_out[(size_t)s * V + v] = u[v];
         }
-        if (u_out) u_out[(size_t)s * V + v] = u[v];
+        qo = bsum<NT>(qo, sh);
+        l2 = bsum<NT>(l2, sh);
     }
-    qo = bsum<NT>(qo, sh);
-    l2 = bsum<NT>(l2, sh);
     if (tid == 0) {
         const double h = 1.0 / (double)N;
-        const double q_out = qo + f * h * 0.5;
-        const double q_l2 = sqrt(l2 * h * h / 24.0);
+        const double q_out = want_out ? qo + f * h * 0.5 : 0.0;
+        const double q_l2 = want_l2 ? sqrt(l2 * h * h / 24.0) : 0.0;
         const double xs = 7.0 / 15.0 * (double)N, ys = 7.0 / 15.0 * (double)N;
         const int ca = min((int)floor(xs), N - 1), cb = min((int)floor(ys), N - 1);
         const double xi = xs - ca, et = ys - cb;
         const double uab = u[cb * W + ca], ua1b = u[cb * W + ca + 1];
         const double uab1 = u[(cb + 1) * W + ca], ua1b1 = u[(cb + 1) * W + ca + 1];
-        const double q_pt = xi >= et ? uab + xi * (ua1b - uab) + et * (ua1b1 - ua1b)
-                                     : uab + et * (uab1 - uab) + xi * (ua1b1 - uab1);
+        const double q_pt = !(qmask & 2) ? 0.0
+                            : xi >= et ? uab + xi * (ua1b - uab) + et * (ua1b1 - ua1b)
+                                       : uab + et * (uab1 - uab) + xi * (ua1b1 - uab1);
         qoi[3 * s + 0] = q_out;
         qoi[3 * s + 1] = q_pt;
         qoi[3 * s + 2] = q_l2;
@@ -220,7 +240,7 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
 
 template <int N, int NT>
 int launch_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
-                 int *status, double *u_out, int *misc, cudaStream_t st) {
+                 int *status, double *u_out, int *misc, int qmask, cudaStream_t st) {
     const size_t smem = SmallLayout<N>::bytes;
     SCE_CUDA(cudaFuncSetAttribute(small_solve_kernel<N, NT>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -228,7 +248,7 @@ int launch_small(const darcy_problem *p, const float *k, int count, double *qoi,
     SceProf pr(KP_SMALL, st, (double)count * SmallLayout<N>::V * (sizeof(float) + 0.0) + 24.0 * count);
     small_solve_kernel<N, NT><<<count, NT, smem, st>>>(k, p->f, p->rtol * p->rtol, in_rel * in_rel,
                                                        p->maxit > 0 ? p->maxit : 1000, qoi, iters,
-                                                       status, u_out, misc, misc + 1);
+                                                       status, u_out, misc, misc + 1, qmask);
     SCE_CUDA(cudaGetLastError());
     return CE_OK;
 }
@@ -243,19 +263,22 @@ int sce_small_max_n() {
 
 int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
                     int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                    int *n_failed_out) {
+                    int *n_failed_out, int qmask) {
     int *misc = nullptr;   // [0] failed samples, [1] max iterations, [2] total iterations
     SCE_TRY(sce_alloc_t(&misc, 3, st));
     SCE_CUDA(cudaMemsetAsync(misc, 0, 3 * sizeof(int), st));
     int rc = CE_ERR_INVALID_ARG;
+#define SCE_SMALL(NN, TT) \
+    rc = launch_small<NN, TT>(p, k, count, qoi, iters, status, u_out, misc, qmask, st)
     switch (p->n) {
-        case 4: rc = launch_small<4, 32>(p, k, count, qoi, iters, status, u_out, misc, st); break;
-        case 8: rc = launch_small<8, 64>(p, k, count, qoi, iters, status, u_out, misc, st); break;
-        case 16: rc = launch_small<16, 128>(p, k, count, qoi, iters, status, u_out, misc, st); break;
-        case 32: rc = launch_small<32, 256>(p, k, count, qoi, iters, status, u_out, misc, st); break;
-        case 64: rc = launch_small<64, 512>(p, k, count, qoi, iters, status, u_out, misc, st); break;
+        case 4: SCE_SMALL(4, 32); break;
+        case 8: SCE_SMALL(8, 64); break;
+        case 16: SCE_SMALL(16, 128); break;
+        case 32: SCE_SMALL(32, 256); break;
+        case 64: SCE_SMALL(64, 512); break;
         default: break;
     }
+#undef SCE_SMALL
     if (rc != CE_OK) {
         sce_free(misc, st);
         return rc;

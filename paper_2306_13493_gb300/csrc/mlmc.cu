@@ -94,14 +94,16 @@ extern "C" int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uin
                                    coarse ? kc : nullptr, st);
         if (rc != CE_OK) { cleanup(); return rc; }
         int mi[2] = {0, 0}, nf = 0;
-        rc = sce_darcy_solve_impl(p, kf, cn, qf_c, nullptr, nullptr, nullptr, st, mi, &nf);
+        rc = sce_darcy_solve_impl(p, kf, cn, qf_c, nullptr, nullptr, nullptr, st, mi, &nf,
+                                  qoi_f ? 7 : (1 << qoi_index));
         if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
         if (rc == CE_ERR_NOT_CONVERGED) result = rc;
         n_failed += nf;
         max_it = std::max(max_it, mi[0]);
         tot_it += mi[1];
         if (coarse) {
-            rc = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, nullptr, st, mi, &nf);
+            rc = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, nullptr, st, mi, &nf,
+                                      qoi_c ? 7 : (1 << qoi_index));
             if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
             if (rc == CE_ERR_NOT_CONVERGED) result = rc;
             n_failed += nf;

@@ -95,10 +95,12 @@ int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
 int sce_small_max_n();
 int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
                     int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                    int *n_failed_out);
+                    int *n_failed_out, int qmask);
 
 // Darcy solver entry used by mlmc_level_estimate.  max_iters_out, if not
 // NULL, points at int[2]: {max iterations over the samples, total iterations}.
+// qmask selects the QoIs computed (bit 0 outflow, 1 point value, 2 L2 norm;
+// the others are written as 0).
 int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                         int *n_failed_out);
+                         int *n_failed_out, int qmask);

@@ -15,17 +15,22 @@ namespace sce {
 template <typename Tk>
 __device__ __forceinline__ void cond_at(const Tk *ks, int i, int j, int n, double *gx,
                                         double *gy) {
-    const int w = n + 1;
-    auto K = [&](int a, int b) { return (double)ks[b * w + a]; };
+    const int w = n + 1, v = j * w + i;
+    const double a = (double)ks[v];                                   // k(i, j)
+    const double b = i < n ? (double)ks[v + 1] : 0.0;                 // k(i+1, j)
+    const double e = j < n ? (double)ks[v + w] : 0.0;                 // k(i, j+1)
+    const double c = (i < n && j < n) ? (double)ks[v + w + 1] : 0.0; // k(i+1, j+1)
     double x = 0.0, y = 0.0;
     if (i < n) {
-        if (j < n) x += K(i, j) + K(i + 1, j) + K(i + 1, j + 1);
-        if (j > 0) x += K(i, j - 1) + K(i, j) + K(i + 1, j);
+        const double ab = a + b;                                      // shared by T1, T2
+        if (j < n) x = ab + c;                                        // T1(i, j)
+        if (j > 0) x += ab + (double)ks[v - w];                       // T2(i, j-1)
         x *= (1.0 / 6.0);
     }
     if (j < n) {
-        if (i < n) y += K(i, j) + K(i, j + 1) + K(i + 1, j + 1);
-        if (i > 0) y += K(i - 1, j) + K(i, j) + K(i, j + 1);
+        const double ae = a + e;
+        if (i < n) y = ae + c;                                        // T2(i, j)
+        if (i > 0) y += ae + (double)ks[v - 1];                       // T1(i-1, j)
         y *= (1.0 / 6.0);
     }
     *gx = x;
