@@ -23,7 +23,14 @@ template <typename R2> __device__ __forceinline__ R2 cmul(R2 a, R2 b) {
 // i * a
 template <typename R2> __device__ __forceinline__ R2 cmuli(R2 a) { return {-a.y, a.x}; }
 
+// Shared-memory line layout: element i of a line lives at fft_pad(i), one
+// padding slot per 16 complex values, so the strided writes of the first
+// Stockham stages (stride 4 and 16 elements) hit distinct banks.
+__host__ __device__ constexpr int fft_pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int fft_line_pitch(int P) { return P + (P >> 4); }
+
 // MAXB = maximum butterflies per thread per stage (N/4 <= MAXB * nthr).
+// buf is a padded line (fft_pad indexing).
 template <typename R, int MAXB>
 __device__ __forceinline__ void smem_fft(typename C2<R>::T *buf, int logN,
                                          const typename C2<R>::T *__restrict__ tw, int tid,
@@ -41,7 +48,7 @@ __device__ __forceinline__ void smem_fft(typename C2<R>::T *buf, int logN,
             jj[b] = j;
             if (j < nb4) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) v[b][r] = buf[j + r * nb4];
+                for (int r = 0; r < 4; ++r) v[b][r] = buf[fft_pad(j + r * nb4)];
             }
         }
         __syncthreads();
@@ -61,10 +68,10 @@ __device__ __forceinline__ void smem_fft(typename C2<R>::T *buf, int logN,
                 const R2 a13 = cadd(v[b][1], v[b][3]);
                 const R2 s13 = cmuli(csub(v[b][1], v[b][3]));
                 const int o = (j - k) * 4 + k;
-                buf[o] = cadd(a02, a13);
-                buf[o + Ns] = cadd(s02, s13);
-                buf[o + 2 * Ns] = csub(a02, a13);
-                buf[o + 3 * Ns] = csub(s02, s13);
+                buf[fft_pad(o)] = cadd(a02, a13);
+                buf[fft_pad(o + Ns)] = cadd(s02, s13);
+                buf[fft_pad(o + 2 * Ns)] = csub(a02, a13);
+                buf[fft_pad(o + 3 * Ns)] = csub(s02, s13);
             }
         }
         __syncthreads();
@@ -76,8 +83,8 @@ __device__ __forceinline__ void smem_fft(typename C2<R>::T *buf, int logN,
         for (int b = 0; b < 2 * MAXB; ++b) {
             const int j = tid + b * nthr;
             if (j < nb2) {
-                v[b][0] = buf[j];
-                v[b][1] = buf[j + nb2];
+                v[b][0] = buf[fft_pad(j)];
+                v[b][1] = buf[fft_pad(j + nb2)];
             }
         }
         __syncthreads();
@@ -86,8 +93,8 @@ __device__ __forceinline__ void smem_fft(typename C2<R>::T *buf, int logN,
             const int j = tid + b * nthr;
             if (j < nb2) {
                 const R2 t = (Ns > 1) ? cmul(v[b][1], tw[j]) : v[b][1];   // k = j, step = 1
-                buf[j] = cadd(v[b][0], t);
-                buf[j + Ns] = csub(v[b][0], t);
+                buf[fft_pad(j)] = cadd(v[b][0], t);
+                buf[fft_pad(j + Ns)] = csub(v[b][0], t);
             }
         }
         __syncthreads();

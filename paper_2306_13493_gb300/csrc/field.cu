@@ -88,10 +88,10 @@ __global__ void fft_lines_f64_kernel(double2 *data, int logP, long long line_str
     extern __shared__ double2 sm_lines[];
     const int P = 1 << logP;
     double2 *base = data + (long long)blockIdx.x * line_stride;
-    for (int q = threadIdx.x; q < P; q += blockDim.x) sm_lines[q] = base[q * elem_stride];
+    for (int q = threadIdx.x; q < P; q += blockDim.x) sm_lines[fft_pad(q)] = base[q * elem_stride];
     __syncthreads();
     smem_fft<double, MAXB>(sm_lines, logP, tw, threadIdx.x, blockDim.x);
-    for (int q = threadIdx.x; q < P; q += blockDim.x) base[q * elem_stride] = sm_lines[q];
+    for (int q = threadIdx.x; q < P; q += blockDim.x) base[q * elem_stride] = sm_lines[fft_pad(q)];
 }
 
 // min Re, max Re, max |Im| (one block, fixed-order tree).
@@ -170,7 +170,7 @@ static int fft2_f64(double2 *d, int P, cudaStream_t st) {
     if (status != CE_OK) return status;
     const int logP = ilog2(P);
     const int nthr = std::max(1, std::min(256, P / 4));
-    const size_t smem = (size_t)P * sizeof(double2);
+    const size_t smem = (size_t)fft_line_pitch(P) * sizeof(double2);
     SCE_CUDA(cudaFuncSetAttribute(fft_lines_f64_kernel<8>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // rows (contiguous), then columns (stride P)
@@ -396,7 +396,8 @@ __global__ void __launch_bounds__(256) ce_row_kernel(
     const int units = masked ? P : P / 2;
     const int u0 = blockIdx.x * F;
     const int unit = u0 + f;
-    R2 *buf = sm + (size_t)f * P;
+    const int LP = fft_line_pitch(P);
+    R2 *buf = sm + (size_t)f * LP;
     const int P4 = P >> 2;
     if (unit < units) {
         if (masked) {
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(256) ce_row_kernel(
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int k1 = 4 * g + r;
-                    buf[k1] = R2{rf[k1] * xi[r], rc[k1] * xi[r]};
+                    buf[fft_pad(k1)] = R2{rf[k1] * xi[r], rc[k1] * xi[r]};
                 }
             }
         } else {
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(256) ce_row_kernel(
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int k1 = 4 * g + r;
-                    buf[k1] = R2{ra[k1] * xa[r], rb[k1] * xb[r]};
+                    buf[fft_pad(k1)] = R2{ra[k1] * xa[r], rb[k1] * xb[r]};
                 }
             }
         }
@@ -441,8 +442,8 @@ __global__ void __launch_bounds__(256) ce_row_kernel(
             const int x = (int)(idx / rows), rr = (int)(idx - (long long)x * rows);
             const int ff = rr >> 1;
             if (u0 + ff >= units) continue;
-            const R2 *b = sm + (size_t)ff * P;
-            const R2 z = b[x], zm = b[(P - x) & (P - 1)];
+            const R2 *b = sm + (size_t)ff * LP;
+            const R2 z = b[fft_pad(x)], zm = b[fft_pad((P - x) & (P - 1))];
             R2 o;
             if ((rr & 1) == 0) o = R2{half * (z.x + zm.x), half * (z.y - zm.y)};
             else o = R2{half * (z.y + zm.y), half * (zm.x - z.x)};
@@ -454,8 +455,8 @@ __global__ void __launch_bounds__(256) ce_row_kernel(
         for (long long idx = threadIdx.x; idx < total; idx += nthr) {
             const int x = (int)(idx / F), ff = (int)(idx - (long long)x * F);
             if (u0 + ff >= units) continue;
-            const R2 *b = sm + (size_t)ff * P;
-            const R2 z = b[x], zm = b[(P - x) & (P - 1)];
+            const R2 *b = sm + (size_t)ff * LP;
+            const R2 z = b[fft_pad(x)], zm = b[fft_pad((P - x) & (P - 1))];
             Yf[((size_t)sl * (m + 1) + x) * P + u0 + ff] = R2{half * (z.x + zm.x), half * (z.y - zm.y)};
             if ((x & 1) == 0)
                 Yc[((size_t)sl * (mc + 1) + (x >> 1)) * P + u0 + ff] =
@@ -484,10 +485,11 @@ __global__ void __launch_bounds__(256) ce_col_kernel(
     const int f = threadIdx.x / tpf, t = threadIdx.x - f * tpf;
     const int x0 = blockIdx.x * F;
     const int col = x0 + f;
-    R2 *buf = sm + (size_t)f * P;
+    const int LP = fft_line_pitch(P);
+    R2 *buf = sm + (size_t)f * LP;
     if (col < ncols) {
         const R2 *src = Y + ((size_t)sl * ncols + col) * P;
-        for (int q = t; q < P; q += tpf) buf[q] = src[q];
+        for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
     }
     __syncthreads();
     smem_fft<R, MAXB>(buf, logP, tw, t, tpf);
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(256) ce_col_kernel(
             const int y = (int)(idx / F), ff = (int)(idx - (long long)y * F);
             const int x = x0 + ff;
             if (x >= ncols) continue;
-            const R2 v = sm[(size_t)ff * P + y];
+            const R2 v = sm[(size_t)ff * LP + fft_pad(y)];
             const R k = exp_r<R>((v.x + v.y) * invP);
             kout[((size_t)sl * (m + 1) + y) * (m + 1) + x] = k;
             if (kc_plain && ((x | y) & 1) == 0)
@@ -512,7 +514,7 @@ __global__ void __launch_bounds__(256) ce_col_kernel(
             const int yc = (int)(idx / F), ff = (int)(idx - (long long)yc * F);
             const int xc = x0 + ff;
             if (xc >= ncols) continue;
-            const R2 v = sm[(size_t)ff * P + 2 * yc];
+            const R2 v = sm[(size_t)ff * LP + fft_pad(2 * yc)];
             kout[((size_t)sl * (mc + 1) + yc) * (mc + 1) + xc] = exp_r<R>((v.x + v.y) * invP);
         }
     }
@@ -530,7 +532,7 @@ static LineCfg line_cfg(int P, int units) {
     const int bpt = (P / 4 + c.tpf - 1) / c.tpf;
     c.maxb = bpt <= 4 ? 4 : 8;
     c.F = std::max(1, 256 / c.tpf);
-    const size_t line = (size_t)P * sizeof(typename C2<R>::T);
+    const size_t line = (size_t)fft_line_pitch(P) * sizeof(typename C2<R>::T);
     const size_t budget = 96 * 1024;
     while (c.F > 1 && (size_t)c.F * line > budget) c.F >>= 1;
     while (c.F > 1 && c.F / 2 >= units) c.F >>= 1;

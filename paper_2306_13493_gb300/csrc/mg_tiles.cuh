@@ -57,6 +57,28 @@ template <typename T> __device__ __forceinline__ T recip(T d);
 template <> __device__ __forceinline__ float recip<float>(float d) { return __frcp_rn(d); }
 template <> __device__ __forceinline__ double recip<double>(double d) { return 1.0 / d; }
 
+// Gauss-Seidel update of the vertices of colour `color` ((gi + gj) % 2) in the
+// local box [lo, hix] x [lo, hiy] of the window.  Lane x of warp y handles the
+// column pair (2x, 2x+1) of rows y + 8b, i.e. exactly the one element of each
+// pair that has the colour, so no lane idles.
+template <typename T>
+__device__ __forceinline__ void tile_color_pass(T *sz, const T *sb, const T *scx, const T *scy,
+                                                const T *sinv, int ox, int oy, int n, int color,
+                                                int lo, int hix, int hiy) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) {
+        const int lj = ty + 8 * bb;
+        const int li = 2 * tx + ((ox + oy + lj + color) & 1);
+        if (li < lo || li > hix || lj < lo || lj > hiy) continue;
+        const int gi = ox + li, gj = oy + lj;
+        if (gi < 1 || gi > n - 1 || gj < 0 || gj > n) continue;
+        const int l = lj * MG_SW + li;
+        sz[l] = (sb[l] + scx[l - 1] * sz[l - 1] + scx[l] * sz[l + 1] +
+                 scy[l - MG_SW] * sz[l - MG_SW] + scy[l] * sz[l + MG_SW]) * sinv[l];
+    }
+}
+
 // Element e (0..7) of this thread: local (li, lj) and offset in the window.
 #define MG_ELEM(e, li, lj, l)                                   \
     const int li = (threadIdx.x & 31) + 32 * ((e) & 1);         \
@@ -106,14 +128,7 @@ __global__ void __launch_bounds__(MG_THREADS) mg_down_kernel(
     }
     __syncthreads();
     // black on local [2, SW-2] x [2, SH-2]
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        MG_ELEM(e, li, lj, l);
-        if (li < 2 || li > MG_SW - 2 || lj < 2 || lj > MG_SH - 2) continue;
-        if (!((unk >> e) & 1) || !(((ox + li) + (oy + lj)) & 1)) continue;
-        sz[l] = (sb[l] + scx[l - 1] * sz[l - 1] + scx[l] * sz[l + 1] +
-                 scy[l - MG_SW] * sz[l - MG_SW] + scy[l] * sz[l + MG_SW]) * sinv[l];
-    }
+    tile_color_pass(sz, sb, scx, scy, sinv, ox, oy, n, 1, 2, MG_SW - 2, MG_SH - 2);
     __syncthreads();
     // fine residual on local [3, SW-3] x [3, SH-3], in place of b
 #pragma unroll
@@ -216,20 +231,10 @@ __global__ void __launch_bounds__(MG_THREADS) mg_up_kernel(
     }
     __syncthreads();
     // black on local [1, UW-2] x [1, UH-2], then red on [2, UW-3] x [2, UH-3]
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-        const int lo = 1 + pass;
-        const int color = pass == 0 ? 1 : 0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            MG_ELEM(e, li, lj, l);
-            if (li < lo || li > UW - 1 - lo || lj < lo || lj > UH - 1 - lo) continue;
-            if (!((unk >> e) & 1) || ((((ox + li) + (oy + lj)) & 1) != color)) continue;
-            sz[l] = (sb[l] + scx[l - 1] * sz[l - 1] + scx[l] * sz[l + 1] +
-                     scy[l - MG_SW] * sz[l - MG_SW] + scy[l] * sz[l + MG_SW]) * sinv[l];
-        }
-        __syncthreads();
-    }
+    tile_color_pass(sz, sb, scx, scy, sinv, ox, oy, n, 1, 1, UW - 2, UH - 2);
+    __syncthreads();
+    tile_color_pass(sz, sb, scx, scy, sinv, ox, oy, n, 0, 2, UW - 3, UH - 3);
+    __syncthreads();
     // owned fine vertices: local [2, 2 + 2 CW) x [2, 2 + 2 CH)
     T rz = T(0);
 #pragma unroll
