@@ -129,13 +129,15 @@ def level_estimate(emb, mask_f, mask_c, seed, level, first_sample, count,
 
 
 def default_masks(emb, smoothing, finest):
-    """Masks for one level: plain CE (both full) or reading A of the coarse
-    mask: fine keeps s - tau_l (none dropped on the finest level), coarse keeps
-    s/4 - tau_(l-1) of this level's eigenvalues, tau = sqrt(s)."""
+    """Masks (fine, coarse) for one level.  Plain CE: both full.  MLMC-CES
+    (§3.5 estimator; §4: the coarse QoI is computed with the smoothed sample
+    used for the fine QoI): the smoothed sample keeps s - tau_l eigenvalues,
+    tau_l = sqrt(s_l), and drives both grids; on the finest level the fine
+    field is unsmoothed (§3.5) while the coarse field keeps the smoothed one."""
     s = emb.s
     if not smoothing:
         full = np.ones(emb.Lam.shape, dtype=bool)
         return full, full
-    keep_f = -1 if finest else s - tau_sqrt_s(s)
-    keep_c = s // 4 - tau_sqrt_s(s // 4)
-    return em.smoothing_mask(emb.Lam, keep_f), em.smoothing_mask(emb.Lam, keep_c)
+    smooth = em.smoothing_mask(emb.Lam, s - tau_sqrt_s(s))
+    fine = np.ones(emb.Lam.shape, dtype=bool) if finest else smooth
+    return fine, smooth

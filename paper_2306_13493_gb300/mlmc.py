@@ -1,0 +1,171 @@
+"""Multilevel Monte Carlo driver on top of the C ABI (host orchestration only).
+
+Every sample -- field, fine and coarse Darcy solves, level differences, level
+sums -- is computed by ``mlmc_level_estimate`` on the GPU; this module keeps
+the per-level running sums, the measured cost per sample, and applies the
+formulas of the paper's §3.3-3.5 and §4:
+
+* estimator, Eq. (3.5): Q_hat = sum_l mean(Y_l) (the MLMC-CES estimator of
+  §3.5 when the levels were set up with the smoothing masks);
+* optimal sample sizes, Eq. (3.6) (``mlmc_optimal_samples`` of the C ABI);
+* Richardson bias estimate of §4: |E[Q_h - Q]| ~ |E[Y_L]| / (2^alpha - 1);
+* rates alpha, beta, gamma by least squares on log2 |E Y_l|, log2 V[Y_l],
+  log2 C_l against l (§4).
+
+The cost of a sample on level l is the GPU time of its level estimate
+divided by its sample count (CUDA events on the launching stream).
+"""
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+import numpy as np
+
+from . import sce
+
+
+@dataclass
+class LevelStats:
+    level: int
+    n: int
+    N: int = 0
+    sumY: float = 0.0
+    sumY2: float = 0.0
+    sumQ: float = 0.0
+    sumQ2: float = 0.0
+    seconds: float = 0.0
+    iters: int = 0
+    next_sample: int = 0
+
+    @property
+    def mean(self):
+        return self.sumY / self.N if self.N else 0.0
+
+    @property
+    def var(self):
+        if self.N < 2:
+            return 0.0
+        m = self.mean
+        return max((self.sumY2 - self.N * m * m) / (self.N - 1), 0.0)
+
+    @property
+    def var_q(self):
+        if self.N < 2:
+            return 0.0
+        m = self.sumQ / self.N
+        return max((self.sumQ2 - self.N * m * m) / (self.N - 1), 0.0)
+
+    @property
+    def cost(self):
+        return self.seconds / self.N if self.N else 0.0
+
+
+@dataclass
+class MLMCResult:
+    estimate: float
+    rmse: float
+    stat_error: float
+    bias: float
+    seconds: float
+    levels: List[LevelStats] = field(default_factory=list)
+    N_opt: Optional[List[int]] = None
+
+
+class LevelRunner:
+    """Runs batches of one MLMC level through mlmc_level_estimate and accumulates sums."""
+
+    def __init__(self, emb, level, seed, qoi=sce.QOI_POINT, f=1.0, rtol=1e-10, precision=32,
+                 maxit=2000, max_batch=65535, stream=None):
+        import torch
+        self.torch = torch
+        self.emb = emb
+        self.stats = LevelStats(level=level, n=emb.n)
+        self.seed, self.qoi, self.f, self.rtol = seed, qoi, f, rtol
+        self.precision, self.maxit, self.max_batch = precision, maxit, max_batch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+
+    def run(self, count):
+        torch = self.torch
+        st = self.stats
+        while count > 0:
+            c = min(count, self.max_batch)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            out, _ = sce.mlmc_level_estimate(self.emb, self.seed, st.level, st.next_sample, c,
+                                             qoi_index=self.qoi, f=self.f, rtol=self.rtol,
+                                             maxit=self.maxit, precision=self.precision,
+                                             stream=self.stream.cuda_stream,
+                                             allow_not_converged=True)
+            e1.record(self.stream)
+            e1.synchronize()
+            st.seconds += e0.elapsed_time(e1) / 1000.0
+            st.N += out.N
+            st.sumY += out.sumY
+            st.sumY2 += out.sumY2
+            st.sumQ += out.sumQf
+            st.sumQ2 += out.sumQf2
+            st.iters += out.total_iters
+            st.next_sample += c
+            count -= c
+        return st
+
+
+def fit_rate(levels, values):
+    """Least-squares slope of -log2(values) against the level index (a rate)."""
+    lv = np.asarray(levels, dtype=float)
+    y = np.log2(np.maximum(np.asarray(values, dtype=float), 1e-300))
+    if len(lv) < 2:
+        return float("nan")
+    A = np.vstack([lv, np.ones_like(lv)]).T
+    slope = np.linalg.lstsq(A, y, rcond=None)[0][0]
+    return float(-slope)
+
+
+def rates(stats: List[LevelStats]):
+    """(alpha, beta, gamma) of §4 from levels l >= 1: |E Y_l| ~ 2^(-alpha l),
+    V[Y_l] ~ 2^(-beta l), C_l ~ 2^(gamma l)."""
+    s = [x for x in stats if x.level >= 1 and x.N > 1]
+    lv = [x.level for x in s]
+    alpha = fit_rate(lv, [abs(x.mean) for x in s])
+    beta = fit_rate(lv, [x.var for x in s])
+    gamma = -fit_rate(lv, [x.cost for x in s])
+    return alpha, beta, gamma
+
+
+def richardson_bias(stats: List[LevelStats], alpha):
+    """§4: |E[Q_h - Q]| ~ |E[Y_L]| / (2^alpha - 1) on the finest level L."""
+    if not math.isfinite(alpha) or alpha <= 0:
+        alpha = 1.0
+    return abs(stats[-1].mean) / (2.0 ** alpha - 1.0)
+
+
+def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rounds=10):
+    """MLMC with the fixed level set of `runners` to a root-mean-square error eps
+    (variance share eps^2/2, Eq. (3.6)): pilot samples, then the optimal N_l
+    from the measured V_l and C_l, topped up until no level needs more than 1 %
+    extra samples.  Returns the estimate, the estimated RMSE (statistical error
+    and Richardson bias) and the GPU seconds spent."""
+    pilot = pilot or [100] * len(runners)
+    for r, p in zip(runners, pilot):
+        if r.stats.N < p:
+            r.run(p - r.stats.N)
+    N_opt = None
+    for _ in range(max_rounds):
+        V = [max(r.stats.var, 1e-300) for r in runners]
+        C = [max(r.stats.cost, 1e-12) for r in runners]
+        N_opt = sce.mlmc_optimal_samples(V, C, eps)
+        extra = [max(0, int(n) - r.stats.N) for n, r in zip(N_opt, runners)]
+        if all(e <= 0.01 * r.stats.N for e, r in zip(extra, runners)):
+            break
+        for e, r in zip(extra, runners):
+            if e > 0:
+                r.run(e)
+    stats = [r.stats for r in runners]
+    est = sum(s.mean for s in stats)
+    stat_err = math.sqrt(sum(s.var / s.N for s in stats))
+    a = alpha if alpha is not None else rates(stats)[0]
+    bias = richardson_bias(stats, a)
+    return MLMCResult(estimate=est, rmse=math.sqrt(stat_err ** 2 + bias ** 2), stat_error=stat_err,
+                      bias=bias, seconds=sum(s.seconds for s in stats), levels=stats,
+                      N_opt=[int(n) for n in N_opt])

@@ -17,15 +17,23 @@ def sce():
 
 @pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("level,smooth,finest,qi", [(0, False, True, 0), (1, False, True, 0),
-                                                   (2, True, False, 1), (1, True, True, 2)])
+                                                   (2, True, False, 1), (1, True, True, 2),
+                                                   (3, "quarter", False, 1)])
 def test_level_estimate_matches_oracle(sce, level, smooth, finest, qi, precision):
+    """smooth = "quarter": a coarse field that keeps only s/4 - sqrt(s/4) of
+    the level's eigenvalues (distinct fine and coarse masks on a non-finest
+    level)."""
     import torch
+    import workloads
     n = 16
     oe = oem.setup_embedding(ocv.MATERN, 0.5, 0.02, 1.0, n, oem.PAD_SMOOTH)
-    mf, mc = omlmc.default_masks(oe, smooth, finest)
     s, P = oe.s, oe.P
-    keep_f = -1 if (not smooth or finest) else s - P
-    keep_c = -1 if not smooth else s // 4 - P // 2
+    if smooth == "quarter":
+        keep_f, keep_c = s - P, s // 4 - P // 2
+        mf, mc = oem.smoothing_mask(oe.Lam, keep_f), oem.smoothing_mask(oe.Lam, keep_c)
+    else:
+        mf, mc = omlmc.default_masks(oe, smooth, finest)
+        keep_f, keep_c = workloads.keep_counts(P, finest, smooth)
     emb = sce.ce_setup_embedding(ocv.MATERN, 0.5, 0.02, 1.0, n, pad_mode=oem.PAD_SMOOTH,
                                  keep_fine=keep_f, keep_coarse=keep_c)
     count, seed, first = 9, 2, 5

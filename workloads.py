@@ -59,10 +59,10 @@ def shard_first_sample(step, rank, world, N):
 
 
 def keep_counts(P, finest, smoothing):
-    """(keep_fine, keep_coarse) for one level: tau = sqrt(s) dropped on the
-    fine field (none on the finest level), s/4 - sqrt(s/4) kept for the coarse
-    field; -1 = no truncation."""
+    """(keep_fine, keep_coarse) for one level of MLMC-CES: the smoothed sample
+    drops tau = sqrt(s) = P eigenvalues and drives both grids, except that the
+    finest level's fine field is unsmoothed; -1 = no truncation."""
     if not smoothing:
         return -1, -1
     s = P * P
-    return (-1 if finest else s - P), (s // 4 - P // 2)
+    return (-1 if finest else s - P), s - P
