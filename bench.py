@@ -176,13 +176,21 @@ def _oracle_task(task):
     return l, time.perf_counter() - t0
 
 
+def _oracle_ready(_):
+    time.sleep(0.2)
+    return isinstance(_ORACLE_LEVELS, Exception)
+
+
 def oracle_pool(wl):
+    """Spawned worker pool with the oracle set-up done in every worker (the
+    set-up finishes here, so it never overlaps a timed GPU region)."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     env_threads = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
     os.environ.update(env_threads)
     ctx = mp.get_context("spawn")
     pool = ctx.Pool(cores, initializer=_oracle_init, initargs=(wl,))
+    pool.map(_oracle_ready, range(2 * cores), chunksize=1)
     return pool, cores
 
 
@@ -423,6 +431,21 @@ def run_ours(args):
                     str(max(1, c // 4)) for c in CPU_SAMPLES) + " samples on levels 0..5, "
                 "scaled to the N_l mix"}
 
+    # MLMC to RMSE 1e-3 (Eq. (3.6) sample sizes from pilot runs; §4 bias estimate)
+    ttr = None
+    if rank == 0 and not args.no_fp64_path:
+        from paper_2306_13493_gb300 import mlmc as gm
+        runners = [gm.LevelRunner(embs[l], l, wl.seed + 1000, qoi=wl.qoi, f=wl.f, rtol=wl.rtol,
+                                  precision=prec, stream=stream) for (l, _, _) in wl.levels]
+        res = gm.run_to_rmse(runners, 1e-3, pilot=[400, 200, 100, 50, 20, 10])
+        a, b, g = gm.rates(res.levels)
+        fp64_s = sum(s.N * per[s.level] for s in res.levels) if fp64 else None
+        ttr = {"eps": 1e-3, "gpu_seconds": round(res.seconds, 4), "estimate": res.estimate,
+               "rmse_est": res.rmse, "stat_error": res.stat_error, "bias_est": res.bias,
+               "N": [s.N for s in res.levels], "alpha": a, "beta": b, "gamma": g,
+               "fp64_per_sample_path_seconds": round(fp64_s, 3) if fp64_s else None,
+               "speedup_vs_fp64_path": round(fp64_s / res.seconds, 1) if fp64_s else None}
+
     cpu = None
     if want_cpu:
         try:
@@ -444,9 +467,11 @@ def run_ours(args):
             "config": {"workload": wl.describe(), "precision": prec,
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": f"dp{world} (samples sharded, level sums all-reduced)"},
-            "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(v[2] for v in prof.values())),
+            "clocks": clk, "e2e": e2e,
+            "gpu_launches": int(sum(v[2] for v in prof.values())) * args.steps,
+            "gpu_launches_per_step": int(sum(v[2] for v in prof.values())),
             "roofline": roof, "kernels": kernels, "per_level": per_level,
-            "fp64_per_sample_path": fp64, "cpu_baseline": cpu,
+            "fp64_per_sample_path": fp64, "time_to_rmse": ttr, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -86,7 +86,7 @@ __device__ __forceinline__ void tile_color_pass(T *sz, const T *sb, const T *scx
     const int l = lj * MG_SW + li
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS) mg_down_kernel(
+__global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ z, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
     constexpr int LS = MG_SW * MG_SH;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(MG_THREADS) mg_down_kernel(
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS) mg_up_kernel(
+__global__ void __launch_bounds__(MG_THREADS, 5) mg_up_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x, const int *__restrict__ act,
     double *__restrict__ part_rz, int nblk) {
@@ -222,12 +222,11 @@ __global__ void __launch_bounds__(MG_THREADS) mg_up_kernel(
         sinv[l] = (li >= 1 && lj >= 1) ? recip(scx[l - 1] + scx[l] + scy[l - MG_SW] + scy[l]) : T(0);
         const int gi = ox + li, gj = oy + lj;
         const int c = ((gj >> 1) - coy) * MG_CCW + ((gi >> 1) - cox);
-        T val;
-        if (!(gi & 1) && !(gj & 1)) val = szc[c];
-        else if ((gi & 1) && !(gj & 1)) val = T(0.5) * (szc[c] + szc[c + 1]);
-        else if (!(gi & 1) && (gj & 1)) val = T(0.5) * (szc[c] + szc[c + MG_CCW]);
-        else val = T(0.25) * (szc[c] + szc[c + 1] + szc[c + MG_CCW] + szc[c + MG_CCW + 1]);
-        sz[l] += val;
+        // bilinear weights: (1, 0) on even fine indices, (1/2, 1/2) on odd ones
+        const T wx1 = (gi & 1) ? T(0.5) : T(0), wy1 = (gj & 1) ? T(0.5) : T(0);
+        const T wx0 = T(1) - wx1, wy0 = T(1) - wy1;
+        sz[l] += wy0 * (wx0 * szc[c] + wx1 * szc[c + 1]) +
+                 wy1 * (wx0 * szc[c + MG_CCW] + wx1 * szc[c + MG_CCW + 1]);
     }
     __syncthreads();
     // black on local [1, UW-2] x [1, UH-2], then red on [2, UW-3] x [2, UH-3]

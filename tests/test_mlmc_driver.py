@@ -1,0 +1,68 @@
+"""Host logic of the MLMC driver (Eq. (3.5), (3.6) and the §4 bias and rate
+estimates) with a synthetic level sampler standing in for the GPU."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlmc as omlmc
+
+
+class FakeRunner:
+    """Level l draws Y ~ N(mu_l, V_l) at cost C_l seconds per sample."""
+
+    def __init__(self, level, mu, V, C, rng):
+        from paper_2306_13493_gb300.mlmc import LevelStats
+        self.stats = LevelStats(level=level, n=16 << level)
+        self.mu, self.V, self.C, self.rng = mu, V, C, rng
+
+    def run(self, count):
+        y = self.rng.normal(self.mu, math.sqrt(self.V), count)
+        st = self.stats
+        st.N += count
+        st.sumY += float(y.sum())
+        st.sumY2 += float((y * y).sum())
+        st.seconds += self.C * count
+        st.next_sample += count
+        return st
+
+
+@pytest.fixture(scope="module")
+def drv():
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    sce.load()
+    from paper_2306_13493_gb300 import mlmc
+    return mlmc
+
+
+def test_rate_fits_recover_power_laws(drv):
+    lv = np.arange(1, 6)
+    assert abs(drv.fit_rate(lv, 3.0 * 2.0 ** (-1.3 * lv)) - 1.3) < 1e-12
+    stats = []
+    for l in range(0, 6):
+        s = drv.LevelStats(level=l, n=16 << l, N=10)
+        mean, var, cost = 0.5 * 2.0 ** (-1.0 * l), 0.1 * 2.0 ** (-1.9 * l), 1e-6 * 2.0 ** (1.87 * l)
+        s.sumY = mean * s.N
+        s.sumY2 = var * (s.N - 1) + s.N * mean * mean
+        s.seconds = cost * s.N
+        stats.append(s)
+    a, b, g = drv.rates(stats)
+    assert abs(a - 1.0) < 1e-9 and abs(b - 1.9) < 1e-9 and abs(g - 1.87) < 1e-9
+    # §4 Richardson: |E Y_L| / (2^alpha - 1)
+    assert abs(drv.richardson_bias(stats, a) - 0.5 * 2.0 ** -5 / (2.0 - 1.0)) < 1e-15
+
+
+def test_run_to_rmse_meets_variance_target(drv):
+    rng = np.random.default_rng(7)
+    V = [1e-3, 2e-4, 5e-5, 1.2e-5]
+    C = [1e-6, 4e-6, 1.6e-5, 6.4e-5]
+    runners = [FakeRunner(l, 0.0, V[l], C[l], rng) for l in range(4)]
+    eps = 2e-3
+    res = drv.run_to_rmse(runners, eps, pilot=[200] * 4, alpha=1.0)
+    # Eq. (3.6) with the true V, C: the sampled N must be close to it
+    want = omlmc.optimal_samples(V, C, eps)
+    got = np.array([r.stats.N for r in runners])
+    assert np.all(got >= 0.7 * want) and np.all(got <= 1.5 * want + 200)
+    assert res.stat_error <= eps / math.sqrt(2.0) * 1.15
+    assert abs(res.estimate - sum(r.stats.mean for r in runners)) < 1e-15
