@@ -219,6 +219,38 @@ int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uint64_t seed,
                         uint64_t first_sample, int count, int qoi_index, mlmc_level_sums *out,
                         double *Y, double *qoi_f, double *qoi_c, void *stream);
 
+/*
+ * One level's share of an MLMC step for mlmc_estimate_levels: the fields
+ * of mlmc_level_estimate's arguments (emb, level, first_sample, count, Y,
+ * qoi_f, qoi_c; same meaning and ownership) and its results.
+ */
+typedef struct mlmc_level_task {
+    ce_embedding_t emb;
+    uint32_t level;
+    uint64_t first_sample;
+    int count;
+    double *Y;             /* device double[count] or NULL           */
+    double *qoi_f, *qoi_c; /* device double[count*3] or NULL         */
+    mlmc_level_sums sums;  /* out: the level sums                    */
+    int status;            /* out: that level's mlmc_level_estimate status */
+} mlmc_level_task;
+
+/*
+ * mlmc_estimate_levels -- all levels of one MLMC step (Eq. (3.5) needs the
+ * level sums of every l = 0..L): each task computes exactly what
+ * mlmc_level_estimate computes for it (bit-identical results), with p->n
+ * taken from the task's handle.  With max_concurrency > 1 up to that many
+ * levels run at once, each on its own CUDA streams driven by its own host
+ * thread, the coarse solves of a level on a second stream; the largest
+ * levels start first.  The streams start after the work queued on `stream`
+ * and `stream` waits for all of them.  max_concurrency <= 1 runs the tasks
+ * one after another on `stream`.  Synchronises the streams it uses.
+ * Returns the first hard error of a task, else CE_ERR_NOT_CONVERGED if a
+ * task reported it, else CE_OK; every task's own status is in its `status`.
+ */
+int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
+                         mlmc_level_task *tasks, int ntasks, int max_concurrency, void *stream);
+
 /* Eq. (3.6): N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)),
  * l = 0..L.  V, C, N: host arrays of length L+1 (C > 0, V >= 0). */
 int mlmc_optimal_samples(int L_plus_1, const double *V, const double *C, double eps, long long *N);

@@ -567,6 +567,7 @@ struct Solver {
     int n[MAXLEV];
     Launch ln[MAXLEV];
     T *cx[MAXLEV], *cy[MAXLEV], *b[MAXLEV], *z[MAXLEV];
+    T *zpre[MAXLEV] = {};   // pre-smoothed z of the tiled levels (fused cycle)
     T *d = nullptr, *p = nullptr, *q = nullptr;
     double *u64 = nullptr, *r64 = nullptr, *cx64 = nullptr, *cy64 = nullptr;
     double *part = nullptr, *part2 = nullptr;
@@ -669,7 +670,7 @@ struct Solver {
         for (int L = 0; L < Lt; ++L) {
             SceProf pr(KP_MG_DOWN, st, vb(L, 4.0) + vb(L + 1, 1.0));
             mg_down_kernel<T><<<dim3(tiles_n[L], count), MG_THREADS, smem, st>>>(
-                cx[L], cy[L], b[L], z[L], n[L], b[L + 1], tiles_x[L], sc.act_in);
+                cx[L], cy[L], b[L], zpre[L], n[L], b[L + 1], tiles_x[L], sc.act_in);
         }
         const bool rz_tail = want_rz && Lt == 0;
         switch (n[Lt]) {
@@ -681,7 +682,7 @@ struct Solver {
         for (int L = Lt - 1; L >= 0; --L) {
             SceProf pr(KP_MG_UP, st, vb(L, 5.0) + vb(L + 1, 1.0));
             mg_up_kernel<T><<<dim3(tiles_n[L], count), MG_THREADS, smem, st>>>(
-                cx[L], cy[L], b[L], z[L], n[L], z[L + 1], tiles_x[L], sc.act_in,
+                cx[L], cy[L], b[L], zpre[L], z[L], n[L], z[L + 1], tiles_x[L], sc.act_in,
                 (want_rz && L == 0) ? part : nullptr, tiles_n[0]);
         }
     }
@@ -744,6 +745,8 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         S.fused = !(e && atoi(e) == 0);
     }
     S.plan_fused();
+    if (S.fused)
+        for (int L = 0; L < S.Lt; ++L) SCE_TRY(S.alloc(&S.zpre[L], (size_t)count * S.ln[L].V));
     const int nblk_part = std::max(S.ln[0].nblk, S.rz_blocks());
     SCE_TRY(S.alloc(&S.part, (size_t)count * nblk_part));
     SCE_TRY(S.alloc(&S.part2, (size_t)count * nblk_part));

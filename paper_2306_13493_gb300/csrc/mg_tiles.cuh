@@ -11,10 +11,12 @@
 // repeated per pass; 1/diag is computed once per element.
 //
 //   mg_down: pre-smoothing from a zero guess (red then black Gauss-Seidel),
-//            fine residual, full-weighting restriction -> z (fine), b (coarse)
-//   mg_up  : z += bilinear prolongation of the coarse correction, then
+//            fine residual, full-weighting restriction -> zpre (fine), b (coarse)
+//   mg_up  : z = zpre + bilinear prolongation of the coarse correction, then
 //            post-smoothing (black then red) -> z (fine); optionally the
-//            partial sums of r . z (level 0, for CG's beta)
+//            partial sums of r . z (level 0, for CG's beta).  zpre and z are
+//            distinct arrays: a tile reads zpre in its halo, which other
+//            tiles of the same launch own and write to z.
 //   mg_tail: the whole V-cycle of the coarse levels n <= NT_N of one sample in
 //            one thread block (shared memory)
 // Together with the exact coarsest solve this is the same symmetric V(1,1)
@@ -88,7 +90,7 @@ __device__ __forceinline__ void tile_color_pass(T *sz, const T *sb, const T *scx
 template <typename T>
 __global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
-    T *__restrict__ z, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
+    T *__restrict__ zpre, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
     constexpr int LS = MG_SW * MG_SH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sb = reinterpret_cast<T *>(smem_raw);
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
         bcs[J * wc + I] = acc;
     }
     // owned fine vertices: local [4, 4 + 2 CW) x [4, 4 + 2 CH)
-    T *zs = z + s * V;
+    T *zs = zpre + s * V;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         MG_ELEM(e, li, lj, l);
@@ -174,8 +176,8 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
 template <typename T>
 __global__ void __launch_bounds__(MG_THREADS, 5) mg_up_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
-    T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x, const int *__restrict__ act,
-    double *__restrict__ part_rz, int nblk) {
+    const T *__restrict__ zpre, T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x,
+    const int *__restrict__ act, double *__restrict__ part_rz, int nblk) {
     constexpr int LS = MG_SW * MG_SH;
     constexpr int UW = 2 * MG_CW + 4, UH = 2 * MG_CH + 4;   // used window: 62 x 30
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_up_kernel(
     const int ox = 2 * I0 - 2, oy = 2 * J0 - 2;
     const int cox = I0 - 1, coy = J0 - 1;
     const T *bs = b + s * V, *xs = cx + s * V, *ys = cy + s * V, *zcs = zc + s * Vc;
+    const T *zps = zpre + s * V;
     T *zs = z + s * V;
     for (int c = threadIdx.x; c < MG_CCW * MG_CCH; c += MG_THREADS) {
         const int ci = c % MG_CCW, cj = c / MG_CCW;
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_up_kernel(
         sb[l] = in ? bs[g] : T(0);
         scx[l] = in ? xs[g] : T(0);
         scy[l] = in ? ys[g] : T(0);
-        sz[l] = in ? zs[g] : T(0);
+        sz[l] = in ? zps[g] : T(0);
         if (in && gi >= 1 && gi <= n - 1) unk |= 1u << e;
     }
     __syncthreads();

@@ -1,7 +1,18 @@
 // One MLMC level of Algorithm 1 (Algorithm 2 with a smoothed handle):
 // fields -> fine and coarse Darcy solves -> Y_l = Q_f - Q_c (Y_0 = Q_f) ->
 // level sums (N, sum Y, sum Y^2, sum Q_f, sum Q_f^2) for Eq. (3.5).
+//
+// mlmc_estimate_levels runs several levels at once: one host worker thread
+// per level in flight, each level on its own CUDA streams (the coarse solve
+// of a level on a second stream, driven by a second host thread, once the
+// fields of the chunk exist).  The solvers' convergence checks synchronise
+// only their own stream, so the phases of one level that leave SMs idle
+// (coarse-grid cycles, reductions, host checks) are filled by the others.
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <future>
+#include <thread>
 #include <vector>
 
 #include "sce_internal.cuh"
@@ -40,31 +51,47 @@ __global__ void level_sums_kernel(const double *__restrict__ Y, const double *__
     if (threadIdx.x < 4) out4[threadIdx.x] = sh[threadIdx.x][0];
 }
 
-}  // namespace
 
-extern "C" int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uint64_t seed,
-                                   uint32_t level, uint64_t first_sample, int count,
-                                   int qoi_index, mlmc_level_sums *out, double *Y, double *qoi_f,
-                                   double *qoi_c, void *stream) {
-    if (!e || !p || !out || count < 0 || qoi_index < 0 || qoi_index > 2) return CE_ERR_INVALID_ARG;
-    if (p->n != e->n || (p->precision != 32 && p->precision != 64)) return CE_ERR_INVALID_ARG;
-    *out = mlmc_level_sums{};
+struct LevelArgs {
+    ce_embedding_t e;
+    uint32_t level;
+    uint64_t first_sample;
+    int count;
+    double *Y, *qoi_f, *qoi_c;
+    mlmc_level_sums *out;
+};
+
+// One level on stream st; the coarse solves go to stream stc (a second host
+// thread) when stc != st, otherwise they follow the fine solve on st.
+static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, int qoi_index,
+                     cudaStream_t st, cudaStream_t stc) {
+    ce_embedding_t e = a.e;
+    const int count = a.count;
+    *a.out = mlmc_level_sums{};
     if (count == 0) return CE_OK;
-    cudaStream_t st = as_stream(stream);
     const int n = e->n, nc = n / 2;
-    const bool coarse = level > 0;
+    const bool coarse = a.level > 0;
+    const bool split = coarse && stc != st;
     const size_t es = p->precision == 64 ? sizeof(double) : sizeof(float);
     const long long Vf = (long long)(n + 1) * (n + 1), Vc = (long long)(nc + 1) * (nc + 1);
     // chunk: bound the number of fine vertices resident at once
-    const long long max_vertices = 1LL << 27;
+    // (SCE_MLMC_CHUNK_VERTICES lowers the bound, to exercise the chunk loop)
+    long long max_vertices = 1LL << 27;
+    if (const char *ev = getenv("SCE_MLMC_CHUNK_VERTICES"))
+        max_vertices = std::max(1LL, std::min(max_vertices, atoll(ev)));
     int chunk = (int)std::max<long long>(1, std::min<long long>(count, max_vertices / Vf));
     chunk = std::min(chunk, 65535);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CE_ERR_CUDA;
 
     void *kf = nullptr, *kc = nullptr;
     double *qf = nullptr, *qc = nullptr, *Yd = nullptr, *sums = nullptr;
+    cudaEvent_t ev_field = nullptr, ev_coarse = nullptr;
     std::vector<void *> owned;
     auto cleanup = [&]() {
         for (void *q : owned) sce_free(q, st);
+        if (ev_field) cudaEventDestroy(ev_field);
+        if (ev_coarse) cudaEventDestroy(ev_coarse);
     };
     int rc = CE_OK;
     auto A = [&](void **ptr, size_t bytes) {
@@ -74,41 +101,68 @@ extern "C" int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uin
     };
     if ((rc = A(&kf, (size_t)chunk * Vf * es)) != CE_OK) { cleanup(); return rc; }
     if (coarse && (rc = A(&kc, (size_t)chunk * Vc * es)) != CE_OK) { cleanup(); return rc; }
-    if (!qoi_f && (rc = A((void **)&qf, (size_t)chunk * 3 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
-    if (coarse && !qoi_c && (rc = A((void **)&qc, (size_t)chunk * 3 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
-    if (!Y && (rc = A((void **)&Yd, (size_t)chunk * sizeof(double))) != CE_OK) { cleanup(); return rc; }
+    if (!a.qoi_f && (rc = A((void **)&qf, (size_t)chunk * 3 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
+    if (coarse && !a.qoi_c && (rc = A((void **)&qc, (size_t)chunk * 3 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
+    if (!a.Y && (rc = A((void **)&Yd, (size_t)chunk * sizeof(double))) != CE_OK) { cleanup(); return rc; }
     if ((rc = A((void **)&sums, 4 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
+    if (split && (cudaEventCreateWithFlags(&ev_field, cudaEventDisableTiming) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&ev_coarse, cudaEventDisableTiming) != cudaSuccess)) {
+        cleanup();
+        return CE_ERR_CUDA;
+    }
 
-    darcy_problem pc = *p;
+    darcy_problem pf = *p, pc = *p;
+    pf.n = n;
     pc.n = nc;
+    const int qmask_f = a.qoi_f ? 7 : (1 << qoi_index);
+    const int qmask_c = a.qoi_c ? 7 : (1 << qoi_index);
     double acc[4] = {0, 0, 0, 0};
     int n_failed = 0, max_it = 0;
     long long tot_it = 0;
     int result = CE_OK;
-    for (int c0 = 0; c0 < count; c0 += chunk) {
-        const int cn = std::min(chunk, count - c0);
-        double *qf_c = qoi_f ? qoi_f + 3 * (size_t)c0 : qf;
-        double *qc_c = coarse ? (qoi_c ? qoi_c + 3 * (size_t)c0 : qc) : nullptr;
-        double *Y_c = Y ? Y + c0 : Yd;
-        rc = sce_sample_batch_impl(e, seed, level, first_sample + (uint64_t)c0, cn, p->precision, kf,
-                                   coarse ? kc : nullptr, st);
-        if (rc != CE_OK) { cleanup(); return rc; }
-        int mi[2] = {0, 0}, nf = 0;
-        rc = sce_darcy_solve_impl(p, kf, cn, qf_c, nullptr, nullptr, nullptr, st, mi, &nf,
-                                  qoi_f ? 7 : (1 << qoi_index));
-        if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
-        if (rc == CE_ERR_NOT_CONVERGED) result = rc;
+    auto account = [&](int r, const int *mi, int nf) {
+        if (r == CE_ERR_NOT_CONVERGED) result = r;
         n_failed += nf;
         max_it = std::max(max_it, mi[0]);
         tot_it += mi[1];
-        if (coarse) {
+    };
+    for (int c0 = 0; c0 < count; c0 += chunk) {
+        const int cn = std::min(chunk, count - c0);
+        double *qf_c = a.qoi_f ? a.qoi_f + 3 * (size_t)c0 : qf;
+        double *qc_c = coarse ? (a.qoi_c ? a.qoi_c + 3 * (size_t)c0 : qc) : nullptr;
+        double *Y_c = a.Y ? a.Y + c0 : Yd;
+        rc = sce_sample_batch_impl(e, seed, a.level, a.first_sample + (uint64_t)c0, cn,
+                                   p->precision, kf, coarse ? kc : nullptr, st);
+        if (rc != CE_OK) { cleanup(); return rc; }
+        int mi_c[2] = {0, 0}, nf_c = 0;
+        std::future<int> fut;
+        if (split) {
+            if (cudaEventRecord(ev_field, st) != cudaSuccess) { cleanup(); return CE_ERR_CUDA; }
+            fut = std::async(std::launch::async, [&, cn]() {
+                if (cudaSetDevice(dev) != cudaSuccess ||
+                    cudaStreamWaitEvent(stc, ev_field, 0) != cudaSuccess)
+                    return (int)CE_ERR_CUDA;
+                const int r = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, nullptr,
+                                                   stc, mi_c, &nf_c, qmask_c);
+                if (cudaEventRecord(ev_coarse, stc) != cudaSuccess) return (int)CE_ERR_CUDA;
+                return r;
+            });
+        }
+        int mi[2] = {0, 0}, nf = 0;
+        rc = sce_darcy_solve_impl(&pf, kf, cn, qf_c, nullptr, nullptr, nullptr, st, mi, &nf,
+                                  qmask_f);
+        const int rc_c = split ? fut.get() : CE_OK;
+        if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
+        account(rc, mi, nf);
+        if (split) {
+            if (rc_c != CE_OK && rc_c != CE_ERR_NOT_CONVERGED) { cleanup(); return rc_c; }
+            account(rc_c, mi_c, nf_c);
+            if (cudaStreamWaitEvent(st, ev_coarse, 0) != cudaSuccess) { cleanup(); return CE_ERR_CUDA; }
+        } else if (coarse) {
             rc = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, nullptr, st, mi, &nf,
-                                      qoi_c ? 7 : (1 << qoi_index));
+                                      qmask_c);
             if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
-            if (rc == CE_ERR_NOT_CONVERGED) result = rc;
-            n_failed += nf;
-            max_it = std::max(max_it, mi[0]);
-            tot_it += mi[1];
+            account(rc, mi, nf);
         }
         level_diff_kernel<<<(cn + 255) / 256, 256, 0, st>>>(qf_c, qc_c, cn, qoi_index, Y_c);
         level_sums_kernel<<<1, 256, 0, st>>>(Y_c, qf_c, cn, qoi_index, sums);
@@ -122,13 +176,130 @@ extern "C" int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uin
         for (int r = 0; r < 4; ++r) acc[r] += h[r];
     }
     cleanup();
-    out->N = count;
-    out->sumY = acc[0];
-    out->sumY2 = acc[1];
-    out->sumQf = acc[2];
-    out->sumQf2 = acc[3];
-    out->n_failed = n_failed;
-    out->max_iters = max_it;
-    out->total_iters = tot_it;
+    mlmc_level_sums &o = *a.out;
+    o.N = count;
+    o.sumY = acc[0];
+    o.sumY2 = acc[1];
+    o.sumQf = acc[2];
+    o.sumQf2 = acc[3];
+    o.n_failed = n_failed;
+    o.max_iters = max_it;
+    o.total_iters = tot_it;
     return result;
+}
+
+static bool valid_problem(const darcy_problem *p, int qoi_index) {
+    return p && qoi_index >= 0 && qoi_index <= 2 && (p->precision == 32 || p->precision == 64);
+}
+
+}  // namespace
+
+extern "C" int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uint64_t seed,
+                                   uint32_t level, uint64_t first_sample, int count,
+                                   int qoi_index, mlmc_level_sums *out, double *Y, double *qoi_f,
+                                   double *qoi_c, void *stream) {
+    if (!e || !out || count < 0 || !valid_problem(p, qoi_index) || p->n != e->n)
+        return CE_ERR_INVALID_ARG;
+    const cudaStream_t st = as_stream(stream);
+    return level_run(LevelArgs{e, level, first_sample, count, Y, qoi_f, qoi_c, out}, p, seed,
+                     qoi_index, st, st);
+}
+
+extern "C" int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
+                                    mlmc_level_task *tasks, int ntasks, int max_concurrency,
+                                    void *stream) {
+    if (!valid_problem(p, qoi_index) || ntasks < 0 || (ntasks > 0 && !tasks))
+        return CE_ERR_INVALID_ARG;
+    for (int i = 0; i < ntasks; ++i)
+        if (!tasks[i].emb || tasks[i].count < 0) return CE_ERR_INVALID_ARG;
+    for (int i = 0; i < ntasks; ++i) {
+        tasks[i].sums = mlmc_level_sums{};
+        tasks[i].status = CE_OK;
+    }
+    const cudaStream_t st = as_stream(stream);
+    auto args_of = [&](int i) {
+        mlmc_level_task &t = tasks[i];
+        return LevelArgs{t.emb, t.level, t.first_sample, t.count, t.Y, t.qoi_f, t.qoi_c, &t.sums};
+    };
+    auto combine = [&]() {
+        int worst = CE_OK;
+        for (int i = 0; i < ntasks; ++i) {
+            const int r = tasks[i].status;
+            if (r != CE_OK && r != CE_ERR_NOT_CONVERGED) return r;
+            if (r == CE_ERR_NOT_CONVERGED) worst = r;
+        }
+        return worst;
+    };
+    if (max_concurrency <= 1 || ntasks <= 1) {
+        for (int i = 0; i < ntasks; ++i) {
+            tasks[i].status = level_run(args_of(i), p, seed, qoi_index, st, st);
+            if (tasks[i].status != CE_OK && tasks[i].status != CE_ERR_NOT_CONVERGED) break;
+        }
+        return combine();
+    }
+
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    // streams: [2 i] fine, [2 i + 1] coarse of task i; all start after the
+    // work already queued on the caller's stream and the caller's stream
+    // waits for all of them at the end
+    std::vector<cudaStream_t> ss(2 * (size_t)ntasks, nullptr);
+    std::vector<cudaEvent_t> evs;
+    auto release = [&]() {
+        for (cudaStream_t s : ss)
+            if (s) cudaStreamDestroy(s);
+        for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+    };
+    auto new_event = [&](cudaEvent_t *ev) {
+        cudaError_t err = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (err == cudaSuccess) evs.push_back(*ev);
+        return err;
+    };
+    cudaEvent_t ev0;
+    if (new_event(&ev0) != cudaSuccess || cudaEventRecord(ev0, st) != cudaSuccess) {
+        release();
+        return CE_ERR_CUDA;
+    }
+    for (int i = 0; i < ntasks; ++i) {
+        for (int k = 0; k < (tasks[i].level > 0 ? 2 : 1); ++k) {
+            cudaStream_t &s = ss[2 * (size_t)i + k];
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamWaitEvent(s, ev0, 0) != cudaSuccess) {
+                release();
+                return CE_ERR_CUDA;
+            }
+        }
+    }
+    // largest levels first: they bound the makespan
+    std::vector<int> order(ntasks);
+    for (int i = 0; i < ntasks; ++i) order[i] = i;
+    auto work = [&](int i) {
+        const long long n = tasks[i].emb->n;
+        return (double)tasks[i].count * (double)((n + 1) * (n + 1)) * (tasks[i].level ? 1.25 : 1.0);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        if (cudaSetDevice(dev) != cudaSuccess) return;
+        for (int k; (k = next.fetch_add(1)) < ntasks;) {
+            const int i = order[k];
+            cudaStream_t sf = ss[2 * (size_t)i], sc = ss[2 * (size_t)i + 1];
+            tasks[i].status = level_run(args_of(i), p, seed, qoi_index, sf, sc ? sc : sf);
+        }
+    };
+    const int nthreads = std::min(max_concurrency, ntasks);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+    for (std::thread &t : pool) t.join();
+    for (cudaStream_t s : ss) {
+        if (!s) continue;
+        cudaEvent_t ev;
+        if (new_event(&ev) != cudaSuccess || cudaEventRecord(ev, s) != cudaSuccess ||
+            cudaStreamWaitEvent(st, ev, 0) != cudaSuccess) {
+            release();
+            return CE_ERR_CUDA;
+        }
+    }
+    release();
+    return combine();
 }

@@ -66,6 +66,13 @@ class mlmc_level_sums(ctypes.Structure):
 
 # name -> (restype, argtypes); the exported C ABI
 _P = ctypes.c_void_p
+class mlmc_level_task(ctypes.Structure):
+    _fields_ = [("emb", ctypes.c_void_p), ("level", ctypes.c_uint32),
+                ("first_sample", ctypes.c_uint64), ("count", ctypes.c_int),
+                ("Y", ctypes.c_void_p), ("qoi_f", ctypes.c_void_p), ("qoi_c", ctypes.c_void_p),
+                ("sums", mlmc_level_sums), ("status", ctypes.c_int)]
+
+
 _SIGS = {
     "ce_setup_embedding": (ctypes.c_int, [ctypes.POINTER(ce_cov), ctypes.c_int,
                                           ctypes.POINTER(ce_pad), ctypes.POINTER(ce_smoothing),
@@ -86,6 +93,9 @@ _SIGS = {
                                            ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
                                            ctypes.c_int, ctypes.POINTER(mlmc_level_sums), _P, _P,
                                            _P, _P]),
+    "mlmc_estimate_levels": (ctypes.c_int, [ctypes.POINTER(darcy_problem), ctypes.c_uint64,
+                                            ctypes.c_int, ctypes.POINTER(mlmc_level_task),
+                                            ctypes.c_int, ctypes.c_int, _P]),
     "mlmc_optimal_samples": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_double, _P]),
     "ce_destroy": (None, [_P]),
     "ce_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -247,6 +257,32 @@ def mlmc_level_estimate(emb, seed, level, first_sample, count, qoi_index=QOI_OUT
                                            _ptr(Y), _ptr(qoi_f), _ptr(qoi_c), _stream(stream, Y)),
                 "mlmc_level_estimate", allow)
     return out, st
+
+
+def mlmc_estimate_levels(tasks, seed, qoi_index=QOI_OUTFLOW, f=0.0, rtol=1e-10, maxit=1000,
+                         precision=32, max_concurrency=8, stream=None, allow_not_converged=False):
+    """All levels of one MLMC step in one call.  ``tasks``: sequence of dicts
+    with keys emb, level, first_sample, count and optionally Y, qoi_f, qoi_c
+    (CUDA tensors).  Returns ([mlmc_level_sums per task], [status per task],
+    overall status)."""
+    if not tasks:
+        return [], [], CE_OK
+    arr = (mlmc_level_task * len(tasks))()
+    for t, d in zip(arr, tasks):
+        h = d["emb"].handle
+        t.emb = h.value if isinstance(h, ctypes.c_void_p) else h
+        t.level = d["level"]
+        t.first_sample = d["first_sample"]
+        t.count = d["count"]
+        t.Y, t.qoi_f, t.qoi_c = (_ptr(d.get(k)).value for k in ("Y", "qoi_f", "qoi_c"))
+    prob = darcy_problem(tasks[0]["emb"].n, f, rtol, maxit, precision)
+    allow = (CE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    ref = next((d[k] for d in tasks for k in ("Y", "qoi_f", "qoi_c") if d.get(k) is not None),
+               None)
+    st = _check(load().mlmc_estimate_levels(ctypes.byref(prob), seed, qoi_index, arr, len(tasks),
+                                            max_concurrency, _stream(stream, ref)),
+                "mlmc_estimate_levels", allow)
+    return [mlmc_level_sums.from_buffer_copy(t.sums) for t in arr], [t.status for t in arr], st
 
 
 def sce_profile_enable(on):

@@ -61,3 +61,29 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(sce.ce_cov) == 32
     assert ctypes.sizeof(sce.ce_embedding_info) == 4 * 3 + 4 + 8 * 3 + 8 * 3
     assert ctypes.sizeof(sce.mlmc_level_sums) == 8 * 5 + 8 + 8
+    # mlmc_level_task: pointer, u32 (+pad), u64, int (+pad), 3 pointers, sums, int (+pad)
+    assert sce.mlmc_level_task.sums.offset == 56
+    assert sce.mlmc_level_task.status.offset == 112
+    assert ctypes.sizeof(sce.mlmc_level_task) == 120
+
+
+def test_estimate_levels_rejects_bad_arguments_on_the_host():
+    """Argument checks return before any CUDA call (safe without a GPU)."""
+    from paper_2306_13493_gb300 import sce
+    lib = sce.load()
+    prob = sce.darcy_problem(16, 1.0, 1e-10, 100, 32)
+    tasks = (sce.mlmc_level_task * 2)()
+    tasks[0].emb, tasks[0].count = 1, 4           # fake handle, never dereferenced
+    tasks[1].emb, tasks[1].count = None, 4        # missing handle
+    assert lib.mlmc_estimate_levels(ctypes.byref(prob), 1, 0, tasks, 2, 4, None) == \
+        sce.CE_ERR_INVALID_ARG
+    tasks[1].emb, tasks[1].count = 1, -1          # negative count
+    assert lib.mlmc_estimate_levels(ctypes.byref(prob), 1, 0, tasks, 2, 4, None) == \
+        sce.CE_ERR_INVALID_ARG
+    assert lib.mlmc_estimate_levels(ctypes.byref(prob), 1, 3, tasks, 0, 4, None) == \
+        sce.CE_ERR_INVALID_ARG                    # qoi_index out of range
+    assert lib.mlmc_estimate_levels(None, 1, 0, tasks, 0, 4, None) == sce.CE_ERR_INVALID_ARG
+    bad = sce.darcy_problem(16, 1.0, 1e-10, 100, 16)   # precision neither 32 nor 64
+    assert lib.mlmc_estimate_levels(ctypes.byref(bad), 1, 0, tasks, 0, 4, None) == \
+        sce.CE_ERR_INVALID_ARG
+    assert lib.mlmc_estimate_levels(ctypes.byref(prob), 1, 0, tasks, 0, 4, None) == sce.CE_OK

@@ -52,3 +52,80 @@ def test_level_estimate_matches_oracle(sce, level, smooth, finest, qi, precision
     assert abs(out.sumQf - f1) < tol * abs(f1) * 1.0 + 1e-12
     assert abs(out.sumY - Yg.sum()) < 1e-12 * max(1.0, abs(out.sumY))
     assert abs(out.sumY2 - (Yg * Yg).sum()) < 1e-12 * max(1.0, out.sumY2)
+
+
+def _level_setup(sce, levels, n0=8):
+    import workloads
+    embs = []
+    L = max(levels)
+    for l in levels:
+        n = n0 << l
+        e0 = sce.ce_setup_embedding(ocv.MATERN, 0.5, 0.05, 1.0, n, pad_mode=oem.PAD_SMOOTH)
+        kf, kc = workloads.keep_counts(e0.P, l == L, True)
+        e0.close()
+        embs.append(sce.ce_setup_embedding(ocv.MATERN, 0.5, 0.05, 1.0, n,
+                                           pad_mode=oem.PAD_SMOOTH, keep_fine=kf, keep_coarse=kc))
+    return embs
+
+
+@pytest.mark.parametrize("conc,chunk_vertices", [(4, None), (8, 700), (1, None)])
+def test_estimate_levels_equals_level_by_level(sce, conc, chunk_vertices, monkeypatch):
+    """All levels in one call (concurrent streams, coarse solves on their own
+    stream, several chunks per level when chunk_vertices is small) give
+    bit-identical Y and level sums to one mlmc_level_estimate per level."""
+    import torch
+    levels = [0, 1, 2, 3, 4]
+    counts = [70, 40, 23, 9, 5]
+    embs = _level_setup(sce, levels)
+    if chunk_vertices is not None:
+        monkeypatch.setenv("SCE_MLMC_CHUNK_VERTICES", str(chunk_vertices))
+    ref, Yref = [], []
+    for l, e, c in zip(levels, embs, counts):
+        Y = torch.empty(c, dtype=torch.float64, device="cuda")
+        qf = torch.empty(c, 3, dtype=torch.float64, device="cuda")
+        out, st = sce.mlmc_level_estimate(e, 7, l, 100 + l, c, qoi_index=1, f=1.0, rtol=1e-10,
+                                          precision=32, Y=Y, qoi_f=qf)
+        assert st == 0
+        ref.append(out)
+        Yref.append((Y.clone(), qf.clone()))
+    tasks = []
+    for l, e, c in zip(levels, embs, counts):
+        tasks.append({"emb": e, "level": l, "first_sample": 100 + l, "count": c,
+                      "Y": torch.full((c,), float("nan"), dtype=torch.float64, device="cuda"),
+                      "qoi_f": torch.full((c, 3), float("nan"), dtype=torch.float64,
+                                          device="cuda")})
+    sums, stats, st = sce.mlmc_estimate_levels(tasks, 7, qoi_index=1, f=1.0, rtol=1e-10,
+                                               precision=32, max_concurrency=conc)
+    torch.cuda.synchronize()
+    assert st == 0 and stats == [0] * len(levels)
+    for r, o, t, (Y, qf) in zip(ref, sums, tasks, Yref):
+        assert (o.N, o.sumY, o.sumY2, o.sumQf, o.sumQf2) == (r.N, r.sumY, r.sumY2, r.sumQf, r.sumQf2)
+        assert (o.n_failed, o.max_iters, o.total_iters) == (r.n_failed, r.max_iters, r.total_iters)
+        assert torch.equal(t["Y"], Y) and torch.equal(t["qoi_f"], qf)
+    for e in embs:
+        e.close()
+
+
+def test_estimate_levels_waits_for_the_callers_stream(sce):
+    """Work queued on the caller's stream before the call (here: the writes
+    of the first samples' index range into Y) is ordered before the levels'
+    streams, and the caller's stream is ordered after them."""
+    import torch
+    embs = _level_setup(sce, [0, 1])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        Y0 = torch.zeros(30, dtype=torch.float64, device="cuda")
+        Y1 = torch.zeros(20, dtype=torch.float64, device="cuda")
+        torch.cuda._sleep(20_000_000)          # keep the stream busy before the call
+        Y0.fill_(float("nan"))
+        tasks = [{"emb": embs[0], "level": 0, "first_sample": 0, "count": 30, "Y": Y0},
+                 {"emb": embs[1], "level": 1, "first_sample": 0, "count": 20, "Y": Y1}]
+        sums, stats, st = sce.mlmc_estimate_levels(tasks, 3, qoi_index=1, f=1.0,
+                                                   max_concurrency=2, stream=s.cuda_stream)
+        tot = Y0.sum() + Y1.sum()               # queued after the call on the same stream
+    s.synchronize()
+    assert st == 0
+    assert torch.isfinite(Y0).all() and torch.isfinite(Y1).all()
+    assert abs(float(tot) - (sums[0].sumY + sums[1].sumY)) < 1e-9
+    for e in embs:
+        e.close()
