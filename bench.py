@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--concurrency", type=int, default=8,
                     help="levels in flight at once (each on its own streams); 1 = one after another")
+    ap.add_argument("--serve-seconds", type=float, default=12.0,
+                    help="open-loop window of the served-requests measurement (0: skip)")
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -253,6 +256,112 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def serving_bench(args, sce):
+    """The served loop (workloads.SERVED): a request server with `slots`
+    concurrent requests, HBM-footprint admission and a resident embedding
+    cache; Poisson arrivals at load x the measured service capacity, while an
+    adaptive MLMC client (Eq. (3.6) loop to RMSE mlmc_eps on the oscillatory
+    covariance, levels 0..4) drives its own level requests through the same
+    server.  Latency = completion - submission of each background request."""
+    import numpy as np
+    from paper_2306_13493_gb300 import mlmc as gm
+    sw = workloads.SERVED
+    tenants = sw.draw_tenants()
+    rng = np.random.default_rng(sw.arrival_seed + 1)
+    next_first = {}
+
+    def place(req):
+        key = (req["tenant"], req["level"])
+        req["first_sample"] = next_first.get(key, 0)
+        next_first[key] = req["first_sample"] + req["count"]
+        return req
+
+    out = {"workload": "levels 0-%d (n=%d..%d), counts log-uniform %d-%d, %d tenants (nu in %s, "
+                       "lambda log-uniform %s, sigma2 uniform %s), smoothing tau=sqrt(s)" % (
+                           sw.levels - 1, sw.n0, sw.n0 << (sw.levels - 1), *sw.count_range,
+                           sw.tenants, list(sw.nu_choices), list(sw.lam_range),
+                           list(sw.sigma2_range)),
+           "slots": args.serve_slots}
+    with sce.Server(slots=args.serve_slots, max_embeddings=256, precision=args.precision,
+                    rtol=1e-10, maxit=2000) as srv:
+        # 1. every (tenant, level) embedding becomes resident
+        t0 = time.perf_counter()
+        tk = [srv.submit(place({**tenants[t], "tenant": t, "level": l, "n": sw.n0 << l,
+                                "count": 1}))
+              for t in range(len(tenants)) for l in range(sw.levels)]
+        for t in tk:
+            srv.wait(t)
+        out["cache_warmup_s"] = round(time.perf_counter() - t0, 2)
+        # 2. service capacity: a closed batch of requests of the mix
+        batch = [place(sw.draw_request(rng, tenants)) for _ in range(48)]
+        t0 = time.perf_counter()
+        tk = [srv.submit(r) for r in batch]
+        for t in tk:
+            srv.wait(t)
+        cap = len(batch) / (time.perf_counter() - t0)
+        rate = sw.load * cap
+        out["capacity_req_per_s"] = round(cap, 3)
+        out["arrival_rate_per_s"] = round(rate, 3)
+        # 3. open loop: Poisson arrivals for serve_seconds, the MLMC client alongside
+        n_req = max(8, int(rate * args.serve_seconds))
+        gaps = rng.exponential(1.0 / rate, n_req)
+        reqs = [place(sw.draw_request(rng, tenants)) for _ in range(n_req)]
+        tickets = [None] * n_req
+        submitted = threading.Event()
+
+        def submitter():
+            t_start = time.perf_counter()
+            at = 0.0
+            for i, (g, r) in enumerate(zip(gaps, reqs)):
+                at += g
+                d = t_start + at - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = srv.submit(r)
+            submitted.set()
+
+        osc = workloads.OSCILLATORY
+        client = {"nu": osc.nu, "lam": osc.lam, "sigma2": osc.sigma2}
+        mres = {}
+
+        def mlmc_client():
+            runners = [gm.ServedLevelRunner(srv, client, l, osc.n0 << l,
+                                            l == sw.mlmc_levels - 1, sw.mlmc_seed, qoi=osc.qoi,
+                                            f=osc.f) for l in range(sw.mlmc_levels)]
+            t0 = time.perf_counter()
+            res = gm.run_to_rmse(runners, sw.mlmc_eps, pilot=[400, 200, 100, 50, 20])
+            mres.update({"eps": sw.mlmc_eps, "wall_s": round(time.perf_counter() - t0, 3),
+                         "estimate": res.estimate, "stat_error": res.stat_error,
+                         "bias_est": res.bias, "N": [s.N for s in res.levels]})
+
+        st0 = srv.stats()
+        th = [threading.Thread(target=submitter), threading.Thread(target=mlmc_client)]
+        for t in th:
+            t.start()
+        submitted.wait()
+        res = [srv.wait(t) for t in tickets]
+        for t in th:
+            t.join()
+        st1 = srv.stats()
+    lat = np.array([r.t_done - r.t_submit for r in res]) * 1e3
+    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+    samples = sum(r.sums.N for r in res)
+    out.update({
+        "requests": n_req, "p50_ms": round(float(np.percentile(lat, 50)), 2),
+        "p99_ms": round(float(np.percentile(lat, 99)), 2),
+        "mean_ms": round(float(lat.mean()), 2), "max_ms": round(float(lat.max()), 2),
+        "samples_per_s": round(samples / span, 1),
+        "failed": int(sum(r.status not in (0, -5) for r in res)),
+        "cache_hits": st1["cache_hits"] - st0["cache_hits"],
+        "cache_misses": st1["cache_misses"] - st0["cache_misses"],
+        "peak_in_flight": st1["peak_in_flight"],
+        "peak_reserved_gb": round(st1["peak_reserved"] / 2 ** 30, 2),
+        "budget_gb": round(st1["budget"] / 2 ** 30, 2),
+        "mlmc_client": mres,
+    })
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -453,6 +562,10 @@ def run_ours(args):
                "fp64_per_sample_path_seconds": round(fp64_s, 3) if fp64_s else None,
                "speedup_vs_fp64_path": round(fp64_s / res.seconds, 1) if fp64_s else None}
 
+    serving = None
+    if rank == 0 and world == 1 and args.serve_seconds > 0:
+        serving = serving_bench(args, sce)
+
     cpu = None
     if want_cpu:
         try:
@@ -479,7 +592,8 @@ def run_ours(args):
             "gpu_launches": int(sum(v[2] for v in prof.values())) * args.steps,
             "gpu_launches_per_step": int(sum(v[2] for v in prof.values())),
             "roofline": roof, "kernels": kernels, "per_level": per_level,
-            "fp64_per_sample_path": fp64, "time_to_rmse": ttr, "cpu_baseline": cpu,
+            "fp64_per_sample_path": fp64, "time_to_rmse": ttr, "serving": serving,
+            "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -64,10 +64,15 @@ typedef struct {
 } ce_pad;
 
 /* Smoothing, §2.4 and Algorithm 2 step 4(b): keep the `keep` largest
- * eigenvalues (keep < 0: all).  keep_fine shapes the fine field, keep_coarse
- * the coarse field of an MLMC level (read at every second vertex).  A tie
- * group (eigenvalues within tie_rel_tol relative of the cut value) that
- * straddles the cut is dropped whole.  tie_rel_tol <= 0 selects 1e-10. */
+ * eigenvalues.  CE_KEEP_ALL (or any other negative value except
+ * CE_KEEP_TAU_SQRT_S): all; CE_KEEP_TAU_SQRT_S: s - sqrt(s), i.e. drop
+ * tau = sqrt(s) = P eigenvalues (the rule of the numerics of §4), resolved
+ * once the padding has fixed P.  keep_fine shapes the fine field,
+ * keep_coarse the coarse field of an MLMC level (read at every second
+ * vertex).  A tie group (eigenvalues within tie_rel_tol relative of the cut
+ * value) that straddles the cut is dropped whole.  tie_rel_tol <= 0 selects
+ * 1e-10. */
+enum { CE_KEEP_ALL = -1, CE_KEEP_TAU_SQRT_S = -2 };
 typedef struct {
     long long keep_fine, keep_coarse;
     double tie_rel_tol;
@@ -250,6 +255,76 @@ typedef struct mlmc_level_task {
  */
 int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
                          mlmc_level_task *tasks, int ntasks, int max_concurrency, void *stream);
+
+/*
+ * Request server -- MLMC level estimates (mlmc_level_estimate) served to
+ * requests that arrive over time, with different grids and covariances, by
+ * continuous batching.  `slots` host worker threads, each with its own
+ * non-blocking CUDA stream on the device current at creation, admit queued
+ * requests as soon as a slot is free and the request's device-memory
+ * footprint (an upper bound of what its level estimate allocates) fits in
+ * what is left of hbm_budget; admission is first-fit in arrival order, and
+ * after 8 overtakes of a blocked head only the head is admitted.  Admitted
+ * requests run concurrently.  Embedding set-ups are cached by (covariance,
+ * n, padding, smoothing rule) and stay resident; unused ones are evicted
+ * least-recently-used beyond max_embeddings.  A request's results are
+ * bit-identical to mlmc_level_estimate on its own.
+ * The paper has no counterpart: this is how the level estimates of §3.4 are
+ * served, not a step of the method.
+ */
+typedef struct sce_server_s *sce_server_t;
+
+typedef struct {
+    int slots;              /* requests in flight at once, 1..64                */
+    long long hbm_budget;   /* bytes for admitted requests; <= 0: 3/4 of the
+                               device memory free at creation                  */
+    int max_embeddings;     /* resident embedding handles, >= 1                 */
+    int precision;          /* 32 (FP32 field and MG, FP64 refinement) or 64    */
+    double rtol;            /* FP64 residual tolerance of every solve           */
+    int maxit;              /* CG iteration bound per solve                     */
+} sce_server_config;
+
+typedef struct {
+    ce_cov cov;
+    ce_pad pad;
+    int n;                  /* cells of the level's fine grid (power of two)    */
+    uint32_t level;         /* MLMC level: > 0 adds the coarse solve on n/2     */
+    int smoothing;          /* 0: full spectrum; 1: tau = sqrt(s) dropped (§4)  */
+    int finest;             /* with smoothing: the fine field unsmoothed (§3.5) */
+    uint64_t seed, first_sample;
+    int count;              /* samples, >= 0                                    */
+    int qoi_index;          /* 0 outflow, 1 point value, 2 L2 norm              */
+    double f;               /* source term                                      */
+    double *Y;              /* device double[count] or NULL; written when done  */
+} sce_request;
+
+typedef struct {
+    mlmc_level_sums sums;   /* the level sums of the request's samples          */
+    int status;             /* mlmc_level_estimate's status (or set-up error)   */
+    int cache_hit;          /* 1: the embedding was resident                    */
+    long long footprint;    /* bytes reserved at admission                      */
+    double t_submit, t_admit, t_setup_done, t_done;  /* server clock, seconds   */
+} sce_result;
+
+typedef struct {
+    long long submitted, completed, queued, in_flight, peak_in_flight;
+    long long cache_hits, cache_misses, cached;
+    long long reserved, peak_reserved, budget;   /* bytes                       */
+    double now;                                  /* server clock, seconds       */
+} sce_server_stats_t;
+
+/* Starts the workers.  Errors: CE_ERR_INVALID_ARG, CE_ERR_OOM, CE_ERR_CUDA. */
+int sce_server_create(const sce_server_config *cfg, sce_server_t *out);
+/* Queues a request (copied; Y must stay valid until it is done) and returns
+ * its ticket.  CE_ERR_INVALID_ARG for bad fields or a server shutting down. */
+int sce_server_submit(sce_server_t s, const sce_request *r, uint64_t *ticket);
+/* Waits up to timeout_s seconds (< 0: without limit) for the ticket; on
+ * CE_OK fills *out and retires the ticket.  CE_ERR_TIMEOUT: not done yet
+ * (the ticket stays valid).  CE_ERR_INVALID_ARG: unknown ticket. */
+int sce_server_wait(sce_server_t s, uint64_t ticket, double timeout_s, sce_result *out);
+int sce_server_stats(sce_server_t s, sce_server_stats_t *out);
+/* Finishes every queued request, stops the workers, releases the cache. */
+void sce_server_destroy(sce_server_t s);
 
 /* Eq. (3.6): N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)),
  * l = 0..L.  V, C, N: host arrays of length L+1 (C > 0, V >= 0). */

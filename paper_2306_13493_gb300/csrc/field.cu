@@ -254,7 +254,9 @@ extern "C" int ce_setup_embedding(const ce_cov *cov, int n, const ce_pad *pad,
     clip_real_kernel<<<(unsigned)((s + 255) / 256), 256, 0, st>>>(Lc, s, e->lam);
     if (cudaGetLastError() != cudaSuccess) return fail(CE_ERR_CUDA);
 
-    long long keep_f = sm ? sm->keep_fine : -1, keep_c = sm ? sm->keep_coarse : -1;
+    // CE_KEEP_TAU_SQRT_S: drop tau = sqrt(s) = P eigenvalues (the rule of §4)
+    auto resolve = [&](long long k) { return k == CE_KEEP_TAU_SQRT_S ? s - (long long)e->P : k; };
+    long long keep_f = sm ? resolve(sm->keep_fine) : -1, keep_c = sm ? resolve(sm->keep_coarse) : -1;
     const double tol = (sm && sm->tie_rel_tol > 0) ? sm->tie_rel_tol : 1e-10;
     const bool need_f = keep_f >= 0 && keep_f < s;
     const bool need_c = keep_c >= 0 && keep_c < s;
@@ -267,7 +269,12 @@ extern "C" int ce_setup_embedding(const ce_cov *cov, int n, const ce_pad *pad,
             return fail(CE_ERR_CUDA);
     }
     e->keep_eff_fine = need_f ? keep_mask(hl, keep_f, tol, e->mask_f) : s;
-    e->keep_eff_coarse = need_c ? keep_mask(hl, keep_c, tol, e->mask_c) : s;
+    if (need_c && need_f && keep_c == keep_f) {
+        e->mask_c = e->mask_f;
+        e->keep_eff_coarse = e->keep_eff_fine;
+    } else {
+        e->keep_eff_coarse = need_c ? keep_mask(hl, keep_c, tol, e->mask_c) : s;
+    }
     if (!need_f) e->mask_f.assign(s, 1);
     if (!need_c) e->mask_c.assign(s, 1);
     e->coarse_distinct = e->mask_c != e->mask_f;

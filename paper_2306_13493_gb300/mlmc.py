@@ -111,6 +111,60 @@ class LevelRunner:
         return st
 
 
+class ServedLevelRunner:
+    """One MLMC level served by a request server (sce.Server): run(count)
+    submits a request for the level's next `count` samples and folds its
+    level sums in; submit/collect split the two so that several levels can
+    be in flight at once.  The cost of a sample is the request's time on the
+    server after admission and set-up, divided by its sample count."""
+
+    def __init__(self, server, tenant, level, n, finest, seed, qoi=sce.QOI_POINT, f=1.0):
+        self.server, self.tenant = server, dict(tenant)
+        self.stats = LevelStats(level=level, n=n)
+        self.finest, self.seed, self.qoi, self.f = finest, seed, qoi, f
+
+    def submit(self, count):
+        st = self.stats
+        t = self.server.submit({**self.tenant, "n": st.n, "level": st.level, "count": count,
+                                "finest": int(self.finest), "seed": self.seed,
+                                "first_sample": st.next_sample, "qoi_index": self.qoi,
+                                "f": self.f})
+        st.next_sample += count
+        return t
+
+    def collect(self, ticket):
+        r = self.server.wait(ticket)
+        if r.status not in (sce.CE_OK, sce.CE_ERR_NOT_CONVERGED):
+            raise sce.SceError(r.status, "served level estimate")
+        st, o = self.stats, r.sums
+        st.N += o.N
+        st.sumY += o.sumY
+        st.sumY2 += o.sumY2
+        st.sumQ += o.sumQf
+        st.sumQ2 += o.sumQf2
+        st.iters += o.total_iters
+        st.seconds += r.t_done - r.t_setup_done
+        return st
+
+    def run(self, count):
+        return self.collect(self.submit(count))
+
+
+def _run_levels(runners, counts):
+    """Runs counts[l] more samples on every level; levels whose runner can
+    submit ahead are all in flight at once."""
+    pending = []
+    for r, c in zip(runners, counts):
+        if c <= 0:
+            continue
+        if hasattr(r, "submit"):
+            pending.append((r, r.submit(c)))
+        else:
+            r.run(c)
+    for r, t in pending:
+        r.collect(t)
+
+
 def fit_rate(levels, values):
     """Least-squares slope of -log2(values) against the level index (a rate)."""
     lv = np.asarray(levels, dtype=float)
@@ -147,9 +201,7 @@ def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rou
     extra samples.  Returns the estimate, the estimated RMSE (statistical error
     and Richardson bias) and the GPU seconds spent."""
     pilot = pilot or [100] * len(runners)
-    for r, p in zip(runners, pilot):
-        if r.stats.N < p:
-            r.run(p - r.stats.N)
+    _run_levels(runners, [p - r.stats.N for r, p in zip(runners, pilot)])
     N_opt = None
     for _ in range(max_rounds):
         V = [max(r.stats.var, 1e-300) for r in runners]
@@ -158,9 +210,7 @@ def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rou
         extra = [max(0, int(n) - r.stats.N) for n, r in zip(N_opt, runners)]
         if all(e <= 0.01 * r.stats.N for e, r in zip(extra, runners)):
             break
-        for e, r in zip(extra, runners):
-            if e > 0:
-                r.run(e)
+        _run_levels(runners, extra)
     stats = [r.stats for r in runners]
     est = sum(s.mean for s in stats)
     stat_err = math.sqrt(sum(s.var / s.N for s in stats))

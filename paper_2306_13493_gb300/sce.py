@@ -25,6 +25,8 @@ CE_COV_SEP_EXP = 1
 CE_PAD_NONE = 0
 CE_PAD_DOUBLING = 1
 CE_PAD_SMOOTH = 2
+CE_KEEP_ALL = -1
+CE_KEEP_TAU_SQRT_S = -2
 
 QOI_OUTFLOW = 0
 QOI_POINT = 1
@@ -73,6 +75,32 @@ class mlmc_level_task(ctypes.Structure):
                 ("sums", mlmc_level_sums), ("status", ctypes.c_int)]
 
 
+class sce_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_longlong),
+                ("max_embeddings", ctypes.c_int), ("precision", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int)]
+
+
+class sce_request(ctypes.Structure):
+    _fields_ = [("cov", ce_cov), ("pad", ce_pad), ("n", ctypes.c_int), ("level", ctypes.c_uint32),
+                ("smoothing", ctypes.c_int), ("finest", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("first_sample", ctypes.c_uint64), ("count", ctypes.c_int),
+                ("qoi_index", ctypes.c_int), ("f", ctypes.c_double), ("Y", ctypes.c_void_p)]
+
+
+class sce_result(ctypes.Structure):
+    _fields_ = [("sums", mlmc_level_sums), ("status", ctypes.c_int), ("cache_hit", ctypes.c_int),
+                ("footprint", ctypes.c_longlong), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_setup_done", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class sce_server_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in (
+        "submitted", "completed", "queued", "in_flight", "peak_in_flight", "cache_hits",
+        "cache_misses", "cached", "reserved", "peak_reserved", "budget")] + [("now", ctypes.c_double)]
+
+
 _SIGS = {
     "ce_setup_embedding": (ctypes.c_int, [ctypes.POINTER(ce_cov), ctypes.c_int,
                                           ctypes.POINTER(ce_pad), ctypes.POINTER(ce_smoothing),
@@ -93,6 +121,13 @@ _SIGS = {
                                            ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
                                            ctypes.c_int, ctypes.POINTER(mlmc_level_sums), _P, _P,
                                            _P, _P]),
+    "sce_server_create": (ctypes.c_int, [ctypes.POINTER(sce_server_config), ctypes.POINTER(_P)]),
+    "sce_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(sce_request),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "sce_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double,
+                                       ctypes.POINTER(sce_result)]),
+    "sce_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(sce_server_stats_t)]),
+    "sce_server_destroy": (None, [_P]),
     "mlmc_estimate_levels": (ctypes.c_int, [ctypes.POINTER(darcy_problem), ctypes.c_uint64,
                                             ctypes.c_int, ctypes.POINTER(mlmc_level_task),
                                             ctypes.c_int, ctypes.c_int, _P]),
@@ -283,6 +318,68 @@ def mlmc_estimate_levels(tasks, seed, qoi_index=QOI_OUTFLOW, f=0.0, rtol=1e-10, 
                                             max_concurrency, _stream(stream, ref)),
                 "mlmc_estimate_levels", allow)
     return [mlmc_level_sums.from_buffer_copy(t.sums) for t in arr], [t.status for t in arr], st
+
+
+class Server:
+    """Request server of the C ABI (sce_server_*): submit MLMC level requests,
+    wait for their results.  Requests are dicts with keys kind, nu, lam,
+    sigma2, n, level, count and optionally pad_mode (2), J (-1), max_P (8192),
+    smoothing (1), finest (0), seed (0), first_sample (0), qoi_index (1), f (1.0),
+    Y (CUDA tensor of count doubles)."""
+
+    def __init__(self, slots=8, hbm_budget=0, max_embeddings=256, precision=32, rtol=1e-10,
+                 maxit=2000):
+        self._lib = load()
+        cfg = sce_server_config(slots, hbm_budget, max_embeddings, precision, rtol, maxit)
+        h = _P()
+        _check(self._lib.sce_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sce_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, req):
+        r = sce_request()
+        r.cov = ce_cov(req.get("kind", CE_COV_MATERN), req.get("nu", 0.5), req["lam"],
+                       req.get("sigma2", 1.0))
+        r.pad = ce_pad(req.get("pad_mode", CE_PAD_SMOOTH), req.get("J", -1),
+                       req.get("max_P", 8192))
+        r.n, r.level, r.count = req["n"], req["level"], req["count"]
+        r.smoothing, r.finest = req.get("smoothing", 1), req.get("finest", 0)
+        r.seed, r.first_sample = req.get("seed", 0), req.get("first_sample", 0)
+        r.qoi_index, r.f = req.get("qoi_index", QOI_POINT), req.get("f", 1.0)
+        r.Y = _ptr(req.get("Y")).value
+        t = ctypes.c_uint64()
+        _check(self._lib.sce_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)),
+               "sce_server_submit")
+        if req.get("Y") is not None:
+            self._keep[t.value] = req["Y"]
+        return t.value
+
+    def wait(self, ticket, timeout=-1.0):
+        """The sce_result of `ticket`, or None if not done within `timeout` s."""
+        res = sce_result()
+        st = self._lib.sce_server_wait(self.handle, ticket, timeout, ctypes.byref(res))
+        if st == CE_ERR_TIMEOUT:
+            return None
+        _check(st, "sce_server_wait")
+        self._keep.pop(ticket, None)
+        return res
+
+    def stats(self):
+        s = sce_server_stats_t()
+        _check(self._lib.sce_server_stats(self.handle, ctypes.byref(s)), "sce_server_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if self.handle:
+            self._lib.sce_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def sce_profile_enable(on):

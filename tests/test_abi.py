@@ -65,6 +65,26 @@ def test_struct_layouts_match_header():
     assert sce.mlmc_level_task.sums.offset == 56
     assert sce.mlmc_level_task.status.offset == 112
     assert ctypes.sizeof(sce.mlmc_level_task) == 120
+    # server structs: config int, (pad), i64, int, int, double, int (+pad)
+    assert ctypes.sizeof(sce.sce_server_config) == 40
+    # request: ce_cov 32, ce_pad 12, n 4, level 4, smoothing 4, finest 4, (pad 4),
+    # seed 8, first_sample 8, count 4, qoi 4, f 8, Y 8
+    assert sce.sce_request.seed.offset == 64 and ctypes.sizeof(sce.sce_request) == 104
+    assert sce.sce_result.footprint.offset == 64 and ctypes.sizeof(sce.sce_result) == 104
+    assert ctypes.sizeof(sce.sce_server_stats_t) == 96
+
+
+def test_server_rejects_bad_configs_on_the_host(lib):
+    """sce_server_create checks its config before any CUDA call."""
+    from paper_2306_13493_gb300 import sce
+    h = ctypes.c_void_p()
+    for cfg in (sce.sce_server_config(0, 0, 8, 32, 1e-10, 100),      # no slots
+                sce.sce_server_config(4, 0, 0, 32, 1e-10, 100),      # no cache
+                sce.sce_server_config(4, 0, 8, 16, 1e-10, 100),      # precision
+                sce.sce_server_config(4, 0, 8, 32, 0.0, 100)):       # rtol
+        assert lib.sce_server_create(ctypes.byref(cfg), ctypes.byref(h)) == sce.CE_ERR_INVALID_ARG
+    assert lib.sce_server_submit(None, None, None) == sce.CE_ERR_INVALID_ARG
+    lib.sce_server_destroy(None)
 
 
 def test_estimate_levels_rejects_bad_arguments_on_the_host():

@@ -66,3 +66,35 @@ def test_run_to_rmse_meets_variance_target(drv):
     assert np.all(got >= 0.7 * want) and np.all(got <= 1.5 * want + 200)
     assert res.stat_error <= eps / math.sqrt(2.0) * 1.15
     assert abs(res.estimate - sum(r.stats.mean for r in runners)) < 1e-15
+
+
+class FakeSubmitRunner(FakeRunner):
+    """FakeRunner with the submit/collect split of a served level."""
+
+    def __init__(self, *a):
+        super().__init__(*a)
+        self.in_flight = 0
+
+    def submit(self, count):
+        self.in_flight += 1
+        return count
+
+    def collect(self, count):
+        self.in_flight -= 1
+        return FakeRunner.run(self, count)
+
+
+def test_levels_in_flight_give_the_same_run(drv):
+    """run_to_rmse with runners that submit ahead (all levels in flight, then
+    collected in level order) reproduces the level-by-level run exactly."""
+    V = [1e-3, 2e-4, 5e-5, 1.2e-5]
+    C = [1e-6, 4e-6, 1.6e-5, 6.4e-5]
+    out = []
+    for cls in (FakeRunner, FakeSubmitRunner):
+        rng = np.random.default_rng(11)
+        runners = [cls(l, 0.0, V[l], C[l], rng) for l in range(4)]
+        res = drv.run_to_rmse(runners, 2e-3, pilot=[200] * 4, alpha=1.0)
+        out.append((res.estimate, res.stat_error, [r.stats.N for r in runners]))
+        if cls is FakeSubmitRunner:
+            assert all(r.in_flight == 0 for r in runners)
+    assert out[0] == out[1]

@@ -66,3 +66,45 @@ def keep_counts(P, finest, smoothing):
         return -1, -1
     s = P * P
     return (-1 if finest else s - P), s - P
+
+
+@dataclass
+class ServedWorkload:
+    """Requests of the served MLMC loop: each request is one MLMC level
+    (fine grid n0 * 2^level, coarse grid half of it) of one covariance
+    ("tenant"), with a log-uniform sample count.  Tenants are drawn once:
+    nu from nu_choices, lambda log-uniform in lam_range, sigma^2 uniform in
+    sigma2_range; requests draw a tenant and a level uniformly."""
+    n0: int = 16
+    levels: int = 7                      # levels 0..6: n = 16..1024
+    count_range: tuple = (1, 4096)
+    nu_choices: tuple = (0.5, 1.5)
+    lam_range: tuple = (0.01, 0.1)
+    sigma2_range: tuple = (0.5, 3.0)
+    tenants: int = 6
+    load: float = 0.75                   # arrival rate / measured service capacity
+    arrival_seed: int = 5
+    mlmc_seed: int = 6
+    mlmc_eps: float = 5e-4
+    mlmc_levels: int = 5                 # the adaptive client's levels 0..4
+
+    def draw_tenants(self):
+        import numpy as np
+        rng = np.random.default_rng(self.arrival_seed)
+        out = []
+        for _ in range(self.tenants):
+            out.append({"nu": float(rng.choice(self.nu_choices)),
+                        "lam": float(np.exp(rng.uniform(*np.log(self.lam_range)))),
+                        "sigma2": float(rng.uniform(*self.sigma2_range))})
+        return out
+
+    def draw_request(self, rng, tenants):
+        import numpy as np
+        t = int(rng.integers(len(tenants)))
+        level = int(rng.integers(self.levels))
+        lo, hi = self.count_range
+        count = int(min(hi, max(lo, round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))))
+        return {**tenants[t], "tenant": t, "level": level, "n": self.n0 << level, "count": count}
+
+
+SERVED = ServedWorkload()
