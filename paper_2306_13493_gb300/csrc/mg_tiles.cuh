@@ -7,11 +7,16 @@
 // Each kernel stages a 64 x 32 window (owned region plus halo) in shared
 // memory, recomputes halo values instead of exchanging them, and writes only
 // what it owns.  Thread (x, y) of the 32 x 8 block handles the window
-// elements (x + 32 a, y + 8 b), a < 2, b < 4, so no index arithmetic is
-// repeated per pass; 1/diag is computed once per element.
+// elements (x + 32 a, y + 8 b), a < 2, b < MG_SH / 8, so no index arithmetic
+// is repeated per pass; 1/diag is computed once per element.
 //
 //   mg_down: pre-smoothing from a zero guess (red then black Gauss-Seidel),
-//            fine residual, full-weighting restriction -> zpre (fine), b (coarse)
+//            fine residual, full-weighting restriction -> zpre (fine), b (coarse).
+//            After the black half-sweep the residual vanishes at the black
+//            vertices (each was just solved for with its red neighbours
+//            fixed), so it is formed at the red vertices only and the
+//            restriction sums the coarse vertex and its four diagonal
+//            neighbours (the red ones of its 3 x 3 stencil).
 //   mg_up  : z = zpre + bilinear prolongation of the coarse correction, then
 //            post-smoothing (black then red) -> z (fine); optionally the
 //            partial sums of r . z (level 0, for CG's beta).  zpre and z are
@@ -29,11 +34,18 @@
 
 namespace sce {
 
+#ifndef SCE_MG_SH
+#define SCE_MG_SH 32
+#endif
 constexpr int MG_SW = 64;                  // window width (= row stride)
-constexpr int MG_SH = 32;                  // window height
+constexpr int MG_SH = SCE_MG_SH;           // window height (multiple of 8)
 constexpr int MG_CW = (MG_SW - 6) / 2;     // 29 coarse vertices per tile in x
-constexpr int MG_CH = (MG_SH - 6) / 2;     // 13 coarse vertices per tile in y
+constexpr int MG_CH = (MG_SH - 6) / 2;     // coarse vertices per tile in y
 constexpr int MG_THREADS = 256;
+constexpr int MG_ROWS = MG_SH / 8;         // row groups per thread
+constexpr int MG_NE = 2 * MG_ROWS;         // window elements per thread
+static_assert(MG_SH % 8 == 0 && MG_NE <= 32, "tile height");
+constexpr int MG_BLOCKS_PER_SM = MG_SH <= 32 ? 5 : (MG_SH <= 48 ? 3 : 2);
 constexpr int MG_CCW = MG_CW + 3;          // coarse window of mg_up
 constexpr int MG_CCH = MG_CH + 3;
 
@@ -68,16 +80,45 @@ __device__ __forceinline__ void tile_color_pass(T *sz, const T *sb, const T *scx
                                                 const T *sinv, int ox, int oy, int n, int color,
                                                 int lo, int hix, int hiy) {
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    // rows ty + 8 bb all have the parity of ty: the column is the same for all bb
+    const int li = 2 * tx + ((ox + oy + ty + color) & 1);
+    const int gi = ox + li;
+    if (li < lo || li > hix || gi < 1 || gi > n - 1) return;
 #pragma unroll
-    for (int bb = 0; bb < 4; ++bb) {
+    for (int bb = 0; bb < MG_ROWS; ++bb) {
         const int lj = ty + 8 * bb;
-        const int li = 2 * tx + ((ox + oy + lj + color) & 1);
-        if (li < lo || li > hix || lj < lo || lj > hiy) continue;
-        const int gi = ox + li, gj = oy + lj;
-        if (gi < 1 || gi > n - 1 || gj < 0 || gj > n) continue;
+        if (lj < lo || lj > hiy) continue;
+        const int gj = oy + lj;
+        if (gj < 0 || gj > n) continue;
         const int l = lj * MG_SW + li;
         sz[l] = (sb[l] + scx[l - 1] * sz[l - 1] + scx[l] * sz[l + 1] +
                  scy[l - MG_SW] * sz[l - MG_SW] + scy[l] * sz[l + MG_SW]) * sinv[l];
+    }
+}
+
+// Residual b - A z at the red vertices ((gi + gj) even) of the local box
+// [3, MG_SW-3] x [3, MG_SH-3], in place of b; 0 at Dirichlet vertices.
+template <typename T>
+__device__ __forceinline__ void tile_red_residual(const T *sz, T *sb, const T *scx,
+                                                  const T *scy, int ox, int oy, int n) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int li = 2 * tx + ((ox + oy + ty) & 1);
+    const int gi = ox + li;
+    if (li < 3 || li > MG_SW - 3) return;
+    const bool unk_x = gi >= 1 && gi <= n - 1;
+#pragma unroll
+    for (int bb = 0; bb < MG_ROWS; ++bb) {
+        const int lj = ty + 8 * bb;
+        if (lj < 3 || lj > MG_SH - 3) continue;
+        const int gj = oy + lj;
+        const int l = lj * MG_SW + li;
+        T rv = T(0);
+        if (unk_x && gj >= 0 && gj <= n) {
+            const T zc = sz[l];
+            rv = sb[l] - (scx[l - 1] * (zc - sz[l - 1]) + scx[l] * (zc - sz[l + 1]) +
+                          scy[l - MG_SW] * (zc - sz[l - MG_SW]) + scy[l] * (zc - sz[l + MG_SW]));
+        }
+        sb[l] = rv;
     }
 }
 
@@ -88,7 +129,7 @@ __device__ __forceinline__ void tile_color_pass(T *sz, const T *sb, const T *scx
     const int l = lj * MG_SW + li
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
+__global__ void __launch_bounds__(MG_THREADS, MG_BLOCKS_PER_SM) mg_down_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ zpre, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
     constexpr int LS = MG_SW * MG_SH;
@@ -105,7 +146,7 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
     const T *bs = b + s * V, *xs = cx + s * V, *ys = cy + s * V;
     unsigned unk = 0;   // bit e: element e is an unknown of the grid
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < MG_NE; ++e) {
         MG_ELEM(e, li, lj, l);
         const int gi = ox + li, gj = oy + lj;
         const bool in = gi >= 0 && gi <= n && gj >= 0 && gj <= n;
@@ -118,7 +159,7 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
     __syncthreads();
     // 1/diag; red from z = 0: z = b / diag
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < MG_NE; ++e) {
         MG_ELEM(e, li, lj, l);
         T inv = T(0), zv = T(0);
         if (li >= 1 && lj >= 1 && ((unk >> e) & 1)) {
@@ -132,21 +173,9 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
     // black on local [2, SW-2] x [2, SH-2]
     tile_color_pass(sz, sb, scx, scy, sinv, ox, oy, n, 1, 2, MG_SW - 2, MG_SH - 2);
     __syncthreads();
-    // fine residual on local [3, SW-3] x [3, SH-3], in place of b
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        MG_ELEM(e, li, lj, l);
-        if (li < 3 || li > MG_SW - 3 || lj < 3 || lj > MG_SH - 3) continue;
-        T rv = T(0);
-        if ((unk >> e) & 1) {
-            const T zc = sz[l];
-            rv = sb[l] - (scx[l - 1] * (zc - sz[l - 1]) + scx[l] * (zc - sz[l + 1]) +
-                          scy[l - MG_SW] * (zc - sz[l - MG_SW]) + scy[l] * (zc - sz[l + MG_SW]));
-        }
-        sb[l] = rv;
-    }
+    tile_red_residual(sz, sb, scx, scy, ox, oy, n);
     __syncthreads();
-    // restriction to the tile's coarse vertices
+    // restriction to the tile's coarse vertices (red stencil points only)
     T *bcs = bc + s * Vc;
     for (int c = threadIdx.x; c < MG_CW * MG_CH; c += MG_THREADS) {
         const int ci = c % MG_CW, cj = c / MG_CW;
@@ -157,14 +186,14 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
             const int l0 = (2 * cj + 4) * MG_SW + 2 * ci + 4;
             acc = T(0.25) * (sb[l0 - MG_SW - 1] + sb[l0 - MG_SW + 1] + sb[l0 + MG_SW - 1] +
                              sb[l0 + MG_SW + 1]) +
-                  T(0.5) * (sb[l0 - 1] + sb[l0 + 1] + sb[l0 - MG_SW] + sb[l0 + MG_SW]) + sb[l0];
+                  sb[l0];
         }
         bcs[J * wc + I] = acc;
     }
     // owned fine vertices: local [4, 4 + 2 CW) x [4, 4 + 2 CH)
     T *zs = zpre + s * V;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < MG_NE; ++e) {
         MG_ELEM(e, li, lj, l);
         if (li < 4 || li >= 4 + 2 * MG_CW || lj < 4 || lj >= 4 + 2 * MG_CH) continue;
         const int gi = ox + li, gj = oy + lj;
@@ -174,7 +203,7 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_down_kernel(
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, 5) mg_up_kernel(
+__global__ void __launch_bounds__(MG_THREADS, MG_BLOCKS_PER_SM) mg_up_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     const T *__restrict__ zpre, T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x,
     const int *__restrict__ act, double *__restrict__ part_rz, int nblk) {
@@ -202,7 +231,7 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_up_kernel(
     }
     unsigned unk = 0;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < MG_NE; ++e) {
         MG_ELEM(e, li, lj, l);
         const int gi = ox + li, gj = oy + lj;
         const bool in = li < UW && lj < UH && gi >= 0 && gi <= n && gj >= 0 && gj <= n;
@@ -216,7 +245,7 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_up_kernel(
     __syncthreads();
     // 1/diag and z += P zc at every unknown of the used window
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < MG_NE; ++e) {
         MG_ELEM(e, li, lj, l);
         if (!((unk >> e) & 1)) {
             sinv[l] = T(0);
@@ -240,7 +269,7 @@ __global__ void __launch_bounds__(MG_THREADS, 5) mg_up_kernel(
     // owned fine vertices: local [2, 2 + 2 CW) x [2, 2 + 2 CH)
     T rz = T(0);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < MG_NE; ++e) {
         MG_ELEM(e, li, lj, l);
         if (li < 2 || li >= 2 + 2 * MG_CW || lj < 2 || lj >= 2 + 2 * MG_CH) continue;
         const int gi = ox + li, gj = oy + lj;
