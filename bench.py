@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--concurrency", type=int, default=8,
                     help="levels in flight at once (each on its own streams); 1 = one after another")
+    ap.add_argument("--study", default=None, choices=[None, "precision"],
+                    help="run a study instead of the benchmark (prints its own JSON line)")
+    ap.add_argument("--study-count", type=int, default=None)
+    ap.add_argument("--study-oracle", type=int, default=None)
     ap.add_argument("--serve-seconds", type=float, default=12.0,
                     help="open-loop window of the served-requests measurement (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
@@ -256,6 +260,97 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------------ precision study
+_PS_EMB = {}
+
+
+def _ps_task(task):
+    """Oracle QoIs (outflow, point value, L2 norm) of one sample of the study."""
+    import numpy as np
+    from oracle import embedding as oem
+    from oracle import mlmc as omlmc
+    ps = workloads.PRECISION_STUDY
+    nu, sample, prec = task
+    if nu not in _PS_EMB:
+        _PS_EMB[nu] = oem.setup_embedding(0, nu, ps.lam, ps.sigma2, ps.n, ps.pad_mode, J=ps.J)
+    e = _PS_EMB[nu]
+    full = np.ones(e.Lam.shape, dtype=bool)
+    Qf, _ = omlmc.level_qois(e, full, None, ps.seed, 0, [sample], f=ps.f, precision=prec,
+                             coarse=False)
+    return nu, sample, prec, Qf[0]
+
+
+def precision_study(args):
+    """Config of workloads.PRECISION_STUDY: per nu, the mixed and the all-FP64
+    GPU paths on the same samples (per-sample QoIs), the FP64 oracle on the
+    first oracle_samples of them (with FP64 normals, and with the FP32 normals
+    the mixed path draws), and the bias of the mixed mean against its
+    statistical error."""
+    import multiprocessing as mp
+    import numpy as np
+    ps = workloads.PRECISION_STUDY
+    K = args.study_oracle if args.study_oracle is not None else ps.oracle_samples
+    os.environ.update({"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1"})
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(min(cores, 16)) if K > 0 else None
+    oracle_async = None
+    if pool:   # the oracle runs on the host while the GPU paths run
+        tasks = [(nu, i, prec) for nu in ps.nus for prec in (64, 32) for i in range(K)]
+        oracle_async = pool.map_async(_ps_task, tasks, chunksize=1)
+    import torch
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    sce.load()
+    dev = torch.device("cuda", 0)
+    count = args.study_count or ps.count
+    out = {"study": "precision", "n": ps.n, "lambda": ps.lam, "sigma2": ps.sigma2, "f": ps.f,
+           "count": count, "oracle_samples": K, "rtol": ps.rtol, "per_nu": []}
+    gpu = {}
+    for nu in ps.nus:
+        emb = sce.ce_setup_embedding(0, nu, ps.lam, ps.sigma2, ps.n, pad_mode=ps.pad_mode, J=ps.J)
+        rec = {"nu": nu, "P": emb.P, "lambda_min_over_max": emb.info.lambda_min /
+               emb.info.lambda_max}
+        for prec in (32, 64):
+            q = torch.empty(count, 3, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            o, st = sce.mlmc_level_estimate(emb, ps.seed, 0, 0, count, qoi_index=1, f=ps.f,
+                                            rtol=ps.rtol, maxit=4000, precision=prec, qoi_f=q,
+                                            allow_not_converged=True)
+            torch.cuda.synchronize()
+            rec[f"seconds_fp{prec}"] = round(time.perf_counter() - t0, 3)
+            rec[f"failed_fp{prec}"] = o.n_failed
+            rec[f"max_iters_fp{prec}"] = o.max_iters
+            gpu[(nu, prec)] = q.cpu().numpy()
+        emb.close()
+        qm, qd = gpu[(nu, 32)], gpu[(nu, 64)]
+        rel = np.abs(qm - qd) / np.maximum(np.abs(qd), 1e-300)
+        se = qd.std(axis=0, ddof=1) / np.sqrt(count)
+        rec["mixed_vs_fp64_gpu"] = {
+            "max_rel": rel.max(axis=0).tolist(), "median_rel": np.median(rel, axis=0).tolist(),
+            "mean_diff": (qm - qd).mean(axis=0).tolist(), "std_error_of_mean": se.tolist(),
+            "bias_over_std_error": (np.abs((qm - qd).mean(axis=0)) / se).tolist()}
+        out["per_nu"].append(rec)
+    if oracle_async is not None:
+        res = oracle_async.get()
+        pool.close()
+        pool.join()
+        orc = {(nu, i, prec): q for nu, i, prec, q in res}
+        for rec in out["per_nu"]:
+            nu = rec["nu"]
+            for name, gprec, oprec in (("mixed_vs_oracle_fp64_normals", 32, 64),
+                                       ("mixed_vs_oracle_fp32_normals", 32, 32),
+                                       ("fp64_gpu_vs_oracle", 64, 64)):
+                g = gpu[(nu, gprec)][:K]
+                o = np.array([orc[(nu, i, oprec)] for i in range(K)])
+                r = np.abs(g - o) / np.maximum(np.abs(o), 1e-300)
+                rec[name] = {"max_rel": r.max(axis=0).tolist(),
+                             "median_rel": np.median(r, axis=0).tolist()}
+    out["qoi_order"] = ["outflow", "u(7/15,7/15)", "L2 norm"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def serving_bench(args, sce):
     """The served loop (workloads.SERVED): a request server with `slots`
     concurrent requests, HBM-footprint admission and a resident embedding
@@ -606,6 +701,8 @@ def main():
     args = parse()
     if args.case:
         return run_case(args)
+    if args.study == "precision":
+        return precision_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

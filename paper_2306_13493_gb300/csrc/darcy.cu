@@ -12,13 +12,17 @@
 // F = f h^2/6 * (number of triangles at the vertex).  Dirichlet columns
 // i = 0 (u = 1) and i = n (u = 0) are kept in the arrays and never updated.
 //
-// Solver.  u (FP64, nodal, Dirichlet values included) is improved by
-// iterative refinement: r = F - A u in FP64; the correction equation A d = r
+// Solver.  u (nodal, Dirichlet values included) is improved by iterative
+// refinement: r = F - A u in high precision; the correction equation A d = r
 // is solved by CG preconditioned with one symmetric multigrid V(1,1) cycle
 // (red-black Gauss-Seidel, full-weighting restriction = transpose of bilinear
 // prolongation, coarse conductances by series/parallel edge averaging, exact
 // tridiagonal solve on the 2-cell grid), in FP32 (precision 32) or FP64
-// (precision 64); u += d.  Batched over samples: grid.y = sample, every
+// (precision 64); u += d.  High precision is FP64 on the FP64 path and
+// float-float (ff.cuh: ~48 bits from FP32 operations, which GB300 runs ~64x
+// faster than FP64 ones) on the mixed path: u, the conductances (hi = the
+// FP32 operator of the inner solve, lo = its rounding error) and the residual.
+// Batched over samples: grid.y = sample, every
 // kernel skips samples whose flag is clear, and all reductions are
 // two-stage in a fixed order (bit-reproducible).
 //
@@ -27,8 +31,10 @@
 // ||u_h||_L2^2 = sum_T |T|/12 [(u_a+u_b+u_c)^2 + u_a^2 + u_b^2 + u_c^2].
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
+#include "ff.cuh"
 #include "mg_tiles.cuh"
 #include "sce_internal.cuh"
 
@@ -79,23 +85,31 @@ __device__ __forceinline__ T block_sum(T val, T *sh) {
 }
 
 // ---------------------------------------------------------------- operator
+// Conductances of the fine grid.  FP64 path (T = double): FP64.  Mixed path
+// (T = float): float-float, hi to cx/cy (the operator of the FP32 inner
+// solve and of the hierarchy), lo to cxl/cyl.
 template <typename Tk, typename T>
 __global__ void cond_kernel(const Tk *__restrict__ k, int n, int vpt, T *__restrict__ cx,
-                            T *__restrict__ cy, double *__restrict__ cx64,
-                            double *__restrict__ cy64) {
+                            T *__restrict__ cy, float *__restrict__ cxl,
+                            float *__restrict__ cyl) {
     const int s = blockIdx.y;
     const long long V = (long long)(n + 1) * (n + 1);
     const Tk *ks = k + s * V;
     const int w = n + 1;
     FOR_VERT(V, vpt) {
         const int j = v / w, i = v - j * w;
-        double gx, gy;
-        cond_at(ks, i, j, n, &gx, &gy);
-        cx[s * V + v] = (T)gx;
-        cy[s * V + v] = (T)gy;
-        if (cx64) {
-            cx64[s * V + v] = gx;
-            cy64[s * V + v] = gy;
+        if constexpr (sizeof(T) == 4 && sizeof(Tk) == 4) {
+            ff gx, gy;
+            cond_at_ff(ks, i, j, n, &gx, &gy);
+            cx[s * V + v] = gx.hi;
+            cy[s * V + v] = gy.hi;
+            cxl[s * V + v] = gx.lo;
+            cyl[s * V + v] = gy.lo;
+        } else {
+            double gx, gy;
+            cond_at(ks, i, j, n, &gx, &gy);
+            cx[s * V + v] = (T)gx;
+            cy[s * V + v] = (T)gy;
         }
     }
 }
@@ -372,105 +386,165 @@ __global__ void reduce_kernel(const double *__restrict__ part, int nblk, int cou
     }
 }
 
-// ---------------------------------------------------------------- FP64 outer
-__global__ void lift_kernel(double *__restrict__ u, int n, int vpt) {
+// ---------------------------------------------------------------- outer refinement
+// High-precision state of the refinement: FP64 path u and conductances in
+// FP64 (the conductances are the hierarchy's level 0); mixed path u as
+// float-float (hi, lo) pairs, conductances hi (level 0) + lo.
+struct OuterD {
+    double *u;
+    const double *cx, *cy;
+};
+struct OuterF {
+    float2 *u;
+    const float *cx, *cy, *cxl, *cyl;
+};
+
+__device__ __forceinline__ double u_at(const OuterD &o, long long i) { return o.u[i]; }
+__device__ __forceinline__ double u_at(const OuterF &o, long long i) {
+    const float2 t = o.u[i];
+    return (double)t.x + (double)t.y;
+}
+__device__ __forceinline__ double cx_at(const OuterD &o, long long i) { return o.cx[i]; }
+__device__ __forceinline__ double cx_at(const OuterF &o, long long i) {
+    return (double)o.cx[i] + (double)o.cxl[i];
+}
+
+// u = lifting of the Dirichlet data: 1 on x1 = 0, 0 elsewhere
+template <class O>
+__global__ void lift_kernel(O o, int n, int vpt) {
     const int s = blockIdx.y;
     const long long V = (long long)(n + 1) * (n + 1);
     const int w = n + 1;
     FOR_VERT(V, vpt) {
         const int i = v % w;
-        u[s * V + v] = i == 0 ? 1.0 : 0.0;
+        if constexpr (std::is_same<O, OuterF>::value) o.u[s * V + v] = make_float2(i == 0 ? 1.0f : 0.0f, 0.0f);
+        else o.u[s * V + v] = i == 0 ? 1.0 : 0.0;
     }
 }
 
-// r64 = F - A u (unknowns; 0 on Dirichlet columns), rin = (T) r64, partial |r64|^2
-template <typename T>
-__global__ void outer_residual_kernel(const double *__restrict__ cx, const double *__restrict__ cy,
-                                      const double *__restrict__ u, double f, int n, int vpt,
-                                      double *__restrict__ r64, T *__restrict__ rin,
+// Load vector entry at a vertex of row j (F = f h^2/6 x triangles): 3 on the
+// Neumann rows j = 0, n, 6 inside; Fd[0] = f h^2/2, Fd[1] = f h^2 (FP64),
+// Ff the same as float-floats.
+struct Load {
+    double Fd[2];
+    ff Ff[2];
+};
+
+// r = F - A u (unknowns; 0 on Dirichlet columns) stored as the working-precision
+// right-hand side rin of the correction equation; partial sums of |r|^2.
+template <typename T, class O>
+__global__ void outer_residual_kernel(O o, Load F, int n, int vpt, T *__restrict__ rin,
                                       double *__restrict__ part, int nblk,
                                       const int *__restrict__ act) {
-    __shared__ double sh[32];
+    __shared__ T sh[32];
     const int s = blockIdx.y;
     if (act && !act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
     const int w = n + 1;
-    const double *ax = cx + s * V, *ay = cy + s * V, *us = u + s * V;
-    const double h2_6 = f / (6.0 * (double)n * (double)n);
-    double acc = 0.0;
+    T acc = T(0);
     FOR_VERT(V, vpt) {
         const int j = v / w, i = v - j * w;
-        double r = 0.0;
+        const long long g = s * V + v;
+        T rv = T(0);
         if (i > 0 && i < n) {
-            const double uc = us[v];
-            double Au = ax[v - 1] * (uc - us[v - 1]) + ax[v] * (uc - us[v + 1]);
-            if (j > 0) Au += ay[v - w] * (uc - us[v - w]);
-            if (j < n) Au += ay[v] * (uc - us[v + w]);
-            const double F = h2_6 * ((j == 0 || j == n) ? 3.0 : 6.0);
-            r = F - Au;
-            acc += r * r;
+            const int inner = (j > 0 && j < n) ? 1 : 0;
+            if constexpr (std::is_same<O, OuterF>::value) {
+                const long long b0 = s * V;
+                const ff Au = apply_at_ff(o.cx + b0, o.cxl + b0, o.cy + b0, o.cyl + b0, o.u + b0,
+                                          i, j, n);
+                rv = ff_sub(F.Ff[inner], Au).hi;
+            } else {
+                const double uc = o.u[g];
+                double Au = o.cx[g - 1] * (uc - o.u[g - 1]) + o.cx[g] * (uc - o.u[g + 1]);
+                if (j > 0) Au += o.cy[g - w] * (uc - o.u[g - w]);
+                if (j < n) Au += o.cy[g] * (uc - o.u[g + w]);
+                rv = (T)(F.Fd[inner] - Au);
+            }
+            acc += rv * rv;
         }
-        r64[s * V + v] = r;
-        rin[s * V + v] = (T)r;
+        rin[g] = rv;
     }
-    const double tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = tot;
+    const T tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
 }
 
 // Residual of the lifting u0 (1 on x1 = 0, 0 elsewhere): A u0 is -cx(0, j) at
 // the vertices (1, j) and 0 at the other unknowns, so r0 = F + [i = 1] cx(0, j).
-template <typename T>
-__global__ void initial_residual_kernel(const double *__restrict__ cx, double f, int n, int vpt,
-                                        double *__restrict__ r64, T *__restrict__ rin,
+template <typename T, class O>
+__global__ void initial_residual_kernel(O o, Load F, int n, int vpt, T *__restrict__ rin,
                                         double *__restrict__ part, int nblk) {
-    __shared__ double sh[32];
+    __shared__ T sh[32];
     const int s = blockIdx.y;
     const long long V = (long long)(n + 1) * (n + 1);
     const int w = n + 1;
-    const double *ax = cx + s * V;
-    const double h2_6 = f / (6.0 * (double)n * (double)n);
-    double acc = 0.0;
+    T acc = T(0);
     FOR_VERT(V, vpt) {
         const int j = v / w, i = v - j * w;
-        double r = 0.0;
+        const long long g = s * V + v;
+        T rv = T(0);
         if (i > 0 && i < n) {
-            r = h2_6 * ((j == 0 || j == n) ? 3.0 : 6.0);
-            if (i == 1) r += ax[v - 1];
-            acc += r * r;
+            const int inner = (j > 0 && j < n) ? 1 : 0;
+            if constexpr (std::is_same<O, OuterF>::value) {
+                ff r = F.Ff[inner];
+                if (i == 1) r = ff_add(r, ff{o.cx[g - 1], o.cxl[g - 1]});
+                rv = r.hi;
+            } else {
+                double r = F.Fd[inner];
+                if (i == 1) r += o.cx[g - 1];
+                rv = (T)r;
+            }
+            acc += rv * rv;
         }
-        r64[s * V + v] = r;
-        rin[s * V + v] = (T)r;
+        rin[g] = rv;
     }
-    const double tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = tot;
+    const T tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
 }
 
-template <typename T>
-__global__ void outer_update_kernel(double *__restrict__ u, const T *__restrict__ d, int n,
-                                    int vpt, const int *__restrict__ act) {
+// u += d (float-float + float on the mixed path)
+template <typename T, class O>
+__global__ void outer_update_kernel(O o, const T *__restrict__ d, int n, int vpt,
+                                    const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
-    FOR_VERT(V, vpt) u[s * V + v] += (double)d[s * V + v];
+    FOR_VERT(V, vpt) {
+        const long long g = s * V + v;
+        if constexpr (std::is_same<O, OuterF>::value) {
+            const float2 t = o.u[g];
+            const ff r = ff_add_f(ff{t.x, t.y}, (float)d[g]);
+            o.u[g] = make_float2(r.hi, r.lo);
+        } else {
+            o.u[g] += (double)d[g];
+        }
+    }
+}
+
+template <class O>
+__global__ void u_to_double_kernel(O o, int n, int vpt, double *__restrict__ out) {
+    const int s = blockIdx.y;
+    const long long V = (long long)(n + 1) * (n + 1);
+    FOR_VERT(V, vpt) out[s * V + v] = u_at(o, s * V + v);
 }
 
 // QoI partials: outflow (vertices i = n-1; bit 0 of qmask) and the P1 mass
 // norm (cells; bit 2).
-__global__ void qoi_partial_kernel(const double *__restrict__ cx, const double *__restrict__ u,
-                                   int n, int vpt, double *__restrict__ part_out,
+template <class O>
+__global__ void qoi_partial_kernel(O o, int n, int vpt, double *__restrict__ part_out,
                                    double *__restrict__ part_l2, int nblk, int qmask) {
     __shared__ double sh[32];
     const int s = blockIdx.y;
     const long long V = (long long)(n + 1) * (n + 1);
     const int w = n + 1;
-    const double *us = u + s * V, *ax = cx + s * V;
+    const long long g0 = s * V;
     const bool want_out = qmask & 1, want_l2 = qmask & 4;
     double qo = 0.0, l2 = 0.0;
     FOR_VERT(V, vpt) {
         const int j = v / w, i = v - j * w;
-        if (want_out && i == n - 1) qo += ax[v] * us[v];
+        if (want_out && i == n - 1) qo += cx_at(o, g0 + v) * u_at(o, g0 + v);
         if (want_l2 && i < n && j < n) {
-            const double a = us[v], b = us[v + 1], c = us[v + w + 1], d = us[v + w];
+            const double a = u_at(o, g0 + v), b = u_at(o, g0 + v + 1);
+            const double c = u_at(o, g0 + v + w + 1), d = u_at(o, g0 + v + w);
             const double s1 = a + b + c, s2 = a + d + c;
             l2 += s1 * s1 + a * a + b * b + c * c + s2 * s2 + a * a + d * d + c * c;
         }
@@ -483,9 +557,10 @@ __global__ void qoi_partial_kernel(const double *__restrict__ cx, const double *
 
 // QoIs per sample (those of qmask; the others are written as 0), status,
 // iteration counts.  part_out / part_l2 may be NULL when qmask has neither.
+template <class O>
 __global__ void qoi_final_kernel(const double *__restrict__ part_out,
                                  const double *__restrict__ part_l2, int nblk, int count,
-                                 const double *__restrict__ u, int n, double f,
+                                 O o, int n, double f,
                                  const Scal sc, double rtol2, double *__restrict__ qoi,
                                  int *__restrict__ iters_out, int *__restrict__ status_out,
                                  int *__restrict__ nfail, int qmask) {
@@ -512,10 +587,11 @@ __global__ void qoi_final_kernel(const double *__restrict__ part_out,
     const int ca = min((int)floor(xs), n - 1), cb = min((int)floor(ys), n - 1);
     const double xi = xs - ca, et = ys - cb;
     const long long V = (long long)(n + 1) * (n + 1);
-    const double *us = u + s * V;
+    const long long g0 = s * V;
     const int w = n + 1;
-    const double uab = us[cb * w + ca], ua1b = us[cb * w + ca + 1];
-    const double uab1 = us[(cb + 1) * w + ca], ua1b1 = us[(cb + 1) * w + ca + 1];
+    const double uab = u_at(o, g0 + cb * w + ca), ua1b = u_at(o, g0 + cb * w + ca + 1);
+    const double uab1 = u_at(o, g0 + (cb + 1) * w + ca);
+    const double ua1b1 = u_at(o, g0 + (cb + 1) * w + ca + 1);
     double q_pt;
     if (xi >= et) q_pt = uab + xi * (ua1b - uab) + et * (ua1b1 - ua1b);   // T1
     else q_pt = uab + et * (uab1 - uab) + xi * (ua1b1 - uab1);             // T2
@@ -569,7 +645,9 @@ struct Solver {
     T *cx[MAXLEV], *cy[MAXLEV], *b[MAXLEV], *z[MAXLEV];
     T *zpre[MAXLEV] = {};   // pre-smoothed z of the tiled levels (fused cycle)
     T *d = nullptr, *p = nullptr, *q = nullptr;
-    double *u64 = nullptr, *r64 = nullptr, *cx64 = nullptr, *cy64 = nullptr;
+    double *u64 = nullptr;                  // FP64 path: u
+    float2 *uff = nullptr;                  // mixed path: u as float-float pairs
+    float *cxl = nullptr, *cyl = nullptr;   // mixed path: lo parts of the conductances
     double *part = nullptr, *part2 = nullptr;
     Scal sc{};
     int *misc = nullptr;   // [0] counter, [1] nfail, [2] max iters
@@ -730,15 +808,27 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     SCE_TRY(S.alloc(&S.d, c0));
     SCE_TRY(S.alloc(&S.p, c0));
     SCE_TRY(S.alloc(&S.q, c0));
-    SCE_TRY(S.alloc(&S.u64, c0));
-    SCE_TRY(S.alloc(&S.r64, c0));
-    const bool same64 = sizeof(T) == sizeof(double);
-    if (same64) {
-        S.cx64 = (double *)S.cx[0];
-        S.cy64 = (double *)S.cy[0];
+    constexpr bool mixed = sizeof(T) == 4;
+    using O = std::conditional_t<mixed, OuterF, OuterD>;
+    O o{};
+    if constexpr (mixed) {
+        SCE_TRY(S.alloc(&S.uff, c0));
+        SCE_TRY(S.alloc(&S.cxl, c0));
+        SCE_TRY(S.alloc(&S.cyl, c0));
+        o = OuterF{S.uff, S.cx[0], S.cy[0], S.cxl, S.cyl};
     } else {
-        SCE_TRY(S.alloc(&S.cx64, c0));
-        SCE_TRY(S.alloc(&S.cy64, c0));
+        SCE_TRY(S.alloc(&S.u64, c0));
+        o = OuterD{S.u64, S.cx[0], S.cy[0]};
+    }
+    Load F{};
+    {
+        const double h2_6 = p->f / (6.0 * (double)n0 * (double)n0);
+        F.Fd[0] = h2_6 * 3.0;   // 3 triangles at a vertex of the rows j = 0, n
+        F.Fd[1] = h2_6 * 6.0;
+        for (int r = 0; r < 2; ++r) {
+            F.Ff[r].hi = (float)F.Fd[r];
+            F.Ff[r].lo = (float)(F.Fd[r] - (double)F.Ff[r].hi);
+        }
     }
     {
         const char *e = getenv("SCE_MG_FUSED");
@@ -774,9 +864,8 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     const dim3 g0 = S.grid(0);
     // operator and hierarchy
     {
-        SceProf pr(KP_COND, st, S.vb(0, 2.0, sizeof(Tk) + (same64 ? 0.0 : 16.0)));
-        cond_kernel<Tk, T><<<g0, l0.tpb, 0, st>>>(k, n0, l0.vpt, S.cx[0], S.cy[0],
-                                                  same64 ? nullptr : S.cx64, same64 ? nullptr : S.cy64);
+        SceProf pr(KP_COND, st, S.vb(0, 2.0, sizeof(Tk) + (mixed ? 8.0 : 0.0)));
+        cond_kernel<Tk, T><<<g0, l0.tpb, 0, st>>>(k, n0, l0.vpt, S.cx[0], S.cy[0], S.cxl, S.cyl);
     }
     SCE_CUDA(cudaGetLastError());
     for (int L = 1; L < S.nlev; ++L) {
@@ -787,7 +876,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     SCE_CUDA(cudaGetLastError());
     {
         SceProf pr(KP_OUTER_UPD, st, S.vb(0, 0.0, 8.0));
-        lift_kernel<<<g0, l0.tpb, 0, st>>>(S.u64, n0, l0.vpt);
+        lift_kernel<<<g0, l0.tpb, 0, st>>>(o, n0, l0.vpt);
     }
 
     const double rtol2 = p->rtol * p->rtol;
@@ -799,9 +888,9 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
 
     // initial residual (of the lifting, in closed form)
     {
-        SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 16.0));
-        initial_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx64, p->f, n0, l0.vpt, S.r64, S.b[0],
-                                                          S.part, l0.nblk);
+        SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0));
+        initial_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(o, F, n0, l0.vpt, S.b[0], S.part,
+                                                          l0.nblk);
     }
     SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
     S.reduce(RED_ORR0, nullptr, rtol2, in_rel2);
@@ -865,13 +954,13 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         SCE_CUDA(cudaGetLastError());
         {
             SceProf pr(KP_OUTER_UPD, st, S.vb(0, 1.0, 16.0));
-            outer_update_kernel<T><<<g0, l0.tpb, 0, st>>>(S.u64, S.d, n0, l0.vpt, S.sc.act_out);
+            outer_update_kernel<T><<<g0, l0.tpb, 0, st>>>(o, S.d, n0, l0.vpt, S.sc.act_out);
         }
         {
-            SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 32.0));
-            outer_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx64, S.cy64, S.u64, p->f, n0,
-                                                            l0.vpt, S.r64, S.b[0], S.part, l0.nblk,
-                                                            S.sc.act_out);
+            // reads u (8 B) and both conductances (16 B: FP64, or FP32 hi + lo), writes rin
+            SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 24.0));
+            outer_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(o, F, n0, l0.vpt, S.b[0], S.part,
+                                                            l0.nblk, S.sc.act_out);
         }
         SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
         S.reduce(RED_ORR, S.sc.act_out, rtol2, in_rel2);
@@ -883,17 +972,22 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     const bool grid_qoi = (qmask & 5) != 0;
     if (grid_qoi) {
         SceProf pr(KP_QOI, st, S.vb(0, 0.0, 16.0));
-        qoi_partial_kernel<<<g0, l0.tpb, 0, st>>>(S.cx64, S.u64, n0, l0.vpt, S.part, S.part2,
-                                                  l0.nblk, qmask);
+        qoi_partial_kernel<<<g0, l0.tpb, 0, st>>>(o, n0, l0.vpt, S.part, S.part2, l0.nblk,
+                                                  qmask);
     }
     SCE_CUDA(cudaMemsetAsync(S.misc + 1, 0, sizeof(int), st));
     qoi_final_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(
-        grid_qoi ? S.part : nullptr, grid_qoi ? S.part2 : nullptr, l0.nblk, count, S.u64, n0,
+        grid_qoi ? S.part : nullptr, grid_qoi ? S.part2 : nullptr, l0.nblk, count, o, n0,
         p->f, S.sc, rtol2, qoi, iters, status, S.misc + 1, qmask);
     max_int_kernel<<<1, 256, 0, st>>>(S.sc.iters, count, S.misc + 2);
     SCE_CUDA(cudaGetLastError());
-    if (u_out)
-        SCE_CUDA(cudaMemcpyAsync(u_out, S.u64, c0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (u_out) {
+        if constexpr (mixed) {
+            u_to_double_kernel<<<g0, l0.tpb, 0, st>>>(o, n0, l0.vpt, u_out);
+        } else {
+            SCE_CUDA(cudaMemcpyAsync(u_out, S.u64, c0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+    }
     int hm[3] = {0, 0, 0};
     SCE_CUDA(cudaMemcpyAsync(hm, S.misc + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     SCE_CUDA(cudaStreamSynchronize(st));

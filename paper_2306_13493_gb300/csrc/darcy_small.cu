@@ -1,8 +1,8 @@
 // One-block-per-sample Darcy solver for small grids (n <= 64), mixed precision.
 //
 // The same discrete problem and the same algorithm as the batched solver in
-// darcy.cu (FP64 iterative refinement around FP32 CG preconditioned with one
-// symmetric multigrid V(1,1) cycle), but the whole solve of one sample --
+// darcy.cu (float-float iterative refinement around FP32 CG preconditioned
+// with one symmetric multigrid V(1,1) cycle), but the whole solve of one sample --
 // conductances, hierarchy, every CG iteration and V-cycle, the QoIs -- runs in
 // one thread block with all state in shared memory: the coefficient field is
 // read from HBM once and three doubles per sample are written back.  Many
@@ -24,10 +24,11 @@ template <int N> struct SmallLayout {
     static constexpr int V = W * W;
     static constexpr int NL = ilog2c(N);            // levels N, N/2, ..., 2
     static constexpr int vof(int L) { return ((N >> L) + 1) * ((N >> L) + 1); }
-    // doubles: u, cx64, cy64, reduction scratch (64); floats: the multigrid
-    // hierarchy, d, p
-    static constexpr size_t bytes = sizeof(double) * (3 * (size_t)V + 64) +
-                                    sizeof(float) * (MGPackedLayout<N>::total() + 2 * (size_t)V);
+    // float2: u as float-float; doubles: reduction scratch (64); floats: the
+    // multigrid hierarchy (level 0 holds the conductances' hi parts), their lo
+    // parts, d, p
+    static constexpr size_t bytes = sizeof(float2) * (size_t)V + sizeof(double) * 64 +
+                                    sizeof(float) * (MGPackedLayout<N>::total() + 4 * (size_t)V);
 };
 
 // Sum over the block, returned to every thread (fixed order).
@@ -67,7 +68,7 @@ __device__ __forceinline__ float bsumf(float v, float *sh) {
 }
 
 template <int N, int NT>
-__global__ void __launch_bounds__(NT) small_solve_kernel(
+__global__ void __launch_bounds__(NT, N == 64 ? 2 : (N == 32 ? 3 : (N == 16 ? 6 : 1))) small_solve_kernel(
     const float *__restrict__ kin, double f, double rtol2, double in_rel2, int maxit,
     double *__restrict__ qoi, int *__restrict__ iters_out, int *__restrict__ status_out,
     double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits, int qmask) {
@@ -75,48 +76,53 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
     using MG = MGPackedLayout<N>;
     constexpr int W = Lay::W, V = Lay::V, NL = Lay::NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *u = reinterpret_cast<double *>(smem_raw);
-    double *cx64 = u + V;
-    double *cy64 = cx64 + V;
-    double *sh = cy64 + V;
-    // FP32 region: the multigrid hierarchy (level 0 = [cx | cy | r | z]), then d, p
+    float2 *u = reinterpret_cast<float2 *>(smem_raw);
+    double *sh = reinterpret_cast<double *>(u + V);
+    // FP32 region: the multigrid hierarchy (level 0 = [cx | cy | r | z]), then
+    // the lo parts of the level-0 conductances, d, p
     float *mg = reinterpret_cast<float *>(sh + 64);
     float *cx0 = mg + MG::off(0, 0), *cy0 = mg + MG::off(0, 1);
     float *r = mg + MG::off(0, 2), *z = mg + MG::off(0, 3);
-    float *d = mg + MG::total();
+    float *cxl = mg + MG::total();
+    float *cyl = cxl + V;
+    float *d = cyl + V;
     float *p = d + V;
     const int s = blockIdx.x;
     const int tid = threadIdx.x;
     const float *ks = kin + (size_t)s * V;
 
-    // operator: FP64 conductances (outer residual, QoIs) and FP32 copies
+    // operator: float-float conductances, hi = the FP32 operator of the inner solve
     for (int v = tid; v < V; v += NT) {
         const int j = v / W, i = v - j * W;
-        double gx, gy;
-        cond_at(ks, i, j, N, &gx, &gy);
-        cx64[v] = gx;
-        cy64[v] = gy;
-        cx0[v] = (float)gx;
-        cy0[v] = (float)gy;
-        u[v] = i == 0 ? 1.0 : 0.0;
+        ff gx, gy;
+        cond_at_ff(ks, i, j, N, &gx, &gy);
+        cx0[v] = gx.hi;
+        cy0[v] = gy.hi;
+        cxl[v] = gx.lo;
+        cyl[v] = gy.lo;
+        u[v] = make_float2(i == 0 ? 1.0f : 0.0f, 0.0f);
     }
     __syncthreads();
     block_coarsen<float, N, NT, MG, 1>(mg);
 
+    // load F = f h^2/6 x (triangles at the vertex): 3 on the rows j = 0, N, 6 inside
     const double h2_6 = f / (6.0 * (double)N * (double)N);
-    // FP64 residual r = F - A u into the FP32 rhs, returns |r|^2
+    ff Fv[2];
+    for (int q = 0; q < 2; ++q) Fv[q] = ff_from_double(h2_6 * (q ? 6.0 : 3.0));
+    // float-float residual r = F - A u, rounded into the FP32 rhs; returns |r|^2
     auto outer_residual = [&]() {
-        double acc = 0.0;
+        float acc = 0.f;
         for (int v = tid; v < V; v += NT) {
             const int j = v / W, i = v - j * W;
-            double rv = 0.0;
+            float rv = 0.f;
             if (i > 0 && i < N) {
-                rv = h2_6 * ((j == 0 || j == N) ? 3.0 : 6.0) - apply_at(cx64, cy64, u, i, j, N);
+                rv = ff_sub(Fv[(j > 0 && j < N) ? 1 : 0],
+                            apply_at_ff(cx0, cxl, cy0, cyl, u, i, j, N)).hi;
                 acc += rv * rv;
             }
-            r[v] = (float)rv;
+            r[v] = rv;
         }
-        return bsum<NT>(acc, sh);
+        return bsum<NT>((double)acc, sh);
     };
 
     // one symmetric V(1,1) cycle: z[0] = M^-1 r
@@ -126,18 +132,19 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
     // residual of the lifting in closed form: r0 = F + [i = 1] cx(0, j)
     double orr;
     {
-        double acc = 0.0;
+        float acc = 0.f;
         for (int v = tid; v < V; v += NT) {
             const int j = v / W, i = v - j * W;
-            double rv = 0.0;
+            float rv = 0.f;
             if (i > 0 && i < N) {
-                rv = h2_6 * ((j == 0 || j == N) ? 3.0 : 6.0);
-                if (i == 1) rv += cx64[v - 1];
+                ff rf = Fv[(j > 0 && j < N) ? 1 : 0];
+                if (i == 1) rf = ff_add(rf, ff{cx0[v - 1], cxl[v - 1]});
+                rv = rf.hi;
                 acc += rv * rv;
             }
-            r[v] = (float)rv;
+            r[v] = rv;
         }
-        orr = bsum<NT>(acc, sh);
+        orr = bsum<NT>((double)acc, sh);
     }
     const double orr0 = orr;
     float *shf = reinterpret_cast<float *>(sh + 48);
@@ -189,7 +196,10 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
             for (int v = tid; v < V; v += NT) p[v] = z[v] + beta * p[v];
             __syncthreads();
         }
-        for (int v = tid; v < V; v += NT) u[v] += (double)d[v];
+        for (int v = tid; v < V; v += NT) {
+            const ff t = ff_add_f(ff{u[v].x, u[v].y}, d[v]);
+            u[v] = make_float2(t.hi, t.lo);
+        }
         __syncthreads();
         orr = outer_residual();
     }
@@ -198,16 +208,17 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
     // pass over the grid, the point value (bit 1) does not
     double qo = 0.0, l2 = 0.0;
     const bool want_out = qmask & 1, want_l2 = qmask & 4;
+    auto ud = [&](int q) { return (double)u[q].x + (double)u[q].y; };
     if (want_out || want_l2 || u_out) {
         for (int v = tid; v < V; v += NT) {
             const int j = v / W, i = v - j * W;
-            if (want_out && i == N - 1) qo += cx64[v] * u[v];
+            if (want_out && i == N - 1) qo += ((double)cx0[v] + (double)cxl[v]) * ud(v);
             if (want_l2 && i < N && j < N) {
-                const double a = u[v], b = u[v + 1], c = u[v + W + 1], e = u[v + W];
+                const double a = ud(v), b = ud(v + 1), c = ud(v + W + 1), e = ud(v + W);
                 const double s1 = a + b + c, s2 = a + e + c;
                 l2 += s1 * s1 + a * a + b * b + c * c + s2 * s2 + a * a + e * e + c * c;
             }
-            if (u_out) u_out[(size_t)s * V + v] = u[v];
+            if (u_out) u_out[(size_t)s * V + v] = ud(v);
         }
         qo = bsum<NT>(qo, sh);
         l2 = bsum<NT>(l2, sh);
@@ -219,8 +230,8 @@ __global__ void __launch_bounds__(NT) small_solve_kernel(
         const double xs = 7.0 / 15.0 * (double)N, ys = 7.0 / 15.0 * (double)N;
         const int ca = min((int)floor(xs), N - 1), cb = min((int)floor(ys), N - 1);
         const double xi = xs - ca, et = ys - cb;
-        const double uab = u[cb * W + ca], ua1b = u[cb * W + ca + 1];
-        const double uab1 = u[(cb + 1) * W + ca], ua1b1 = u[(cb + 1) * W + ca + 1];
+        const double uab = ud(cb * W + ca), ua1b = ud(cb * W + ca + 1);
+        const double uab1 = ud((cb + 1) * W + ca), ua1b1 = ud((cb + 1) * W + ca + 1);
         const double q_pt = !(qmask & 2) ? 0.0
                             : xi >= et ? uab + xi * (ua1b - uab) + et * (ua1b1 - ua1b)
                                        : uab + et * (uab1 - uab) + xi * (ua1b1 - uab1);

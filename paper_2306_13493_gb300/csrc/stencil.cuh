@@ -4,6 +4,8 @@
 // (row-major, x-fastest, width n+1); they work on global or shared memory.
 #pragma once
 
+#include "ff.cuh"
+
 namespace sce {
 
 // Edge conductances at vertex (i, j) from the vertex values of k, in FP64:
@@ -35,6 +37,50 @@ __device__ __forceinline__ void cond_at(const Tk *ks, int i, int j, int n, doubl
     }
     *gx = x;
     *gy = y;
+}
+
+// 1/6 as a float-float (nearest float, and the float nearest to the rest)
+__device__ __forceinline__ ff ff_sixth() { return {0x1.555556p-3f, -0x1.555556p-28f}; }
+
+// cond_at in float-float from FP32 k: the same sums of at most six vertex
+// values and one scaling by 1/6.
+__device__ __forceinline__ void cond_at_ff(const float *ks, int i, int j, int n, ff *gx, ff *gy) {
+    const int w = n + 1, v = j * w + i;
+    const float a = ks[v];
+    const float b = i < n ? ks[v + 1] : 0.0f;
+    const float e = j < n ? ks[v + w] : 0.0f;
+    const float c = (i < n && j < n) ? ks[v + w + 1] : 0.0f;
+    ff x = {0.0f, 0.0f}, y = {0.0f, 0.0f};
+    if (i < n) {
+        const ff ab = two_sum(a, b);
+        if (j < n) x = ff_add_f(ab, c);
+        if (j > 0) x = ff_add(x, ff_add_f(ab, ks[v - w]));
+        x = ff_mul(x, ff_sixth());
+    }
+    if (j < n) {
+        const ff ae = two_sum(a, e);
+        if (i < n) y = ff_add_f(ae, c);
+        if (i > 0) y = ff_add(y, ff_add_f(ae, ks[v - 1]));
+        y = ff_mul(y, ff_sixth());
+    }
+    *gx = x;
+    *gy = y;
+}
+
+// (A u)(i, j) of an unknown vertex in float-float: u as (hi, lo) pairs,
+// conductances hi (cx, cy) + lo (cxl, cyl); differences of u are formed
+// before the products (both exact-ish in float-float).
+__device__ __forceinline__ ff apply_at_ff(const float *cx, const float *cxl, const float *cy,
+                                          const float *cyl, const float2 *u, int i, int j,
+                                          int n) {
+    const int w = n + 1, v = j * w + i;
+    auto U = [&](int q) { const float2 t = u[q]; return ff{t.x, t.y}; };
+    const ff uc = U(v);
+    ff a = ff_mul(ff{cx[v - 1], cxl[v - 1]}, ff_sub(uc, U(v - 1)));
+    a = ff_add(a, ff_mul(ff{cx[v], cxl[v]}, ff_sub(uc, U(v + 1))));
+    if (j > 0) a = ff_add(a, ff_mul(ff{cy[v - w], cyl[v - w]}, ff_sub(uc, U(v - w))));
+    if (j < n) a = ff_add(a, ff_mul(ff{cy[v], cyl[v]}, ff_sub(uc, U(v + w))));
+    return a;
 }
 
 template <typename T>

@@ -108,3 +108,24 @@ class ServedWorkload:
 
 
 SERVED = ServedWorkload()
+
+
+@dataclass
+class PrecisionStudy:
+    """Precision study at scale: the mixed path (FP32 normals, FFT, exp and
+    multigrid, FP64 eigenvalues and refinement) against the all-FP64 path and
+    the FP64 oracle, on one fine grid without padding beyond P = 2n."""
+    nus: tuple = (0.5, 2.5)
+    lam: float = 0.01
+    sigma2: float = 3.0
+    n: int = 1024                        # 1025^2 vertices
+    pad_mode: int = 1                    # classical embedding, doubled only if not PSD
+    J: int = 0                           # P = 2n = 2048
+    count: int = 512
+    oracle_samples: int = 16
+    f: float = 1.0
+    seed: int = 4
+    rtol: float = 1e-10
+
+
+PRECISION_STUDY = PrecisionStudy()
