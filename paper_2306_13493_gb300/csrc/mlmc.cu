@@ -230,7 +230,7 @@ extern "C" int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int q
         }
         return worst;
     };
-    if (max_concurrency <= 1 || ntasks <= 1) {
+    if (max_concurrency <= 1 || ntasks == 0) {
         for (int i = 0; i < ntasks; ++i) {
             tasks[i].status = level_run(args_of(i), p, seed, qoi_index, st, st);
             if (tasks[i].status != CE_OK && tasks[i].status != CE_ERR_NOT_CONVERGED) break;
