@@ -1,14 +1,21 @@
-// Fused, shared-memory-tiled multigrid kernels for the batched solver.
+// Fused, register-blocked multigrid kernels for the batched solver.
 //
 // The fine grid of a level is partitioned by tiles of CW x CH coarse vertices;
 // tile (tx, ty) owns the fine vertices [2 I0, 2 I0 + 2 CW) x [2 J0, 2 J0 + 2 CH)
 // (I0 = tx CW, J0 = ty CH), so the owned regions of all tiles cover the fine
 // grid exactly once and the coarse tiles cover the coarse grid exactly once.
-// Each kernel stages a 64 x 32 window (owned region plus halo) in shared
-// memory, recomputes halo values instead of exchanging them, and writes only
-// what it owns.  Thread (x, y) of the 32 x 8 block handles the window
-// elements (x + 32 a, y + 8 b), a < 2, b < MG_SH / 8, so no index arithmetic
-// is repeated per pass; 1/diag is computed once per element.
+// Each kernel works on a 64 x 32 window (owned region plus halo), recomputes
+// halo values instead of exchanging them with other tiles, and writes only
+// what it owns.  The window lives in registers: warp w holds rows
+// [4 w, 4 w + 4), lane x the columns (2 x, 2 x + 1) of them, i.e. a 2 x 4
+// block per lane.  Horizontal neighbours come from the lanes beside (warp
+// shuffles), vertical ones from the lane's own block except across the
+// warps' strip boundaries, whose rows go through shared memory (double
+// buffered, one barrier per half-sweep).  The window origin is even in both
+// directions, so the colour of block element (c, r) is (c + r) % 2 for every
+// lane and every loop over a colour unrolls with compile-time register
+// indices.  Elements outside the grid hold zero data; at Dirichlet columns and
+// outside the grid 1/diag is 0, so their z stays 0.
 //
 //   mg_down: pre-smoothing from a zero guess (red then black Gauss-Seidel),
 //            fine residual, full-weighting restriction -> zpre (fine), b (coarse).
@@ -34,24 +41,21 @@
 
 namespace sce {
 
-#ifndef SCE_MG_SH
-#define SCE_MG_SH 32
-#endif
-constexpr int MG_SW = 64;                  // window width (= row stride)
-constexpr int MG_SH = SCE_MG_SH;           // window height (multiple of 8)
+constexpr int MG_SW = 64;                  // window width: 32 lanes x 2 columns
+constexpr int MG_SH = 32;                  // window height: 8 warps x 4 rows
 constexpr int MG_CW = (MG_SW - 6) / 2;     // 29 coarse vertices per tile in x
-constexpr int MG_CH = (MG_SH - 6) / 2;     // coarse vertices per tile in y
+constexpr int MG_CH = (MG_SH - 6) / 2;     // 13 coarse vertices per tile in y
 constexpr int MG_THREADS = 256;
-constexpr int MG_ROWS = MG_SH / 8;         // row groups per thread
-constexpr int MG_NE = 2 * MG_ROWS;         // window elements per thread
-static_assert(MG_SH % 8 == 0 && MG_NE <= 32, "tile height");
-constexpr int MG_BLOCKS_PER_SM = MG_SH <= 32 ? 5 : (MG_SH <= 48 ? 3 : 2);
-constexpr int MG_CCW = MG_CW + 3;          // coarse window of mg_up
+constexpr int MG_CCW = MG_CW + 3;          // coarse window of mg_up: 32 x 16 (+1 row)
 constexpr int MG_CCH = MG_CH + 3;
+constexpr unsigned MG_FULL = 0xffffffffu;
 
+// shared memory: z of rows 0 and 3 of every warp (2 buffers), one row per
+// warp for cy / residual exchange, the coarse window of mg_up with a spare row
 template <typename T>
 constexpr size_t mg_tile_smem_bytes() {
-    return sizeof(T) * (5 * (size_t)MG_SW * MG_SH + (size_t)MG_CCW * MG_CCH);
+    return sizeof(T) * (2 * 2 * 8 * (size_t)MG_SW + 8 * (size_t)MG_SW +
+                        (size_t)(MG_CCH + 1) * MG_CCW + 1);
 }
 
 template <typename T>
@@ -71,219 +75,272 @@ template <typename T> __device__ __forceinline__ T recip(T d);
 template <> __device__ __forceinline__ float recip<float>(float d) { return __frcp_rn(d); }
 template <> __device__ __forceinline__ double recip<double>(double d) { return 1.0 / d; }
 
-// Gauss-Seidel update of the vertices of colour `color` ((gi + gj) % 2) in the
-// local box [lo, hix] x [lo, hiy] of the window.  Lane x of warp y handles the
-// column pair (2x, 2x+1) of rows y + 8b, i.e. exactly the one element of each
-// pair that has the colour, so no lane idles.
+// A lane's 2 x 4 block: element e = 2 r + c is window element
+// (2 lane + c, 4 warp + r).  Conductances: cxe = cx at the element (edge to
+// the east), cyn = cy (edge to the north); cxw0[r] = west edge of the c = 0
+// column (from lane - 1), cys0[c] = south edge of row 0 (from warp - 1).
 template <typename T>
-__device__ __forceinline__ void tile_color_pass(T *sz, const T *sb, const T *scx, const T *scy,
-                                                const T *sinv, int ox, int oy, int n, int color,
-                                                int lo, int hix, int hiy) {
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    // rows ty + 8 bb all have the parity of ty: the column is the same for all bb
-    const int li = 2 * tx + ((ox + oy + ty + color) & 1);
-    const int gi = ox + li;
-    if (li < lo || li > hix || gi < 1 || gi > n - 1) return;
-#pragma unroll
-    for (int bb = 0; bb < MG_ROWS; ++bb) {
-        const int lj = ty + 8 * bb;
-        if (lj < lo || lj > hiy) continue;
-        const int gj = oy + lj;
-        if (gj < 0 || gj > n) continue;
-        const int l = lj * MG_SW + li;
-        sz[l] = (sb[l] + scx[l - 1] * sz[l - 1] + scx[l] * sz[l + 1] +
-                 scy[l - MG_SW] * sz[l - MG_SW] + scy[l] * sz[l + MG_SW]) * sinv[l];
-    }
-}
+struct TileBlock {
+    T b[8], z[8], cxe[8], cyn[8], inv[8], cxw0[4], cys0[2];
+    T zs[2], zn[2];   // z of the rows below (r = -1) and above (r = 4) the strip
+};
 
-// Residual b - A z at the red vertices ((gi + gj) even) of the local box
-// [3, MG_SW-3] x [3, MG_SH-3], in place of b; 0 at Dirichlet vertices.
+// Loads b, cx, cy of the block (zero outside the grid); returns the bitmask
+// of elements that are unknowns (1 <= gi <= n-1, 0 <= gj <= n).
 template <typename T>
-__device__ __forceinline__ void tile_red_residual(const T *sz, T *sb, const T *scx,
-                                                  const T *scy, int ox, int oy, int n) {
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int li = 2 * tx + ((ox + oy + ty) & 1);
-    const int gi = ox + li;
-    if (li < 3 || li > MG_SW - 3) return;
-    const bool unk_x = gi >= 1 && gi <= n - 1;
+__device__ __forceinline__ unsigned tile_load(TileBlock<T> &t, const T *bs, const T *xs,
+                                              const T *ys, int gi0, int gj0, int n) {
+    const int w = n + 1;
+    unsigned unk = 0;
 #pragma unroll
-    for (int bb = 0; bb < MG_ROWS; ++bb) {
-        const int lj = ty + 8 * bb;
-        if (lj < 3 || lj > MG_SH - 3) continue;
-        const int gj = oy + lj;
-        const int l = lj * MG_SW + li;
-        T rv = T(0);
-        if (unk_x && gj >= 0 && gj <= n) {
-            const T zc = sz[l];
-            rv = sb[l] - (scx[l - 1] * (zc - sz[l - 1]) + scx[l] * (zc - sz[l + 1]) +
-                          scy[l - MG_SW] * (zc - sz[l - MG_SW]) + scy[l] * (zc - sz[l + MG_SW]));
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int e = 2 * r + c, gi = gi0 + c, gj = gj0 + r;
+            const bool in = gi >= 0 && gi <= n && gj >= 0 && gj <= n;
+            const long long g = (long long)gj * w + gi;
+            t.b[e] = in ? bs[g] : T(0);
+            t.cxe[e] = in ? xs[g] : T(0);
+            t.cyn[e] = in ? ys[g] : T(0);
+            if (in && gi >= 1 && gi <= n - 1) unk |= 1u << e;
         }
-        sb[l] = rv;
+    }
+    return unk;
+}
+
+// West/south edge conductances from the neighbouring lane / warp (xrow: one
+// shared row per warp), then 1/diag (0 where not an unknown).  Contains a
+// barrier.
+template <typename T>
+__device__ __forceinline__ void tile_diag(TileBlock<T> &t, T *xrow, int lane, int warp,
+                                          unsigned unk) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) t.cxw0[r] = __shfl_up_sync(MG_FULL, t.cxe[2 * r + 1], 1);
+    xrow[warp * MG_SW + 2 * lane] = t.cyn[6];
+    xrow[warp * MG_SW + 2 * lane + 1] = t.cyn[7];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+        t.cys0[c] = warp > 0 ? xrow[(warp - 1) * MG_SW + 2 * lane + c] : T(0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int e = 2 * r + c;
+            const T cw = c == 0 ? t.cxw0[r] : t.cxe[2 * r];
+            const T cs = r == 0 ? t.cys0[c] : t.cyn[2 * (r - 1) + c];
+            t.inv[e] = ((unk >> e) & 1) ? recip(cw + t.cxe[e] + cs + t.cyn[e]) : T(0);
+        }
     }
 }
 
-// Element e (0..7) of this thread: local (li, lj) and offset in the window.
-#define MG_ELEM(e, li, lj, l)                                   \
-    const int li = (threadIdx.x & 31) + 32 * ((e) & 1);         \
-    const int lj = (threadIdx.x >> 5) + 8 * ((e) >> 1);         \
-    const int l = lj * MG_SW + li
+// Publishes rows 0 and 3 of z in buffer buf, waits, and reads the rows below
+// and above the strip (zero beyond the window).
+template <typename T>
+__device__ __forceinline__ void tile_exchange(TileBlock<T> &t, T *xz, int buf, int lane,
+                                              int warp) {
+    T *lo = xz + (buf * 2 + 0) * 8 * MG_SW, *hi = xz + (buf * 2 + 1) * 8 * MG_SW;
+    lo[warp * MG_SW + 2 * lane] = t.z[0];
+    lo[warp * MG_SW + 2 * lane + 1] = t.z[1];
+    hi[warp * MG_SW + 2 * lane] = t.z[6];
+    hi[warp * MG_SW + 2 * lane + 1] = t.z[7];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        t.zs[c] = warp > 0 ? hi[(warp - 1) * MG_SW + 2 * lane + c] : T(0);
+        t.zn[c] = warp < 7 ? lo[(warp + 1) * MG_SW + 2 * lane + c] : T(0);
+    }
+}
+
+// Neighbours of element (c, r) in the order west, east, south, north: their z
+// and the conductances of the four edges.  The horizontal neighbour in the
+// next lane comes by shuffle, so every lane of the warp must call this for
+// the same (c, r).
+template <typename T, int C, int R>
+__device__ __forceinline__ void tile_nbrs(const TileBlock<T> &t, T *zw, T *ze, T *zsv, T *znv,
+                                          T *cw, T *cs) {
+    if constexpr (C == 0) {
+        *zw = __shfl_up_sync(MG_FULL, t.z[2 * R + 1], 1);
+        *ze = t.z[2 * R + 1];
+        *cw = t.cxw0[R];
+    } else {
+        *zw = t.z[2 * R];
+        *ze = __shfl_down_sync(MG_FULL, t.z[2 * R], 1);
+        *cw = t.cxe[2 * R];
+    }
+    *zsv = R == 0 ? t.zs[C] : t.z[2 * (R - 1) + C];
+    *znv = R == 3 ? t.zn[C] : t.z[2 * (R + 1) + C];
+    *cs = R == 0 ? t.cys0[C] : t.cyn[2 * (R - 1) + C];
+}
+
+// One Gauss-Seidel half-sweep over the elements of colour COL of the block.
+template <typename T, int COL, int R = 0>
+__device__ __forceinline__ void tile_half_sweep(TileBlock<T> &t) {
+    if constexpr (R < 4) {
+        constexpr int C = (COL + R) & 1, e = 2 * R + C;
+        T zw, ze, zsv, znv, cw, cs;
+        tile_nbrs<T, C, R>(t, &zw, &ze, &zsv, &znv, &cw, &cs);
+        t.z[e] = (t.b[e] + cw * zw + t.cxe[e] * ze + cs * zsv + t.cyn[e] * znv) * t.inv[e];
+        tile_half_sweep<T, COL, R + 1>(t);
+    }
+}
+
+// Residual b - A z at the red element of row R (c = R % 2); 0 where not an unknown.
+template <typename T, int R>
+__device__ __forceinline__ T tile_red_residual(const TileBlock<T> &t, unsigned unk) {
+    constexpr int C = R & 1, e = 2 * R + C;
+    T zw, ze, zsv, znv, cw, cs;
+    tile_nbrs<T, C, R>(t, &zw, &ze, &zsv, &znv, &cw, &cs);
+    const T zc = t.z[e];
+    const T rv = t.b[e] - (cw * (zc - zw) + t.cxe[e] * (zc - ze) + cs * (zc - zsv) +
+                           t.cyn[e] * (zc - znv));
+    return ((unk >> e) & 1) ? rv : T(0);
+}
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, MG_BLOCKS_PER_SM) mg_down_kernel(
+__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 3 : 2) mg_down_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ zpre, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
-    constexpr int LS = MG_SW * MG_SH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sb = reinterpret_cast<T *>(smem_raw);
-    T *scx = sb + LS, *scy = scx + LS, *sz = scy + LS, *sinv = sz + LS;
+    T *xz = reinterpret_cast<T *>(smem_raw);
+    T *xrow = xz + 2 * 2 * 8 * MG_SW;
     const int s = blockIdx.y;
     if (!act[s]) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nc = n / 2, w = n + 1, wc = nc + 1;
     const long long V = (long long)w * w, Vc = (long long)wc * wc;
     const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
     const int I0 = tx * MG_CW, J0 = ty * MG_CH;
-    const int ox = 2 * I0 - 4, oy = 2 * J0 - 4;
-    const T *bs = b + s * V, *xs = cx + s * V, *ys = cy + s * V;
-    unsigned unk = 0;   // bit e: element e is an unknown of the grid
+    const int gi0 = 2 * I0 - 4 + 2 * lane, gj0 = 2 * J0 - 4 + 4 * warp;
+    TileBlock<T> t;
+    const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n);
+    tile_diag(t, xrow, lane, warp, unk);
+    // red from z = 0: z = b / diag at red elements ((c + r) even), 0 at black
 #pragma unroll
-    for (int e = 0; e < MG_NE; ++e) {
-        MG_ELEM(e, li, lj, l);
-        const int gi = ox + li, gj = oy + lj;
-        const bool in = gi >= 0 && gi <= n && gj >= 0 && gj <= n;
-        const int g = gj * w + gi;
-        sb[l] = in ? bs[g] : T(0);
-        scx[l] = in ? xs[g] : T(0);
-        scy[l] = in ? ys[g] : T(0);
-        if (in && gi >= 1 && gi <= n - 1) unk |= 1u << e;
-    }
-    __syncthreads();
-    // 1/diag; red from z = 0: z = b / diag
+    for (int r = 0; r < 4; ++r) {
 #pragma unroll
-    for (int e = 0; e < MG_NE; ++e) {
-        MG_ELEM(e, li, lj, l);
-        T inv = T(0), zv = T(0);
-        if (li >= 1 && lj >= 1 && ((unk >> e) & 1)) {
-            inv = recip(scx[l - 1] + scx[l] + scy[l - MG_SW] + scy[l]);
-            if (!(((ox + li) + (oy + lj)) & 1)) zv = sb[l] * inv;
+        for (int c = 0; c < 2; ++c) {
+            const int e = 2 * r + c;
+            t.z[e] = ((c + r) & 1) == 0 ? t.b[e] * t.inv[e] : T(0);
         }
-        sinv[l] = inv;
-        sz[l] = zv;
     }
+    tile_exchange(t, xz, 0, lane, warp);
+    tile_half_sweep<T, 1>(t);
+    tile_exchange(t, xz, 1, lane, warp);
+    // red residuals of rows 0..3 (c = r % 2)
+    const T r0 = tile_red_residual<T, 0>(t, unk), r1 = tile_red_residual<T, 1>(t, unk);
+    const T r2 = tile_red_residual<T, 2>(t, unk), r3 = tile_red_residual<T, 3>(t, unk);
+    // row 3's red residual (c = 1) to the warp above, for its row -1
+    xrow[warp * MG_SW + lane] = r3;
     __syncthreads();
-    // black on local [2, SW-2] x [2, SH-2]
-    tile_color_pass(sz, sb, scx, scy, sinv, ox, oy, n, 1, 2, MG_SW - 2, MG_SH - 2);
-    __syncthreads();
-    tile_red_residual(sz, sb, scx, scy, ox, oy, n);
-    __syncthreads();
-    // restriction to the tile's coarse vertices (red stencil points only)
+    const T rm = warp > 0 ? xrow[(warp - 1) * MG_SW + lane] : T(0);
+    const T l1 = __shfl_up_sync(MG_FULL, r1, 1), l3 = __shfl_up_sync(MG_FULL, r3, 1);
+    const T lm = __shfl_up_sync(MG_FULL, rm, 1);
+    // coarse vertices at (c = 0, r = 0) and (c = 0, r = 2): centre + 1/4 x the
+    // four diagonal (red) neighbours, in the order SW, SE, NW, NE
+    const int I = I0 - 2 + lane, Jb = J0 - 2 + 2 * warp;
+    const T acc[2] = {T(0.25) * (lm + rm + l1 + r1) + r0, T(0.25) * (l1 + r1 + l3 + r3) + r2};
     T *bcs = bc + s * Vc;
-    for (int c = threadIdx.x; c < MG_CW * MG_CH; c += MG_THREADS) {
-        const int ci = c % MG_CW, cj = c / MG_CW;
-        const int I = I0 + ci, J = J0 + cj;
-        if (I > nc || J > nc) continue;
-        T acc = T(0);
-        if (I > 0 && I < nc) {
-            const int l0 = (2 * cj + 4) * MG_SW + 2 * ci + 4;
-            acc = T(0.25) * (sb[l0 - MG_SW - 1] + sb[l0 - MG_SW + 1] + sb[l0 + MG_SW - 1] +
-                             sb[l0 + MG_SW + 1]) +
-                  sb[l0];
-        }
-        bcs[J * wc + I] = acc;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int J = Jb + k;
+        if (I - I0 >= 0 && I - I0 < MG_CW && J - J0 >= 0 && J - J0 < MG_CH && I <= nc && J <= nc)
+            bcs[(long long)J * wc + I] = (I > 0 && I < nc) ? acc[k] : T(0);
     }
-    // owned fine vertices: local [4, 4 + 2 CW) x [4, 4 + 2 CH)
+    // owned fine vertices: window [4, 4 + 2 CW) x [4, 4 + 2 CH)
     T *zs = zpre + s * V;
 #pragma unroll
-    for (int e = 0; e < MG_NE; ++e) {
-        MG_ELEM(e, li, lj, l);
-        if (li < 4 || li >= 4 + 2 * MG_CW || lj < 4 || lj >= 4 + 2 * MG_CH) continue;
-        const int gi = ox + li, gj = oy + lj;
-        if (gi > n || gj > n) continue;
-        zs[gj * w + gi] = sz[l];
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int li = 2 * lane + c, lj = 4 * warp + r;
+            const int gi = gi0 + c, gj = gj0 + r;
+            if (li >= 4 && li < 4 + 2 * MG_CW && lj >= 4 && lj < 4 + 2 * MG_CH && gi <= n && gj <= n)
+                zs[(long long)gj * w + gi] = t.z[2 * r + c];
+        }
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, MG_BLOCKS_PER_SM) mg_up_kernel(
+__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 3 : 2) mg_up_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     const T *__restrict__ zpre, T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x,
     const int *__restrict__ act, double *__restrict__ part_rz, int nblk) {
-    constexpr int LS = MG_SW * MG_SH;
-    constexpr int UW = 2 * MG_CW + 4, UH = 2 * MG_CH + 4;   // used window: 62 x 30
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T sred[32];
-    T *sb = reinterpret_cast<T *>(smem_raw);
-    T *scx = sb + LS, *scy = scx + LS, *sz = scy + LS, *sinv = sz + LS, *szc = sinv + LS;
+    T *xz = reinterpret_cast<T *>(smem_raw);
+    T *xrow = xz + 2 * 2 * 8 * MG_SW;
+    T *szc = xrow + 8 * MG_SW;   // coarse window, row stride MG_CCW, MG_CCH + 1 rows
     const int s = blockIdx.y;
     if (!act[s]) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nc = n / 2, w = n + 1, wc = nc + 1;
     const long long V = (long long)w * w, Vc = (long long)wc * wc;
     const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
     const int I0 = tx * MG_CW, J0 = ty * MG_CH;
-    const int ox = 2 * I0 - 2, oy = 2 * J0 - 2;
+    const int gi0 = 2 * I0 - 2 + 2 * lane, gj0 = 2 * J0 - 2 + 4 * warp;
     const int cox = I0 - 1, coy = J0 - 1;
-    const T *bs = b + s * V, *xs = cx + s * V, *ys = cy + s * V, *zcs = zc + s * Vc;
-    const T *zps = zpre + s * V;
-    T *zs = z + s * V;
-    for (int c = threadIdx.x; c < MG_CCW * MG_CCH; c += MG_THREADS) {
-        const int ci = c % MG_CCW, cj = c / MG_CCW;
+    const T *zcs = zc + s * Vc;
+    for (int q = threadIdx.x; q < (MG_CCH + 1) * MG_CCW + 1; q += MG_THREADS) {
+        const int ci = q % MG_CCW, cj = q / MG_CCW;
         const int I = cox + ci, J = coy + cj;
-        szc[c] = (I >= 0 && I <= nc && J >= 0 && J <= nc) ? zcs[J * wc + I] : T(0);
+        szc[q] = (cj < MG_CCH && I >= 0 && I <= nc && J >= 0 && J <= nc)
+                     ? zcs[(long long)J * wc + I] : T(0);
     }
-    unsigned unk = 0;
+    TileBlock<T> t;
+    const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n);
+    const T *zps = zpre + s * V;
 #pragma unroll
-    for (int e = 0; e < MG_NE; ++e) {
-        MG_ELEM(e, li, lj, l);
-        const int gi = ox + li, gj = oy + lj;
-        const bool in = li < UW && lj < UH && gi >= 0 && gi <= n && gj >= 0 && gj <= n;
-        const int g = gj * w + gi;
-        sb[l] = in ? bs[g] : T(0);
-        scx[l] = in ? xs[g] : T(0);
-        scy[l] = in ? ys[g] : T(0);
-        sz[l] = in ? zps[g] : T(0);
-        if (in && gi >= 1 && gi <= n - 1) unk |= 1u << e;
-    }
-    __syncthreads();
-    // 1/diag and z += P zc at every unknown of the used window
+    for (int r = 0; r < 4; ++r) {
 #pragma unroll
-    for (int e = 0; e < MG_NE; ++e) {
-        MG_ELEM(e, li, lj, l);
-        if (!((unk >> e) & 1)) {
-            sinv[l] = T(0);
-            continue;
+        for (int c = 0; c < 2; ++c) {
+            const int gi = gi0 + c, gj = gj0 + r;
+            t.z[2 * r + c] = (gi >= 0 && gi <= n && gj >= 0 && gj <= n)
+                                 ? zps[(long long)gj * w + gi] : T(0);
         }
-        sinv[l] = (li >= 1 && lj >= 1) ? recip(scx[l - 1] + scx[l] + scy[l - MG_SW] + scy[l]) : T(0);
-        const int gi = ox + li, gj = oy + lj;
-        const int c = ((gj >> 1) - coy) * MG_CCW + ((gi >> 1) - cox);
-        // bilinear weights: (1, 0) on even fine indices, (1/2, 1/2) on odd ones
-        const T wx1 = (gi & 1) ? T(0.5) : T(0), wy1 = (gj & 1) ? T(0.5) : T(0);
-        const T wx0 = T(1) - wx1, wy0 = T(1) - wy1;
-        sz[l] += wy0 * (wx0 * szc[c] + wx1 * szc[c + 1]) +
-                 wy1 * (wx0 * szc[c + MG_CCW] + wx1 * szc[c + MG_CCW + 1]);
     }
-    __syncthreads();
-    // black on local [1, UW-2] x [1, UH-2], then red on [2, UW-3] x [2, UH-3]
-    tile_color_pass(sz, sb, scx, scy, sinv, ox, oy, n, 1, 1, UW - 2, UH - 2);
-    __syncthreads();
-    tile_color_pass(sz, sb, scx, scy, sinv, ox, oy, n, 0, 2, UW - 3, UH - 3);
-    __syncthreads();
-    // owned fine vertices: local [2, 2 + 2 CW) x [2, 2 + 2 CH)
+    tile_diag(t, xrow, lane, warp, unk);   // its barrier also covers szc
+    // z += P zc: coarse column lane (and lane + 1), rows 2 warp + {0, 1, 2};
+    // weights (1, 0) at even fine indices, (1/2, 1/2) at odd ones
+    const T *q0 = szc + (2 * warp) * MG_CCW + lane;
+    const T a0 = q0[0], a1 = q0[1], b0 = q0[MG_CCW], b1 = q0[MG_CCW + 1];
+    const T c0 = q0[2 * MG_CCW], c1 = q0[2 * MG_CCW + 1];
+    const T h = T(0.5), qq = T(0.25);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (!((unk >> k) & 1)) continue;
+        const int r = k >> 1, c = k & 1;
+        T pv;
+        const T x0 = r < 2 ? a0 : b0, x1 = r < 2 ? a1 : b1;   // row J_lo
+        const T y0 = r < 2 ? b0 : c0, y1 = r < 2 ? b1 : c1;   // row J_lo + 1
+        if ((r & 1) == 0) pv = c == 0 ? x0 : h * (x0 + x1);
+        else pv = c == 0 ? h * (x0 + y0) : qq * ((x0 + x1) + (y0 + y1));
+        t.z[k] += pv;
+    }
+    tile_exchange(t, xz, 0, lane, warp);
+    tile_half_sweep<T, 1>(t);
+    tile_exchange(t, xz, 1, lane, warp);
+    tile_half_sweep<T, 0>(t);
+    // owned fine vertices: window [2, 2 + 2 CW) x [2, 2 + 2 CH)
+    T *zs = z + s * V;
     T rz = T(0);
 #pragma unroll
-    for (int e = 0; e < MG_NE; ++e) {
-        MG_ELEM(e, li, lj, l);
-        if (li < 2 || li >= 2 + 2 * MG_CW || lj < 2 || lj >= 2 + 2 * MG_CH) continue;
-        const int gi = ox + li, gj = oy + lj;
-        if (gi > n || gj > n) continue;
-        zs[gj * w + gi] = sz[l];
-        rz += sb[l] * sz[l];
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int li = 2 * lane + c, lj = 4 * warp + r;
+            const int gi = gi0 + c, gj = gj0 + r;
+            if (li >= 2 && li < 2 + 2 * MG_CW && lj >= 2 && lj < 2 + 2 * MG_CH && gi <= n && gj <= n) {
+                zs[(long long)gj * w + gi] = t.z[2 * r + c];
+                rz += t.b[2 * r + c] * t.z[2 * r + c];
+            }
+        }
     }
     if (part_rz) {
         const T tot = block_sum_t(rz, sred);
         if (threadIdx.x == 0) part_rz[(long long)s * nblk + blockIdx.x] = (double)tot;
     }
 }
-
-#undef MG_ELEM
 
 struct TailPtrs {
     void *cx[8], *cy[8];
