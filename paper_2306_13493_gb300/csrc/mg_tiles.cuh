@@ -198,7 +198,7 @@ __device__ __forceinline__ T tile_red_residual(const TileBlock<T> &t, unsigned u
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 3 : 2) mg_down_kernel(
+__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 4 : 2) mg_down_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ zpre, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 3 : 2) mg_down_ke
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 3 : 2) mg_up_kernel(
+__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 4 : 2) mg_up_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     const T *__restrict__ zpre, T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x,
     const int *__restrict__ act, double *__restrict__ part_rz, int nblk) {

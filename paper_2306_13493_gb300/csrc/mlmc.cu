@@ -10,8 +10,11 @@
 // (coarse-grid cycles, reductions, host checks) are filled by the others.
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
 #include <cstdlib>
 #include <future>
+#include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -135,6 +138,7 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
                                    p->precision, kf, coarse ? kc : nullptr, st);
         if (rc != CE_OK) { cleanup(); return rc; }
         int mi_c[2] = {0, 0}, nf_c = 0;
+        char coarse_err[512] = {0};
         std::future<int> fut;
         if (split) {
             if (cudaEventRecord(ev_field, st) != cudaSuccess) { cleanup(); return CE_ERR_CUDA; }
@@ -144,6 +148,7 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
                     return (int)CE_ERR_CUDA;
                 const int r = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, nullptr,
                                                    stc, mi_c, &nf_c, qmask_c);
+                if (r != CE_OK && r != CE_ERR_NOT_CONVERGED) snprintf(coarse_err, sizeof(coarse_err), "%s", sce_last_error());
                 if (cudaEventRecord(ev_coarse, stc) != cudaSuccess) return (int)CE_ERR_CUDA;
                 return r;
             });
@@ -152,6 +157,7 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
         rc = sce_darcy_solve_impl(&pf, kf, cn, qf_c, nullptr, nullptr, nullptr, st, mi, &nf,
                                   qmask_f);
         const int rc_c = split ? fut.get() : CE_OK;
+        if (split && rc_c != CE_OK && rc_c != CE_ERR_NOT_CONVERGED) sce_set_last_error_text(coarse_err);
         if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
         account(rc, mi, nf);
         if (split) {
@@ -279,18 +285,26 @@ extern "C" int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int q
     };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
     std::atomic<int> next{0};
+    // a failing task's error text (the workers' sce_last_error is thread-local)
+    std::mutex err_mu;
+    std::string err_text;
     auto worker = [&]() {
         if (cudaSetDevice(dev) != cudaSuccess) return;
         for (int k; (k = next.fetch_add(1)) < ntasks;) {
             const int i = order[k];
             cudaStream_t sf = ss[2 * (size_t)i], sc = ss[2 * (size_t)i + 1];
             tasks[i].status = level_run(args_of(i), p, seed, qoi_index, sf, sc ? sc : sf);
+            if (tasks[i].status != CE_OK && tasks[i].status != CE_ERR_NOT_CONVERGED) {
+                std::lock_guard<std::mutex> lk(err_mu);
+                if (err_text.empty()) err_text = sce_last_error();
+            }
         }
     };
     const int nthreads = std::min(max_concurrency, ntasks);
     std::vector<std::thread> pool;
     for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
     for (std::thread &t : pool) t.join();
+    if (!err_text.empty()) sce_set_last_error_text(err_text.c_str());
     for (cudaStream_t s : ss) {
         if (!s) continue;
         cudaEvent_t ev;

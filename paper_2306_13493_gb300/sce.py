@@ -148,7 +148,11 @@ _lib = None
 class SceError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
-        super().__init__(f"{what}: {status_string(status)} ({status})")
+        detail = ""
+        if status in (CE_ERR_CUDA, CE_ERR_OOM, CE_ERR_INVALID_ARG) and _lib is not None:
+            text = _lib.sce_last_error()
+            detail = f" [{text.decode(errors='replace')}]" if text else ""
+        super().__init__(f"{what}: {status_string(status)} ({status}){detail}")
 
 
 def load(path=None):
