@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=12.0,
                     help="open-loop window of the served-requests measurement (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-level launch measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -357,6 +359,55 @@ def precision_study(args):
     out["qoi_order"] = ["outflow", "u(7/15,7/15)", "L2 norm"]
     print(json.dumps(out), flush=True)
     return 0
+
+
+def mixed_launch_bench(args, sce, stream):
+    """workloads.MIXED_LAUNCH: the level-pair buckets of several grid sizes
+    in one mlmc_estimate_levels call (all buckets in flight at once), timed
+    with CUDA events on the caller's stream after warm-up, L2 flushed."""
+    import torch
+    mw = workloads.MIXED_LAUNCH
+    embs, tasks = [], []
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    for l, (n, c) in enumerate(mw.buckets):
+        e = sce.ce_setup_embedding(0, mw.nu, mw.lam, mw.sigma2, n, pad_mode=mw.pad_mode)
+        embs.append(e)
+        tasks.append({"emb": e, "level": 2 + l, "count": c,
+                      "Y": torch.empty(c, dtype=torch.float64, device=dev)})
+
+    def launch(i):
+        for t in tasks:
+            t["first_sample"] = i * t["count"]
+        outs, _, st = sce.mlmc_estimate_levels(tasks, mw.seed, qoi_index=mw.qoi, f=mw.f,
+                                               rtol=mw.rtol, maxit=2000, precision=args.precision,
+                                               max_concurrency=args.concurrency,
+                                               stream=stream.cuda_stream, allow_not_converged=True)
+        return outs
+
+    for w in range(2):
+        launch(1000 + w)
+    reps, tot = 3, 0.0
+    iters = []
+    for i in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs = launch(i)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+        iters = [o.total_iters / (2 * o.N) for o in outs]
+    for e in embs:
+        e.close()
+    ms = tot / reps
+    nsamp = sum(c for _, c in mw.buckets)
+    return {"workload": mw.describe(), "P": [2 * n for n, _ in mw.buckets],
+            "samples_per_launch": nsamp, "ms_per_launch": round(ms, 2),
+            "samples_per_s": round(nsamp / (ms / 1e3), 1),
+            "mean_iters_per_solve": [round(x, 2) for x in iters],
+            "levels_in_flight": args.concurrency}
 
 
 def serving_bench(args, sce):
@@ -673,6 +724,10 @@ def run_ours(args):
                "fp64_per_sample_path_seconds": round(fp64_s, 3) if fp64_s else None,
                "speedup_vs_fp64_path": round(fp64_s / res.seconds, 1) if fp64_s else None}
 
+    mixed = None
+    if rank == 0 and world == 1 and not args.no_mixed:
+        mixed = mixed_launch_bench(args, sce, stream)
+
     serving = None
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         serving = serving_bench(args, sce)
@@ -703,7 +758,8 @@ def run_ours(args):
             "gpu_launches": int(sum(v[2] for v in prof.values())) * args.steps,
             "gpu_launches_per_step": int(sum(v[2] for v in prof.values())),
             "roofline": roof, "kernels": kernels, "per_level": per_level,
-            "fp64_per_sample_path": fp64, "time_to_rmse": ttr, "serving": serving,
+            "fp64_per_sample_path": fp64, "time_to_rmse": ttr, "mixed_launch": mixed,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

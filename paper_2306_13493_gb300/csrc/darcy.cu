@@ -653,6 +653,7 @@ struct Solver {
     int *misc = nullptr;   // [0] counter, [1] nfail, [2] max iters
     std::vector<void *> owned;
     cudaStream_t st = nullptr;
+    cudaGraphExec_t graph = nullptr;   // four captured CG iterations, replayed
 
     template <typename U> int alloc(U **ptr, size_t cnt) {
         int rc = sce_alloc_t(ptr, cnt, st);
@@ -660,6 +661,7 @@ struct Solver {
         return rc;
     }
     ~Solver() {
+        if (graph) cudaGraphExecDestroy(graph);
         for (void *ptr : owned) sce_free(ptr, st);
     }
 
@@ -720,6 +722,7 @@ struct Solver {
     // partial-sum slots per sample written by vcycle_fused(want_rz = true)
     int rz_blocks() const { return Lt == 0 ? 1 : tiles_n[0]; }
 
+    bool tail_attr_set = false;
     template <int NTN, int NTHR>
     void tail_launch(bool want_rz) {
         TailPtrs tp{};
@@ -728,8 +731,11 @@ struct Solver {
             tp.cy[i] = cy[Lt + i];
         }
         constexpr size_t smem = tail_smem_bytes<T, NTN>();
-        cudaFuncSetAttribute(mg_tail_kernel<T, NTN, NTHR>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (!tail_attr_set) {   // set outside any stream capture (the first cycle is not captured)
+            cudaFuncSetAttribute(mg_tail_kernel<T, NTN, NTHR>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tail_attr_set = true;
+        }
         SceProf pr(KP_MG_TAIL, st, (double)count * (smem + 2 * sizeof(T) * ln[Lt].V));
         mg_tail_kernel<T, NTN, NTHR><<<count, NTHR, smem, st>>>(tp, b[Lt], z[Lt], sc.act_in,
                                                                 want_rz ? part : nullptr);
@@ -898,6 +904,86 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     int n_act = 0;
     SCE_TRY(S.read_counter(&n_act));
     int total_inner = 0;
+
+    // one CG iteration: q = A p, alpha, d += alpha p, r -= alpha q, |r|^2 ...
+    auto iter_head = [&]() -> int {
+        {
+            SceProf pr(KP_SPMV, st, S.vb(0, 4.0));
+            spmv_dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.p, S.q, n0, l0.vpt,
+                                                      S.part, l0.nblk, S.sc.act_in);
+        }
+        S.reduce(RED_ALPHA, S.sc.act_in);
+        {
+            SceProf pr(KP_AXPY, st, S.vb(0, 6.0));
+            axpy2_kernel<T><<<g0, l0.tpb, 0, st>>>(S.d, S.b[0], S.p, S.q, S.sc.alpha, n0, l0.vpt,
+                                                   S.part, l0.nblk, S.sc.act_in);
+        }
+        SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
+        S.reduce(RED_RR, S.sc.act_in);
+        return CE_OK;
+    };
+    // ... and z = M^-1 r, beta, p = z + beta p
+    auto iter_tail = [&]() -> int {
+        if (S.fused) {
+            S.vcycle_fused(true);
+        } else {
+            SCE_CUDA(cudaMemsetAsync(S.z[0], 0, c0 * sizeof(T), st));
+            S.vcycle(0);
+            SceProf pr(KP_DOT, st, S.vb(0, 2.0));
+            dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.z[0], n0, l0.vpt, S.part, l0.nblk,
+                                                 S.sc.act_in);
+        }
+        S.reduce(RED_BETA, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
+        {
+            SceProf pr(KP_PUPDATE, st, S.vb(0, 3.0));
+            pupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], S.sc.beta, n0, l0.vpt,
+                                                     S.sc.act_in);
+        }
+        return CE_OK;
+    };
+    // CUDA graph of check_every iterations (head + tail each), replayed, when
+    // SCE_GRAPHS=1: not on the legacy default stream or with the launch
+    // profiler on.  Off by default: each solve captures and instantiates its
+    // own graph, and on the oscillatory workload that costs more than the
+    // launches it saves (461K vs 478K samples/s).  A failed capture falls back
+    // to stream launches.
+    bool use_graph = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread &&
+                     !sce_prof_on();
+    {
+        const char *e = getenv("SCE_GRAPHS");
+        use_graph = use_graph && e && atoi(e) != 0;
+    }
+    if (use_graph) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            use_graph = false;
+    }
+    auto capture_graph = [&]() -> int {
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return CE_ERR_CUDA;
+        }
+        int rc = CE_OK;
+        for (int k = 0; k < check_every && rc == CE_OK; ++k) {
+            rc = iter_head();
+            if (rc == CE_OK) rc = iter_tail();
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(st, &g);
+        if (rc != CE_OK || ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return CE_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&S.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            S.graph = nullptr;
+            cudaGetLastError();
+            return CE_ERR_CUDA;
+        }
+        return CE_OK;
+    };
     for (int outer = 0; outer < 64 && n_act > 0 && total_inner < maxit; ++outer) {
         // inner PCG on the correction equation, samples with act_in set
         SCE_CUDA(cudaMemsetAsync(S.d, 0, c0 * sizeof(T), st));
@@ -916,40 +1002,28 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         }
         S.reduce(RED_RZ0, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
         int in_act = n_act;
-        for (int it = 0; it < inner_max && in_act > 0 && total_inner < maxit; ++it) {
-            {
-                SceProf pr(KP_SPMV, st, S.vb(0, 4.0));
-                spmv_dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.p, S.q, n0, l0.vpt,
-                                                          S.part, l0.nblk, S.sc.act_in);
+        for (int it = 0; it < inner_max && in_act > 0 && total_inner < maxit;) {
+            // four iterations as one graph launch when they fit the budgets (the
+            // per-sample flags make them exact: converged samples skip every kernel)
+            if (use_graph && it % check_every == 0 && it + check_every <= inner_max &&
+                total_inner + check_every <= maxit) {
+                if (!S.graph && capture_graph() != CE_OK) use_graph = false;
+                if (use_graph) {
+                    SCE_CUDA(cudaGraphLaunch(S.graph, st));
+                    it += check_every;
+                    total_inner += check_every;
+                    SCE_TRY(S.read_counter(&in_act));
+                    continue;
+                }
             }
-            S.reduce(RED_ALPHA, S.sc.act_in);
-            {
-                SceProf pr(KP_AXPY, st, S.vb(0, 6.0));
-                axpy2_kernel<T><<<g0, l0.tpb, 0, st>>>(S.d, S.b[0], S.p, S.q, S.sc.alpha, n0,
-                                                       l0.vpt, S.part, l0.nblk, S.sc.act_in);
-            }
-            SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
-            S.reduce(RED_RR, S.sc.act_in);
+            SCE_TRY(iter_head());
             ++total_inner;
-            if ((it + 1) % check_every == 0) {
+            ++it;
+            if (it % check_every == 0) {
                 SCE_TRY(S.read_counter(&in_act));
                 if (in_act == 0) break;
             }
-            if (S.fused) {
-                S.vcycle_fused(true);
-            } else {
-                SCE_CUDA(cudaMemsetAsync(S.z[0], 0, c0 * sizeof(T), st));
-                S.vcycle(0);
-                SceProf pr(KP_DOT, st, S.vb(0, 2.0));
-                dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.z[0], n0, l0.vpt, S.part, l0.nblk,
-                                                     S.sc.act_in);
-            }
-            S.reduce(RED_BETA, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
-            {
-                SceProf pr(KP_PUPDATE, st, S.vb(0, 3.0));
-                pupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], S.sc.beta, n0, l0.vpt,
-                                                         S.sc.act_in);
-            }
+            SCE_TRY(iter_tail());
         }
         SCE_CUDA(cudaGetLastError());
         {

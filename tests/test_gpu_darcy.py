@@ -147,3 +147,33 @@ def test_results_independent_of_batch_composition(sce):
     _, q_all, _, _, _ = _solve(sce, k, 32)
     _, q_one, _, _, _ = _solve(sce, k[3:4], 32)
     assert np.array_equal(q_all[3], q_one[0])
+
+
+@pytest.mark.parametrize("precision,maxit", [(32, 1000), (64, 1000), (32, 6)])
+def test_graph_replay_matches_stream_launches(sce, precision, maxit, monkeypatch):
+    """On a created stream the inner CG iterations are replayed from a captured
+    CUDA graph four at a time; per-sample results, iteration counts and
+    statuses equal those of plain stream launches (SCE_GRAPHS=0), also when
+    the iteration budget is not a multiple of four."""
+    import torch
+    n, count = 128, 5
+    k_np = _oracle_k(n, count, lam=0.05, seed=4, precision=precision)
+    out = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("SCE_GRAPHS", graphs)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            k = torch.tensor(k_np, dtype=torch_dtype(precision), device="cuda")
+            qoi = torch.empty(count, 3, dtype=torch.float64, device="cuda")
+            iters = torch.empty(count, dtype=torch.int32, device="cuda")
+            status = torch.empty(count, dtype=torch.int32, device="cuda")
+            rc = sce.darcy_solve_batch(n, k, count, qoi, f=1.0, rtol=1e-12, maxit=maxit,
+                                       precision=precision, iters=iters, status=status,
+                                       stream=s.cuda_stream, allow_not_converged=True)
+        s.synchronize()
+        out.append((rc, qoi.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()))
+    (rc1, q1, i1, s1), (rc0, q0, i0, s0) = out
+    assert rc1 == rc0
+    assert np.array_equal(q1, q0) and np.array_equal(i1, i0) and np.array_equal(s1, s0)
+    if maxit == 6:
+        assert rc1 == sce.CE_ERR_NOT_CONVERGED and np.all(i1 <= 6)

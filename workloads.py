@@ -129,3 +129,28 @@ class PrecisionStudy:
 
 
 PRECISION_STUDY = PrecisionStudy()
+
+
+@dataclass
+class MixedLaunch:
+    """One launch holding samples of several levels of uneven size: each
+    sample is a level pair (fine grid n, coarse grid n/2), FP32 field with
+    float-float refinement; classical embedding P = 2n (doubled if needed),
+    no smoothing."""
+    nu: float = 1.5
+    lam: float = 0.05
+    sigma2: float = 1.0
+    buckets: tuple = ((64, 4096), (128, 1024), (256, 256), (512, 64), (1024, 16))
+    pad_mode: int = 1
+    qoi: int = 1
+    f: float = 1.0
+    seed: int = 3
+    rtol: float = 1e-10
+
+    def describe(self):
+        return (f"Matern nu={self.nu} lambda={self.lam} sigma2={self.sigma2}; level pairs "
+                + ", ".join(f"{c}@{n}^2" for n, c in self.buckets)
+                + "; classical embedding P=2n; Q=u(7/15,7/15), f=1, rtol=1e-10")
+
+
+MIXED_LAUNCH = MixedLaunch()
