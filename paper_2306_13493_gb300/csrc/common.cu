@@ -92,6 +92,20 @@ struct TwKey {
     int dev, P;
     bool operator<(const TwKey &o) const { return dev != o.dev ? dev < o.dev : P < o.P; }
 };
+static std::mutex g_smem_mu;
+static std::map<std::pair<int, const void *>, size_t> g_smem_limit;
+
+int sce_raise_smem_limit(const void *func, size_t bytes) {
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    size_t &cur = g_smem_limit[{dev, func}];
+    if (bytes <= cur) return CE_OK;
+    SCE_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return CE_OK;
+}
+
 static std::mutex g_tw_mu;
 static std::map<TwKey, std::pair<double2 *, float2 *>> g_tw;
 

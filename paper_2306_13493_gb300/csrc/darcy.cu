@@ -732,8 +732,7 @@ struct Solver {
         }
         constexpr size_t smem = tail_smem_bytes<T, NTN>();
         if (!tail_attr_set) {   // set outside any stream capture (the first cycle is not captured)
-            cudaFuncSetAttribute(mg_tail_kernel<T, NTN, NTHR>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            sce_raise_smem_limit((const void *)mg_tail_kernel<T, NTN, NTHR>, smem);
             tail_attr_set = true;
         }
         SceProf pr(KP_MG_TAIL, st, (double)count * (smem + 2 * sizeof(T) * ln[Lt].V));
@@ -745,10 +744,8 @@ struct Solver {
     void vcycle_fused(bool want_rz) {
         constexpr size_t smem = mg_tile_smem_bytes<T>();
         if (!tile_attr_set) {
-            cudaFuncSetAttribute(mg_down_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-            cudaFuncSetAttribute(mg_up_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+            sce_raise_smem_limit((const void *)mg_down_kernel<T>, smem);
+            sce_raise_smem_limit((const void *)mg_up_kernel<T>, smem);
             tile_attr_set = true;
         }
         for (int L = 0; L < Lt; ++L) {

@@ -68,7 +68,7 @@ __device__ __forceinline__ float bsumf(float v, float *sh) {
 }
 
 template <int N, int NT>
-__global__ void __launch_bounds__(NT, N == 64 ? 2 : (N == 32 ? 3 : (N == 16 ? 6 : 1))) small_solve_kernel(
+__global__ void __launch_bounds__(NT, N == 64 ? 2 : (N == 32 ? 4 : (N == 16 ? 8 : 1))) small_solve_kernel(
     const float *__restrict__ kin, double f, double rtol2, double in_rel2, int maxit,
     double *__restrict__ qoi, int *__restrict__ iters_out, int *__restrict__ status_out,
     double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits, int qmask) {
@@ -253,8 +253,7 @@ template <int N, int NT>
 int launch_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
                  int *status, double *u_out, int *misc, int qmask, cudaStream_t st) {
     const size_t smem = SmallLayout<N>::bytes;
-    SCE_CUDA(cudaFuncSetAttribute(small_solve_kernel<N, NT>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SCE_TRY(sce_raise_smem_limit((const void *)small_solve_kernel<N, NT>, smem));
     const double in_rel = 1e-5;
     SceProf pr(KP_SMALL, st, (double)count * SmallLayout<N>::V * (sizeof(float) + 0.0) + 24.0 * count);
     small_solve_kernel<N, NT><<<count, NT, smem, st>>>(k, p->f, p->rtol * p->rtol, in_rel * in_rel,

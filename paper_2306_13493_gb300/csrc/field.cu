@@ -171,8 +171,7 @@ static int fft2_f64(double2 *d, int P, cudaStream_t st) {
     const int logP = ilog2(P);
     const int nthr = std::max(1, std::min(256, P / 4));
     const size_t smem = (size_t)fft_line_pitch(P) * sizeof(double2);
-    SCE_CUDA(cudaFuncSetAttribute(fft_lines_f64_kernel<8>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SCE_TRY(sce_raise_smem_limit((const void *)fft_lines_f64_kernel<8>, smem));
     // rows (contiguous), then columns (stride P)
     fft_lines_f64_kernel<8><<<P, nthr, smem, st>>>(d, logP, P, 1, tw);
     SCE_CUDA(cudaGetLastError());
@@ -561,8 +560,7 @@ static int launch_row(const ce_embedding_s *e, bool masked, const typename C2<R>
         sqc = (const R *)e->sq32_c;
     }
     const int units = masked ? e->P : e->P / 2;
-    SCE_CUDA(cudaFuncSetAttribute(ce_row_kernel<R, MAXB>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+    SCE_TRY(sce_raise_smem_limit((const void *)ce_row_kernel<R, MAXB>, c.smem));
     dim3 grid((units + c.F - 1) / c.F, count);
     const int m = e->n;
     SceProf pr(KP_ROW, st,
@@ -579,8 +577,7 @@ template <typename R, int MAXB>
 static int launch_col(const ce_embedding_s *e, const typename C2<R>::T *Y, int ncols, int coarse,
                       const typename C2<R>::T *tw, int count, R *kout, R *kc_plain,
                       const LineCfg &c, cudaStream_t st) {
-    SCE_CUDA(cudaFuncSetAttribute(ce_col_kernel<R, MAXB>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+    SCE_TRY(sce_raise_smem_limit((const void *)ce_col_kernel<R, MAXB>, c.smem));
     dim3 grid((ncols + c.F - 1) / c.F, count);
     const double rows_out = coarse ? (e->n / 2 + 1) : (e->n + 1);
     SceProf pr(KP_COL, st,

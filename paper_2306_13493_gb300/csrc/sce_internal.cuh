@@ -35,6 +35,12 @@ static inline int ilog2(long long v) {
     return r;
 }
 
+// Raises the dynamic shared-memory limit of kernel `func` on the current
+// device to at least `bytes`, never lowering it.  The limit is a process-wide
+// attribute of the kernel: calls on several host threads with different sizes
+// must not lower it between another thread's setting and its launch.
+int sce_raise_smem_limit(const void *func, size_t bytes);
+
 // Stream-ordered device allocation from the device's default pool.
 int sce_alloc(void **p, size_t bytes, cudaStream_t st);
 int sce_free(void *p, cudaStream_t st);

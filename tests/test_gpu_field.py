@@ -150,3 +150,48 @@ def test_fields_full_size_sampled(sce, precision):
     for c in range(2):
         okf, _ = ofield.sample_k(oe, full, None, 2, 5, 40 + c, precision)
         assert rel_err(kf[c], okf) < tol
+
+
+def test_concurrent_sampling_of_different_sizes():
+    """Host threads sampling fields of very different embedding sizes at the
+    same time (the situation of levels in flight together) all succeed and
+    give the fields a single thread gives: the FFT kernels' shared-memory
+    limit is only ever raised, so one thread cannot shrink it under another's
+    launch."""
+    import threading
+    import torch
+    from tests.gpu_common import lib
+    sce = lib()
+    sizes = [(16, 16), (64, 2), (256, 1)]
+    embs = [sce.ce_setup_embedding(ocv.MATERN, 0.5, 0.05, 1.0, n, pad_mode=oem.PAD_SMOOTH)
+            for n, _ in sizes]
+    ref = []
+    for e, (n, c) in zip(embs, sizes):
+        k = torch.empty(c, n + 1, n + 1, dtype=torch.float32, device="cuda")
+        sce.ce_sample_batch(e, 5, 0, 0, c, 32, k_fine=k)
+        torch.cuda.synchronize()
+        ref.append(k.clone())
+    errors, bad = [], []
+
+    def worker(i):
+        e, (n, c) = embs[i], sizes[i]
+        s = torch.cuda.Stream()
+        k = torch.empty(c, n + 1, n + 1, dtype=torch.float32, device="cuda")
+        try:
+            for _ in range(40):
+                sce.ce_sample_batch(e, 5, 0, 0, c, 32, k_fine=k, stream=s.cuda_stream)
+            s.synchronize()
+            if not torch.equal(k, ref[i]):
+                bad.append(i)
+        except Exception as exc:   # reported below
+            errors.append(repr(exc))
+
+    ts = [threading.Thread(target=worker, args=(i,)) for i in range(len(sizes))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for e in embs:
+        e.close()
+    assert not errors, errors
+    assert not bad
