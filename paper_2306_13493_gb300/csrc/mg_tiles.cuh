@@ -42,10 +42,16 @@
 namespace sce {
 
 constexpr int MG_SW = 64;                  // window width: 32 lanes x 2 columns
-constexpr int MG_SH = 32;                  // window height: 8 warps x 4 rows
+#ifndef SCE_MG_SH
+#define SCE_MG_SH 32
+#endif
+constexpr int MG_SH = SCE_MG_SH;           // window height: MG_SH / 4 warps x 4 rows
+constexpr int MG_NW = MG_SH / 4;           // warps per block
 constexpr int MG_CW = (MG_SW - 6) / 2;     // 29 coarse vertices per tile in x
 constexpr int MG_CH = (MG_SH - 6) / 2;     // 13 coarse vertices per tile in y
-constexpr int MG_THREADS = 256;
+constexpr int MG_THREADS = 32 * MG_NW;
+constexpr int MG_BLOCKS_PER_SM = 1024 / MG_THREADS;   // 64 registers per thread
+static_assert(MG_SH % 4 == 0 && MG_NW <= 32, "tile height");
 constexpr int MG_CCW = MG_CW + 3;          // coarse window of mg_up: 32 x 16 (+1 row)
 constexpr int MG_CCH = MG_CH + 3;
 constexpr unsigned MG_FULL = 0xffffffffu;
@@ -54,7 +60,7 @@ constexpr unsigned MG_FULL = 0xffffffffu;
 // warp for cy / residual exchange, the coarse window of mg_up with a spare row
 template <typename T>
 constexpr size_t mg_tile_smem_bytes() {
-    return sizeof(T) * (2 * 2 * 8 * (size_t)MG_SW + 8 * (size_t)MG_SW +
+    return sizeof(T) * (2 * 2 * MG_NW * (size_t)MG_SW + MG_NW * (size_t)MG_SW +
                         (size_t)(MG_CCH + 1) * MG_CCW + 1);
 }
 
@@ -139,7 +145,7 @@ __device__ __forceinline__ void tile_diag(TileBlock<T> &t, T *xrow, int lane, in
 template <typename T>
 __device__ __forceinline__ void tile_exchange(TileBlock<T> &t, T *xz, int buf, int lane,
                                               int warp) {
-    T *lo = xz + (buf * 2 + 0) * 8 * MG_SW, *hi = xz + (buf * 2 + 1) * 8 * MG_SW;
+    T *lo = xz + (buf * 2 + 0) * MG_NW * MG_SW, *hi = xz + (buf * 2 + 1) * MG_NW * MG_SW;
     lo[warp * MG_SW + 2 * lane] = t.z[0];
     lo[warp * MG_SW + 2 * lane + 1] = t.z[1];
     hi[warp * MG_SW + 2 * lane] = t.z[6];
@@ -148,7 +154,7 @@ __device__ __forceinline__ void tile_exchange(TileBlock<T> &t, T *xz, int buf, i
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         t.zs[c] = warp > 0 ? hi[(warp - 1) * MG_SW + 2 * lane + c] : T(0);
-        t.zn[c] = warp < 7 ? lo[(warp + 1) * MG_SW + 2 * lane + c] : T(0);
+        t.zn[c] = warp < MG_NW - 1 ? lo[(warp + 1) * MG_SW + 2 * lane + c] : T(0);
     }
 }
 
@@ -198,12 +204,12 @@ __device__ __forceinline__ T tile_red_residual(const TileBlock<T> &t, unsigned u
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 4 : 2) mg_down_kernel(
+__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM : MG_BLOCKS_PER_SM / 2) mg_down_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ zpre, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xz = reinterpret_cast<T *>(smem_raw);
-    T *xrow = xz + 2 * 2 * 8 * MG_SW;
+    T *xrow = xz + 2 * 2 * MG_NW * MG_SW;
     const int s = blockIdx.y;
     if (!act[s]) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -262,15 +268,15 @@ __global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 4 : 2) mg_down_ke
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? 4 : 2) mg_up_kernel(
+__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM : MG_BLOCKS_PER_SM / 2) mg_up_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     const T *__restrict__ zpre, T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x,
     const int *__restrict__ act, double *__restrict__ part_rz, int nblk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T sred[32];
     T *xz = reinterpret_cast<T *>(smem_raw);
-    T *xrow = xz + 2 * 2 * 8 * MG_SW;
-    T *szc = xrow + 8 * MG_SW;   // coarse window, row stride MG_CCW, MG_CCH + 1 rows
+    T *xrow = xz + 2 * 2 * MG_NW * MG_SW;
+    T *szc = xrow + MG_NW * MG_SW;   // coarse window, row stride MG_CCW, MG_CCH + 1 rows
     const int s = blockIdx.y;
     if (!act[s]) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
