@@ -43,7 +43,10 @@ using namespace sce;
 namespace {
 
 constexpr int MAXLEV = 14;
-constexpr int TAIL_N = 32;   // levels with n <= TAIL_N run in one block per sample
+#ifndef SCE_TAIL_N
+#define SCE_TAIL_N 32
+#endif
+constexpr int TAIL_N = SCE_TAIL_N;   // levels with n <= TAIL_N run in one block per sample
 
 struct Launch {
     int tpb, vpt, epb, nblk;
@@ -755,6 +758,7 @@ struct Solver {
         }
         const bool rz_tail = want_rz && Lt == 0;
         switch (n[Lt]) {
+            case 64: tail_launch<64, 512>(rz_tail); break;
             case 32: tail_launch<32, 256>(rz_tail); break;
             case 16: tail_launch<16, 128>(rz_tail); break;
             case 8: tail_launch<8, 64>(rz_tail); break;
