@@ -219,30 +219,7 @@ __global__ void coarsest_kernel(const T *__restrict__ cx, const T *__restrict__ 
                                 const int *__restrict__ act) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= count || !act[s]) return;
-    const T *ax = cx + s * 9, *ay = cy + s * 9, *bs = b + s * 9;
-    T *zs = z + s * 9;
-    double d[3], o[2], r[3];
-    for (int j = 0; j < 3; ++j) {
-        const int v = j * 3 + 1;
-        d[j] = (double)ax[v - 1] + (double)ax[v] + (j > 0 ? (double)ay[v - 3] : 0.0) +
-               (j < 2 ? (double)ay[v] : 0.0);
-        r[j] = (double)bs[v];
-    }
-    o[0] = -(double)ay[1];
-    o[1] = -(double)ay[4];
-    // Thomas algorithm
-    double c0 = o[0] / d[0];
-    double r0 = r[0] / d[0];
-    double den1 = d[1] - o[0] * c0;
-    double c1 = o[1] / den1;
-    double r1 = (r[1] - o[0] * r0) / den1;
-    double den2 = d[2] - o[1] * c1;
-    double x2 = (r[2] - o[1] * r1) / den2;
-    double x1 = r1 - c1 * x2;
-    double x0 = r0 - c0 * x1;
-    zs[1] = (T)x0;
-    zs[4] = (T)x1;
-    zs[7] = (T)x2;
+    coarsest_solve(cx + s * 9, cy + s * 9, b + s * 9, z + s * 9);
 }
 
 // ---------------------------------------------------------------- Krylov pieces

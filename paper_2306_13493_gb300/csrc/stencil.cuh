@@ -177,26 +177,28 @@ __device__ __forceinline__ T prolong_at(const T *c, int nc, int i, int j) {
 // Exact solve on the 2-cell grid (unknowns (1, j), j = 0..2; tridiagonal in j).
 template <typename T>
 __device__ __forceinline__ void coarsest_solve(const T *ax, const T *ay, const T *b, T *z) {
-    double d[3], r[3];
+    // Thomas algorithm in the working precision (one thread; FP64 division
+    // runs at a small fraction of the FP32 rate on GB300 and this sits on the
+    // critical path of every cycle)
+    T d[3], r[3];
     for (int j = 0; j < 3; ++j) {
         const int v = j * 3 + 1;
-        d[j] = (double)ax[v - 1] + (double)ax[v] + (j > 0 ? (double)ay[v - 3] : 0.0) +
-               (j < 2 ? (double)ay[v] : 0.0);
-        r[j] = (double)b[v];
+        d[j] = ax[v - 1] + ax[v] + (j > 0 ? ay[v - 3] : T(0)) + (j < 2 ? ay[v] : T(0));
+        r[j] = b[v];
     }
-    const double o0 = -(double)ay[1], o1 = -(double)ay[4];
-    const double c0 = o0 / d[0];
-    const double r0 = r[0] / d[0];
-    const double den1 = d[1] - o0 * c0;
-    const double c1 = o1 / den1;
-    const double r1 = (r[1] - o0 * r0) / den1;
-    const double den2 = d[2] - o1 * c1;
-    const double x2 = (r[2] - o1 * r1) / den2;
-    const double x1 = r1 - c1 * x2;
-    const double x0 = r0 - c0 * x1;
-    z[1] = (T)x0;
-    z[4] = (T)x1;
-    z[7] = (T)x2;
+    const T o0 = -ay[1], o1 = -ay[4];
+    const T c0 = o0 / d[0];
+    const T r0 = r[0] / d[0];
+    const T den1 = d[1] - o0 * c0;
+    const T c1 = o1 / den1;
+    const T r1 = (r[1] - o0 * r0) / den1;
+    const T den2 = d[2] - o1 * c1;
+    const T x2 = (r[2] - o1 * r1) / den2;
+    const T x1 = r1 - c1 * x2;
+    const T x0 = r0 - c0 * x1;
+    z[1] = x0;
+    z[4] = x1;
+    z[7] = x2;
 }
 
 }  // namespace sce
