@@ -56,8 +56,11 @@ struct Launch {
 static Launch launch_for(int n) {
     Launch L;
     L.V = (long long)(n + 1) * (n + 1);
+#ifndef SCE_EPB
+#define SCE_EPB 2048
+#endif
     long long e = 1;
-    while (e < L.V && e < 1024) e <<= 1;
+    while (e < L.V && e < SCE_EPB) e <<= 1;
     L.epb = (int)e;
     L.tpb = std::min(256, L.epb);
     L.vpt = L.epb / L.tpb;
