@@ -68,7 +68,7 @@ __device__ __forceinline__ float bsumf(float v, float *sh) {
 }
 
 template <int N, int NT>
-__global__ void __launch_bounds__(NT, N == 64 ? 2 : (N == 32 ? 4 : (N == 16 ? 8 : 1))) small_solve_kernel(
+__global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kernel(
     const float *__restrict__ kin, double f, double rtol2, double in_rel2, int maxit,
     double *__restrict__ qoi, int *__restrict__ iters_out, int *__restrict__ status_out,
     double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits, int qmask) {
@@ -283,7 +283,10 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
     switch (p->n) {
         case 4: SCE_SMALL(4, 32); break;
         case 8: SCE_SMALL(8, 64); break;
-        case 16: SCE_SMALL(16, 128); break;
+#ifndef SCE_SMALL_NT16
+#define SCE_SMALL_NT16 64
+#endif
+        case 16: SCE_SMALL(16, SCE_SMALL_NT16); break;
         case 32: SCE_SMALL(32, 256); break;
         case 64: SCE_SMALL(64, 512); break;
         default: break;
