@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--concurrency", type=int, default=8,
                     help="levels in flight at once (each on its own streams); 1 = one after another")
-    ap.add_argument("--study", default=None, choices=[None, "precision"],
+    ap.add_argument("--study", default=None, choices=[None, "precision", "smoothing"],
                     help="run a study instead of the benchmark (prints its own JSON line)")
     ap.add_argument("--study-count", type=int, default=None)
     ap.add_argument("--study-oracle", type=int, default=None)
@@ -288,6 +288,79 @@ def _ps_task(task):
     Qf, _ = omlmc.level_qois(e, full, None, ps.seed, 0, [sample], f=ps.f, precision=prec,
                              coarse=False)
     return nu, sample, prec, Qf[0]
+
+
+def smoothing_study(args):
+    """workloads.SMOOTHING_STUDY: per covariance and grid, the level-0 QoI
+    with the full and with the smoothed spectrum (same normals), the sup-norm
+    of the field difference and the Theorem 1 bound shape
+    s^(-1/2) (Lambda^ord_(s-tau+1))^(1/2) tau (p = 1)."""
+    import numpy as np
+    import torch
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    sce.load()
+    ss = workloads.SMOOTHING_STUDY
+    dev = torch.device("cuda", 0)
+    out = {"study": "smoothing", "sigma2": ss.sigma2, "qoi": "L2 norm", "f": ss.f, "tau": "sqrt(s)",
+           "cases": []}
+    for kind, nu, lam in ss.covs:
+        pad = sce.CE_PAD_NONE if kind == sce.CE_COV_SEP_EXP else sce.CE_PAD_SMOOTH
+        rows = []
+        for n, N in zip(ss.ns, ss.samples):
+            ep = sce.ce_setup_embedding(kind, nu, lam, ss.sigma2, n, pad_mode=pad,
+                                        J=0 if pad == sce.CE_PAD_NONE else -1)
+            es = sce.ce_setup_embedding(kind, nu, lam, ss.sigma2, n, pad_mode=pad,
+                                        J=0 if pad == sce.CE_PAD_NONE else -1,
+                                        keep_fine=sce.CE_KEEP_TAU_SQRT_S,
+                                        keep_coarse=sce.CE_KEEP_TAU_SQRT_S)
+            P, s_ = ep.P, ep.info.s
+            tau = s_ - es.info.keep_eff_fine
+            lam_all = torch.empty(s_, dtype=torch.float64)
+            sce.ce_get_eigenvalues(ep, lam_all)
+            lam_ord = np.sort(lam_all.numpy())[::-1]
+            lam_cut = float(lam_ord[s_ - tau]) if tau > 0 else 0.0   # Lambda^ord_(s-tau+1)
+            q = {}
+            zdiff = []
+            for tag, e in (("full", ep), ("smooth", es)):
+                qf = torch.empty(N, 3, dtype=torch.float64, device=dev)
+                sce.mlmc_level_estimate(e, ss.seed, 0, 0, N, qoi_index=ss.qoi, f=ss.f, rtol=1e-10,
+                                        maxit=4000, precision=64, qoi_f=qf,
+                                        allow_not_converged=True)
+                q[tag] = qf[:, ss.qoi].cpu().numpy()
+            # sup-norm of Z - Z~ on the grid (FP64 fields, chunks of 64 samples)
+            for c0 in range(0, N, 64):
+                c = min(64, N - c0)
+                ka = torch.empty(c, n + 1, n + 1, dtype=torch.float64, device=dev)
+                kb = torch.empty_like(ka)
+                sce.ce_sample_batch(ep, ss.seed, 0, c0, c, 64, k_fine=ka)
+                sce.ce_sample_batch(es, ss.seed, 0, c0, c, 64, k_fine=kb)
+                zdiff.append((ka.log() - kb.log()).abs().amax(dim=(1, 2)).cpu().numpy())
+            zdiff = np.concatenate(zdiff)
+            d = q["full"] - q["smooth"]
+            bound = s_ ** -0.5 * lam_cut ** 0.5 * tau
+            rows.append({"n": n, "P": P, "s": s_, "tau": int(tau), "N": N,
+                         "lambda_ord_s_minus_tau_plus_1": lam_cut,
+                         "mean_abs_dQ": float(abs(d.mean())), "mean_dQ_std_error":
+                             float(d.std(ddof=1) / np.sqrt(N)),
+                         "var_dQ": float(d.var(ddof=1)),
+                         "E_sup_dZ": float(zdiff.mean()), "thm1_bound_shape": bound,
+                         "ratio_E_sup_dZ_to_bound": float(zdiff.mean() / bound) if bound > 0 else None})
+            ep.close()
+            es.close()
+        hs = np.log2([1.0 / r["n"] for r in rows])
+        def rate(key):
+            y = np.log2(np.maximum([r[key] for r in rows], 1e-300))
+            return float(np.polyfit(hs, y, 1)[0])
+        out["cases"].append({"kind": "sep_exp" if kind == sce.CE_COV_SEP_EXP else "matern",
+                             "nu": nu, "lambda": lam,
+                             "padding": "none (P = 2n)" if pad == sce.CE_PAD_NONE else
+                             "smooth periodisation",
+                             "rate_mean_abs_dQ_in_h": rate("mean_abs_dQ"),
+                             "rate_var_dQ_in_h": rate("var_dQ"),
+                             "rate_E_sup_dZ_in_h": rate("E_sup_dZ"), "rows": rows})
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def precision_study(args):
@@ -798,6 +871,8 @@ def main():
         return run_case(args)
     if args.study == "precision":
         return precision_study(args)
+    if args.study == "smoothing":
+        return smoothing_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

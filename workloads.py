@@ -154,3 +154,21 @@ class MixedLaunch:
 
 
 MIXED_LAUNCH = MixedLaunch()
+
+
+@dataclass
+class SmoothingStudy:
+    """Smoothing error on one grid (§4.1): Q_h with the full spectrum against
+    Q~_h with tau = sqrt(s) eigenvalues dropped, from the same normals, for
+    the separable exponential covariance (no padding needed, Lemma 3) and
+    Matern nu = 1.5 (smooth periodisation); QoI ||u||_L2, f = 1."""
+    covs: tuple = ((1, 0.0, 0.3), (1, 0.0, 0.1), (0, 1.5, 0.1), (0, 1.5, 0.03))   # (kind, nu, lam)
+    sigma2: float = 1.0
+    ns: tuple = (16, 32, 64, 128, 256)
+    samples: tuple = (1024, 1024, 512, 256, 128)
+    seed: int = 7
+    f: float = 1.0
+    qoi: int = 2
+
+
+SMOOTHING_STUDY = SmoothingStudy()
