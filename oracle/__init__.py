@@ -18,6 +18,7 @@ Modules
   embedding   first column, eigenvalues (naive DFT), PSD check and padding,
               smoothing masks (Algorithm 2 step 4(b))
   field       Algorithm 1 step 4(a)-(f): xi -> w -> v = F w -> u -> Z -> k
+  qmc         randomly shifted rank-1 lattice normals (the MLQMC sampler)
   darcy       P1 finite elements with nodal quadrature, direct solve, QoIs
   mlmc        level differences, level sums, MLMC estimator and N_l rule
 

@@ -47,8 +47,13 @@ def sample_k(emb, mask_f, mask_c, seed, level, sample, precision=64, naive=None)
     precision selects the normal spec (FP64 or FP32 words); all arithmetic
     after the normals is FP64.
     """
+    xi = rng.normals(seed, level, sample, emb.P * emb.P, precision).astype(np.float64)
+    return k_from_normals(emb, mask_f, mask_c, xi, naive)
+
+
+def k_from_normals(emb, mask_f, mask_c, xi, naive=None):
+    """Steps 4(b)-(f) for given normals xi (length P*P, index k1 + P k2)."""
     P, m = emb.P, emb.m
-    xi = rng.normals(seed, level, sample, P * P, precision).astype(np.float64)
     Lf = em.masked_eigenvalues(emb.Lam, mask_f)
     Zf = hartley_field(Lf, xi, m, naive)
     kf = np.exp(Zf)
