@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--concurrency", type=int, default=8,
                     help="levels in flight at once (each on its own streams); 1 = one after another")
-    ap.add_argument("--study", default=None, choices=[None, "precision", "smoothing"],
+    ap.add_argument("--study", default=None, choices=[None, "precision", "smoothing", "qmc"],
                     help="run a study instead of the benchmark (prints its own JSON line)")
     ap.add_argument("--study-count", type=int, default=None)
     ap.add_argument("--study-oracle", type=int, default=None)
@@ -359,6 +359,62 @@ def smoothing_study(args):
                              "rate_mean_abs_dQ_in_h": rate("mean_abs_dQ"),
                              "rate_var_dQ_in_h": rate("var_dQ"),
                              "rate_E_sup_dZ_in_h": rate("E_sup_dZ"), "rows": rows})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def qmc_study(args):
+    """workloads.QMC_STUDY: standard error of each level mean with the lattice
+    sampler (R shifts x N points; error from the spread of the shift means)
+    against Philox Monte Carlo with the same R N samples."""
+    import numpy as np
+    import torch
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    sce.load()
+    qs = workloads.QMC_STUDY
+    dev = torch.device("cuda", 0)
+    L = qs.levels - 1
+    out = {"study": "qmc", "nu": qs.nu, "lambda": qs.lam, "sigma2": qs.sigma2, "N": qs.N,
+           "R": qs.R, "a": qs.a, "qoi": ["outflow", "u(7/15,7/15)", "L2 norm"][qs.qoi],
+           "levels": []}
+    for l in range(qs.levels):
+        n = qs.n0 << l
+        e0 = sce.ce_setup_embedding(0, qs.nu, qs.lam, qs.sigma2, n, pad_mode=sce.CE_PAD_SMOOTH)
+        kf, kc = workloads.keep_counts(e0.P, l == L, True)
+        e0.close()
+        emb = sce.ce_setup_embedding(0, qs.nu, qs.lam, qs.sigma2, n, pad_mode=sce.CE_PAD_SMOOTH,
+                                     keep_fine=kf, keep_coarse=kc)
+        lat = sce.QmcLattice(emb, qs.N, qs.a)
+        Y = torch.empty(qs.N * qs.R, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sce.mlmc_level_estimate(emb, qs.seed, l, 0, qs.N * qs.R, qoi_index=qs.qoi, f=qs.f,
+                                rtol=1e-10, maxit=2000, precision=32, Y=Y,
+                                allow_not_converged=True)
+        torch.cuda.synchronize()
+        t_mc = time.perf_counter() - t0
+        y_mc = Y.cpu().numpy()
+        means = []
+        t0 = time.perf_counter()
+        for r in range(qs.R):
+            Yq = torch.empty(qs.N, dtype=torch.float64, device=dev)
+            o, _ = sce.mlmc_level_estimate_qmc(lat, qs.seed, l, r, 0, qs.N, qoi_index=qs.qoi,
+                                               f=qs.f, rtol=1e-10, maxit=2000, precision=32, Y=Yq,
+                                               allow_not_converged=True)
+            means.append(o.sumY / o.N)
+        torch.cuda.synchronize()
+        t_qmc = time.perf_counter() - t0
+        means = np.array(means)
+        se_mc = float(y_mc.std(ddof=1) / np.sqrt(y_mc.size))
+        se_qmc = float(means.std(ddof=1) / np.sqrt(qs.R))
+        out["levels"].append({"level": l, "n": n, "P": emb.P,
+                              "mean_mc": float(y_mc.mean()), "mean_qmc": float(means.mean()),
+                              "std_error_mc": se_mc, "std_error_qmc": se_qmc,
+                              "variance_reduction": (se_mc / se_qmc) ** 2 if se_qmc > 0 else None,
+                              "seconds_mc": round(t_mc, 4), "seconds_qmc": round(t_qmc, 4)})
+        lat.close()
+        emb.close()
     print(json.dumps(out), flush=True)
     return 0
 
@@ -873,6 +929,8 @@ def main():
         return precision_study(args)
     if args.study == "smoothing":
         return smoothing_study(args)
+    if args.study == "qmc":
+        return qmc_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -326,6 +326,43 @@ int sce_server_stats(sce_server_t s, sce_server_stats_t *out);
 /* Finishes every queued request, stops the workers, releases the cache. */
 void sce_server_destroy(sce_server_t s);
 
+/*
+ * Quasi-Monte Carlo sampler (multilevel quasi-Monte Carlo, the outlook of
+ * §5): the normals of Algorithm 1 step 4(a) replaced by a randomly shifted
+ * rank-1 lattice rule with N points (a power of two, <= 2^31):
+ *     y_j = frac((i z_r(j) mod N) / N + Delta_j),    xi_j = Phi^-1(y_j),
+ * i = lattice point, r(j) = rank of frequency j = k1 + P k2 in increasing
+ * wavenumber d(k1)^2 + d(k2)^2, d(k) = min(k, P-k), ties by j (low
+ * frequencies carry the large eigenvalues of a decreasing spectral density;
+ * an exact integer order, independent of eigenvalue rounding), z_r = a^r
+ * mod N (Korobov vector, a odd), and Delta_j the uniform
+ * shift (word + 0.5) 2^-32 of Philox4x32-10 with key (seed lo, seed hi) and
+ * counter (j/4, shift, level, 0xFFFFFFFF), word j mod 4.  Each shift gives
+ * an unbiased estimate; independent shifts estimate the error.  y is formed
+ * exactly in FP64; Phi^-1 is evaluated on the smaller tail (symmetric).
+ */
+typedef struct ce_qmc_s *ce_qmc_t;
+
+/* Builds the lattice table of handle e (P*P uint32 on the device; the handle
+ * must outlive it).  Synchronises.  Errors: CE_ERR_INVALID_ARG (N not a power
+ * of two or > 2^31, a even), CE_ERR_OOM, CE_ERR_CUDA. */
+int ce_qmc_setup(ce_embedding_t e, uint32_t N, uint32_t a, ce_qmc_t *out);
+void ce_qmc_destroy(ce_qmc_t q);
+
+/* ce_sample_batch with the lattice normals of points first_point ..
+ * first_point+count-1 (<= N) of shift `shift` on MLMC level `level`. */
+int ce_sample_batch_qmc(ce_qmc_t q, uint64_t seed, uint32_t level, uint32_t shift,
+                        uint32_t first_point, int count, int precision, void *k_fine,
+                        void *k_coarse, void *stream);
+
+/* mlmc_level_estimate with the lattice normals (same arguments and results;
+ * the samples are lattice points first_point .. first_point+count-1 of one
+ * shift). */
+int mlmc_level_estimate_qmc(ce_qmc_t q, const darcy_problem *p, uint64_t seed, uint32_t level,
+                            uint32_t shift, uint32_t first_point, int count, int qoi_index,
+                            mlmc_level_sums *out, double *Y, double *qoi_f, double *qoi_c,
+                            void *stream);
+
 /* Eq. (3.6): N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)),
  * l = 0..L.  V, C, N: host arrays of length L+1 (C > 0, V >= 0). */
 int mlmc_optimal_samples(int L_plus_1, const double *V, const double *C, double eps, long long *N);

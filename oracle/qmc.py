@@ -5,8 +5,11 @@ estimator of §3.4 into multilevel quasi-Monte Carlo (the paper's outlook, §5).
     y_j = frac( (i z_r(j) mod N) / N + Delta_j ),     xi_j = Phi^{-1}(y_j)
 
 for lattice point i = 0..N-1 (N a power of two), where r(j) is the rank of
-eigenvalue j in decreasing order (the most important directions of the
-spectral representation get the first lattice dimensions), z_r = a^r mod N is
+grid frequency j = k1 + P k2 in increasing wavenumber d(k1)^2 + d(k2)^2,
+d(k) = min(k, P - k), ties by j: the low frequencies, where a decreasing
+spectral density puts the large eigenvalues, get the first lattice
+dimensions (an exact integer order, so that it cannot depend on the rounding
+of the computed eigenvalues, which are equal in symmetric groups), z_r = a^r mod N is
 the Korobov generating vector of an odd parameter a, and Delta is a uniform
 random shift drawn from the same Philox4x32-10 generator as the Monte Carlo
 normals (key = seed, counter = (j/4, shift index, level, 0xFFFFFFFF), word
@@ -34,9 +37,13 @@ def korobov(a, N, s):
     return z
 
 
-def ranks(Lam):
-    """rank[j] = position of eigenvalue j in decreasing order (ties by index)."""
-    order = np.argsort(-Lam.reshape(-1), kind="stable")
+def ranks(P):
+    """rank[j], j = k1 + P k2: position of frequency j in increasing
+    d(k1)^2 + d(k2)^2 (ties by j)."""
+    k = np.arange(P)
+    d = np.minimum(k, P - k)
+    key = (d[None, :] ** 2 + d[:, None] ** 2).reshape(-1)     # [k2][k1] -> j
+    order = np.argsort(key, kind="stable")
     rk = np.empty(order.size, dtype=np.int64)
     rk[order] = np.arange(order.size)
     return rk
@@ -63,7 +70,7 @@ def inv_normal(y):
 
 def lattice_normals(Lam, N, a, seed, level, shift, i):
     s = Lam.size
-    zr = korobov(a, N, s)[ranks(Lam)]
+    zr = korobov(a, N, s)[ranks(Lam.shape[0])]
     return inv_normal(lattice_uniforms(zr, N, i, shifts(seed, level, shift, s)))
 
 

@@ -387,11 +387,36 @@ extern "C" int ce_normals(uint64_t seed, uint32_t level, uint64_t first_sample, 
 // Block = F lines x tpf threads.  Plain mode (sq_c == nullptr): line u packs
 // rows 2u and 2u+1 as real and imaginary parts.  Masked mode: line u = row u
 // with the fine-masked w as real part and the coarse-masked w as imaginary part.
-template <typename R, int MAXB>
+// Four normals of grid indices 4q .. 4q+3 (q = g + P/4 k2): Philox (Monte
+// Carlo) or the shifted lattice of point `sample` (QMC, qa.zr != nullptr).
+template <typename R, bool QMC>
+__device__ __forceinline__ void row_normals4(uint64_t seed, uint32_t level, uint64_t sample,
+                                             uint32_t q, const QmcArgs &qa, R xi[4]) {
+    if constexpr (!QMC) {
+        Normals<R>::gen4(philox_block(seed, level, sample, q), xi);
+    } else {
+        const uint4 w = philox_block(seed, SCE_QMC_SHIFT_LEVEL, qa.shift_sample, q);
+        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+        const double invN = 1.0 / (double)qa.N;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint64_t zi = (sample * (uint64_t)qa.zr[4 * (size_t)q + r]) & (uint64_t)(qa.N - 1);
+            double y = (double)zi * invN + ((double)ww[r] + 0.5) * 0x1p-32;
+            y -= floor(y);
+            if constexpr (sizeof(R) == 8) {
+                xi[r] = y < 0.5 ? normcdfinv(y) : -normcdfinv(1.0 - y);
+            } else {
+                xi[r] = y < 0.5 ? normcdfinvf((float)y) : -normcdfinvf((float)(1.0 - y));
+            }
+        }
+    }
+}
+
+template <typename R, int MAXB, bool QMC = false>
 __global__ void __launch_bounds__(256) ce_row_kernel(
     const R *__restrict__ sq_f, const R *__restrict__ sq_c, const typename C2<R>::T *__restrict__ tw,
     int P, int logP, int m, uint64_t seed, uint32_t level, uint64_t first_sample, int F, int tpf,
-    typename C2<R>::T *__restrict__ Yf, typename C2<R>::T *__restrict__ Yc) {
+    typename C2<R>::T *__restrict__ Yf, typename C2<R>::T *__restrict__ Yc, QmcArgs qa) {
     using R2 = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R2 *sm = reinterpret_cast<R2 *>(smem_raw);
@@ -412,7 +437,7 @@ __global__ void __launch_bounds__(256) ce_row_kernel(
             const R *rc = sq_c + (size_t)k2 * P;
             for (int g = t; g < P4; g += tpf) {
                 R xi[4];
-                Normals<R>::gen4(philox_block(seed, level, sample, (uint32_t)(g + P4 * k2)), xi);
+                row_normals4<R, QMC>(seed, level, sample, (uint32_t)(g + P4 * k2), qa, xi);
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int k1 = 4 * g + r;
@@ -425,8 +450,8 @@ __global__ void __launch_bounds__(256) ce_row_kernel(
             const R *rb = sq_f + (size_t)kb * P;
             for (int g = t; g < P4; g += tpf) {
                 R xa[4], xb[4];
-                Normals<R>::gen4(philox_block(seed, level, sample, (uint32_t)(g + P4 * ka)), xa);
-                Normals<R>::gen4(philox_block(seed, level, sample, (uint32_t)(g + P4 * kb)), xb);
+                row_normals4<R, QMC>(seed, level, sample, (uint32_t)(g + P4 * ka), qa, xa);
+                row_normals4<R, QMC>(seed, level, sample, (uint32_t)(g + P4 * kb), qa, xb);
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int k1 = 4 * g + r;
@@ -550,7 +575,7 @@ template <typename R, int MAXB>
 static int launch_row(const ce_embedding_s *e, bool masked, const typename C2<R>::T *tw,
                       uint64_t seed, uint32_t level, uint64_t first, int count,
                       typename C2<R>::T *Yf, typename C2<R>::T *Yc, const LineCfg &c,
-                      cudaStream_t st) {
+                      cudaStream_t st, const QmcArgs *qa = nullptr) {
     const R *sqf, *sqc;
     if constexpr (sizeof(R) == 8) {
         sqf = (const R *)e->sq64_f;
@@ -560,15 +585,23 @@ static int launch_row(const ce_embedding_s *e, bool masked, const typename C2<R>
         sqc = (const R *)e->sq32_c;
     }
     const int units = masked ? e->P : e->P / 2;
-    SCE_TRY(sce_raise_smem_limit((const void *)ce_row_kernel<R, MAXB>, c.smem));
+    SCE_TRY(sce_raise_smem_limit(qa ? (const void *)ce_row_kernel<R, MAXB, true>
+                                    : (const void *)ce_row_kernel<R, MAXB, false>,
+                                 c.smem));
     dim3 grid((units + c.F - 1) / c.F, count);
     const int m = e->n;
     SceProf pr(KP_ROW, st,
                (double)e->s * sizeof(R) * (masked ? 2 : 1) +
                    (double)count * (m + 1) * e->P * 2 * sizeof(R) * (masked ? 1.5 : 1.0));
-    ce_row_kernel<R, MAXB><<<grid, c.F * c.tpf, c.smem, st>>>(
-        sqf, masked ? sqc : nullptr, tw, e->P, ilog2(e->P), e->n, seed, level, first, c.F, c.tpf,
-        Yf, Yc);
+    const QmcArgs q = qa ? *qa : QmcArgs{nullptr, 1u, 0};
+    if (qa)
+        ce_row_kernel<R, MAXB, true><<<grid, c.F * c.tpf, c.smem, st>>>(
+            sqf, masked ? sqc : nullptr, tw, e->P, ilog2(e->P), e->n, seed, level, first, c.F,
+            c.tpf, Yf, Yc, q);
+    else
+        ce_row_kernel<R, MAXB, false><<<grid, c.F * c.tpf, c.smem, st>>>(
+            sqf, masked ? sqc : nullptr, tw, e->P, ilog2(e->P), e->n, seed, level, first, c.F,
+            c.tpf, Yf, Yc, q);
     SCE_CUDA(cudaGetLastError());
     return CE_OK;
 }
@@ -592,7 +625,7 @@ static int launch_col(const ce_embedding_s *e, const typename C2<R>::T *Y, int n
 
 template <typename R>
 static int sample_batch_t(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first,
-                          int count, R *kf, R *kc, cudaStream_t st) {
+                          int count, R *kf, R *kc, cudaStream_t st, const QmcArgs *qa) {
     using R2 = typename C2<R>::T;
     int status = CE_OK;
     const R2 *tw;
@@ -621,9 +654,9 @@ static int sample_batch_t(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
         R *kf_c = kf ? kf + (size_t)c0 * (m + 1) * (m + 1) : kf_tmp;
         R *kc_c = kc ? kc + (size_t)c0 * (mc + 1) * (mc + 1) : nullptr;
         if (rc.maxb == 4)
-            rcode = launch_row<R, 4>(e, masked, tw, seed, level, first + c0, cn, Yf, Yc, rc, st);
+            rcode = launch_row<R, 4>(e, masked, tw, seed, level, first + c0, cn, Yf, Yc, rc, st, qa);
         else
-            rcode = launch_row<R, 8>(e, masked, tw, seed, level, first + c0, cn, Yf, Yc, rc, st);
+            rcode = launch_row<R, 8>(e, masked, tw, seed, level, first + c0, cn, Yf, Yc, rc, st, qa);
         if (rcode != CE_OK) break;
         if (need_fine) {
             R *kcp = masked ? nullptr : kc_c;
@@ -647,7 +680,8 @@ static int sample_batch_t(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
 }
 
 int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,
-                          int count, int precision, void *k_fine, void *k_coarse, cudaStream_t st) {
+                          int count, int precision, void *k_fine, void *k_coarse, cudaStream_t st,
+                          const QmcArgs *qa) {
     if (!e || count < 0 || (precision != 32 && precision != 64)) return CE_ERR_INVALID_ARG;
     if (count == 0 || (!k_fine && !k_coarse)) return CE_OK;
     int dev = 0;
@@ -655,9 +689,9 @@ int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
     if (dev != e->device) return CE_ERR_INVALID_ARG;
     if (precision == 64)
         return sample_batch_t<double>(e, seed, level, first_sample, count, (double *)k_fine,
-                                      (double *)k_coarse, st);
+                                      (double *)k_coarse, st, qa);
     return sample_batch_t<float>(e, seed, level, first_sample, count, (float *)k_fine,
-                                 (float *)k_coarse, st);
+                                 (float *)k_coarse, st, qa);
 }
 
 extern "C" int ce_sample_batch(ce_embedding_t e, uint64_t seed, uint32_t level,
@@ -770,4 +804,68 @@ extern "C" int ce_sample_batch_noalloc(ce_embedding_t e, uint64_t seed, uint32_t
                                              (unsigned char *)scratch, st);
     return sample_batch_static_t<float>(e, seed, level, first_sample, count, (float *)k_fine,
                                         (float *)k_coarse, (unsigned char *)scratch, st);
+}
+
+// ------------------------------------------------------------------ quasi-Monte Carlo sampler
+extern "C" int ce_qmc_setup(ce_embedding_t e, uint32_t N, uint32_t a, ce_qmc_t *out) {
+    if (!e || !out || N == 0 || (N & (N - 1)) != 0 || N > (1u << 31) || (a & 1u) == 0)
+        return CE_ERR_INVALID_ARG;
+    *out = nullptr;
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    if (dev != e->device) return CE_ERR_INVALID_ARG;
+    const size_t s = (size_t)e->s;
+    const int P = e->P;
+    // lattice dimensions by increasing wavenumber d(k1)^2 + d(k2)^2, d(k) =
+    // min(k, P - k), ties by grid index j = k1 + P k2 (an exact integer order)
+    std::vector<uint32_t> order(s);
+    std::vector<uint64_t> key(s);
+    for (size_t j = 0; j < s; ++j) {
+        const uint64_t k1 = j % P, k2 = j / P;
+        const uint64_t d1 = std::min<uint64_t>(k1, P - k1), d2 = std::min<uint64_t>(k2, P - k2);
+        key[j] = d1 * d1 + d2 * d2;
+        order[j] = (uint32_t)j;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return key[x] < key[y]; });
+    // Korobov vector z_r = a^r mod N, placed at the grid index of rank r
+    std::vector<uint32_t> zr(s);
+    uint64_t z = 1 % N;
+    for (size_t r = 0; r < s; ++r) {
+        zr[order[r]] = (uint32_t)z;
+        z = (z * a) % N;
+    }
+    ce_qmc_s *q = new (std::nothrow) ce_qmc_s{e, N, a, nullptr, dev};
+    if (!q) return CE_ERR_OOM;
+    if (cudaMalloc(&q->zr, s * sizeof(uint32_t)) != cudaSuccess) {
+        delete q;
+        return CE_ERR_OOM;
+    }
+    if (cudaMemcpy(q->zr, zr.data(), s * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(q->zr);
+        delete q;
+        return CE_ERR_CUDA;
+    }
+    *out = q;
+    return CE_OK;
+}
+
+extern "C" void ce_qmc_destroy(ce_qmc_t q) {
+    if (!q) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(q->device);
+    cudaDeviceSynchronize();
+    cudaFree(q->zr);
+    cudaSetDevice(cur);
+    delete q;
+}
+
+extern "C" int ce_sample_batch_qmc(ce_qmc_t q, uint64_t seed, uint32_t level, uint32_t shift,
+                                   uint32_t first_point, int count, int precision, void *k_fine,
+                                   void *k_coarse, void *stream) {
+    if (!q || count < 0 || (uint64_t)first_point + (uint64_t)count > q->N) return CE_ERR_INVALID_ARG;
+    const QmcArgs qa{q->zr, q->N, ((uint64_t)level << 32) | shift};
+    return sce_sample_batch_impl(q->e, seed, level, first_point, count, precision, k_fine,
+                                 k_coarse, as_stream(stream), &qa);
 }

@@ -62,6 +62,7 @@ struct LevelArgs {
     int count;
     double *Y, *qoi_f, *qoi_c;
     mlmc_level_sums *out;
+    const QmcArgs *qa = nullptr;   // lattice sampler (nullptr: Philox)
 };
 
 // One level on stream st; the coarse solves go to stream stc (a second host
@@ -135,7 +136,7 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
         double *qc_c = coarse ? (a.qoi_c ? a.qoi_c + 3 * (size_t)c0 : qc) : nullptr;
         double *Y_c = a.Y ? a.Y + c0 : Yd;
         rc = sce_sample_batch_impl(e, seed, a.level, a.first_sample + (uint64_t)c0, cn,
-                                   p->precision, kf, coarse ? kc : nullptr, st);
+                                   p->precision, kf, coarse ? kc : nullptr, st, a.qa);
         if (rc != CE_OK) { cleanup(); return rc; }
         int mi_c[2] = {0, 0}, nf_c = 0;
         char coarse_err[512] = {0};
@@ -316,4 +317,18 @@ extern "C" int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int q
     }
     release();
     return combine();
+}
+
+extern "C" int mlmc_level_estimate_qmc(ce_qmc_t q, const darcy_problem *p, uint64_t seed,
+                                       uint32_t level, uint32_t shift, uint32_t first_point,
+                                       int count, int qoi_index, mlmc_level_sums *out, double *Y,
+                                       double *qoi_f, double *qoi_c, void *stream) {
+    if (!q || !out || count < 0 || !valid_problem(p, qoi_index) || p->n != q->e->n ||
+        (uint64_t)first_point + (uint64_t)count > q->N)
+        return CE_ERR_INVALID_ARG;
+    const QmcArgs qa{q->zr, q->N, ((uint64_t)level << 32) | shift};
+    LevelArgs a{q->e, level, first_point, count, Y, qoi_f, qoi_c, out};
+    a.qa = &qa;
+    const cudaStream_t st = as_stream(stream);
+    return level_run(a, p, seed, qoi_index, st, st);
 }

@@ -94,8 +94,27 @@ struct SceProf {
 };
 
 // Field path entry used by mlmc_level_estimate (same as ce_sample_batch).
+// Lattice normals of the quasi-Monte Carlo sampler (ce_qmc_setup): for point i
+// and grid index j, y = frac((i zr[j] mod N)/N + Delta_j), xi = Phi^-1(y), with
+// Delta_j from Philox (counter (j/4, shift_sample, SCE_QMC_SHIFT_LEVEL)).
+constexpr uint32_t SCE_QMC_SHIFT_LEVEL = 0xFFFFFFFFu;
+struct QmcArgs {
+    const uint32_t *zr;      // device, P*P: a^rank(j) mod N
+    uint32_t N;              // points, a power of two
+    uint64_t shift_sample;   // (level << 32) | shift
+};
+struct ce_qmc_s {
+    ce_embedding_t e;
+    uint32_t N, a;
+    uint32_t *zr;
+    int device;
+};
+
+// qa == nullptr: Philox normals (the Monte Carlo sampler); otherwise lattice
+// point first_sample + c of the shift in qa.
 int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,
-                          int count, int precision, void *k_fine, void *k_coarse, cudaStream_t st);
+                          int count, int precision, void *k_fine, void *k_coarse, cudaStream_t st,
+                          const QmcArgs *qa = nullptr);
 
 // One-block-per-sample solver for small grids (mixed precision).
 int sce_small_max_n();

@@ -128,6 +128,15 @@ _SIGS = {
                                        ctypes.POINTER(sce_result)]),
     "sce_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(sce_server_stats_t)]),
     "sce_server_destroy": (None, [_P]),
+    "ce_qmc_setup": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_P)]),
+    "ce_qmc_destroy": (None, [_P]),
+    "ce_sample_batch_qmc": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_uint32, ctypes.c_int, ctypes.c_int, _P, _P,
+                                           _P]),
+    "mlmc_level_estimate_qmc": (ctypes.c_int, [_P, ctypes.POINTER(darcy_problem),
+                                               ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                               ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(mlmc_level_sums), _P, _P, _P, _P]),
     "mlmc_estimate_levels": (ctypes.c_int, [ctypes.POINTER(darcy_problem), ctypes.c_uint64,
                                             ctypes.c_int, ctypes.POINTER(mlmc_level_task),
                                             ctypes.c_int, ctypes.c_int, _P]),
@@ -384,6 +393,49 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+class QmcLattice:
+    """Lattice table of the quasi-Monte Carlo sampler (ce_qmc_setup) for an
+    Embedding: N points (a power of two), Korobov parameter a (odd)."""
+
+    def __init__(self, emb, N, a):
+        h = _P()
+        _check(load().ce_qmc_setup(emb.handle, N, a, ctypes.byref(h)), "ce_qmc_setup")
+        self.handle, self.emb, self.N, self.a = h, emb, N, a
+
+    def close(self):
+        if self.handle:
+            load().ce_qmc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ce_sample_batch_qmc(q, seed, level, shift, first_point, count, precision, k_fine=None,
+                        k_coarse=None, stream=None):
+    t = k_fine if k_fine is not None else k_coarse
+    _check(load().ce_sample_batch_qmc(q.handle, seed, level, shift, first_point, count, precision,
+                                      _ptr(k_fine), _ptr(k_coarse), _stream(stream, t)),
+           "ce_sample_batch_qmc")
+
+
+def mlmc_level_estimate_qmc(q, seed, level, shift, first_point, count, qoi_index=QOI_OUTFLOW,
+                            f=0.0, rtol=1e-10, maxit=1000, precision=32, Y=None, qoi_f=None,
+                            qoi_c=None, stream=None, allow_not_converged=False):
+    prob = darcy_problem(q.emb.n, f, rtol, maxit, precision)
+    out = mlmc_level_sums()
+    allow = (CE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    st = _check(load().mlmc_level_estimate_qmc(q.handle, ctypes.byref(prob), seed, level, shift,
+                                               first_point, count, qoi_index, ctypes.byref(out),
+                                               _ptr(Y), _ptr(qoi_f), _ptr(qoi_c),
+                                               _stream(stream, Y)),
+                "mlmc_level_estimate_qmc", allow)
+    return out, st
 
 
 def sce_profile_enable(on):

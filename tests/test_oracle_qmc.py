@@ -19,11 +19,18 @@ def test_korobov_vector_and_one_dimensional_projections():
         assert np.array_equal(pts, i)
 
 
-def test_ranks_order_the_eigenvalues():
-    lam = np.array([0.5, 3.0, 3.0, 1.0, 0.0, 2.0])
-    rk = qmc.ranks(lam)
-    assert list(rk) == [4, 0, 1, 3, 5, 2]      # ties in index order
-    assert sorted(rk) == list(range(6))
+def test_ranks_order_the_frequencies():
+    P = 8
+    rk = qmc.ranks(P)
+    assert sorted(rk) == list(range(P * P))
+    assert rk[0] == 0                               # k = (0, 0) first
+    # next: the four wavenumber-1 frequencies (1,0), (7,0), (0,1), (0,7) in index order
+    first = sorted(range(P * P), key=lambda j: rk[j])[1:5]
+    assert first == [1, 7, 8, 56]
+    # a decreasing isotropic spectral density: eigenvalues fall along the order
+    e = oem.setup_embedding(ocv.MATERN, 1.5, 0.2, 1.0, 8, oem.PAD_DOUBLING)
+    lam = e.Lam.reshape(-1)[np.argsort(qmc.ranks(e.P))]
+    assert stats.spearmanr(np.arange(lam.size), lam).correlation < -0.9
 
 
 def test_shifts_are_the_philox_stream_of_their_own_counter():

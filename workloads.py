@@ -172,3 +172,23 @@ class SmoothingStudy:
 
 
 SMOOTHING_STUDY = SmoothingStudy()
+
+
+@dataclass
+class QmcStudy:
+    """MLQMC against MLMC at equal sample counts: per level, R random shifts
+    of an N-point Korobov lattice against R N Philox samples."""
+    nu: float = 1.5
+    lam: float = 0.1
+    sigma2: float = 1.0
+    n0: int = 16
+    levels: int = 4
+    N: int = 256
+    R: int = 16
+    a: int = 1597
+    qoi: int = 2
+    f: float = 1.0
+    seed: int = 8
+
+
+QMC_STUDY = QmcStudy()
