@@ -843,7 +843,7 @@ def run_ours(args):
     # the statistical error meets eps/sqrt(2); the bias of the level-L hierarchy is
     # estimated as in §4 (Richardson, alpha fitted on the three finest levels)
     ttr = None
-    if rank == 0 and not args.no_fp64_path:
+    if rank == 0 and world == 1 and not args.no_fp64_path:
         from paper_2306_13493_gb300 import mlmc as gm
         eps = 1e-3
         ttr = {"eps": eps, "target": "statistical error <= eps/sqrt(2) (the variance share "
