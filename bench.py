@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=12.0,
                     help="open-loop window of the served-requests measurement (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default FFT launch shapes (no tuning before the timed steps)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-level launch measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -680,6 +682,16 @@ def run_ours(args):
         e0.close()
         embs.append(sce.ce_setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n,
                                            pad_mode=wl.pad_mode, keep_fine=kf, keep_coarse=kc))
+    # FFT launch shapes per embedding size, tuned before anything is timed
+    autotune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        shapes = {}
+        for (l, n, N) in wl.levels:
+            shapes[str(embs[l].P)] = sce.ce_autotune_fft(embs[l], prec, count=min(N, 64), reps=3)
+        autotune = {"fft_shapes_by_P": {P: {"row_tpf_F": v["row"], "col_tpf_F": v["col"]}
+                                        for P, v in shapes.items()},
+                    "seconds": round(time.perf_counter() - t0, 2)}
     Ybuf = [torch.empty(N, dtype=torch.float64, device=dev) for (_, _, N) in wl.levels]
     Yhost = [torch.empty(N, dtype=torch.float64, pin_memory=True) for (_, _, N) in wl.levels]
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
@@ -910,6 +922,7 @@ def run_ours(args):
             "gpu_launches": int(sum(v[2] for v in prof.values())) * args.steps,
             "gpu_launches_per_step": int(sum(v[2] for v in prof.values())),
             "roofline": roof, "kernels": kernels, "per_level": per_level,
+            "autotune": autotune,
             "fp64_per_sample_path": fp64, "time_to_rmse": ttr, "mixed_launch": mixed,
             "serving": serving,
             "cpu_baseline": cpu,

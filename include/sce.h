@@ -363,6 +363,21 @@ int mlmc_level_estimate_qmc(ce_qmc_t q, const darcy_problem *p, uint64_t seed, u
                             mlmc_level_sums *out, double *Y, double *qoi_f, double *qoi_c,
                             void *stream);
 
+/*
+ * ce_autotune_fft -- picks the launch shapes (threads per FFT line, lines per
+ * thread block) of the row and column passes of ce_sample_batch for handle
+ * e's embedding size and `precision` by timing `reps` calls of `count`
+ * samples for every admissible shape (CUDA events on `stream`), first for
+ * the row pass, then for the column pass.  The choice holds for every later
+ * call of the process with the same P and precision.  Every shape computes
+ * each butterfly identically: tuning changes the time, never the fields.
+ * Not a step of the paper's method.  Outputs (may be NULL): the chosen
+ * shapes.  Synchronises `stream`.  Errors: CE_ERR_INVALID_ARG, CE_ERR_OOM,
+ * CE_ERR_CUDA.
+ */
+int ce_autotune_fft(ce_embedding_t e, int precision, int count, int reps, void *stream,
+                    int *row_tpf, int *row_F, int *col_tpf, int *col_F);
+
 /* Eq. (3.6): N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)),
  * l = 0..L.  V, C, N: host arrays of length L+1 (C > 0, V >= 0). */
 int mlmc_optimal_samples(int L_plus_1, const double *V, const double *C, double eps, long long *N);

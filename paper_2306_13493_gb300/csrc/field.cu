@@ -17,7 +17,9 @@
 //                (1/sqrt(s) = 1/P), k = exp(u) written x-fastest; the plain
 //                coarse field is the fine field at even vertices.
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -571,6 +573,37 @@ static LineCfg line_cfg(int P, int units) {
     return c;
 }
 
+// FFT launch shapes chosen by ce_autotune_fft: threads per line and lines
+// per block of the row pass (plain / masked) and of the column pass, per
+// (P, precision).  Absent entries use line_cfg's rule.  Every shape computes
+// each butterfly the same way, so a shape changes the time, never the result.
+enum { TUNE_ROW_PLAIN = 0, TUNE_ROW_MASKED = 1, TUNE_COL = 2 };
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;   // -> (tpf, F)
+
+template <typename R>
+static bool shape_cfg(int P, int tpf, int F, LineCfg *c) {
+    const int bpt = (P / 4 + tpf - 1) / tpf;
+    if (tpf < 1 || tpf > 256 || F < 1 || F * tpf > 256 || bpt > 8) return false;
+    c->tpf = tpf;
+    c->maxb = bpt <= 4 ? 4 : 8;
+    c->F = F;
+    c->smem = (size_t)F * fft_line_pitch(P) * sizeof(typename C2<R>::T);
+    return c->smem <= 160 * 1024;
+}
+
+template <typename R>
+static LineCfg line_cfg_tuned(int P, int units, int pass) {
+    LineCfg c = line_cfg<R>(P, units);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find({P, (int)sizeof(R), pass});
+    if (it != g_tune.end()) {
+        LineCfg t;
+        if (shape_cfg<R>(P, it->second.first, it->second.second, &t)) c = t;
+    }
+    return c;
+}
+
 template <typename R, int MAXB>
 static int launch_row(const ce_embedding_s *e, bool masked, const typename C2<R>::T *tw,
                       uint64_t seed, uint32_t level, uint64_t first, int count,
@@ -645,9 +678,10 @@ static int sample_batch_t(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
     SCE_TRY(sce_alloc_t(&Yf, (size_t)chunk * (m + 1) * P, st));
     if (masked) SCE_TRY(sce_alloc_t(&Yc, (size_t)chunk * (mc + 1) * P, st));
     if (need_fine && kf == nullptr) SCE_TRY(sce_alloc_t(&kf_tmp, (size_t)chunk * (m + 1) * (m + 1), st));
-    const LineCfg rc = line_cfg<R>(P, masked ? P : P / 2);
-    const LineCfg cc = line_cfg<R>(P, m + 1);
-    const LineCfg ccc = line_cfg<R>(P, mc + 1);
+    const LineCfg rc = line_cfg_tuned<R>(P, masked ? P : P / 2,
+                                         masked ? TUNE_ROW_MASKED : TUNE_ROW_PLAIN);
+    const LineCfg cc = line_cfg_tuned<R>(P, m + 1, TUNE_COL);
+    const LineCfg ccc = line_cfg_tuned<R>(P, mc + 1, TUNE_COL);
     int rcode = CE_OK;
     for (int c0 = 0; c0 < count && rcode == CE_OK; c0 += chunk) {
         const int cn = std::min(chunk, count - c0);
@@ -868,4 +902,90 @@ extern "C" int ce_sample_batch_qmc(ce_qmc_t q, uint64_t seed, uint32_t level, ui
     const QmcArgs qa{q->zr, q->N, ((uint64_t)level << 32) | shift};
     return sce_sample_batch_impl(q->e, seed, level, first_point, count, precision, k_fine,
                                  k_coarse, as_stream(stream), &qa);
+}
+
+// ------------------------------------------------------------------ FFT autotuner
+// Times ce_sample_batch of `count` samples of handle e for every admissible
+// shape of the row pass (with the column pass at its current shape), keeps
+// the fastest, then does the same for the column pass.
+extern "C" int ce_autotune_fft(ce_embedding_t e, int precision, int count, int reps,
+                               void *stream, int *row_tpf, int *row_F, int *col_tpf, int *col_F) {
+    if (!e || count < 1 || reps < 1 || (precision != 32 && precision != 64))
+        return CE_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    const int P = e->P, m = e->n, mc = m / 2;
+    const size_t es = precision == 64 ? sizeof(double) : sizeof(float);
+    const bool masked = e->coarse_distinct;
+    void *kf = nullptr, *kc = nullptr;
+    SCE_TRY(sce_alloc(&kf, (size_t)count * (m + 1) * (m + 1) * es, st));
+    if (sce_alloc(&kc, (size_t)count * (mc + 1) * (mc + 1) * es, st) != CE_OK) {
+        sce_free(kf, st);
+        return CE_ERR_OOM;
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int row_pass = masked ? TUNE_ROW_MASKED : TUNE_ROW_PLAIN;
+    int rc = CE_OK;
+    auto time_it = [&](float *ms) {
+        for (int w = 0; w < 2 && rc == CE_OK; ++w)   // warm-up (also loads the kernels)
+            rc = sce_sample_batch_impl(e, 1, 0, 0, count, precision, kf, kc, st);
+        if (rc != CE_OK) return;
+        cudaEventRecord(a, st);
+        for (int r = 0; r < reps && rc == CE_OK; ++r)
+            rc = sce_sample_batch_impl(e, 1, 0, 0, count, precision, kf, kc, st);
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) rc = CE_ERR_CUDA;
+        cudaEventElapsedTime(ms, a, b);
+    };
+    for (int pass : {row_pass, (int)TUNE_COL}) {
+        const std::tuple<int, int, int> key{P, (int)es, pass};
+        float best = 1e30f;
+        std::pair<int, int> best_shape{0, 0};
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) best_shape = it->second;
+        }
+        for (int div : {32, 16, 8, 4}) {
+            const int tpf = std::max(1, P / div);
+            for (int fdiv : {1, 2, 4}) {
+                const int F = std::max(1, 256 / tpf / fdiv);
+                LineCfg c;
+                const bool ok = es == 8 ? shape_cfg<double>(P, tpf, F, &c)
+                                        : shape_cfg<float>(P, tpf, F, &c);
+                if (!ok) continue;
+                {
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    g_tune[key] = {tpf, F};
+                }
+                float ms = 0.f;
+                time_it(&ms);
+                if (rc != CE_OK) break;
+                if (ms < best) {
+                    best = ms;
+                    best_shape = {tpf, F};
+                }
+            }
+            if (rc != CE_OK) break;
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (best_shape.first > 0) g_tune[key] = best_shape;
+        else g_tune.erase(key);
+        if (rc != CE_OK) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    sce_free(kf, st);
+    sce_free(kc, st);
+    if (rc != CE_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto get = [&](int pass, int *tpf, int *F) {
+        auto it = g_tune.find({P, (int)es, pass});
+        if (tpf) *tpf = it != g_tune.end() ? it->second.first : 0;
+        if (F) *F = it != g_tune.end() ? it->second.second : 0;
+    };
+    get(row_pass, row_tpf, row_F);
+    get(TUNE_COL, col_tpf, col_F);
+    return CE_OK;
 }

@@ -128,6 +128,10 @@ _SIGS = {
                                        ctypes.POINTER(sce_result)]),
     "sce_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(sce_server_stats_t)]),
     "sce_server_destroy": (None, [_P]),
+    "ce_autotune_fft": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]),
     "ce_qmc_setup": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_P)]),
     "ce_qmc_destroy": (None, [_P]),
     "ce_sample_batch_qmc": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
@@ -393,6 +397,14 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def ce_autotune_fft(emb, precision=32, count=32, reps=3, stream=None):
+    """Tunes the FFT launch shapes for emb's P; returns {"row": (tpf, F), "col": (tpf, F)}."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().ce_autotune_fft(emb.handle, precision, count, reps, _stream(stream),
+                                  *[ctypes.byref(x) for x in v]), "ce_autotune_fft")
+    return {"row": (v[0].value, v[1].value), "col": (v[2].value, v[3].value)}
 
 
 class QmcLattice:

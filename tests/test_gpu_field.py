@@ -195,3 +195,30 @@ def test_concurrent_sampling_of_different_sizes():
         e.close()
     assert not errors, errors
     assert not bad
+
+
+def test_fft_autotune_changes_time_not_fields():
+    """ce_autotune_fft picks launch shapes for the row and column passes; the
+    fields sampled before and after are bit-identical (plain and masked)."""
+    import torch
+    from tests.gpu_common import lib
+    sce = lib()
+    for n, kf, kc in ((32, -1, -1), (64, None, None)):
+        emb = sce.ce_setup_embedding(ocv.MATERN, 0.5, 0.05, 1.0, n, pad_mode=oem.PAD_SMOOTH)
+        if kf is None:   # distinct coarse mask: the masked row pass
+            s, P = emb.info.s, emb.P
+            emb.close()
+            emb = sce.ce_setup_embedding(ocv.MATERN, 0.5, 0.05, 1.0, n, pad_mode=oem.PAD_SMOOTH,
+                                         keep_fine=s - P, keep_coarse=s // 4)
+        out = []
+        for tune in (False, True):
+            if tune:
+                shapes = sce.ce_autotune_fft(emb, 32, count=8, reps=2)
+                assert shapes["row"][0] >= 1 and shapes["col"][0] >= 1
+            k = torch.empty(6, n + 1, n + 1, dtype=torch.float32, device="cuda")
+            kc_t = torch.empty(6, n // 2 + 1, n // 2 + 1, dtype=torch.float32, device="cuda")
+            sce.ce_sample_batch(emb, 3, 1, 10, 6, 32, k_fine=k, k_coarse=kc_t)
+            torch.cuda.synchronize()
+            out.append((k.clone(), kc_t.clone()))
+        assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+        emb.close()
