@@ -68,6 +68,14 @@ static Launch launch_for(int n) {
     return L;
 }
 
+// FOR_VERT with a compile-time count VPT (> 0; unrolled, so the loads of all
+// elements are in flight together) or the run-time count vpt (VPT == 0)
+#define FOR_VERT_C(V, VPT, vpt)                                                        \
+    _Pragma("unroll") for (int e_ = 0, v = blockIdx.x * (blockDim.x * ((VPT) ? (VPT) : (vpt))) + \
+                                           threadIdx.x;                                \
+                           e_ < ((VPT) ? (VPT) : (vpt)); ++e_, v += blockDim.x)        \
+        if (v < (V))
+
 // vertex loop of one block: v = blockIdx.x*epb + threadIdx.x + e*blockDim.x
 #define FOR_VERT(V, vpt)                                                               \
     for (int e_ = 0, v = blockIdx.x * (blockDim.x * (vpt)) + threadIdx.x; e_ < (vpt);  \
@@ -226,7 +234,7 @@ __global__ void coarsest_kernel(const T *__restrict__ cx, const T *__restrict__ 
 }
 
 // ---------------------------------------------------------------- Krylov pieces
-template <typename T>
+template <typename T, int VPT = 0>
 __global__ void spmv_dot_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
                                 const T *__restrict__ p, T *__restrict__ q, int n, int vpt,
                                 double *__restrict__ part, int nblk, const int *__restrict__ act) {
@@ -238,7 +246,7 @@ __global__ void spmv_dot_kernel(const T *__restrict__ cx, const T *__restrict__ 
     const T *ax = cx + s * V, *ay = cy + s * V, *ps = p + s * V;
     T *qs = q + s * V;
     T acc = T(0);
-    FOR_VERT(V, vpt) {
+    FOR_VERT_C(V, VPT, vpt) {
         const int j = v / w, i = v - j * w;
         T val = T(0);
         if (i > 0 && i < n) {
@@ -254,7 +262,7 @@ __global__ void spmv_dot_kernel(const T *__restrict__ cx, const T *__restrict__ 
     if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
 }
 
-template <typename T>
+template <typename T, int VPT = 0>
 __global__ void axpy2_kernel(T *__restrict__ d, T *__restrict__ r, const T *__restrict__ p,
                              const T *__restrict__ q, const double *__restrict__ alpha, int n,
                              int vpt, double *__restrict__ part, int nblk,
@@ -265,7 +273,7 @@ __global__ void axpy2_kernel(T *__restrict__ d, T *__restrict__ r, const T *__re
     const long long V = (long long)(n + 1) * (n + 1);
     const T a = (T)alpha[s];
     T acc = T(0);
-    FOR_VERT(V, vpt) {
+    FOR_VERT_C(V, VPT, vpt) {
         const long long g = s * V + v;
         d[g] += a * p[g];
         const T rv = r[g] - a * q[g];
@@ -289,7 +297,7 @@ __global__ void dot_kernel(const T *__restrict__ a, const T *__restrict__ b, int
     if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
 }
 
-template <typename T>
+template <typename T, int VPT = 0>
 __global__ void pupdate_kernel(T *__restrict__ p, const T *__restrict__ z,
                                const double *__restrict__ beta, int n, int vpt,
                                const int *__restrict__ act) {
@@ -297,19 +305,19 @@ __global__ void pupdate_kernel(T *__restrict__ p, const T *__restrict__ z,
     if (!act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
     const T bt = (T)beta[s];
-    FOR_VERT(V, vpt) {
+    FOR_VERT_C(V, VPT, vpt) {
         const long long g = s * V + v;
         p[g] = z[g] + bt * p[g];
     }
 }
 
-template <typename T>
+template <typename T, int VPT = 0>
 __global__ void copy_kernel(T *__restrict__ dst, const T *__restrict__ src, int n, int vpt,
                             const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
-    FOR_VERT(V, vpt) dst[s * V + v] = src[s * V + v];
+    FOR_VERT_C(V, VPT, vpt) dst[s * V + v] = src[s * V + v];
 }
 
 // Per-sample scalar state.
@@ -890,14 +898,22 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     auto iter_head = [&]() -> int {
         {
             SceProf pr(KP_SPMV, st, S.vb(0, 4.0));
-            spmv_dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.p, S.q, n0, l0.vpt,
-                                                      S.part, l0.nblk, S.sc.act_in);
+            if (l0.vpt == 8)
+                spmv_dot_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.p, S.q, n0, 8,
+                                                             S.part, l0.nblk, S.sc.act_in);
+            else
+                spmv_dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.p, S.q, n0, l0.vpt,
+                                                          S.part, l0.nblk, S.sc.act_in);
         }
         S.reduce(RED_ALPHA, S.sc.act_in);
         {
             SceProf pr(KP_AXPY, st, S.vb(0, 6.0));
-            axpy2_kernel<T><<<g0, l0.tpb, 0, st>>>(S.d, S.b[0], S.p, S.q, S.sc.alpha, n0, l0.vpt,
-                                                   S.part, l0.nblk, S.sc.act_in);
+            if (l0.vpt == 8)
+                axpy2_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.d, S.b[0], S.p, S.q, S.sc.alpha, n0, 8,
+                                                          S.part, l0.nblk, S.sc.act_in);
+            else
+                axpy2_kernel<T><<<g0, l0.tpb, 0, st>>>(S.d, S.b[0], S.p, S.q, S.sc.alpha, n0,
+                                                       l0.vpt, S.part, l0.nblk, S.sc.act_in);
         }
         SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
         S.reduce(RED_RR, S.sc.act_in);
@@ -917,8 +933,12 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         S.reduce(RED_BETA, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
         {
             SceProf pr(KP_PUPDATE, st, S.vb(0, 3.0));
-            pupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], S.sc.beta, n0, l0.vpt,
-                                                     S.sc.act_in);
+            if (l0.vpt == 8)
+                pupdate_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], S.sc.beta, n0, 8,
+                                                            S.sc.act_in);
+            else
+                pupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], S.sc.beta, n0, l0.vpt,
+                                                         S.sc.act_in);
         }
         return CE_OK;
     };
@@ -979,7 +999,10 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         }
         {
             SceProf pr(KP_COPY, st, S.vb(0, 2.0));
-            copy_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], n0, l0.vpt, S.sc.act_in);
+            if (l0.vpt == 8)
+                copy_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], n0, 8, S.sc.act_in);
+            else
+                copy_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], n0, l0.vpt, S.sc.act_in);
         }
         S.reduce(RED_RZ0, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
         int in_act = n_act;
