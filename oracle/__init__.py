@@ -20,6 +20,8 @@ Modules
   field       Algorithm 1 step 4(a)-(f): xi -> w -> v = F w -> u -> Z -> k
   qmc         randomly shifted rank-1 lattice normals (the MLQMC sampler)
   darcy       P1 finite elements with nodal quadrature, direct solve, QoIs
+  field3d     the d = 3 embedding (C_ext over Z^3, threefold DFT) and field
+  darcy3d     the d = 3 Darcy problem on Kuhn tetrahedra, direct solve, QoIs
   mlmc        level differences, level sums, MLMC estimator and N_l rule
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py
