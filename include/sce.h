@@ -378,6 +378,87 @@ int mlmc_level_estimate_qmc(ce_qmc_t q, const darcy_problem *p, uint64_t seed, u
 int ce_autotune_fft(ce_embedding_t e, int precision, int count, int reps, void *stream,
                     int *row_tpf, int *row_F, int *col_tpf, int *col_F);
 
+/*
+ * Three-dimensional domains.  The paper writes the embedding (§2.1) and the
+ * model problem (§3.1-3.2) for d <= 2 and states that higher dimensions
+ * follow the same pattern; Eq. (2.7), the smoothing of §2.4 and its theorem
+ * are stated for general d.  These entry points are the d = 3 instance:
+ *   - grid: an n-cell grid has (n+1)^3 vertices p/n on [0,1]^3, vertex
+ *     (i, j, k) at index (k*(n+1) + j)*(n+1) + i; n a power of two,
+ *     2 <= n <= 256;
+ *   - embedding side P = 2(n + J), a power of two, 4 <= P <= 512; s = P^3,
+ *     array index k1 + P k2 + P^2 k3;
+ *   - fields are FP32; the solver refines its FP32 multigrid-CG corrections
+ *     against an FP64 residual.
+ */
+typedef struct ce3_embedding_s *ce3_embedding_t;
+
+/*
+ * ce3_setup_embedding -- Algorithm 1 steps 1-3 in d = 3: first column
+ * c[k3][k2][k1] = C_pad(d(k1)/n, d(k2)/n, d(k3)/n) (C_ext of Eq. (2.7) sums
+ * the shifts in Z^3 with the cutoff of |x|_inf), Lambda = the unnormalised
+ * +i DFT along the three axes in FP64, then the positivity check, padding
+ * loop and smoothing masks of ce_setup_embedding.  CE_KEEP_TAU_SQRT_S drops
+ * tau = floor(sqrt(s)) = floor(P^(3/2)) eigenvalues.  info->s = P^3.
+ * Arguments, ownership and errors as ce_setup_embedding (max_P <= 512).
+ */
+int ce3_setup_embedding(const ce_cov *cov, int n, const ce_pad *pad, const ce_smoothing *sm,
+                        void *stream, ce3_embedding_t *out, ce_embedding_info *info);
+int ce3_get_info(ce3_embedding_t e, ce_embedding_info *info);
+/* P^3 eigenvalues (clipped, unmasked), index k1 + P k2 + P^2 k3. */
+int ce3_get_eigenvalues(ce3_embedding_t e, double *dst, int dst_on_device, void *stream);
+/* P^3 keep-mask bytes, fine (which = 0) or coarse (1), to host memory. */
+int ce3_get_mask(ce3_embedding_t e, int which, unsigned char *dst_host);
+/* Releases the handle and its device tables (synchronises the device). */
+void ce3_destroy(ce3_embedding_t e);
+
+/*
+ * ce3_sample_batch -- Algorithm 1 step 4 in d = 3 (Algorithm 2 with masks),
+ * FP32, for samples first_sample .. first_sample+count-1 of `level`: xi_j,
+ * j = k1 + P k2 + P^2 k3, is normal j of the sample's stream as ce_normals
+ * with precision 32 -> w = sqrt(Lambda~) xi -> v = F w (threefold DFT, +i,
+ * unitary) -> u = Re v + Im v on the (n+1)^3 grid -> k = exp(u).
+ *   k_fine   : device float[count*(n+1)^3] or NULL
+ *   k_coarse : device float[count*(n/2+1)^3] or NULL: the coarse field of
+ *              the level (coarse mask) at the even vertices
+ * Errors: CE_ERR_INVALID_ARG, CE_ERR_OOM, CE_ERR_CUDA.
+ */
+int ce3_sample_batch(ce3_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,
+                     int count, float *k_fine, float *k_coarse, void *stream);
+
+/*
+ * darcy3_solve_batch -- -div(k grad u) = f on (0,1)^3, u = 1 at x1 = 0,
+ * u = 0 at x1 = 1, zero flux on the other faces; P1 elements on the Kuhn
+ * tetrahedra of each cell (the six simplices a, a+e_pi1, a+e_pi1+e_pi2,
+ * a+(1,1,1), pi a permutation of the axes), k averaged over each
+ * tetrahedron's four vertices (nodal quadrature).  Only axis-parallel edges
+ * couple, so the operator is a seven-point stencil.  Solved by FP32
+ * multigrid-preconditioned CG corrections of an FP64 residual (iterative
+ * refinement) to ||r|| <= rtol ||r_0||.
+ *   p      : p->n as above, p->precision must be 32
+ *   k      : device float[count*(n+1)^3]
+ *   qoi    : device double[count*3]: [outflow through x1 = 1 (consistent
+ *            flux), u(7/15, 7/15, 7/15) (P1 interpolant), ||u_h||_L2]
+ *   iters, status, u_out : device or NULL, as darcy_solve_batch
+ *            (u_out double[count*(n+1)^3])
+ * Returns CE_ERR_NOT_CONVERGED if any sample missed rtol (results written).
+ * Synchronises `stream`.
+ */
+int darcy3_solve_batch(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
+                       int *status, double *u_out, void *stream);
+
+/*
+ * mlmc3_level_estimate -- Algorithm 1 (Algorithm 2 with a smoothed handle)
+ * for one level in d = 3: fields by ce3_sample_batch, solves on the n- and
+ * (level > 0) n/2-cell grids, Y = Q_f - Q_c of QoI qoi_index, level sums in
+ * fixed order.  p->n must equal the handle's n.
+ *   out : host, the level sums;  Y : device double[count] or NULL
+ * Synchronises `stream`; CE_ERR_NOT_CONVERGED as mlmc_level_estimate.
+ */
+int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, uint64_t seed, uint32_t level,
+                         uint64_t first_sample, int count, int qoi_index, mlmc_level_sums *out,
+                         double *Y, void *stream);
+
 /* Eq. (3.6): N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)),
  * l = 0..L.  V, C, N: host arrays of length L+1 (C > 0, V >= 0). */
 int mlmc_optimal_samples(int L_plus_1, const double *V, const double *C, double eps, long long *N);

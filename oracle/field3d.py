@@ -65,15 +65,22 @@ def c_ext3(kind, x1, x2, x3, nu, lam, sigma2, ell):
 
 
 def first_column3(kind, nu, lam, sigma2, m, J, mode):
-    """The P x P x P first column c[i3, i2, i1] of the padded embedding matrix."""
+    """The P x P x P first column c[i3, i2, i1] of the padded embedding matrix.
+
+    c depends on the indices only through the lags d(i) in 0..P/2, so C_pad is
+    evaluated once per distinct lag triple and spread by indexing.
+    """
     P = 2 * (m + J)
-    t = em.lag_index(P) / float(m)
+    t = np.arange(P // 2 + 1) / float(m)
     t1 = t[None, None, :]
     t2 = t[None, :, None]
     t3 = t[:, None, None]
     if mode == em.PAD_SMOOTH:
-        return c_ext3(kind, t1, t2, t3, nu, lam, sigma2, 1.0 + J / float(m))
-    return cov3(kind, t1, t2, t3, nu, lam, sigma2)
+        cu = c_ext3(kind, t1, t2, t3, nu, lam, sigma2, 1.0 + J / float(m))
+    else:
+        cu = cov3(kind, t1, t2, t3, nu, lam, sigma2)
+    d = em.lag_index(P)
+    return cu[np.ix_(d, d, d)]
 
 
 NAIVE_DFT_MAX_P = 128

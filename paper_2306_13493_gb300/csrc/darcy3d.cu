@@ -1,0 +1,1027 @@
+// Darcy problem on the unit cube (§3.1-3.2 in d = 3) and the MLMC level
+// estimate built on it.
+//
+//   -div(k grad u) = f on (0,1)^3, u = 1 at x1 = 0, u = 0 at x1 = 1, zero
+//   flux on the other faces; P1 elements on the six Kuhn tetrahedra of every
+//   cell, k averaged over each tetrahedron's four vertices.
+//
+// Operator.  For the Kuhn tetrahedron {a, a+e_p0, a+e_p0+e_p1, a+(1,1,1)} the
+// barycentric gradients are -e_p0/h, (e_p0-e_p1)/h, (e_p1-e_p2)/h, e_p2/h, so
+// only the three path edges (all axis-parallel) have a non-zero stiffness
+// entry, -|T|/h^2 = -h/6.  The stiffness matrix is therefore a seven-point
+// stencil whose edge conductance is (h/6) sum over the tetrahedra containing
+// the edge of kbar_T = (h/24) sum_T sum_{v in T} k_v.  An edge along axis e
+// from vertex p lies in (a1, a2 the other two axes; a term only where its cell
+// exists):
+//   cell p          : {p, p+e, p+e+a1, p+e+a1+a2}, {p, p+e, p+e+a2, p+e+a1+a2}
+//   cell p-a1       : {p-a1, p, p+e, p+e+a2}
+//   cell p-a2       : {p-a2, p, p+e, p+e+a1}
+//   cell p-a1-a2    : {p-a1-a2, p-a2, p, p+e}, {p-a1-a2, p-a1, p, p+e}
+// The system is divided by h: conductances g = S/24 (S the vertex sum above)
+// and load F'_p = f h^2 N(p)/24, N(p) = number of tetrahedra at p (6 for the
+// cell corners a and a+(1,1,1) of each adjacent cell, 2 for the others).
+//
+// Solver: iterative refinement; the residual F' - A'u is formed in FP64 from
+// FP64 conductances and u, the correction solves A'd = r by FP32 CG
+// preconditioned with one geometric multigrid V(1,1) cycle (red-black
+// Gauss-Seidel in the (i+j+k) parity, full-weighting restriction, trilinear
+// prolongation, coarse conductances from two fine edges in series averaged
+// over the 3x3 transverse lines with weights 1, 1/2; exact solve of the 9
+// unknowns of the 2-cell grid).  Per-sample flags stop converged samples, so a
+// sample's result does not depend on the batch it is solved in.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sce_internal.cuh"
+
+namespace {
+
+constexpr int MAXLEV3 = 9;    // n <= 256
+constexpr int TPB3 = 256;
+constexpr int VPT3 = 8;
+constexpr int EPB3 = TPB3 * VPT3;
+
+__device__ __forceinline__ void decode3(long long v, int w, int *i, int *j, int *k) {
+    const long long r = v / w;
+    *i = (int)(v - r * w);
+    *k = (int)(r / w);
+    *j = (int)(r - (long long)(*k) * w);
+}
+
+template <int E> struct Axes {
+    static constexpr int A1 = (E + 1) % 3, A2 = (E + 2) % 3;
+};
+
+__device__ __forceinline__ long long stride3(int axis, int w) {
+    return axis == 0 ? 1 : (axis == 1 ? (long long)w : (long long)w * w);
+}
+
+// S of the edge along axis E from (c0, c1, c2) (see the file comment); 0 on
+// the last plane of E.  k in FP32, S exact in FP64 (at most 24 terms).
+template <int E>
+__device__ __forceinline__ double edge_sum3(const float *__restrict__ ks, int n, const int c[3],
+                                            long long v) {
+    constexpr int A1 = Axes<E>::A1, A2 = Axes<E>::A2;
+    if (c[E] >= n) return 0.0;
+    const int w = n + 1;
+    const long long se = stride3(E, w), s1 = stride3(A1, w), s2 = stride3(A2, w);
+    auto K = [&](int de, int d1, int d2) { return (double)ks[v + de * se + d1 * s1 + d2 * s2]; };
+    const bool lo1 = c[A1] > 0, hi1 = c[A1] < n, lo2 = c[A2] > 0, hi2 = c[A2] < n;
+    const double base = K(0, 0, 0) + K(1, 0, 0);
+    double S = 0.0;
+    if (hi1 && hi2) S += 2.0 * base + K(1, 1, 0) + K(1, 0, 1) + 2.0 * K(1, 1, 1);
+    if (lo1 && hi2) S += base + K(0, -1, 0) + K(1, 0, 1);
+    if (hi1 && lo2) S += base + K(0, 0, -1) + K(1, 1, 0);
+    if (lo1 && lo2) S += 2.0 * base + 2.0 * K(0, -1, -1) + K(0, 0, -1) + K(0, -1, 0);
+    return S;
+}
+
+// tetrahedra at vertex (i, j, k) of an n-cell grid
+__device__ __forceinline__ int tets_at(int i, int j, int k, int n) {
+    int N = 0;
+    for (int d = 0; d < 8; ++d) {
+        const int di = d & 1, dj = (d >> 1) & 1, dk = (d >> 2) & 1;
+        const bool ok = (di ? i > 0 : i < n) && (dj ? j > 0 : j < n) && (dk ? k > 0 : k < n);
+        if (ok) N += (d == 0 || d == 7) ? 6 : 2;
+    }
+    return N;
+}
+
+// ---------------------------------------------------------------- per-vertex kernels
+// grid: (blocks over vertices, samples); a thread visits VPT3 vertices
+#define FOR_V3(V)                                                                          \
+    _Pragma("unroll") for (int e_ = 0; e_ < VPT3; ++e_)                                    \
+        for (long long v = (long long)blockIdx.x * EPB3 + threadIdx.x + (long long)e_ * TPB3; \
+             v < (V); v = (V))
+
+__global__ void cond3_kernel(const float *__restrict__ k, int n, double *__restrict__ g64x,
+                             double *__restrict__ g64y, double *__restrict__ g64z,
+                             float *__restrict__ gx, float *__restrict__ gy,
+                             float *__restrict__ gz) {
+    const int s = blockIdx.y;
+    const int w = n + 1;
+    const long long V = (long long)w * w * w, off = (long long)s * V;
+    const float *ks = k + off;
+    FOR_V3(V) {
+        int c[3];
+        decode3(v, w, &c[0], &c[1], &c[2]);
+        const double x = edge_sum3<0>(ks, n, c, v) * (1.0 / 24.0);
+        const double y = edge_sum3<1>(ks, n, c, v) * (1.0 / 24.0);
+        const double z = edge_sum3<2>(ks, n, c, v) * (1.0 / 24.0);
+        g64x[off + v] = x;
+        g64y[off + v] = y;
+        g64z[off + v] = z;
+        gx[off + v] = (float)x;
+        gy[off + v] = (float)y;
+        gz[off + v] = (float)z;
+    }
+}
+
+__device__ __forceinline__ float series3(float a, float b) {
+    const float t = a + b;
+    return t > 0.0f ? a * b / t : 0.0f;
+}
+
+// coarse conductance along axis E at coarse vertex c (coarse grid nc = nf/2):
+// two fine edges in series, averaged over the transverse fine lines with
+// weights 1 (through the coarse line) and 1/2 (its neighbours)
+template <int E>
+__device__ __forceinline__ float coarse_cond3(const float *__restrict__ gf, int nf, const int c[3]) {
+    constexpr int A1 = Axes<E>::A1, A2 = Axes<E>::A2;
+    const int nc = nf / 2;
+    if (c[E] >= nc) return 0.0f;
+    const int wf = nf + 1;
+    const long long se = stride3(E, wf), s1 = stride3(A1, wf), s2 = stride3(A2, wf);
+    const long long base = 2 * (c[0] * stride3(0, wf) + c[1] * stride3(1, wf) + c[2] * stride3(2, wf));
+    float acc = 0.0f;
+    for (int d2 = -1; d2 <= 1; ++d2) {
+        const int f2 = 2 * c[A2] + d2;
+        if (f2 < 0 || f2 > nf) continue;
+        const float w2 = d2 == 0 ? 1.0f : 0.5f;
+        for (int d1 = -1; d1 <= 1; ++d1) {
+            const int f1 = 2 * c[A1] + d1;
+            if (f1 < 0 || f1 > nf) continue;
+            const float w1 = d1 == 0 ? 1.0f : 0.5f;
+            const long long q = base + d1 * s1 + d2 * s2;
+            acc += w1 * w2 * series3(gf[q], gf[q + se]);
+        }
+    }
+    return acc;
+}
+
+__global__ void coarsen3_kernel(const float *__restrict__ fx, const float *__restrict__ fy,
+                                const float *__restrict__ fz, int nf, float *__restrict__ cx,
+                                float *__restrict__ cy, float *__restrict__ cz) {
+    const int s = blockIdx.y;
+    const int nc = nf / 2, wc = nc + 1, wf = nf + 1;
+    const long long Vc = (long long)wc * wc * wc, Vf = (long long)wf * wf * wf;
+    const float *ax = fx + s * Vf, *ay = fy + s * Vf, *az = fz + s * Vf;
+    FOR_V3(Vc) {
+        int c[3];
+        decode3(v, wc, &c[0], &c[1], &c[2]);
+        cx[s * Vc + v] = coarse_cond3<0>(ax, nf, c);
+        cy[s * Vc + v] = coarse_cond3<1>(ay, nf, c);
+        cz[s * Vc + v] = coarse_cond3<2>(az, nf, c);
+    }
+}
+
+// sum of g_e (z_p - z_q) over the six edges of an unknown vertex
+template <typename T>
+__device__ __forceinline__ T apply3(const T *gx, const T *gy, const T *gz, const T *z, long long v,
+                                    int j, int k, int n) {
+    const int w = n + 1;
+    const long long w2 = (long long)w * w;
+    const T zc = z[v];
+    T a = gx[v - 1] * (zc - z[v - 1]) + gx[v] * (zc - z[v + 1]);
+    if (j > 0) a += gy[v - w] * (zc - z[v - w]);
+    if (j < n) a += gy[v] * (zc - z[v + w]);
+    if (k > 0) a += gz[v - w2] * (zc - z[v - w2]);
+    if (k < n) a += gz[v] * (zc - z[v + w2]);
+    return a;
+}
+
+// red-black Gauss-Seidel half-sweep: vertices with (i + j + k) % 2 == color
+__global__ void smooth3_kernel(const float *__restrict__ gx, const float *__restrict__ gy,
+                               const float *__restrict__ gz, const float *__restrict__ b,
+                               float *__restrict__ z, int n, int color,
+                               const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int w = n + 1, half = (n + 2) / 2;
+    const long long V = (long long)w * w * w, off = (long long)s * V;
+    const long long total = (long long)half * w * w;
+    const long long w2 = (long long)w * w;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / half;
+        const int ii = (int)(t - r * half);
+        const int k = (int)(r / w), j = (int)(r - (long long)k * w);
+        const int i = 2 * ii + ((color + j + k) & 1);
+        if (i < 1 || i > n - 1) continue;
+        const long long v = off + r * w + i;
+        const float cw = gx[v - 1], ce = gx[v];
+        const float cs = j > 0 ? gy[v - w] : 0.0f, cn = j < n ? gy[v] : 0.0f;
+        const float cd = k > 0 ? gz[v - w2] : 0.0f, cu = k < n ? gz[v] : 0.0f;
+        float acc = b[v] + cw * z[v - 1] + ce * z[v + 1];
+        if (j > 0) acc += cs * z[v - w];
+        if (j < n) acc += cn * z[v + w];
+        if (k > 0) acc += cd * z[v - w2];
+        if (k < n) acc += cu * z[v + w2];
+        z[v] = acc / (cw + ce + cs + cn + cd + cu);
+    }
+}
+
+// res = b - A z at the unknowns, 0 on the Dirichlet planes
+__global__ void resid3_kernel(const float *__restrict__ gx, const float *__restrict__ gy,
+                              const float *__restrict__ gz, const float *__restrict__ b,
+                              const float *__restrict__ z, float *__restrict__ res, int n,
+                              const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int w = n + 1;
+    const long long V = (long long)w * w * w, off = (long long)s * V;
+    FOR_V3(V) {
+        int i, j, k;
+        decode3(v, w, &i, &j, &k);
+        float r = 0.0f;
+        if (i > 0 && i < n)
+            r = b[off + v] - apply3(gx + off, gy + off, gz + off, z + off, v, j, k, n);
+        res[off + v] = r;
+    }
+}
+
+// coarse right-hand side by full weighting (the transpose of trilinear
+// prolongation) at coarse unknowns, 0 on the coarse Dirichlet planes; zc = 0
+__global__ void restrict3_kernel(const float *__restrict__ res, int nf, float *__restrict__ bc,
+                                 float *__restrict__ zc, const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int nc = nf / 2, wc = nc + 1, wf = nf + 1;
+    const long long Vc = (long long)wc * wc * wc, Vf = (long long)wf * wf * wf;
+    const float *rs = res + s * Vf;
+    FOR_V3(Vc) {
+        int I, J, K;
+        decode3(v, wc, &I, &J, &K);
+        float acc = 0.0f;
+        if (I > 0 && I < nc) {
+            for (int dk = -1; dk <= 1; ++dk) {
+                const int k = 2 * K + dk;
+                if (k < 0 || k > nf) continue;
+                const float wk = dk == 0 ? 1.0f : 0.5f;
+                for (int dj = -1; dj <= 1; ++dj) {
+                    const int j = 2 * J + dj;
+                    if (j < 0 || j > nf) continue;
+                    const float wj = dj == 0 ? 1.0f : 0.5f;
+                    const long long row = ((long long)k * wf + j) * wf + 2 * I;
+                    acc += wk * wj * (0.5f * rs[row - 1] + rs[row] + 0.5f * rs[row + 1]);
+                }
+            }
+        }
+        bc[s * Vc + v] = acc;
+        zc[s * Vc + v] = 0.0f;
+    }
+}
+
+// z += trilinear interpolation of the coarse correction (unknowns only)
+__global__ void prolong3_kernel(const float *__restrict__ zc, int nc, float *__restrict__ zf,
+                                const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int nf = 2 * nc, wf = nf + 1, wc = nc + 1;
+    const long long Vf = (long long)wf * wf * wf, Vc = (long long)wc * wc * wc;
+    const float *c = zc + s * Vc;
+    FOR_V3(Vf) {
+        int i, j, k;
+        decode3(v, wf, &i, &j, &k);
+        if (i < 1 || i > nf - 1) continue;
+        const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+        const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
+        const float wi = (i & 1) ? 0.5f : 1.0f, wj = (j & 1) ? 0.5f : 1.0f,
+                    wk = (k & 1) ? 0.5f : 1.0f;
+        auto C = [&](int a, int b, int d) { return c[((long long)d * wc + b) * wc + a]; };
+        float acc = C(i0, j0, k0);
+        if (i & 1) acc += C(i1, j0, k0);
+        if (j & 1) acc += C(i0, j1, k0) + ((i & 1) ? C(i1, j1, k0) : 0.0f);
+        if (k & 1) {
+            float t = C(i0, j0, k1);
+            if (i & 1) t += C(i1, j0, k1);
+            if (j & 1) t += C(i0, j1, k1) + ((i & 1) ? C(i1, j1, k1) : 0.0f);
+            acc += t;
+        }
+        zf[s * Vf + v] += wi * wj * wk * acc;
+    }
+}
+
+// exact solve on the 2-cell grid: unknowns (1, j, k), j, k = 0..2, one
+// thread per sample, Gaussian elimination of the 9 x 9 SPD system
+__global__ void coarsest3_kernel(const float *__restrict__ gx, const float *__restrict__ gy,
+                                 const float *__restrict__ gz, const float *__restrict__ b,
+                                 float *__restrict__ z, int count, const int *__restrict__ act) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= count || !act[s]) return;
+    const long long off = (long long)s * 27;
+    float A[9][9], r[9];
+    for (int a = 0; a < 9; ++a) {
+        for (int c = 0; c < 9; ++c) A[a][c] = 0.0f;
+    }
+    for (int k = 0; k < 3; ++k) {
+        for (int j = 0; j < 3; ++j) {
+            const int u = j + 3 * k;
+            const long long v = off + (k * 3 + j) * 3 + 1;
+            float d = gx[v - 1] + gx[v];
+            if (j > 0) d += gy[v - 3];
+            if (j < 2) {
+                d += gy[v];
+                A[u][u + 1] = A[u + 1][u] = -gy[v];
+            }
+            if (k > 0) d += gz[v - 9];
+            if (k < 2) {
+                d += gz[v];
+                A[u][u + 3] = A[u + 3][u] = -gz[v];
+            }
+            A[u][u] = d;
+            r[u] = b[v];
+        }
+    }
+    for (int p = 0; p < 9; ++p) {
+        for (int q = p + 1; q < 9; ++q) {
+            const float m = A[q][p] / A[p][p];
+            for (int c = p; c < 9; ++c) A[q][c] -= m * A[p][c];
+            r[q] -= m * r[p];
+        }
+    }
+    float x[9];
+    for (int p = 8; p >= 0; --p) {
+        float t = r[p];
+        for (int c = p + 1; c < 9; ++c) t -= A[p][c] * x[c];
+        x[p] = t / A[p][p];
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j) z[off + (k * 3 + j) * 3 + 1] = x[j + 3 * k];
+}
+
+// ---------------------------------------------------------------- Krylov pieces
+__device__ __forceinline__ float block_sum3(float v, float *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    float t = 0.0f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    return t;
+}
+
+__global__ void __launch_bounds__(TPB3) spmv_dot3_kernel(
+    const float *__restrict__ gx, const float *__restrict__ gy, const float *__restrict__ gz,
+    const float *__restrict__ p, float *__restrict__ q, int n, double *__restrict__ part,
+    int nblk, const int *__restrict__ act) {
+    __shared__ float sh[32];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int w = n + 1;
+    const long long V = (long long)w * w * w, off = (long long)s * V;
+    float acc = 0.0f;
+    FOR_V3(V) {
+        int i, j, k;
+        decode3(v, w, &i, &j, &k);
+        float val = 0.0f;
+        if (i > 0 && i < n) {
+            val = apply3(gx + off, gy + off, gz + off, p + off, v, j, k, n);
+            acc += p[off + v] * val;
+        }
+        q[off + v] = val;
+    }
+    const float tot = block_sum3(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
+}
+
+__global__ void __launch_bounds__(TPB3) axpy2_3_kernel(
+    float *__restrict__ d, float *__restrict__ r, const float *__restrict__ p,
+    const float *__restrict__ q, const double *__restrict__ alpha, long long V,
+    double *__restrict__ part, int nblk, const int *__restrict__ act) {
+    __shared__ float sh[32];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const float a = (float)alpha[s];
+    const long long off = (long long)s * V;
+    float acc = 0.0f;
+    FOR_V3(V) {
+        const long long g = off + v;
+        d[g] += a * p[g];
+        const float rv = r[g] - a * q[g];
+        r[g] = rv;
+        acc += rv * rv;
+    }
+    const float tot = block_sum3(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
+}
+
+__global__ void __launch_bounds__(TPB3) dot3_kernel(const float *__restrict__ a,
+                                                    const float *__restrict__ b, long long V,
+                                                    double *__restrict__ part, int nblk,
+                                                    const int *__restrict__ act) {
+    __shared__ float sh[32];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long off = (long long)s * V;
+    float acc = 0.0f;
+    FOR_V3(V) acc += a[off + v] * b[off + v];
+    const float tot = block_sum3(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
+}
+
+// p = z + beta p (first == 1: p = z)
+__global__ void __launch_bounds__(TPB3) pupdate3_kernel(float *__restrict__ p,
+                                                        const float *__restrict__ z,
+                                                        const double *__restrict__ beta,
+                                                        long long V, int first,
+                                                        const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const float bt = first ? 0.0f : (float)beta[s];
+    const long long off = (long long)s * V;
+    FOR_V3(V) {
+        const long long g = off + v;
+        p[g] = first ? z[g] : z[g] + bt * p[g];
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+struct Scal3 {
+    double *rz, *pq, *rr, *alpha, *beta, *orr, *orr0, *thr;
+    int *act_out, *act_in, *iters, *counter;
+};
+
+enum { R3_ALPHA = 0, R3_RR = 1, R3_BETA = 2, R3_RZ0 = 3, R3_ORR = 4, R3_ORR0 = 5 };
+
+// one warp per sample: fixed-order sum of the block partials, then the
+// scalar update of `mode`
+__global__ void reduce3_kernel(const double *__restrict__ part, int nblk, int count, int mode,
+                               Scal3 sc, const int *__restrict__ act, double rtol2,
+                               double in_rel2) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= count) return;
+    const int s = warp;
+    if (act && !act[s]) return;
+    double v = 0.0;
+    for (int i = lane; i < nblk; i += 32) v += part[(long long)s * nblk + i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane != 0) return;
+    switch (mode) {
+        case R3_ALPHA:
+            sc.pq[s] = v;
+            sc.alpha[s] = v > 0.0 ? sc.rz[s] / v : 0.0;
+            break;
+        case R3_RR: {
+            sc.rr[s] = v;
+            sc.iters[s] += 1;
+            if (!(v > sc.thr[s])) sc.act_in[s] = 0;
+            else atomicAdd(sc.counter, 1);
+            break;
+        }
+        case R3_BETA:
+            sc.beta[s] = sc.rz[s] > 0.0 ? v / sc.rz[s] : 0.0;
+            sc.rz[s] = v;
+            break;
+        case R3_RZ0:
+            sc.rz[s] = v;
+            break;
+        default: {   // R3_ORR, R3_ORR0
+            sc.orr[s] = v;
+            if (mode == R3_ORR0) sc.orr0[s] = v;
+            const bool more = v > rtol2 * sc.orr0[s] && v == v;
+            sc.act_out[s] = more ? 1 : 0;
+            sc.act_in[s] = sc.act_out[s];
+            sc.thr[s] = fmax(in_rel2 * v, 0.0625 * rtol2 * sc.orr0[s]);
+            if (more) atomicAdd(sc.counter, 1);
+            break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- refinement (FP64)
+__global__ void lift3_kernel(double *__restrict__ u, int n) {
+    const int s = blockIdx.y;
+    const int w = n + 1;
+    const long long V = (long long)w * w * w, off = (long long)s * V;
+    FOR_V3(V) u[off + v] = (v % w == 0) ? 1.0 : 0.0;
+}
+
+// r = F' - A'u (FP64) at unknowns -> b (FP32), partial |r|^2; samples with act == 0 skip
+__global__ void __launch_bounds__(TPB3) outer_residual3_kernel(
+    const double *__restrict__ g64x, const double *__restrict__ g64y,
+    const double *__restrict__ g64z, const double *__restrict__ u, int n, double fh2,
+    float *__restrict__ b, double *__restrict__ part, int nblk, const int *__restrict__ act) {
+    __shared__ double shd[32];
+    const int s = blockIdx.y;
+    if (act && !act[s]) return;
+    const int w = n + 1;
+    const long long V = (long long)w * w * w, off = (long long)s * V;
+    double acc = 0.0;
+    FOR_V3(V) {
+        int i, j, k;
+        decode3(v, w, &i, &j, &k);
+        double r = 0.0;
+        if (i > 0 && i < n) {
+            r = fh2 * (double)tets_at(i, j, k, n) * (1.0 / 24.0) -
+                apply3(g64x + off, g64y + off, g64z + off, u + off, v, j, k, n);
+            acc += r * r;
+        }
+        b[off + v] = (float)r;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) shd[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += shd[i];
+        part[(long long)s * nblk + blockIdx.x] = t;
+    }
+}
+
+__global__ void outer_update3_kernel(double *__restrict__ u, const float *__restrict__ d, int n,
+                                     const int *__restrict__ act) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int w = n + 1;
+    const long long V = (long long)w * w * w, off = (long long)s * V;
+    FOR_V3(V) {
+        const int i = (int)(v % w);
+        if (i > 0 && i < n) u[off + v] += (double)d[off + v];
+    }
+}
+
+// ---------------------------------------------------------------- QoIs (FP64)
+// partials of the outflow h sum_{j,k} [g_x(n-1, j, k) u(n-1, j, k) + F'(n, j, k)]
+// (over the vertices of the x1 = 1 plane) and of sum_T (sum u_i^2 + (sum u_i)^2)
+// over the six tetrahedra of every cell
+__global__ void __launch_bounds__(TPB3) qoi3_partial_kernel(
+    const double *__restrict__ g64x, const double *__restrict__ u, int n, double fh2,
+    double *__restrict__ part_out, double *__restrict__ part_l2, int nblk) {
+    __shared__ double sa[32], sb[32];
+    const int s = blockIdx.y;
+    const int w = n + 1;
+    const long long V = (long long)w * w * w, off = (long long)s * V;
+    const double *us = u + off;
+    const long long w2 = (long long)w * w;
+    double a = 0.0, b = 0.0;
+    FOR_V3(V) {
+        int i, j, k;
+        decode3(v, w, &i, &j, &k);
+        if (i == n)
+            a += g64x[off + v - 1] * us[v - 1] + fh2 * (double)tets_at(i, j, k, n) * (1.0 / 24.0);
+        if (i < n && j < n && k < n) {
+            // corners: bit 0 = +x, bit 1 = +y, bit 2 = +z
+            double c[8];
+            for (int d = 0; d < 8; ++d) c[d] = us[v + (d & 1) + ((d >> 1) & 1) * w + (d >> 2) * w2];
+            // Kuhn tetrahedra 0, e_p0, e_p0 + e_p1, (1,1,1) for the six orders
+            const int path[6][2] = {{1, 3}, {1, 5}, {2, 3}, {2, 6}, {4, 5}, {4, 6}};
+            for (int t = 0; t < 6; ++t) {
+                const double x0 = c[0], x1 = c[path[t][0]], x2 = c[path[t][1]], x3 = c[7];
+                const double sum = x0 + x1 + x2 + x3;
+                b += x0 * x0 + x1 * x1 + x2 * x2 + x3 * x3 + sum * sum;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            ta += sa[i];
+            tb += sb[i];
+        }
+        part_out[(long long)s * nblk + blockIdx.x] = ta;
+        part_l2[(long long)s * nblk + blockIdx.x] = tb;
+    }
+}
+
+__global__ void qoi3_final_kernel(const double *__restrict__ part_out,
+                                  const double *__restrict__ part_l2, int nblk, int count,
+                                  const double *__restrict__ u, int n, Scal3 sc, double rtol2,
+                                  double *__restrict__ qoi, int *__restrict__ iters_out,
+                                  int *__restrict__ status_out, int *__restrict__ misc) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= count) return;
+    const int s = warp;
+    double a = 0.0, b = 0.0;
+    for (int i = lane; i < nblk; i += 32) {
+        a += part_out[(long long)s * nblk + i];
+        b += part_l2[(long long)s * nblk + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane != 0) return;
+    const double h = 1.0 / (double)n;
+    const int w = n + 1;
+    const long long off = (long long)s * w * w * w;
+    // point value at (7/15)^3: cell a, local t; the Kuhn tetrahedron of the
+    // descending order of the local coordinates
+    const double xs = 7.0 / 15.0 * (double)n;
+    const int ca = min((int)floor(xs), n - 1);
+    double t[3] = {xs - ca, xs - ca, xs - ca};
+    int ord[3] = {0, 1, 2};
+    for (int p = 0; p < 3; ++p)
+        for (int q = p + 1; q < 3; ++q)
+            if (t[ord[q]] > t[ord[p]]) {
+                const int tmp = ord[p];
+                ord[p] = ord[q];
+                ord[q] = tmp;
+            }
+    int c[3] = {ca, ca, ca};
+    auto U = [&](const int *cc) { return u[off + ((long long)cc[2] * w + cc[1]) * w + cc[0]]; };
+    double q_pt = (1.0 - t[ord[0]]) * U(c);
+    c[ord[0]] += 1;
+    q_pt += (t[ord[0]] - t[ord[1]]) * U(c);
+    c[ord[1]] += 1;
+    q_pt += (t[ord[1]] - t[ord[2]]) * U(c);
+    c[ord[2]] += 1;
+    q_pt += t[ord[2]] * U(c);
+    const double q_out = h * a;
+    const double q_l2 = sqrt(b * h * h * h / 120.0);   // |T| / 20 = h^3 / 120
+    qoi[3 * s + 0] = q_out;
+    qoi[3 * s + 1] = q_pt;
+    qoi[3 * s + 2] = q_l2;
+    int st = 0;
+    if (!(fabs(q_out) < 1e300 && fabs(q_pt) < 1e300 && fabs(q_l2) < 1e300))
+        st = CE_ERR_NONFINITE;
+    else if (!(sc.orr[s] <= rtol2 * sc.orr0[s]))
+        st = CE_ERR_NOT_CONVERGED;
+    if (status_out) status_out[s] = st;
+    if (iters_out) iters_out[s] = sc.iters[s];
+    if (st != 0) atomicAdd(&misc[0], 1);
+    atomicMax(&misc[1], sc.iters[s]);
+    atomicAdd(&misc[2], sc.iters[s]);
+}
+
+// ---------------------------------------------------------------- driver
+struct Solver3 {
+    cudaStream_t st = nullptr;
+    int count = 0, NL = 0;
+    int n[MAXLEV3];
+    long long V[MAXLEV3];
+    float *gx[MAXLEV3] = {}, *gy[MAXLEV3] = {}, *gz[MAXLEV3] = {}, *b[MAXLEV3] = {},
+          *z[MAXLEV3] = {};
+    float *res = nullptr, *p = nullptr, *q = nullptr, *d = nullptr;
+    double *g64x = nullptr, *g64y = nullptr, *g64z = nullptr, *u = nullptr;
+    double *part = nullptr, *part2 = nullptr, *sdbl = nullptr;
+    int *sint = nullptr;
+    Scal3 sc{};
+    int nblk0 = 0;
+    std::vector<void *> owned;
+
+    template <typename T>
+    int alloc(T **ptr, size_t cnt) {
+        int rc = sce_alloc_t(ptr, cnt, st);
+        if (rc == CE_OK) owned.push_back(*ptr);
+        return rc;
+    }
+    ~Solver3() {
+        for (void *ptr : owned) sce_free(ptr, st);
+    }
+    dim3 grid(int L) const { return dim3((unsigned)((V[L] + EPB3 - 1) / EPB3), count); }
+    double vb(int L, double per) const { return (double)count * V[L] * per; }
+
+    int init(int n0, int cnt) {
+        count = cnt;
+        NL = 0;
+        for (int m = n0; m >= 2; m >>= 1) {
+            n[NL] = m;
+            V[NL] = (long long)(m + 1) * (m + 1) * (m + 1);
+            ++NL;
+        }
+        for (int L = 0; L < NL; ++L) {
+            const size_t c = (size_t)count * V[L];
+            SCE_TRY(alloc(&gx[L], c));
+            SCE_TRY(alloc(&gy[L], c));
+            SCE_TRY(alloc(&gz[L], c));
+            SCE_TRY(alloc(&b[L], c));
+            SCE_TRY(alloc(&z[L], c));
+        }
+        const size_t c0 = (size_t)count * V[0];
+        SCE_TRY(alloc(&res, c0));
+        SCE_TRY(alloc(&p, c0));
+        SCE_TRY(alloc(&q, c0));
+        SCE_TRY(alloc(&d, c0));
+        SCE_TRY(alloc(&g64x, c0));
+        SCE_TRY(alloc(&g64y, c0));
+        SCE_TRY(alloc(&g64z, c0));
+        SCE_TRY(alloc(&u, c0));
+        nblk0 = (int)((V[0] + EPB3 - 1) / EPB3);
+        SCE_TRY(alloc(&part, (size_t)count * nblk0));
+        SCE_TRY(alloc(&part2, (size_t)count * nblk0));
+        SCE_TRY(alloc(&sdbl, (size_t)count * 8));
+        SCE_TRY(alloc(&sint, (size_t)count * 4 + 4));
+        sc.rz = sdbl;
+        sc.pq = sdbl + count;
+        sc.rr = sdbl + 2 * count;
+        sc.alpha = sdbl + 3 * count;
+        sc.beta = sdbl + 4 * count;
+        sc.orr = sdbl + 5 * count;
+        sc.orr0 = sdbl + 6 * count;
+        sc.thr = sdbl + 7 * count;
+        sc.act_out = sint;
+        sc.act_in = sint + count;
+        sc.iters = sint + 2 * count;
+        sc.counter = sint + 4 * count;
+        SCE_CUDA(cudaMemsetAsync(sdbl, 0, (size_t)count * 8 * sizeof(double), st));
+        SCE_CUDA(cudaMemsetAsync(sint, 0, ((size_t)count * 4 + 4) * sizeof(int), st));
+        return CE_OK;
+    }
+
+    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0) {
+        SceProf pr(KP_REDUCE, st, (double)count * nblk0 * 8.0);
+        reduce3_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(part, nblk0, count, mode, sc, act,
+                                                                 rtol2, in_rel2);
+    }
+
+    int read_counter(int *host) {
+        SCE_CUDA(cudaMemcpyAsync(host, sc.counter, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SCE_CUDA(cudaStreamSynchronize(st));
+        return CE_OK;
+    }
+
+    // z[0] = M^-1 b[0] for the samples with act set
+    void vcycle(const int *act) {
+        cudaMemsetAsync(z[0], 0, (size_t)count * V[0] * sizeof(float), st);
+        for (int L = 0; L < NL - 1; ++L) {
+            const int half = (n[L] + 2) / 2, w = n[L] + 1;
+            const long long tot = (long long)half * w * w;
+            dim3 gs((unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), count);
+            {
+                SceProf pr(KP_SMOOTH3, st, vb(L, 2 * 4 * 4.0 + 2 * 4.0));
+                smooth3_kernel<<<gs, 256, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], n[L], 0, act);
+                smooth3_kernel<<<gs, 256, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], n[L], 1, act);
+            }
+            {
+                SceProf pr(KP_RESID3, st, vb(L, 6 * 4.0));
+                resid3_kernel<<<grid(L), TPB3, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], res, n[L],
+                                                        act);
+            }
+            {
+                SceProf pr(KP_RESTRICT3, st, vb(L, 4.0) + vb(L + 1, 8.0));
+                restrict3_kernel<<<grid(L + 1), TPB3, 0, st>>>(res, n[L], b[L + 1], z[L + 1], act);
+            }
+        }
+        {
+            const int L = NL - 1;
+            SceProf pr(KP_COARSEST, st, vb(L, 5 * 4.0));
+            coarsest3_kernel<<<(count + 127) / 128, 128, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L],
+                                                                   count, act);
+        }
+        for (int L = NL - 2; L >= 0; --L) {
+            {
+                SceProf pr(KP_PROLONG3, st, vb(L, 8.0) + vb(L + 1, 4.0));
+                prolong3_kernel<<<grid(L), TPB3, 0, st>>>(z[L + 1], n[L + 1], z[L], act);
+            }
+            const int half = (n[L] + 2) / 2, w = n[L] + 1;
+            const long long tot = (long long)half * w * w;
+            dim3 gs((unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), count);
+            SceProf pr(KP_SMOOTH3, st, vb(L, 2 * 4 * 4.0 + 2 * 4.0));
+            smooth3_kernel<<<gs, 256, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], n[L], 1, act);
+            smooth3_kernel<<<gs, 256, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], n[L], 0, act);
+        }
+    }
+};
+
+int solve3(const darcy_problem *pr, const float *k, int count, double *qoi, int *iters,
+           int *status, double *u_out, cudaStream_t st, int *misc_out) {
+    Solver3 S;
+    S.st = st;
+    SCE_TRY(S.init(pr->n, count));
+    const int n0 = pr->n;
+    const dim3 g0 = S.grid(0);
+    const long long V0 = S.V[0];
+    {
+        SceProf pf(KP_COND3, st, S.vb(0, 4.0 + 3 * 12.0));
+        cond3_kernel<<<g0, TPB3, 0, st>>>(k, n0, S.g64x, S.g64y, S.g64z, S.gx[0], S.gy[0], S.gz[0]);
+    }
+    for (int L = 1; L < S.NL; ++L) {
+        SceProf pf(KP_COARSEN, st, S.vb(L - 1, 12.0) + S.vb(L, 12.0));
+        coarsen3_kernel<<<S.grid(L), TPB3, 0, st>>>(S.gx[L - 1], S.gy[L - 1], S.gz[L - 1], S.n[L - 1],
+                                                    S.gx[L], S.gy[L], S.gz[L]);
+    }
+    lift3_kernel<<<g0, TPB3, 0, st>>>(S.u, n0);
+    SCE_CUDA(cudaGetLastError());
+
+    const double h = 1.0 / (double)n0;
+    const double fh2 = pr->f * h * h;
+    const double rtol2 = pr->rtol * pr->rtol;
+    const double in_rel2 = 1e-10;   // inner target: relative drop 1e-5
+    const int maxit = pr->maxit > 0 ? pr->maxit : 1000;
+    const int inner_max = 40, check_every = 4;
+
+    auto outer_residual = [&](const int *act, int mode) -> int {
+        {
+            SceProf pf(KP_OUTER3, st, S.vb(0, 4 * 8.0 + 4.0));
+            outer_residual3_kernel<<<g0, TPB3, 0, st>>>(S.g64x, S.g64y, S.g64z, S.u, n0, fh2,
+                                                        S.b[0], S.part, S.nblk0, act);
+        }
+        SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
+        S.reduce(mode, act, rtol2, in_rel2);
+        SCE_CUDA(cudaGetLastError());
+        return CE_OK;
+    };
+    SCE_TRY(outer_residual(nullptr, R3_ORR0));
+    int n_act = 0;
+    SCE_TRY(S.read_counter(&n_act));
+    int total_inner = 0;
+    for (int outer = 0; outer < 64 && n_act > 0 && total_inner < maxit; ++outer) {
+        SCE_CUDA(cudaMemsetAsync(S.d, 0, (size_t)count * V0 * sizeof(float), st));
+        S.vcycle(S.sc.act_in);
+        {
+            SceProf pf(KP_DOT, st, S.vb(0, 8.0));
+            dot3_kernel<<<g0, TPB3, 0, st>>>(S.b[0], S.z[0], V0, S.part, S.nblk0, S.sc.act_in);
+        }
+        {
+            SceProf pf(KP_VEC3, st, S.vb(0, 8.0));
+            pupdate3_kernel<<<g0, TPB3, 0, st>>>(S.p, S.z[0], S.sc.beta, V0, 1, S.sc.act_in);
+        }
+        S.reduce(R3_RZ0, S.sc.act_in);
+        int in_act = n_act;
+        for (int it = 0; it < inner_max && in_act > 0 && total_inner < maxit;) {
+            {
+                SceProf pf(KP_SPMV3, st, S.vb(0, 5 * 4.0));
+                spmv_dot3_kernel<<<g0, TPB3, 0, st>>>(S.gx[0], S.gy[0], S.gz[0], S.p, S.q, n0,
+                                                      S.part, S.nblk0, S.sc.act_in);
+            }
+            S.reduce(R3_ALPHA, S.sc.act_in);
+            {
+                SceProf pf(KP_VEC3, st, S.vb(0, 6 * 4.0));
+                axpy2_3_kernel<<<g0, TPB3, 0, st>>>(S.d, S.b[0], S.p, S.q, S.sc.alpha, V0, S.part,
+                                                    S.nblk0, S.sc.act_in);
+            }
+            SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
+            S.reduce(R3_RR, S.sc.act_in);
+            ++total_inner;
+            ++it;
+            if (it % check_every == 0) {
+                SCE_TRY(S.read_counter(&in_act));
+                if (in_act == 0) break;
+            }
+            S.vcycle(S.sc.act_in);
+            {
+                SceProf pf(KP_DOT, st, S.vb(0, 8.0));
+                dot3_kernel<<<g0, TPB3, 0, st>>>(S.b[0], S.z[0], V0, S.part, S.nblk0, S.sc.act_in);
+            }
+            S.reduce(R3_BETA, S.sc.act_in);
+            {
+                SceProf pf(KP_VEC3, st, S.vb(0, 3 * 4.0));
+                pupdate3_kernel<<<g0, TPB3, 0, st>>>(S.p, S.z[0], S.sc.beta, V0, 0, S.sc.act_in);
+            }
+        }
+        SCE_CUDA(cudaGetLastError());
+        {
+            SceProf pf(KP_OUTER3, st, S.vb(0, 2 * 8.0 + 4.0));
+            outer_update3_kernel<<<g0, TPB3, 0, st>>>(S.u, S.d, n0, S.sc.act_out);
+        }
+        SCE_TRY(outer_residual(S.sc.act_out, R3_ORR));
+        SCE_TRY(S.read_counter(&n_act));
+    }
+
+    {
+        SceProf pf(KP_QOI, st, S.vb(0, 16.0));
+        qoi3_partial_kernel<<<g0, TPB3, 0, st>>>(S.g64x, S.u, n0, fh2, S.part, S.part2, S.nblk0);
+    }
+    int *misc = S.sint + 4 * count + 1;   // [failed, max iters, total iters]
+    SCE_CUDA(cudaMemsetAsync(misc, 0, 3 * sizeof(int), st));
+    qoi3_final_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(
+        S.part, S.part2, S.nblk0, count, S.u, n0, S.sc, rtol2, qoi, iters, status, misc);
+    SCE_CUDA(cudaGetLastError());
+    if (u_out)
+        SCE_CUDA(cudaMemcpyAsync(u_out, S.u, (size_t)count * V0 * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+    int hm[3] = {0, 0, 0};
+    SCE_CUDA(cudaMemcpyAsync(hm, misc, sizeof(hm), cudaMemcpyDeviceToHost, st));
+    SCE_CUDA(cudaStreamSynchronize(st));
+    if (misc_out) {
+        misc_out[0] = hm[0];
+        misc_out[1] = hm[1];
+        misc_out[2] = hm[2];
+    }
+    return hm[0] > 0 ? CE_ERR_NOT_CONVERGED : CE_OK;
+}
+
+// samples per solve call: device memory bounded to about 8 GB
+int chunk3(int n) {
+    const double V = (double)(n + 1) * (n + 1) * (n + 1);
+    const double per = V * (9 * 4.0 + 4 * 8.0) * 1.15 + 1024;
+    return (int)std::max(1.0, std::min(65535.0, std::floor(8e9 / per)));
+}
+
+int solve3_batched(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
+                   int *status, double *u_out, cudaStream_t st, int *misc_out) {
+    const int chunk = chunk3(p->n);
+    const long long V = (long long)(p->n + 1) * (p->n + 1) * (p->n + 1);
+    int worst = CE_OK;
+    int tot[3] = {0, 0, 0};
+    for (int c0 = 0; c0 < count; c0 += chunk) {
+        const int cn = std::min(chunk, count - c0);
+        int m[3] = {0, 0, 0};
+        const int rc = solve3(p, k + (size_t)c0 * V, cn, qoi + 3 * (size_t)c0,
+                              iters ? iters + c0 : nullptr, status ? status + c0 : nullptr,
+                              u_out ? u_out + (size_t)c0 * V : nullptr, st, m);
+        if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) return rc;
+        if (rc != CE_OK) worst = rc;
+        tot[0] += m[0];
+        tot[1] = std::max(tot[1], m[1]);
+        tot[2] += m[2];
+    }
+    if (misc_out) {
+        misc_out[0] = tot[0];
+        misc_out[1] = tot[1];
+        misc_out[2] = tot[2];
+    }
+    return worst;
+}
+
+}  // namespace
+
+extern "C" int darcy3_solve_batch(const darcy_problem *p, const float *k, int count, double *qoi,
+                                  int *iters, int *status, double *u_out, void *stream) {
+    if (!p || !k || !qoi || count < 0) return CE_ERR_INVALID_ARG;
+    if (!is_pow2(p->n) || p->n < 2 || p->n > 256 || p->precision != 32 || !(p->rtol > 0))
+        return CE_ERR_INVALID_ARG;
+    if (count == 0) return CE_OK;
+    return solve3_batched(p, k, count, qoi, iters, status, u_out, as_stream(stream), nullptr);
+}
+
+extern "C" int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, uint64_t seed,
+                                    uint32_t level, uint64_t first_sample, int count,
+                                    int qoi_index, mlmc_level_sums *out, double *Y,
+                                    void *stream) {
+    if (!e || !p || !out || count < 0 || qoi_index < 0 || qoi_index > 2) return CE_ERR_INVALID_ARG;
+    ce_embedding_info info;
+    SCE_TRY(ce3_get_info(e, &info));
+    if (p->n != info.n || p->precision != 32 || !(p->rtol > 0)) return CE_ERR_INVALID_ARG;
+    if (level > 0 && p->n < 4) return CE_ERR_INVALID_ARG;
+    *out = mlmc_level_sums{};
+    if (count == 0) return CE_OK;
+    cudaStream_t st = as_stream(stream);
+    const int n = p->n, nc = n / 2;
+    const long long Vf = (long long)(n + 1) * (n + 1) * (n + 1);
+    const long long Vc = (long long)(nc + 1) * (nc + 1) * (nc + 1);
+    const int chunk = std::min(count, std::max(1, chunk3(n) / 2));
+    float *kf = nullptr, *kc = nullptr;
+    double *qf = nullptr, *qc = nullptr;
+    int rc = sce_alloc_t(&kf, (size_t)chunk * Vf, st);
+    if (rc == CE_OK && level > 0) rc = sce_alloc_t(&kc, (size_t)chunk * Vc, st);
+    if (rc == CE_OK) rc = sce_alloc_t(&qf, (size_t)chunk * 3, st);
+    if (rc == CE_OK && level > 0) rc = sce_alloc_t(&qc, (size_t)chunk * 3, st);
+    std::vector<double> hf((size_t)chunk * 3), hc((size_t)chunk * 3), hy(chunk);
+    darcy_problem pc = *p;
+    pc.n = nc;
+    int worst = CE_OK;
+    for (int c0 = 0; c0 < count && rc == CE_OK; c0 += chunk) {
+        const int cn = std::min(chunk, count - c0);
+        rc = ce3_sample_batch(e, seed, level, first_sample + c0, cn, kf, level > 0 ? kc : nullptr,
+                              stream);
+        int m[3] = {0, 0, 0};
+        if (rc == CE_OK) {
+            rc = solve3_batched(p, kf, cn, qf, nullptr, nullptr, nullptr, st, m);
+            out->n_failed += m[0];
+            out->max_iters = std::max(out->max_iters, m[1]);
+            out->total_iters += m[2];
+            if (rc == CE_ERR_NOT_CONVERGED) {
+                worst = rc;
+                rc = CE_OK;
+            }
+        }
+        if (rc == CE_OK && level > 0) {
+            rc = solve3_batched(&pc, kc, cn, qc, nullptr, nullptr, nullptr, st, m);
+            out->n_failed += m[0];
+            out->max_iters = std::max(out->max_iters, m[1]);
+            out->total_iters += m[2];
+            if (rc == CE_ERR_NOT_CONVERGED) {
+                worst = rc;
+                rc = CE_OK;
+            }
+        }
+        if (rc != CE_OK) break;
+        if (cudaMemcpyAsync(hf.data(), qf, (size_t)cn * 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                            st) != cudaSuccess ||
+            (level > 0 && cudaMemcpyAsync(hc.data(), qc, (size_t)cn * 3 * sizeof(double),
+                                          cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = CE_ERR_CUDA;
+            break;
+        }
+        // level sums in sample order (Eq. (3.5))
+        for (int i = 0; i < cn; ++i) {
+            const double Qf = hf[3 * (size_t)i + qoi_index];
+            const double Yi = level > 0 ? Qf - hc[3 * (size_t)i + qoi_index] : Qf;
+            hy[i] = Yi;
+            out->sumY += Yi;
+            out->sumY2 += Yi * Yi;
+            out->sumQf += Qf;
+            out->sumQf2 += Qf * Qf;
+        }
+        out->N += cn;
+        if (Y && cudaMemcpyAsync(Y + c0, hy.data(), (size_t)cn * sizeof(double),
+                                 cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            rc = CE_ERR_CUDA;
+            break;
+        }
+        if (Y && cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = CE_ERR_CUDA;
+            break;
+        }
+    }
+    sce_free(kf, st);
+    sce_free(kc, st);
+    sce_free(qf, st);
+    sce_free(qc, st);
+    cudaStreamSynchronize(st);
+    return rc != CE_OK ? rc : worst;
+}

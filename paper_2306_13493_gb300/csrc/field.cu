@@ -142,8 +142,8 @@ __global__ void sqrt_table_kernel(const double *lam, const unsigned char *mask, 
 // Keep-mask of §2.4 / Algorithm 2 step 4(b) with the tie rule: a = keep-th
 // largest, b = (keep+1)-th largest; if a - b > tol |a| keep Lambda >= a, else
 // keep Lambda > a + tol |a| (the straddling tie group is dropped whole).
-static long long keep_mask(const std::vector<double> &L, long long keep, double tol,
-                           std::vector<unsigned char> &mask) {
+long long sce_keep_mask(const std::vector<double> &L, long long keep, double tol,
+                        std::vector<unsigned char> &mask) {
     const long long s = (long long)L.size();
     mask.assign(s, 1);
     if (keep < 0 || keep >= s) return s;
@@ -269,12 +269,12 @@ extern "C" int ce_setup_embedding(const ce_cov *cov, int n, const ce_pad *pad,
             cudaStreamSynchronize(st) != cudaSuccess)
             return fail(CE_ERR_CUDA);
     }
-    e->keep_eff_fine = need_f ? keep_mask(hl, keep_f, tol, e->mask_f) : s;
+    e->keep_eff_fine = need_f ? sce_keep_mask(hl, keep_f, tol, e->mask_f) : s;
     if (need_c && need_f && keep_c == keep_f) {
         e->mask_c = e->mask_f;
         e->keep_eff_coarse = e->keep_eff_fine;
     } else {
-        e->keep_eff_coarse = need_c ? keep_mask(hl, keep_c, tol, e->mask_c) : s;
+        e->keep_eff_coarse = need_c ? sce_keep_mask(hl, keep_c, tol, e->mask_c) : s;
     }
     if (!need_f) e->mask_f.assign(s, 1);
     if (!need_c) e->mask_c.assign(s, 1);

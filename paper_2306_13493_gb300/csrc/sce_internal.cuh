@@ -41,6 +41,12 @@ static inline int ilog2(long long v) {
 // must not lower it between another thread's setting and its launch.
 int sce_raise_smem_limit(const void *func, size_t bytes);
 
+// Keep-mask of the smoothing step (Algorithm 2 step 4(b)) over the flattened
+// eigenvalues L: the keep largest, a tie group straddling the cut dropped whole
+// (relative tolerance tol).  keep < 0 or >= L.size(): all.  Returns the count kept.
+long long sce_keep_mask(const std::vector<double> &L, long long keep, double tol,
+                        std::vector<unsigned char> &mask);
+
 // Stream-ordered device allocation from the device's default pool.
 int sce_alloc(void **p, size_t bytes, cudaStream_t st);
 int sce_free(void *p, cudaStream_t st);
@@ -79,7 +85,10 @@ struct ce_embedding_s {
 enum SceKernel {
     KP_ROW = 0, KP_COL, KP_COND, KP_COARSEN, KP_SMOOTH, KP_RESTRICT, KP_PROLONG, KP_COARSEST,
     KP_SPMV, KP_AXPY, KP_DOT, KP_PUPDATE, KP_COPY, KP_REDUCE, KP_OUTER_RES, KP_OUTER_UPD, KP_QOI,
-    KP_SETUP, KP_NORMALS, KP_LEVEL, KP_SMALL, KP_MG_DOWN, KP_MG_UP, KP_MG_TAIL, KP_COUNT_
+    KP_SETUP, KP_NORMALS, KP_LEVEL, KP_SMALL, KP_MG_DOWN, KP_MG_UP, KP_MG_TAIL,
+    // three-dimensional path
+    KP_X3, KP_Y3, KP_Z3, KP_COND3, KP_SMOOTH3, KP_RESID3, KP_RESTRICT3, KP_PROLONG3, KP_SPMV3,
+    KP_VEC3, KP_OUTER3, KP_COUNT_
 };
 
 bool sce_prof_on();

@@ -145,6 +145,22 @@ _SIGS = {
                                             ctypes.c_int, ctypes.POINTER(mlmc_level_task),
                                             ctypes.c_int, ctypes.c_int, _P]),
     "mlmc_optimal_samples": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_double, _P]),
+    "ce3_setup_embedding": (ctypes.c_int, [ctypes.POINTER(ce_cov), ctypes.c_int,
+                                           ctypes.POINTER(ce_pad), ctypes.POINTER(ce_smoothing),
+                                           _P, ctypes.POINTER(_P),
+                                           ctypes.POINTER(ce_embedding_info)]),
+    "ce3_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ce_embedding_info)]),
+    "ce3_get_eigenvalues": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "ce3_get_mask": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "ce3_destroy": (None, [_P]),
+    "ce3_sample_batch": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                        ctypes.c_int, _P, _P, _P]),
+    "darcy3_solve_batch": (ctypes.c_int, [ctypes.POINTER(darcy_problem), _P, ctypes.c_int, _P,
+                                          _P, _P, _P, _P]),
+    "mlmc3_level_estimate": (ctypes.c_int, [_P, ctypes.POINTER(darcy_problem), ctypes.c_uint64,
+                                            ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.c_int, ctypes.POINTER(mlmc_level_sums), _P,
+                                            _P]),
     "ce_destroy": (None, [_P]),
     "ce_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sce_last_error": (ctypes.c_char_p, []),
@@ -447,6 +463,72 @@ def mlmc_level_estimate_qmc(q, seed, level, shift, first_point, count, qoi_index
                                                _ptr(Y), _ptr(qoi_f), _ptr(qoi_c),
                                                _stream(stream, Y)),
                 "mlmc_level_estimate_qmc", allow)
+    return out, st
+
+
+class Embedding3(Embedding):
+    """Owner of a ce3_embedding_t handle (three-dimensional grids)."""
+
+    def close(self):
+        if self.handle:
+            load().ce3_destroy(self.handle)
+            self.handle = None
+
+
+def ce3_setup_embedding(kind, nu, lam, sigma2, n, pad_mode=CE_PAD_DOUBLING, J=-1, max_P=512,
+                        keep_fine=-1, keep_coarse=-1, tie_rel_tol=1e-10, stream=None):
+    lib = load()
+    cov = ce_cov(kind, nu, lam, sigma2)
+    pad = ce_pad(pad_mode, J, max_P)
+    sm = ce_smoothing(keep_fine, keep_coarse, tie_rel_tol)
+    h = ctypes.c_void_p()
+    info = ce_embedding_info()
+    _check(lib.ce3_setup_embedding(ctypes.byref(cov), n, ctypes.byref(pad), ctypes.byref(sm),
+                                   _stream(stream), ctypes.byref(h), ctypes.byref(info)),
+           "ce3_setup_embedding")
+    return Embedding3(h, info)
+
+
+def ce3_get_eigenvalues(emb, out, stream=None):
+    """out: torch float64 tensor of P^3 elements (device or host)."""
+    _check(load().ce3_get_eigenvalues(emb.handle, _ptr(out), int(out.is_cuda),
+                                      _stream(stream, out)), "ce3_get_eigenvalues")
+    return out
+
+
+def ce3_get_mask(emb, which, out):
+    """out: contiguous host uint8 array/tensor of P^3 elements."""
+    ptr = out.ctypes.data if hasattr(out, "ctypes") else out.data_ptr()
+    _check(load().ce3_get_mask(emb.handle, which, ctypes.c_void_p(ptr)), "ce3_get_mask")
+    return out
+
+
+def ce3_sample_batch(emb, seed, level, first_sample, count, k_fine=None, k_coarse=None,
+                     stream=None):
+    """FP32 fields: k_fine (count*(n+1)^3), k_coarse (count*(n/2+1)^3), torch float32 on the device."""
+    t = k_fine if k_fine is not None else k_coarse
+    _check(load().ce3_sample_batch(emb.handle, seed, level, first_sample, count, _ptr(k_fine),
+                                   _ptr(k_coarse), _stream(stream, t)), "ce3_sample_batch")
+
+
+def darcy3_solve_batch(n, k, count, qoi, f=0.0, rtol=1e-10, maxit=1000, iters=None, status=None,
+                       u_out=None, stream=None, allow_not_converged=False):
+    prob = darcy_problem(n, f, rtol, maxit, 32)
+    allow = (CE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    return _check(load().darcy3_solve_batch(ctypes.byref(prob), _ptr(k), count, _ptr(qoi),
+                                            _ptr(iters), _ptr(status), _ptr(u_out),
+                                            _stream(stream, k)), "darcy3_solve_batch", allow)
+
+
+def mlmc3_level_estimate(emb, seed, level, first_sample, count, qoi_index=QOI_OUTFLOW, f=0.0,
+                         rtol=1e-10, maxit=1000, Y=None, stream=None, allow_not_converged=False):
+    prob = darcy_problem(emb.n, f, rtol, maxit, 32)
+    out = mlmc_level_sums()
+    allow = (CE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    st = _check(load().mlmc3_level_estimate(emb.handle, ctypes.byref(prob), seed, level,
+                                            first_sample, count, qoi_index, ctypes.byref(out),
+                                            _ptr(Y), _stream(stream, Y)),
+                "mlmc3_level_estimate", allow)
     return out, st
 
 

@@ -107,3 +107,29 @@ def test_estimate_levels_rejects_bad_arguments_on_the_host():
     assert lib.mlmc_estimate_levels(ctypes.byref(bad), 1, 0, tasks, 0, 4, None) == \
         sce.CE_ERR_INVALID_ARG
     assert lib.mlmc_estimate_levels(ctypes.byref(prob), 1, 0, tasks, 0, 4, None) == sce.CE_OK
+
+
+def test_three_dimensional_entry_points_reject_bad_arguments_on_the_host():
+    """Argument checks of the d = 3 entry points return before any CUDA call."""
+    from paper_2306_13493_gb300 import sce
+    lib = sce.load()
+    cov = sce.ce_cov(0, 0.5, 0.1, 1.0)
+    pad = sce.ce_pad(sce.CE_PAD_DOUBLING, -1, 512)
+    h = ctypes.c_void_p()
+    for n in (3, 1, 512):                                  # not a power of two / out of range
+        assert lib.ce3_setup_embedding(ctypes.byref(cov), n, ctypes.byref(pad), None, None,
+                                       ctypes.byref(h), None) == sce.CE_ERR_INVALID_ARG
+    bad_nu = sce.ce_cov(0, 0.7, 0.1, 1.0)
+    assert lib.ce3_setup_embedding(ctypes.byref(bad_nu), 8, ctypes.byref(pad), None, None,
+                                   ctypes.byref(h), None) == sce.CE_ERR_INVALID_ARG
+    fake = ctypes.c_void_p(16)                             # never dereferenced
+    for prob in (sce.darcy_problem(8, 1.0, 1e-10, 100, 64),     # FP32 fields only
+                 sce.darcy_problem(6, 1.0, 1e-10, 100, 32),
+                 sce.darcy_problem(8, 1.0, 0.0, 100, 32)):
+        assert lib.darcy3_solve_batch(ctypes.byref(prob), fake, 1, fake, None, None, None,
+                                      None) == sce.CE_ERR_INVALID_ARG
+    out = sce.mlmc_level_sums()
+    prob = sce.darcy_problem(8, 1.0, 1e-10, 100, 32)
+    assert lib.mlmc3_level_estimate(None, ctypes.byref(prob), 1, 0, 0, 4, 0, ctypes.byref(out),
+                                    None, None) == sce.CE_ERR_INVALID_ARG
+    assert lib.ce3_sample_batch(None, 1, 0, 0, 4, None, None, None) == sce.CE_ERR_INVALID_ARG
