@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--concurrency", type=int, default=8,
                     help="levels in flight at once (each on its own streams); 1 = one after another")
-    ap.add_argument("--study", default=None, choices=[None, "precision", "smoothing", "qmc"],
+    ap.add_argument("--study", default=None,
+                    choices=[None, "precision", "smoothing", "qmc", "3d"],
                     help="run a study instead of the benchmark (prints its own JSON line)")
     ap.add_argument("--study-count", type=int, default=None)
     ap.add_argument("--study-oracle", type=int, default=None)
@@ -68,16 +69,53 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="multiply the per-level sample counts (tests only)")
-    ap.add_argument("--case", default=None, choices=[None, "darcy", "field"],
+    ap.add_argument("--case", default=None, choices=[None, "darcy", "field", "darcy3", "field3"],
                     help="time one kernel family on one batch (profiling driver)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--count", type=int, default=64)
     return ap.parse_args()
 
 
+def run_case3(args):
+    """One batch of the three-dimensional workload's field at n cells per side,
+    then one Darcy solve (a small launch sequence for kernel captures)."""
+    import numpy as np
+    import torch
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    sce.load()
+    wl = workloads.THREE_D
+    n, count = args.n, args.count
+    emb = sce.ce3_setup_embedding(0, wl.nu, wl.lam, wl.sigma2, n, pad_mode=sce.CE_PAD_SMOOTH)
+    k = torch.empty(count, n + 1, n + 1, n + 1, dtype=torch.float32, device="cuda")
+    qoi = torch.empty(count, 3, dtype=torch.float64, device="cuda")
+    iters = torch.empty(count, dtype=torch.int32, device="cuda")
+    times = []
+    for rep in range(1 + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if args.case == "field3" or rep == 0:
+            sce.ce3_sample_batch(emb, wl.seed, 0, rep * count, count, k)
+        if args.case == "darcy3":
+            sce.darcy3_solve_batch(n, k, count, qoi, f=wl.f, rtol=wl.rtol, iters=iters,
+                                   allow_not_converged=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep > 0:
+            times.append(e0.elapsed_time(e1))
+    it = iters.cpu().numpy() if args.case == "darcy3" else np.zeros(1)
+    print(json.dumps({"case": args.case, "n": n, "count": count,
+                      "ms": statistics.mean(times) if times else None,
+                      "iters_mean": float(it.mean()), "iters_max": int(it.max())}), flush=True)
+    emb.close()
+    return 0
+
+
 def run_case(args):
     """One batch of the oscillatory field at n cells: fields, then one Darcy
     solve (the small, fixed launch sequence used for kernel captures)."""
+    if args.case in ("darcy3", "field3"):
+        return run_case3(args)
     import torch
     from paper_2306_13493_gb300 import build, sce
     build.build_library()
@@ -418,6 +456,188 @@ def qmc_study(args):
         lat.close()
         emb.close()
     print(json.dumps(out), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ three dimensions
+_ORACLE3 = None
+
+
+def _oracle3_init(wl):
+    global _ORACLE3
+    try:
+        import math as _m
+        from oracle import embedding as oem
+        from oracle import field3d as of3
+        levels = {}
+        for l in range(len(wl.cpu_samples)):
+            e = of3.setup_embedding3(0, wl.nu, wl.lam, wl.sigma2, wl.n0 << l, oem.PAD_SMOOTH)
+            s = e.Lam.size
+            keep = s - _m.isqrt(s)
+            mask = oem.smoothing_mask(e.Lam, keep)
+            levels[l] = (e, mask)
+        _ORACLE3 = (wl, levels)
+    except Exception as exc:
+        _ORACLE3 = exc
+
+
+def _oracle3_task(task):
+    from oracle import darcy3d as od3
+    from oracle import field3d as of3
+    if isinstance(_ORACLE3, Exception):
+        raise RuntimeError(f"oracle worker set-up failed: {_ORACLE3!r}")
+    wl, levels = _ORACLE3
+    l, sample = task
+    e, mask = levels[l]
+    t0 = time.perf_counter()
+    kf, kc = of3.sample_k3(e, mask, mask if l > 0 else None, wl.seed, l, sample, 64)
+    y = od3.solve_qois3(kf, wl.f)[wl.qoi]
+    if l > 0:
+        y -= od3.solve_qois3(kc, wl.f)[wl.qoi]
+    return l, time.perf_counter() - t0
+
+
+def _oracle3_ready(_):
+    time.sleep(0.2)
+    return isinstance(_ORACLE3, Exception)
+
+
+def three_d_study(args):
+    """workloads.THREE_D: one step = one MLMC sweep over the 3D levels through
+    mlmc3_level_estimate (fields by the three-pass FFT sampler, Kuhn-P1 solves
+    on the fine and coarse grids, level sums).  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    sce.load()
+    wl = workloads.THREE_D
+    dev = torch.device("cuda", 0)
+    L = len(wl.N) - 1
+    t0 = time.perf_counter()
+    embs = []
+    for (l, n, N) in wl.levels:
+        embs.append(sce.ce3_setup_embedding(
+            0, wl.nu, wl.lam, wl.sigma2, n, pad_mode=sce.CE_PAD_SMOOTH,
+            keep_fine=-1 if l == L else sce.CE_KEEP_TAU_SQRT_S,
+            keep_coarse=sce.CE_KEEP_TAU_SQRT_S))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+
+    def sweep(step):
+        outs = []
+        for (l, n, N) in wl.levels:
+            o, _ = sce.mlmc3_level_estimate(embs[l], wl.seed, l, step * N, N, qoi_index=wl.qoi,
+                                            f=wl.f, rtol=wl.rtol, maxit=2000,
+                                            allow_not_converged=True)
+            outs.append(o)
+        return outs
+
+    steps = args.steps if args.steps else 3
+    warmup = max(3, args.warmup if args.warmup is not None else 3)
+    for w in range(warmup):
+        sweep(100000 + w)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    acc = [[0, 0.0, 0.0, 0, 0] for _ in wl.N]     # N, sumY, sumY2, failed, max iters
+    ms = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    for k in range(steps):
+        flush.fill_(k & 255)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        outs = sweep(k)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        for l, o in enumerate(outs):
+            a = acc[l]
+            a[0] += o.N
+            a[1] += o.sumY
+            a[2] += o.sumY2
+            a[3] += o.n_failed
+            a[4] = max(a[4], o.max_iters)
+    clk = clocks.stop()
+    ms_step = statistics.mean(ms)
+    total = sum(wl.N)
+
+    sce.sce_profile_enable(1)
+    sweep(900000)
+    prof = sce.sce_profile_read()
+    sce.sce_profile_enable(0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    prof = {k: v for k, v in prof.items() if v[2] > 0}
+    ptot = sum(v[0] for v in prof.values())
+    kernels = {name: {"ms": round(m, 3), "launches": nl, "share": round(m / ptot, 4),
+                      "GBps": round(by / (m * 1e6), 1) if m > 0 else None}
+               for name, (m, by, nl) in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    roof = None
+    hbm_kernels = {k: v for k, v in prof.items() if k not in ("ce3_x", "reduce", "mg_coarsest")}
+    if hbm_kernels:
+        name, (m, by, nl) = max(hbm_kernels.items(), key=lambda kv: kv[1][0])
+        ach = by / (m * 1e6)
+        roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+                "algorithmic_bytes_per_launch": round(by / nl), "peak_source": peak_src,
+                "avg_launch_us": round(1000 * m / nl, 2),
+                "timed": "one extra sweep with CUDA events around every launch"}
+    x3 = prof.get("ce3_x")
+    per_level = []
+    for (l, n, N), a in zip(wl.levels, acc):
+        mean = a[1] / a[0]
+        var = (a[2] - a[0] * mean * mean) / (a[0] - 1)
+        per_level.append({"level": l, "n": n, "P": embs[l].P, "N": N, "mean_Y": mean,
+                          "var_Y": var, "failed": a[3], "max_iters": a[4]})
+    line = {"study": "3d", "metric": "fine-level samples/s (3D field+Darcy solve)",
+            "value": total / (ms_step / 1000.0), "unit": "samples/s", "n_gpus": 1,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": wl.describe(),
+                       "l2": "flushed before every timed step (258 MB write)"},
+            "setup_seconds": round(setup_s, 3), "clocks": clk, "per_level": per_level,
+            "kernels": kernels, "roofline": roof,
+            "field_x_pass": ({"ms": round(x3[0], 3), "launches": x3[2],
+                              "bound": "alu (Philox + Box-Muller + FFT)"} if x3 else None)}
+    if not args.no_cpu_baseline:
+        import multiprocessing as mp
+        cores = os.cpu_count() or 1
+        os.environ.update({"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1",
+                           "MKL_NUM_THREADS": "1"})
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores, initializer=_oracle3_init, initargs=(wl,)) as pool:
+            pool.map(_oracle3_ready, range(2 * cores), chunksize=1)
+            tasks = [(l, 20_000_000 + i) for l in range(len(wl.cpu_samples))
+                     for i in range(wl.cpu_samples[l])]
+            tw = time.perf_counter()
+            res = pool.map(_oracle3_task, sorted(tasks, key=lambda t: -t[0]), chunksize=1)
+            wall = time.perf_counter() - tw
+        per = {}
+        for l, t in res:
+            per.setdefault(l, []).append(t)
+        mean = {l: sum(v) / len(v) for l, v in per.items()}
+        lv = range(len(wl.cpu_samples))
+        sec = sum(wl.N[l] * mean[l] for l in lv) / sum(wl.N[l] for l in lv)
+        line["cpu_baseline"] = {
+            "value": cores / sec, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": (f"oracle (numpy/scipy FP64, direct sparse solves) on {cores} host cores, "
+                       f"{'/'.join(map(str, wl.cpu_samples))} samples on levels "
+                       f"0..{len(wl.cpu_samples) - 1} (n = "
+                       f"{'/'.join(str(wl.n0 << l) for l in lv)}), per-sample times scaled to "
+                       f"their N_l mix; level 3 not sampled (one direct solve on 65^3 takes "
+                       f"minutes), so this rate is an upper bound for the full mix"),
+            "wall_seconds": round(wall, 2),
+            "per_level_seconds": {str(l): round(mean[l], 4) for l in lv}}
+    for e in embs:
+        e.close()
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -944,6 +1164,8 @@ def main():
         return smoothing_study(args)
     if args.study == "qmc":
         return qmc_study(args)
+    if args.study == "3d":
+        return three_d_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

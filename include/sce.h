@@ -389,7 +389,7 @@ int ce_autotune_fft(ce_embedding_t e, int precision, int count, int reps, void *
  *   - embedding side P = 2(n + J), a power of two, 4 <= P <= 512; s = P^3,
  *     array index k1 + P k2 + P^2 k3;
  *   - fields are FP32; the solver refines its FP32 multigrid-CG corrections
- *     against an FP64 residual.
+ *     against a float-float residual.
  */
 typedef struct ce3_embedding_s *ce3_embedding_t;
 
@@ -433,8 +433,8 @@ int ce3_sample_batch(ce3_embedding_t e, uint64_t seed, uint32_t level, uint64_t 
  * a+(1,1,1), pi a permutation of the axes), k averaged over each
  * tetrahedron's four vertices (nodal quadrature).  Only axis-parallel edges
  * couple, so the operator is a seven-point stencil.  Solved by FP32
- * multigrid-preconditioned CG corrections of an FP64 residual (iterative
- * refinement) to ||r|| <= rtol ||r_0||.
+ * multigrid-preconditioned CG corrections of a float-float residual (FP32
+ * pairs, ~48 significant bits; iterative refinement) to ||r|| <= rtol ||r_0||.
  *   p      : p->n as above, p->precision must be 32
  *   k      : device float[count*(n+1)^3]
  *   qoi    : device double[count*3]: [outflow through x1 = 1 (consistent

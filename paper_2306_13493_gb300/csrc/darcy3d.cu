@@ -21,19 +21,36 @@
 // and load F'_p = f h^2 N(p)/24, N(p) = number of tetrahedra at p (6 for the
 // cell corners a and a+(1,1,1) of each adjacent cell, 2 for the others).
 //
-// Solver: iterative refinement; the residual F' - A'u is formed in FP64 from
-// FP64 conductances and u, the correction solves A'd = r by FP32 CG
+// Solver: iterative refinement; the residual F' - A'u is formed in
+// float-float (pairs of FP32 numbers, ~48 significant bits) from float-float
+// conductances and u, the correction solves A'd = r by FP32 CG
 // preconditioned with one geometric multigrid V(1,1) cycle (red-black
 // Gauss-Seidel in the (i+j+k) parity, full-weighting restriction, trilinear
 // prolongation, coarse conductances from two fine edges in series averaged
 // over the 3x3 transverse lines with weights 1, 1/2; exact solve of the 9
 // unknowns of the 2-cell grid).  Per-sample flags stop converged samples, so a
 // sample's result does not depend on the batch it is solved in.
+//
+// The multigrid cycle reads FP16 copies of its conductances (the smoother,
+// residual and transfers are streaming passes); it is then a fixed symmetric
+// preconditioner for a nearby operator, while CG applies the FP32 operator and
+// the refinement the FP64 one, so the converged solution is unchanged.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "ff.cuh"
 #include "sce_internal.cuh"
+
+using sce::ff;
+using sce::ff_add;
+using sce::ff_add_f;
+using sce::ff_from_double;
+using sce::ff_mul;
+using sce::ff_sub;
+using sce::two_prod;
 
 namespace {
 
@@ -42,11 +59,13 @@ constexpr int TPB3 = 256;
 constexpr int VPT3 = 8;
 constexpr int EPB3 = TPB3 * VPT3;
 
-__device__ __forceinline__ void decode3(long long v, int w, int *i, int *j, int *k) {
-    const long long r = v / w;
-    *i = (int)(v - r * w);
-    *k = (int)(r / w);
-    *j = (int)(r - (long long)(*k) * w);
+// vertex index within one sample -> (i, j, k); 32-bit arithmetic (a sample
+// has at most 257^3 vertices)
+__device__ __forceinline__ void decode3(int v, int w, int *i, int *j, int *k) {
+    const unsigned r = (unsigned)v / (unsigned)w;
+    *i = v - (int)r * w;
+    *k = (int)(r / (unsigned)w);
+    *j = (int)r - *k * w;
 }
 
 template <int E> struct Axes {
@@ -58,7 +77,10 @@ __device__ __forceinline__ long long stride3(int axis, int w) {
 }
 
 // S of the edge along axis E from (c0, c1, c2) (see the file comment); 0 on
-// the last plane of E.  k in FP32, S exact in FP64 (at most 24 terms).
+// the last plane of E.  The at most 24 FP32 terms are summed in float-float
+// (each term added with an error-free two-sum), so the FP64 value hi + lo is
+// the sum to ~2^-48 relative without FP64 additions (FP64 runs at a small
+// fraction of the FP32 rate on this GPU).
 template <int E>
 __device__ __forceinline__ double edge_sum3(const float *__restrict__ ks, int n, const int c[3],
                                             long long v) {
@@ -66,15 +88,38 @@ __device__ __forceinline__ double edge_sum3(const float *__restrict__ ks, int n,
     if (c[E] >= n) return 0.0;
     const int w = n + 1;
     const long long se = stride3(E, w), s1 = stride3(A1, w), s2 = stride3(A2, w);
-    auto K = [&](int de, int d1, int d2) { return (double)ks[v + de * se + d1 * s1 + d2 * s2]; };
+    auto K = [&](int de, int d1, int d2) { return ks[v + de * se + d1 * s1 + d2 * s2]; };
     const bool lo1 = c[A1] > 0, hi1 = c[A1] < n, lo2 = c[A2] > 0, hi2 = c[A2] < n;
-    const double base = K(0, 0, 0) + K(1, 0, 0);
-    double S = 0.0;
-    if (hi1 && hi2) S += 2.0 * base + K(1, 1, 0) + K(1, 0, 1) + 2.0 * K(1, 1, 1);
-    if (lo1 && hi2) S += base + K(0, -1, 0) + K(1, 0, 1);
-    if (hi1 && lo2) S += base + K(0, 0, -1) + K(1, 1, 0);
-    if (lo1 && lo2) S += 2.0 * base + 2.0 * K(0, -1, -1) + K(0, 0, -1) + K(0, -1, 0);
-    return S;
+    const float k0 = K(0, 0, 0), ke = K(1, 0, 0);
+    int cnt = 0;   // multiplicity of k0 and ke: one per tetrahedron
+    ff S = {0.0f, 0.0f};
+    if (hi1 && hi2) {
+        cnt += 2;
+        S = ff_add_f(S, K(1, 1, 0));
+        S = ff_add_f(S, K(1, 0, 1));
+        S = ff_add_f(S, 2.0f * K(1, 1, 1));
+    }
+    if (lo1 && hi2) {
+        cnt += 1;
+        S = ff_add_f(S, K(0, -1, 0));
+        S = ff_add_f(S, K(1, 0, 1));
+    }
+    if (hi1 && lo2) {
+        cnt += 1;
+        S = ff_add_f(S, K(0, 0, -1));
+        S = ff_add_f(S, K(1, 1, 0));
+    }
+    if (lo1 && lo2) {
+        cnt += 2;
+        S = ff_add_f(S, 2.0f * K(0, -1, -1));
+        S = ff_add_f(S, K(0, 0, -1));
+        S = ff_add_f(S, K(0, -1, 0));
+    }
+    // cnt (k0 + ke): cnt <= 6, each product cnt * k exact in FP32 up to a
+    // 3-bit growth of the significand, added as two terms
+    S = ff_add(S, two_prod((float)cnt, k0));
+    S = ff_add(S, two_prod((float)cnt, ke));
+    return (double)S.hi + (double)S.lo;
 }
 
 // tetrahedra at vertex (i, j, k) of an n-cell grid
@@ -92,13 +137,13 @@ __device__ __forceinline__ int tets_at(int i, int j, int k, int n) {
 // grid: (blocks over vertices, samples); a thread visits VPT3 vertices
 #define FOR_V3(V)                                                                          \
     _Pragma("unroll") for (int e_ = 0; e_ < VPT3; ++e_)                                    \
-        for (long long v = (long long)blockIdx.x * EPB3 + threadIdx.x + (long long)e_ * TPB3; \
-             v < (V); v = (V))
+        if (const int v = (int)blockIdx.x * EPB3 + (int)threadIdx.x + e_ * TPB3; v < (int)(V))
 
-__global__ void cond3_kernel(const float *__restrict__ k, int n, double *__restrict__ g64x,
-                             double *__restrict__ g64y, double *__restrict__ g64z,
-                             float *__restrict__ gx, float *__restrict__ gy,
-                             float *__restrict__ gz) {
+// conductances g = S/24 as float-float: hi (the FP32 operator of CG) and lo
+__global__ void cond3_kernel(const float *__restrict__ k, int n, float *__restrict__ gx,
+                             float *__restrict__ gy, float *__restrict__ gz,
+                             float *__restrict__ glx, float *__restrict__ gly,
+                             float *__restrict__ glz) {
     const int s = blockIdx.y;
     const int w = n + 1;
     const long long V = (long long)w * w * w, off = (long long)s * V;
@@ -109,12 +154,13 @@ __global__ void cond3_kernel(const float *__restrict__ k, int n, double *__restr
         const double x = edge_sum3<0>(ks, n, c, v) * (1.0 / 24.0);
         const double y = edge_sum3<1>(ks, n, c, v) * (1.0 / 24.0);
         const double z = edge_sum3<2>(ks, n, c, v) * (1.0 / 24.0);
-        g64x[off + v] = x;
-        g64y[off + v] = y;
-        g64z[off + v] = z;
-        gx[off + v] = (float)x;
-        gy[off + v] = (float)y;
-        gz[off + v] = (float)z;
+        const ff fx = ff_from_double(x), fy = ff_from_double(y), fz = ff_from_double(z);
+        gx[off + v] = fx.hi;
+        gy[off + v] = fy.hi;
+        gz[off + v] = fz.hi;
+        glx[off + v] = fx.lo;
+        gly[off + v] = fy.lo;
+        glz[off + v] = fz.lo;
     }
 }
 
@@ -152,7 +198,9 @@ __device__ __forceinline__ float coarse_cond3(const float *__restrict__ gf, int 
 
 __global__ void coarsen3_kernel(const float *__restrict__ fx, const float *__restrict__ fy,
                                 const float *__restrict__ fz, int nf, float *__restrict__ cx,
-                                float *__restrict__ cy, float *__restrict__ cz) {
+                                float *__restrict__ cy, float *__restrict__ cz,
+                                __half *__restrict__ hx, __half *__restrict__ hy,
+                                __half *__restrict__ hz) {
     const int s = blockIdx.y;
     const int nc = nf / 2, wc = nc + 1, wf = nf + 1;
     const long long Vc = (long long)wc * wc * wc, Vf = (long long)wf * wf * wf;
@@ -160,61 +208,96 @@ __global__ void coarsen3_kernel(const float *__restrict__ fx, const float *__res
     FOR_V3(Vc) {
         int c[3];
         decode3(v, wc, &c[0], &c[1], &c[2]);
-        cx[s * Vc + v] = coarse_cond3<0>(ax, nf, c);
-        cy[s * Vc + v] = coarse_cond3<1>(ay, nf, c);
-        cz[s * Vc + v] = coarse_cond3<2>(az, nf, c);
+        const float x = coarse_cond3<0>(ax, nf, c), y = coarse_cond3<1>(ay, nf, c),
+                    z = coarse_cond3<2>(az, nf, c);
+        cx[s * Vc + v] = x;
+        cy[s * Vc + v] = y;
+        cz[s * Vc + v] = z;
+        hx[s * Vc + v] = __float2half_rn(x);
+        hy[s * Vc + v] = __float2half_rn(y);
+        hz[s * Vc + v] = __float2half_rn(z);
     }
 }
 
+__device__ __forceinline__ float gval(float x) { return x; }
+__device__ __forceinline__ float gval(__half x) { return __half2float(x); }
+
 // sum of g_e (z_p - z_q) over the six edges of an unknown vertex
-template <typename T>
-__device__ __forceinline__ T apply3(const T *gx, const T *gy, const T *gz, const T *z, long long v,
-                                    int j, int k, int n) {
+template <typename T, typename Tg>
+__device__ __forceinline__ T apply3(const Tg *gx, const Tg *gy, const Tg *gz, const T *z,
+                                    long long v, int j, int k, int n) {
     const int w = n + 1;
     const long long w2 = (long long)w * w;
     const T zc = z[v];
-    T a = gx[v - 1] * (zc - z[v - 1]) + gx[v] * (zc - z[v + 1]);
-    if (j > 0) a += gy[v - w] * (zc - z[v - w]);
-    if (j < n) a += gy[v] * (zc - z[v + w]);
-    if (k > 0) a += gz[v - w2] * (zc - z[v - w2]);
-    if (k < n) a += gz[v] * (zc - z[v + w2]);
+    T a = (T)gval(gx[v - 1]) * (zc - z[v - 1]) + (T)gval(gx[v]) * (zc - z[v + 1]);
+    if (j > 0) a += (T)gval(gy[v - w]) * (zc - z[v - w]);
+    if (j < n) a += (T)gval(gy[v]) * (zc - z[v + w]);
+    if (k > 0) a += (T)gval(gz[v - w2]) * (zc - z[v - w2]);
+    if (k < n) a += (T)gval(gz[v]) * (zc - z[v + w2]);
     return a;
 }
 
-// red-black Gauss-Seidel half-sweep: vertices with (i + j + k) % 2 == color
-__global__ void smooth3_kernel(const float *__restrict__ gx, const float *__restrict__ gy,
-                               const float *__restrict__ gz, const float *__restrict__ b,
+__global__ void half3_kernel(const float *__restrict__ gx, const float *__restrict__ gy,
+                             const float *__restrict__ gz, long long total,
+                             __half *__restrict__ hx, __half *__restrict__ hy,
+                             __half *__restrict__ hz) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        hx[i] = __float2half_rn(gx[i]);
+        hy[i] = __float2half_rn(gy[i]);
+        hz[i] = __float2half_rn(gz[i]);
+    }
+}
+
+// red-black Gauss-Seidel half-sweep of colour `color` ((i + j + k) % 2), one
+// thread per vertex of the colour.  FROM_ZERO: the first half-sweep from
+// z = 0 (z = b/diag at the colour's unknowns and 0 at the other colour's,
+// so z is not read and needs no clearing).  The Dirichlet planes i = 0, n
+// are never written: z there is zeroed once when the hierarchy is allocated.
+template <typename Tg, bool FROM_ZERO>
+__global__ void smooth3_kernel(const Tg *__restrict__ gx, const Tg *__restrict__ gy,
+                               const Tg *__restrict__ gz, const float *__restrict__ b,
                                float *__restrict__ z, int n, int color,
                                const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
     const int w = n + 1, half = (n + 2) / 2;
-    const long long V = (long long)w * w * w, off = (long long)s * V;
-    const long long total = (long long)half * w * w;
-    const long long w2 = (long long)w * w;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long r = t / half;
-        const int ii = (int)(t - r * half);
-        const int k = (int)(r / w), j = (int)(r - (long long)k * w);
-        const int i = 2 * ii + ((color + j + k) & 1);
+    const long long off = (long long)s * w * w * w, w2 = (long long)w * w;
+    const int total = half * w * w;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int r = (int)((unsigned)t / (unsigned)half);
+        const int ii = t - r * half;
+        const int k = (int)((unsigned)r / (unsigned)w), j = r - k * w;
+        const int par = (color + j + k) & 1;
+        const int i = 2 * ii + par;
+        const long long row = off + (long long)r * w;
+        if (FROM_ZERO) {
+            const int io = 2 * ii + (1 - par);
+            if (io >= 1 && io <= n - 1) z[row + io] = 0.0f;
+        }
         if (i < 1 || i > n - 1) continue;
-        const long long v = off + r * w + i;
-        const float cw = gx[v - 1], ce = gx[v];
-        const float cs = j > 0 ? gy[v - w] : 0.0f, cn = j < n ? gy[v] : 0.0f;
-        const float cd = k > 0 ? gz[v - w2] : 0.0f, cu = k < n ? gz[v] : 0.0f;
-        float acc = b[v] + cw * z[v - 1] + ce * z[v + 1];
-        if (j > 0) acc += cs * z[v - w];
-        if (j < n) acc += cn * z[v + w];
-        if (k > 0) acc += cd * z[v - w2];
-        if (k < n) acc += cu * z[v + w2];
-        z[v] = acc / (cw + ce + cs + cn + cd + cu);
+        const long long v = row + i;
+        const float cw = gval(gx[v - 1]), ce = gval(gx[v]);
+        const float cs = j > 0 ? gval(gy[v - w]) : 0.0f, cn = j < n ? gval(gy[v]) : 0.0f;
+        const float cd = k > 0 ? gval(gz[v - w2]) : 0.0f, cu = k < n ? gval(gz[v]) : 0.0f;
+        const float d = cw + ce + cs + cn + cd + cu;
+        if (FROM_ZERO) {
+            z[v] = b[v] / d;
+        } else {
+            float acc = b[v] + cw * z[v - 1] + ce * z[v + 1];
+            if (j > 0) acc += cs * z[v - w];
+            if (j < n) acc += cn * z[v + w];
+            if (k > 0) acc += cd * z[v - w2];
+            if (k < n) acc += cu * z[v + w2];
+            z[v] = acc / d;
+        }
     }
 }
 
-// res = b - A z at the unknowns, 0 on the Dirichlet planes
-__global__ void resid3_kernel(const float *__restrict__ gx, const float *__restrict__ gy,
-                              const float *__restrict__ gz, const float *__restrict__ b,
+// res = b - A z at the unknowns (the Dirichlet planes of res are never read)
+template <typename Tg>
+__global__ void resid3_kernel(const Tg *__restrict__ gx, const Tg *__restrict__ gy,
+                              const Tg *__restrict__ gz, const float *__restrict__ b,
                               const float *__restrict__ z, float *__restrict__ res, int n,
                               const int *__restrict__ act) {
     const int s = blockIdx.y;
@@ -224,10 +307,8 @@ __global__ void resid3_kernel(const float *__restrict__ gx, const float *__restr
     FOR_V3(V) {
         int i, j, k;
         decode3(v, w, &i, &j, &k);
-        float r = 0.0f;
         if (i > 0 && i < n)
-            r = b[off + v] - apply3(gx + off, gy + off, gz + off, z + off, v, j, k, n);
-        res[off + v] = r;
+            res[off + v] = b[off + v] - apply3(gx + off, gy + off, gz + off, z + off, v, j, k, n);
     }
 }
 
@@ -275,21 +356,15 @@ __global__ void prolong3_kernel(const float *__restrict__ zc, int nc, float *__r
         int i, j, k;
         decode3(v, wf, &i, &j, &k);
         if (i < 1 || i > nf - 1) continue;
+        // the coarse neighbours (a >> 1, (a + 1) >> 1) per axis coincide on
+        // even fine indices, so the eight-term mean is the trilinear weight
         const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-        const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
-        const float wi = (i & 1) ? 0.5f : 1.0f, wj = (j & 1) ? 0.5f : 1.0f,
-                    wk = (k & 1) ? 0.5f : 1.0f;
-        auto C = [&](int a, int b, int d) { return c[((long long)d * wc + b) * wc + a]; };
-        float acc = C(i0, j0, k0);
-        if (i & 1) acc += C(i1, j0, k0);
-        if (j & 1) acc += C(i0, j1, k0) + ((i & 1) ? C(i1, j1, k0) : 0.0f);
-        if (k & 1) {
-            float t = C(i0, j0, k1);
-            if (i & 1) t += C(i1, j0, k1);
-            if (j & 1) t += C(i0, j1, k1) + ((i & 1) ? C(i1, j1, k1) : 0.0f);
-            acc += t;
-        }
-        zf[s * Vf + v] += wi * wj * wk * acc;
+        const int i1 = (i + 1) >> 1, j1 = (j + 1) >> 1, k1 = (k + 1) >> 1;
+        const float *c00 = c + ((long long)k0 * wc + j0) * wc, *c01 = c + ((long long)k0 * wc + j1) * wc;
+        const float *c10 = c + ((long long)k1 * wc + j0) * wc, *c11 = c + ((long long)k1 * wc + j1) * wc;
+        const float acc = ((c00[i0] + c00[i1]) + (c01[i0] + c01[i1])) +
+                          ((c10[i0] + c10[i1]) + (c11[i0] + c11[i1]));
+        zf[s * Vf + v] += 0.125f * acc;
     }
 }
 
@@ -481,37 +556,71 @@ __global__ void reduce3_kernel(const double *__restrict__ part, int nblk, int co
     }
 }
 
-// ---------------------------------------------------------------- refinement (FP64)
-__global__ void lift3_kernel(double *__restrict__ u, int n) {
+// ---------------------------------------------------------------- refinement (float-float)
+// u and the conductances as float-float (hi, lo): ~48 significant bits, with
+// FP32 instructions only (FP64 runs at a small fraction of the FP32 rate)
+struct Outer3 {
+    const float *gx, *gy, *gz, *glx, *gly, *glz;
+    float2 *u;
+};
+
+__global__ void lift3_kernel(float2 *__restrict__ u, int n) {
     const int s = blockIdx.y;
     const int w = n + 1;
     const long long V = (long long)w * w * w, off = (long long)s * V;
-    FOR_V3(V) u[off + v] = (v % w == 0) ? 1.0 : 0.0;
+    FOR_V3(V) u[off + v] = make_float2((v % w == 0) ? 1.0f : 0.0f, 0.0f);
 }
 
-// r = F' - A'u (FP64) at unknowns -> b (FP32), partial |r|^2; samples with act == 0 skip
+// (A'u)_p of an unknown vertex in float-float (differences of u formed first)
+__device__ __forceinline__ ff apply3_ff(const Outer3 &o, long long v, int j, int k, int n) {
+    const int w = n + 1;
+    const long long w2 = (long long)w * w;
+    auto U = [&](long long q) {
+        const float2 t = o.u[q];
+        return ff{t.x, t.y};
+    };
+    const ff uc = U(v);
+    ff a = ff_mul(ff{o.gx[v - 1], o.glx[v - 1]}, ff_sub(uc, U(v - 1)));
+    a = ff_add(a, ff_mul(ff{o.gx[v], o.glx[v]}, ff_sub(uc, U(v + 1))));
+    if (j > 0) a = ff_add(a, ff_mul(ff{o.gy[v - w], o.gly[v - w]}, ff_sub(uc, U(v - w))));
+    if (j < n) a = ff_add(a, ff_mul(ff{o.gy[v], o.gly[v]}, ff_sub(uc, U(v + w))));
+    if (k > 0) a = ff_add(a, ff_mul(ff{o.gz[v - w2], o.glz[v - w2]}, ff_sub(uc, U(v - w2))));
+    if (k < n) a = ff_add(a, ff_mul(ff{o.gz[v], o.glz[v]}, ff_sub(uc, U(v + w2))));
+    return a;
+}
+
+// r = F' - A'u at unknowns -> b (FP32), partial |r|^2 (FP64); samples with act == 0 skip
 __global__ void __launch_bounds__(TPB3) outer_residual3_kernel(
-    const double *__restrict__ g64x, const double *__restrict__ g64y,
-    const double *__restrict__ g64z, const double *__restrict__ u, int n, double fh2,
-    float *__restrict__ b, double *__restrict__ part, int nblk, const int *__restrict__ act) {
+    Outer3 o, int n, double fh2, float *__restrict__ b, double *__restrict__ part, int nblk,
+    const int *__restrict__ act) {
     __shared__ double shd[32];
     const int s = blockIdx.y;
     if (act && !act[s]) return;
     const int w = n + 1;
     const long long V = (long long)w * w * w, off = (long long)s * V;
+    Outer3 os = o;
+    os.gx += off;
+    os.gy += off;
+    os.gz += off;
+    os.glx += off;
+    os.gly += off;
+    os.glz += off;
+    os.u += off;
     double acc = 0.0;
     FOR_V3(V) {
         int i, j, k;
         decode3(v, w, &i, &j, &k);
-        double r = 0.0;
+        float rb = 0.0f;
         if (i > 0 && i < n) {
-            r = fh2 * (double)tets_at(i, j, k, n) * (1.0 / 24.0) -
-                apply3(g64x + off, g64y + off, g64z + off, u + off, v, j, k, n);
-            acc += r * r;
+            const ff r = ff_sub(ff_from_double(fh2 * (double)tets_at(i, j, k, n) * (1.0 / 24.0)),
+                                apply3_ff(os, v, j, k, n));
+            rb = r.hi + r.lo;
+            const double rd = (double)r.hi + (double)r.lo;
+            acc += rd * rd;
         }
-        b[off + v] = (float)r;
+        b[off + v] = rb;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    for (int q = 16; q > 0; q >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, q);
     if ((threadIdx.x & 31) == 0) shd[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -521,15 +630,28 @@ __global__ void __launch_bounds__(TPB3) outer_residual3_kernel(
     }
 }
 
-__global__ void outer_update3_kernel(double *__restrict__ u, const float *__restrict__ d, int n,
+__global__ void outer_update3_kernel(float2 *__restrict__ u, const float *__restrict__ d, int n,
                                      const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
     const int w = n + 1;
     const long long V = (long long)w * w * w, off = (long long)s * V;
     FOR_V3(V) {
-        const int i = (int)(v % w);
-        if (i > 0 && i < n) u[off + v] += (double)d[off + v];
+        const int i = v % w;
+        if (i > 0 && i < n) {
+            const float2 t = u[off + v];
+            const ff r = ff_add_f(ff{t.x, t.y}, d[off + v]);
+            u[off + v] = make_float2(r.hi, r.lo);
+        }
+    }
+}
+
+__global__ void u_to_double3_kernel(const float2 *__restrict__ u, long long total,
+                                    double *__restrict__ out) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const float2 t = u[q];
+        out[q] = (double)t.x + (double)t.y;
     }
 }
 
@@ -538,8 +660,8 @@ __global__ void outer_update3_kernel(double *__restrict__ u, const float *__rest
 // (over the vertices of the x1 = 1 plane) and of sum_T (sum u_i^2 + (sum u_i)^2)
 // over the six tetrahedra of every cell
 __global__ void __launch_bounds__(TPB3) qoi3_partial_kernel(
-    const double *__restrict__ g64x, const double *__restrict__ u, int n, double fh2,
-    double *__restrict__ part_out, double *__restrict__ part_l2, int nblk) {
+    const float *__restrict__ gx, const float *__restrict__ glx, const double *__restrict__ u,
+    int n, double fh2, double *__restrict__ part_out, double *__restrict__ part_l2, int nblk) {
     __shared__ double sa[32], sb[32];
     const int s = blockIdx.y;
     const int w = n + 1;
@@ -551,7 +673,8 @@ __global__ void __launch_bounds__(TPB3) qoi3_partial_kernel(
         int i, j, k;
         decode3(v, w, &i, &j, &k);
         if (i == n)
-            a += g64x[off + v - 1] * us[v - 1] + fh2 * (double)tets_at(i, j, k, n) * (1.0 / 24.0);
+            a += ((double)gx[off + v - 1] + (double)glx[off + v - 1]) * us[v - 1] +
+                 fh2 * (double)tets_at(i, j, k, n) * (1.0 / 24.0);
         if (i < n && j < n && k < n) {
             // corners: bit 0 = +x, bit 1 = +y, bit 2 = +z
             double c[8];
@@ -585,16 +708,19 @@ __global__ void __launch_bounds__(TPB3) qoi3_partial_kernel(
     }
 }
 
+// QoIs of qmask (bit 0 outflow, 1 point value, 2 L2 norm; the others are
+// written as 0; part_out / part_l2 may be NULL when qmask has neither)
 __global__ void qoi3_final_kernel(const double *__restrict__ part_out,
                                   const double *__restrict__ part_l2, int nblk, int count,
                                   const double *__restrict__ u, int n, Scal3 sc, double rtol2,
                                   double *__restrict__ qoi, int *__restrict__ iters_out,
-                                  int *__restrict__ status_out, int *__restrict__ misc) {
+                                  int *__restrict__ status_out, int *__restrict__ misc,
+                                  int qmask) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= count) return;
     const int s = warp;
     double a = 0.0, b = 0.0;
-    for (int i = lane; i < nblk; i += 32) {
+    for (int i = lane; part_out && i < nblk; i += 32) {
         a += part_out[(long long)s * nblk + i];
         b += part_l2[(long long)s * nblk + i];
     }
@@ -630,9 +756,9 @@ __global__ void qoi3_final_kernel(const double *__restrict__ part_out,
     q_pt += t[ord[2]] * U(c);
     const double q_out = h * a;
     const double q_l2 = sqrt(b * h * h * h / 120.0);   // |T| / 20 = h^3 / 120
-    qoi[3 * s + 0] = q_out;
-    qoi[3 * s + 1] = q_pt;
-    qoi[3 * s + 2] = q_l2;
+    qoi[3 * s + 0] = (qmask & 1) ? q_out : 0.0;
+    qoi[3 * s + 1] = (qmask & 2) ? q_pt : 0.0;
+    qoi[3 * s + 2] = (qmask & 4) ? q_l2 : 0.0;
     int st = 0;
     if (!(fabs(q_out) < 1e300 && fabs(q_pt) < 1e300 && fabs(q_l2) < 1e300))
         st = CE_ERR_NONFINITE;
@@ -653,8 +779,11 @@ struct Solver3 {
     long long V[MAXLEV3];
     float *gx[MAXLEV3] = {}, *gy[MAXLEV3] = {}, *gz[MAXLEV3] = {}, *b[MAXLEV3] = {},
           *z[MAXLEV3] = {};
+    __half *hx[MAXLEV3] = {}, *hy[MAXLEV3] = {}, *hz[MAXLEV3] = {};   // multigrid copies
     float *res = nullptr, *p = nullptr, *q = nullptr, *d = nullptr;
-    double *g64x = nullptr, *g64y = nullptr, *g64z = nullptr, *u = nullptr;
+    float *glx = nullptr, *gly = nullptr, *glz = nullptr;   // lo parts of the level-0 conductances
+    float2 *uf = nullptr;                                    // u as float-float
+    double *u = nullptr;                                     // u in FP64 for the QoIs
     double *part = nullptr, *part2 = nullptr, *sdbl = nullptr;
     int *sint = nullptr;
     Scal3 sc{};
@@ -688,15 +817,19 @@ struct Solver3 {
             SCE_TRY(alloc(&gz[L], c));
             SCE_TRY(alloc(&b[L], c));
             SCE_TRY(alloc(&z[L], c));
+            SCE_TRY(alloc(&hx[L], c));
+            SCE_TRY(alloc(&hy[L], c));
+            SCE_TRY(alloc(&hz[L], c));
         }
         const size_t c0 = (size_t)count * V[0];
         SCE_TRY(alloc(&res, c0));
         SCE_TRY(alloc(&p, c0));
         SCE_TRY(alloc(&q, c0));
         SCE_TRY(alloc(&d, c0));
-        SCE_TRY(alloc(&g64x, c0));
-        SCE_TRY(alloc(&g64y, c0));
-        SCE_TRY(alloc(&g64z, c0));
+        SCE_TRY(alloc(&glx, c0));
+        SCE_TRY(alloc(&gly, c0));
+        SCE_TRY(alloc(&glz, c0));
+        SCE_TRY(alloc(&uf, c0));
         SCE_TRY(alloc(&u, c0));
         nblk0 = (int)((V[0] + EPB3 - 1) / EPB3);
         SCE_TRY(alloc(&part, (size_t)count * nblk0));
@@ -715,6 +848,8 @@ struct Solver3 {
         sc.act_in = sint + count;
         sc.iters = sint + 2 * count;
         sc.counter = sint + 4 * count;
+        for (int L = 0; L < NL; ++L)
+            SCE_CUDA(cudaMemsetAsync(z[L], 0, (size_t)count * V[L] * sizeof(float), st));
         SCE_CUDA(cudaMemsetAsync(sdbl, 0, (size_t)count * 8 * sizeof(double), st));
         SCE_CUDA(cudaMemsetAsync(sint, 0, ((size_t)count * 4 + 4) * sizeof(int), st));
         return CE_OK;
@@ -733,21 +868,26 @@ struct Solver3 {
     }
 
     // z[0] = M^-1 b[0] for the samples with act set
+    dim3 sgrid(int L) const {
+        const long long tot = (long long)((n[L] + 2) / 2) * (n[L] + 1) * (n[L] + 1);
+        return dim3((unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), count);
+    }
+
+    // z[0] = M^-1 b[0] for the samples with act set
     void vcycle(const int *act) {
-        cudaMemsetAsync(z[0], 0, (size_t)count * V[0] * sizeof(float), st);
+        if (NL == 1) cudaMemsetAsync(z[0], 0, (size_t)count * V[0] * sizeof(float), st);
         for (int L = 0; L < NL - 1; ++L) {
-            const int half = (n[L] + 2) / 2, w = n[L] + 1;
-            const long long tot = (long long)half * w * w;
-            dim3 gs((unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), count);
             {
-                SceProf pr(KP_SMOOTH3, st, vb(L, 2 * 4 * 4.0 + 2 * 4.0));
-                smooth3_kernel<<<gs, 256, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], n[L], 0, act);
-                smooth3_kernel<<<gs, 256, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], n[L], 1, act);
+                SceProf pr(KP_SMOOTH3, st, vb(L, 2 * 6.0 + 3 * 4.0 + 2 * 4.0));
+                smooth3_kernel<__half, true><<<sgrid(L), 256, 0, st>>>(hx[L], hy[L], hz[L], b[L],
+                                                                       z[L], n[L], 0, act);
+                smooth3_kernel<__half, false><<<sgrid(L), 256, 0, st>>>(hx[L], hy[L], hz[L], b[L],
+                                                                        z[L], n[L], 1, act);
             }
             {
-                SceProf pr(KP_RESID3, st, vb(L, 6 * 4.0));
-                resid3_kernel<<<grid(L), TPB3, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], res, n[L],
-                                                        act);
+                SceProf pr(KP_RESID3, st, vb(L, 6.0 + 3 * 4.0));
+                resid3_kernel<__half><<<grid(L), TPB3, 0, st>>>(hx[L], hy[L], hz[L], b[L], z[L],
+                                                                res, n[L], act);
             }
             {
                 SceProf pr(KP_RESTRICT3, st, vb(L, 4.0) + vb(L + 1, 8.0));
@@ -765,18 +905,17 @@ struct Solver3 {
                 SceProf pr(KP_PROLONG3, st, vb(L, 8.0) + vb(L + 1, 4.0));
                 prolong3_kernel<<<grid(L), TPB3, 0, st>>>(z[L + 1], n[L + 1], z[L], act);
             }
-            const int half = (n[L] + 2) / 2, w = n[L] + 1;
-            const long long tot = (long long)half * w * w;
-            dim3 gs((unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), count);
-            SceProf pr(KP_SMOOTH3, st, vb(L, 2 * 4 * 4.0 + 2 * 4.0));
-            smooth3_kernel<<<gs, 256, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], n[L], 1, act);
-            smooth3_kernel<<<gs, 256, 0, st>>>(gx[L], gy[L], gz[L], b[L], z[L], n[L], 0, act);
+            SceProf pr(KP_SMOOTH3, st, vb(L, 2 * (6.0 + 3 * 4.0)));
+            smooth3_kernel<__half, false><<<sgrid(L), 256, 0, st>>>(hx[L], hy[L], hz[L], b[L],
+                                                                    z[L], n[L], 1, act);
+            smooth3_kernel<__half, false><<<sgrid(L), 256, 0, st>>>(hx[L], hy[L], hz[L], b[L],
+                                                                    z[L], n[L], 0, act);
         }
     }
 };
 
 int solve3(const darcy_problem *pr, const float *k, int count, double *qoi, int *iters,
-           int *status, double *u_out, cudaStream_t st, int *misc_out) {
+           int *status, double *u_out, cudaStream_t st, int *misc_out, int qmask) {
     Solver3 S;
     S.st = st;
     SCE_TRY(S.init(pr->n, count));
@@ -785,14 +924,19 @@ int solve3(const darcy_problem *pr, const float *k, int count, double *qoi, int 
     const long long V0 = S.V[0];
     {
         SceProf pf(KP_COND3, st, S.vb(0, 4.0 + 3 * 12.0));
-        cond3_kernel<<<g0, TPB3, 0, st>>>(k, n0, S.g64x, S.g64y, S.g64z, S.gx[0], S.gy[0], S.gz[0]);
+        cond3_kernel<<<g0, TPB3, 0, st>>>(k, n0, S.gx[0], S.gy[0], S.gz[0], S.glx, S.gly, S.glz);
+        const long long tot = (long long)count * V0;
+        half3_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), 256, 0, st>>>(
+            S.gx[0], S.gy[0], S.gz[0], tot, S.hx[0], S.hy[0], S.hz[0]);
     }
     for (int L = 1; L < S.NL; ++L) {
         SceProf pf(KP_COARSEN, st, S.vb(L - 1, 12.0) + S.vb(L, 12.0));
         coarsen3_kernel<<<S.grid(L), TPB3, 0, st>>>(S.gx[L - 1], S.gy[L - 1], S.gz[L - 1], S.n[L - 1],
-                                                    S.gx[L], S.gy[L], S.gz[L]);
+                                                    S.gx[L], S.gy[L], S.gz[L], S.hx[L], S.hy[L],
+                                                    S.hz[L]);
     }
-    lift3_kernel<<<g0, TPB3, 0, st>>>(S.u, n0);
+    lift3_kernel<<<g0, TPB3, 0, st>>>(S.uf, n0);
+    const Outer3 ost{S.gx[0], S.gy[0], S.gz[0], S.glx, S.gly, S.glz, S.uf};
     SCE_CUDA(cudaGetLastError());
 
     const double h = 1.0 / (double)n0;
@@ -805,8 +949,8 @@ int solve3(const darcy_problem *pr, const float *k, int count, double *qoi, int 
     auto outer_residual = [&](const int *act, int mode) -> int {
         {
             SceProf pf(KP_OUTER3, st, S.vb(0, 4 * 8.0 + 4.0));
-            outer_residual3_kernel<<<g0, TPB3, 0, st>>>(S.g64x, S.g64y, S.g64z, S.u, n0, fh2,
-                                                        S.b[0], S.part, S.nblk0, act);
+            outer_residual3_kernel<<<g0, TPB3, 0, st>>>(ost, n0, fh2, S.b[0], S.part, S.nblk0,
+                                                        act);
         }
         SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
         S.reduce(mode, act, rtol2, in_rel2);
@@ -864,20 +1008,28 @@ int solve3(const darcy_problem *pr, const float *k, int count, double *qoi, int 
         SCE_CUDA(cudaGetLastError());
         {
             SceProf pf(KP_OUTER3, st, S.vb(0, 2 * 8.0 + 4.0));
-            outer_update3_kernel<<<g0, TPB3, 0, st>>>(S.u, S.d, n0, S.sc.act_out);
+            outer_update3_kernel<<<g0, TPB3, 0, st>>>(S.uf, S.d, n0, S.sc.act_out);
         }
         SCE_TRY(outer_residual(S.sc.act_out, R3_ORR));
         SCE_TRY(S.read_counter(&n_act));
     }
 
     {
+        const long long tot = (long long)count * V0;
+        u_to_double3_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), 256, 0,
+                              st>>>(S.uf, tot, S.u);
+    }
+    const bool grid_qoi = (qmask & 5) != 0;   // outflow and L2 norm need a pass over the grid
+    if (grid_qoi) {
         SceProf pf(KP_QOI, st, S.vb(0, 16.0));
-        qoi3_partial_kernel<<<g0, TPB3, 0, st>>>(S.g64x, S.u, n0, fh2, S.part, S.part2, S.nblk0);
+        qoi3_partial_kernel<<<g0, TPB3, 0, st>>>(S.gx[0], S.glx, S.u, n0, fh2, S.part, S.part2,
+                                                 S.nblk0);
     }
     int *misc = S.sint + 4 * count + 1;   // [failed, max iters, total iters]
     SCE_CUDA(cudaMemsetAsync(misc, 0, 3 * sizeof(int), st));
     qoi3_final_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(
-        S.part, S.part2, S.nblk0, count, S.u, n0, S.sc, rtol2, qoi, iters, status, misc);
+        grid_qoi ? S.part : nullptr, grid_qoi ? S.part2 : nullptr, S.nblk0, count, S.u, n0, S.sc,
+        rtol2, qoi, iters, status, misc, qmask);
     SCE_CUDA(cudaGetLastError());
     if (u_out)
         SCE_CUDA(cudaMemcpyAsync(u_out, S.u, (size_t)count * V0 * sizeof(double),
@@ -901,7 +1053,7 @@ int chunk3(int n) {
 }
 
 int solve3_batched(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
-                   int *status, double *u_out, cudaStream_t st, int *misc_out) {
+                   int *status, double *u_out, cudaStream_t st, int *misc_out, int qmask) {
     const int chunk = chunk3(p->n);
     const long long V = (long long)(p->n + 1) * (p->n + 1) * (p->n + 1);
     int worst = CE_OK;
@@ -911,7 +1063,7 @@ int solve3_batched(const darcy_problem *p, const float *k, int count, double *qo
         int m[3] = {0, 0, 0};
         const int rc = solve3(p, k + (size_t)c0 * V, cn, qoi + 3 * (size_t)c0,
                               iters ? iters + c0 : nullptr, status ? status + c0 : nullptr,
-                              u_out ? u_out + (size_t)c0 * V : nullptr, st, m);
+                              u_out ? u_out + (size_t)c0 * V : nullptr, st, m, qmask);
         if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) return rc;
         if (rc != CE_OK) worst = rc;
         tot[0] += m[0];
@@ -934,7 +1086,7 @@ extern "C" int darcy3_solve_batch(const darcy_problem *p, const float *k, int co
     if (!is_pow2(p->n) || p->n < 2 || p->n > 256 || p->precision != 32 || !(p->rtol > 0))
         return CE_ERR_INVALID_ARG;
     if (count == 0) return CE_OK;
-    return solve3_batched(p, k, count, qoi, iters, status, u_out, as_stream(stream), nullptr);
+    return solve3_batched(p, k, count, qoi, iters, status, u_out, as_stream(stream), nullptr, 7);
 }
 
 extern "C" int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, uint64_t seed,
@@ -969,7 +1121,7 @@ extern "C" int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, u
                               stream);
         int m[3] = {0, 0, 0};
         if (rc == CE_OK) {
-            rc = solve3_batched(p, kf, cn, qf, nullptr, nullptr, nullptr, st, m);
+            rc = solve3_batched(p, kf, cn, qf, nullptr, nullptr, nullptr, st, m, 1 << qoi_index);
             out->n_failed += m[0];
             out->max_iters = std::max(out->max_iters, m[1]);
             out->total_iters += m[2];
@@ -979,7 +1131,7 @@ extern "C" int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, u
             }
         }
         if (rc == CE_OK && level > 0) {
-            rc = solve3_batched(&pc, kc, cn, qc, nullptr, nullptr, nullptr, st, m);
+            rc = solve3_batched(&pc, kc, cn, qc, nullptr, nullptr, nullptr, st, m, 1 << qoi_index);
             out->n_failed += m[0];
             out->max_iters = std::max(out->max_iters, m[1]);
             out->total_iters += m[2];

@@ -192,3 +192,38 @@ class QmcStudy:
 
 
 QMC_STUDY = QmcStudy()
+
+
+@dataclass
+class ThreeD:
+    """Three-dimensional MLMC-CES (the d = 3 instance of the method): unit
+    cube, Matern covariance, smooth periodisation (J = n, P = 4n), levels
+    n = n0 * 2^l, tau = floor(sqrt(s)) eigenvalues dropped from every field
+    except the finest level's fine field; Q = u(7/15, 7/15, 7/15), f = 1.
+    The CPU baseline runs the oracle on levels 0..2 only: one direct solve on
+    the 65^3 grid of level 3 takes minutes."""
+    nu: float = 0.5
+    lam: float = 0.1
+    sigma2: float = 1.0
+    n0: int = 8
+    N: tuple = (4000, 1000, 250, 60)
+    qoi: int = 1
+    f: float = 1.0
+    seed: int = 9
+    rtol: float = 1e-10
+    cpu_samples: tuple = (32, 16, 1)
+
+    @property
+    def levels(self):
+        return [(l, self.n0 << l, self.N[l]) for l in range(len(self.N))]
+
+    def describe(self):
+        ns = [self.n0 << l for l in range(len(self.N))]
+        return (f"3D MLMC-CES Matern nu={self.nu} lambda={self.lam} sigma2={self.sigma2}; "
+                f"n={ns[0]}..{ns[-1]} per side (L={len(ns) - 1}); "
+                f"N_l={'/'.join(map(str, self.N))}; smooth periodisation J=n (P=4n); "
+                f"tau_l=floor(sqrt(s_l)), finest unsmoothed; Q=u(7/15,7/15,7/15), f={self.f}, "
+                f"rtol={self.rtol}")
+
+
+THREE_D = ThreeD()
