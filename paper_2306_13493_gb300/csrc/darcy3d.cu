@@ -249,123 +249,132 @@ __global__ void half3_kernel(const float *__restrict__ gx, const float *__restri
     }
 }
 
-// red-black Gauss-Seidel half-sweep of colour `color` ((i + j + k) % 2), one
-// thread per vertex of the colour.  FROM_ZERO: the first half-sweep from
+// Row-structured launches of the stencil kernels: a row is the grid line
+// (j, k); 2^lt threads per row (at least its work items), 256 / 2^lt rows per
+// block, grid (rows, samples).  One division per thread, 32-bit offsets from
+// the sample's base pointers.
+__device__ __forceinline__ bool row3(int w, int lt, int *t, int *j, int *k) {
+    const int row = blockIdx.x * (256 >> lt) + (threadIdx.x >> lt);
+    if (row >= w * w) return false;
+    *t = threadIdx.x & ((1 << lt) - 1);
+    *k = (int)((unsigned)row / (unsigned)w);
+    *j = row - *k * w;
+    return true;
+}
+
+// red-black Gauss-Seidel half-sweep of colour `color` ((i + j + k) % 2): n/2
+// threads per row, i = 2t + parity.  FROM_ZERO: the first half-sweep from
 // z = 0 (z = b/diag at the colour's unknowns and 0 at the other colour's,
 // so z is not read and needs no clearing).  The Dirichlet planes i = 0, n
 // are never written: z there is zeroed once when the hierarchy is allocated.
+// The division is the fast single-precision one: the smoother only has to be
+// a fixed symmetric operation, not correctly rounded.
 template <typename Tg, bool FROM_ZERO>
-__global__ void smooth3_kernel(const Tg *__restrict__ gx, const Tg *__restrict__ gy,
-                               const Tg *__restrict__ gz, const float *__restrict__ b,
-                               float *__restrict__ z, int n, int color,
-                               const int *__restrict__ act) {
+__global__ void __launch_bounds__(256) smooth3_kernel(
+    const Tg *__restrict__ gx, const Tg *__restrict__ gy, const Tg *__restrict__ gz,
+    const float *__restrict__ b, float *__restrict__ z, int n, int lt, int color,
+    const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
-    const int w = n + 1, half = (n + 2) / 2;
-    const long long off = (long long)s * w * w * w, w2 = (long long)w * w;
-    const int total = half * w * w;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int r = (int)((unsigned)t / (unsigned)half);
-        const int ii = t - r * half;
-        const int k = (int)((unsigned)r / (unsigned)w), j = r - k * w;
-        const int par = (color + j + k) & 1;
-        const int i = 2 * ii + par;
-        const long long row = off + (long long)r * w;
-        if (FROM_ZERO) {
-            const int io = 2 * ii + (1 - par);
-            if (io >= 1 && io <= n - 1) z[row + io] = 0.0f;
-        }
-        if (i < 1 || i > n - 1) continue;
-        const long long v = row + i;
-        const float cw = gval(gx[v - 1]), ce = gval(gx[v]);
-        const float cs = j > 0 ? gval(gy[v - w]) : 0.0f, cn = j < n ? gval(gy[v]) : 0.0f;
-        const float cd = k > 0 ? gval(gz[v - w2]) : 0.0f, cu = k < n ? gval(gz[v]) : 0.0f;
-        const float d = cw + ce + cs + cn + cd + cu;
-        if (FROM_ZERO) {
-            z[v] = b[v] / d;
-        } else {
-            float acc = b[v] + cw * z[v - 1] + ce * z[v + 1];
-            if (j > 0) acc += cs * z[v - w];
-            if (j < n) acc += cn * z[v + w];
-            if (k > 0) acc += cd * z[v - w2];
-            if (k < n) acc += cu * z[v + w2];
-            z[v] = acc / d;
-        }
+    const int w = n + 1, w2 = w * w;
+    int t, j, k;
+    if (!row3(w, lt, &t, &j, &k)) return;
+    const long long off = (long long)s * w2 * w;
+    const Tg *ax = gx + off, *ay = gy + off, *az = gz + off;
+    const float *bs = b + off;
+    float *zs = z + off;
+    const int par = (color + j + k) & 1;
+    const int rowv = (k * w + j) * w;
+    if (FROM_ZERO) {
+        const int io = 2 * t + (1 - par);
+        if (io >= 1) zs[rowv + io] = 0.0f;
+    }
+    const int i = 2 * t + par;
+    if (i < 1) return;
+    const int v = rowv + i;
+    const float cw = gval(ax[v - 1]), ce = gval(ax[v]);
+    const float cs = j > 0 ? gval(ay[v - w]) : 0.0f, cn = j < n ? gval(ay[v]) : 0.0f;
+    const float cd = k > 0 ? gval(az[v - w2]) : 0.0f, cu = k < n ? gval(az[v]) : 0.0f;
+    const float d = cw + ce + cs + cn + cd + cu;
+    if (FROM_ZERO) {
+        zs[v] = __fdividef(bs[v], d);
+    } else {
+        float acc = bs[v] + cw * zs[v - 1] + ce * zs[v + 1];
+        if (j > 0) acc += cs * zs[v - w];
+        if (j < n) acc += cn * zs[v + w];
+        if (k > 0) acc += cd * zs[v - w2];
+        if (k < n) acc += cu * zs[v + w2];
+        zs[v] = __fdividef(acc, d);
     }
 }
 
-// res = b - A z at the unknowns (the Dirichlet planes of res are never read)
+// res = b - A z at the unknowns (n threads per row, i = 1 + t); the
+// Dirichlet planes of res are never read
 template <typename Tg>
-__global__ void resid3_kernel(const Tg *__restrict__ gx, const Tg *__restrict__ gy,
-                              const Tg *__restrict__ gz, const float *__restrict__ b,
-                              const float *__restrict__ z, float *__restrict__ res, int n,
-                              const int *__restrict__ act) {
+__global__ void __launch_bounds__(256) resid3_kernel(
+    const Tg *__restrict__ gx, const Tg *__restrict__ gy, const Tg *__restrict__ gz,
+    const float *__restrict__ b, const float *__restrict__ z, float *__restrict__ res, int n,
+    int lt, const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
     const int w = n + 1;
-    const long long V = (long long)w * w * w, off = (long long)s * V;
-    FOR_V3(V) {
-        int i, j, k;
-        decode3(v, w, &i, &j, &k);
-        if (i > 0 && i < n)
-            res[off + v] = b[off + v] - apply3(gx + off, gy + off, gz + off, z + off, v, j, k, n);
-    }
+    int t, j, k;
+    if (!row3(w, lt, &t, &j, &k) || t >= n - 1) return;
+    const long long off = (long long)s * w * w * w;
+    const int v = (k * w + j) * w + 1 + t;
+    res[off + v] = b[off + v] - apply3(gx + off, gy + off, gz + off, z + off, (long long)v, j, k, n);
 }
 
 // coarse right-hand side by full weighting (the transpose of trilinear
-// prolongation) at coarse unknowns, 0 on the coarse Dirichlet planes; zc = 0
-__global__ void restrict3_kernel(const float *__restrict__ res, int nf, float *__restrict__ bc,
-                                 float *__restrict__ zc, const int *__restrict__ act) {
+// prolongation) at coarse unknowns (nc threads per coarse row, I = 1 + t);
+// the coarse Dirichlet planes of bc are never read
+__global__ void __launch_bounds__(256) restrict3_kernel(const float *__restrict__ res, int nf,
+                                                        float *__restrict__ bc, int lt,
+                                                        const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
     const int nc = nf / 2, wc = nc + 1, wf = nf + 1;
-    const long long Vc = (long long)wc * wc * wc, Vf = (long long)wf * wf * wf;
-    const float *rs = res + s * Vf;
-    FOR_V3(Vc) {
-        int I, J, K;
-        decode3(v, wc, &I, &J, &K);
-        float acc = 0.0f;
-        if (I > 0 && I < nc) {
-            for (int dk = -1; dk <= 1; ++dk) {
-                const int k = 2 * K + dk;
-                if (k < 0 || k > nf) continue;
-                const float wk = dk == 0 ? 1.0f : 0.5f;
-                for (int dj = -1; dj <= 1; ++dj) {
-                    const int j = 2 * J + dj;
-                    if (j < 0 || j > nf) continue;
-                    const float wj = dj == 0 ? 1.0f : 0.5f;
-                    const long long row = ((long long)k * wf + j) * wf + 2 * I;
-                    acc += wk * wj * (0.5f * rs[row - 1] + rs[row] + 0.5f * rs[row + 1]);
-                }
-            }
+    int t, J, K;
+    if (!row3(wc, lt, &t, &J, &K) || t >= nc - 1) return;
+    const int I = 1 + t;
+    const float *rs = res + (long long)s * wf * wf * wf;
+    float acc = 0.0f;
+    for (int dk = -1; dk <= 1; ++dk) {
+        const int k = 2 * K + dk;
+        if (k < 0 || k > nf) continue;
+        const float wk = dk == 0 ? 1.0f : 0.5f;
+        for (int dj = -1; dj <= 1; ++dj) {
+            const int j = 2 * J + dj;
+            if (j < 0 || j > nf) continue;
+            const float wj = dj == 0 ? 1.0f : 0.5f;
+            const int row = (k * wf + j) * wf + 2 * I;
+            acc += wk * wj * (0.5f * rs[row - 1] + rs[row] + 0.5f * rs[row + 1]);
         }
-        bc[s * Vc + v] = acc;
-        zc[s * Vc + v] = 0.0f;
     }
+    bc[(long long)s * wc * wc * wc + (K * wc + J) * wc + I] = acc;
 }
 
-// z += trilinear interpolation of the coarse correction (unknowns only)
-__global__ void prolong3_kernel(const float *__restrict__ zc, int nc, float *__restrict__ zf,
-                                const int *__restrict__ act) {
+// z += trilinear interpolation of the coarse correction (unknowns only; nf
+// threads per fine row, i = 1 + t)
+__global__ void __launch_bounds__(256) prolong3_kernel(const float *__restrict__ zc, int nc,
+                                                       float *__restrict__ zf, int lt,
+                                                       const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
     const int nf = 2 * nc, wf = nf + 1, wc = nc + 1;
-    const long long Vf = (long long)wf * wf * wf, Vc = (long long)wc * wc * wc;
-    const float *c = zc + s * Vc;
-    FOR_V3(Vf) {
-        int i, j, k;
-        decode3(v, wf, &i, &j, &k);
-        if (i < 1 || i > nf - 1) continue;
-        // the coarse neighbours (a >> 1, (a + 1) >> 1) per axis coincide on
-        // even fine indices, so the eight-term mean is the trilinear weight
-        const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-        const int i1 = (i + 1) >> 1, j1 = (j + 1) >> 1, k1 = (k + 1) >> 1;
-        const float *c00 = c + ((long long)k0 * wc + j0) * wc, *c01 = c + ((long long)k0 * wc + j1) * wc;
-        const float *c10 = c + ((long long)k1 * wc + j0) * wc, *c11 = c + ((long long)k1 * wc + j1) * wc;
-        const float acc = ((c00[i0] + c00[i1]) + (c01[i0] + c01[i1])) +
-                          ((c10[i0] + c10[i1]) + (c11[i0] + c11[i1]));
-        zf[s * Vf + v] += 0.125f * acc;
-    }
+    int t, j, k;
+    if (!row3(wf, lt, &t, &j, &k) || t >= nf - 1) return;
+    const int i = 1 + t;
+    const float *c = zc + (long long)s * wc * wc * wc;
+    // the coarse neighbours (a >> 1, (a + 1) >> 1) per axis coincide on
+    // even fine indices, so the eight-term mean is the trilinear weight
+    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+    const int i1 = (i + 1) >> 1, j1 = (j + 1) >> 1, k1 = (k + 1) >> 1;
+    const float *c00 = c + (k0 * wc + j0) * wc, *c01 = c + (k0 * wc + j1) * wc;
+    const float *c10 = c + (k1 * wc + j0) * wc, *c11 = c + (k1 * wc + j1) * wc;
+    const float acc = ((c00[i0] + c00[i1]) + (c01[i0] + c01[i1])) +
+                      ((c10[i0] + c10[i1]) + (c11[i0] + c11[i1]));
+    zf[(long long)s * wf * wf * wf + (k * wf + j) * wf + i] += 0.125f * acc;
 }
 
 // exact solve on the 2-cell grid: unknowns (1, j, k), j, k = 0..2, one
@@ -428,6 +437,8 @@ __device__ __forceinline__ float block_sum3(float v, float *sh) {
     return t;
 }
 
+// q = A p at the unknowns (q on the Dirichlet planes stays 0 from the clear at
+// allocation), partial p.q per block
 __global__ void __launch_bounds__(TPB3) spmv_dot3_kernel(
     const float *__restrict__ gx, const float *__restrict__ gy, const float *__restrict__ gz,
     const float *__restrict__ p, float *__restrict__ q, int n, double *__restrict__ part,
@@ -441,12 +452,11 @@ __global__ void __launch_bounds__(TPB3) spmv_dot3_kernel(
     FOR_V3(V) {
         int i, j, k;
         decode3(v, w, &i, &j, &k);
-        float val = 0.0f;
         if (i > 0 && i < n) {
-            val = apply3(gx + off, gy + off, gz + off, p + off, v, j, k, n);
+            const float val = apply3(gx + off, gy + off, gz + off, p + off, (long long)v, j, k, n);
             acc += p[off + v] * val;
+            q[off + v] = val;
         }
-        q[off + v] = val;
     }
     const float tot = block_sum3(acc, sh);
     if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
@@ -848,17 +858,27 @@ struct Solver3 {
         sc.act_in = sint + count;
         sc.iters = sint + 2 * count;
         sc.counter = sint + 4 * count;
+        // vertices the kernels never write (Dirichlet planes of z and q) stay 0
         for (int L = 0; L < NL; ++L)
             SCE_CUDA(cudaMemsetAsync(z[L], 0, (size_t)count * V[L] * sizeof(float), st));
+        SCE_CUDA(cudaMemsetAsync(q, 0, c0 * sizeof(float), st));
         SCE_CUDA(cudaMemsetAsync(sdbl, 0, (size_t)count * 8 * sizeof(double), st));
         SCE_CUDA(cudaMemsetAsync(sint, 0, ((size_t)count * 4 + 4) * sizeof(int), st));
         return CE_OK;
     }
 
-    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0) {
-        SceProf pr(KP_REDUCE, st, (double)count * nblk0 * 8.0);
-        reduce3_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(part, nblk0, count, mode, sc, act,
+    // nb = partials per sample of the producing kernel (-1: nblk0)
+    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0, int nb = -1) {
+        if (nb < 0) nb = nblk0;
+        SceProf pr(KP_REDUCE, st, (double)count * nb * 8.0);
+        reduce3_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(part, nb, count, mode, sc, act,
                                                                  rtol2, in_rel2);
+    }
+
+    // row-structured launch: 2^lt threads per row of the w-wide grid
+    dim3 rgrid(int w, int lt) const {
+        const int rpb = 256 >> lt;
+        return dim3((unsigned)((w * w + rpb - 1) / rpb), count);
     }
 
     int read_counter(int *host) {
@@ -868,30 +888,27 @@ struct Solver3 {
     }
 
     // z[0] = M^-1 b[0] for the samples with act set
-    dim3 sgrid(int L) const {
-        const long long tot = (long long)((n[L] + 2) / 2) * (n[L] + 1) * (n[L] + 1);
-        return dim3((unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), count);
-    }
-
     // z[0] = M^-1 b[0] for the samples with act set
     void vcycle(const int *act) {
         if (NL == 1) cudaMemsetAsync(z[0], 0, (size_t)count * V[0] * sizeof(float), st);
         for (int L = 0; L < NL - 1; ++L) {
+            const int w = n[L] + 1, lt = ilog2(n[L]);
             {
                 SceProf pr(KP_SMOOTH3, st, vb(L, 2 * 6.0 + 3 * 4.0 + 2 * 4.0));
-                smooth3_kernel<__half, true><<<sgrid(L), 256, 0, st>>>(hx[L], hy[L], hz[L], b[L],
-                                                                       z[L], n[L], 0, act);
-                smooth3_kernel<__half, false><<<sgrid(L), 256, 0, st>>>(hx[L], hy[L], hz[L], b[L],
-                                                                        z[L], n[L], 1, act);
+                smooth3_kernel<__half, true><<<rgrid(w, lt - 1), 256, 0, st>>>(
+                    hx[L], hy[L], hz[L], b[L], z[L], n[L], lt - 1, 0, act);
+                smooth3_kernel<__half, false><<<rgrid(w, lt - 1), 256, 0, st>>>(
+                    hx[L], hy[L], hz[L], b[L], z[L], n[L], lt - 1, 1, act);
             }
             {
                 SceProf pr(KP_RESID3, st, vb(L, 6.0 + 3 * 4.0));
-                resid3_kernel<__half><<<grid(L), TPB3, 0, st>>>(hx[L], hy[L], hz[L], b[L], z[L],
-                                                                res, n[L], act);
+                resid3_kernel<__half><<<rgrid(w, lt), 256, 0, st>>>(hx[L], hy[L], hz[L], b[L], z[L],
+                                                                    res, n[L], lt, act);
             }
             {
-                SceProf pr(KP_RESTRICT3, st, vb(L, 4.0) + vb(L + 1, 8.0));
-                restrict3_kernel<<<grid(L + 1), TPB3, 0, st>>>(res, n[L], b[L + 1], z[L + 1], act);
+                SceProf pr(KP_RESTRICT3, st, vb(L, 4.0) + vb(L + 1, 4.0));
+                restrict3_kernel<<<rgrid(n[L + 1] + 1, lt - 1), 256, 0, st>>>(res, n[L], b[L + 1],
+                                                                             lt - 1, act);
             }
         }
         {
@@ -901,15 +918,16 @@ struct Solver3 {
                                                                    count, act);
         }
         for (int L = NL - 2; L >= 0; --L) {
+            const int w = n[L] + 1, lt = ilog2(n[L]);
             {
                 SceProf pr(KP_PROLONG3, st, vb(L, 8.0) + vb(L + 1, 4.0));
-                prolong3_kernel<<<grid(L), TPB3, 0, st>>>(z[L + 1], n[L + 1], z[L], act);
+                prolong3_kernel<<<rgrid(w, lt), 256, 0, st>>>(z[L + 1], n[L + 1], z[L], lt, act);
             }
             SceProf pr(KP_SMOOTH3, st, vb(L, 2 * (6.0 + 3 * 4.0)));
-            smooth3_kernel<__half, false><<<sgrid(L), 256, 0, st>>>(hx[L], hy[L], hz[L], b[L],
-                                                                    z[L], n[L], 1, act);
-            smooth3_kernel<__half, false><<<sgrid(L), 256, 0, st>>>(hx[L], hy[L], hz[L], b[L],
-                                                                    z[L], n[L], 0, act);
+            smooth3_kernel<__half, false><<<rgrid(w, lt - 1), 256, 0, st>>>(
+                hx[L], hy[L], hz[L], b[L], z[L], n[L], lt - 1, 1, act);
+            smooth3_kernel<__half, false><<<rgrid(w, lt - 1), 256, 0, st>>>(
+                hx[L], hy[L], hz[L], b[L], z[L], n[L], lt - 1, 0, act);
         }
     }
 };
