@@ -504,8 +504,9 @@ def _oracle3_ready(_):
 
 def three_d_study(args):
     """workloads.THREE_D: one step = one MLMC sweep over the 3D levels through
-    mlmc3_level_estimate (fields by the three-pass FFT sampler, Kuhn-P1 solves
-    on the fine and coarse grids, level sums).  Prints one JSON line."""
+    mlmc3_estimate_levels (all levels in one call, --concurrency of them in
+    flight; fields by the three-pass FFT sampler, Kuhn-P1 solves on the fine
+    and coarse grids, level sums).  Prints one JSON line."""
     import numpy as np
     import torch
     from paper_2306_13493_gb300 import build, sce
@@ -524,13 +525,15 @@ def three_d_study(args):
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
 
-    def sweep(step):
-        outs = []
-        for (l, n, N) in wl.levels:
-            o, _ = sce.mlmc3_level_estimate(embs[l], wl.seed, l, step * N, N, qoi_index=wl.qoi,
-                                            f=wl.f, rtol=wl.rtol, maxit=2000,
-                                            allow_not_converged=True)
-            outs.append(o)
+    conc = max(1, min(args.concurrency, len(wl.N)))
+
+    def sweep(step, c=None):
+        tasks = [{"emb": embs[l], "level": l, "first_sample": step * N, "count": N}
+                 for (l, n, N) in wl.levels]
+        outs, _, _ = sce.mlmc3_estimate_levels(tasks, wl.seed, qoi_index=wl.qoi, f=wl.f,
+                                               rtol=wl.rtol, maxit=2000,
+                                               max_concurrency=conc if c is None else c,
+                                               allow_not_converged=True)
         return outs
 
     steps = args.steps if args.steps else 3
@@ -563,7 +566,7 @@ def three_d_study(args):
     total = sum(wl.N)
 
     sce.sce_profile_enable(1)
-    sweep(900000)
+    sweep(900000, c=1)      # levels one after another: each launch's events time it alone
     prof = sce.sce_profile_read()
     sce.sce_profile_enable(0)
     peaks = {}
@@ -600,7 +603,7 @@ def three_d_study(args):
             "value": total / (ms_step / 1000.0), "unit": "samples/s", "n_gpus": 1,
             "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": wl.describe(),
+            "config": {"workload": wl.describe(), "levels_in_flight": conc,
                        "l2": "flushed before every timed step (258 MB write)"},
             "setup_seconds": round(setup_s, 3), "clocks": clk, "per_level": per_level,
             "kernels": kernels, "roofline": roof,

@@ -459,6 +459,30 @@ int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, uint64_t see
                          uint64_t first_sample, int count, int qoi_index, mlmc_level_sums *out,
                          double *Y, void *stream);
 
+/* One level of an MLMC step in d = 3 for mlmc3_estimate_levels: the fields of
+ * mlmc3_level_estimate's arguments (same meaning and ownership) and its results. */
+typedef struct mlmc3_level_task {
+    ce3_embedding_t emb;
+    uint32_t level;
+    uint64_t first_sample;
+    int count;
+    double *Y;             /* device double[count] or NULL           */
+    mlmc_level_sums sums;  /* out: the level sums                    */
+    int status;            /* out: that level's mlmc3_level_estimate status */
+} mlmc3_level_task;
+
+/*
+ * mlmc3_estimate_levels -- all levels of one d = 3 MLMC step: each task
+ * computes exactly what mlmc3_level_estimate computes for it (bit-identical),
+ * with p->n taken from the task's handle.  With max_concurrency > 1 up to that
+ * many levels run at once, each on its own CUDA stream driven by its own host
+ * thread, largest levels first; the streams start after the work queued on
+ * `stream` and `stream` waits for all of them.  max_concurrency <= 1 runs the
+ * tasks one after another on `stream`.  Returns as mlmc_estimate_levels.
+ */
+int mlmc3_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
+                          mlmc3_level_task *tasks, int ntasks, int max_concurrency, void *stream);
+
 /* Eq. (3.6): N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)),
  * l = 0..L.  V, C, N: host arrays of length L+1 (C > 0, V >= 0). */
 int mlmc_optimal_samples(int L_plus_1, const double *V, const double *C, double eps, long long *N);

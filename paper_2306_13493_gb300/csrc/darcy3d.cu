@@ -38,7 +38,11 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "ff.cuh"
@@ -1194,4 +1198,112 @@ extern "C" int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, u
     sce_free(qc, st);
     cudaStreamSynchronize(st);
     return rc != CE_OK ? rc : worst;
+}
+
+extern "C" int mlmc3_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
+                                     mlmc3_level_task *tasks, int ntasks, int max_concurrency,
+                                     void *stream) {
+    if (!p || ntasks < 0 || (ntasks > 0 && !tasks) || qoi_index < 0 || qoi_index > 2 ||
+        p->precision != 32 || !(p->rtol > 0))
+        return CE_ERR_INVALID_ARG;
+    for (int i = 0; i < ntasks; ++i)
+        if (!tasks[i].emb || tasks[i].count < 0) return CE_ERR_INVALID_ARG;
+    for (int i = 0; i < ntasks; ++i) {
+        tasks[i].sums = mlmc_level_sums{};
+        tasks[i].status = CE_OK;
+    }
+    const cudaStream_t st = as_stream(stream);
+    auto run = [&](int i, cudaStream_t s) {
+        ce_embedding_info info;
+        int rc = ce3_get_info(tasks[i].emb, &info);
+        if (rc == CE_OK) {
+            darcy_problem q = *p;
+            q.n = info.n;
+            rc = mlmc3_level_estimate(tasks[i].emb, &q, seed, tasks[i].level,
+                                      tasks[i].first_sample, tasks[i].count, qoi_index,
+                                      &tasks[i].sums, tasks[i].Y, (void *)s);
+        }
+        tasks[i].status = rc;
+    };
+    auto combine = [&]() {
+        int worst = CE_OK;
+        for (int i = 0; i < ntasks; ++i) {
+            const int r = tasks[i].status;
+            if (r != CE_OK && r != CE_ERR_NOT_CONVERGED) return r;
+            if (r == CE_ERR_NOT_CONVERGED) worst = r;
+        }
+        return worst;
+    };
+    if (max_concurrency <= 1 || ntasks == 0) {
+        for (int i = 0; i < ntasks; ++i) {
+            run(i, st);
+            if (tasks[i].status != CE_OK && tasks[i].status != CE_ERR_NOT_CONVERGED) break;
+        }
+        return combine();
+    }
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    std::vector<cudaStream_t> ss((size_t)ntasks, nullptr);
+    std::vector<cudaEvent_t> evs;
+    auto release = [&]() {
+        for (cudaStream_t s : ss)
+            if (s) cudaStreamDestroy(s);
+        for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+    };
+    auto new_event = [&](cudaEvent_t *ev) {
+        const cudaError_t err = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (err == cudaSuccess) evs.push_back(*ev);
+        return err;
+    };
+    cudaEvent_t ev0;
+    if (new_event(&ev0) != cudaSuccess || cudaEventRecord(ev0, st) != cudaSuccess) {
+        release();
+        return CE_ERR_CUDA;
+    }
+    for (int i = 0; i < ntasks; ++i) {
+        if (cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamWaitEvent(ss[i], ev0, 0) != cudaSuccess) {
+            release();
+            return CE_ERR_CUDA;
+        }
+    }
+    // largest levels first: they bound the makespan
+    std::vector<int> order(ntasks);
+    std::vector<double> work(ntasks, 0.0);
+    for (int i = 0; i < ntasks; ++i) {
+        order[i] = i;
+        ce_embedding_info info;
+        if (ce3_get_info(tasks[i].emb, &info) == CE_OK)
+            work[i] = (double)tasks[i].count * (info.n + 1.0) * (info.n + 1.0) * (info.n + 1.0);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    std::atomic<int> next{0};
+    std::mutex err_mu;
+    std::string err_text;
+    auto worker = [&]() {
+        if (cudaSetDevice(dev) != cudaSuccess) return;
+        for (int k; (k = next.fetch_add(1)) < ntasks;) {
+            const int i = order[k];
+            run(i, ss[i]);
+            if (tasks[i].status != CE_OK && tasks[i].status != CE_ERR_NOT_CONVERGED) {
+                std::lock_guard<std::mutex> lk(err_mu);
+                if (err_text.empty()) err_text = sce_last_error();
+            }
+        }
+    };
+    const int nthreads = std::min(max_concurrency, ntasks);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+    for (std::thread &t : pool) t.join();
+    if (!err_text.empty()) sce_set_last_error_text(err_text.c_str());
+    for (cudaStream_t s : ss) {
+        cudaEvent_t ev;
+        if (new_event(&ev) != cudaSuccess || cudaEventRecord(ev, s) != cudaSuccess ||
+            cudaStreamWaitEvent(st, ev, 0) != cudaSuccess) {
+            release();
+            return CE_ERR_CUDA;
+        }
+    }
+    release();
+    return combine();
 }

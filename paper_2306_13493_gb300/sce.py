@@ -75,6 +75,12 @@ class mlmc_level_task(ctypes.Structure):
                 ("sums", mlmc_level_sums), ("status", ctypes.c_int)]
 
 
+class mlmc3_level_task(ctypes.Structure):
+    _fields_ = [("emb", ctypes.c_void_p), ("level", ctypes.c_uint32),
+                ("first_sample", ctypes.c_uint64), ("count", ctypes.c_int),
+                ("Y", ctypes.c_void_p), ("sums", mlmc_level_sums), ("status", ctypes.c_int)]
+
+
 class sce_server_config(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_longlong),
                 ("max_embeddings", ctypes.c_int), ("precision", ctypes.c_int),
@@ -157,6 +163,9 @@ _SIGS = {
                                         ctypes.c_int, _P, _P, _P]),
     "darcy3_solve_batch": (ctypes.c_int, [ctypes.POINTER(darcy_problem), _P, ctypes.c_int, _P,
                                           _P, _P, _P, _P]),
+    "mlmc3_estimate_levels": (ctypes.c_int, [ctypes.POINTER(darcy_problem), ctypes.c_uint64,
+                                             ctypes.c_int, ctypes.POINTER(mlmc3_level_task),
+                                             ctypes.c_int, ctypes.c_int, _P]),
     "mlmc3_level_estimate": (ctypes.c_int, [_P, ctypes.POINTER(darcy_problem), ctypes.c_uint64,
                                             ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
                                             ctypes.c_int, ctypes.POINTER(mlmc_level_sums), _P,
@@ -530,6 +539,31 @@ def mlmc3_level_estimate(emb, seed, level, first_sample, count, qoi_index=QOI_OU
                                             _ptr(Y), _stream(stream, Y)),
                 "mlmc3_level_estimate", allow)
     return out, st
+
+
+def mlmc3_estimate_levels(tasks, seed, qoi_index=QOI_OUTFLOW, f=0.0, rtol=1e-10, maxit=1000,
+                          max_concurrency=8, stream=None, allow_not_converged=False):
+    """All levels of one d = 3 MLMC step in one call.  ``tasks``: sequence of
+    dicts with keys emb (Embedding3), level, first_sample, count and optionally
+    Y (CUDA tensor).  Returns ([mlmc_level_sums per task], [status per task],
+    overall status)."""
+    if not tasks:
+        return [], [], CE_OK
+    arr = (mlmc3_level_task * len(tasks))()
+    for t, d in zip(arr, tasks):
+        h = d["emb"].handle
+        t.emb = h.value if isinstance(h, ctypes.c_void_p) else h
+        t.level = d["level"]
+        t.first_sample = d["first_sample"]
+        t.count = d["count"]
+        t.Y = _ptr(d.get("Y")).value
+    prob = darcy_problem(tasks[0]["emb"].n, f, rtol, maxit, 32)
+    allow = (CE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    ref = next((d["Y"] for d in tasks if d.get("Y") is not None), None)
+    st = _check(load().mlmc3_estimate_levels(ctypes.byref(prob), seed, qoi_index, arr,
+                                             len(tasks), max_concurrency, _stream(stream, ref)),
+                "mlmc3_estimate_levels", allow)
+    return [mlmc_level_sums.from_buffer_copy(t.sums) for t in arr], [t.status for t in arr], st
 
 
 def sce_profile_enable(on):

@@ -65,6 +65,10 @@ def test_struct_layouts_match_header():
     assert sce.mlmc_level_task.sums.offset == 56
     assert sce.mlmc_level_task.status.offset == 112
     assert ctypes.sizeof(sce.mlmc_level_task) == 120
+    # mlmc3_level_task: pointer, u32 (+pad), u64, int (+pad), pointer, sums, int (+pad)
+    assert sce.mlmc3_level_task.sums.offset == 40
+    assert sce.mlmc3_level_task.status.offset == 96
+    assert ctypes.sizeof(sce.mlmc3_level_task) == 104
     # server structs: config int, (pad), i64, int, int, double, int (+pad)
     assert ctypes.sizeof(sce.sce_server_config) == 40
     # request: ce_cov 32, ce_pad 12, n 4, level 4, smoothing 4, finest 4, (pad 4),
@@ -133,3 +137,11 @@ def test_three_dimensional_entry_points_reject_bad_arguments_on_the_host():
     assert lib.mlmc3_level_estimate(None, ctypes.byref(prob), 1, 0, 0, 4, 0, ctypes.byref(out),
                                     None, None) == sce.CE_ERR_INVALID_ARG
     assert lib.ce3_sample_batch(None, 1, 0, 0, 4, None, None, None) == sce.CE_ERR_INVALID_ARG
+    tasks = (sce.mlmc3_level_task * 2)()
+    tasks[0].emb, tasks[0].count = 16, 4
+    tasks[1].emb, tasks[1].count = None, 4                 # missing handle
+    assert lib.mlmc3_estimate_levels(ctypes.byref(prob), 1, 0, tasks, 2, 4, None) == \
+        sce.CE_ERR_INVALID_ARG
+    assert lib.mlmc3_estimate_levels(ctypes.byref(prob), 1, 3, tasks, 0, 4, None) == \
+        sce.CE_ERR_INVALID_ARG                             # qoi_index out of range
+    assert lib.mlmc3_estimate_levels(ctypes.byref(prob), 1, 0, tasks, 0, 4, None) == sce.CE_OK

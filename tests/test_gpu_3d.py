@@ -260,3 +260,30 @@ def test_mlmc3_level_estimate_against_oracle(sce, level, smooth):
     got = Y.cpu().numpy()
     assert np.max(np.abs(got - np.array(want))) < QOI_TOL
     assert abs(out.sumY - got.sum()) < 1e-12 * max(1.0, abs(got).sum())
+
+
+def test_mlmc3_estimate_levels_concurrent_matches_serial(sce):
+    """All levels in one call, levels in flight together on their own streams,
+    give the level sums and Y of one level-by-level call each, bit for bit."""
+    import torch
+    ns, counts, seed = (4, 8, 16), (9, 5, 3), 13
+    embs = [sce.ce3_setup_embedding(ocv.MATERN, 0.5, 0.1, 1.0, n, pad_mode=oem.PAD_SMOOTH,
+                                    keep_fine=-1 if l == len(ns) - 1 else sce.CE_KEEP_TAU_SQRT_S,
+                                    keep_coarse=sce.CE_KEEP_TAU_SQRT_S)
+            for l, n in enumerate(ns)]
+    ser = []
+    for l, (e, c) in enumerate(zip(embs, counts)):
+        Y = torch.empty(c, dtype=torch.float64, device="cuda")
+        o, _ = sce.mlmc3_level_estimate(e, seed, l, 2 * c, c, qoi_index=1, f=1.0, rtol=1e-10, Y=Y)
+        ser.append((o, Y.cpu().numpy()))
+    Ys = [torch.empty(c, dtype=torch.float64, device="cuda") for c in counts]
+    tasks = [{"emb": e, "level": l, "first_sample": 2 * c, "count": c, "Y": Y}
+             for l, (e, c, Y) in enumerate(zip(embs, counts, Ys))]
+    sums, stats, st = sce.mlmc3_estimate_levels(tasks, seed, qoi_index=1, f=1.0, rtol=1e-10,
+                                                max_concurrency=3)
+    torch.cuda.synchronize()
+    assert st == 0 and all(s == 0 for s in stats)
+    for (o, y), s, Y in zip(ser, sums, Ys):
+        assert np.array_equal(Y.cpu().numpy(), y)
+        assert (s.N, s.sumY, s.sumY2, s.sumQf, s.sumQf2) == (o.N, o.sumY, o.sumY2, o.sumQf, o.sumQf2)
+        assert (s.max_iters, s.total_iters) == (o.max_iters, o.total_iters)
