@@ -401,6 +401,21 @@ __device__ __forceinline__ double cx_at(const OuterF &o, long long i) {
 }
 
 // u = lifting of the Dirichlet data: 1 on x1 = 0, 0 elsewhere
+// u = u0 (FP64 nodal values, Dirichlet values included)
+template <class O>
+__global__ void set_u_kernel(O o, const double *__restrict__ u0, int n, int vpt) {
+    const int s = blockIdx.y;
+    const long long V = (long long)(n + 1) * (n + 1);
+    FOR_VERT(V, vpt) {
+        if constexpr (std::is_same<O, OuterF>::value) {
+            const ff t = ff_from_double(u0[s * V + v]);
+            o.u[s * V + v] = make_float2(t.hi, t.lo);
+        } else {
+            o.u[s * V + v] = u0[s * V + v];
+        }
+    }
+}
+
 template <class O>
 __global__ void lift_kernel(O o, int n, int vpt) {
     const int s = blockIdx.y;
@@ -779,7 +794,7 @@ struct Solver {
 template <typename T, typename Tk>
 static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                         int *n_failed_out, int qmask) {
+                         int *n_failed_out, int qmask, const double *u_init) {
     Solver<T> S;
     S.st = st;
     S.count = count;
@@ -890,6 +905,19 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
     S.reduce(RED_ORR0, nullptr, rtol2, in_rel2);
     SCE_CUDA(cudaGetLastError());
+    // a given first iterate: the stopping rule stays relative to the lifting's
+    // residual (orr0 above); refinement starts from u_init's residual
+    if (u_init) {
+        set_u_kernel<<<g0, l0.tpb, 0, st>>>(o, u_init, n0, l0.vpt);
+        {
+            SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 24.0));
+            outer_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(o, F, n0, l0.vpt, S.b[0], S.part,
+                                                            l0.nblk, S.sc.act_out);
+        }
+        SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
+        S.reduce(RED_ORR, S.sc.act_out, rtol2, in_rel2);
+        SCE_CUDA(cudaGetLastError());
+    }
     int n_act = 0;
     SCE_TRY(S.read_counter(&n_act));
     int total_inner = 0;
@@ -1081,7 +1109,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
 
 int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                         int *n_failed_out, int qmask) {
+                         int *n_failed_out, int qmask, const double *u_init) {
     if (!p || !k || !qoi || count < 0) return CE_ERR_INVALID_ARG;
     if (!is_pow2(p->n) || p->n < 4 || p->n > 4096) return CE_ERR_INVALID_ARG;
     if (p->precision != 32 && p->precision != 64) return CE_ERR_INVALID_ARG;
@@ -1093,9 +1121,10 @@ int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, doubl
                                max_iters_out, n_failed_out, qmask);
     if (p->precision == 64)
         return darcy_solve_t<double, double>(p, (const double *)k, count, qoi, iters, status,
-                                             u_out, st, max_iters_out, n_failed_out, qmask);
+                                             u_out, st, max_iters_out, n_failed_out, qmask,
+                                             u_init);
     return darcy_solve_t<float, float>(p, (const float *)k, count, qoi, iters, status, u_out, st,
-                                       max_iters_out, n_failed_out, qmask);
+                                       max_iters_out, n_failed_out, qmask, u_init);
 }
 
 extern "C" int darcy_solve_batch(const darcy_problem *p, const void *k, int count, double *qoi,

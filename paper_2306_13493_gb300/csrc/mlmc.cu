@@ -54,6 +54,24 @@ __global__ void level_sums_kernel(const double *__restrict__ Y, const double *__
     if (threadIdx.x < 4) out4[threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// Bilinear prolongation of the coarse solution (nc cells) to the fine grid
+// (2 nc cells): the first iterate of the fine solve of the same field.  The
+// Dirichlet columns stay exact (means of equal values).
+__global__ void prolong_u_kernel(const double *__restrict__ uc, int nc, int count,
+                                 double *__restrict__ uf) {
+    const int nf = 2 * nc, wf = nf + 1, wc = nc + 1;
+    const long long Vf = (long long)wf * wf, Vc = (long long)wc * wc;
+    const long long total = (long long)count * Vf;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long s = q / Vf;
+        const int v = (int)(q - s * Vf);
+        const int j = v / wf, i = v - j * wf;
+        const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
+        const double *c = uc + s * Vc;
+        uf[q] = 0.25 * ((c[j0 * wc + i0] + c[j0 * wc + i1]) + (c[j1 * wc + i0] + c[j1 * wc + i1]));
+    }
+}
 
 struct LevelArgs {
     ce_embedding_t e;
@@ -75,7 +93,14 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
     if (count == 0) return CE_OK;
     const int n = e->n, nc = n / 2;
     const bool coarse = a.level > 0;
-    const bool split = coarse && stc != st;
+    // nested iteration: on levels with a coarse grid whose fine solve is the
+    // batched solver, the coarse solve runs first and its prolonged solution
+    // is the fine solve's first iterate (SCE_NESTED=0: both start from the
+    // lifting, the coarse solve on a second stream)
+    const bool fine_batched = !(p->precision == 32 && n <= sce_small_max_n() && n <= 64);
+    bool nested = coarse && fine_batched;
+    if (const char *ev = getenv("SCE_NESTED")) nested = nested && atoi(ev) != 0;
+    const bool split = coarse && stc != st && !nested;
     const size_t es = p->precision == 64 ? sizeof(double) : sizeof(float);
     const long long Vf = (long long)(n + 1) * (n + 1), Vc = (long long)(nc + 1) * (nc + 1);
     // chunk: bound the number of fine vertices resident at once
@@ -90,6 +115,7 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
 
     void *kf = nullptr, *kc = nullptr;
     double *qf = nullptr, *qc = nullptr, *Yd = nullptr, *sums = nullptr;
+    double *ucs = nullptr, *uf0 = nullptr;   // nested iteration: coarse solution, fine first iterate
     cudaEvent_t ev_field = nullptr, ev_coarse = nullptr;
     std::vector<void *> owned;
     auto cleanup = [&]() {
@@ -109,6 +135,11 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
     if (coarse && !a.qoi_c && (rc = A((void **)&qc, (size_t)chunk * 3 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
     if (!a.Y && (rc = A((void **)&Yd, (size_t)chunk * sizeof(double))) != CE_OK) { cleanup(); return rc; }
     if ((rc = A((void **)&sums, 4 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
+    if (nested && ((rc = A((void **)&ucs, (size_t)chunk * Vc * sizeof(double))) != CE_OK ||
+                   (rc = A((void **)&uf0, (size_t)chunk * Vf * sizeof(double))) != CE_OK)) {
+        cleanup();
+        return rc;
+    }
     if (split && (cudaEventCreateWithFlags(&ev_field, cudaEventDisableTiming) != cudaSuccess ||
                   cudaEventCreateWithFlags(&ev_coarse, cudaEventDisableTiming) != cudaSuccess)) {
         cleanup();
@@ -155,8 +186,18 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
             });
         }
         int mi[2] = {0, 0}, nf = 0;
+        if (nested) {
+            rc = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, ucs, st, mi_c, &nf_c,
+                                      qmask_c);
+            if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
+            account(rc, mi_c, nf_c);
+            const long long tot = (long long)cn * Vf;
+            prolong_u_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), 256, 0,
+                               st>>>(ucs, nc, cn, uf0);
+            if (cudaGetLastError() != cudaSuccess) { cleanup(); return CE_ERR_CUDA; }
+        }
         rc = sce_darcy_solve_impl(&pf, kf, cn, qf_c, nullptr, nullptr, nullptr, st, mi, &nf,
-                                  qmask_f);
+                                  qmask_f, nested ? uf0 : nullptr);
         const int rc_c = split ? fut.get() : CE_OK;
         if (split && rc_c != CE_OK && rc_c != CE_ERR_NOT_CONVERGED) sce_set_last_error_text(coarse_err);
         if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
@@ -165,7 +206,7 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
             if (rc_c != CE_OK && rc_c != CE_ERR_NOT_CONVERGED) { cleanup(); return rc_c; }
             account(rc_c, mi_c, nf_c);
             if (cudaStreamWaitEvent(st, ev_coarse, 0) != cudaSuccess) { cleanup(); return CE_ERR_CUDA; }
-        } else if (coarse) {
+        } else if (coarse && !nested) {
             rc = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, nullptr, st, mi, &nf,
                                       qmask_c);
             if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
