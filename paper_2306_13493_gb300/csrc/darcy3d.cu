@@ -660,6 +660,37 @@ __global__ void outer_update3_kernel(float2 *__restrict__ u, const float *__rest
     }
 }
 
+// u = u0 (FP64 nodal values, Dirichlet planes included) as float-float
+__global__ void set_u3_kernel(float2 *__restrict__ u, const double *__restrict__ u0,
+                              long long total) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const ff t = ff_from_double(u0[q]);
+        u[q] = make_float2(t.hi, t.lo);
+    }
+}
+
+// trilinear prolongation of the coarse solution (nc cells per side) to the
+// fine grid: the first iterate of the fine solve of the same field
+__global__ void prolong_u3_kernel(const double *__restrict__ uc, int nc, int count,
+                                  double *__restrict__ uf) {
+    const int nf = 2 * nc, wf = nf + 1, wc = nc + 1;
+    const long long Vf = (long long)wf * wf * wf, Vc = (long long)wc * wc * wc;
+    const long long total = (long long)count * Vf;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long s = q / Vf;
+        int i, j, k;
+        decode3((int)(q - s * Vf), wf, &i, &j, &k);
+        const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
+        const int k0 = k >> 1, k1 = (k + 1) >> 1;
+        const double *c = uc + s * Vc;
+        auto C = [&](int a, int b, int d) { return c[((long long)d * wc + b) * wc + a]; };
+        uf[q] = 0.125 * (((C(i0, j0, k0) + C(i1, j0, k0)) + (C(i0, j1, k0) + C(i1, j1, k0))) +
+                         ((C(i0, j0, k1) + C(i1, j0, k1)) + (C(i0, j1, k1) + C(i1, j1, k1))));
+    }
+}
+
 __global__ void u_to_double3_kernel(const float2 *__restrict__ u, long long total,
                                     double *__restrict__ out) {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -936,8 +967,11 @@ struct Solver3 {
     }
 };
 
+// u_init: device double[count*(n+1)^3] or NULL (the lifting): the first
+// iterate; the convergence test stays relative to the lifting's residual
 int solve3(const darcy_problem *pr, const float *k, int count, double *qoi, int *iters,
-           int *status, double *u_out, cudaStream_t st, int *misc_out, int qmask) {
+           int *status, double *u_out, cudaStream_t st, int *misc_out, int qmask,
+           const double *u_init) {
     Solver3 S;
     S.st = st;
     SCE_TRY(S.init(pr->n, count));
@@ -980,6 +1014,12 @@ int solve3(const darcy_problem *pr, const float *k, int count, double *qoi, int 
         return CE_OK;
     };
     SCE_TRY(outer_residual(nullptr, R3_ORR0));
+    if (u_init) {
+        const long long tot = (long long)count * V0;
+        set_u3_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), 256, 0, st>>>(
+            S.uf, u_init, tot);
+        SCE_TRY(outer_residual(S.sc.act_out, R3_ORR));
+    }
     int n_act = 0;
     SCE_TRY(S.read_counter(&n_act));
     int total_inner = 0;
@@ -1075,7 +1115,8 @@ int chunk3(int n) {
 }
 
 int solve3_batched(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
-                   int *status, double *u_out, cudaStream_t st, int *misc_out, int qmask) {
+                   int *status, double *u_out, cudaStream_t st, int *misc_out, int qmask,
+                   const double *u_init = nullptr) {
     const int chunk = chunk3(p->n);
     const long long V = (long long)(p->n + 1) * (p->n + 1) * (p->n + 1);
     int worst = CE_OK;
@@ -1085,7 +1126,8 @@ int solve3_batched(const darcy_problem *p, const float *k, int count, double *qo
         int m[3] = {0, 0, 0};
         const int rc = solve3(p, k + (size_t)c0 * V, cn, qoi + 3 * (size_t)c0,
                               iters ? iters + c0 : nullptr, status ? status + c0 : nullptr,
-                              u_out ? u_out + (size_t)c0 * V : nullptr, st, m, qmask);
+                              u_out ? u_out + (size_t)c0 * V : nullptr, st, m, qmask,
+                              u_init ? u_init + (size_t)c0 * V : nullptr);
         if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) return rc;
         if (rc != CE_OK) worst = rc;
         tot[0] += m[0];
@@ -1128,9 +1170,13 @@ extern "C" int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, u
     const long long Vc = (long long)(nc + 1) * (nc + 1) * (nc + 1);
     const int chunk = std::min(count, std::max(1, chunk3(n) / 2));
     float *kf = nullptr, *kc = nullptr;
-    double *qf = nullptr, *qc = nullptr;
+    double *qf = nullptr, *qc = nullptr, *ucs = nullptr, *uf0 = nullptr;
     int rc = sce_alloc_t(&kf, (size_t)chunk * Vf, st);
     if (rc == CE_OK && level > 0) rc = sce_alloc_t(&kc, (size_t)chunk * Vc, st);
+    // nested iteration: the coarse solve first, its prolonged solution the
+    // fine solve's first iterate
+    if (rc == CE_OK && level > 0) rc = sce_alloc_t(&ucs, (size_t)chunk * Vc, st);
+    if (rc == CE_OK && level > 0) rc = sce_alloc_t(&uf0, (size_t)chunk * Vf, st);
     if (rc == CE_OK) rc = sce_alloc_t(&qf, (size_t)chunk * 3, st);
     if (rc == CE_OK && level > 0) rc = sce_alloc_t(&qc, (size_t)chunk * 3, st);
     std::vector<double> hf((size_t)chunk * 3), hc((size_t)chunk * 3), hy(chunk);
@@ -1142,8 +1188,8 @@ extern "C" int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, u
         rc = ce3_sample_batch(e, seed, level, first_sample + c0, cn, kf, level > 0 ? kc : nullptr,
                               stream);
         int m[3] = {0, 0, 0};
-        if (rc == CE_OK) {
-            rc = solve3_batched(p, kf, cn, qf, nullptr, nullptr, nullptr, st, m, 1 << qoi_index);
+        if (rc == CE_OK && level > 0) {
+            rc = solve3_batched(&pc, kc, cn, qc, nullptr, nullptr, ucs, st, m, 1 << qoi_index);
             out->n_failed += m[0];
             out->max_iters = std::max(out->max_iters, m[1]);
             out->total_iters += m[2];
@@ -1151,9 +1197,16 @@ extern "C" int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, u
                 worst = rc;
                 rc = CE_OK;
             }
+            if (rc == CE_OK) {
+                const long long tot = (long long)cn * Vf;
+                prolong_u3_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), 256,
+                                    0, st>>>(ucs, nc, cn, uf0);
+                if (cudaGetLastError() != cudaSuccess) rc = CE_ERR_CUDA;
+            }
         }
-        if (rc == CE_OK && level > 0) {
-            rc = solve3_batched(&pc, kc, cn, qc, nullptr, nullptr, nullptr, st, m, 1 << qoi_index);
+        if (rc == CE_OK) {
+            rc = solve3_batched(p, kf, cn, qf, nullptr, nullptr, nullptr, st, m, 1 << qoi_index,
+                                level > 0 ? uf0 : nullptr);
             out->n_failed += m[0];
             out->max_iters = std::max(out->max_iters, m[1]);
             out->total_iters += m[2];
@@ -1196,6 +1249,8 @@ extern "C" int mlmc3_level_estimate(ce3_embedding_t e, const darcy_problem *p, u
     sce_free(kc, st);
     sce_free(qf, st);
     sce_free(qc, st);
+    sce_free(ucs, st);
+    sce_free(uf0, st);
     cudaStreamSynchronize(st);
     return rc != CE_OK ? rc : worst;
 }
