@@ -287,3 +287,23 @@ def test_mlmc3_estimate_levels_concurrent_matches_serial(sce):
         assert np.array_equal(Y.cpu().numpy(), y)
         assert (s.N, s.sumY, s.sumY2, s.sumQf, s.sumQf2) == (o.N, o.sumY, o.sumY2, o.sumQf, o.sumQf2)
         assert (s.max_iters, s.total_iters) == (o.max_iters, o.total_iters)
+
+
+def test_three_dimensional_empty_batches_and_bad_sizes(sce):
+    """count = 0 is a no-op for every 3D entry point; a problem whose n does
+    not match the handle is refused."""
+    import ctypes
+    import torch
+    emb = sce.ce3_setup_embedding(ocv.MATERN, 0.5, 0.2, 1.0, 4, pad_mode=oem.PAD_DOUBLING)
+    k = torch.empty(1, dtype=torch.float32, device="cuda")
+    q = torch.empty(3, dtype=torch.float64, device="cuda")
+    sce.ce3_sample_batch(emb, 1, 0, 0, 0, k, None)
+    assert sce.darcy3_solve_batch(4, k, 0, q) == 0
+    out, st = sce.mlmc3_level_estimate(emb, 1, 1, 0, 0)
+    assert st == 0 and out.N == 0
+    sums, stats, st = sce.mlmc3_estimate_levels([], 1)
+    assert st == 0 and sums == []
+    bad = sce.darcy_problem(8, 1.0, 1e-10, 100, 32)          # handle has n = 4
+    o = sce.mlmc_level_sums()
+    assert sce.load().mlmc3_level_estimate(emb.handle, ctypes.byref(bad), 1, 0, 0, 2, 0,
+                                           ctypes.byref(o), None, None) == sce.CE_ERR_INVALID_ARG
