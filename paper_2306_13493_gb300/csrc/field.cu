@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(256) ce_row_kernel(
         }
     }
     __syncthreads();
-    smem_fft<R, MAXB>(buf, logP, tw, t, tpf);
+    line_fft<R, MAXB>(buf, logP, tw, t, tpf);
     // split the packed transform: A = (Z[x] + conj Z[-x])/2, B = (Z[x] - conj Z[-x])/(2i)
     const R half = R(0.5);
     const int nthr = blockDim.x;
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(256) ce_col_kernel(
         for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
     }
     __syncthreads();
-    smem_fft<R, MAXB>(buf, logP, tw, t, tpf);
+    line_fft<R, MAXB>(buf, logP, tw, t, tpf);
     const R invP = R(1) / R(P);
     const int mc = m / 2;
     const int nthr = blockDim.x;
@@ -947,7 +947,10 @@ extern "C" int ce_autotune_fft(ce_embedding_t e, int precision, int count, int r
             auto it = g_tune.find(key);
             if (it != g_tune.end()) best_shape = it->second;
         }
-        for (int div : {32, 16, 8, 4}) {
+        // FP32 lines run the radix-16 FFT at P/16 threads per line (other
+        // thread counts would take the radix-4 form, with other rounding)
+        const std::vector<int> divs = es == 4 ? std::vector<int>{16} : std::vector<int>{32, 16, 8, 4};
+        for (int div : divs) {
             const int tpf = std::max(1, P / div);
             for (int fdiv : {1, 2, 4}) {
                 const int F = std::max(1, 256 / tpf / fdiv);

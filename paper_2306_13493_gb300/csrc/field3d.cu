@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) ce3_x_kernel(
         }
     }
     __syncthreads();
-    smem_fft<float, MAXB>(buf, logP, tw, t, tpf);
+    line_fft<float, MAXB>(buf, logP, tw, t, tpf);
     // split the packed transform: A = (Z[x] + conj Z[-x])/2, B = (Z[x] - conj Z[-x])/(2i)
     const float half = 0.5f;
     const int nthr = blockDim.x;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) ce3_y_kernel(const float2 *__restrict__ Y
     const float2 *src = Yin + (((size_t)sl * P + k30 + f) * nx + x) * P;
     for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
     __syncthreads();
-    smem_fft<float, MAXB>(buf, logP, tw, t, tpf);
+    line_fft<float, MAXB>(buf, logP, tw, t, tpf);
     const int total = ny * F;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int yo = idx / F, ff = idx - yo * F;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256) ce3_z_kernel(const float2 *__restrict__ Y
         for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
     }
     __syncthreads();
-    smem_fft<float, MAXB>(buf, logP, tw, t, tpf);
+    line_fft<float, MAXB>(buf, logP, tw, t, tpf);
     const int total = nz * F;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int zo = idx / F, ff = idx - zo * F;
