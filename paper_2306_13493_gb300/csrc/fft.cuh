@@ -212,14 +212,14 @@ __device__ __forceinline__ void fft_last_pass(R2 *buf, int N, const R2 *__restri
     __syncthreads();
 }
 
+// Passes from span Ns on (Ns = 1: the whole transform).
 template <typename R>
-__device__ __forceinline__ void smem_fft16(typename C2<R>::T *buf, int logN,
-                                           const typename C2<R>::T *__restrict__ tw, int tid,
-                                           int nthr) {
+__device__ __forceinline__ void smem_fft16_from(typename C2<R>::T *buf, int logN,
+                                                const typename C2<R>::T *__restrict__ tw, int tid,
+                                                int nthr, int Ns) {
     using R2 = typename C2<R>::T;
     const int N = 1 << logN;
     const int nb16 = N >> 4;   // == nthr
-    int Ns = 1;
     for (; (Ns << 4) <= N; Ns <<= 4) {
         R2 v[16];
         const int j = tid;
@@ -242,6 +242,29 @@ __device__ __forceinline__ void smem_fft16(typename C2<R>::T *buf, int logN,
     if (rf == 8) fft_last_pass<R2, R, 8>(buf, N, tw, tid, nthr);
     else if (rf == 4) fft_last_pass<R2, R, 4>(buf, N, tw, tid, nthr);
     else if (rf == 2) fft_last_pass<R2, R, 2>(buf, N, tw, tid, nthr);
+}
+
+template <typename R>
+__device__ __forceinline__ void smem_fft16(typename C2<R>::T *buf, int logN,
+                                           const typename C2<R>::T *__restrict__ tw, int tid,
+                                           int nthr) {
+    smem_fft16_from<R>(buf, logN, tw, tid, nthr, 1);
+}
+
+// The radix-16 transform of a line whose first-pass inputs v[r] = x[tid + r N/16]
+// are already in registers (loaded by the caller straight from global memory):
+// the first pass writes its outputs to the (padded) shared line, the others
+// follow.  N >= 16, nthr = N/16.
+template <typename R>
+__device__ __forceinline__ void smem_fft16_regs(typename C2<R>::T *buf,
+                                                typename C2<R>::T v[16], int logN,
+                                                const typename C2<R>::T *__restrict__ tw,
+                                                int tid, int nthr) {
+    dft16<typename C2<R>::T, R>(v);
+#pragma unroll
+    for (int p = 0; p < 16; ++p) buf[fft_pad(16 * tid + p)] = v[4 * (p & 3) + (p >> 2)];
+    __syncthreads();
+    smem_fft16_from<R>(buf, logN, tw, tid, nthr, 16);
 }
 
 // The line FFT of the per-sample passes: in FP32, radix 16 when the line has

@@ -296,9 +296,16 @@ __global__ void __launch_bounds__(256) ce3_y_kernel(const float2 *__restrict__ Y
     const int LP = fft_line_pitch(P);
     float2 *buf = sm + (size_t)f * LP;
     const float2 *src = Yin + (((size_t)sl * P + k30 + f) * nx + x) * P;
-    for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
-    __syncthreads();
-    line_fft<float, MAXB>(buf, logP, tw, t, tpf);
+    if (tpf * 16 == P) {   // radix 16: the first pass's inputs straight into registers
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = src[t + r * tpf];
+        smem_fft16_regs<float>(buf, v, logP, tw, t, tpf);
+    } else {
+        for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
+        __syncthreads();
+        line_fft<float, MAXB>(buf, logP, tw, t, tpf);
+    }
     const int total = ny * F;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int yo = idx / F, ff = idx - yo * F;
@@ -325,12 +332,20 @@ __global__ void __launch_bounds__(256) ce3_z_kernel(const float2 *__restrict__ Y
     const int f = threadIdx.x / tpf, t = threadIdx.x - f * tpf;
     const int LP = fft_line_pitch(P);
     float2 *buf = sm + (size_t)f * LP;
-    if (x0 + f < nx) {
-        const float2 *src = Yin + (((size_t)sl * ny + yo) * nx + x0 + f) * P;
-        for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
+    if (tpf * 16 == P) {   // radix 16: the first pass's inputs straight into registers
+        float2 v[16];
+        const float2 *src = Yin + (((size_t)sl * ny + yo) * nx + min(x0 + f, nx - 1)) * P;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = src[t + r * tpf];
+        smem_fft16_regs<float>(buf, v, logP, tw, t, tpf);
+    } else {
+        if (x0 + f < nx) {
+            const float2 *src = Yin + (((size_t)sl * ny + yo) * nx + x0 + f) * P;
+            for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
+        }
+        __syncthreads();
+        line_fft<float, MAXB>(buf, logP, tw, t, tpf);
     }
-    __syncthreads();
-    line_fft<float, MAXB>(buf, logP, tw, t, tpf);
     const int total = nz * F;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int zo = idx / F, ff = idx - zo * F;
