@@ -415,7 +415,7 @@ __device__ __forceinline__ void row_normals4(uint64_t seed, uint32_t level, uint
 }
 
 template <typename R, int MAXB, bool QMC = false>
-__global__ void __launch_bounds__(256) ce_row_kernel(
+__global__ void __launch_bounds__(256, 4) ce_row_kernel(
     const R *__restrict__ sq_f, const R *__restrict__ sq_c, const typename C2<R>::T *__restrict__ tw,
     int P, int logP, int m, uint64_t seed, uint32_t level, uint64_t first_sample, int F, int tpf,
     typename C2<R>::T *__restrict__ Yf, typename C2<R>::T *__restrict__ Yc, QmcArgs qa) {
