@@ -234,55 +234,7 @@ __global__ void coarsest_kernel(const T *__restrict__ cx, const T *__restrict__ 
 }
 
 // ---------------------------------------------------------------- Krylov pieces
-template <typename T, int VPT = 0>
-__global__ void spmv_dot_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
-                                const T *__restrict__ p, T *__restrict__ q, int n, int vpt,
-                                double *__restrict__ part, int nblk, const int *__restrict__ act) {
-    __shared__ T sh[32];
-    const int s = blockIdx.y;
-    if (!act[s]) return;
-    const long long V = (long long)(n + 1) * (n + 1);
-    const int w = n + 1;
-    const T *ax = cx + s * V, *ay = cy + s * V, *ps = p + s * V;
-    T *qs = q + s * V;
-    T acc = T(0);
-    FOR_VERT_C(V, VPT, vpt) {
-        const int j = v / w, i = v - j * w;
-        T val = T(0);
-        if (i > 0 && i < n) {
-            const T pc = ps[v];
-            val = ax[v - 1] * (pc - ps[v - 1]) + ax[v] * (pc - ps[v + 1]);
-            if (j > 0) val += ay[v - w] * (pc - ps[v - w]);
-            if (j < n) val += ay[v] * (pc - ps[v + w]);
-            acc += pc * val;
-        }
-        qs[v] = val;
-    }
-    const T tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
-}
 
-template <typename T, int VPT = 0>
-__global__ void axpy2_kernel(T *__restrict__ d, T *__restrict__ r, const T *__restrict__ p,
-                             const T *__restrict__ q, const double *__restrict__ alpha, int n,
-                             int vpt, double *__restrict__ part, int nblk,
-                             const int *__restrict__ act) {
-    __shared__ T sh[32];
-    const int s = blockIdx.y;
-    if (!act[s]) return;
-    const long long V = (long long)(n + 1) * (n + 1);
-    const T a = (T)alpha[s];
-    T acc = T(0);
-    FOR_VERT_C(V, VPT, vpt) {
-        const long long g = s * V + v;
-        d[g] += a * p[g];
-        const T rv = r[g] - a * q[g];
-        r[g] = rv;
-        acc += rv * rv;
-    }
-    const T tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
-}
 
 template <typename T>
 __global__ void dot_kernel(const T *__restrict__ a, const T *__restrict__ b, int n, int vpt,
@@ -297,33 +249,93 @@ __global__ void dot_kernel(const T *__restrict__ a, const T *__restrict__ b, int
     if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
 }
 
+
+
+// Fused CG pass of iteration k (one read of p_{k-1}): p_k = z + beta p_{k-1}
+// (beta = 0 at the start of an inner solve, so p_0 = z), the deferred update
+// d += alpha_{k-1} p_{k-1} of iteration k-1 (alpha = 0 at the start), q = A p_k
+// and the p_k.q partials.  p ping-pongs: p_in holds p_{k-1}, p_out gets p_k;
+// the neighbours' p_k are formed from z and p_in, so no block reads what
+// another writes.  On the Dirichlet columns z = p = 0, so p_k stays 0 there.
 template <typename T, int VPT = 0>
-__global__ void pupdate_kernel(T *__restrict__ p, const T *__restrict__ z,
-                               const double *__restrict__ beta, int n, int vpt,
+__global__ void pspmv_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
+                             const T *__restrict__ z, const T *__restrict__ p_in,
+                             T *__restrict__ p_out, T *__restrict__ q, T *__restrict__ d,
+                             const double *__restrict__ beta, const double *__restrict__ alpha,
+                             int n, int vpt, double *__restrict__ part, int nblk,
+                             const int *__restrict__ act) {
+    __shared__ T sh[32];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const int w = n + 1;
+    const T bt = (T)beta[s], al = (T)alpha[s];
+    const T *ax = cx + s * V, *ay = cy + s * V, *zs = z + s * V, *pi = p_in + s * V;
+    T *po = p_out + s * V, *qs = q + s * V, *ds = d + s * V;
+    auto pk = [&](long long u) { return zs[u] + bt * pi[u]; };
+    T acc = T(0);
+    FOR_VERT_C(V, VPT, vpt) {
+        const int j = v / w, i = v - j * w;
+        const T pold = pi[v];
+        const T pc = zs[v] + bt * pold;
+        po[v] = pc;
+        ds[v] += al * pold;
+        T val = T(0);
+        if (i > 0 && i < n) {
+            val = ax[v - 1] * (pc - pk(v - 1)) + ax[v] * (pc - pk(v + 1));
+            if (j > 0) val += ay[v - w] * (pc - pk(v - w));
+            if (j < n) val += ay[v] * (pc - pk(v + w));
+            acc += pc * val;
+        }
+        qs[v] = val;
+    }
+    const T tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
+}
+
+// r -= alpha q and the r.r partials (the d update is deferred to pspmv_kernel)
+template <typename T, int VPT = 0>
+__global__ void rupdate_kernel(T *__restrict__ r, const T *__restrict__ q,
+                               const double *__restrict__ alpha, int n, int vpt,
+                               double *__restrict__ part, int nblk, const int *__restrict__ act) {
+    __shared__ T sh[32];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const T a = (T)alpha[s];
+    T acc = T(0);
+    FOR_VERT_C(V, VPT, vpt) {
+        const long long g = s * V + v;
+        const T rv = r[g] - a * q[g];
+        r[g] = rv;
+        acc += rv * rv;
+    }
+    const T tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
+}
+
+// The last deferred update of an inner solve: d += alpha p with the p array
+// (ppar) the sample's last iteration wrote.
+template <typename T>
+__global__ void dfinish_kernel(T *__restrict__ d, const T *__restrict__ p0,
+                               const T *__restrict__ p1, const double *__restrict__ alpha,
+                               const int *__restrict__ ppar, int n, int vpt,
                                const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
-    const T bt = (T)beta[s];
-    FOR_VERT_C(V, VPT, vpt) {
+    const T a = (T)alpha[s];
+    const T *p = ppar[s] ? p1 : p0;
+    FOR_VERT(V, vpt) {
         const long long g = s * V + v;
-        p[g] = z[g] + bt * p[g];
+        d[g] += a * p[g];
     }
 }
 
-template <typename T, int VPT = 0>
-__global__ void copy_kernel(T *__restrict__ dst, const T *__restrict__ src, int n, int vpt,
-                            const int *__restrict__ act) {
-    const int s = blockIdx.y;
-    if (!act[s]) return;
-    const long long V = (long long)(n + 1) * (n + 1);
-    FOR_VERT_C(V, VPT, vpt) dst[s * V + v] = src[s * V + v];
-}
-
-// Per-sample scalar state.
+// Per-sample scalar state.  ppar: the p array of the pending update (alpha, p).
 struct Scal {
     double *rz, *pq, *rr, *rr0, *alpha, *beta, *orr, *orr0, *thr;
-    int *act_out, *act_in, *iters, *counter;
+    int *act_out, *act_in, *iters, *counter, *ppar;
 };
 
 enum { RED_ALPHA = 0, RED_RR = 1, RED_BETA = 2, RED_RZ0 = 3, RED_ORR = 4, RED_ORR0 = 5 };
@@ -332,7 +344,7 @@ enum { RED_ALPHA = 0, RED_RR = 1, RED_BETA = 2, RED_RZ0 = 3, RED_ORR = 4, RED_OR
 // scalar update of `mode`.
 __global__ void reduce_kernel(const double *__restrict__ part, int nblk, int count, int mode,
                               Scal sc, const int *__restrict__ act, double rtol2,
-                              double in_rel2) {
+                              double in_rel2, int par) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= count) return;
     const int s = warp;
@@ -345,6 +357,7 @@ __global__ void reduce_kernel(const double *__restrict__ part, int nblk, int cou
         case RED_ALPHA:
             sc.pq[s] = v;
             sc.alpha[s] = v > 0.0 ? sc.rz[s] / v : 0.0;
+            sc.ppar[s] = par;
             break;
         case RED_RR: {
             sc.rr[s] = v;
@@ -651,6 +664,8 @@ struct Solver {
     T *cx[MAXLEV], *cy[MAXLEV], *b[MAXLEV], *z[MAXLEV];
     T *zpre[MAXLEV] = {};   // pre-smoothed z of the tiled levels (fused cycle)
     T *d = nullptr, *p = nullptr, *q = nullptr;
+    T *p2 = nullptr;   // second p array (p ping-pongs between p and p2)
+    int par = 0;       // the array the next fused pass writes: 0 = p, 1 = p2
     double *u64 = nullptr;                  // FP64 path: u
     float2 *uff = nullptr;                  // mixed path: u as float-float pairs
     float *cxl = nullptr, *cyl = nullptr;   // mixed path: lo parts of the conductances
@@ -775,13 +790,14 @@ struct Solver {
         }
     }
 
-    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0, int nblk = -1) {
+    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0, int nblk = -1,
+                int rpar = 0) {
         const int threads = 256;
         const int blocks = (count * 32 + threads - 1) / threads;
         if (nblk < 0) nblk = ln[0].nblk;
         SceProf pr(KP_REDUCE, st, (double)count * nblk * 8.0);
         reduce_kernel<<<blocks, threads, 0, st>>>(part, nblk, count, mode, sc, act, rtol2,
-                                                  in_rel2);
+                                                  in_rel2, rpar);
     }
 
     int read_counter(int *host) {
@@ -817,6 +833,10 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     const size_t c0 = (size_t)count * V0;
     SCE_TRY(S.alloc(&S.d, c0));
     SCE_TRY(S.alloc(&S.p, c0));
+    SCE_TRY(S.alloc(&S.p2, c0));
+    // both p arrays start finite (the first fused pass multiplies p_in by 0)
+    SCE_CUDA(cudaMemsetAsync(S.p, 0, c0 * sizeof(T), st));
+    SCE_CUDA(cudaMemsetAsync(S.p2, 0, c0 * sizeof(T), st));
     SCE_TRY(S.alloc(&S.q, c0));
     constexpr bool mixed = sizeof(T) == 4;
     using O = std::conditional_t<mixed, OuterF, OuterD>;
@@ -862,13 +882,14 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     S.sc.orr0 = scal + 7 * count;
     S.sc.thr = scal + 8 * count;
     int *ints = nullptr;
-    SCE_TRY(S.alloc(&ints, (size_t)count * 3 + 4));
+    SCE_TRY(S.alloc(&ints, (size_t)count * 4 + 4));
     S.sc.act_out = ints;
     S.sc.act_in = ints + count;
     S.sc.iters = ints + 2 * count;
-    S.misc = ints + 3 * count;
+    S.sc.ppar = ints + 3 * count;
+    S.misc = ints + 4 * count;
     S.sc.counter = S.misc;
-    SCE_CUDA(cudaMemsetAsync(ints, 0, ((size_t)count * 3 + 4) * sizeof(int), st));
+    SCE_CUDA(cudaMemsetAsync(ints, 0, ((size_t)count * 4 + 4) * sizeof(int), st));
 
     const Launch &l0 = S.ln[0];
     const dim3 g0 = S.grid(0);
@@ -922,32 +943,37 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     SCE_TRY(S.read_counter(&n_act));
     int total_inner = 0;
 
-    // one CG iteration: q = A p, alpha, d += alpha p, r -= alpha q, |r|^2 ...
+    // one CG iteration: p = z + beta p, the deferred d += alpha p, q = A p,
+    // alpha, r -= alpha q, |r|^2 ...
     auto iter_head = [&]() -> int {
+        T *pin = S.par ? S.p : S.p2, *pout = S.par ? S.p2 : S.p;
         {
-            SceProf pr(KP_SPMV, st, S.vb(0, 4.0));
+            // reads cx, cy, z, p_in, d; writes p_out, d, q
+            SceProf pr(KP_SPMV, st, S.vb(0, 8.0));
             if (l0.vpt == 8)
-                spmv_dot_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.p, S.q, n0, 8,
-                                                             S.part, l0.nblk, S.sc.act_in);
-            else
-                spmv_dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.p, S.q, n0, l0.vpt,
+                pspmv_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.z[0], pin, pout, S.q,
+                                                          S.d, S.sc.beta, S.sc.alpha, n0, 8,
                                                           S.part, l0.nblk, S.sc.act_in);
+            else
+                pspmv_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.z[0], pin, pout, S.q,
+                                                       S.d, S.sc.beta, S.sc.alpha, n0, l0.vpt,
+                                                       S.part, l0.nblk, S.sc.act_in);
         }
-        S.reduce(RED_ALPHA, S.sc.act_in);
+        S.reduce(RED_ALPHA, S.sc.act_in, 0.0, 0.0, -1, S.par);
         {
-            SceProf pr(KP_AXPY, st, S.vb(0, 6.0));
+            SceProf pr(KP_AXPY, st, S.vb(0, 3.0));
             if (l0.vpt == 8)
-                axpy2_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.d, S.b[0], S.p, S.q, S.sc.alpha, n0, 8,
-                                                          S.part, l0.nblk, S.sc.act_in);
+                rupdate_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.b[0], S.q, S.sc.alpha, n0, 8, S.part,
+                                                            l0.nblk, S.sc.act_in);
             else
-                axpy2_kernel<T><<<g0, l0.tpb, 0, st>>>(S.d, S.b[0], S.p, S.q, S.sc.alpha, n0,
-                                                       l0.vpt, S.part, l0.nblk, S.sc.act_in);
+                rupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.q, S.sc.alpha, n0, l0.vpt,
+                                                         S.part, l0.nblk, S.sc.act_in);
         }
         SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
         S.reduce(RED_RR, S.sc.act_in);
         return CE_OK;
     };
-    // ... and z = M^-1 r, beta, p = z + beta p
+    // ... and z = M^-1 r, beta (the p update is the next iteration's fused pass)
     auto iter_tail = [&]() -> int {
         if (S.fused) {
             S.vcycle_fused(true);
@@ -959,15 +985,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
                                                  S.sc.act_in);
         }
         S.reduce(RED_BETA, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
-        {
-            SceProf pr(KP_PUPDATE, st, S.vb(0, 3.0));
-            if (l0.vpt == 8)
-                pupdate_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], S.sc.beta, n0, 8,
-                                                            S.sc.act_in);
-            else
-                pupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], S.sc.beta, n0, l0.vpt,
-                                                         S.sc.act_in);
-        }
+        S.par ^= 1;
         return CE_OK;
     };
     // CUDA graph of check_every iterations (head + tail each), replayed, when
@@ -1014,8 +1032,12 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         return CE_OK;
     };
     for (int outer = 0; outer < 64 && n_act > 0 && total_inner < maxit; ++outer) {
-        // inner PCG on the correction equation, samples with act_in set
+        // inner PCG on the correction equation, samples with act_in set; no
+        // pending d update and p_0 = z (alpha = beta = 0)
         SCE_CUDA(cudaMemsetAsync(S.d, 0, c0 * sizeof(T), st));
+        SCE_CUDA(cudaMemsetAsync(S.sc.alpha, 0, (size_t)count * sizeof(double), st));
+        SCE_CUDA(cudaMemsetAsync(S.sc.beta, 0, (size_t)count * sizeof(double), st));
+        S.par = 0;
         if (S.fused) {
             S.vcycle_fused(true);
         } else {
@@ -1024,13 +1046,6 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
             SceProf pr(KP_DOT, st, S.vb(0, 2.0));
             dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.z[0], n0, l0.vpt, S.part, l0.nblk,
                                                  S.sc.act_in);
-        }
-        {
-            SceProf pr(KP_COPY, st, S.vb(0, 2.0));
-            if (l0.vpt == 8)
-                copy_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], n0, 8, S.sc.act_in);
-            else
-                copy_kernel<T><<<g0, l0.tpb, 0, st>>>(S.p, S.z[0], n0, l0.vpt, S.sc.act_in);
         }
         S.reduce(RED_RZ0, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
         int in_act = n_act;
@@ -1056,6 +1071,12 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
                 if (in_act == 0) break;
             }
             SCE_TRY(iter_tail());
+        }
+        {
+            // the pending d += alpha p of every sample's last iteration
+            SceProf pr(KP_COPY, st, S.vb(0, 3.0));
+            dfinish_kernel<T><<<g0, l0.tpb, 0, st>>>(S.d, S.p, S.p2, S.sc.alpha, S.sc.ppar, n0,
+                                                     l0.vpt, S.sc.act_out);
         }
         SCE_CUDA(cudaGetLastError());
         {
