@@ -314,23 +314,6 @@ __global__ void rupdate_kernel(T *__restrict__ r, const T *__restrict__ q,
     if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
 }
 
-// The last deferred update of an inner solve: d += alpha p with the p array
-// (ppar) the sample's last iteration wrote.
-template <typename T>
-__global__ void dfinish_kernel(T *__restrict__ d, const T *__restrict__ p0,
-                               const T *__restrict__ p1, const double *__restrict__ alpha,
-                               const int *__restrict__ ppar, int n, int vpt,
-                               const int *__restrict__ act) {
-    const int s = blockIdx.y;
-    if (!act[s]) return;
-    const long long V = (long long)(n + 1) * (n + 1);
-    const T a = (T)alpha[s];
-    const T *p = ppar[s] ? p1 : p0;
-    FOR_VERT(V, vpt) {
-        const long long g = s * V + v;
-        d[g] += a * p[g];
-    }
-}
 
 // Per-sample scalar state.  ppar: the p array of the pending update (alpha, p).
 struct Scal {
@@ -414,17 +397,25 @@ __device__ __forceinline__ double cx_at(const OuterF &o, long long i) {
 }
 
 // u = lifting of the Dirichlet data: 1 on x1 = 0, 0 elsewhere
-// u = u0 (FP64 nodal values, Dirichlet values included)
+// u = the bilinear prolongation of uc, the FP64 solution of the same field on
+// the n/2-cell grid (the first iterate of nested iteration; the Dirichlet
+// columns stay exact, means of equal values)
 template <class O>
-__global__ void set_u_kernel(O o, const double *__restrict__ u0, int n, int vpt) {
+__global__ void set_u_kernel(O o, const double *__restrict__ uc, int n, int vpt) {
     const int s = blockIdx.y;
     const long long V = (long long)(n + 1) * (n + 1);
+    const int w = n + 1, nc = n / 2, wc = nc + 1;
+    const double *c = uc + (long long)s * wc * wc;
     FOR_VERT(V, vpt) {
+        const int j = v / w, i = v - j * w;
+        const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
+        const double u = 0.25 * ((c[j0 * wc + i0] + c[j0 * wc + i1]) +
+                                 (c[j1 * wc + i0] + c[j1 * wc + i1]));
         if constexpr (std::is_same<O, OuterF>::value) {
-            const ff t = ff_from_double(u0[s * V + v]);
+            const ff t = ff_from_double(u);
             o.u[s * V + v] = make_float2(t.hi, t.lo);
         } else {
-            o.u[s * V + v] = u0[s * V + v];
+            o.u[s * V + v] = u;
         }
     }
 }
@@ -520,21 +511,28 @@ __global__ void initial_residual_kernel(O o, Load F, int n, int vpt, T *__restri
     if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
 }
 
-// u += d (float-float + float on the mixed path)
+// u += d + alpha p: the inner solve's correction with its last deferred CG
+// update (alpha and the p array ppar of the sample's last iteration; alpha = 0
+// when none is pending).  float-float + float on the mixed path.
 template <typename T, class O>
-__global__ void outer_update_kernel(O o, const T *__restrict__ d, int n, int vpt,
+__global__ void outer_update_kernel(O o, const T *__restrict__ d, const T *__restrict__ p0,
+                                    const T *__restrict__ p1, const double *__restrict__ alpha,
+                                    const int *__restrict__ ppar, int n, int vpt,
                                     const int *__restrict__ act) {
     const int s = blockIdx.y;
     if (!act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
+    const T a = (T)alpha[s];
+    const T *p = ppar[s] ? p1 : p0;
     FOR_VERT(V, vpt) {
         const long long g = s * V + v;
+        const T dv = d[g] + a * p[g];
         if constexpr (std::is_same<O, OuterF>::value) {
             const float2 t = o.u[g];
-            const ff r = ff_add_f(ff{t.x, t.y}, (float)d[g]);
+            const ff r = ff_add_f(ff{t.x, t.y}, (float)dv);
             o.u[g] = make_float2(r.hi, r.lo);
         } else {
-            o.u[g] += (double)d[g];
+            o.u[g] += (double)dv;
         }
     }
 }
@@ -1072,16 +1070,12 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
             }
             SCE_TRY(iter_tail());
         }
-        {
-            // the pending d += alpha p of every sample's last iteration
-            SceProf pr(KP_COPY, st, S.vb(0, 3.0));
-            dfinish_kernel<T><<<g0, l0.tpb, 0, st>>>(S.d, S.p, S.p2, S.sc.alpha, S.sc.ppar, n0,
-                                                     l0.vpt, S.sc.act_out);
-        }
         SCE_CUDA(cudaGetLastError());
         {
-            SceProf pr(KP_OUTER_UPD, st, S.vb(0, 1.0, 16.0));
-            outer_update_kernel<T><<<g0, l0.tpb, 0, st>>>(o, S.d, n0, l0.vpt, S.sc.act_out);
+            // reads d, p and u, writes u (the last deferred CG update folded in)
+            SceProf pr(KP_OUTER_UPD, st, S.vb(0, 2.0, 16.0));
+            outer_update_kernel<T><<<g0, l0.tpb, 0, st>>>(o, S.d, S.p, S.p2, S.sc.alpha,
+                                                          S.sc.ppar, n0, l0.vpt, S.sc.act_out);
         }
         {
             // reads u (8 B) and both conductances (16 B: FP64, or FP32 hi + lo), writes rin

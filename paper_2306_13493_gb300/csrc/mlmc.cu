@@ -54,24 +54,6 @@ __global__ void level_sums_kernel(const double *__restrict__ Y, const double *__
     if (threadIdx.x < 4) out4[threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// Bilinear prolongation of the coarse solution (nc cells) to the fine grid
-// (2 nc cells): the first iterate of the fine solve of the same field.  The
-// Dirichlet columns stay exact (means of equal values).
-__global__ void prolong_u_kernel(const double *__restrict__ uc, int nc, int count,
-                                 double *__restrict__ uf) {
-    const int nf = 2 * nc, wf = nf + 1, wc = nc + 1;
-    const long long Vf = (long long)wf * wf, Vc = (long long)wc * wc;
-    const long long total = (long long)count * Vf;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (long long)gridDim.x * blockDim.x) {
-        const long long s = q / Vf;
-        const int v = (int)(q - s * Vf);
-        const int j = v / wf, i = v - j * wf;
-        const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
-        const double *c = uc + s * Vc;
-        uf[q] = 0.25 * ((c[j0 * wc + i0] + c[j0 * wc + i1]) + (c[j1 * wc + i0] + c[j1 * wc + i1]));
-    }
-}
 
 struct LevelArgs {
     ce_embedding_t e;
@@ -115,7 +97,7 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
 
     void *kf = nullptr, *kc = nullptr;
     double *qf = nullptr, *qc = nullptr, *Yd = nullptr, *sums = nullptr;
-    double *ucs = nullptr, *uf0 = nullptr;   // nested iteration: coarse solution, fine first iterate
+    double *ucs = nullptr;   // nested iteration: the coarse solution
     cudaEvent_t ev_field = nullptr, ev_coarse = nullptr;
     std::vector<void *> owned;
     auto cleanup = [&]() {
@@ -135,8 +117,7 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
     if (coarse && !a.qoi_c && (rc = A((void **)&qc, (size_t)chunk * 3 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
     if (!a.Y && (rc = A((void **)&Yd, (size_t)chunk * sizeof(double))) != CE_OK) { cleanup(); return rc; }
     if ((rc = A((void **)&sums, 4 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
-    if (nested && ((rc = A((void **)&ucs, (size_t)chunk * Vc * sizeof(double))) != CE_OK ||
-                   (rc = A((void **)&uf0, (size_t)chunk * Vf * sizeof(double))) != CE_OK)) {
+    if (nested && (rc = A((void **)&ucs, (size_t)chunk * Vc * sizeof(double))) != CE_OK) {
         cleanup();
         return rc;
     }
@@ -191,13 +172,9 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
                                       qmask_c);
             if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
             account(rc, mi_c, nf_c);
-            const long long tot = (long long)cn * Vf;
-            prolong_u_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 1 << 20), 256, 0,
-                               st>>>(ucs, nc, cn, uf0);
-            if (cudaGetLastError() != cudaSuccess) { cleanup(); return CE_ERR_CUDA; }
         }
         rc = sce_darcy_solve_impl(&pf, kf, cn, qf_c, nullptr, nullptr, nullptr, st, mi, &nf,
-                                  qmask_f, nested ? uf0 : nullptr);
+                                  qmask_f, nested ? ucs : nullptr);
         const int rc_c = split ? fut.get() : CE_OK;
         if (split && rc_c != CE_OK && rc_c != CE_ERR_NOT_CONVERGED) sce_set_last_error_text(coarse_err);
         if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }

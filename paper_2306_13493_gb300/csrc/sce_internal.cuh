@@ -134,8 +134,9 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
 // Darcy solver entry used by mlmc_level_estimate.  max_iters_out, if not
 // NULL, points at int[2]: {max iterations over the samples, total iterations}.
 // qmask selects the QoIs computed (bit 0 outflow, 1 point value, 2 L2 norm;
-// the others are written as 0).  u_init (device, count*(n+1)^2 doubles, or
-// NULL = the lifting) is the first iterate of the batched solver; the
+// the others are written as 0).  u_init (device, count*(n/2+1)^2 doubles, or
+// NULL = the lifting): the solution of the same field on the n/2-cell grid,
+// whose bilinear prolongation is the batched solver's first iterate; the
 // convergence test stays relative to the lifting's residual.  The one-block
 // solver (small n) ignores it.
 int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
