@@ -92,12 +92,31 @@ struct TileBlock {
 };
 
 // Loads b, cx, cy of the block (zero outside the grid); returns the bitmask
-// of elements that are unknowns (1 <= gi <= n-1, 0 <= gj <= n).
+// of elements that are unknowns (1 <= gi <= n-1, 0 <= gj <= n).  inside: the
+// whole window lies in the grid (block-uniform), so no element needs a bounds
+// test and the rows are constant offsets from one base per lane.
 template <typename T>
 __device__ __forceinline__ unsigned tile_load(TileBlock<T> &t, const T *bs, const T *xs,
-                                              const T *ys, int gi0, int gj0, int n) {
+                                              const T *ys, int gi0, int gj0, int n,
+                                              bool inside) {
     const int w = n + 1;
     unsigned unk = 0;
+    if (inside) {
+        const long long base = (long long)gj0 * w + gi0;
+        const T *pb = bs + base, *px = xs + base, *py = ys + base;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int e = 2 * r + c, o = r * w + c;
+                t.b[e] = pb[o];
+                t.cxe[e] = px[o];
+                t.cyn[e] = py[o];
+                if (gi0 + c >= 1 && gi0 + c <= n - 1) unk |= 1u << e;
+            }
+        }
+        return unk;
+    }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
 #pragma unroll
@@ -218,8 +237,10 @@ __global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM 
     const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
     const int I0 = tx * MG_CW, J0 = ty * MG_CH;
     const int gi0 = 2 * I0 - 4 + 2 * lane, gj0 = 2 * J0 - 4 + 4 * warp;
+    const bool inside = 2 * I0 - 4 >= 0 && 2 * I0 - 4 + MG_SW - 1 <= n && 2 * J0 - 4 >= 0 &&
+                        2 * J0 - 4 + MG_SH - 1 <= n;
     TileBlock<T> t;
-    const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n);
+    const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n, inside);
     tile_diag(t, xrow, lane, warp, unk);
     // red from z = 0: z = b / diag at red elements ((c + r) even), 0 at black
 #pragma unroll
@@ -293,16 +314,26 @@ __global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM 
         szc[q] = (cj < MG_CCH && I >= 0 && I <= nc && J >= 0 && J <= nc)
                      ? zcs[(long long)J * wc + I] : T(0);
     }
+    const bool inside = 2 * I0 - 2 >= 0 && 2 * I0 - 2 + MG_SW - 1 <= n && 2 * J0 - 2 >= 0 &&
+                        2 * J0 - 2 + MG_SH - 1 <= n;
     TileBlock<T> t;
-    const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n);
+    const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n, inside);
     const T *zps = zpre + s * V;
+    if (inside) {
+        const T *pz = zps + (long long)gj0 * w + gi0;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int gi = gi0 + c, gj = gj0 + r;
-            t.z[2 * r + c] = (gi >= 0 && gi <= n && gj >= 0 && gj <= n)
-                                 ? zps[(long long)gj * w + gi] : T(0);
+            for (int c = 0; c < 2; ++c) t.z[2 * r + c] = pz[r * w + c];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int gi = gi0 + c, gj = gj0 + r;
+                t.z[2 * r + c] = (gi >= 0 && gi <= n && gj >= 0 && gj <= n)
+                                     ? zps[(long long)gj * w + gi] : T(0);
+            }
         }
     }
     tile_diag(t, xrow, lane, warp, unk);   // its barrier also covers szc
