@@ -164,7 +164,7 @@ __global__ void smooth_kernel(const T *__restrict__ cx, const T *__restrict__ cy
         T acc = bs[v] + cw * zs[v - 1] + ce * zs[v + 1];
         if (j > 0) acc += cs * zs[v - w];
         if (j < n) acc += cn * zs[v + w];
-        zs[v] = acc / (cw + ce + cs + cn);
+        zs[v] = smooth_div(acc, cw + ce + cs + cn);
     }
 }
 

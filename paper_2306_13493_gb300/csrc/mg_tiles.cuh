@@ -78,7 +78,7 @@ __device__ __forceinline__ T block_sum_t(T val, T *sh) {
 }
 
 template <typename T> __device__ __forceinline__ T recip(T d);
-template <> __device__ __forceinline__ float recip<float>(float d) { return __frcp_rn(d); }
+template <> __device__ __forceinline__ float recip<float>(float d) { return __fdividef(1.0f, d); }
 template <> __device__ __forceinline__ double recip<double>(double d) { return 1.0 / d; }
 
 // A lane's 2 x 4 block: element e = 2 r + c is window element

@@ -131,6 +131,12 @@ __device__ __forceinline__ T resid_at(const T *ax, const T *ay, const T *b, cons
     return b[j * (n + 1) + i] - apply_at(ax, ay, z, i, j, n);
 }
 
+// Division in the smoothers: the fast single-precision form in FP32 (a
+// smoother only has to be a fixed symmetric operation, the refinement removes
+// its rounding), the correctly rounded one in FP64.
+__device__ __forceinline__ float smooth_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double smooth_div(double a, double b) { return a / b; }
+
 // Gauss-Seidel update of one unknown vertex.
 template <typename T>
 __device__ __forceinline__ void smooth_at(const T *ax, const T *ay, const T *b, T *z, int i, int j,
@@ -141,7 +147,7 @@ __device__ __forceinline__ void smooth_at(const T *ax, const T *ay, const T *b, 
     T acc = b[v] + cw * z[v - 1] + ce * z[v + 1];
     if (j > 0) acc += cs * z[v - w];
     if (j < n) acc += cn * z[v + w];
-    z[v] = acc / (cw + ce + cs + cn);
+    z[v] = smooth_div(acc, cw + ce + cs + cn);
 }
 
 // Full-weighting restriction (transpose of bilinear prolongation) of the
