@@ -507,7 +507,7 @@ template <> __device__ __forceinline__ double exp_r<double>(double x) { return e
 //              (kc_plain != nullptr) kc_plain at even (x, y).
 // coarse == 1: lines xc = 0..m/2 of Y (coarse-masked), outputs y = 2 yc -> kout.
 template <typename R, int MAXB>
-__global__ void __launch_bounds__(256) ce_col_kernel(
+__global__ void __launch_bounds__(256, 4) ce_col_kernel(
     const typename C2<R>::T *__restrict__ Y, int ncols, int P, int logP, int m, int F, int tpf,
     const typename C2<R>::T *__restrict__ tw, int coarse, R *__restrict__ kout,
     R *__restrict__ kc_plain) {
@@ -520,12 +520,25 @@ __global__ void __launch_bounds__(256) ce_col_kernel(
     const int col = x0 + f;
     const int LP = fft_line_pitch(P);
     R2 *buf = sm + (size_t)f * LP;
-    if (col < ncols) {
-        const R2 *src = Y + ((size_t)sl * ncols + col) * P;
-        for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+        if (tpf * 16 == P) {   // radix 16: the first pass's inputs straight into registers
+            R2 v[16];
+            const R2 *src = Y + ((size_t)sl * ncols + min(col, ncols - 1)) * P;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = src[t + r * tpf];
+            smem_fft16_regs<R>(buf, v, logP, tw, t, tpf);
+            done = true;
+        }
     }
-    __syncthreads();
-    line_fft<R, MAXB>(buf, logP, tw, t, tpf);
+    if (!done) {
+        if (col < ncols) {
+            const R2 *src = Y + ((size_t)sl * ncols + col) * P;
+            for (int q = t; q < P; q += tpf) buf[fft_pad(q)] = src[q];
+        }
+        __syncthreads();
+        line_fft<R, MAXB>(buf, logP, tw, t, tpf);
+    }
     const R invP = R(1) / R(P);
     const int mc = m / 2;
     const int nthr = blockDim.x;
