@@ -31,39 +31,22 @@ template <int N> struct SmallLayout {
                                     sizeof(float) * (MGPackedLayout<N>::total() + 4 * (size_t)V);
 };
 
-// Sum over the block, returned to every thread (fixed order).
-template <int NT>
-__device__ __forceinline__ double bsum(double v, double *sh) {
+// Sum over the block, returned to every thread (fixed order: warp trees,
+// then the warp partials in index order by every thread).  One barrier: the
+// partials alternate between two buffers (`par` flips per call), so a thread
+// that runs ahead writes the other buffer while the slower ones still read
+// this one, and the next call's barrier orders the reuse.
+template <int NT, typename R>
+__device__ __forceinline__ R bsum1(R v, R *sh, int &par) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    R *buf = sh + (par ? 16 : 0);
+    par ^= 1;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) sh[w] = v;
+    if (lane == 0) buf[w] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < NT / 32; ++i) t += sh[i];
-        sh[32] = t;
-    }
-    __syncthreads();
-    const double t = sh[32];
-    __syncthreads();
-    return t;
-}
-
-// FP32 version (the inner Krylov scalars), fixed order, returned to all threads.
-template <int NT>
-__device__ __forceinline__ float bsumf(float v, float *sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int i = 0; i < NT / 32; ++i) t += sh[i];
-        sh[31] = t;
-    }
-    __syncthreads();
-    const float t = sh[31];
-    __syncthreads();
+    R t = R(0);
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) t += buf[i];
     return t;
 }
 
@@ -90,6 +73,7 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
     const int s = blockIdx.x;
     const int tid = threadIdx.x;
     const float *ks = kin + (size_t)s * V;
+    int pard = 0, parf = 0;   // buffer parity of the FP64 and FP32 block sums
 
     // operator: float-float conductances, hi = the FP32 operator of the inner solve
     for (int v = tid; v < V; v += NT) {
@@ -122,7 +106,7 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             }
             r[v] = rv;
         }
-        return bsum<NT>((double)acc, sh);
+        return bsum1<NT>((double)acc, sh, pard);
     };
 
     // one symmetric V(1,1) cycle: z[0] = M^-1 r
@@ -144,10 +128,10 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             }
             r[v] = rv;
         }
-        orr = bsum<NT>((double)acc, sh);
+        orr = bsum1<NT>((double)acc, sh, pard);
     }
     const double orr0 = orr;
-    float *shf = reinterpret_cast<float *>(sh + 48);
+    float *shf = reinterpret_cast<float *>(sh + 40);
     int its = 0;
     for (int outer = 0; outer < 64 && orr > rtol2 * orr0 && its < maxit; ++outer) {
         // inner CG on A d = r, entirely in FP32 (dot products included)
@@ -156,7 +140,7 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             d[v] = 0.f;
             rr0 += r[v] * r[v];
         }
-        rr0 = bsumf<NT>(rr0, shf);
+        rr0 = bsum1<NT>(rr0, shf, parf);
         const float thr = (float)fmax(in_rel2 * (double)rr0, 0.0625 * rtol2 * orr0);
         vcycle();
         float rz = 0.f;
@@ -164,33 +148,38 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             p[v] = z[v];
             rz += r[v] * z[v];
         }
-        rz = bsumf<NT>(rz, shf);
+        rz = bsum1<NT>(rz, shf, parf);
         for (int it = 0; it < 40 && its < maxit; ++it) {
+            // q = A p, kept in the multigrid z array (free until the next cycle)
             float pq = 0.f;
             for (int v = tid; v < V; v += NT) {
                 const int j = v / W, i = v - j * W;
-                if (i > 0 && i < N) pq += p[v] * apply_at(cx0, cy0, p, i, j, N);
+                if (i > 0 && i < N) {
+                    const float ap = apply_at(cx0, cy0, p, i, j, N);
+                    z[v] = ap;
+                    pq += p[v] * ap;
+                }
             }
-            pq = bsumf<NT>(pq, shf);
+            pq = bsum1<NT>(pq, shf, parf);
             const float alpha = pq > 0.f ? rz / pq : 0.f;
             float rr = 0.f;
             for (int v = tid; v < V; v += NT) {
                 const int j = v / W, i = v - j * W;
                 if (i > 0 && i < N) {
-                    const float ap = apply_at(cx0, cy0, p, i, j, N);
+                    const float ap = z[v];
                     d[v] += alpha * p[v];
                     const float rv = r[v] - alpha * ap;
                     r[v] = rv;
                     rr += rv * rv;
                 }
             }
-            rr = bsumf<NT>(rr, shf);
+            rr = bsum1<NT>(rr, shf, parf);
             ++its;
             if (rr <= thr) break;
             vcycle();
             float rzn = 0.f;
             for (int v = tid; v < V; v += NT) rzn += r[v] * z[v];
-            rzn = bsumf<NT>(rzn, shf);
+            rzn = bsum1<NT>(rzn, shf, parf);
             const float beta = rz > 0.f ? rzn / rz : 0.f;
             rz = rzn;
             for (int v = tid; v < V; v += NT) p[v] = z[v] + beta * p[v];
@@ -220,8 +209,8 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             }
             if (u_out) u_out[(size_t)s * V + v] = ud(v);
         }
-        qo = bsum<NT>(qo, sh);
-        l2 = bsum<NT>(l2, sh);
+        qo = bsum1<NT>(qo, sh, pard);
+        l2 = bsum1<NT>(l2, sh, pard);
     }
     if (tid == 0) {
         const double h = 1.0 / (double)N;
