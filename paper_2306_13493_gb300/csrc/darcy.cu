@@ -266,10 +266,11 @@ __global__ void pspmv_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
                              const int *__restrict__ act) {
     __shared__ T sh[32];
     const int s = blockIdx.y;
+    // the per-sample scalars are loaded together with the flag (one latency)
+    const T bt = (T)beta[s], al = (T)alpha[s];
     if (!act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
     const int w = n + 1;
-    const T bt = (T)beta[s], al = (T)alpha[s];
     const T *ax = cx + s * V, *ay = cy + s * V, *zs = z + s * V, *pi = p_in + s * V;
     T *po = p_out + s * V, *qs = q + s * V, *ds = d + s * V;
     auto pk = [&](long long u) { return zs[u] + bt * pi[u]; };
@@ -300,9 +301,9 @@ __global__ void rupdate_kernel(T *__restrict__ r, const T *__restrict__ q,
                                double *__restrict__ part, int nblk, const int *__restrict__ act) {
     __shared__ T sh[32];
     const int s = blockIdx.y;
+    const T a = (T)alpha[s];   // loaded together with the flag (one latency)
     if (!act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
-    const T a = (T)alpha[s];
     T acc = T(0);
     FOR_VERT_C(V, VPT, vpt) {
         const long long g = s * V + v;
