@@ -50,7 +50,7 @@ constexpr int MG_NW = MG_SH / 4;           // warps per block
 constexpr int MG_CW = (MG_SW - 6) / 2;     // 29 coarse vertices per tile in x
 constexpr int MG_CH = (MG_SH - 6) / 2;     // 13 coarse vertices per tile in y
 constexpr int MG_THREADS = 32 * MG_NW;
-constexpr int MG_BLOCKS_PER_SM = 1024 / MG_THREADS;   // 64 registers per thread
+constexpr int MG_BLOCKS_PER_SM = 5 * 256 / MG_THREADS;   // 48 registers per thread (a few bytes spill)
 static_assert(MG_SH % 4 == 0 && MG_NW <= 32, "tile height");
 constexpr int MG_CCW = MG_CW + 3;          // coarse window of mg_up: 32 x 16 (+1 row)
 constexpr int MG_CCH = MG_CH + 3;
