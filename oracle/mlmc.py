@@ -9,9 +9,12 @@
   N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)).
 * Richardson bias estimate of §4: |E[Q_h - Q]| = |E[Q_h - Q_2h] / (1 - 2^alpha)|,
   and the smoothed variant with the ratio C~_alpha / C_alpha.
-* tau rules of §3.5 (eq. for the exponential covariance and the equation for
-  the Matern covariance solved numerically): parity unpinned -- the constants
-  C_s and C_alpha are not given by the paper and are user inputs here.
+* tau rules of §3.5 (the closed form for the separable exponential
+  covariance, the equation for the Matern covariance solved numerically); the
+  ratio C_s / C_alpha is not given by the paper and is an input here. Pinned
+  for every value of it: each rule balances the two terms of its corollary's
+  bound, and at nu = 1, J = 0 the Matern rule equals the exponential one with
+  the ratio halved.
 """
 import math
 
@@ -70,7 +73,7 @@ def tau_sqrt_s(s):
 def tau_exponential(s, alpha, cs_over_calpha=1.0):
     """§3.5, separable exponential covariance: tau = (s+1)/(C_s/(2^a C_a) s^(a/2) + 1).
 
-    Parity unpinned: C_s / C_alpha is a user input.
+    C_s / C_alpha is an input (the paper does not give it).
     """
     return (s + 1.0) / (cs_over_calpha / 2.0 ** alpha * s ** (alpha / 2.0) + 1.0)
 
@@ -79,7 +82,7 @@ def tau_matern(h, J, nu, alpha, cs_over_calpha=1.0):
     """§3.5, Matern covariance: solve
     (4(1/h + J)^2 - tau + 1)^(-(1+nu)/2) tau = 2 (C_a/C_s) h^(a+1) (1/h + J)
     for tau in [1, s] by bisection (the left side increases with tau).
-    Parity unpinned: C_s / C_alpha is a user input.
+    C_s / C_alpha is an input (the paper does not give it).
     """
     s = 4.0 * (1.0 / h + J) ** 2
     rhs = 2.0 / cs_over_calpha * h ** (alpha + 1.0) * (1.0 / h + J)

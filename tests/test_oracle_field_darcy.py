@@ -149,8 +149,8 @@ def test_level_estimate_end_to_end_small():
 
 
 def test_tau_rules_solve_their_equations():
-    """Parity unpinned (constants not in the paper); this only checks that the
-    numerical solve satisfies the stated equation."""
+    """The numerical solve satisfies the stated equation (the pins against the
+    error bounds the rules come from are in test_oracle_tau.py)."""
     assert mlmc.tau_sqrt_s(64 * 64) == 64
     t = mlmc.tau_matern(1 / 32, 32, 1.5, 1.0, 1.0)
     s = 4.0 * (32 + 32) ** 2
