@@ -487,6 +487,32 @@ int mlmc3_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
  * l = 0..L.  V, C, N: host arrays of length L+1 (C > 0, V >= 0). */
 int mlmc_optimal_samples(int L_plus_1, const double *V, const double *C, double eps, long long *N);
 
+/*
+ * The rules of §3.5 for the number of eigenvalues tau_l to drop on level l:
+ * the tau at which the smoothing term of the level's error bound equals the
+ * discretisation term C_alpha h_l^alpha.  The paper leaves the ratio
+ * C_s / C_alpha to the user (cs_over_calpha > 0); alpha > 0 is the
+ * discretisation rate.  Host-only (no device work); the result is real, the
+ * caller rounds it to a count and passes s - tau as a keep count to
+ * ce_setup_embedding (s is known once the padding loop has fixed P).
+ *
+ * mlmc_tau_exponential: separable exponential covariance (Eq. (2.3), p = 1)
+ * without padding, s = 4 h^-2 (s >= 1): the closed form
+ * tau = (s + 1) / ((C_s / (2^alpha C_alpha)) s^(alpha/2) + 1), not restricted
+ * to [1, s].
+ *
+ * mlmc_tau_matern: Matern covariance (Eq. (2.2), nu > 0) under smooth
+ * periodisation, s = 4 (1/h + J)^2 (h > 0, J >= 0): the root in [1, s] of
+ * (s - tau + 1)^(-(1+nu)/2) tau = 2 (C_alpha / C_s) h^(alpha+1) (1/h + J),
+ * clamped to 1 or s when the root lies outside.
+ *
+ * Both return CE_OK, or CE_ERR_INVALID_ARG for an argument outside the ranges
+ * above or a NULL tau.
+ */
+int mlmc_tau_exponential(double s, double alpha, double cs_over_calpha, double *tau);
+int mlmc_tau_matern(double h, double J, double nu, double alpha, double cs_over_calpha,
+                    double *tau);
+
 /* Releases a handle and its device tables (synchronises the device). */
 void ce_destroy(ce_embedding_t e);
 

@@ -192,3 +192,51 @@ extern "C" int mlmc_optimal_samples(int L_plus_1, const double *V, const double 
         N[l] = (long long)std::ceil(2.0 / (eps * eps) * total * std::sqrt(V[l] / C[l]));
     return CE_OK;
 }
+
+// §3.5, separable exponential covariance without padding (s = 4 h^-2): the
+// smoothing term C_s tau / (s - tau + 1) of the error bound equals the
+// discretisation term C_alpha h^alpha.  With h = 2 s^-1/2 that is
+// tau / (s - tau + 1) = r, r = 2^alpha s^(-alpha/2) / (C_s / C_alpha), solved
+// for tau directly.
+extern "C" int mlmc_tau_exponential(double s, double alpha, double cs_over_calpha, double *tau) {
+    if (!tau || !(s >= 1.0) || !(alpha > 0.0) || !(cs_over_calpha > 0.0) || !std::isfinite(s))
+        return CE_ERR_INVALID_ARG;
+    const double r = std::exp(alpha * (std::log(2.0) - 0.5 * std::log(s))) / cs_over_calpha;
+    *tau = r * (s + 1.0) / (1.0 + r);
+    return CE_OK;
+}
+
+// §3.5, Matern covariance under smooth periodisation (s = 4 (1/h + J)^2): the
+// tau in [1, s] at which C_s s^-1/2 h^-1 (s - tau + 1)^-(1+nu)/2 tau equals
+// C_alpha h^alpha.  In logarithms the condition is g(t) = 0 with
+//   g(t) = ln t - (1+nu)/2 ln(s - t + 1) - ln(2 h^(alpha+1) (1/h + J) C_alpha / C_s),
+// strictly increasing on [1, s]; Newton's method on g, a step that leaves the
+// current bracket replaced by the bracket's midpoint.  A root below 1 or above
+// s gives 1 or s.
+extern "C" int mlmc_tau_matern(double h, double J, double nu, double alpha, double cs_over_calpha,
+                               double *tau) {
+    if (!tau || !(h > 0.0) || !(J >= 0.0) || !(nu > 0.0) || !(alpha > 0.0) ||
+        !(cs_over_calpha > 0.0) || !std::isfinite(h) || !std::isfinite(J))
+        return CE_ERR_INVALID_ARG;
+    const double q = 1.0 / h + J, s = 4.0 * q * q, e = 0.5 * (1.0 + nu);
+    const double lr = std::log(2.0 / cs_over_calpha) + (alpha + 1.0) * std::log(h) + std::log(q);
+    auto g = [&](double t) { return std::log(t) - e * std::log(s - t + 1.0) - lr; };
+    double lo = 1.0, hi = s;
+    if (g(lo) >= 0.0) { *tau = lo; return CE_OK; }
+    if (g(hi) <= 0.0) { *tau = hi; return CE_OK; }
+    // first guess for tau << s: ln t = lr + e ln s
+    double t = std::exp(lr + e * std::log(s));
+    if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        const double gt = g(t);
+        if (gt == 0.0) break;
+        if (gt > 0.0) hi = t; else lo = t;
+        double tn = t - gt / (1.0 / t + e / (s - t + 1.0));
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        const bool done = std::fabs(tn - t) <= 1e-15 * t || hi - lo <= 1e-15 * hi;
+        t = tn;
+        if (done) break;
+    }
+    *tau = t;
+    return CE_OK;
+}

@@ -10,7 +10,12 @@ formulas of the paper's §3.3-3.5 and §4:
 * optimal sample sizes, Eq. (3.6) (``mlmc_optimal_samples`` of the C ABI);
 * Richardson bias estimate of §4: |E[Q_h - Q]| ~ |E[Y_L]| / (2^alpha - 1);
 * rates alpha, beta, gamma by least squares on log2 |E Y_l|, log2 V[Y_l],
-  log2 C_l against l (§4).
+  log2 C_l against l (§4);
+* the smoothing rules of §3.5 (``mlmc_tau_exponential`` and
+  ``mlmc_tau_matern`` of the C ABI) give a real tau_l; ``keep_for_tau`` turns
+  it into the keep count ce_setup_embedding takes (s = P^2 is known once the
+  embedding has been set up, so a rule that depends on s is applied by a
+  second set-up with that count).
 
 The cost of a sample on level l is the GPU time of its level estimate
 divided by its sample count (CUDA events on the launching stream).
@@ -163,6 +168,14 @@ def _run_levels(runners, counts):
             r.run(c)
     for r, t in pending:
         r.collect(t)
+
+
+def keep_for_tau(s, tau):
+    """Eigenvalues to keep when tau (real) are to be dropped: s - round(tau),
+    at least one kept (the tie rule of the set-up may drop a few more)."""
+    s = int(s)
+    drop = int(round(float(tau)))
+    return max(1, min(s, s - max(drop, 0)))
 
 
 def fit_rate(levels, values):

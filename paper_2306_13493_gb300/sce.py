@@ -151,6 +151,11 @@ _SIGS = {
                                             ctypes.c_int, ctypes.POINTER(mlmc_level_task),
                                             ctypes.c_int, ctypes.c_int, _P]),
     "mlmc_optimal_samples": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_double, _P]),
+    "mlmc_tau_exponential": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "mlmc_tau_matern": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_double)]),
     "ce3_setup_embedding": (ctypes.c_int, [ctypes.POINTER(ce_cov), ctypes.c_int,
                                            ctypes.POINTER(ce_pad), ctypes.POINTER(ce_smoothing),
                                            _P, ctypes.POINTER(_P),
@@ -592,3 +597,17 @@ def mlmc_optimal_samples(V, C, eps):
                                        ctypes.c_void_p(C.ctypes.data), eps,
                                        ctypes.c_void_p(N.ctypes.data)), "mlmc_optimal_samples")
     return N
+
+
+def mlmc_tau_exponential(s, alpha, cs_over_calpha=1.0):
+    t = ctypes.c_double()
+    _check(load().mlmc_tau_exponential(float(s), float(alpha), float(cs_over_calpha),
+                                       ctypes.byref(t)), "mlmc_tau_exponential")
+    return t.value
+
+
+def mlmc_tau_matern(h, J, nu, alpha, cs_over_calpha=1.0):
+    t = ctypes.c_double()
+    _check(load().mlmc_tau_matern(float(h), float(J), float(nu), float(alpha),
+                                  float(cs_over_calpha), ctypes.byref(t)), "mlmc_tau_matern")
+    return t.value

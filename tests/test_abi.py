@@ -56,6 +56,39 @@ def test_optimal_samples_matches_oracle(lib):
         sce.mlmc_optimal_samples([1.0], [0.0], 1e-2)
 
 
+def test_tau_rules_match_oracle(lib):
+    """§3.5: the library's closed form and Newton solve against the oracle's
+    closed form and bisection, for any C_s / C_alpha (the oracle's rules are
+    pinned against the error bounds in test_oracle_tau.py)."""
+    from paper_2306_13493_gb300 import sce
+    for alpha in (0.5, 1.0, 1.5, 2.0):
+        for ratio in (0.05, 1.0, 20.0):
+            for h in (1 / 4, 1 / 16, 1 / 64, 1 / 512):
+                s = 4.0 / (h * h)
+                got = sce.mlmc_tau_exponential(s, alpha, ratio)
+                assert got == pytest.approx(omlmc.tau_exponential(s, alpha, ratio), rel=1e-12)
+                for J in (0, 3, 16, 64):
+                    for nu in (0.5, 1.5, 2.5):
+                        got = sce.mlmc_tau_matern(h, J, nu, alpha, ratio)
+                        want = omlmc.tau_matern(h, J, nu, alpha, ratio)
+                        assert got == pytest.approx(want, rel=1e-10), (alpha, ratio, h, J, nu)
+    for bad in ((0.5, 1.0, 1.0), (16.0, 0.0, 1.0), (16.0, 1.0, -1.0), (float("inf"), 1.0, 1.0)):
+        with pytest.raises(sce.SceError):
+            sce.mlmc_tau_exponential(*bad)
+    for bad in ((0.0, 0, 1.5, 1.0, 1.0), (0.1, -1, 1.5, 1.0, 1.0), (0.1, 0, 0.0, 1.0, 1.0),
+                (0.1, 0, 1.5, 0.0, 1.0), (0.1, 0, 1.5, 1.0, 0.0)):
+        with pytest.raises(sce.SceError):
+            sce.mlmc_tau_matern(*bad)
+
+
+def test_keep_counts_from_tau():
+    from paper_2306_13493_gb300 import mlmc
+    assert mlmc.keep_for_tau(4096, 64.0) == 4032
+    assert mlmc.keep_for_tau(4096, 63.5) == 4032      # rounds half to even: 64 dropped
+    assert mlmc.keep_for_tau(4096, 0.4) == 4096
+    assert mlmc.keep_for_tau(4096, 5000.0) == 1       # at least one eigenvalue kept
+
+
 def test_struct_layouts_match_header():
     from paper_2306_13493_gb300 import sce
     assert ctypes.sizeof(sce.ce_cov) == 32
