@@ -8,7 +8,12 @@ formulas of the paper's §3.3-3.5 and §4:
 * estimator, Eq. (3.5): Q_hat = sum_l mean(Y_l) (the MLMC-CES estimator of
   §3.5 when the levels were set up with the smoothing masks);
 * optimal sample sizes, Eq. (3.6) (``mlmc_optimal_samples`` of the C ABI);
-* Richardson bias estimate of §4: |E[Q_h - Q]| ~ |E[Y_L]| / (2^alpha - 1);
+* Richardson bias estimate of §4: |E[Q_h - Q]| ~ |E[Y_L] / (1 - 2^alpha)|,
+  and with smoothing (extrapolant the smoothed coarse QoI)
+  |E[Y_L] / (1 - (C~_alpha / C_alpha) 2^alpha)|;
+* levels added until that bias is within the bias share eps / sqrt(2) of the
+  mean-square error (``run_adaptive``; the weak-error test of the adaptive MLMC
+  algorithm of Giles, which §3.4 builds on);
 * rates alpha, beta, gamma by least squares on log2 |E Y_l|, log2 V[Y_l],
   log2 C_l against l (§4);
 * the smoothing rules of §3.5 (``mlmc_tau_exponential`` and
@@ -200,14 +205,21 @@ def rates(stats: List[LevelStats]):
     return alpha, beta, gamma
 
 
-def richardson_bias(stats: List[LevelStats], alpha):
-    """§4: |E[Q_h - Q]| ~ |E[Y_L]| / (2^alpha - 1) on the finest level L."""
+def richardson_bias(stats: List[LevelStats], alpha, ratio=1.0):
+    """§4: |E[Q_h - Q]| from the finest level's mean E[Y_L] = E[Q_h - Q_2h] by
+    Richardson extrapolation, |E[Y_L] / (1 - 2^alpha)|.  With smoothing the
+    extrapolant is the smoothed coarse QoI and the denominator becomes
+    1 - ratio 2^alpha, ratio = C~_alpha / C_alpha (the constants of the
+    smoothed and plain bias, |E[Q~_h - Q]| = C~_alpha h^alpha); infinite when
+    that denominator vanishes."""
     if not math.isfinite(alpha) or alpha <= 0:
         alpha = 1.0
-    return abs(stats[-1].mean) / (2.0 ** alpha - 1.0)
+    d = 1.0 - ratio * 2.0 ** alpha
+    return abs(stats[-1].mean / d) if d != 0.0 else math.inf
 
 
-def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rounds=10):
+def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rounds=10,
+                ratio=1.0):
     """MLMC with the fixed level set of `runners` to a root-mean-square error eps
     (variance share eps^2/2, Eq. (3.6)): pilot samples, then the optimal N_l
     from the measured V_l and C_l, topped up until no level needs more than 1 %
@@ -228,7 +240,40 @@ def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rou
     est = sum(s.mean for s in stats)
     stat_err = math.sqrt(sum(s.var / s.N for s in stats))
     a = alpha if alpha is not None else rates(stats)[0]
-    bias = richardson_bias(stats, a)
+    bias = richardson_bias(stats, a, ratio)
     return MLMCResult(estimate=est, rmse=math.sqrt(stat_err ** 2 + bias ** 2), stat_error=stat_err,
                       bias=bias, seconds=sum(s.seconds for s in stats), levels=stats,
                       N_opt=[int(n) for n in N_opt])
+
+
+def run_adaptive(make_runner: Callable[[int, bool], LevelRunner], eps, L0=2, L_max=8,
+                 pilot=100, alpha=None, ratio=1.0, max_rounds=10, restart_previous_finest=True):
+    """MLMC to a root-mean-square error eps with the number of levels chosen as
+    it runs: start on levels 0..L0, run ``run_to_rmse`` (variance share
+    eps^2/2), and while the Richardson bias of the finest level exceeds the
+    bias share eps/sqrt(2) and fewer than L_max + 1 levels are in use, add the
+    next level (pilot samples, then the sample sizes of Eq. (3.6) again).
+
+    make_runner(level, finest) builds the runner of a level.  Under MLMC-CES
+    the finest level's fine field is not smoothed (§3.5), so a level that stops
+    being the finest is rebuilt with make_runner(level, False) and sampled
+    afresh (restart_previous_finest; the time of its discarded samples is kept
+    in the cost).  Plain MLMC, whose levels do not depend on which is finest,
+    passes restart_previous_finest=False.  Returns the MLMCResult of the final
+    level set; its `seconds` include every discarded sample."""
+    if L0 < 0 or L_max < L0:
+        raise ValueError("need 0 <= L0 <= L_max")
+    runners = [make_runner(l, l == L0) for l in range(L0 + 1)]
+    discarded = 0.0
+    while True:
+        res = run_to_rmse(runners, eps, pilot=[pilot] * len(runners), alpha=alpha,
+                          max_rounds=max_rounds, ratio=ratio)
+        L = len(runners) - 1
+        if res.bias <= eps / math.sqrt(2.0) or L >= L_max:
+            break
+        if restart_previous_finest:
+            discarded += runners[L].stats.seconds
+            runners[L] = make_runner(L, False)
+        runners.append(make_runner(L + 1, True))
+    res.seconds += discarded
+    return res

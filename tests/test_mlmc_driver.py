@@ -98,3 +98,53 @@ def test_levels_in_flight_give_the_same_run(drv):
         if cls is FakeSubmitRunner:
             assert all(r.in_flight == 0 for r in runners)
     assert out[0] == out[1]
+
+
+def test_richardson_bias_with_smoothing(drv):
+    """§4: with |E[Q_h - Q]| = C h^a and |E[Q~_2h - Q]| = C~ (2h)^a (same sign),
+    E[Q_h - Q~_2h] = h^a (C - C~ 2^a), and the smoothed Richardson estimate
+    with ratio C~/C recovers C h^a exactly; ratio 1 is the plain estimate.
+    The oracle's form agrees."""
+    for a in (0.7, 1.0, 1.9):
+        for C, Ct in ((0.3, 0.3), (0.3, 0.25), (0.2, 0.05), (0.1, 0.4)):
+            h = 2.0 ** -5
+            s = drv.LevelStats(level=5, n=512, N=4)
+            s.sumY = s.N * h ** a * (C - Ct * 2.0 ** a)
+            got = drv.richardson_bias([s], a, Ct / C)
+            assert got == pytest.approx(C * h ** a, rel=1e-12)
+            assert got == pytest.approx(omlmc.richardson_bias(s.mean, a, Ct / C), rel=1e-15)
+    s = drv.LevelStats(level=1, n=32, N=1, sumY=1.0)
+    assert drv.richardson_bias([s], 1.0, 0.5) == math.inf
+
+
+def test_run_adaptive_adds_levels_until_the_bias_test_passes(drv):
+    """Level l has E[Y_l] = 0.08 2^-l, so the Richardson bias of a finest level
+    L is 0.08 2^-L; with eps = 0.006 the test (bias <= eps/sqrt(2)) first
+    passes at L = 5.  Every level that stops being the finest is rebuilt and
+    its discarded samples' time is kept in the cost."""
+    rng = np.random.default_rng(3)
+    made, all_runners = [], []
+
+    def make_runner(level, finest):
+        made.append((level, finest))
+        r = FakeRunner(level, 0.08 * 2.0 ** -level, 1e-6 * 4.0 ** -level, 1e-6 * 4.0 ** level, rng)
+        r.finest = finest
+        all_runners.append(r)
+        return r
+
+    eps = 0.006
+    res = drv.run_adaptive(make_runner, eps, L0=2, L_max=8, pilot=100)
+    assert len(res.levels) == 6 and [s.level for s in res.levels] == list(range(6))
+    assert made == [(0, False), (1, False), (2, True), (2, False), (3, True), (3, False),
+                    (4, True), (4, False), (5, True)]
+    assert res.bias <= eps / math.sqrt(2.0) and res.bias == pytest.approx(0.08 / 32, rel=0.02)
+    assert res.seconds == pytest.approx(sum(r.stats.seconds for r in all_runners), rel=1e-12)
+    # stopping at L_max even when the test fails
+    res2 = drv.run_adaptive(make_runner, eps, L0=1, L_max=3, pilot=100)
+    assert len(res2.levels) == 4 and res2.bias > eps / math.sqrt(2.0)
+    # plain MLMC: no rebuilds
+    made.clear()
+    drv.run_adaptive(make_runner, eps, L0=2, L_max=8, pilot=100, restart_previous_finest=False)
+    assert [l for l, _ in made] == [0, 1, 2, 3, 4, 5]
+    with pytest.raises(ValueError):
+        drv.run_adaptive(make_runner, eps, L0=3, L_max=2)
