@@ -1104,7 +1104,12 @@ def run_ours(args):
                 "alpha_finest3": a3, "bias_est": bias,
                 "rmse_est": (res.stat_error ** 2 + bias ** 2) ** 0.5,
                 "fp64_per_sample_path_seconds": round(fp64_s, 3) if fp64_s else None,
-                "speedup_vs_fp64_path": round(fp64_s / res.seconds, 1) if fp64_s else None}
+                "speedup_vs_fp64_path": round(fp64_s / res.seconds, 1) if fp64_s else None,
+                # predicted GPU seconds versus eps from these level statistics (§4.2-4.3)
+                "cost_vs_eps": [{"eps": c["eps"], "mlmc_s": round(c["mlmc_seconds"], 5),
+                                 "mc_s": round(c["mc_seconds"], 5)}
+                                for c in gm.cost_versus_eps(res.levels,
+                                                            [1e-2, 5e-3, 2e-3, 1e-3, 5e-4])]}
             if variant == "plain":
                 for e in lembs:
                     e.close()

@@ -11,6 +11,8 @@ formulas of the paper's §3.3-3.5 and §4:
 * Richardson bias estimate of §4: |E[Q_h - Q]| ~ |E[Y_L] / (1 - 2^alpha)|,
   and with smoothing (extrapolant the smoothed coarse QoI)
   |E[Y_L] / (1 - (C~_alpha / C_alpha) 2^alpha)|;
+* predicted cost versus eps of MLMC / MLMC-CES and of plain MC on the finest
+  grid from measured level statistics (``cost_versus_eps``, §4.2-4.3);
 * levels added until that bias is within the bias share eps / sqrt(2) of the
   mean-square error (``run_adaptive``; the weak-error test of the adaptive MLMC
   algorithm of Giles, which §3.4 builds on);
@@ -216,6 +218,33 @@ def richardson_bias(stats: List[LevelStats], alpha, ratio=1.0):
         alpha = 1.0
     d = 1.0 - ratio * 2.0 ** alpha
     return abs(stats[-1].mean / d) if d != 0.0 else math.inf
+
+
+def cost_versus_eps(stats: List[LevelStats], eps_list, mc_cost_per_sample=None):
+    """Predicted cost to a root-mean-square error eps from measured level
+    statistics, for the cost-versus-accuracy comparisons of §4.2-4.3 (the
+    variance share eps^2/2 in both; the bias is that of the finest grid):
+
+    * multilevel (MLMC, or MLMC-CES when the levels were smoothed):
+      sum_l N_l C_l with N_l of Eq. (3.6) from the measured V_l and C_l;
+    * plain MC on the finest grid: N = ceil(2 eps^-2 V[Q_L]) samples, V[Q_L]
+      the variance of the finest level's fine QoI, at mc_cost_per_sample each
+      (default: the finest level's cost per sample, which also solves the
+      coarse grid, so an upper bound).
+
+    Returns one dict per eps: eps, N (per level), mlmc_seconds, mc_N,
+    mc_seconds."""
+    V = [max(s.var, 1e-300) for s in stats]
+    C = [max(s.cost, 1e-12) for s in stats]
+    vq = stats[-1].var_q
+    c_mc = C[-1] if mc_cost_per_sample is None else float(mc_cost_per_sample)
+    out = []
+    for eps in eps_list:
+        N = [int(n) for n in sce.mlmc_optimal_samples(V, C, eps)]
+        mc_N = int(math.ceil(2.0 * vq / (eps * eps)))
+        out.append({"eps": eps, "N": N, "mlmc_seconds": sum(n * c for n, c in zip(N, C)),
+                    "mc_N": mc_N, "mc_seconds": mc_N * c_mc})
+    return out
 
 
 def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rounds=10,

@@ -148,3 +148,34 @@ def test_run_adaptive_adds_levels_until_the_bias_test_passes(drv):
     assert [l for l, _ in made] == [0, 1, 2, 3, 4, 5]
     with pytest.raises(ValueError):
         drv.run_adaptive(make_runner, eps, L0=3, L_max=2)
+
+
+def test_cost_versus_eps(drv):
+    """Multilevel cost = sum N_l C_l with N_l of Eq. (3.6) (the oracle's rule);
+    plain MC = ceil(2 eps^-2 V[Q_L]) samples at the finest level's cost; with
+    V_l falling faster than C_l grows, the multilevel cost scales as eps^-2
+    and MC's ratio to it grows as the finest level's variance share does."""
+    V = [1e-3, 2e-4, 5e-5, 1.2e-5]
+    C = [1e-6, 4e-6, 1.6e-5, 6.4e-5]
+    vq = 2.5e-3
+    stats = []
+    for l in range(4):
+        s = drv.LevelStats(level=l, n=16 << l, N=1000)
+        s.sumY, s.sumY2 = 0.0, V[l] * (s.N - 1)
+        s.sumQ, s.sumQ2 = 0.0, vq * (s.N - 1)
+        s.seconds = C[l] * s.N
+        stats.append(s)
+    eps_list = [1e-2, 1e-3]
+    out = drv.cost_versus_eps(stats, eps_list)
+    for e, c in zip(eps_list, out):
+        N = omlmc.optimal_samples(V, C, e)
+        assert c["N"] == list(N)
+        assert c["mlmc_seconds"] == pytest.approx(float(np.dot(N, C)), rel=1e-12)
+        assert c["mc_N"] == math.ceil(2.0 * vq / e ** 2)
+        assert c["mc_seconds"] == pytest.approx(c["mc_N"] * C[-1], rel=1e-12)
+    # eps^-2 scaling once the ceilings of Eq. (3.6) no longer matter
+    far = drv.cost_versus_eps(stats, [1e-3, 1e-4])
+    assert far[1]["mlmc_seconds"] / far[0]["mlmc_seconds"] == pytest.approx(100.0, rel=5e-3)
+    assert out[0]["mc_seconds"] > out[0]["mlmc_seconds"]
+    assert drv.cost_versus_eps(stats, [1e-3], mc_cost_per_sample=1.0)[0]["mc_seconds"] == \
+        math.ceil(2.0 * vq / 1e-6)
