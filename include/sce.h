@@ -290,7 +290,7 @@ typedef struct {
     int n;                  /* cells of the level's fine grid (power of two)    */
     uint32_t level;         /* MLMC level: > 0 adds the coarse solve on n/2     */
     int smoothing;          /* 0: full spectrum; 1: tau = sqrt(s) dropped (§4)  */
-    int finest;             /* with smoothing: the fine field unsmoothed (§3.5) */
+    int finest;             /* with smoothing: the fine field unsmoothed (§3.6) */
     uint64_t seed, first_sample;
     int count;              /* samples, >= 0                                    */
     int qoi_index;          /* 0 outflow, 1 point value, 2 L2 norm              */
@@ -488,7 +488,7 @@ int mlmc3_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
 int mlmc_optimal_samples(int L_plus_1, const double *V, const double *C, double eps, long long *N);
 
 /*
- * The rules of §3.5 for the number of eigenvalues tau_l to drop on level l:
+ * The rules of §3.6 for the number of eigenvalues tau_l to drop on level l:
  * the tau at which the smoothing term of the level's error bound equals the
  * discretisation term C_alpha h_l^alpha.  The paper leaves the ratio
  * C_s / C_alpha to the user (cs_over_calpha > 0); alpha > 0 is the

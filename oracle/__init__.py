@@ -25,7 +25,7 @@ Modules
   mlmc        level differences, level sums, MLMC estimator and N_l rule
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py.
-The tau-selection rules of §3.5 (``mlmc.tau_exponential``, ``mlmc.tau_matern``)
+The tau-selection rules of §3.6 (``mlmc.tau_exponential``, ``mlmc.tau_matern``)
 take the ratio C_s / C_alpha as an input, because the paper does not give it;
 for every value of it they are pinned against the error bounds they balance
 and against each other (tests/test_oracle_tau.py).

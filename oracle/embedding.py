@@ -129,7 +129,7 @@ def setup_embedding(kind, nu, lam, sigma2, m, mode=PAD_DOUBLING, J=None, max_P=8
 def smoothing_mask(Lam, keep, tie_rel_tol=1e-10):
     """Algorithm 2 step 4(b): keep the `keep` largest eigenvalues (keep < 0: all).
 
-    Sorts Lambda non-increasingly (the permutation pi of §3.5), zeroes the
+    Sorts Lambda non-increasingly (the permutation pi of §3.6), zeroes the
     tail, and maps back by pi^-1 -- returned as a boolean mask on the P x P
     grid, with the tie rule in the module docstring.
     """

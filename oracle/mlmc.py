@@ -1,15 +1,15 @@
-"""Monte Carlo / multilevel Monte Carlo combination (§3.3-3.5, §4).
+"""Monte Carlo / multilevel Monte Carlo combination (§3.3-3.6, §4).
 
 * Y_l = Q_{h_l} - Q_{h_(l-1)} for l >= 1 with the same sample k(., w_i) on
   both grids, Y_0 = Q_{h_0} (§3.4); level sums N, sum Y, sum Y^2, sum Q_f,
   sum Q_f^2.
-* MLMC estimator Eq. (3.5): Q_hat = sum_l mean(Y_l); with smoothing (§3.5,
+* MLMC estimator Eq. (3.5): Q_hat = sum_l mean(Y_l); with smoothing (§3.6,
   MLMC-CES) the same sum with the smoothed differences of Algorithm 2.
 * Optimal sample sizes Eq. (3.6):
   N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)).
 * Richardson bias estimate of §4: |E[Q_h - Q]| = |E[Q_h - Q_2h] / (1 - 2^alpha)|,
   and the smoothed variant with the ratio C~_alpha / C_alpha.
-* tau rules of §3.5 (the closed form for the separable exponential
+* tau rules of §3.6 (the closed form for the separable exponential
   covariance, the equation for the Matern covariance solved numerically); the
   ratio C_s / C_alpha is not given by the paper and is an input here. Pinned
   for every value of it: each rule balances the two terms of its corollary's
@@ -71,7 +71,7 @@ def tau_sqrt_s(s):
 
 
 def tau_exponential(s, alpha, cs_over_calpha=1.0):
-    """§3.5, separable exponential covariance: tau = (s+1)/(C_s/(2^a C_a) s^(a/2) + 1).
+    """§3.6, separable exponential covariance: tau = (s+1)/(C_s/(2^a C_a) s^(a/2) + 1).
 
     C_s / C_alpha is an input (the paper does not give it).
     """
@@ -79,7 +79,7 @@ def tau_exponential(s, alpha, cs_over_calpha=1.0):
 
 
 def tau_matern(h, J, nu, alpha, cs_over_calpha=1.0):
-    """§3.5, Matern covariance: solve
+    """§3.6, Matern covariance: solve
     (4(1/h + J)^2 - tau + 1)^(-(1+nu)/2) tau = 2 (C_a/C_s) h^(a+1) (1/h + J)
     for tau in [1, s] by bisection (the left side increases with tau).
     C_s / C_alpha is an input (the paper does not give it).
@@ -133,10 +133,10 @@ def level_estimate(emb, mask_f, mask_c, seed, level, first_sample, count,
 
 def default_masks(emb, smoothing, finest):
     """Masks (fine, coarse) for one level.  Plain CE: both full.  MLMC-CES
-    (§3.5 estimator; §4: the coarse QoI is computed with the smoothed sample
+    (§3.6 estimator; §4: the coarse QoI is computed with the smoothed sample
     used for the fine QoI): the smoothed sample keeps s - tau_l eigenvalues,
     tau_l = sqrt(s_l), and drives both grids; on the finest level the fine
-    field is unsmoothed (§3.5) while the coarse field keeps the smoothed one."""
+    field is unsmoothed (§3.6) while the coarse field keeps the smoothed one."""
     s = emb.s
     if not smoothing:
         full = np.ones(emb.Lam.shape, dtype=bool)

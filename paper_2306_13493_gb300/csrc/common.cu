@@ -193,7 +193,7 @@ extern "C" int mlmc_optimal_samples(int L_plus_1, const double *V, const double 
     return CE_OK;
 }
 
-// §3.5, separable exponential covariance without padding (s = 4 h^-2): the
+// §3.6, separable exponential covariance without padding (s = 4 h^-2): the
 // smoothing term C_s tau / (s - tau + 1) of the error bound equals the
 // discretisation term C_alpha h^alpha.  With h = 2 s^-1/2 that is
 // tau / (s - tau + 1) = r, r = 2^alpha s^(-alpha/2) / (C_s / C_alpha), solved
@@ -206,7 +206,7 @@ extern "C" int mlmc_tau_exponential(double s, double alpha, double cs_over_calph
     return CE_OK;
 }
 
-// §3.5, Matern covariance under smooth periodisation (s = 4 (1/h + J)^2): the
+// §3.6, Matern covariance under smooth periodisation (s = 4 (1/h + J)^2): the
 // tau in [1, s] at which C_s s^-1/2 h^-1 (s - tau + 1)^-(1+nu)/2 tau equals
 // C_alpha h^alpha.  In logarithms the condition is g(t) = 0 with
 //   g(t) = ln t - (1+nu)/2 ln(s - t + 1) - ln(2 h^(alpha+1) (1/h + J) C_alpha / C_s),

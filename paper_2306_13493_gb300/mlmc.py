@@ -3,10 +3,10 @@
 Every sample -- field, fine and coarse Darcy solves, level differences, level
 sums -- is computed by ``mlmc_level_estimate`` on the GPU; this module keeps
 the per-level running sums, the measured cost per sample, and applies the
-formulas of the paper's §3.3-3.5 and §4:
+formulas of the paper's §3.3-3.6 and §4:
 
 * estimator, Eq. (3.5): Q_hat = sum_l mean(Y_l) (the MLMC-CES estimator of
-  §3.5 when the levels were set up with the smoothing masks);
+  §3.6 when the levels were set up with the smoothing masks);
 * optimal sample sizes, Eq. (3.6) (``mlmc_optimal_samples`` of the C ABI);
 * Richardson bias estimate of §4: |E[Q_h - Q]| ~ |E[Y_L] / (1 - 2^alpha)|,
   and with smoothing (extrapolant the smoothed coarse QoI)
@@ -18,7 +18,7 @@ formulas of the paper's §3.3-3.5 and §4:
   algorithm of Giles, which §3.4 builds on);
 * rates alpha, beta, gamma by least squares on log2 |E Y_l|, log2 V[Y_l],
   log2 C_l against l (§4);
-* the smoothing rules of §3.5 (``mlmc_tau_exponential`` and
+* the smoothing rules of §3.6 (``mlmc_tau_exponential`` and
   ``mlmc_tau_matern`` of the C ABI) give a real tau_l; ``keep_for_tau`` turns
   it into the keep count ce_setup_embedding takes (s = P^2 is known once the
   embedding has been set up, so a rule that depends on s is applied by a
@@ -284,7 +284,7 @@ def run_adaptive(make_runner: Callable[[int, bool], LevelRunner], eps, L0=2, L_m
     next level (pilot samples, then the sample sizes of Eq. (3.6) again).
 
     make_runner(level, finest) builds the runner of a level.  Under MLMC-CES
-    the finest level's fine field is not smoothed (§3.5), so a level that stops
+    the finest level's fine field is not smoothed (§3.6), so a level that stops
     being the finest is rebuilt with make_runner(level, False) and sampled
     afresh (restart_previous_finest; the time of its discarded samples is kept
     in the cost).  Plain MLMC, whose levels do not depend on which is finest,

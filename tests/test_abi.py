@@ -57,7 +57,7 @@ def test_optimal_samples_matches_oracle(lib):
 
 
 def test_tau_rules_match_oracle(lib):
-    """§3.5: the library's closed form and Newton solve against the oracle's
+    """§3.6: the library's closed form and Newton solve against the oracle's
     closed form and bisection, for any C_s / C_alpha (the oracle's rules are
     pinned against the error bounds in test_oracle_tau.py)."""
     from paper_2306_13493_gb300 import sce

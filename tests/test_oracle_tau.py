@@ -1,9 +1,9 @@
-"""Pins of the smoothing rules of §3.5 (oracle.mlmc.tau_exponential, tau_matern).
+"""Pins of the smoothing rules of §3.6 (oracle.mlmc.tau_exponential, tau_matern).
 
 The paper leaves the constant ratio C_s / C_alpha to the user, so these tests
 take it as a free input and check what the paper fixes for every value of it:
 
-* the exponential rule (§3.5, no padding, s = 4 h^-2) is the tau at which the
+* the exponential rule (§3.6, no padding, s = 4 h^-2) is the tau at which the
   two terms of the bound of the exponential-covariance corollary are equal,
   C_alpha h^alpha = C_s (s - tau + 1)^-1 tau;
 * the Matern rule comes from the Matern corollary's bound
