@@ -9,6 +9,8 @@
   N_l = ceil(2 eps^-2 (sum_k sqrt(C_k V_k)) sqrt(V_l / C_l)).
 * Richardson bias estimate of §4: |E[Q_h - Q]| = |E[Q_h - Q_2h] / (1 - 2^alpha)|,
   and the smoothed variant with the ratio C~_alpha / C_alpha.
+* the coarsest mesh of plain MLMC, Eq. (3.7)-(3.8) (§3.6), pinned by the
+  examples the paper states in §4.2-4.3 (tests/golden/coarsest_mesh_examples.txt);
 * tau rules of §3.6 (the closed form for the separable exponential
   covariance, the equation for the Matern covariance solved numerically); the
   ratio C_s / C_alpha is not given by the paper and is an input here. Pinned
@@ -63,6 +65,16 @@ def mse(level_sum_list, bias):
     for N, s1, s2, *_ in level_sum_list:
         var += mean_var(N, s1, s2)[1] / N
     return var + bias * bias
+
+
+def coarsest_mesh_exponent(kind, nu, lam):
+    """Eq. (3.7) / (3.8): the coarsest mesh of plain MLMC, h0 = 2^-k with the
+    largest h0 not above lambda (separable exponential covariance) or
+    sqrt(8 nu) lambda (Matern, via the correlation length of Lindgren et al.);
+    returns k >= 0."""
+    from . import covariance as cv
+    bound = lam if kind == cv.SEP_EXP else math.sqrt(8.0 * nu) * lam
+    return max(0, math.ceil(-math.log2(bound)))
 
 
 def tau_sqrt_s(s):

@@ -11,6 +11,8 @@ formulas of the paper's §3.3-3.6 and §4:
 * Richardson bias estimate of §4: |E[Q_h - Q]| ~ |E[Y_L] / (1 - 2^alpha)|,
   and with smoothing (extrapolant the smoothed coarse QoI)
   |E[Y_L] / (1 - (C~_alpha / C_alpha) 2^alpha)|;
+* the coarsest level of plain MLMC from the correlation length,
+  Eq. (3.7)-(3.8) (``coarsest_cells``);
 * predicted cost versus eps of MLMC / MLMC-CES and of plain MC on the finest
   grid from measured level statistics (``cost_versus_eps``, §4.2-4.3);
 * levels added until that bias is within the bias share eps / sqrt(2) of the
@@ -175,6 +177,20 @@ def _run_levels(runners, counts):
             r.run(c)
     for r, t in pending:
         r.collect(t)
+
+
+def coarsest_cells(kind, nu, lam):
+    """Cells per side n0 = 1/h0 of the coarsest level of plain MLMC: the
+    smallest power of two with 1/n0 <= lambda (separable exponential
+    covariance, Eq. (3.7)) or 1/n0 <= sqrt(8 nu) lambda (Matern, Eq. (3.8)).
+    MLMC-CES may start coarser (§3.6)."""
+    bound = lam if kind == sce.CE_COV_SEP_EXP else math.sqrt(8.0 * nu) * lam
+    if not bound > 0:
+        raise ValueError("lambda and nu must be positive")
+    n0 = 1
+    while 1.0 / n0 > bound:
+        n0 *= 2
+    return n0
 
 
 def keep_for_tau(s, tau):

@@ -179,3 +179,16 @@ def test_cost_versus_eps(drv):
     assert out[0]["mc_seconds"] > out[0]["mlmc_seconds"]
     assert drv.cost_versus_eps(stats, [1e-3], mc_cost_per_sample=1.0)[0]["mc_seconds"] == \
         math.ceil(2.0 * vq / 1e-6)
+
+
+def test_coarsest_cells_matches_the_paper_examples(golden_dir):
+    from paper_2306_13493_gb300 import mlmc, sce
+    import os
+    with open(os.path.join(golden_dir, "coarsest_mesh_examples.txt")) as fh:
+        rows = [l.split()[:4] for l in fh if l.strip() and not l.startswith("#")]
+    for kind, nu, lam, k in rows:
+        c = sce.CE_COV_SEP_EXP if kind == "sep_exp" else sce.CE_COV_MATERN
+        assert mlmc.coarsest_cells(c, float(nu), float(lam)) == 2 ** int(k)
+    assert mlmc.coarsest_cells(sce.CE_COV_SEP_EXP, 0.5, 0.25) == 4
+    with pytest.raises(ValueError):
+        mlmc.coarsest_cells(sce.CE_COV_MATERN, 0.0, 0.1)

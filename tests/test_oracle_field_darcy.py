@@ -158,3 +158,27 @@ def test_tau_rules_solve_their_equations():
     assert abs(lhs - 2 * (1 / 32) ** 2 * 64) < 1e-9 * lhs
     te = mlmc.tau_exponential(4096.0, 1.0, 1.0)
     assert 1 <= te <= 4096
+
+
+def _coarsest_examples(golden_dir):
+    import os
+    rows = []
+    with open(os.path.join(golden_dir, "coarsest_mesh_examples.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                kind, nu, lam, k = line.split()[:4]
+                rows.append((kind, float(nu), float(lam), int(k)))
+    return rows
+
+
+def test_coarsest_mesh_matches_the_paper_examples(golden_dir):
+    """Eq. (3.7)-(3.8) against the h0 the paper states for its experiments."""
+    rows = _coarsest_examples(golden_dir)
+    assert len(rows) == 6
+    for kind, nu, lam, k in rows:
+        c = cv.SEP_EXP if kind == "sep_exp" else cv.MATERN
+        assert mlmc.coarsest_mesh_exponent(c, nu, lam) == k, (kind, nu, lam)
+    # the bound itself is admissible (h0 <= bound) and exact powers of two stay
+    assert mlmc.coarsest_mesh_exponent(cv.SEP_EXP, 0.5, 0.25) == 2
+    assert mlmc.coarsest_mesh_exponent(cv.MATERN, 0.5, 0.125) == 2
+    assert mlmc.coarsest_mesh_exponent(cv.SEP_EXP, 0.5, 3.0) == 0
