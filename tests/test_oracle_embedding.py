@@ -210,3 +210,40 @@ def test_sampler_naive_and_fft_branches_agree():
     a = field.hartley_field(e.Lam, xi, 16, naive=True)
     b = field.hartley_field(e.Lam, xi, 16, naive=False)
     assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_smoothing_illustration_of_section_2_4():
+    """The paper's illustration of smoothing (§2.4): separable exponential
+    covariance (Eq. (2.3), p = 1), sigma2 = 1, lambda = 0.1 on a 32 x 32 mesh,
+    tau = 7s/8 eigenvalues dropped.  Exact second moments of the oracle's
+    sampler (its linear map xi -> Z, column by column), no sampling:
+    * unsmoothed, the separable covariance needs no padding (Lemma 2) and the
+      field has covariance C exactly: variance 1 and lag-h covariance
+      exp(-h/lambda) along either axis;
+    * smoothed, the pointwise variance is sum(Lambda~)/s at every vertex
+      (the mask keeps tie groups whole, so the field stays stationary) and
+      the relative increment variance E[(Z(x+h) - Z(x))^2] / E[Z(x)^2] falls
+      below the unsmoothed 2 (1 - exp(-h/lambda)): the sample is smoother."""
+    m, lam = 32, 0.1
+    e = em.setup_embedding(cv.SEP_EXP, 0.5, lam, 1.0, m, em.PAD_NONE)
+    assert e.P == 2 * m
+    keep = e.s - 7 * e.s // 8
+    mk = em.smoothing_mask(e.Lam, keep)
+    assert keep - 16 <= mk.sum() <= keep          # a straddling tie group is dropped whole
+    Lt = em.masked_eigenvalues(e.Lam, mk)
+    rho = math.exp(-(1.0 / m) / lam)
+    # a vertex away from the boundary and its two axis neighbours
+    i, j = 10, 13
+    rows = [i + (m + 1) * j, i + 1 + (m + 1) * j, i + (m + 1) * (j + 1)]
+    for L_, smoothed in ((e.Lam, False), (Lt, True)):
+        M = _field_matrix(L_, m)[rows]
+        C = M @ M.T
+        if not smoothed:
+            assert abs(C[0, 0] - 1.0) < 1e-12
+            assert abs(C[0, 1] - rho) < 1e-12 and abs(C[0, 2] - rho) < 1e-12
+            rough = [2 * (C[0, 0] - C[0, 1]) / C[0, 0], 2 * (C[0, 0] - C[0, 2]) / C[0, 0]]
+        else:
+            assert np.allclose(np.diag(C), Lt.sum() / e.s, rtol=0, atol=1e-12)
+            smooth = [2 * (C[0, 0] - C[0, 1]) / C[0, 0], 2 * (C[0, 0] - C[0, 2]) / C[0, 0]]
+    assert rough[0] == pytest.approx(2 * (1 - rho), rel=1e-10)
+    assert smooth[0] < 0.5 * rough[0] and smooth[1] < 0.5 * rough[1]
