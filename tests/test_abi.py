@@ -178,3 +178,10 @@ def test_three_dimensional_entry_points_reject_bad_arguments_on_the_host():
     assert lib.mlmc3_estimate_levels(ctypes.byref(prob), 1, 3, tasks, 0, 4, None) == \
         sce.CE_ERR_INVALID_ARG                             # qoi_index out of range
     assert lib.mlmc3_estimate_levels(ctypes.byref(prob), 1, 0, tasks, 0, 4, None) == sce.CE_OK
+
+
+def test_missing_library_is_an_error(tmp_path):
+    """No fallback: a library that is not there makes load() raise."""
+    from paper_2306_13493_gb300 import sce
+    with pytest.raises(RuntimeError, match="not built"):
+        sce.load(str(tmp_path / "libsce.so"))
