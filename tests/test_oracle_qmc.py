@@ -89,3 +89,32 @@ def test_lattice_field_has_the_embedding_covariance_on_average():
     z = np.array(vals)
     var = z.var(axis=0, ddof=1).mean()
     assert abs(var - e.Lam.sum() / e.Lam.size) < 0.25 * e.Lam.sum() / e.Lam.size
+
+
+def test_lattice_points_have_the_character_property():
+    """A rank-1 lattice rule with generating vector z averages the character
+    exp(2 pi i h.y) over its N points to 1 when h.z = 0 mod N and to 0
+    otherwise (the dual-lattice property of lattice rules); a random shift
+    Delta only multiplies the average by exp(2 pi i h.Delta).  Checked on the
+    oracle's points in a 4-dimensional projection, so a wrong product, modulus
+    or shift in lattice_uniforms fails."""
+    N, a = 512, 1597
+    z = qmc.korobov(a, N, 64)
+    coords = np.array([0, 5, 17, 63])
+    zr = z[coords]
+    rng_ = np.random.default_rng(4)
+    delta = rng_.random(coords.size)
+    pts0 = np.array([qmc.lattice_uniforms(zr, N, i, np.zeros(coords.size)) for i in range(N)])
+    pts = np.array([qmc.lattice_uniforms(zr, N, i, delta) for i in range(N)])
+    hs = [rng_.integers(-40, 41, coords.size) for _ in range(200)]
+    # a few vectors in the dual lattice: h.z = 0 mod N
+    hs += [np.array([N - zr[1], 1, 0, 0]), np.array([zr[2], 0, -1, 0]), np.array([0, 0, 0, N])]
+    seen_dual = 0
+    for h in hs:
+        dual = int(np.dot(h, zr)) % N == 0
+        seen_dual += dual
+        avg0 = np.mean(np.exp(2j * np.pi * (pts0 @ h)))
+        avg = np.mean(np.exp(2j * np.pi * (pts @ h)))
+        assert abs(avg0 - (1.0 if dual else 0.0)) < 1e-11
+        assert abs(avg - avg0 * np.exp(2j * np.pi * np.dot(h, delta))) < 1e-11
+    assert seen_dual >= 3
