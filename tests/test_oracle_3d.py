@@ -117,6 +117,20 @@ def test_embedding3_identity_against_brute_force(m, J, mode):
     assert abs(L.real.sum() - P ** 3 * s2) < 1e-10 * P ** 3
 
 
+@pytest.mark.parametrize("m,J", [(2, 2), (4, 1), (4, 4)])
+def test_smooth_first_column3_is_c_ext_on_the_grid_period(m, J):
+    """As in two dimensions: C_ext's period 2l must be the grid's period P/m,
+    so the first column at every raw lag (i1, i2, i3)/m is C_ext there (a
+    wrong l keeps S restricted to R equal to R)."""
+    kind, nu, lam, sigma2 = cv.MATERN, 0.5, 0.3, 1.0
+    c = f3.first_column3(kind, nu, lam, sigma2, m, J, em.PAD_SMOOTH)
+    P = c.shape[0]
+    t = np.arange(P) / m
+    want = f3.c_ext3(kind, t[None, None, :], t[None, :, None], t[:, None, None], nu, lam,
+                     sigma2, P / (2.0 * m))
+    assert np.max(np.abs(c - want)) < 1e-14
+
+
 def test_naive_dft3_matches_fft():
     c = f3.first_column3(cv.MATERN, 0.5, 0.2, 1.0, 8, 8, em.PAD_SMOOTH)
     a = f3.dft3_naive(c)

@@ -79,6 +79,23 @@ def test_c_ext_equals_c_on_unit_square_periodic_and_even(kind, nu):
     assert np.max(np.abs(a - cv.c_ext(kind, -Y1, -Y2, nu, 0.1, 1.0, ell))) < 1e-15
 
 
+@pytest.mark.parametrize("m,J", [(4, 4), (6, 2), (8, 3), (16, 16)])
+def test_smooth_first_column_is_c_ext_on_the_grid_period(m, J):
+    """Under smooth periodisation the embedding is the circulant of C_ext
+    sampled on the grid (§2.2): the period of C_ext, 2l, must be the grid's
+    period P/m = 2(m + J)/m, so the first column at every raw lag i/m (not
+    only the folded lag min(i, P - i)/m) is C_ext there.  A wrong l keeps
+    S restricted to R equal to R, so only this catches it."""
+    kind, nu, lam, sigma2 = cv.MATERN, 0.5, 0.3, 1.0
+    c = em.first_column(kind, nu, lam, sigma2, m, J, em.PAD_SMOOTH)
+    P = c.shape[0]
+    ell_grid = P / (2.0 * m)
+    t = np.arange(P) / m
+    T1, T2 = np.meshgrid(t, t)
+    want = cv.c_ext(kind, T1, T2, nu, lam, sigma2, ell_grid)
+    assert np.max(np.abs(c - want)) < 1e-14
+
+
 @pytest.mark.parametrize("m,J,mode", [(4, 0, em.PAD_NONE), (4, 4, em.PAD_DOUBLING),
                                       (4, 4, em.PAD_SMOOTH), (6, 2, em.PAD_SMOOTH)])
 def test_embedding_identity_against_brute_force(m, J, mode):
