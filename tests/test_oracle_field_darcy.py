@@ -182,3 +182,34 @@ def test_coarsest_mesh_matches_the_paper_examples(golden_dir):
     assert mlmc.coarsest_mesh_exponent(cv.SEP_EXP, 0.5, 0.25) == 2
     assert mlmc.coarsest_mesh_exponent(cv.MATERN, 0.5, 0.125) == 2
     assert mlmc.coarsest_mesh_exponent(cv.SEP_EXP, 0.5, 3.0) == 0
+
+
+def test_sample_variance_is_the_unbiased_one():
+    """V_l in Eq. (3.6) is the unbiased sample variance: for 1, 2, 3, 6 the
+    mean is 3 and the variance (4 + 1 + 0 + 9) / 3 = 14/3."""
+    y = [1.0, 2.0, 3.0, 6.0]
+    mean, var = mlmc.mean_var(len(y), sum(y), sum(v * v for v in y))
+    assert mean == 3.0 and abs(var - 14.0 / 3.0) < 1e-15
+    assert mlmc.mean_var(1, 2.0, 4.0) == (2.0, 0.0)
+
+
+def test_default_masks_follow_the_smoothing_reading():
+    """MLMC-CES masks (§3.6, with tau_l = sqrt(s_l) as in the numerics of §4):
+    plain CE keeps everything; on a level below the finest one smoothed mask,
+    dropping the tau smallest eigenvalues (a few more when a tie group
+    straddles the cut), drives both grids; on the finest level the fine field
+    is unsmoothed and the coarse field keeps the smoothed mask."""
+    e = em.setup_embedding(cv.MATERN, 0.5, 0.1, 1.0, 16, em.PAD_SMOOTH)
+    s = e.s
+    tau = math.isqrt(s)
+    assert tau * tau == s                     # s = P^2: tau = P
+    f0, c0 = mlmc.default_masks(e, smoothing=False, finest=False)
+    assert f0.all() and c0.all()
+    f1, c1 = mlmc.default_masks(e, smoothing=True, finest=False)
+    dropped = s - int(c1.sum())
+    assert np.array_equal(f1, c1)
+    assert tau <= dropped <= tau + 8          # symmetric groups of at most 8 on a square grid
+    kept, gone = e.Lam[c1], e.Lam[~c1]
+    assert kept.min() >= gone.max() * (1 - 1e-10)   # the smallest ones are dropped
+    f2, c2 = mlmc.default_masks(e, smoothing=True, finest=True)
+    assert f2.all() and np.array_equal(c2, c1)
