@@ -27,6 +27,11 @@ def test_ranks_order_the_frequencies():
     # next: the four wavenumber-1 frequencies (1,0), (7,0), (0,1), (0,7) in index order
     first = sorted(range(P * P), key=lambda j: rk[j])[1:5]
     assert first == [1, 7, 8, 56]
+    # then the squared wavenumber 2 (the diagonal neighbours (1,1), (7,1), (1,7),
+    # (7,7)) before 4 (the axis frequencies (2,0), (6,0), (0,2), (0,6)); an
+    # order by d(k1) + d(k2) would tie them and put j = 2 first
+    nxt = sorted(range(P * P), key=lambda j: rk[j])[5:13]
+    assert nxt == [9, 15, 57, 63, 2, 6, 16, 48]
     # a decreasing isotropic spectral density: eigenvalues fall along the order
     e = oem.setup_embedding(ocv.MATERN, 1.5, 0.2, 1.0, 8, oem.PAD_DOUBLING)
     lam = e.Lam.reshape(-1)[np.argsort(qmc.ranks(e.P))]
