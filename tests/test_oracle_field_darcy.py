@@ -213,3 +213,29 @@ def test_default_masks_follow_the_smoothing_reading():
     assert kept.min() >= gone.max() * (1 - 1e-10)   # the smallest ones are dropped
     f2, c2 = mlmc.default_masks(e, smoothing=True, finest=True)
     assert f2.all() and np.array_equal(c2, c1)
+
+
+@pytest.mark.parametrize("m,seed", [(8, 0), (16, 1), (32, 2)])
+def test_k_of_x_outflow_between_rayleigh_bounds(m, seed):
+    """k varying along the flow only, f = 0.  With the diagonal split the
+    five-point conductance of the horizontal edge (a, b)-(a+1, b) is, from the
+    legs of the right triangles (each contributes kbar_T / 2),
+      (k_a + k_a+1) / 2 on interior rows, (k_a + 2 k_a+1) / 6 on the bottom row
+      and (2 k_a + k_a+1) / 6 on the top row,
+    so the solution is not y-independent and the series formula is not exact.
+    Rayleigh's monotonicity law bounds the outflow (the conductance between
+    the Dirichlet sides): cutting every vertical edge gives the independent row
+    chains (lower bound); shorting them merges each column into conductance
+    m (k_a + k_a+1) / 2, the series formula 1 / sum_a h / ((k_a + k_a+1) / 2)
+    (upper bound).  Both coincide at k = 1 (outflow 1)."""
+    kx = np.exp(np.random.default_rng(seed).standard_normal(m + 1))
+    k = np.tile(kx[None, :], (m + 1, 1))
+    q = darcy.solve_qois(k, 0.0)[0]
+    ka, kb = kx[:-1], kx[1:]
+    rows = [(ka + kb) / 2.0] * (m - 1) + [(ka + 2.0 * kb) / 6.0, (2.0 * ka + kb) / 6.0]
+    lower = sum(1.0 / np.sum(1.0 / g) for g in rows)
+    upper = 1.0 / np.sum((1.0 / m) / ((ka + kb) / 2.0))
+    assert lower * (1 - 1e-12) <= q <= upper * (1 + 1e-12)
+    assert upper - lower > 1e-6 * upper            # a genuine interval for random k
+    ones = np.ones((m + 1, m + 1))
+    assert abs(darcy.solve_qois(ones, 0.0)[0] - 1.0) < 1e-12
