@@ -315,3 +315,26 @@ def test_point_value3_and_mass_exact_on_linear_functions():
     want = a * a + a * b.sum() + (b ** 2).sum() / 3 + (b[0] * b[1] + b[0] * b[2] + b[1] * b[2]) / 2
     uf = u.ravel()
     assert abs(uf @ (M @ uf) - want) < 1e-13
+
+
+@pytest.mark.parametrize("m,seed", [(4, 0), (6, 1)])
+def test_k_of_x3_outflow_below_the_series_bound(m, seed):
+    """k varying along the flow only, f = 0.  Every Kuhn tetrahedron spans one
+    x-layer [a, a+1] and has one, two or three of its four vertices on the far
+    plane (two permutations each), so its vertex mean of k averages to
+    (k_a + k_a+1)/2 over a cell.  The energy of u = x equals both
+    sum_T kbar_T |T| and h^2 times the summed conductance of the layer's
+    x-edges (only they see a potential difference), so with |T| = h^3/6 and
+    6 m^2 tetrahedra per layer that conductance is
+    m^2 h^3 (k_a + k_a+1)/2 / h^2 = m (k_a + k_a+1)/2.
+    Shorting every y- and z-edge (Rayleigh's monotonicity law) can only raise
+    the outflow, so it is at most the series formula
+    1 / sum_a h / ((k_a + k_a+1)/2), with equality for constant k."""
+    kx = np.exp(np.random.default_rng(seed).standard_normal(m + 1))
+    k = np.broadcast_to(kx[None, None, :], (m + 1, m + 1, m + 1)).copy()
+    q = d3.solve_qois3(k, 0.0)[0]
+    upper = 1.0 / np.sum((1.0 / m) / ((kx[:-1] + kx[1:]) / 2.0))
+    assert q <= upper * (1 + 1e-12)
+    assert q > 0.9 * upper
+    c = 1.7 * np.ones((m + 1, m + 1, m + 1))
+    assert abs(d3.solve_qois3(c, 0.0)[0] - 1.7) < 1e-11
