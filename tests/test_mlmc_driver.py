@@ -192,3 +192,22 @@ def test_coarsest_cells_matches_the_paper_examples(golden_dir):
     assert mlmc.coarsest_cells(sce.CE_COV_SEP_EXP, 0.5, 0.25) == 4
     with pytest.raises(ValueError):
         mlmc.coarsest_cells(sce.CE_COV_MATERN, 0.0, 0.1)
+
+
+def test_workloads_keep_the_stated_configurations():
+    """The synthetic workloads keep the parameters their JSON `config` quotes
+    (the paper-shaped oscillatory MLMC-CES step and the plain 33 x 33 case),
+    and the CES keep counts drop tau = sqrt(s) = P except on the finest level's
+    fine field."""
+    import workloads as w
+    o = w.OSCILLATORY
+    assert (o.nu, o.lam, o.sigma2, o.n0) == (0.5, 0.02, 1.0, 16)
+    assert o.N == [20000, 8000, 3000, 1000, 300, 100]
+    assert [n for _, n, _ in o.levels] == [16, 32, 64, 128, 256, 512]
+    assert o.pad_mode == 2 and o.smoothing and o.rtol == 1e-10
+    p = w.PLAIN_SMALL
+    assert (p.nu, p.lam, p.sigma2, p.n0, p.N, p.pad_mode, p.smoothing, p.qoi, p.f, p.seed) == \
+        (0.5, 0.3, 1.0, 32, [256], 1, False, 0, 0.0, 0)
+    assert w.keep_counts(64, finest=False, smoothing=True) == (64 * 64 - 64, 64 * 64 - 64)
+    assert w.keep_counts(64, finest=True, smoothing=True) == (-1, 64 * 64 - 64)
+    assert w.keep_counts(64, finest=True, smoothing=False) == (-1, -1)
