@@ -157,6 +157,8 @@ int ce_sample_batch(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t fi
  *     any stream capture.
  *   - All calls share the array: calls that overlap on the GPU (other streams,
  *     other threads) race on it and must be serialised by the caller.
+ *   - Uses the FFT launch shapes ce_autotune_fft chose, as ce_sample_batch
+ *     does, so both entry points take the same time per chunk.
  *   - k_fine must not be NULL (k_coarse may be).  Other arguments, layouts and
  *     errors as ce_sample_batch.
  */
@@ -537,6 +539,27 @@ void sce_profile_enable(int on);
 int sce_profile_read(int kernel, double *ms, double *bytes, long long *launches);
 int sce_profile_count(void);
 const char *sce_profile_name(int kernel);
+
+/*
+ * Machine peaks -- instrumentation of this library, not a step of the paper's
+ * method: the denominators of the roofline fractions of kernels that HBM
+ * bandwidth does not bound.  Both only launch one kernel on `stream`; the
+ * caller times it with CUDA events on that stream.
+ * sce_peak_fma: `blocks` blocks of 256 threads; every thread runs
+ *   iters * 128 FP32 FMAs in eight independent chains, i.e.
+ *   blocks * 8 * iters * 128 FMA warp instructions and
+ *   blocks * 256 * iters * 256 FLOP in all.  out: device float[blocks],
+ *   written only in a case that cannot occur (keeps the work live).
+ * sce_peak_l2: `blocks` blocks of 256 threads read the device buffer `buf`
+ *   (16-byte aligned, `bytes` a multiple of 16) `reps` times through L2 only
+ *   (ld.global.cg), bytes * reps bytes in all; size it well below the L2
+ *   capacity and discard the first launch so that the reads hit L2.
+ *   out: device float[blocks], as above.
+ * Errors: CE_ERR_INVALID_ARG for null pointers, non-positive counts or a
+ * misaligned buffer; CE_ERR_CUDA if the launch fails.
+ */
+int sce_peak_fma(float *out, int blocks, int iters, void *stream);
+int sce_peak_l2(const void *buf, size_t bytes, int reps, int blocks, float *out, void *stream);
 
 #ifdef __cplusplus
 }

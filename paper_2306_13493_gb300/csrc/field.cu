@@ -804,9 +804,12 @@ static int sample_batch_static_t(ce_embedding_t e, uint64_t seed, uint32_t level
     R2 *Yf = reinterpret_cast<R2 *>(scratch);
     R2 *Yc = masked ? reinterpret_cast<R2 *>(scratch + (((size_t)chunk * yf + 255) & ~(size_t)255))
                     : nullptr;
-    const LineCfg rc = line_cfg<R>(P, masked ? P : P / 2);
-    const LineCfg cc = line_cfg<R>(P, m + 1);
-    const LineCfg ccc = line_cfg<R>(P, mc + 1);
+    // the launch shapes ce_autotune_fft chose, as ce_sample_batch uses them
+    // (a map lookup under a mutex; no allocation)
+    const LineCfg rc = line_cfg_tuned<R>(P, masked ? P : P / 2,
+                                         masked ? TUNE_ROW_MASKED : TUNE_ROW_PLAIN);
+    const LineCfg cc = line_cfg_tuned<R>(P, m + 1, TUNE_COL);
+    const LineCfg ccc = line_cfg_tuned<R>(P, mc + 1, TUNE_COL);
     int rcode = CE_OK;
     for (int c0 = 0; c0 < count && rcode == CE_OK; c0 += chunk) {
         const int cn = std::min(chunk, count - c0);

@@ -101,6 +101,10 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
     cudaEvent_t ev_field = nullptr, ev_coarse = nullptr;
     std::vector<void *> owned;
     auto cleanup = [&]() {
+        // coarse kernels of the split path may still be in flight on stc
+        // after an error return: the stream-ordered frees on st must not
+        // hand their buffers to the next allocation before they finish
+        if (split) cudaStreamSynchronize(stc);
         for (void *q : owned) sce_free(q, st);
         if (ev_field) cudaEventDestroy(ev_field);
         if (ev_coarse) cudaEventDestroy(ev_coarse);

@@ -129,3 +129,87 @@ def test_estimate_levels_waits_for_the_callers_stream(sce):
     assert abs(float(tot) - (sums[0].sumY + sums[1].sumY)) < 1e-9
     for e in embs:
         e.close()
+
+
+# Levels of the oscillatory workload (Matern nu = 0.5, lambda = 0.02, smooth
+# periodisation J = n, n_l = 16 * 2^l) whose fine solve is the batched
+# multigrid-CG solver: levels 2 (n = 64) and 3 (n = 128).  By default the
+# coarse solve runs first and the fine solve starts from its prolonged
+# solution (nested iteration); SCE_NESTED=0 starts both from the lifting.
+# The chunk bound splits the level into several chunks (2 samples each).
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("nested", [True, False])
+@pytest.mark.parametrize("level,finest", [(2, False), (3, True)])
+def test_batched_level_estimate_matches_oracle(sce, level, finest, nested, precision,
+                                               monkeypatch):
+    """Algorithm 2 step 4 and Eq. (3.5) on the path the oscillatory MLMC step
+    runs for n >= 64: per-sample Y against the oracle's direct solves, 1e-9
+    (FP64) / 1e-5 (FP32 normals and field), and the level sums."""
+    import torch
+    import workloads
+    w = workloads.OSCILLATORY
+    n = w.n0 << level
+    monkeypatch.setenv("SCE_MLMC_CHUNK_VERTICES", str(2 * (n + 1) * (n + 1)))
+    monkeypatch.setenv("SCE_NESTED", "1" if nested else "0")
+    oe = oem.setup_embedding(ocv.MATERN, w.nu, w.lam, w.sigma2, n, oem.PAD_SMOOTH)
+    mf, mc = omlmc.default_masks(oe, True, finest)
+    keep_f, keep_c = workloads.keep_counts(oe.P, finest, True)
+    emb = sce.ce_setup_embedding(ocv.MATERN, w.nu, w.lam, w.sigma2, n, pad_mode=oem.PAD_SMOOTH,
+                                 keep_fine=keep_f, keep_coarse=keep_c)
+    assert emb.P == oe.P
+    count, first = 5, 1 << 33
+    Y = torch.full((count,), float("nan"), dtype=torch.float64, device="cuda")
+    out, st = sce.mlmc_level_estimate(emb, w.seed, level, first, count, qoi_index=w.qoi,
+                                      f=w.f, rtol=1e-12, precision=precision, Y=Y)
+    torch.cuda.synchronize()
+    emb.close()
+    assert st == 0 and out.N == count and out.n_failed == 0
+    (N, s1, s2, f1, f2), oY = omlmc.level_estimate(oe, mf, mc, w.seed, level, first, count,
+                                                   qoi_index=w.qoi, f=w.f, precision=precision)
+    tol = 1e-9 if precision == 64 else 1e-5
+    Yg = Y.cpu().numpy()
+    assert np.max(np.abs(Yg - oY)) < tol
+    assert abs(out.sumY - s1) < tol * count
+    assert abs(out.sumQf - f1) < tol * abs(f1)
+    assert abs(out.sumQf2 - f2) < 2 * tol * abs(f2)
+    assert abs(out.sumY - Yg.sum()) < 1e-12 * max(1.0, abs(out.sumY))
+    assert abs(out.sumY2 - (Yg * Yg).sum()) < 1e-12 * max(1.0, out.sumY2)
+
+
+@pytest.mark.parametrize("nested", [True, False])
+def test_estimate_levels_batched_levels_match_oracle(sce, nested, monkeypatch):
+    """The all-levels call on levels 2 and 3 of the oscillatory workload
+    (concurrent streams, chunked, FP32 path): per-sample Y equals the
+    oracle's to 1e-5."""
+    import torch
+    import workloads
+    w = workloads.OSCILLATORY
+    monkeypatch.setenv("SCE_NESTED", "1" if nested else "0")
+    monkeypatch.setenv("SCE_MLMC_CHUNK_VERTICES", str(3 * 129 * 129))
+    tasks, oracle_Y = [], []
+    embs = []
+    for level, count in ((2, 7), (3, 4)):
+        n = w.n0 << level
+        finest = level == 3
+        oe = oem.setup_embedding(ocv.MATERN, w.nu, w.lam, w.sigma2, n, oem.PAD_SMOOTH)
+        mf, mc = omlmc.default_masks(oe, True, finest)
+        kf, kc = workloads.keep_counts(oe.P, finest, True)
+        e = sce.ce_setup_embedding(ocv.MATERN, w.nu, w.lam, w.sigma2, n,
+                                   pad_mode=oem.PAD_SMOOTH, keep_fine=kf, keep_coarse=kc)
+        embs.append(e)
+        first = 11 * level
+        tasks.append({"emb": e, "level": level, "first_sample": first, "count": count,
+                      "Y": torch.full((count,), float("nan"), dtype=torch.float64,
+                                      device="cuda")})
+        oracle_Y.append(omlmc.level_estimate(oe, mf, mc, w.seed, level, first, count,
+                                             qoi_index=w.qoi, f=w.f, precision=32)[1])
+    sums, stats, st = sce.mlmc_estimate_levels(tasks, w.seed, qoi_index=w.qoi, f=w.f,
+                                               rtol=1e-12, precision=32, max_concurrency=2)
+    torch.cuda.synchronize()
+    assert st == 0 and stats == [0, 0]
+    for t, oY, s in zip(tasks, oracle_Y, sums):
+        Yg = t["Y"].cpu().numpy()
+        assert np.max(np.abs(Yg - oY)) < 1e-5
+        assert s.N == t["count"] and s.n_failed == 0
+    for e in embs:
+        e.close()
