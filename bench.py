@@ -11,8 +11,10 @@ sums, through mlmc_level_estimate of the C ABI.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 32|64]
     python bench.py --impl reference ...      # the FP64 CPU oracle, bounded sample
 
-Prints one JSON line (rank 0).  value = fine-level samples (Y_l samples, each a
-field + fine + coarse solve) per second over all ranks.
+Prints one JSON line (rank 0).  value = MLMC level-samples per second over all
+levels and ranks (each a Y_l sample: field + fine and coarse solve + QoI); the
+finest-level rate (the n = 512 samples of a sweep per second) and each level's
+rate are reported beside it.
 """
 import argparse
 import json
@@ -29,8 +31,10 @@ if ROOT not in sys.path:
 
 import workloads  # noqa: E402
 
-METRIC = "fine-level samples/s (field+Darcy solve)"
-UNIT = "samples/s"
+METRIC = ("MLMC level-samples/s, all levels of one sweep (each sample: field + fine and "
+          "coarse Darcy solves + QoI + Y_l)")
+UNIT = "level-samples/s"
+DTYPE_MIXED = "f32+ff(fp32x2)+f64 eig/QoI"
 L2_BYTES = 129 * 1024 * 1024
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of
 # the dominant kernel family, from a capture of its n = 256 launch (profiles/ summary of
@@ -65,6 +69,8 @@ def parse():
                     help="keep the default FFT launch shapes (no tuning before the timed steps)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-level launch measurement")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP32 FMA issue rate and the L2 read bandwidth and exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -715,6 +721,100 @@ def precision_study(args):
     return 0
 
 
+# bound of each kernel family that HBM bandwidth does not bound: the coarse
+# multigrid tail reads its levels from L2 (judged against the measured L2 read
+# bandwidth); the row pass (Philox, Box-Muller, butterflies) and the one-block
+# solver (whole solve in shared memory) are bound by instruction issue; the
+# reductions (one warp per sample over a few partials) by launch latency.  The
+# rest are HBM-bound.
+KERNEL_BOUND = {"mg_tail": "l2", "ce_row": "issue", "darcy_small": "issue",
+                "reduce": "latency", "level_sums": "latency"}
+
+
+def measure_peaks(sce, stream, reps=10):
+    """FP32 FMA issue rate and L2 read bandwidth of this GPU, by the library's
+    two peak kernels (sce_peak_fma / sce_peak_l2): best of `reps` CUDA-event
+    timings after a warm-up launch."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks, dtype=torch.float32, device="cuda")
+
+    def best(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    iters = 2000
+    ms = best(lambda: sce.sce_peak_fma(out, blocks, iters, stream=stream.cuda_stream))
+    warp_inst = blocks * 8 * iters * 128
+    l2_bytes, l2_reps = 32 << 20, 400
+    buf = torch.ones(l2_bytes // 4, dtype=torch.float32, device="cuda")
+    ms2 = best(lambda: sce.sce_peak_l2(buf, l2_reps, blocks, out, stream=stream.cuda_stream))
+    return {"fma_warp_inst_per_s": warp_inst / (ms / 1000.0),
+            "fp32_tflops": warp_inst * 32 * 2 / (ms / 1000.0) / 1e12,
+            "l2_read_gbs": l2_bytes * l2_reps / (ms2 / 1000.0) / 1e9,
+            "sms": sms,
+            "how": "sce_peak_fma: %d blocks x 256 threads x %d x 128 FMAs in 8 independent "
+                   "chains; sce_peak_l2: %d MiB buffer read %d times by ld.global.cg, %d blocks; "
+                   "best of %d CUDA-event timings" % (blocks, iters, l2_bytes >> 20, l2_reps,
+                                                       blocks, reps)}
+
+
+def run_peaks(args):
+    import torch
+    from paper_2306_13493_gb300 import build, sce
+    build.build_library()
+    sce.load()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    clocks.start()
+    pk = measure_peaks(sce, stream, reps=20)
+    pk["clocks"] = clocks.stop()
+    print(json.dumps(pk), flush=True)
+    return 0
+
+
+def plain_small_bench(sce, stream, flush):
+    """The plain small workload (workloads.PLAIN_SMALL: 33 x 33 vertices,
+    doubled embedding, no smoothing, f = 0, outflow): its 256 samples in one
+    level call, FP64 (as quoted) and on the mixed path; CUDA events, L2 flushed."""
+    import torch
+    wl = workloads.PLAIN_SMALL
+    n, N = wl.n0, wl.N[0]
+    emb = sce.ce_setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n, pad_mode=wl.pad_mode)
+    Y = torch.empty(N, dtype=torch.float64, device="cuda")
+    out = {"workload": wl.describe(), "P": emb.P}
+    for prec in (64, 32):
+        ms = []
+        for r in range(6):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sce.mlmc_level_estimate(emb, wl.seed, 0, r * N, N, qoi_index=wl.qoi, f=wl.f,
+                                    rtol=wl.rtol, maxit=2000, precision=prec, Y=Y,
+                                    stream=stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= 2:
+                ms.append(e0.elapsed_time(e1))
+        m = statistics.mean(ms)
+        out["f64" if prec == 64 else "mixed"] = {"ms": round(m, 3),
+                                                  "samples_per_s": round(N / (m / 1000.0), 1)}
+    emb.close()
+    return out
+
+
 def mixed_launch_bench(args, sce, stream):
     """workloads.MIXED_LAUNCH: the level-pair buckets of several grid sizes
     in one mlmc_estimate_levels call (all buckets in flight at once), timed
@@ -923,13 +1023,14 @@ def run_ours(args):
     iters_tot = [0] * len(wl.N)
     solves = [0] * len(wl.N)
 
-    def step(i, copy_y=False, record=True, conc=None):
+    def step(i, copy_y=False, record=True, conc=None, precision=None):
         sums = torch.zeros(len(wl.N), 5, dtype=torch.float64)
         tasks = [{"emb": embs[l], "level": l, "count": N, "Y": Ybuf[l],
                   "first_sample": workloads.shard_first_sample(i, rank, world, N)}
                  for (l, n, N) in wl.levels]
         outs, _, _ = sce.mlmc_estimate_levels(
-            tasks, wl.seed, qoi_index=wl.qoi, f=wl.f, rtol=wl.rtol, maxit=2000, precision=prec,
+            tasks, wl.seed, qoi_index=wl.qoi, f=wl.f, rtol=wl.rtol, maxit=2000,
+            precision=prec if precision is None else precision,
             max_concurrency=args.concurrency if conc is None else conc,
             stream=stream.cuda_stream, allow_not_converged=True)
         for (l, n, N), out in zip(wl.levels, outs):
@@ -1021,9 +1122,18 @@ def run_ours(args):
     roof = None
     kernels = {}
     prof_total = sum(v[0] for v in prof.values()) if prof else 0.0
+    mpk = measure_peaks(sce, stream)
     for name, (ms, by, nl) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        gbs = by / (ms * 1e6) if ms > 0 else None
+        bound = KERNEL_BOUND.get(name, "hbm")
+        frac = None
+        if gbs is not None and bound == "hbm":
+            frac = round(gbs / hbm, 4)
+        elif gbs is not None and bound == "l2":
+            frac = round(gbs / mpk["l2_read_gbs"], 4)
         kernels[name] = {"ms": round(ms, 3), "launches": nl, "share": round(ms / prof_total, 4),
-                         "GBps": round(by / (ms * 1e6), 1) if ms > 0 else None}
+                         "GBps": round(gbs, 1) if gbs is not None else None, "bound": bound,
+                         "frac": frac}
     if top:
         name, (ms, by, nl) = top
         ach = by / (ms * 1e6)
@@ -1041,6 +1151,48 @@ def run_ours(args):
                 "timed": "one extra step after the timed ones, levels one after another, "
                          "CUDA events around every launch on its stream"}
 
+    # each level alone (one mlmc_level_estimate call of its N_l samples, CUDA
+    # events, L2 flushed): its samples/s when it has the GPU to itself
+    alone = []
+    for (l, n, N) in wl.levels:
+        ms = []
+        for r in range(3):
+            flush.zero_()
+            barrier()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            sce.mlmc_level_estimate(embs[l], wl.seed, l, 70_000_000 + r * N, N, qoi_index=wl.qoi,
+                                    f=wl.f, rtol=wl.rtol, maxit=2000, precision=prec,
+                                    Y=Ybuf[l], stream=stream.cuda_stream,
+                                    allow_not_converged=True)
+            a1.record(stream)
+            barrier()
+            if r:
+                ms.append(a0.elapsed_time(a1))
+        alone.append(statistics.mean(ms))
+
+    # the same sweep on the all-FP64 batched path (FP64 field, FP64 multigrid-CG)
+    fp64_batched = None
+    if not args.no_fp64_path and prec == 32:
+        step(300, record=False, precision=64)
+        ms = []
+        for i in range(2):
+            flush.zero_()
+            barrier()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            step(310 + i, record=False, precision=64)
+            b1.record(stream)
+            barrier()
+            ms.append(b0.elapsed_time(b1))
+        fms = statistics.mean(ms)
+        fp64_batched = {"value": world * Ntot / (fms / 1000.0), "unit": UNIT,
+                        "ms_per_step": round(fms, 3),
+                        "fine_level_samples_per_s": round(world * wl.N[-1] / (fms / 1000.0), 1),
+                        "dtype": "f64", "steps": 2,
+                        "note": "the same sweep, all levels in flight, FP64 field and FP64 "
+                                "multigrid-preconditioned CG; CUDA events, L2 flushed"}
+
     # level statistics of the timed steps
     per_level = []
     for (l, n, N) in wl.levels:
@@ -1051,26 +1203,33 @@ def run_ours(args):
         qv = (q2 - Nn * qm * qm) / (Nn - 1)
         per_level.append({"level": l, "n": n, "N": N, "mean_Y": mean, "var_Y": var,
                           "var_Qf": qv, "max_iters": iters_max[l],
-                          "mean_iters": round(iters_tot[l] / max(1, solves[l]), 2)})
+                          "mean_iters": round(iters_tot[l] / max(1, solves[l]), 2),
+                          "samples_per_s_in_sweep": round(world * N / (ms_per_step / 1000.0), 1),
+                          "ms_alone": round(alone[l], 3),
+                          "samples_per_s_alone": round(N / (alone[l] / 1000.0), 1)})
 
     # plain FP64 per-sample path (batch 1, FP64 field and solver), bounded sample
     fp64 = None
     if not args.no_fp64_path:
-        per = []
+        per, ks = [], []
         for (l, n, N) in wl.levels:
-            k = max(1, CPU_SAMPLES[l] // 4)
+            # at least 20 samples, or at least 2 s, per level
             barrier()
             t0 = time.perf_counter()
-            for i in range(k):
-                sce.mlmc_level_estimate(embs[l], wl.seed, l, 50_000_000 + i, 1, qoi_index=wl.qoi,
+            k = 0
+            while k < 20 and time.perf_counter() - t0 < 2.0:
+                sce.mlmc_level_estimate(embs[l], wl.seed, l, 50_000_000 + k, 1, qoi_index=wl.qoi,
                                         f=wl.f, rtol=wl.rtol, maxit=2000, precision=64,
                                         stream=stream.cuda_stream, allow_not_converged=True)
+                k += 1
             barrier()
             per.append((time.perf_counter() - t0) / k)
+            ks.append(k)
         sec = sum(N * per[l] for (l, _, N) in wl.levels) / Ntot
         fp64 = {"value": 1.0 / sec, "unit": UNIT, "speedup": value / world * sec,
-                "sample": "batch-1 FP64 calls, " + "/".join(
-                    str(max(1, c // 4)) for c in CPU_SAMPLES) + " samples on levels 0..5, "
+                "per_level_ms": [round(1000 * x, 3) for x in per],
+                "sample": "batch-1 FP64 calls (host wall clock), " + "/".join(map(str, ks)) +
+                " samples on levels 0..5 (20 per level, or as many as 2 s allow), "
                 "scaled to the N_l mix"}
 
     # MLMC to RMSE 1e-3 on the fixed levels 0..L, smoothed (MLMC-CES) and plain CE:
@@ -1116,6 +1275,10 @@ def run_ours(args):
         ttr["cost_ratio_plain_over_ces"] = round(ttr["plain"]["gpu_seconds"] /
                                                  ttr["ces"]["gpu_seconds"], 3)
 
+    plain_small = None
+    if rank == 0 and world == 1 and not args.no_mixed:
+        plain_small = plain_small_bench(sce, stream, flush)
+
     mixed = None
     if rank == 0 and world == 1 and not args.no_mixed:
         mixed = mixed_launch_bench(args, sce, stream)
@@ -1141,7 +1304,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if prec == 32 else "f64", "data": "synthetic",
+            "dtype": DTYPE_MIXED if prec == 32 else "f64", "data": "synthetic",
             "config": {"workload": wl.describe(), "precision": prec,
                        "levels_in_flight": args.concurrency,
                        "l2": "flushed before every timed step (256 MB write)",
@@ -1149,9 +1312,21 @@ def run_ours(args):
             "clocks": clk, "e2e": e2e,
             "gpu_launches": int(sum(v[2] for v in prof.values())) * args.steps,
             "gpu_launches_per_step": int(sum(v[2] for v in prof.values())),
+            "sweeps_per_s": round(1000.0 / ms_per_step, 3),
+            "fine_level": {"value": round(world * wl.N[-1] / (ms_per_step / 1000.0), 1),
+                           "unit": "finest-level samples/s",
+                           "n": wl.levels[-1][1],
+                           "note": "the finest level's N_L samples (n = %d fine, %d coarse) per "
+                                   "second of the full sweep; alone on the GPU: %.1f samples/s"
+                                   % (wl.levels[-1][1], wl.levels[-1][1] // 2,
+                                      per_level[-1]["samples_per_s_alone"])},
+            "fp64_batched": fp64_batched,
             "roofline": roof, "kernels": kernels, "per_level": per_level,
+            "measured_peaks": {k: (round(v, 4) if isinstance(v, float) else v)
+                               for k, v in mpk.items()},
             "autotune": autotune,
             "fp64_per_sample_path": fp64, "time_to_rmse": ttr, "mixed_launch": mixed,
+            "plain_small": plain_small,
             "serving": serving,
             "cpu_baseline": cpu,
         }
@@ -1166,6 +1341,8 @@ def main():
     args = parse()
     if args.case:
         return run_case(args)
+    if args.peaks:
+        return run_peaks(args)
     if args.study == "precision":
         return precision_study(args)
     if args.study == "smoothing":

@@ -178,6 +178,8 @@ _SIGS = {
     "ce_destroy": (None, [_P]),
     "ce_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sce_last_error": (ctypes.c_char_p, []),
+    "sce_peak_fma": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "sce_peak_l2": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _P, _P]),
     "sce_profile_enable": (None, [ctypes.c_int]),
     "sce_profile_read": (ctypes.c_int, [ctypes.c_int, _P, _P, _P]),
     "sce_profile_count": (ctypes.c_int, []),
@@ -611,3 +613,17 @@ def mlmc_tau_matern(h, J, nu, alpha, cs_over_calpha=1.0):
     _check(load().mlmc_tau_matern(float(h), float(J), float(nu), float(alpha),
                                   float(cs_over_calpha), ctypes.byref(t)), "mlmc_tau_matern")
     return t.value
+
+
+def sce_peak_fma(out, blocks, iters, stream=None):
+    """Launches the FP32 FMA issue-rate kernel (blocks * 8 * iters * 128 FMA
+    warp instructions); the caller times it on ``stream``."""
+    _check(load().sce_peak_fma(_ptr(out), blocks, iters, _stream(stream, out)), "sce_peak_fma")
+
+
+def sce_peak_l2(buf, reps, blocks, out, stream=None):
+    """Launches the L2 read-bandwidth kernel over the CUDA tensor ``buf``
+    (buf.nbytes * reps bytes); the caller times it on ``stream``."""
+    nbytes = buf.numel() * buf.element_size()
+    _check(load().sce_peak_l2(_ptr(buf), nbytes, reps, blocks, _ptr(out), _stream(stream, out)),
+           "sce_peak_l2")
