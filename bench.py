@@ -784,6 +784,154 @@ def run_peaks(args):
     return 0
 
 
+def cufft_comparison(sce, stream, flush, sizes=(32, 64, 128, 256, 512)):
+    """The library's FP32 field passes against cuFFT (through torch.fft, a
+    comparison only: the library never calls cuFFT) on the oscillatory
+    covariance at n = 32..512 (P = 4n = 128..2048), the finest-level masks
+    (fine field unsmoothed).  Accuracy: max relative error of each FP32 field
+    against the FP64 field of the library (which matches the FP64 oracle to
+    1e-10), from the same normals.  Time (CUDA events, L2 flushed):
+    ce_sample_batch for the whole field (normals, sqrt(Lambda~) scaling,
+    pruned row and column FFTs, Hartley, exp), against cuFFT for the
+    transform alone (a full P x P complex-to-complex +i transform of the
+    pre-computed, pre-scaled spectrum) and for transform + Hartley + exp of
+    the kept (n+1)^2 vertices."""
+    import torch
+    wl = workloads.OSCILLATORY
+    rows = []
+    for n in sizes:
+        emb = sce.ce_setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n, pad_mode=wl.pad_mode)
+        P = emb.P
+        count = max(2, min(64, (256 << 20) // (P * P * 8)))
+        lam = torch.empty(P * P, dtype=torch.float64, device="cuda")
+        sce.ce_get_eigenvalues(emb, lam)
+        sq = lam.clamp_min(0).sqrt().view(P, P)
+        xi64 = torch.empty(count, P * P, dtype=torch.float64, device="cuda")
+        xi32 = torch.empty(count, P * P, dtype=torch.float32, device="cuda")
+        sce.ce_normals(wl.seed, 0, 0, count, P * P, 64, xi64)
+        sce.ce_normals(wl.seed, 0, 0, count, P * P, 32, xi32)
+        k64 = torch.empty(count, n + 1, n + 1, dtype=torch.float64, device="cuda")
+        k32 = torch.empty(count, n + 1, n + 1, dtype=torch.float32, device="cuda")
+        sce.ce_sample_batch(emb, wl.seed, 0, 0, count, 64, k64)
+        sce.ce_sample_batch(emb, wl.seed, 0, 0, count, 32, k32)
+        w32 = (xi32.view(count, P, P) * sq.float()).to(torch.complex64)
+
+        def cufft_field(w):
+            v = torch.fft.ifft2(w, norm="forward")[:, :n + 1, :n + 1]
+            return torch.exp((v.real + v.imag) / P)
+
+        kc = cufft_field(w32)
+        # reference: the FP32 normals in FP64 arithmetic (both FP32 fields use them)
+        ref = cufft_field((xi32.double().view(count, P, P) * sq).to(torch.complex128))
+        rel = lambda a: float(((a.double() - ref).abs().max() / ref.abs().max()).item())
+
+        def t_ms(fn, reps=5):
+            fn()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            return statistics.median(ts)
+
+        ours = t_ms(lambda: sce.ce_sample_batch(emb, wl.seed, 0, 0, count, 32, k32,
+                                                stream=stream.cuda_stream))
+        tr = t_ms(lambda: torch.fft.ifft2(w32, norm="forward"))
+        full = t_ms(lambda: cufft_field(w32))
+        rows.append({"n": n, "P": P, "count": count,
+                     "ours_ms": round(ours, 4), "cufft_transform_ms": round(tr, 4),
+                     "cufft_field_ms": round(full, 4),
+                     "ours_rel_err_vs_fp64": rel(k32), "cufft_rel_err_vs_fp64": rel(kc),
+                     "ours_fp64_vs_ref": float(((k64 - cufft_field(
+                         (xi64.view(count, P, P) * sq).to(torch.complex128))).abs().max() /
+                         k64.abs().max()).item())})
+        emb.close()
+        del xi64, xi32, w32, k64, k32, kc, ref
+    return {"note": cufft_comparison.__doc__.split("\n\n")[0].replace("\n", " "),
+            "rows": rows}
+
+
+def time_to_rmse_study(sce, stream, prec, eps=1e-3, n_max=2048):
+    """Cost to a total root-mean-square error eps of the oscillatory covariance
+    (Matern nu = 0.5, lambda = 0.02, sigma^2 = 1, smooth periodisation J = n,
+    f = 1) for the QoI ||u||_L2 -- the paper's QoI for its Matern experiments
+    (§4.3); for the point value u(7/15, 7/15) the Richardson bias is still
+    ~1.5e-3 on the 2048^2 grid, so eps = 1e-3 is out of reach below it.
+    Variants: MLMC-CES (tau_l = sqrt(s_l), finest level unsmoothed) from
+    h0 = 1/4, 1/8, 1/16, and plain MLMC from its own coarsest mesh,
+    Eq. (3.8): the largest h0 = 2^-k <= sqrt(8 nu) lambda = 0.04, i.e. 1/32.
+    Each runs mlmc.run_adaptive: levels added (pilot 100 on the first three,
+    20 on each added one) until the Richardson bias (alpha fitted on the three
+    finest levels, at most 2; the three-level form of the test) is at most
+    eps/sqrt(2), up to the 2048^2 grid; there, with the bias below eps, the
+    variance target becomes eps^2 - bias^2 (fill_variance).  Cost = GPU seconds of every level
+    estimate (CUDA events), the samples of levels rebuilt when they stopped
+    being the finest included; embedding set-up is not counted (reported
+    apart as wall time).  cost_vs_eps predicts each variant's cost for other
+    eps from its measured level statistics with the finest level each eps
+    needs (the same bias test), and plain MC on that level's grid from
+    V[Q_L] and its cost per sample."""
+    import math as _m
+    from paper_2306_13493_gb300 import mlmc as gm
+    wl = workloads.OSCILLATORY
+    qoi = 2
+    seed = wl.seed + 1000
+    plain_n0 = gm.coarsest_cells(wl.kind, wl.nu, wl.lam)
+    variants = [("mlmc_ces", 4), ("mlmc_ces", 8), ("mlmc_ces", 16), ("mlmc_plain", plain_n0)]
+    out = {"eps": eps, "qoi": "||u||_L2", "f": wl.f,
+           "note": " ".join(time_to_rmse_study.__doc__.split())}
+    eps_list = [1e-2, 5e-3, 2e-3, 1e-3, 5e-4]
+    for name, n0 in variants:
+        smooth = name == "mlmc_ces"
+        L_max = int(round(_m.log2(n_max // n0)))
+        created = []
+
+        def make_runner(l, finest, n0=n0, smooth=smooth, created=created):
+            n = n0 << l
+            e0 = sce.ce_setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n,
+                                        pad_mode=wl.pad_mode)
+            kf, kc = workloads.keep_counts(e0.P, finest, smooth)
+            e0.close()
+            e = sce.ce_setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n,
+                                       pad_mode=wl.pad_mode, keep_fine=kf, keep_coarse=kc)
+            created.append(e)
+            return gm.LevelRunner(e, l, seed, qoi=qoi, f=wl.f, rtol=wl.rtol, precision=prec,
+                                  stream=stream)
+
+        t0 = time.perf_counter()
+        res = gm.run_adaptive(make_runner, eps, L0=min(2, L_max), L_max=L_max, pilot=100,
+                              pilot_new=20, alpha_levels=3, alpha_max=2.0, bias_levels=3,
+                              fill_variance=True, restart_previous_finest=smooth)
+        wall = time.perf_counter() - t0
+        for e in created:
+            e.close()
+        key = "%s_h0_1/%d" % (name, n0)
+        out[key] = {
+            "h0": 1.0 / n0, "levels_n": [x.n for x in res.levels],
+            "gpu_seconds": round(res.seconds, 4), "wall_seconds": round(wall, 2),
+            "estimate": res.estimate, "stat_error": res.stat_error, "bias_est": res.bias,
+            "rmse_est": res.rmse, "rmse_met": bool(res.rmse <= eps),
+            "var_share": round(res.var_share, 4), "alpha_finest3": res.alpha,
+            "N": [x.N for x in res.levels], "mean_Y": [x.mean for x in res.levels],
+            "var_Y": [x.var for x in res.levels],
+            "cost_per_sample_s": [x.cost for x in res.levels],
+            "cost_vs_eps": [{"eps": c["eps"], "finest_n": res.levels[c["L"]].n,
+                             "mlmc_s": round(c["mlmc_seconds"], 5),
+                             "mc_s": round(c["mc_seconds"], 5)}
+                            for c in gm.cost_versus_eps(res.levels, eps_list, choose_levels=True,
+                                                        alpha_levels=3, alpha_max=2.0,
+                                                        bias_levels=3)]}
+    ces = [v["gpu_seconds"] for k, v in out.items() if k.startswith("mlmc_ces")]
+    pl = out["mlmc_plain_h0_1/%d" % plain_n0]["gpu_seconds"]
+    out["cost_ratio_plain_over_best_ces"] = round(pl / min(ces), 3) if ces else None
+    return out
+
+
 def plain_small_bench(sce, stream, flush):
     """The plain small workload (workloads.PLAIN_SMALL: 33 x 33 vertices,
     doubled embedding, no smoothing, f = 0, outflow): its 256 samples in one
@@ -970,6 +1118,39 @@ def serving_bench(args, sce):
     return out
 
 
+def sharded_step_sums(run_levels, levels, step, rank, world, device=None):
+    """One step of the multi-GPU path: this rank runs its contiguous block of
+    every level's samples (workloads.shard_first_sample: the blocks of all
+    (step, rank) pairs tile the sample indices, so any partition draws the
+    samples of a single-rank run) and the per-level sums (N, sum Y, sum Y^2,
+    sum Q_f, sum Q_f^2) are all-reduced -- the estimator's one exchange.
+
+    run_levels(tasks) takes [(level, first_sample, count)] and returns one
+    5-tuple of sums per task.  device: where the all-reduce runs (the GPU
+    under NCCL, None = CPU under gloo).  Returns a (levels, 5) float64 tensor
+    on the CPU."""
+    import torch
+    tasks = [(l, workloads.shard_first_sample(step, rank, world, N), N) for (l, n, N) in levels]
+    sums = torch.tensor([list(r) for r in run_levels(tasks)], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        t = sums.to(device) if device is not None else sums
+        dist.all_reduce(t)
+        sums = t.cpu()
+    return sums
+
+
+def max_over_ranks(value, world, device=None):
+    """The largest of every rank's `value` (all ranks must call it)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -1024,28 +1205,24 @@ def run_ours(args):
     solves = [0] * len(wl.N)
 
     def step(i, copy_y=False, record=True, conc=None, precision=None):
-        sums = torch.zeros(len(wl.N), 5, dtype=torch.float64)
-        tasks = [{"emb": embs[l], "level": l, "count": N, "Y": Ybuf[l],
-                  "first_sample": workloads.shard_first_sample(i, rank, world, N)}
-                 for (l, n, N) in wl.levels]
-        outs, _, _ = sce.mlmc_estimate_levels(
-            tasks, wl.seed, qoi_index=wl.qoi, f=wl.f, rtol=wl.rtol, maxit=2000,
-            precision=prec if precision is None else precision,
-            max_concurrency=args.concurrency if conc is None else conc,
-            stream=stream.cuda_stream, allow_not_converged=True)
-        for (l, n, N), out in zip(wl.levels, outs):
-            sums[l] = torch.tensor([out.N, out.sumY, out.sumY2, out.sumQf, out.sumQf2])
-            iters_max[l] = max(iters_max[l], out.max_iters)
-            if record:
-                iters_tot[l] += out.total_iters
-                solves[l] += N * (2 if l > 0 else 1)
-            if copy_y:
-                Yhost[l].copy_(Ybuf[l], non_blocking=True)
-        if world > 1:
-            import torch.distributed as dist
-            t = sums.to(dev)
-            dist.all_reduce(t)
-            sums = t.cpu()
+        def run_levels(tl):
+            tasks = [{"emb": embs[l], "level": l, "count": N, "Y": Ybuf[l],
+                      "first_sample": first} for (l, first, N) in tl]
+            outs, _, _ = sce.mlmc_estimate_levels(
+                tasks, wl.seed, qoi_index=wl.qoi, f=wl.f, rtol=wl.rtol, maxit=2000,
+                precision=prec if precision is None else precision,
+                max_concurrency=args.concurrency if conc is None else conc,
+                stream=stream.cuda_stream, allow_not_converged=True)
+            for (l, n, N), out in zip(wl.levels, outs):
+                iters_max[l] = max(iters_max[l], out.max_iters)
+                if record:
+                    iters_tot[l] += out.total_iters
+                    solves[l] += N * (2 if l > 0 else 1)
+                if copy_y:
+                    Yhost[l].copy_(Ybuf[l], non_blocking=True)
+            return [(o.N, o.sumY, o.sumY2, o.sumQf, o.sumQf2) for o in outs]
+
+        sums = sharded_step_sums(run_levels, wl.levels, i, rank, world, dev)
         if copy_y:
             stream.synchronize()
         if record:
@@ -1075,11 +1252,7 @@ def run_ours(args):
         barrier()
         total_ms += e0.elapsed_time(e1)
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     ms_per_step = total_ms / args.steps
     Ntot = sum(wl.N)
     value = world * Ntot / (ms_per_step / 1000.0)
@@ -1091,12 +1264,7 @@ def run_ours(args):
     for i in range(e2e_steps):
         step(100 + i, copy_y=True, record=False)
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     e2e = {"value": world * Ntot / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * Ntot + 56 * len(wl.N),
            "note": "inputs are the scalar sample ranges (normals are drawn on the device); "
@@ -1232,52 +1400,17 @@ def run_ours(args):
                 " samples on levels 0..5 (20 per level, or as many as 2 s allow), "
                 "scaled to the N_l mix"}
 
-    # MLMC to RMSE 1e-3 on the fixed levels 0..L, smoothed (MLMC-CES) and plain CE:
-    # pilot runs, Eq. (3.6) sample sizes from the measured V_l and C_l, top-ups until
-    # the statistical error meets eps/sqrt(2); the bias of the level-L hierarchy is
-    # estimated as in §4 (Richardson, alpha fitted on the three finest levels)
+    # MLMC to a total RMSE of 1e-3 (§4.2-4.3): MLMC-CES from coarse meshes and plain
+    # MLMC from its own coarsest mesh (Eq. (3.8)), levels added adaptively
     ttr = None
     if rank == 0 and world == 1 and not args.no_fp64_path:
-        from paper_2306_13493_gb300 import mlmc as gm
-        eps = 1e-3
-        ttr = {"eps": eps, "target": "statistical error <= eps/sqrt(2) (the variance share "
-               "of Eq. (3.6)) on levels 0..%d; bias of that hierarchy reported" % L}
-        for variant in ("ces", "plain"):
-            lembs = embs
-            if variant == "plain":
-                lembs = [sce.ce_setup_embedding(wl.kind, wl.nu, wl.lam, wl.sigma2, n,
-                                                pad_mode=wl.pad_mode) for (_, n, _) in wl.levels]
-            runners = [gm.LevelRunner(lembs[l], l, wl.seed + 1000, qoi=wl.qoi, f=wl.f,
-                                      rtol=wl.rtol, precision=prec, stream=stream)
-                       for (l, _, _) in wl.levels]
-            res = gm.run_to_rmse(runners, eps, pilot=[400, 200, 100, 50, 20, 10])
-            fin = res.levels[-3:]
-            a3 = gm.fit_rate([x.level for x in fin], [abs(x.mean) for x in fin])
-            bias = gm.richardson_bias(res.levels, a3)
-            fp64_s = sum(x.N * per[x.level] for x in res.levels) if fp64 else None
-            ttr[variant] = {
-                "gpu_seconds": round(res.seconds, 4), "estimate": res.estimate,
-                "stat_error": res.stat_error, "N": [x.N for x in res.levels],
-                "mean_Y": [x.mean for x in res.levels], "var_Y": [x.var for x in res.levels],
-                "cost_per_sample_s": [x.cost for x in res.levels],
-                "alpha_finest3": a3, "bias_est": bias,
-                "rmse_est": (res.stat_error ** 2 + bias ** 2) ** 0.5,
-                "fp64_per_sample_path_seconds": round(fp64_s, 3) if fp64_s else None,
-                "speedup_vs_fp64_path": round(fp64_s / res.seconds, 1) if fp64_s else None,
-                # predicted GPU seconds versus eps from these level statistics (§4.2-4.3)
-                "cost_vs_eps": [{"eps": c["eps"], "mlmc_s": round(c["mlmc_seconds"], 5),
-                                 "mc_s": round(c["mc_seconds"], 5)}
-                                for c in gm.cost_versus_eps(res.levels,
-                                                            [1e-2, 5e-3, 2e-3, 1e-3, 5e-4])]}
-            if variant == "plain":
-                for e in lembs:
-                    e.close()
-        ttr["cost_ratio_plain_over_ces"] = round(ttr["plain"]["gpu_seconds"] /
-                                                 ttr["ces"]["gpu_seconds"], 3)
+        ttr = time_to_rmse_study(sce, stream, prec)
 
     plain_small = None
+    cufft = None
     if rank == 0 and world == 1 and not args.no_mixed:
         plain_small = plain_small_bench(sce, stream, flush)
+        cufft = cufft_comparison(sce, stream, flush)
 
     mixed = None
     if rank == 0 and world == 1 and not args.no_mixed:
@@ -1326,7 +1459,7 @@ def run_ours(args):
                                for k, v in mpk.items()},
             "autotune": autotune,
             "fp64_per_sample_path": fp64, "time_to_rmse": ttr, "mixed_launch": mixed,
-            "plain_small": plain_small,
+            "plain_small": plain_small, "cufft_comparison": cufft,
             "serving": serving,
             "cpu_baseline": cpu,
         }

@@ -83,6 +83,8 @@ class MLMCResult:
     seconds: float
     levels: List[LevelStats] = field(default_factory=list)
     N_opt: Optional[List[int]] = None
+    alpha: float = float("nan")
+    var_share: float = 0.5      # variance target / eps^2 used for the sample sizes
 
 
 class LevelRunner:
@@ -223,60 +225,114 @@ def rates(stats: List[LevelStats]):
     return alpha, beta, gamma
 
 
-def richardson_bias(stats: List[LevelStats], alpha, ratio=1.0):
+def richardson_bias(stats: List[LevelStats], alpha, ratio=1.0, levels=1):
     """§4: |E[Q_h - Q]| from the finest level's mean E[Y_L] = E[Q_h - Q_2h] by
     Richardson extrapolation, |E[Y_L] / (1 - 2^alpha)|.  With smoothing the
     extrapolant is the smoothed coarse QoI and the denominator becomes
     1 - ratio 2^alpha, ratio = C~_alpha / C_alpha (the constants of the
     smoothed and plain bias, |E[Q~_h - Q]| = C~_alpha h^alpha); infinite when
-    that denominator vanishes."""
+    that denominator vanishes.
+
+    levels > 1: the robust form of Giles' adaptive algorithm -- the largest of
+    |E[Y_(L-j)]| 2^(-j alpha), j < levels (levels l >= 1 only), in the
+    numerator, so that one finest level whose mean happens to be small (a
+    sign change of E[Y_l] in the pre-asymptotic range) does not end the
+    level loop."""
     if not math.isfinite(alpha) or alpha <= 0:
         alpha = 1.0
     d = 1.0 - ratio * 2.0 ** alpha
-    return abs(stats[-1].mean / d) if d != 0.0 else math.inf
+    if d == 0.0:
+        return math.inf
+    top = abs(stats[-1].mean)
+    for j in range(1, levels):
+        if len(stats) - 1 - j < 1:
+            break
+        top = max(top, abs(stats[-1 - j].mean) * 2.0 ** (-j * alpha))
+    return abs(top / d)
 
 
-def cost_versus_eps(stats: List[LevelStats], eps_list, mc_cost_per_sample=None):
+def cost_versus_eps(stats: List[LevelStats], eps_list, mc_cost_per_sample=None,
+                    choose_levels=False, alpha=None, ratio=1.0, bias_levels=1,
+                    alpha_levels=3, alpha_max=None):
     """Predicted cost to a root-mean-square error eps from measured level
     statistics, for the cost-versus-accuracy comparisons of §4.2-4.3 (the
-    variance share eps^2/2 in both; the bias is that of the finest grid):
+    variance share eps^2/2 in both):
 
     * multilevel (MLMC, or MLMC-CES when the levels were smoothed):
       sum_l N_l C_l with N_l of Eq. (3.6) from the measured V_l and C_l;
-    * plain MC on the finest grid: N = ceil(2 eps^-2 V[Q_L]) samples, V[Q_L]
-      the variance of the finest level's fine QoI, at mc_cost_per_sample each
-      (default: the finest level's cost per sample, which also solves the
-      coarse grid, so an upper bound).
+    * plain MC on the finest grid used: N = ceil(2 eps^-2 V[Q_L]) samples,
+      V[Q_L] the variance of that level's fine QoI, at mc_cost_per_sample each
+      (default: that level's cost per sample, which also solves the coarse
+      grid, so an upper bound).
 
-    Returns one dict per eps: eps, N (per level), mlmc_seconds, mc_N,
+    choose_levels: the finest level L(eps) is the coarsest one whose
+    Richardson bias (alpha fitted on the `alpha_levels` finest of the measured
+    levels, at most alpha_max; ``richardson_bias`` with `bias_levels`) is at
+    most eps/sqrt(2), as the adaptive algorithm would pick it (the last
+    measured level if none is); otherwise every measured level is used.  The
+    statistics of a level that is not the finest stand in for it as the
+    finest (under smoothing its fine field would then be unsmoothed).
+
+    Returns one dict per eps: eps, L, N (per level), mlmc_seconds, mc_N,
     mc_seconds."""
     V = [max(s.var, 1e-300) for s in stats]
     C = [max(s.cost, 1e-12) for s in stats]
-    vq = stats[-1].var_q
-    c_mc = C[-1] if mc_cost_per_sample is None else float(mc_cost_per_sample)
+    a = alpha
+    if choose_levels and a is None:
+        a = fit_alpha(stats, alpha_levels, alpha_max)
     out = []
     for eps in eps_list:
-        N = [int(n) for n in sce.mlmc_optimal_samples(V, C, eps)]
+        L = len(stats) - 1
+        if choose_levels:
+            for l in range(1, len(stats)):
+                if richardson_bias(stats[:l + 1], a, ratio, bias_levels) <= eps / math.sqrt(2.0):
+                    L = l
+                    break
+        N = [int(n) for n in sce.mlmc_optimal_samples(V[:L + 1], C[:L + 1], eps)]
+        vq = stats[L].var_q
+        c_mc = C[L] if mc_cost_per_sample is None else float(mc_cost_per_sample)
         mc_N = int(math.ceil(2.0 * vq / (eps * eps)))
-        out.append({"eps": eps, "N": N, "mlmc_seconds": sum(n * c for n, c in zip(N, C)),
+        out.append({"eps": eps, "L": L, "N": N,
+                    "mlmc_seconds": sum(n * c for n, c in zip(N, C[:L + 1])),
                     "mc_N": mc_N, "mc_seconds": mc_N * c_mc})
     return out
 
 
+def fit_alpha(stats: List[LevelStats], finest=None, alpha_max=None):
+    """alpha of §4 from |E Y_l| of levels l >= 1; with `finest`, from the
+    `finest` finest levels only (the coarse levels of a rough field are not
+    yet in the asymptotic regime, and the Richardson estimate extrapolates
+    from the finest one); at most alpha_max when given (a fit through a
+    pre-asymptotic dip of |E Y_l| can return rates no discretisation has)."""
+    s = [x for x in stats if x.level >= 1 and x.N > 1]
+    if finest is not None:
+        s = s[-finest:]
+    a = fit_rate([x.level for x in s], [abs(x.mean) for x in s])
+    if alpha_max is not None and math.isfinite(a):
+        a = min(a, alpha_max)
+    return a
+
+
 def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rounds=10,
-                ratio=1.0):
-    """MLMC with the fixed level set of `runners` to a root-mean-square error eps
-    (variance share eps^2/2, Eq. (3.6)): pilot samples, then the optimal N_l
-    from the measured V_l and C_l, topped up until no level needs more than 1 %
-    extra samples.  Returns the estimate, the estimated RMSE (statistical error
-    and Richardson bias) and the GPU seconds spent."""
+                ratio=1.0, var_share=0.5, alpha_levels=None, alpha_max=None, bias_levels=1):
+    """MLMC with the fixed level set of `runners` to a root-mean-square error eps:
+    pilot samples, then the optimal N_l from the measured V_l and C_l for the
+    variance target var_share * eps^2 (Eq. (3.6) as printed: var_share = 1/2),
+    topped up until no level needs more than 1 % extra samples.  alpha (given,
+    or fitted on the `alpha_levels` finest levels, all levels l >= 1 if None)
+    enters the Richardson bias.  Returns the estimate, the estimated RMSE
+    (statistical error and bias) and the GPU seconds spent."""
+    if not 0.0 < var_share <= 1.0:
+        raise ValueError("var_share must be in (0, 1]")
     pilot = pilot or [100] * len(runners)
     _run_levels(runners, [p - r.stats.N for r, p in zip(runners, pilot)])
     N_opt = None
+    # Eq. (3.6) sizes for the variance target eps_v^2 / 2 = var_share eps^2
+    eps_v = eps * math.sqrt(2.0 * var_share)
     for _ in range(max_rounds):
         V = [max(r.stats.var, 1e-300) for r in runners]
         C = [max(r.stats.cost, 1e-12) for r in runners]
-        N_opt = sce.mlmc_optimal_samples(V, C, eps)
+        N_opt = sce.mlmc_optimal_samples(V, C, eps_v)
         extra = [max(0, int(n) - r.stats.N) for n, r in zip(N_opt, runners)]
         if all(e <= 0.01 * r.stats.N for e, r in zip(extra, runners)):
             break
@@ -284,20 +340,31 @@ def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rou
     stats = [r.stats for r in runners]
     est = sum(s.mean for s in stats)
     stat_err = math.sqrt(sum(s.var / s.N for s in stats))
-    a = alpha if alpha is not None else rates(stats)[0]
-    bias = richardson_bias(stats, a, ratio)
+    a = alpha if alpha is not None else fit_alpha(stats, alpha_levels, alpha_max)
+    bias = richardson_bias(stats, a, ratio, bias_levels)
     return MLMCResult(estimate=est, rmse=math.sqrt(stat_err ** 2 + bias ** 2), stat_error=stat_err,
                       bias=bias, seconds=sum(s.seconds for s in stats), levels=stats,
-                      N_opt=[int(n) for n in N_opt])
+                      N_opt=[int(n) for n in N_opt], alpha=a, var_share=var_share)
 
 
 def run_adaptive(make_runner: Callable[[int, bool], LevelRunner], eps, L0=2, L_max=8,
-                 pilot=100, alpha=None, ratio=1.0, max_rounds=10, restart_previous_finest=True):
+                 pilot=100, alpha=None, ratio=1.0, max_rounds=10, restart_previous_finest=True,
+                 alpha_levels=None, fill_variance=False, pilot_new=None, alpha_max=None,
+                 bias_levels=1):
     """MLMC to a root-mean-square error eps with the number of levels chosen as
     it runs: start on levels 0..L0, run ``run_to_rmse`` (variance share
     eps^2/2), and while the Richardson bias of the finest level exceeds the
     bias share eps/sqrt(2) and fewer than L_max + 1 levels are in use, add the
     next level (pilot samples, then the sample sizes of Eq. (3.6) again).
+
+    fill_variance: when L_max is reached with a bias b between eps/sqrt(2) and
+    eps, the mean-square error eps^2 = b^2 + variance can still be met by a
+    smaller variance share: the sample sizes are recomputed for the variance
+    target eps^2 - b^2 (var_share = 1 - (b/eps)^2, the general split of the
+    MSE between bias and variance of the adaptive MLMC algorithm of Giles, of
+    which Eq. (3.6)'s ratio 1/2 is one choice) and topped up; the bias is then
+    re-estimated from the larger samples and the share recomputed, up to three
+    times.  The result's var_share records the share used.
 
     make_runner(level, finest) builds the runner of a level.  Under MLMC-CES
     the finest level's fine field is not smoothed (§3.6), so a level that stops
@@ -305,20 +372,38 @@ def run_adaptive(make_runner: Callable[[int, bool], LevelRunner], eps, L0=2, L_m
     afresh (restart_previous_finest; the time of its discarded samples is kept
     in the cost).  Plain MLMC, whose levels do not depend on which is finest,
     passes restart_previous_finest=False.  Returns the MLMCResult of the final
-    level set; its `seconds` include every discarded sample."""
+    level set; its `seconds` include every discarded sample.
+
+    pilot_new: pilot samples of a level added (or rebuilt) after the first
+    L0 + 1 (default `pilot`): on fine levels Eq. (3.6) asks for few samples,
+    and a large pilot there dominates the cost.  alpha_levels, alpha_max and
+    bias_levels go to the bias estimate (``fit_alpha``, ``richardson_bias``)."""
     if L0 < 0 or L_max < L0:
         raise ValueError("need 0 <= L0 <= L_max")
     runners = [make_runner(l, l == L0) for l in range(L0 + 1)]
+    pilots = [pilot] * (L0 + 1)
+    pnew = pilot if pilot_new is None else pilot_new
     discarded = 0.0
+    kw = dict(alpha=alpha, max_rounds=max_rounds, ratio=ratio, alpha_levels=alpha_levels,
+              alpha_max=alpha_max, bias_levels=bias_levels)
     while True:
-        res = run_to_rmse(runners, eps, pilot=[pilot] * len(runners), alpha=alpha,
-                          max_rounds=max_rounds, ratio=ratio)
+        res = run_to_rmse(runners, eps, pilot=pilots, **kw)
         L = len(runners) - 1
         if res.bias <= eps / math.sqrt(2.0) or L >= L_max:
             break
         if restart_previous_finest:
             discarded += runners[L].stats.seconds
             runners[L] = make_runner(L, False)
+            pilots[L] = pnew
         runners.append(make_runner(L + 1, True))
+        pilots.append(pnew)
+    if fill_variance:
+        for _ in range(3):
+            if not eps / math.sqrt(2.0) < res.bias < eps:
+                break
+            share = 1.0 - (res.bias / eps) ** 2
+            if share >= res.var_share * 0.999 and res.rmse <= eps:
+                break
+            res = run_to_rmse(runners, eps, pilot=pilots, var_share=share, **kw)
     res.seconds += discarded
     return res

@@ -211,3 +211,79 @@ def test_workloads_keep_the_stated_configurations():
     assert w.keep_counts(64, finest=False, smoothing=True) == (64 * 64 - 64, 64 * 64 - 64)
     assert w.keep_counts(64, finest=True, smoothing=True) == (-1, 64 * 64 - 64)
     assert w.keep_counts(64, finest=True, smoothing=False) == (-1, -1)
+
+
+def test_run_adaptive_fills_the_variance_share_when_the_levels_run_out(drv):
+    """E[Y_l] = 0.08 2^-l and L_max = 4: the bias 0.005 exceeds eps/sqrt(2)
+    for eps = 0.006, but is below eps, so the variance target becomes
+    eps^2 - bias^2 (a smaller share than Eq. (3.6)'s 1/2) and the estimated
+    total RMSE meets eps; without fill_variance it does not."""
+    rng = np.random.default_rng(11)
+
+    def make_runner(level, finest):
+        return FakeRunner(level, 0.08 * 2.0 ** -level, 1e-2 * 16.0 ** -level,
+                          1e-6 * 4.0 ** level, rng)
+
+    eps = 0.006
+    plain = drv.run_adaptive(make_runner, eps, L0=2, L_max=4, pilot=100, alpha=1.0)
+    assert plain.var_share == 0.5 and plain.rmse > eps
+    res = drv.run_adaptive(make_runner, eps, L0=2, L_max=4, pilot=100, alpha=1.0,
+                           fill_variance=True)
+    assert len(res.levels) == 5
+    assert res.bias == pytest.approx(0.005, rel=0.05)
+    assert res.var_share == pytest.approx(1.0 - (res.bias / eps) ** 2, rel=0.05)
+    assert res.var_share < 0.5
+    assert res.stat_error <= eps * math.sqrt(res.var_share) * 1.1
+    assert res.rmse <= eps * 1.02
+    assert sum(s.N for s in res.levels) > sum(s.N for s in plain.levels)
+
+
+def test_alpha_from_the_finest_levels(drv):
+    """Pre-asymptotic coarse levels (E[Y_1] small) spoil a fit over all
+    levels; the fit over the three finest recovers the rate."""
+    stats = []
+    for l, m in zip(range(6), [0.6, 0.003, 0.016, 0.008, 0.004, 0.002]):
+        s = drv.LevelStats(level=l, n=16 << l, N=10)
+        s.sumY = m * s.N
+        stats.append(s)
+    assert abs(drv.fit_alpha(stats, 3) - 1.0) < 1e-12
+    assert abs(drv.fit_alpha(stats) - 1.0) > 0.2
+
+
+def test_robust_bias_and_alpha_cap(drv):
+    """A finest level whose mean is accidentally small does not end the level
+    loop under the three-level test: the bias is the largest of
+    |E Y_(L-j)| 2^(-j alpha); alpha_max caps a fit through such a dip."""
+    stats = []
+    for l, m in zip(range(4), [0.6, 0.02, 0.012, 1e-6]):
+        s = drv.LevelStats(level=l, n=4 << l, N=10)
+        s.sumY = m * s.N
+        stats.append(s)
+    assert drv.richardson_bias(stats, 1.0) == pytest.approx(1e-6)
+    assert drv.richardson_bias(stats, 1.0, levels=3) == pytest.approx(0.012 / 2)
+    # level 0 (Q itself) never enters: levels 3, 2, 1 give 1e-6, 0.006, 0.005
+    assert drv.richardson_bias(stats, 1.0, levels=5) == pytest.approx(0.006)
+    assert drv.fit_alpha(stats, 3) > 5
+    assert drv.fit_alpha(stats, 3, alpha_max=2.0) == 2.0
+
+
+def test_cost_versus_eps_chooses_the_finest_level(drv):
+    """With E[Y_l] = 0.08 2^-l (alpha = 1), eps = 0.01 needs the bias
+    0.08 2^-L <= eps/sqrt(2), i.e. L = 4; eps = 0.004 needs L = 5 = the last
+    level; a smaller eps falls back to the last level.  Plain MC runs on the
+    chosen level's grid."""
+    stats = []
+    for l in range(6):
+        s = drv.LevelStats(level=l, n=16 << l, N=100)
+        mean, var, cost = 0.08 * 2.0 ** -l, 1e-3 * 4.0 ** -l, 1e-6 * 4.0 ** l
+        s.sumY = mean * s.N
+        s.sumY2 = var * (s.N - 1) + s.N * mean * mean
+        s.sumQ2 = (1e-3 + 0.4) * s.N
+        s.sumQ = math.sqrt(0.4) * s.N
+        s.seconds = cost * s.N
+        stats.append(s)
+    out = drv.cost_versus_eps(stats, [0.01, 0.004, 1e-4], choose_levels=True, alpha=1.0)
+    assert [o["L"] for o in out] == [4, 5, 5]
+    assert len(out[0]["N"]) == 5 and len(out[1]["N"]) == 6
+    assert out[0]["mc_seconds"] == pytest.approx(out[0]["mc_N"] * 1e-6 * 4.0 ** 4)
+    assert [o["L"] for o in drv.cost_versus_eps(stats, [0.01])] == [5]
