@@ -723,11 +723,13 @@ def precision_study(args):
 
 # bound of each kernel family that HBM bandwidth does not bound: the coarse
 # multigrid tail reads its levels from L2 (judged against the measured L2 read
-# bandwidth); the row pass (Philox, Box-Muller, butterflies) and the one-block
-# solver (whole solve in shared memory) are bound by instruction issue; the
+# bandwidth); the row pass (Philox, Box-Muller, butterflies), the one-block
+# solver (whole solve in shared memory) and the fused n = 64 V-cycle (one
+# level in registers, the levels below in shared memory) are bound by
+# instruction issue and barriers; the
 # reductions (one warp per sample over a few partials) by launch latency.  The
 # rest are HBM-bound.
-KERNEL_BOUND = {"mg_tail": "l2", "ce_row": "issue", "darcy_small": "issue",
+KERNEL_BOUND = {"mg_tail": "l2", "ce_row": "issue", "darcy_small": "issue", "mg_v64": "issue",
                 "reduce": "latency", "level_sums": "latency"}
 
 

@@ -36,6 +36,7 @@
 
 #include "ff.cuh"
 #include "mg_tiles.cuh"
+#include "mg_v64.cuh"
 #include "sce_internal.cuh"
 
 using namespace sce;
@@ -729,9 +730,19 @@ struct Solver {
     int Lt = 0;                 // first level of the tail
     int tiles_x[MAXLEV], tiles_n[MAXLEV];
 
+    // FP32: an n = 64 level and everything below it run as one fused kernel
+    // per sample (mg_v64_kernel; SCE_V64=0 keeps the tiled kernels for it)
+    bool v64 = false;
+
     void plan_fused() {
+        int tail_n = TAIL_N;
+        if constexpr (sizeof(T) == 4) {
+            const char *e = getenv("SCE_V64");
+            if (!(e && atoi(e) == 0) && TAIL_N < V64_N) tail_n = V64_N;
+        }
         Lt = 0;
-        while (n[Lt] > TAIL_N) ++Lt;
+        while (n[Lt] > tail_n) ++Lt;
+        v64 = sizeof(T) == 4 && tail_n == V64_N && n[Lt] == V64_N;
         for (int L = 0; L < Lt; ++L) {
             const int nc1 = n[L] / 2 + 1;
             tiles_x[L] = (nc1 + MG_CW - 1) / MG_CW;
@@ -760,6 +771,29 @@ struct Solver {
                                                                 want_rz ? part : nullptr);
     }
 
+    bool v64_attr_set = false;
+    void v64_launch(bool want_rz) {
+        if constexpr (sizeof(T) == 4) {
+            TailPtrs tp{};
+            for (int i = 0; Lt + 1 + i < nlev && i < 8; ++i) {
+                tp.cx[i] = cx[Lt + 1 + i];
+                tp.cy[i] = cy[Lt + 1 + i];
+            }
+            constexpr size_t smem = v64_smem_bytes<T>();
+            if (!v64_attr_set) {   // outside any stream capture (the first cycle is not captured)
+                sce_raise_smem_limit((const void *)mg_v64_kernel<T>, smem);
+                v64_attr_set = true;
+            }
+            // b, cx, cy in, z out on the level; the conductances of the levels below in
+            double tail_v = 0.0;
+            for (int L = Lt + 1; L < nlev; ++L) tail_v += (double)ln[L].V;
+            SceProf pr(KP_MG_V64, st, vb(Lt, 4.0) + (double)count * tail_v * 2.0 * sizeof(T));
+            mg_v64_kernel<T><<<count, V64_THREADS, smem, st>>>(cx[Lt], cy[Lt], b[Lt], z[Lt], tp,
+                                                              sc.act_in,
+                                                              want_rz ? part : nullptr);
+        }
+    }
+
     // z[0] = M^{-1} b[0]; with want_rz the partial sums of b[0] . z[0] go to part
     void vcycle_fused(bool want_rz) {
         constexpr size_t smem = mg_tile_smem_bytes<T>();
@@ -774,7 +808,8 @@ struct Solver {
                 cx[L], cy[L], b[L], zpre[L], n[L], b[L + 1], tiles_x[L], sc.act_in);
         }
         const bool rz_tail = want_rz && Lt == 0;
-        switch (n[Lt]) {
+        if (v64) v64_launch(rz_tail);
+        else switch (n[Lt]) {
             case 64: tail_launch<64, 512>(rz_tail); break;
             case 32: tail_launch<32, 256>(rz_tail); break;
             case 16: tail_launch<16, 128>(rz_tail); break;

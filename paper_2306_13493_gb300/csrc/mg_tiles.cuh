@@ -135,8 +135,8 @@ __device__ __forceinline__ unsigned tile_load(TileBlock<T> &t, const T *bs, cons
 
 // West/south edge conductances from the neighbouring lane / warp (xrow: one
 // shared row per warp), then 1/diag (0 where not an unknown).  Contains a
-// barrier.
-template <typename T>
+// barrier.  NW: warps of the block.
+template <typename T, int NW = MG_NW>
 __device__ __forceinline__ void tile_diag(TileBlock<T> &t, T *xrow, int lane, int warp,
                                           unsigned unk) {
 #pragma unroll
@@ -160,11 +160,11 @@ __device__ __forceinline__ void tile_diag(TileBlock<T> &t, T *xrow, int lane, in
 }
 
 // Publishes rows 0 and 3 of z in buffer buf, waits, and reads the rows below
-// and above the strip (zero beyond the window).
-template <typename T>
+// and above the strip (zero beyond the window).  NW: warps of the block.
+template <typename T, int NW = MG_NW>
 __device__ __forceinline__ void tile_exchange(TileBlock<T> &t, T *xz, int buf, int lane,
                                               int warp) {
-    T *lo = xz + (buf * 2 + 0) * MG_NW * MG_SW, *hi = xz + (buf * 2 + 1) * MG_NW * MG_SW;
+    T *lo = xz + (buf * 2 + 0) * NW * MG_SW, *hi = xz + (buf * 2 + 1) * NW * MG_SW;
     lo[warp * MG_SW + 2 * lane] = t.z[0];
     lo[warp * MG_SW + 2 * lane + 1] = t.z[1];
     hi[warp * MG_SW + 2 * lane] = t.z[6];
@@ -173,15 +173,16 @@ __device__ __forceinline__ void tile_exchange(TileBlock<T> &t, T *xz, int buf, i
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         t.zs[c] = warp > 0 ? hi[(warp - 1) * MG_SW + 2 * lane + c] : T(0);
-        t.zn[c] = warp < MG_NW - 1 ? lo[(warp + 1) * MG_SW + 2 * lane + c] : T(0);
+        t.zn[c] = warp < NW - 1 ? lo[(warp + 1) * MG_SW + 2 * lane + c] : T(0);
     }
 }
 
 // Neighbours of element (c, r) in the order west, east, south, north: their z
 // and the conductances of the four edges.  The horizontal neighbour in the
 // next lane comes by shuffle, so every lane of the warp must call this for
-// the same (c, r).
-template <typename T, int C, int R>
+// the same (c, r).  EAST0: the window's last column is the grid's last
+// unknown column, whose east neighbour (the Dirichlet column) has z = 0.
+template <typename T, int C, int R, bool EAST0 = false>
 __device__ __forceinline__ void tile_nbrs(const TileBlock<T> &t, T *zw, T *ze, T *zsv, T *znv,
                                           T *cw, T *cs) {
     if constexpr (C == 0) {
@@ -191,6 +192,9 @@ __device__ __forceinline__ void tile_nbrs(const TileBlock<T> &t, T *zw, T *ze, T
     } else {
         *zw = t.z[2 * R];
         *ze = __shfl_down_sync(MG_FULL, t.z[2 * R], 1);
+        if constexpr (EAST0) {
+            if ((threadIdx.x & 31) == 31) *ze = T(0);
+        }
         *cw = t.cxe[2 * R];
     }
     *zsv = R == 0 ? t.zs[C] : t.z[2 * (R - 1) + C];
@@ -199,23 +203,23 @@ __device__ __forceinline__ void tile_nbrs(const TileBlock<T> &t, T *zw, T *ze, T
 }
 
 // One Gauss-Seidel half-sweep over the elements of colour COL of the block.
-template <typename T, int COL, int R = 0>
+template <typename T, int COL, int R = 0, bool EAST0 = false>
 __device__ __forceinline__ void tile_half_sweep(TileBlock<T> &t) {
     if constexpr (R < 4) {
         constexpr int C = (COL + R) & 1, e = 2 * R + C;
         T zw, ze, zsv, znv, cw, cs;
-        tile_nbrs<T, C, R>(t, &zw, &ze, &zsv, &znv, &cw, &cs);
+        tile_nbrs<T, C, R, EAST0>(t, &zw, &ze, &zsv, &znv, &cw, &cs);
         t.z[e] = (t.b[e] + cw * zw + t.cxe[e] * ze + cs * zsv + t.cyn[e] * znv) * t.inv[e];
-        tile_half_sweep<T, COL, R + 1>(t);
+        tile_half_sweep<T, COL, R + 1, EAST0>(t);
     }
 }
 
 // Residual b - A z at the red element of row R (c = R % 2); 0 where not an unknown.
-template <typename T, int R>
+template <typename T, int R, bool EAST0 = false>
 __device__ __forceinline__ T tile_red_residual(const TileBlock<T> &t, unsigned unk) {
     constexpr int C = R & 1, e = 2 * R + C;
     T zw, ze, zsv, znv, cw, cs;
-    tile_nbrs<T, C, R>(t, &zw, &ze, &zsv, &znv, &cw, &cs);
+    tile_nbrs<T, C, R, EAST0>(t, &zw, &ze, &zsv, &znv, &cw, &cs);
     const T zc = t.z[e];
     const T rv = t.b[e] - (cw * (zc - zw) + t.cxe[e] * (zc - ze) + cs * (zc - zsv) +
                            t.cyn[e] * (zc - znv));
