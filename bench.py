@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=12.0,
                     help="open-loop window of the served-requests measurement (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-slice-vertices", type=int, default=0,
+                    help="server slice size in fine vertices (0: 2^24, <0: no slicing)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default FFT launch shapes (no tuning before the timed steps)")
     ap.add_argument("--no-mixed", action="store_true",
@@ -868,10 +870,14 @@ def time_to_rmse_study(sce, stream, prec, eps=1e-3, n_max=2048):
     h0 = 1/4, 1/8, 1/16, and plain MLMC from its own coarsest mesh,
     Eq. (3.8): the largest h0 = 2^-k <= sqrt(8 nu) lambda = 0.04, i.e. 1/32.
     Each runs mlmc.run_adaptive: levels added (pilot 100 on the first three,
-    20 on each added one) until the Richardson bias (alpha fitted on the three
+    50 on each added one) until the Richardson bias (alpha fitted on the three
     finest levels, at most 2; the three-level form of the test) is at most
-    eps/sqrt(2), up to the 2048^2 grid; there, with the bias below eps, the
-    variance target becomes eps^2 - bias^2 (fill_variance).  Cost = GPU seconds of every level
+    eps/sqrt(2) -- and at least until the finest mesh is 4 x finer than the
+    plain-MLMC mesh of Eq. (3.8), so that the levels of the bias test are all
+    in the range where plain MLMC may start (below it E[Y_l] can be small by
+    accident and end the loop early) -- up to the 2048^2 grid; there, with
+    the bias below eps, the variance target becomes eps^2 - bias^2
+    (fill_variance).  Cost = GPU seconds of every level
     estimate (CUDA events), the samples of levels rebuilt when they stopped
     being the finest included; embedding set-up is not counted (reported
     apart as wall time).  cost_vs_eps predicts each variant's cost for other
@@ -906,15 +912,17 @@ def time_to_rmse_study(sce, stream, prec, eps=1e-3, n_max=2048):
                                   stream=stream)
 
         t0 = time.perf_counter()
+        # the three finest levels of the bias test at or below the plain-MLMC mesh
+        L_min = min(L_max, max(0, int(round(_m.log2(4 * plain_n0 / n0)))))
         res = gm.run_adaptive(make_runner, eps, L0=min(2, L_max), L_max=L_max, pilot=100,
-                              pilot_new=20, alpha_levels=3, alpha_max=2.0, bias_levels=3,
-                              fill_variance=True, restart_previous_finest=smooth)
+                              pilot_new=50, alpha_levels=3, alpha_max=2.0, bias_levels=3,
+                              fill_variance=True, restart_previous_finest=smooth, L_min=L_min)
         wall = time.perf_counter() - t0
         for e in created:
             e.close()
         key = "%s_h0_1/%d" % (name, n0)
         out[key] = {
-            "h0": 1.0 / n0, "levels_n": [x.n for x in res.levels],
+            "h0": 1.0 / n0, "levels_n": [x.n for x in res.levels], "L_min": L_min,
             "gpu_seconds": round(res.seconds, 4), "wall_seconds": round(wall, 2),
             "estimate": res.estimate, "stat_error": res.stat_error, "bias_est": res.bias,
             "rmse_est": res.rmse, "rmse_met": bool(res.rmse <= eps),
@@ -927,7 +935,7 @@ def time_to_rmse_study(sce, stream, prec, eps=1e-3, n_max=2048):
                              "mc_s": round(c["mc_seconds"], 5)}
                             for c in gm.cost_versus_eps(res.levels, eps_list, choose_levels=True,
                                                         alpha_levels=3, alpha_max=2.0,
-                                                        bias_levels=3)]}
+                                                        bias_levels=3, L_min=L_min)]}
     ces = [v["gpu_seconds"] for k, v in out.items() if k.startswith("mlmc_ces")]
     pl = out["mlmc_plain_h0_1/%d" % plain_n0]["gpu_seconds"]
     out["cost_ratio_plain_over_best_ces"] = round(pl / min(ces), 3) if ces else None
@@ -980,38 +988,72 @@ def mixed_launch_bench(args, sce, stream):
         tasks.append({"emb": e, "level": 2 + l, "count": c,
                       "Y": torch.empty(c, dtype=torch.float64, device=dev)})
 
-    def launch(i):
+    persistent_ok = args.precision == 32
+
+    def launch(i, persistent=False):
         for t in tasks:
             t["first_sample"] = i * t["count"]
         outs, _, st = sce.mlmc_estimate_levels(tasks, mw.seed, qoi_index=mw.qoi, f=mw.f,
                                                rtol=mw.rtol, maxit=2000, precision=args.precision,
                                                max_concurrency=args.concurrency,
-                                               stream=stream.cuda_stream, allow_not_converged=True)
+                                               stream=stream.cuda_stream, allow_not_converged=True,
+                                               persistent=persistent)
         return outs
 
-    for w in range(2):
-        launch(1000 + w)
-    reps, tot = 3, 0.0
-    iters = []
-    for i in range(reps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        outs = launch(i)
-        e1.record(stream)
-        e1.synchronize()
-        tot += e0.elapsed_time(e1)
-        iters = [o.total_iters / (2 * o.N) for o in outs]
+    def timed(fn, reps=3):
+        fn(1000)
+        fn(1001)
+        tot, last = 0.0, None
+        for i in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = fn(i)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps, last
+
+    ms, outs = timed(launch)
+    iters = [o.total_iters / (2 * o.N) for o in outs]
+    nsamp = sum(c for _, c in mw.buckets)
+    out = {"workload": mw.describe(), "P": [2 * n for n, _ in mw.buckets],
+           "samples_per_launch": nsamp, "ms_per_launch": round(ms, 2),
+           "samples_per_s": round(nsamp / (ms / 1e3), 1),
+           "mean_iters_per_solve": [round(x, 2) for x in iters],
+           "levels_in_flight": args.concurrency,
+           "tile_heights": "as tuned before the timed steps"}
+    if persistent_ok:
+        pms, _ = timed(lambda i: launch(i, persistent=True))
+        # the fields alone: one persistent launch for every bucket against one
+        # ce_sample_batch call per bucket on the same stream
+        ks = [(torch.empty(c, n + 1, n + 1, dtype=torch.float32, device=dev),
+               torch.empty(c, n // 2 + 1, n // 2 + 1, dtype=torch.float32, device=dev))
+              for n, c in mw.buckets]
+        ftasks = [{"emb": t["emb"], "level": t["level"], "first_sample": 0, "count": t["count"],
+                   "k_fine": kf, "k_coarse": kc} for t, (kf, kc) in zip(tasks, ks)]
+
+        def fields_one(i):
+            sce.ce_sample_levels(ftasks, mw.seed, stream=stream.cuda_stream)
+
+        def fields_each(i):
+            for ft in ftasks:
+                sce.ce_sample_batch(ft["emb"], mw.seed, ft["level"], 0, ft["count"], 32,
+                                    ft["k_fine"], ft["k_coarse"], stream=stream.cuda_stream)
+
+        f1, _ = timed(fields_one)
+        fe, _ = timed(fields_each)
+        out["persistent"] = {
+            "ms_per_launch": round(pms, 2), "samples_per_s": round(nsamp / (pms / 1e3), 1),
+            "note": "every bucket's fields in one persistent launch (ce_sample_levels: device "
+                    "work queue over all row and column blocks, bounded per-sample waits), "
+                    "then the solves as in the streams path; bit-identical results",
+            "fields_one_launch_ms": round(f1, 3), "fields_per_bucket_calls_ms": round(fe, 3)}
+        del ks
     for e in embs:
         e.close()
-    ms = tot / reps
-    nsamp = sum(c for _, c in mw.buckets)
-    return {"workload": mw.describe(), "P": [2 * n for n, _ in mw.buckets],
-            "samples_per_launch": nsamp, "ms_per_launch": round(ms, 2),
-            "samples_per_s": round(nsamp / (ms / 1e3), 1),
-            "mean_iters_per_solve": [round(x, 2) for x in iters],
-            "levels_in_flight": args.concurrency}
+    return out
 
 
 def serving_bench(args, sce):
@@ -1041,6 +1083,7 @@ def serving_bench(args, sce):
                            list(sw.sigma2_range)),
            "slots": args.serve_slots}
     with sce.Server(slots=args.serve_slots, max_embeddings=256, precision=args.precision,
+                    slice_vertices=args.serve_slice_vertices,
                     rtol=1e-10, maxit=2000) as srv:
         # 1. every (tenant, level) embedding becomes resident
         t0 = time.perf_counter()
@@ -1104,6 +1147,19 @@ def serving_bench(args, sce):
     lat = np.array([r.t_done - r.t_submit for r in res]) * 1e3
     span = max(r.t_done for r in res) - min(r.t_submit for r in res)
     samples = sum(r.sums.N for r in res)
+    # latency per size class: work = count x (n+1)^2 fine vertices
+    work = np.array([q["count"] * (q["n"] + 1) ** 2 for q in reqs], dtype=np.float64)
+    classes = {}
+    for name, lo, hi in (("small", 0, 2 ** 20), ("medium", 2 ** 20, 2 ** 26),
+                         ("large", 2 ** 26, np.inf)):
+        sel = (work >= lo) & (work < hi)
+        if sel.any():
+            cl = lat[sel]
+            classes[name] = {"work_vertices": [lo, hi if np.isfinite(hi) else None],
+                             "requests": int(sel.sum()),
+                             "p50_ms": round(float(np.percentile(cl, 50)), 2),
+                             "p99_ms": round(float(np.percentile(cl, 99)), 2),
+                             "max_ms": round(float(cl.max()), 2)}
     out.update({
         "requests": n_req, "p50_ms": round(float(np.percentile(lat, 50)), 2),
         "p99_ms": round(float(np.percentile(lat, 99)), 2),
@@ -1116,6 +1172,8 @@ def serving_bench(args, sce):
         "peak_reserved_gb": round(st1["peak_reserved"] / 2 ** 30, 2),
         "budget_gb": round(st1["budget"] / 2 ** 30, 2),
         "mlmc_client": mres,
+        "by_size": classes,
+        "slice_vertices": args.serve_slice_vertices or 2 ** 24,
     })
     return out
 
@@ -1195,8 +1253,16 @@ def run_ours(args):
         shapes = {}
         for (l, n, N) in wl.levels:
             shapes[str(embs[l].P)] = sce.ce_autotune_fft(embs[l], prec, count=min(N, 64), reps=3)
+        # multigrid window heights of the tiled levels (n <= 64 runs fused), smallest
+        # first; 1024 is a level of the mixed-level launch
+        tiles = {}
+        for nn in (128, 256, 512, 1024):
+            cnt = max(4, min(256, (1 << 24) // ((nn + 1) * (nn + 1))))
+            tiles[str(nn)] = sce.darcy_autotune_tiles(nn, prec, count=cnt, reps=2,
+                                                      stream=stream.cuda_stream)
         autotune = {"fft_shapes_by_P": {P: {"row_tpf_F": v["row"], "col_tpf_F": v["col"]}
                                         for P, v in shapes.items()},
+                    "tile_height_by_n": tiles,
                     "seconds": round(time.perf_counter() - t0, 2)}
     Ybuf = [torch.empty(N, dtype=torch.float64, device=dev) for (_, _, N) in wl.levels]
     Yhost = [torch.empty(N, dtype=torch.float64, pin_memory=True) for (_, _, N) in wl.levels]

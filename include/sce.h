@@ -166,6 +166,47 @@ int ce_sample_batch_noalloc(ce_embedding_t e, uint64_t seed, uint32_t level,
                             uint64_t first_sample, int count, int precision, void *k_fine,
                             void *k_coarse, void *stream);
 
+/*
+ * ce_sample_levels -- the fields of several MLMC levels (Algorithm 1/2 step
+ * 4(a)-(f), FP32) in one persistent kernel launch: the batching pattern for a
+ * step that mixes levels of different grid sizes.  Each task is one
+ * ce_sample_batch call (same handle, level, samples and outputs; a distinct
+ * coarse mask gives the coarse field its own column pass), and its fields are
+ * bit-identical to that call's.
+ *   The launch's blocks take work items from a queue in device memory (one
+ *   atomic counter): first every row-pass block of every task, then every
+ *   column-pass block.  A column block of a sample waits until all row blocks
+ *   of that sample are done (a per-sample counter); the wait is bounded by
+ *   opts->wait_cycles SM clock cycles (default 2^31, about a second), after
+ *   which the launch stops taking items and the call returns CE_ERR_TIMEOUT.
+ *   A waiting block only depends on items handed out before its own, whose
+ *   blocks never wait, so the launch needs no co-residency to finish.
+ *   tasks : host array of ntasks (1..16) tasks; k_fine must not be NULL
+ *   opts  : may be NULL.  opts->starve_task >= 0 makes that task's column
+ *           blocks wait for one row block more than exist (a wait that runs
+ *           out, for testing the timeout path); -1 = none.
+ * Allocates the row/column intermediates of all tasks at once (stream
+ * ordered) and synchronises `stream` to read the timeout flag.  Errors:
+ * CE_ERR_INVALID_ARG, CE_ERR_OOM, CE_ERR_CUDA, CE_ERR_TIMEOUT.  Not a step of
+ * the paper's method beyond the fields it computes.
+ */
+typedef struct {
+    ce_embedding_t emb;
+    uint32_t level;
+    uint64_t first_sample;
+    int count;
+    void *k_fine;     /* device float, count*(n+1)^2 */
+    void *k_coarse;   /* device float, count*(n/2+1)^2, or NULL */
+} ce_field_task;
+
+typedef struct {
+    long long wait_cycles;   /* bound of a column block's wait; <= 0: default */
+    int starve_task;         /* -1, or a task whose waits must run out (tests) */
+} ce_levels_opts;
+
+int ce_sample_levels(const ce_field_task *tasks, int ntasks, uint64_t seed,
+                     const ce_levels_opts *opts, void *stream);
+
 /* Darcy problem of §3.1, Eq. (3.1), on the n-cell grid:
  *   -div(k grad u) = f, u = 1 at x1 = 0, u = 0 at x1 = 1, zero flux at x2 = 0, 1;
  * P1 elements with nodal quadrature (§3.2; each cell split by the diagonal
@@ -259,6 +300,20 @@ int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
                          mlmc_level_task *tasks, int ntasks, int max_concurrency, void *stream);
 
 /*
+ * mlmc_estimate_levels_persistent -- mlmc_estimate_levels with the fields of
+ * every level generated first, in one persistent kernel launch on `stream`
+ * (ce_sample_levels: a device work queue over all levels' row and column
+ * blocks); then each level's solves, Y and sums as mlmc_estimate_levels runs
+ * them.  Results are bit-identical to mlmc_estimate_levels.  FP32 path only
+ * (p->precision == 32), 1..16 tasks, embeddings with P <= 4096.  Allocates
+ * every level's fields at once (stream ordered).  Errors as
+ * mlmc_estimate_levels, plus CE_ERR_TIMEOUT from the field launch.
+ */
+int mlmc_estimate_levels_persistent(const darcy_problem *p, uint64_t seed, int qoi_index,
+                                    mlmc_level_task *tasks, int ntasks, int max_concurrency,
+                                    void *stream);
+
+/*
  * Request server -- MLMC level estimates (mlmc_level_estimate) served to
  * requests that arrive over time, with different grids and covariances, by
  * continuous batching.  `slots` host worker threads, each with its own
@@ -269,8 +324,16 @@ int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
  * after 8 overtakes of a blocked head only the head is admitted.  Admitted
  * requests run concurrently.  Embedding set-ups are cached by (covariance,
  * n, padding, smoothing rule) and stay resident; unused ones are evicted
- * least-recently-used beyond max_embeddings.  A request's results are
- * bit-identical to mlmc_level_estimate on its own.
+ * least-recently-used beyond max_embeddings.  A large request (above
+ * slice_vertices) is cut into consecutive sample slices: at most `slots` of
+ * its slices are queued or running at a time, and each finished slice puts
+ * the next one at the back of the queue, so requests that arrive meanwhile
+ * are served between them.  The slices' level sums are added in slice order, so
+ * a request's results do not depend on the other requests in the server:
+ * they are bit-identical alone and in any mix (and, unsliced, bit-identical
+ * to mlmc_level_estimate on its own).  Multigrid hierarchies are built per
+ * sample from its own coefficient field inside each solve and cannot be
+ * kept; what stays resident between requests are the embeddings.
  * The paper has no counterpart: this is how the level estimates of §3.4 are
  * served, not a step of the method.
  */
@@ -284,6 +347,10 @@ typedef struct {
     int precision;          /* 32 (FP32 field and MG, FP64 refinement) or 64    */
     double rtol;            /* FP64 residual tolerance of every solve           */
     int maxit;              /* CG iteration bound per solve                     */
+    long long slice_vertices; /* a request of more than this many fine-grid
+                               vertices of work (count * (n+1)^2) runs as
+                               slices of samples that each stay within it; 0:
+                               2^24; < 0: never sliced                         */
 } sce_server_config;
 
 typedef struct {
@@ -328,6 +395,13 @@ int sce_server_stats(sce_server_t s, sce_server_stats_t *out);
 /* Finishes every queued request, stops the workers, releases the cache. */
 void sce_server_destroy(sce_server_t s);
 
+/* Test hook (host side; not a step of the method): the next `count`
+ * stream-ordered allocations of the library, in any thread, fail with
+ * CE_ERR_OOM before reaching the CUDA allocator, to exercise the error paths
+ * of the callers (the server's admission and recovery among them) without
+ * exhausting device memory.  count <= 0 clears it. */
+void sce_test_fail_allocs(int count);
+
 /*
  * Quasi-Monte Carlo sampler (multilevel quasi-Monte Carlo, the outlook of
  * §5): the normals of Algorithm 1 step 4(a) replaced by a randomly shifted
@@ -364,6 +438,27 @@ int mlmc_level_estimate_qmc(ce_qmc_t q, const darcy_problem *p, uint64_t seed, u
                             uint32_t shift, uint32_t first_point, int count, int qoi_index,
                             mlmc_level_sums *out, double *Y, double *qoi_f, double *qoi_c,
                             void *stream);
+
+/*
+ * darcy_autotune_tiles -- picks the window height (16, 24, 32 or 48 rows; the
+ * width is 64 columns) of the tiled multigrid kernels for grids of n cells
+ * (n >= 128, a power of two) in `precision` by timing `reps` solves of
+ * `count` samples of a smooth synthetic coefficient for every height (CUDA
+ * events on `stream`, after one warm-up solve each).  The choice holds for
+ * every later solve of the process in that precision whose hierarchy has an
+ * n-cell level.  Tune the sizes in increasing order (a solve on n also runs
+ * the levels below it).  Every height computes each vertex of a V-cycle
+ * identically; the per-tile partial sums of r . z are added in an order that
+ * follows the tiling, so solutions agree to rounding across heights (and
+ * each height is deterministic).  Do not run other solves on
+ * the device meanwhile (they would use the heights under trial).  The
+ * environment variable SCE_TILE_SH, if set to one of the heights, overrides
+ * every choice.  Not a step of the paper's method.
+ *   height : host, may be NULL; receives the chosen height.
+ * Errors: CE_ERR_INVALID_ARG (n not a power of two in [128, 4096], count not
+ * in [1, 65535], reps < 1), CE_ERR_OOM, CE_ERR_CUDA.
+ */
+int darcy_autotune_tiles(int n, int precision, int count, int reps, void *stream, int *height);
 
 /*
  * ce_autotune_fft -- picks the launch shapes (threads per FFT line, lines per

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <utility>
 
@@ -26,9 +27,21 @@ void sce_set_last_error_text(const char *text) {
 static std::mutex g_pool_mu;
 static bool g_pool_configured[64];
 
+// Test hook: the next g_fail_allocs stream-ordered allocations fail with
+// CE_ERR_OOM before reaching the allocator (sce_test_fail_allocs).
+static std::atomic<int> g_fail_allocs{0};
+
+extern "C" void sce_test_fail_allocs(int count) { g_fail_allocs.store(count > 0 ? count : 0); }
+
 int sce_alloc(void **p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) return CE_OK;
+    for (int left = g_fail_allocs.load(); left > 0;) {
+        if (g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+            sce_set_last_error_text("allocation refused by sce_test_fail_allocs");
+            return CE_ERR_OOM;
+        }
+    }
     int dev = 0;
     SCE_CUDA(cudaGetDevice(&dev));
     {

@@ -31,7 +31,11 @@
 // ||u_h||_L2^2 = sum_T |T|/12 [(u_a+u_b+u_c)^2 + u_a^2 + u_b^2 + u_c^2].
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "ff.cuh"
@@ -48,6 +52,26 @@ constexpr int MAXLEV = 14;
 #define SCE_TAIL_N 32
 #endif
 constexpr int TAIL_N = SCE_TAIL_N;   // levels with n <= TAIL_N run in one block per sample
+
+// Window heights of the tiled multigrid kernels, per (precision, grid size),
+// chosen by darcy_autotune_tiles; MG_SH where absent (SCE_TILE_SH forces one
+// for every level).  Every height computes each vertex of a V-cycle
+// identically; the per-tile r . z partial sums follow the tiling, so results
+// agree to rounding across heights.
+constexpr int kTileHeights[] = {16, 24, 32, 48};
+std::mutex g_tile_mu;
+std::map<std::pair<int, int>, int> g_tile_sh;   // (sizeof T, n) -> window height
+
+int tile_height_for(int tsize, int n) {
+    if (const char *e = getenv("SCE_TILE_SH")) {
+        const int v = atoi(e);
+        for (int h : kTileHeights)
+            if (h == v) return v;
+    }
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tile_sh.find({tsize, n});
+    return it == g_tile_sh.end() ? MG_SH : it->second;
+}
 
 struct Launch {
     int tpb, vpt, epb, nblk;
@@ -726,9 +750,8 @@ struct Solver {
     // ---- fused cycle: tiled down/up kernels above the tail, one block per
     // sample for the levels n <= TAIL_N
     bool fused = true;
-    bool tile_attr_set = false;
     int Lt = 0;                 // first level of the tail
-    int tiles_x[MAXLEV], tiles_n[MAXLEV];
+    int tiles_x[MAXLEV], tiles_n[MAXLEV], sh[MAXLEV];
 
     // FP32: an n = 64 level and everything below it run as one fused kernel
     // per sample (mg_v64_kernel; SCE_V64=0 keeps the tiled kernels for it)
@@ -745,9 +768,35 @@ struct Solver {
         v64 = sizeof(T) == 4 && tail_n == V64_N && n[Lt] == V64_N;
         for (int L = 0; L < Lt; ++L) {
             const int nc1 = n[L] / 2 + 1;
+            sh[L] = tile_height_for((int)sizeof(T), n[L]);
+            const int ch = (sh[L] - 6) / 2;
             tiles_x[L] = (nc1 + MG_CW - 1) / MG_CW;
-            tiles_n[L] = tiles_x[L] * ((nc1 + MG_CH - 1) / MG_CH);
+            tiles_n[L] = tiles_x[L] * ((nc1 + ch - 1) / ch);
         }
+    }
+
+    // launches of the tiled kernels of window height SH
+    unsigned tile_attr_mask = 0;
+    template <int SH>
+    void tile_down(int L) {
+        constexpr size_t smem = mg_tile_smem_bytes<T, SH>();
+        constexpr unsigned bit = 1u << (SH / 8);
+        if (!(tile_attr_mask & bit)) {   // outside any capture (the first cycle is not captured)
+            sce_raise_smem_limit((const void *)mg_down_kernel<T, SH>, smem);
+            sce_raise_smem_limit((const void *)mg_up_kernel<T, SH>, smem);
+            tile_attr_mask |= bit;
+        }
+        SceProf pr(KP_MG_DOWN, st, vb(L, 4.0) + vb(L + 1, 1.0));
+        mg_down_kernel<T, SH><<<dim3(tiles_n[L], count), MGTile<SH>::THREADS, smem, st>>>(
+            cx[L], cy[L], b[L], zpre[L], n[L], b[L + 1], tiles_x[L], sc.act_in);
+    }
+    template <int SH>
+    void tile_up(int L, bool want_rz) {
+        constexpr size_t smem = mg_tile_smem_bytes<T, SH>();
+        SceProf pr(KP_MG_UP, st, vb(L, 5.0) + vb(L + 1, 1.0));
+        mg_up_kernel<T, SH><<<dim3(tiles_n[L], count), MGTile<SH>::THREADS, smem, st>>>(
+            cx[L], cy[L], b[L], zpre[L], z[L], n[L], z[L + 1], tiles_x[L], sc.act_in,
+            (want_rz && L == 0) ? part : nullptr, tiles_n[0]);
     }
 
     // partial-sum slots per sample written by vcycle_fused(want_rz = true)
@@ -796,16 +845,13 @@ struct Solver {
 
     // z[0] = M^{-1} b[0]; with want_rz the partial sums of b[0] . z[0] go to part
     void vcycle_fused(bool want_rz) {
-        constexpr size_t smem = mg_tile_smem_bytes<T>();
-        if (!tile_attr_set) {
-            sce_raise_smem_limit((const void *)mg_down_kernel<T>, smem);
-            sce_raise_smem_limit((const void *)mg_up_kernel<T>, smem);
-            tile_attr_set = true;
-        }
         for (int L = 0; L < Lt; ++L) {
-            SceProf pr(KP_MG_DOWN, st, vb(L, 4.0) + vb(L + 1, 1.0));
-            mg_down_kernel<T><<<dim3(tiles_n[L], count), MG_THREADS, smem, st>>>(
-                cx[L], cy[L], b[L], zpre[L], n[L], b[L + 1], tiles_x[L], sc.act_in);
+            switch (sh[L]) {
+                case 16: tile_down<16>(L); break;
+                case 24: tile_down<24>(L); break;
+                case 48: tile_down<48>(L); break;
+                default: tile_down<32>(L); break;
+            }
         }
         const bool rz_tail = want_rz && Lt == 0;
         if (v64) v64_launch(rz_tail);
@@ -817,10 +863,12 @@ struct Solver {
             default: tail_launch<4, 32>(rz_tail); break;
         }
         for (int L = Lt - 1; L >= 0; --L) {
-            SceProf pr(KP_MG_UP, st, vb(L, 5.0) + vb(L + 1, 1.0));
-            mg_up_kernel<T><<<dim3(tiles_n[L], count), MG_THREADS, smem, st>>>(
-                cx[L], cy[L], b[L], zpre[L], z[L], n[L], z[L + 1], tiles_x[L], sc.act_in,
-                (want_rz && L == 0) ? part : nullptr, tiles_n[0]);
+            switch (sh[L]) {
+                case 16: tile_up<16>(L, want_rz); break;
+                case 24: tile_up<24>(L, want_rz); break;
+                case 48: tile_up<48>(L, want_rz); break;
+                default: tile_up<32>(L, want_rz); break;
+            }
         }
     }
 
@@ -1183,3 +1231,92 @@ extern "C" int darcy_solve_batch(const darcy_problem *p, const void *k, int coun
     return sce_darcy_solve_impl(p, k, count, qoi, iters, status, u_out, as_stream(stream), nullptr,
                                 nullptr, 7);
 }
+
+// ---------------------------------------------------------------- tile tuner
+namespace {
+// A smooth synthetic coefficient for timing: k = exp(0.8 sin(6 pi x) cos(4 pi y)
+// + 0.1 (s mod 7)), per sample s; the timings compare window heights at equal
+// iteration counts (every height computes the same iterates up to rounding).
+template <typename T>
+__global__ void tuner_field_kernel(T *k, int n, int count) {
+    const long long V = (long long)(n + 1) * (n + 1);
+    const long long tot = V * count;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(q / V);
+        const int v = (int)(q - (long long)s * V);
+        const int j = v / (n + 1), i = v - j * (n + 1);
+        const double x = (double)i / n, y = (double)j / n;
+        k[q] = (T)exp(0.8 * sin(6.0 * M_PI * x) * cos(4.0 * M_PI * y) + 0.1 * (s % 7));
+    }
+}
+}  // namespace
+
+extern "C" int darcy_autotune_tiles(int n, int precision, int count, int reps, void *stream,
+                                    int *height) {
+    if (n < 128 || n > 4096 || !is_pow2(n) || (precision != 32 && precision != 64) ||
+        count <= 0 || count > 65535 || reps <= 0)
+        return CE_ERR_INVALID_ARG;
+    const cudaStream_t st = as_stream(stream);
+    const int tsize = precision == 64 ? 8 : 4;
+    const long long V = (long long)(n + 1) * (n + 1);
+    void *k = nullptr;
+    double *qoi = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    auto release = [&]() {
+        if (k) sce_free(k, st);
+        if (qoi) sce_free(qoi, st);
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    };
+    int rc = sce_alloc(&k, (size_t)count * V * tsize, st);
+    if (rc == CE_OK) rc = sce_alloc((void **)&qoi, (size_t)count * 3 * sizeof(double), st);
+    if (rc != CE_OK) {
+        release();
+        return rc;
+    }
+    if (precision == 64) tuner_field_kernel<double><<<1024, 256, 0, st>>>((double *)k, n, count);
+    else tuner_field_kernel<float><<<1024, 256, 0, st>>>((float *)k, n, count);
+    if (cudaGetLastError() != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
+        cudaEventCreate(&b) != cudaSuccess) {
+        release();
+        return CE_ERR_CUDA;
+    }
+    const darcy_problem p{n, 1.0, 1e-8, 1000, precision};
+    int best = MG_SH;
+    float best_ms = 0.0f;
+    for (int h : kTileHeights) {
+        {
+            std::lock_guard<std::mutex> lk(g_tile_mu);
+            g_tile_sh[{tsize, n}] = h;
+        }
+        float ms_min = 0.0f;
+        for (int r = 0; r <= reps; ++r) {   // the first call warms up
+            if (cudaEventRecord(a, st) != cudaSuccess) rc = CE_ERR_CUDA;
+            if (rc == CE_OK)
+                rc = sce_darcy_solve_impl(&p, k, count, qoi, nullptr, nullptr, nullptr, st, nullptr,
+                                          nullptr, 7);
+            if (rc == CE_ERR_NOT_CONVERGED) rc = CE_OK;
+            float ms = 0.0f;
+            if (rc == CE_OK && (cudaEventRecord(b, st) != cudaSuccess ||
+                                cudaEventSynchronize(b) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+                rc = CE_ERR_CUDA;
+            if (rc != CE_OK) break;
+            if (r > 0 && (r == 1 || ms < ms_min)) ms_min = ms;
+        }
+        if (rc != CE_OK) break;
+        if (h == kTileHeights[0] || ms_min < best_ms) {
+            best_ms = ms_min;
+            best = h;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        g_tile_sh[{tsize, n}] = rc == CE_OK ? best : MG_SH;
+    }
+    release();
+    if (rc == CE_OK && height) *height = best;
+    return rc;
+}
+

@@ -414,20 +414,21 @@ __device__ __forceinline__ void row_normals4(uint64_t seed, uint32_t level, uint
     }
 }
 
-template <typename R, int MAXB, bool QMC = false>
-__global__ void __launch_bounds__(256, 4) ce_row_kernel(
+// The row-pass work of block (bx, sample slot sl) of a launch with F * tpf
+// threads; every thread of the block calls it (it synchronises the block).
+template <typename R, int MAXB, bool QMC>
+__device__ __forceinline__ void ce_row_block(
     const R *__restrict__ sq_f, const R *__restrict__ sq_c, const typename C2<R>::T *__restrict__ tw,
     int P, int logP, int m, uint64_t seed, uint32_t level, uint64_t first_sample, int F, int tpf,
-    typename C2<R>::T *__restrict__ Yf, typename C2<R>::T *__restrict__ Yc, QmcArgs qa) {
+    typename C2<R>::T *__restrict__ Yf, typename C2<R>::T *__restrict__ Yc, const QmcArgs &qa,
+    int bx, int sl, unsigned char *smem_raw) {
     using R2 = typename C2<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R2 *sm = reinterpret_cast<R2 *>(smem_raw);
-    const int sl = blockIdx.y;
     const uint64_t sample = first_sample + (uint64_t)sl;
     const int f = threadIdx.x / tpf, t = threadIdx.x - f * tpf;
     const bool masked = sq_c != nullptr;
     const int units = masked ? P : P / 2;
-    const int u0 = blockIdx.x * F;
+    const int u0 = bx * F;
     const int unit = u0 + f;
     const int LP = fft_line_pitch(P);
     R2 *buf = sm + (size_t)f * LP;
@@ -498,6 +499,16 @@ __global__ void __launch_bounds__(256, 4) ce_row_kernel(
     }
 }
 
+template <typename R, int MAXB, bool QMC = false>
+__global__ void __launch_bounds__(256, 4) ce_row_kernel(
+    const R *__restrict__ sq_f, const R *__restrict__ sq_c, const typename C2<R>::T *__restrict__ tw,
+    int P, int logP, int m, uint64_t seed, uint32_t level, uint64_t first_sample, int F, int tpf,
+    typename C2<R>::T *__restrict__ Yf, typename C2<R>::T *__restrict__ Yc, QmcArgs qa) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ce_row_block<R, MAXB, QMC>(sq_f, sq_c, tw, P, logP, m, seed, level, first_sample, F, tpf, Yf,
+                               Yc, qa, blockIdx.x, blockIdx.y, smem_raw);
+}
+
 template <typename R> __device__ __forceinline__ R exp_r(R x);
 template <> __device__ __forceinline__ float exp_r<float>(float x) { return expf(x); }
 template <> __device__ __forceinline__ double exp_r<double>(double x) { return exp(x); }
@@ -506,17 +517,17 @@ template <> __device__ __forceinline__ double exp_r<double>(double x) { return e
 // coarse == 0: lines x = 0..m of Y (fine field), outputs y = 0..m -> kf, and
 //              (kc_plain != nullptr) kc_plain at even (x, y).
 // coarse == 1: lines xc = 0..m/2 of Y (coarse-masked), outputs y = 2 yc -> kout.
+// The column-pass work of block (bx, sample slot sl) of a launch with F * tpf
+// threads; every thread of the block calls it (it synchronises the block).
 template <typename R, int MAXB>
-__global__ void __launch_bounds__(256, 4) ce_col_kernel(
+__device__ __forceinline__ void ce_col_block(
     const typename C2<R>::T *__restrict__ Y, int ncols, int P, int logP, int m, int F, int tpf,
     const typename C2<R>::T *__restrict__ tw, int coarse, R *__restrict__ kout,
-    R *__restrict__ kc_plain) {
+    R *__restrict__ kc_plain, int bx, int sl, unsigned char *smem_raw) {
     using R2 = typename C2<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R2 *sm = reinterpret_cast<R2 *>(smem_raw);
-    const int sl = blockIdx.y;
     const int f = threadIdx.x / tpf, t = threadIdx.x - f * tpf;
-    const int x0 = blockIdx.x * F;
+    const int x0 = bx * F;
     const int col = x0 + f;
     const int LP = fft_line_pitch(P);
     R2 *buf = sm + (size_t)f * LP;
@@ -564,6 +575,16 @@ __global__ void __launch_bounds__(256, 4) ce_col_kernel(
             kout[((size_t)sl * (mc + 1) + yc) * (mc + 1) + xc] = exp_r<R>((v.x + v.y) * invP);
         }
     }
+}
+
+template <typename R, int MAXB>
+__global__ void __launch_bounds__(256, 4) ce_col_kernel(
+    const typename C2<R>::T *__restrict__ Y, int ncols, int P, int logP, int m, int F, int tpf,
+    const typename C2<R>::T *__restrict__ tw, int coarse, R *__restrict__ kout,
+    R *__restrict__ kc_plain) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ce_col_block<R, MAXB>(Y, ncols, P, logP, m, F, tpf, tw, coarse, kout, kc_plain, blockIdx.x,
+                          blockIdx.y, smem_raw);
 }
 
 struct LineCfg {
@@ -724,6 +745,296 @@ static int sample_batch_t(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
     sce_free(Yc, st);
     sce_free(kf_tmp, st);
     return rcode;
+}
+
+// ------------------------------------------------------------------ all levels in one launch
+// ce_sample_levels: the row and column passes of several levels' fields (FP32)
+// in one persistent launch.  Work items -- all row blocks of all tasks, then
+// all column blocks -- are claimed in order from one device counter; a
+// column block of (task, sample) first waits, bounded by clock64, for the
+// per-sample counter of finished row blocks.  A waiting block only depends
+// on items handed out before its own, whose blocks never wait, so the
+// launch cannot deadlock whatever the residency of its blocks.
+constexpr int kLevelsMax = 16;
+
+struct LevelFieldDesc {
+    const float *sqf, *sqc;   // sqc: coarse-masked sqrt(Lambda~) (masked rows), else nullptr
+    const float2 *tw;
+    float2 *Yf, *Yc;
+    float *kf, *kc;
+    uint64_t first_sample;
+    uint32_t level;
+    int P, logP, m, count;
+    int r_tpf, r_F, r_maxb, r_blocks;   // row pass, per sample
+    int c_tpf, c_F, c_maxb, c_blocks;   // fine column pass, per sample
+    int q_tpf, q_F, q_maxb, q_blocks;   // coarse column pass (masked), per sample
+    long long row_begin, col_begin;
+    int done_off, need;                 // row counters of this task start at done_off
+};
+
+struct LevelFieldArgs {
+    const LevelFieldDesc *t;   // device array of ntasks descriptors
+    int ntasks;
+    long long rows_total, items_total;
+    uint64_t seed;
+    long long wait_cycles;
+};
+
+// One item of each pass, inlined with the transform length as a compile-time
+// constant (the shape then needs no registers: in the stand-alone kernels it
+// comes from the constant bank).
+template <int LOGP>
+__device__ __forceinline__ void levels_row_item_p(const LevelFieldDesc &d, uint64_t seed, int bx,
+                                                  int sl, unsigned char *smem_raw) {
+    constexpr int P = 1 << LOGP, TPF = P / 16 < 256 ? P / 16 : 256, F = 256 / TPF;
+    const QmcArgs q0{nullptr, 1u, 0};
+    ce_row_block<float, 4, false>(d.sqf, d.sqc, d.tw, P, LOGP, d.m, seed, d.level,
+                                  d.first_sample, F, TPF, d.Yf, d.Yc, q0, bx, sl, smem_raw);
+}
+
+template <int LOGP>
+__device__ __forceinline__ void levels_col_item_p(const LevelFieldDesc &d, int bx, int sl,
+                                                  unsigned char *smem_raw) {
+    constexpr int P = 1 << LOGP, TPF = P / 16 < 256 ? P / 16 : 256, F = 256 / TPF;
+    const bool fine = bx < d.c_blocks;
+    ce_col_block<float, 4>(fine ? d.Yf : d.Yc, fine ? d.m + 1 : d.m / 2 + 1, P, LOGP, d.m, F, TPF,
+                           d.tw, fine ? 0 : 1, fine ? d.kf : d.kc,
+                           fine && !d.sqc ? d.kc : nullptr, fine ? bx : bx - d.c_blocks, sl,
+                           smem_raw);
+}
+
+__device__ __noinline__ void levels_row_item(const LevelFieldDesc &d, uint64_t seed, int bx, int sl,
+                                             unsigned char *smem_raw) {
+    switch (d.logP) {
+        case 4: levels_row_item_p<4>(d, seed, bx, sl, smem_raw); break;
+        case 5: levels_row_item_p<5>(d, seed, bx, sl, smem_raw); break;
+        case 6: levels_row_item_p<6>(d, seed, bx, sl, smem_raw); break;
+        case 7: levels_row_item_p<7>(d, seed, bx, sl, smem_raw); break;
+        case 8: levels_row_item_p<8>(d, seed, bx, sl, smem_raw); break;
+        case 9: levels_row_item_p<9>(d, seed, bx, sl, smem_raw); break;
+        case 10: levels_row_item_p<10>(d, seed, bx, sl, smem_raw); break;
+        case 11: levels_row_item_p<11>(d, seed, bx, sl, smem_raw); break;
+        default: levels_row_item_p<12>(d, seed, bx, sl, smem_raw); break;
+    }
+}
+
+__device__ __noinline__ void levels_col_item(const LevelFieldDesc &d, int bx, int sl,
+                                             unsigned char *smem_raw) {
+    switch (d.logP) {
+        case 4: levels_col_item_p<4>(d, bx, sl, smem_raw); break;
+        case 5: levels_col_item_p<5>(d, bx, sl, smem_raw); break;
+        case 6: levels_col_item_p<6>(d, bx, sl, smem_raw); break;
+        case 7: levels_col_item_p<7>(d, bx, sl, smem_raw); break;
+        case 8: levels_col_item_p<8>(d, bx, sl, smem_raw); break;
+        case 9: levels_col_item_p<9>(d, bx, sl, smem_raw); break;
+        case 10: levels_col_item_p<10>(d, bx, sl, smem_raw); break;
+        case 11: levels_col_item_p<11>(d, bx, sl, smem_raw); break;
+        default: levels_col_item_p<12>(d, bx, sl, smem_raw); break;
+    }
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(256, 4) ce_levels_kernel(const LevelFieldArgs a,
+                                                           unsigned long long *next,
+                                                           int *rowdone, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_item;
+    __shared__ int s_go;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = *(volatile int *)err ? a.items_total : (long long)atomicAdd(next, 1ull);
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= a.items_total) return;
+        if (it < a.rows_total) {
+            int i = 0;
+            while (i + 1 < a.ntasks && it >= a.t[i + 1].row_begin) ++i;
+            const LevelFieldDesc &d = a.t[i];
+            const long long r = it - d.row_begin;
+            const int sl = (int)(r / d.r_blocks), bx = (int)(r - (long long)sl * d.r_blocks);
+            levels_row_item(d, a.seed, bx, sl, smem_raw);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();   // release: this block's rows before the count
+                atomicAdd(rowdone + d.done_off + sl, 1);
+            }
+        } else {
+            int i = 0;
+            while (i + 1 < a.ntasks && it >= a.t[i + 1].col_begin) ++i;
+            const LevelFieldDesc &d = a.t[i];
+            const int per = d.c_blocks + d.q_blocks;
+            const long long c = it - d.col_begin;
+            const int sl = (int)(c / per), bx = (int)(c - (long long)sl * per);
+            if (threadIdx.x == 0) {
+                const long long t0 = clock64();
+                int ok = 1;
+                while (ld_acquire_gpu(rowdone + d.done_off + sl) < d.need) {
+                    if (clock64() - t0 > a.wait_cycles || *(volatile int *)err) {
+                        atomicCAS(err, 0, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+                s_go = ok;
+            }
+            __syncthreads();
+            if (s_go) {
+                __threadfence();
+                levels_col_item(d, bx, sl, smem_raw);
+            }
+        }
+        __syncthreads();   // shared memory and s_item are reused by the next item
+    }
+}
+
+// Launch shape of a pass in the persistent kernel: P/16 threads per line (as
+// every FP32 shape of ce_sample_batch) and 256 threads per block, lines
+// beyond the pass's count idle.
+static LineCfg levels_cfg(int P) {
+    LineCfg c;
+    c.tpf = std::max(1, std::min(256, P / 16));
+    const int bpt = (P / 4 + c.tpf - 1) / c.tpf;
+    c.maxb = bpt <= 4 ? 4 : 8;
+    c.F = std::max(1, 256 / c.tpf);
+    c.smem = (size_t)c.F * fft_line_pitch(P) * sizeof(float2);
+    return c;
+}
+
+extern "C" int ce_sample_levels(const ce_field_task *tasks, int ntasks, uint64_t seed,
+                                const ce_levels_opts *opts, void *stream) {
+    if (!tasks || ntasks < 1 || ntasks > kLevelsMax) return CE_ERR_INVALID_ARG;
+    const cudaStream_t st = as_stream(stream);
+    int dev = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    LevelFieldArgs a{};
+    std::vector<LevelFieldDesc> desc(ntasks);
+    a.ntasks = ntasks;
+    a.seed = seed;
+    a.wait_cycles = (opts && opts->wait_cycles > 0) ? opts->wait_cycles : (1LL << 31);
+    const int starve = opts ? opts->starve_task : -1;
+    size_t ybytes = 0, smem = 0;
+    long long items = 0;
+    int done_total = 0;
+    std::vector<size_t> yoff(ntasks), ycoff(ntasks);
+    auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    // row items of every task, then column items of every task
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i < ntasks; ++i) {
+            const ce_field_task &t = tasks[i];
+            const ce_embedding_s *e = t.emb;
+            if (!e || e->device != dev || t.count < 0 || !t.k_fine || e->P > 4096)
+                return CE_ERR_INVALID_ARG;
+            LevelFieldDesc &d = desc[i];
+            const bool masked = e->coarse_distinct && t.k_coarse != nullptr;
+            if (pass == 0) {
+                int status = CE_OK;
+                d.tw = sce_twiddles32(e->P, &status);
+                if (status != CE_OK) return status;
+                d.sqf = e->sq32_f;
+                d.sqc = masked ? e->sq32_c : nullptr;
+                d.kf = (float *)t.k_fine;
+                d.kc = (float *)t.k_coarse;
+                d.first_sample = t.first_sample;
+                d.level = t.level;
+                d.P = e->P;
+                d.logP = ilog2(e->P);
+                d.m = e->n;
+                d.count = t.count;
+                const LineCfg r = levels_cfg(e->P);
+                d.r_tpf = r.tpf;
+                d.r_F = r.F;
+                d.r_maxb = r.maxb;
+                d.r_blocks = ((masked ? e->P : e->P / 2) + r.F - 1) / r.F;
+                d.c_tpf = r.tpf;
+                d.c_F = r.F;
+                d.c_maxb = r.maxb;
+                d.c_blocks = (e->n + 1 + r.F - 1) / r.F;
+                d.q_tpf = r.tpf;
+                d.q_F = r.F;
+                d.q_maxb = r.maxb;
+                d.q_blocks = masked ? (e->n / 2 + 1 + r.F - 1) / r.F : 0;
+                smem = std::max(smem, r.smem);
+                d.done_off = done_total;
+                done_total += t.count;
+                d.need = d.r_blocks + (i == starve ? 1 : 0);
+                d.row_begin = items;
+                items += (long long)t.count * d.r_blocks;
+                yoff[i] = ybytes;
+                ybytes += align((size_t)t.count * (e->n + 1) * e->P * sizeof(float2));
+                ycoff[i] = ybytes;
+                if (masked) ybytes += align((size_t)t.count * (e->n / 2 + 1) * e->P * sizeof(float2));
+            } else {
+                d.col_begin = items;
+                items += (long long)t.count * (d.c_blocks + d.q_blocks);
+            }
+        }
+        if (pass == 0) a.rows_total = items;
+    }
+    a.items_total = items;
+    if (items == 0) return CE_OK;
+    unsigned char *Y = nullptr;
+    int *ctr = nullptr;   // [0..1] next (64-bit), [2] err, [3] unused, [4..] row counters
+    LevelFieldDesc *dd = nullptr;
+    SCE_TRY(sce_alloc((void **)&Y, std::max<size_t>(ybytes, 256), st));
+    const size_t cbytes = sizeof(int) * (4 + (size_t)done_total);
+    int rc = sce_alloc((void **)&ctr, cbytes, st);
+    if (rc == CE_OK) rc = sce_alloc((void **)&dd, sizeof(LevelFieldDesc) * ntasks, st);
+    if (rc != CE_OK) {
+        sce_free(Y, st);
+        sce_free(ctr, st);
+        return rc;
+    }
+    for (int i = 0; i < ntasks; ++i) {
+        desc[i].Yf = reinterpret_cast<float2 *>(Y + yoff[i]);
+        desc[i].Yc = desc[i].sqc ? reinterpret_cast<float2 *>(Y + ycoff[i]) : nullptr;
+    }
+    a.t = dd;
+    int blocks_per_sm = 0, sms = 0;
+    rc = sce_raise_smem_limit((const void *)ce_levels_kernel, smem);
+    // the descriptors travel with the stream (the host vector outlives the
+    // copy: the call synchronises the stream before returning)
+    if (rc == CE_OK &&
+        (cudaMemcpyAsync(dd, desc.data(), sizeof(LevelFieldDesc) * ntasks,
+                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemsetAsync(ctr, 0, cbytes, st) != cudaSuccess ||
+         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, ce_levels_kernel, 256,
+                                                       smem) != cudaSuccess))
+        rc = CE_ERR_CUDA;
+    if (rc == CE_OK) {
+        const long long grid = std::min<long long>(items, (long long)sms * std::max(1, blocks_per_sm));
+        double bytes = 0.0;
+        for (int i = 0; i < ntasks; ++i) {
+            const LevelFieldDesc &d = desc[i];
+            const double per = (double)(d.m + 1) * d.P * 8.0 * (d.sqc ? 1.5 : 1.0);
+            bytes += (double)d.count * (2.0 * per + 4.0 * (d.m + 1) * (d.m + 1));
+        }
+        SceProf pr(KP_LEVELS, st, bytes);
+        ce_levels_kernel<<<(unsigned)grid, 256, smem, st>>>(
+            a, reinterpret_cast<unsigned long long *>(ctr), ctr + 4, ctr + 2);
+        if (cudaGetLastError() != cudaSuccess) rc = CE_ERR_CUDA;
+    }
+    int herr = 0;
+    if (rc == CE_OK && (cudaMemcpyAsync(&herr, ctr + 2, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(st) != cudaSuccess))
+        rc = CE_ERR_CUDA;
+    if (rc != CE_OK) cudaStreamSynchronize(st);   // the pageable copy reads desc until done
+    sce_free(Y, st);
+    sce_free(ctr, st);
+    sce_free(dd, st);
+    if (rc == CE_OK && herr) {
+        sce_set_last_error_text("ce_sample_levels: a column block gave up waiting for the row "
+                                "blocks of its sample");
+        rc = CE_ERR_TIMEOUT;
+    }
+    return rc;
 }
 
 int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,

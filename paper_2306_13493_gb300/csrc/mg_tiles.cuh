@@ -56,12 +56,27 @@ constexpr int MG_CCW = MG_CW + 3;          // coarse window of mg_up: 32 x 16 (+
 constexpr int MG_CCH = MG_CH + 3;
 constexpr unsigned MG_FULL = 0xffffffffu;
 
+// Window shape of the tiled kernels by window height SH (the width is always
+// 64): SH / 4 warps, CH coarse vertices per tile in y, and blocks per SM
+// such that a thread keeps 48 registers (each of the four schedulers of an SM
+// has 16384: at most 10 warps of 48 registers, so 40 warps per SM; twice
+// fewer blocks in FP64).  The solver
+// picks SH per grid size (table set by darcy_autotune_tiles; MG_SH otherwise).
+template <int SH>
+struct MGTile {
+    static_assert(SH % 4 == 0 && SH >= 16 && SH <= 64, "tile height");
+    static constexpr int H = SH, NW = SH / 4, CH = (SH - 6) / 2, THREADS = 32 * NW;
+    static constexpr int CCH = CH + 3;
+    static constexpr int BPS = 40 / NW;
+};
+
 // shared memory: z of rows 0 and 3 of every warp (2 buffers), one row per
 // warp for cy / residual exchange, the coarse window of mg_up with a spare row
-template <typename T>
+template <typename T, int SH = MG_SH>
 constexpr size_t mg_tile_smem_bytes() {
-    return sizeof(T) * (2 * 2 * MG_NW * (size_t)MG_SW + MG_NW * (size_t)MG_SW +
-                        (size_t)(MG_CCH + 1) * MG_CCW + 1);
+    using G = MGTile<SH>;
+    return sizeof(T) * (2 * 2 * G::NW * (size_t)MG_SW + G::NW * (size_t)MG_SW +
+                        (size_t)(G::CCH + 1) * MG_CCW + 1);
 }
 
 template <typename T>
@@ -226,10 +241,12 @@ __device__ __forceinline__ T tile_red_residual(const TileBlock<T> &t, unsigned u
     return ((unk >> e) & 1) ? rv : T(0);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM : MG_BLOCKS_PER_SM / 2) mg_down_kernel(
+template <typename T, int SH = MG_SH>
+__global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<SH>::BPS : MGTile<SH>::BPS / 2) mg_down_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ zpre, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
+    using G = MGTile<SH>;
+    constexpr int MG_SH = SH, MG_NW = G::NW, MG_CH = G::CH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xz = reinterpret_cast<T *>(smem_raw);
     T *xrow = xz + 2 * 2 * MG_NW * MG_SW;
@@ -245,7 +262,7 @@ __global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM 
                         2 * J0 - 4 + MG_SH - 1 <= n;
     TileBlock<T> t;
     const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n, inside);
-    tile_diag(t, xrow, lane, warp, unk);
+    tile_diag<T, MG_NW>(t, xrow, lane, warp, unk);
     // red from z = 0: z = b / diag at red elements ((c + r) even), 0 at black
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -255,9 +272,9 @@ __global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM 
             t.z[e] = ((c + r) & 1) == 0 ? t.b[e] * t.inv[e] : T(0);
         }
     }
-    tile_exchange(t, xz, 0, lane, warp);
+    tile_exchange<T, MG_NW>(t, xz, 0, lane, warp);
     tile_half_sweep<T, 1>(t);
-    tile_exchange(t, xz, 1, lane, warp);
+    tile_exchange<T, MG_NW>(t, xz, 1, lane, warp);
     // red residuals of rows 0..3 (c = r % 2)
     const T r0 = tile_red_residual<T, 0>(t, unk), r1 = tile_red_residual<T, 1>(t, unk);
     const T r2 = tile_red_residual<T, 2>(t, unk), r3 = tile_red_residual<T, 3>(t, unk);
@@ -292,11 +309,14 @@ __global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM 
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM : MG_BLOCKS_PER_SM / 2) mg_up_kernel(
+template <typename T, int SH = MG_SH>
+__global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<SH>::BPS : MGTile<SH>::BPS / 2) mg_up_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     const T *__restrict__ zpre, T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x,
     const int *__restrict__ act, double *__restrict__ part_rz, int nblk) {
+    using G = MGTile<SH>;
+    constexpr int MG_SH = SH, MG_NW = G::NW, MG_CH = G::CH, MG_CCH = G::CCH;
+    constexpr int MG_THREADS = G::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T sred[32];
     T *xz = reinterpret_cast<T *>(smem_raw);
@@ -340,7 +360,7 @@ __global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM 
             }
         }
     }
-    tile_diag(t, xrow, lane, warp, unk);   // its barrier also covers szc
+    tile_diag<T, MG_NW>(t, xrow, lane, warp, unk);   // its barrier also covers szc
     // z += P zc: coarse column lane (and lane + 1), rows 2 warp + {0, 1, 2};
     // weights (1, 0) at even fine indices, (1/2, 1/2) at odd ones
     const T *q0 = szc + (2 * warp) * MG_CCW + lane;
@@ -358,9 +378,9 @@ __global__ void __launch_bounds__(MG_THREADS, sizeof(T) == 4 ? MG_BLOCKS_PER_SM 
         else pv = c == 0 ? h * (x0 + y0) : qq * ((x0 + x1) + (y0 + y1));
         t.z[k] += pv;
     }
-    tile_exchange(t, xz, 0, lane, warp);
+    tile_exchange<T, MG_NW>(t, xz, 0, lane, warp);
     tile_half_sweep<T, 1>(t);
-    tile_exchange(t, xz, 1, lane, warp);
+    tile_exchange<T, MG_NW>(t, xz, 1, lane, warp);
     tile_half_sweep<T, 0>(t);
     // owned fine vertices: window [2, 2 + 2 CW) x [2, 2 + 2 CH)
     T *zs = z + s * V;

@@ -63,6 +63,8 @@ struct LevelArgs {
     double *Y, *qoi_f, *qoi_c;
     mlmc_level_sums *out;
     const QmcArgs *qa = nullptr;   // lattice sampler (nullptr: Philox)
+    const void *kf_pre = nullptr;  // fields computed beforehand (count of them), or nullptr
+    const void *kc_pre = nullptr;
 };
 
 // One level on stream st; the coarse solves go to stream stc (a second host
@@ -115,8 +117,9 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
         if (r == CE_OK) owned.push_back(*ptr);
         return r;
     };
-    if ((rc = A(&kf, (size_t)chunk * Vf * es)) != CE_OK) { cleanup(); return rc; }
-    if (coarse && (rc = A(&kc, (size_t)chunk * Vc * es)) != CE_OK) { cleanup(); return rc; }
+    const bool pre = a.kf_pre != nullptr;
+    if (!pre && (rc = A(&kf, (size_t)chunk * Vf * es)) != CE_OK) { cleanup(); return rc; }
+    if (!pre && coarse && (rc = A(&kc, (size_t)chunk * Vc * es)) != CE_OK) { cleanup(); return rc; }
     if (!a.qoi_f && (rc = A((void **)&qf, (size_t)chunk * 3 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
     if (coarse && !a.qoi_c && (rc = A((void **)&qc, (size_t)chunk * 3 * sizeof(double))) != CE_OK) { cleanup(); return rc; }
     if (!a.Y && (rc = A((void **)&Yd, (size_t)chunk * sizeof(double))) != CE_OK) { cleanup(); return rc; }
@@ -151,9 +154,14 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
         double *qf_c = a.qoi_f ? a.qoi_f + 3 * (size_t)c0 : qf;
         double *qc_c = coarse ? (a.qoi_c ? a.qoi_c + 3 * (size_t)c0 : qc) : nullptr;
         double *Y_c = a.Y ? a.Y + c0 : Yd;
-        rc = sce_sample_batch_impl(e, seed, a.level, a.first_sample + (uint64_t)c0, cn,
-                                   p->precision, kf, coarse ? kc : nullptr, st, a.qa);
-        if (rc != CE_OK) { cleanup(); return rc; }
+        if (pre) {
+            kf = (char *)a.kf_pre + (size_t)c0 * Vf * es;
+            kc = coarse ? (char *)a.kc_pre + (size_t)c0 * Vc * es : nullptr;
+        } else {
+            rc = sce_sample_batch_impl(e, seed, a.level, a.first_sample + (uint64_t)c0, cn,
+                                       p->precision, kf, coarse ? kc : nullptr, st, a.qa);
+            if (rc != CE_OK) { cleanup(); return rc; }
+        }
         int mi_c[2] = {0, 0}, nf_c = 0;
         char coarse_err[512] = {0};
         std::future<int> fut;
@@ -234,21 +242,19 @@ extern "C" int mlmc_level_estimate(ce_embedding_t e, const darcy_problem *p, uin
                      qoi_index, st, st);
 }
 
-extern "C" int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
-                                    mlmc_level_task *tasks, int ntasks, int max_concurrency,
-                                    void *stream) {
-    if (!valid_problem(p, qoi_index) || ntasks < 0 || (ntasks > 0 && !tasks))
-        return CE_ERR_INVALID_ARG;
-    for (int i = 0; i < ntasks; ++i)
-        if (!tasks[i].emb || tasks[i].count < 0) return CE_ERR_INVALID_ARG;
-    for (int i = 0; i < ntasks; ++i) {
-        tasks[i].sums = mlmc_level_sums{};
-        tasks[i].status = CE_OK;
-    }
-    const cudaStream_t st = as_stream(stream);
+// All levels of a step; pre_f / pre_c: per task, fields computed beforehand
+// (or nullptr: each level samples its own).
+static int estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
+                           mlmc_level_task *tasks, int ntasks, int max_concurrency,
+                           cudaStream_t st, void *const *pre_f, void *const *pre_c) {
     auto args_of = [&](int i) {
         mlmc_level_task &t = tasks[i];
-        return LevelArgs{t.emb, t.level, t.first_sample, t.count, t.Y, t.qoi_f, t.qoi_c, &t.sums};
+        LevelArgs a{t.emb, t.level, t.first_sample, t.count, t.Y, t.qoi_f, t.qoi_c, &t.sums};
+        if (pre_f) {
+            a.kf_pre = pre_f[i];
+            a.kc_pre = pre_c[i];
+        }
+        return a;
     };
     auto combine = [&]() {
         int worst = CE_OK;
@@ -339,6 +345,58 @@ extern "C" int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int q
     }
     release();
     return combine();
+}
+
+extern "C" int mlmc_estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
+                                    mlmc_level_task *tasks, int ntasks, int max_concurrency,
+                                    void *stream) {
+    if (!valid_problem(p, qoi_index) || ntasks < 0 || (ntasks > 0 && !tasks))
+        return CE_ERR_INVALID_ARG;
+    for (int i = 0; i < ntasks; ++i)
+        if (!tasks[i].emb || tasks[i].count < 0) return CE_ERR_INVALID_ARG;
+    for (int i = 0; i < ntasks; ++i) {
+        tasks[i].sums = mlmc_level_sums{};
+        tasks[i].status = CE_OK;
+    }
+    return estimate_levels(p, seed, qoi_index, tasks, ntasks, max_concurrency, as_stream(stream),
+                           nullptr, nullptr);
+}
+
+extern "C" int mlmc_estimate_levels_persistent(const darcy_problem *p, uint64_t seed,
+                                               int qoi_index, mlmc_level_task *tasks, int ntasks,
+                                               int max_concurrency, void *stream) {
+    if (!valid_problem(p, qoi_index) || p->precision != 32 || ntasks < 1 || ntasks > 16 || !tasks)
+        return CE_ERR_INVALID_ARG;
+    for (int i = 0; i < ntasks; ++i)
+        if (!tasks[i].emb || tasks[i].count < 0 || tasks[i].emb->P > 4096)
+            return CE_ERR_INVALID_ARG;
+    for (int i = 0; i < ntasks; ++i) {
+        tasks[i].sums = mlmc_level_sums{};
+        tasks[i].status = CE_OK;
+    }
+    const cudaStream_t st = as_stream(stream);
+    // every level's fields in one persistent launch on the caller's stream
+    std::vector<void *> pf(ntasks, nullptr), pc(ntasks, nullptr);
+    std::vector<ce_field_task> ft(ntasks);
+    int rc = CE_OK;
+    for (int i = 0; i < ntasks && rc == CE_OK; ++i) {
+        const mlmc_level_task &t = tasks[i];
+        const long long n = t.emb->n, nc = n / 2;
+        const size_t cnt = (size_t)std::max(t.count, 1);
+        rc = sce_alloc(&pf[i], cnt * (n + 1) * (n + 1) * sizeof(float), st);
+        if (rc == CE_OK && t.level > 0)
+            rc = sce_alloc(&pc[i], cnt * (nc + 1) * (nc + 1) * sizeof(float), st);
+        ft[i] = ce_field_task{t.emb, t.level, t.first_sample, t.count, pf[i], pc[i]};
+    }
+    if (rc == CE_OK) rc = ce_sample_levels(ft.data(), ntasks, seed, nullptr, st);
+    if (rc == CE_OK)
+        rc = estimate_levels(p, seed, qoi_index, tasks, ntasks, max_concurrency, st, pf.data(),
+                             pc.data());
+    for (int i = 0; i < ntasks; ++i) {
+        if (pf[i]) sce_free(pf[i], st);
+        if (pc[i]) sce_free(pc[i], st);
+    }
+    return rc;
 }
 
 extern "C" int mlmc_level_estimate_qmc(ce_qmc_t q, const darcy_problem *p, uint64_t seed,

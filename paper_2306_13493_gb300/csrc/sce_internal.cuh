@@ -88,7 +88,7 @@ enum SceKernel {
     KP_SETUP, KP_NORMALS, KP_LEVEL, KP_SMALL, KP_MG_DOWN, KP_MG_UP, KP_MG_TAIL,
     // three-dimensional path
     KP_X3, KP_Y3, KP_Z3, KP_COND3, KP_SMOOTH3, KP_RESID3, KP_RESTRICT3, KP_PROLONG3, KP_SPMV3,
-    KP_VEC3, KP_OUTER3, KP_MG_V64, KP_COUNT_
+    KP_VEC3, KP_OUTER3, KP_MG_V64, KP_LEVELS, KP_COUNT_
 };
 
 bool sce_prof_on();

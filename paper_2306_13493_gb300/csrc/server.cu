@@ -60,6 +60,13 @@ struct Job {
     sce_result res{};
     long long fp = 0;
     bool done = false;
+    // a slice of a sliced request (parent != 0): slice index within it
+    unsigned long long parent = 0;
+    int slice = 0;
+    // a sliced request: slices, the next one to queue, those done, samples
+    // per slice, and each slice's sums and status (added in slice order)
+    int nslices = 0, next_slice = 0, slices_done = 0, per_slice = 0;
+    std::vector<sce_result> part;
 };
 
 constexpr int kMaxHeadSkips = 8;
@@ -105,6 +112,65 @@ struct sce_server_s {
     std::vector<std::thread> workers;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+
+    // Queues the next slice of sliced request `pid` at the back (caller holds mu).
+    void enqueue_slice(unsigned long long pid) {
+        Job &P = jobs.at(pid);
+        const int k = P.next_slice++;
+        Job j;
+        j.r = P.r;
+        j.r.first_sample = P.r.first_sample + (uint64_t)k * P.per_slice;
+        j.r.count = std::min(P.per_slice, P.r.count - k * P.per_slice);
+        if (P.r.Y) j.r.Y = P.r.Y + (size_t)k * P.per_slice;
+        j.fp = std::min(request_footprint(j.r, cfg.precision), budget);
+        j.res.footprint = j.fp;
+        j.res.t_submit = P.res.t_submit;
+        j.parent = pid;
+        j.slice = k;
+        const unsigned long long id = next_id++;
+        jobs.emplace(id, j);
+        queue.push_back(id);
+    }
+
+    // A finished slice: keep its results, queue the next slice, and complete
+    // the request once every slice is done (caller holds mu).  Returns true
+    // when the request completed.
+    bool slice_done(unsigned long long sid) {
+        Job &sj = jobs.at(sid);
+        const unsigned long long pid = sj.parent;
+        Job &P = jobs.at(pid);
+        P.part[sj.slice] = sj.res;
+        P.res.footprint = std::max(P.res.footprint, sj.fp);
+        jobs.erase(sid);
+        ++P.slices_done;
+        if (P.next_slice < P.nslices) enqueue_slice(pid);
+        if (P.slices_done < P.nslices) return false;
+        mlmc_level_sums tot{};
+        int status = CE_OK, hit = 1;
+        for (int k = 0; k < P.nslices; ++k) {   // fixed order: independent of timing
+            const sce_result &r = P.part[k];
+            tot.N += r.sums.N;
+            tot.sumY += r.sums.sumY;
+            tot.sumY2 += r.sums.sumY2;
+            tot.sumQf += r.sums.sumQf;
+            tot.sumQf2 += r.sums.sumQf2;
+            tot.n_failed += r.sums.n_failed;
+            tot.max_iters = std::max(tot.max_iters, r.sums.max_iters);
+            tot.total_iters += r.sums.total_iters;
+            if (status == CE_OK || status == CE_ERR_NOT_CONVERGED)
+                if (r.status != CE_OK) status = r.status;
+            hit &= r.cache_hit;
+        }
+        P.res.sums = tot;
+        P.res.status = status;
+        P.res.cache_hit = hit;
+        P.res.t_admit = P.part[0].t_admit;
+        P.res.t_setup_done = P.part[0].t_setup_done;
+        P.res.t_done = now();
+        P.done = true;
+        P.part.clear();
+        return true;
+    }
 
     // Next admissible job (caller holds mu); 0 if none.
     unsigned long long pick() {
@@ -243,10 +309,14 @@ struct sce_server_s {
             {
                 std::lock_guard<std::mutex> lk(mu);
                 j->res.t_done = now();
-                j->done = true;
                 reserved -= j->fp;
                 --in_flight;
-                ++completed;
+                if (j->parent) {
+                    if (slice_done(id)) ++completed;
+                } else {
+                    j->done = true;
+                    ++completed;
+                }
             }
             cv_done.notify_all();
             cv_work.notify_all();
@@ -290,15 +360,32 @@ extern "C" int sce_server_submit(sce_server_t S, const sce_request *r, uint64_t 
         return CE_ERR_INVALID_ARG;
     Job j;
     j.r = *r;
-    j.fp = std::min(request_footprint(*r, S->cfg.precision), S->budget);
-    j.res.footprint = j.fp;
+    const long long Vf = (long long)(r->n + 1) * (r->n + 1);
+    const long long sv = S->cfg.slice_vertices == 0 ? (1LL << 24) : S->cfg.slice_vertices;
+    const long long per = sv > 0 ? std::max(1LL, sv / Vf) : (long long)r->count;
+    const bool sliced = sv > 0 && (long long)r->count > per;
+    if (sliced) {
+        j.per_slice = (int)per;
+        j.nslices = (int)(((long long)r->count + per - 1) / per);
+        j.part.assign(j.nslices, sce_result{});
+    } else {
+        j.fp = std::min(request_footprint(*r, S->cfg.precision), S->budget);
+        j.res.footprint = j.fp;
+    }
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->stop) return CE_ERR_INVALID_ARG;
         const unsigned long long id = S->next_id++;
         j.res.t_submit = S->now();
         S->jobs.emplace(id, j);
-        S->queue.push_back(id);
+        if (sliced) {
+            // up to `slots` slices queued or running: an idle server gives a large
+            // request every slot, and each finished slice queues the next one
+            // behind the requests that arrived meanwhile
+            for (int k = 0; k < std::min(S->cfg.slots, j.nslices); ++k) S->enqueue_slice(id);
+        } else {
+            S->queue.push_back(id);
+        }
         ++S->submitted;
         *ticket = id;
     }

@@ -253,7 +253,7 @@ def richardson_bias(stats: List[LevelStats], alpha, ratio=1.0, levels=1):
 
 def cost_versus_eps(stats: List[LevelStats], eps_list, mc_cost_per_sample=None,
                     choose_levels=False, alpha=None, ratio=1.0, bias_levels=1,
-                    alpha_levels=3, alpha_max=None):
+                    alpha_levels=3, alpha_max=None, L_min=1):
     """Predicted cost to a root-mean-square error eps from measured level
     statistics, for the cost-versus-accuracy comparisons of §4.2-4.3 (the
     variance share eps^2/2 in both):
@@ -269,7 +269,8 @@ def cost_versus_eps(stats: List[LevelStats], eps_list, mc_cost_per_sample=None,
     Richardson bias (alpha fitted on the `alpha_levels` finest of the measured
     levels, at most alpha_max; ``richardson_bias`` with `bias_levels`) is at
     most eps/sqrt(2), as the adaptive algorithm would pick it (the last
-    measured level if none is); otherwise every measured level is used.  The
+    measured level if none is), and at least L_min (as in ``run_adaptive``);
+    otherwise every measured level is used.  The
     statistics of a level that is not the finest stand in for it as the
     finest (under smoothing its fine field would then be unsmoothed).
 
@@ -284,7 +285,7 @@ def cost_versus_eps(stats: List[LevelStats], eps_list, mc_cost_per_sample=None,
     for eps in eps_list:
         L = len(stats) - 1
         if choose_levels:
-            for l in range(1, len(stats)):
+            for l in range(max(1, L_min), len(stats)):
                 if richardson_bias(stats[:l + 1], a, ratio, bias_levels) <= eps / math.sqrt(2.0):
                     L = l
                     break
@@ -350,7 +351,7 @@ def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rou
 def run_adaptive(make_runner: Callable[[int, bool], LevelRunner], eps, L0=2, L_max=8,
                  pilot=100, alpha=None, ratio=1.0, max_rounds=10, restart_previous_finest=True,
                  alpha_levels=None, fill_variance=False, pilot_new=None, alpha_max=None,
-                 bias_levels=1):
+                 bias_levels=1, L_min=0):
     """MLMC to a root-mean-square error eps with the number of levels chosen as
     it runs: start on levels 0..L0, run ``run_to_rmse`` (variance share
     eps^2/2), and while the Richardson bias of the finest level exceeds the
@@ -377,7 +378,11 @@ def run_adaptive(make_runner: Callable[[int, bool], LevelRunner], eps, L0=2, L_m
     pilot_new: pilot samples of a level added (or rebuilt) after the first
     L0 + 1 (default `pilot`): on fine levels Eq. (3.6) asks for few samples,
     and a large pilot there dominates the cost.  alpha_levels, alpha_max and
-    bias_levels go to the bias estimate (``fit_alpha``, ``richardson_bias``)."""
+    bias_levels go to the bias estimate (``fit_alpha``, ``richardson_bias``).
+    L_min: the bias test may end the level loop only once the finest level is
+    at least L_min (the Richardson estimate assumes the asymptotic regime,
+    which the coarse meshes MLMC-CES allows do not reach: below the coarsest
+    mesh of plain MLMC, Eq. (3.7)-(3.8), E[Y_l] can be small by accident)."""
     if L0 < 0 or L_max < L0:
         raise ValueError("need 0 <= L0 <= L_max")
     runners = [make_runner(l, l == L0) for l in range(L0 + 1)]
@@ -389,7 +394,7 @@ def run_adaptive(make_runner: Callable[[int, bool], LevelRunner], eps, L0=2, L_m
     while True:
         res = run_to_rmse(runners, eps, pilot=pilots, **kw)
         L = len(runners) - 1
-        if res.bias <= eps / math.sqrt(2.0) or L >= L_max:
+        if (res.bias <= eps / math.sqrt(2.0) and L >= L_min) or L >= L_max:
             break
         if restart_previous_finest:
             discarded += runners[L].stats.seconds

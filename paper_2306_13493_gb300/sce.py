@@ -59,6 +59,16 @@ class darcy_problem(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
+class ce_field_task(ctypes.Structure):
+    _fields_ = [("emb", ctypes.c_void_p), ("level", ctypes.c_uint32),
+                ("first_sample", ctypes.c_uint64), ("count", ctypes.c_int),
+                ("k_fine", ctypes.c_void_p), ("k_coarse", ctypes.c_void_p)]
+
+
+class ce_levels_opts(ctypes.Structure):
+    _fields_ = [("wait_cycles", ctypes.c_longlong), ("starve_task", ctypes.c_int)]
+
+
 class mlmc_level_sums(ctypes.Structure):
     _fields_ = [("N", ctypes.c_longlong), ("sumY", ctypes.c_double), ("sumY2", ctypes.c_double),
                 ("sumQf", ctypes.c_double), ("sumQf2", ctypes.c_double),
@@ -84,7 +94,8 @@ class mlmc3_level_task(ctypes.Structure):
 class sce_server_config(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_longlong),
                 ("max_embeddings", ctypes.c_int), ("precision", ctypes.c_int),
-                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int)]
+                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("slice_vertices", ctypes.c_longlong)]
 
 
 class sce_request(ctypes.Structure):
@@ -150,6 +161,9 @@ _SIGS = {
     "mlmc_estimate_levels": (ctypes.c_int, [ctypes.POINTER(darcy_problem), ctypes.c_uint64,
                                             ctypes.c_int, ctypes.POINTER(mlmc_level_task),
                                             ctypes.c_int, ctypes.c_int, _P]),
+    "mlmc_estimate_levels_persistent": (ctypes.c_int, [ctypes.POINTER(darcy_problem), ctypes.c_uint64,
+                                            ctypes.c_int, ctypes.POINTER(mlmc_level_task),
+                                            ctypes.c_int, ctypes.c_int, _P]),
     "mlmc_optimal_samples": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_double, _P]),
     "mlmc_tau_exponential": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                             ctypes.POINTER(ctypes.c_double)]),
@@ -178,6 +192,11 @@ _SIGS = {
     "ce_destroy": (None, [_P]),
     "ce_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sce_last_error": (ctypes.c_char_p, []),
+    "ce_sample_levels": (ctypes.c_int, [ctypes.POINTER(ce_field_task), ctypes.c_int,
+                                        ctypes.c_uint64, ctypes.POINTER(ce_levels_opts), _P]),
+    "darcy_autotune_tiles": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int)]),
+    "sce_test_fail_allocs": (None, [ctypes.c_int]),
     "sce_peak_fma": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "sce_peak_l2": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _P, _P]),
     "sce_profile_enable": (None, [ctypes.c_int]),
@@ -344,11 +363,13 @@ def mlmc_level_estimate(emb, seed, level, first_sample, count, qoi_index=QOI_OUT
 
 
 def mlmc_estimate_levels(tasks, seed, qoi_index=QOI_OUTFLOW, f=0.0, rtol=1e-10, maxit=1000,
-                         precision=32, max_concurrency=8, stream=None, allow_not_converged=False):
+                         precision=32, max_concurrency=8, stream=None, allow_not_converged=False,
+                         persistent=False):
     """All levels of one MLMC step in one call.  ``tasks``: sequence of dicts
     with keys emb, level, first_sample, count and optionally Y, qoi_f, qoi_c
-    (CUDA tensors).  Returns ([mlmc_level_sums per task], [status per task],
-    overall status)."""
+    (CUDA tensors).  persistent=True: every level's fields in one persistent
+    launch first (mlmc_estimate_levels_persistent).  Returns
+    ([mlmc_level_sums per task], [status per task], overall status)."""
     if not tasks:
         return [], [], CE_OK
     arr = (mlmc_level_task * len(tasks))()
@@ -363,9 +384,10 @@ def mlmc_estimate_levels(tasks, seed, qoi_index=QOI_OUTFLOW, f=0.0, rtol=1e-10, 
     allow = (CE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
     ref = next((d[k] for d in tasks for k in ("Y", "qoi_f", "qoi_c") if d.get(k) is not None),
                None)
-    st = _check(load().mlmc_estimate_levels(ctypes.byref(prob), seed, qoi_index, arr, len(tasks),
-                                            max_concurrency, _stream(stream, ref)),
-                "mlmc_estimate_levels", allow)
+    fn = load().mlmc_estimate_levels_persistent if persistent else load().mlmc_estimate_levels
+    st = _check(fn(ctypes.byref(prob), seed, qoi_index, arr, len(tasks), max_concurrency,
+                   _stream(stream, ref)),
+                "mlmc_estimate_levels_persistent" if persistent else "mlmc_estimate_levels", allow)
     return [mlmc_level_sums.from_buffer_copy(t.sums) for t in arr], [t.status for t in arr], st
 
 
@@ -377,9 +399,10 @@ class Server:
     Y (CUDA tensor of count doubles)."""
 
     def __init__(self, slots=8, hbm_budget=0, max_embeddings=256, precision=32, rtol=1e-10,
-                 maxit=2000):
+                 maxit=2000, slice_vertices=0):
         self._lib = load()
-        cfg = sce_server_config(slots, hbm_budget, max_embeddings, precision, rtol, maxit)
+        cfg = sce_server_config(slots, hbm_budget, max_embeddings, precision, rtol, maxit,
+                                slice_vertices)
         h = _P()
         _check(self._lib.sce_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sce_server_create")
         self.handle = h
@@ -437,6 +460,32 @@ def ce_autotune_fft(emb, precision=32, count=32, reps=3, stream=None):
     _check(load().ce_autotune_fft(emb.handle, precision, count, reps, _stream(stream),
                                   *[ctypes.byref(x) for x in v]), "ce_autotune_fft")
     return {"row": (v[0].value, v[1].value), "col": (v[2].value, v[3].value)}
+
+
+def ce_sample_levels(tasks, seed, wait_cycles=0, starve_task=-1, stream=None):
+    """Fields of several levels in one persistent launch (FP32).  ``tasks``:
+    dicts with emb, level, first_sample, count, k_fine and optionally
+    k_coarse (CUDA float tensors).  Synchronises the stream."""
+    arr = (ce_field_task * len(tasks))()
+    for t, d in zip(arr, tasks):
+        h = d["emb"].handle
+        t.emb = h.value if isinstance(h, ctypes.c_void_p) else h
+        t.level = d["level"]
+        t.first_sample = d["first_sample"]
+        t.count = d["count"]
+        t.k_fine = d["k_fine"].data_ptr()
+        t.k_coarse = d["k_coarse"].data_ptr() if d.get("k_coarse") is not None else None
+    opts = ce_levels_opts(wait_cycles, starve_task)
+    _check(load().ce_sample_levels(arr, len(tasks), seed, ctypes.byref(opts),
+                                   _stream(stream, tasks[0]["k_fine"])), "ce_sample_levels")
+
+
+def darcy_autotune_tiles(n, precision=32, count=64, reps=3, stream=None):
+    """Tunes the multigrid window height for n-cell grids; returns the height."""
+    h = ctypes.c_int()
+    _check(load().darcy_autotune_tiles(n, precision, count, reps, _stream(stream),
+                                       ctypes.byref(h)), "darcy_autotune_tiles")
+    return h.value
 
 
 class QmcLattice:
@@ -627,3 +676,8 @@ def sce_peak_l2(buf, reps, blocks, out, stream=None):
     nbytes = buf.numel() * buf.element_size()
     _check(load().sce_peak_l2(_ptr(buf), nbytes, reps, blocks, _ptr(out), _stream(stream, out)),
            "sce_peak_l2")
+
+
+def sce_test_fail_allocs(count):
+    """Test hook: the next `count` library allocations fail with CE_ERR_OOM."""
+    load().sce_test_fail_allocs(int(count))

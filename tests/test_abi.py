@@ -102,8 +102,12 @@ def test_struct_layouts_match_header():
     assert sce.mlmc3_level_task.sums.offset == 40
     assert sce.mlmc3_level_task.status.offset == 96
     assert ctypes.sizeof(sce.mlmc3_level_task) == 104
-    # server structs: config int, (pad), i64, int, int, double, int (+pad)
-    assert ctypes.sizeof(sce.sce_server_config) == 40
+    # server structs: config int, (pad), i64, int, int, double, int (+pad), i64
+    assert ctypes.sizeof(sce.sce_server_config) == 48
+    assert sce.sce_server_config.slice_vertices.offset == 40
+    # persistent field task: pointer, u32 (+pad), u64, int (+pad), 2 pointers
+    assert ctypes.sizeof(sce.ce_field_task) == 48 and sce.ce_field_task.k_fine.offset == 32
+    assert ctypes.sizeof(sce.ce_levels_opts) == 16
     # request: ce_cov 32, ce_pad 12, n 4, level 4, smoothing 4, finest 4, (pad 4),
     # seed 8, first_sample 8, count 4, qoi 4, f 8, Y 8
     assert sce.sce_request.seed.offset == 64 and ctypes.sizeof(sce.sce_request) == 104

@@ -177,3 +177,42 @@ def test_graph_replay_matches_stream_launches(sce, precision, maxit, monkeypatch
     assert np.array_equal(q1, q0) and np.array_equal(i1, i0) and np.array_equal(s1, s0)
     if maxit == 6:
         assert rc1 == sce.CE_ERR_NOT_CONVERGED and np.all(i1 <= 6)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_tile_heights_give_the_same_solves(sce, precision, monkeypatch):
+    """Every window height of the tiled multigrid kernels (16, 24, 32, 48
+    rows) computes each vertex of a V-cycle identically; only the order in
+    which the per-tile partial sums of r . z are added follows the tiling.
+    The solutions and QoIs of a random field on n = 256 (tiled levels 256
+    and 128, ragged tiles at the grid's edges) agree to rounding across
+    heights, and match the oracle's direct solve."""
+    n, count = 256, 3
+    k = _oracle_k(n, count, lam=0.05, seed=4, precision=precision)
+    ref = None
+    for h in (32, 16, 24, 48):
+        monkeypatch.setenv("SCE_TILE_SH", str(h))
+        rc, q, it, stt, u = _solve(sce, k, precision, f=1.0)
+        assert rc == 0 and np.all(stt == 0)
+        if ref is None:
+            ref = (q, it, u)
+            Q = np.array([odarcy.solve_qois(k[i].astype(np.float64), 1.0) for i in range(count)])
+            assert np.max(np.abs(q - Q)) < QOI_TOL
+        else:
+            assert np.max(np.abs(q - ref[0])) < 1e-12, h
+            assert np.max(np.abs(it - ref[1])) <= 1, h
+            assert np.max(np.abs(u - ref[2])) < 1e-11, h
+
+
+def test_tile_autotuner_picks_a_height(sce, monkeypatch):
+    monkeypatch.delenv("SCE_TILE_SH", raising=False)
+    n, count = 128, 4
+    k = _oracle_k(n, count, lam=0.05, seed=5, precision=32)
+    before = _solve(sce, k, 32, f=1.0)
+    h = sce.darcy_autotune_tiles(n, 32, count=64, reps=1)
+    assert h in (16, 24, 32, 48)
+    after = _solve(sce, k, 32, f=1.0)
+    assert np.max(np.abs(before[1] - after[1])) < 1e-12
+    assert np.max(np.abs(before[4] - after[4])) < 1e-11
+    with pytest.raises(sce.SceError):
+        sce.darcy_autotune_tiles(64, 32)

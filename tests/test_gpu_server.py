@@ -131,3 +131,64 @@ def test_tau_rule_equals_explicit_keep_counts(sce):
     assert a.info.keep_eff_fine == b.info.keep_eff_fine <= s - P
     a.close()
     b.close()
+
+
+def test_sliced_request_is_the_same_alone_and_in_the_mix(sce):
+    """A request above slice_vertices runs as sample slices (at most `slots`
+    in flight, each finished slice queueing the next behind newer requests):
+    its per-sample Y equals mlmc_level_estimate's, its sums equal the
+    slice-order sum of the slices' own level estimates, and both are the
+    same alone and among other requests."""
+    import torch
+    big = dict(nu=0.5, lam=0.05, sigma2=1.0, n=64, level=2, count=23, first_sample=5)
+    per = (3 * 65 * 65) // (65 * 65)          # slice_vertices = 3 (n+1)^2: 3 samples a slice
+    _, _, Y_ref = _alone(sce, big)
+    want = np.zeros(5)
+    for k0 in range(0, big["count"], per):
+        out, st, _ = _alone(sce, {**big, "first_sample": big["first_sample"] + k0,
+                                  "count": min(per, big["count"] - k0)})
+        assert st == 0
+        want += [out.N, out.sumY, out.sumY2, out.sumQf, out.sumQf2]
+    got = []
+    for mix in ([], MIX[:5]):
+        with sce.Server(slots=3, precision=32, rtol=1e-10, maxit=2000,
+                        slice_vertices=3 * 65 * 65) as srv:
+            Y = torch.full((big["count"],), float("nan"), dtype=torch.float64, device="cuda")
+            t = srv.submit({**big, "Y": Y})
+            others = [srv.submit(r) for r in mix]
+            r = srv.wait(t)
+            for o in others:
+                assert srv.wait(o).status == 0
+            stats = srv.stats()
+        torch.cuda.synchronize()
+        assert r.status == 0 and stats["reserved"] == 0 and stats["queued"] == 0
+        s = r.sums
+        got.append(((s.N, s.sumY, s.sumY2, s.sumQf, s.sumQf2), Y.clone()))
+        assert torch.equal(Y, Y_ref)
+    assert got[0][0] == got[1][0] == tuple(want)
+
+
+def test_injected_oom_fails_one_request_and_the_server_recovers(sce):
+    """Host-side fault injection: the library's next allocation fails with
+    CE_ERR_OOM inside a request's level estimate.  That request reports it,
+    its reservation is released, and the following request (same embedding,
+    now cached) is served and equals the result alone."""
+    import torch
+    r = dict(nu=0.5, lam=0.05, sigma2=1.0, n=64, level=2, count=6)
+    out, st, Y_ref = _alone(sce, r)
+    with sce.Server(slots=1, precision=32, rtol=1e-10, maxit=2000) as srv:
+        assert srv.wait(srv.submit(r)).status == 0          # embedding now resident
+        sce.sce_test_fail_allocs(1)
+        try:
+            bad = srv.wait(srv.submit(r))
+        finally:
+            sce.sce_test_fail_allocs(0)
+        assert bad.status == sce.CE_ERR_OOM
+        assert srv.stats()["reserved"] == 0
+        Y = torch.full((r["count"],), float("nan"), dtype=torch.float64, device="cuda")
+        good = srv.wait(srv.submit({**r, "Y": Y}))
+        stats = srv.stats()
+    torch.cuda.synchronize()
+    assert good.status == 0 and torch.equal(Y, Y_ref)
+    assert good.sums.sumY == out.sumY
+    assert stats["completed"] == 3 and stats["reserved"] == 0

@@ -287,3 +287,22 @@ def test_cost_versus_eps_chooses_the_finest_level(drv):
     assert len(out[0]["N"]) == 5 and len(out[1]["N"]) == 6
     assert out[0]["mc_seconds"] == pytest.approx(out[0]["mc_N"] * 1e-6 * 4.0 ** 4)
     assert [o["L"] for o in drv.cost_versus_eps(stats, [0.01])] == [5]
+
+
+def test_run_adaptive_respects_the_minimum_finest_level(drv):
+    """Levels whose means vanish by accident (pre-asymptotic) would end the
+    loop at once; with L_min the loop goes on to at least L_min and the bias
+    is then estimated in the asymptotic range."""
+    rng = np.random.default_rng(2)
+    means = [0.6, 1e-7, 1e-7, 0.004, 0.002, 0.001, 0.0005]
+
+    def make_runner(level, finest):
+        return FakeRunner(level, means[level], 1e-12, 1e-6 * 4.0 ** level, rng)
+
+    eps = 2e-3
+    early = drv.run_adaptive(make_runner, eps, L0=2, L_max=6, pilot=50, alpha=1.0,
+                             bias_levels=1, restart_previous_finest=False)
+    assert len(early.levels) == 3
+    res = drv.run_adaptive(make_runner, eps, L0=2, L_max=6, pilot=50, alpha=1.0, bias_levels=1,
+                           restart_previous_finest=False, L_min=5)
+    assert len(res.levels) == 6 and res.bias == pytest.approx(0.001, rel=1e-3)
