@@ -325,10 +325,10 @@ int mlmc_estimate_levels_persistent(const darcy_problem *p, uint64_t seed, int q
  * requests run concurrently.  Embedding set-ups are cached by (covariance,
  * n, padding, smoothing rule) and stay resident; unused ones are evicted
  * least-recently-used beyond max_embeddings.  A large request (above
- * slice_vertices) is cut into consecutive sample slices: at most `slots` of
- * its slices are queued or running at a time, and each finished slice puts
- * the next one at the back of the queue, so requests that arrive meanwhile
- * are served between them.  The slices' level sums are added in slice order, so
+ * slice_vertices) is cut into consecutive sample slices: at most two of its
+ * slices are queued or running at a time, and each finished slice puts the
+ * next one at the back of the queue, so requests that arrive meanwhile are
+ * served between them.  The slices' level sums are added in slice order, so
  * a request's results do not depend on the other requests in the server:
  * they are bit-identical alone and in any mix (and, unsliced, bit-identical
  * to mlmc_level_estimate on its own).  Multigrid hierarchies are built per
@@ -438,6 +438,21 @@ int mlmc_level_estimate_qmc(ce_qmc_t q, const darcy_problem *p, uint64_t seed, u
                             uint32_t shift, uint32_t first_point, int count, int qoi_index,
                             mlmc_level_sums *out, double *Y, double *qoi_f, double *qoi_c,
                             void *stream);
+
+/*
+ * Cached solvers and graphs.  With the environment variable SCE_GRAPHS=1 a
+ * batched solve (darcy_solve_batch, and the solves of the MLMC calls) on a
+ * stream other than the legacy default stream keeps its device buffers and a
+ * CUDA graph of four captured CG iterations after it returns, in a pool of at
+ * most 16 idle solvers per precision; a later solve with the same plan (sample
+ * count, grid, window heights) on the same device takes them over and replays
+ * the graph instead of launching the iterations one by one (the graph is
+ * captured once per solver, on its first solve).  Results are identical to
+ * the uncached path.  The pool holds device memory until this call frees it
+ * (stream-ordered on `stream`, which it synchronises).  Not used while a
+ * stream capture is in progress or the launch profiler is on.
+ */
+int darcy_solver_cache_clear(void *stream);
 
 /*
  * darcy_autotune_tiles -- picks the window height (16, 24, 32 or 48 rows; the

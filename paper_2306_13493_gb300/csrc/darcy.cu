@@ -33,6 +33,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <type_traits>
 #include <utility>
@@ -330,11 +331,33 @@ __global__ void rupdate_kernel(T *__restrict__ r, const T *__restrict__ q,
     if (!act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
     T acc = T(0);
-    FOR_VERT_C(V, VPT, vpt) {
-        const long long g = s * V + v;
-        const T rv = r[g] - a * q[g];
-        r[g] = rv;
-        acc += rv * rv;
+    if constexpr (VPT > 0) {
+        // every load of the thread first (all in flight together), then the
+        // updates and stores in the same order as the run-time loop
+        T rv[VPT], qv[VPT];
+        const long long v0 = (long long)blockIdx.x * (blockDim.x * VPT) + threadIdx.x;
+#pragma unroll
+        for (int e = 0; e < VPT; ++e) {
+            const long long v = v0 + (long long)e * blockDim.x;
+            rv[e] = v < V ? r[s * V + v] : T(0);
+            qv[e] = v < V ? q[s * V + v] : T(0);
+        }
+#pragma unroll
+        for (int e = 0; e < VPT; ++e) {
+            const long long v = v0 + (long long)e * blockDim.x;
+            if (v < V) {
+                const T t = rv[e] - a * qv[e];
+                r[s * V + v] = t;
+                acc += t * t;
+            }
+        }
+    } else {
+        FOR_VERT_C(V, VPT, vpt) {
+            const long long g = s * V + v;
+            const T rv = r[g] - a * q[g];
+            r[g] = rv;
+            acc += rv * rv;
+        }
     }
     const T tot = block_sum(acc, sh);
     if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
@@ -426,13 +449,13 @@ __device__ __forceinline__ double cx_at(const OuterF &o, long long i) {
 // u = the bilinear prolongation of uc, the FP64 solution of the same field on
 // the n/2-cell grid (the first iterate of nested iteration; the Dirichlet
 // columns stay exact, means of equal values)
-template <class O>
+template <class O, int VPT = 0>
 __global__ void set_u_kernel(O o, const double *__restrict__ uc, int n, int vpt) {
     const int s = blockIdx.y;
     const long long V = (long long)(n + 1) * (n + 1);
     const int w = n + 1, nc = n / 2, wc = nc + 1;
     const double *c = uc + (long long)s * wc * wc;
-    FOR_VERT(V, vpt) {
+    FOR_VERT_C(V, VPT, vpt) {
         const int j = v / w, i = v - j * w;
         const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
         const double u = 0.25 * ((c[j0 * wc + i0] + c[j0 * wc + i1]) +
@@ -468,7 +491,7 @@ struct Load {
 
 // r = F - A u (unknowns; 0 on Dirichlet columns) stored as the working-precision
 // right-hand side rin of the correction equation; partial sums of |r|^2.
-template <typename T, class O>
+template <typename T, class O, int VPT = 0>
 __global__ void outer_residual_kernel(O o, Load F, int n, int vpt, T *__restrict__ rin,
                                       double *__restrict__ part, int nblk,
                                       const int *__restrict__ act) {
@@ -478,7 +501,7 @@ __global__ void outer_residual_kernel(O o, Load F, int n, int vpt, T *__restrict
     const long long V = (long long)(n + 1) * (n + 1);
     const int w = n + 1;
     T acc = T(0);
-    FOR_VERT(V, vpt) {
+    FOR_VERT_C(V, VPT, vpt) {
         const int j = v / w, i = v - j * w;
         const long long g = s * V + v;
         T rv = T(0);
@@ -540,7 +563,7 @@ __global__ void initial_residual_kernel(O o, Load F, int n, int vpt, T *__restri
 // u += d + alpha p: the inner solve's correction with its last deferred CG
 // update (alpha and the p array ppar of the sample's last iteration; alpha = 0
 // when none is pending).  float-float + float on the mixed path.
-template <typename T, class O>
+template <typename T, class O, int VPT = 0>
 __global__ void outer_update_kernel(O o, const T *__restrict__ d, const T *__restrict__ p0,
                                     const T *__restrict__ p1, const double *__restrict__ alpha,
                                     const int *__restrict__ ppar, int n, int vpt,
@@ -550,7 +573,29 @@ __global__ void outer_update_kernel(O o, const T *__restrict__ d, const T *__res
     const long long V = (long long)(n + 1) * (n + 1);
     const T a = (T)alpha[s];
     const T *p = ppar[s] ? p1 : p0;
-    FOR_VERT(V, vpt) {
+    if constexpr (VPT > 0 && std::is_same<O, OuterF>::value) {
+        // every load of the thread first, then the updates
+        float2 uv[VPT];
+        T dv[VPT];
+        const long long v0 = (long long)blockIdx.x * (blockDim.x * VPT) + threadIdx.x;
+#pragma unroll
+        for (int e = 0; e < VPT; ++e) {
+            const long long v = v0 + (long long)e * blockDim.x;
+            const long long g = s * V + (v < V ? v : 0);
+            uv[e] = o.u[g];
+            dv[e] = d[g] + a * p[g];
+        }
+#pragma unroll
+        for (int e = 0; e < VPT; ++e) {
+            const long long v = v0 + (long long)e * blockDim.x;
+            if (v < V) {
+                const ff r = ff_add_f(ff{uv[e].x, uv[e].y}, (float)dv[e]);
+                o.u[s * V + v] = make_float2(r.hi, r.lo);
+            }
+        }
+        return;
+    }
+    FOR_VERT_C(V, VPT, vpt) {
         const long long g = s * V + v;
         const T dv = d[g] + a * p[g];
         if constexpr (std::is_same<O, OuterF>::value) {
@@ -775,6 +820,75 @@ struct Solver {
         }
     }
 
+    // levels and launch plan of an n0-cell hierarchy of `cnt` samples (no allocation)
+    void init_plan(int n0, int cnt) {
+        count = cnt;
+        int lv = 0;
+        for (int nn = n0; nn >= 2; nn /= 2) {
+            n[lv] = nn;
+            ln[lv] = launch_for(nn);
+            ++lv;
+        }
+        nlev = lv;
+        const char *e = getenv("SCE_MG_FUSED");
+        fused = !(e && atoi(e) == 0);
+        plan_fused();
+    }
+
+    // what a cached solver must match to be reused: samples, grid and plan
+    std::vector<int> signature() const {
+        std::vector<int> sg{count, n[0], fused ? 1 : 0, Lt, v64 ? 1 : 0};
+        for (int L = 0; L < Lt; ++L) sg.push_back(sh[L]);
+        return sg;
+    }
+
+    int alloc_all() {
+        for (int L = 0; L < nlev; ++L) {
+            const size_t cnt = (size_t)count * ln[L].V;
+            SCE_TRY(alloc(&cx[L], cnt));
+            SCE_TRY(alloc(&cy[L], cnt));
+            SCE_TRY(alloc(&b[L], cnt));
+            SCE_TRY(alloc(&z[L], cnt));
+        }
+        const size_t c0 = (size_t)count * ln[0].V;
+        SCE_TRY(alloc(&d, c0));
+        SCE_TRY(alloc(&p, c0));
+        SCE_TRY(alloc(&p2, c0));
+        SCE_TRY(alloc(&q, c0));
+        if constexpr (sizeof(T) == 4) {
+            SCE_TRY(alloc(&uff, c0));
+            SCE_TRY(alloc(&cxl, c0));
+            SCE_TRY(alloc(&cyl, c0));
+        } else {
+            SCE_TRY(alloc(&u64, c0));
+        }
+        if (fused)
+            for (int L = 0; L < Lt; ++L) SCE_TRY(alloc(&zpre[L], (size_t)count * ln[L].V));
+        const int nblk_part = std::max(ln[0].nblk, rz_blocks());
+        SCE_TRY(alloc(&part, (size_t)count * nblk_part));
+        SCE_TRY(alloc(&part2, (size_t)count * nblk_part));
+        double *scal = nullptr;
+        SCE_TRY(alloc(&scal, (size_t)count * 9));
+        sc.rz = scal;
+        sc.pq = scal + count;
+        sc.rr = scal + 2 * count;
+        sc.rr0 = scal + 3 * count;
+        sc.alpha = scal + 4 * count;
+        sc.beta = scal + 5 * count;
+        sc.orr = scal + 6 * count;
+        sc.orr0 = scal + 7 * count;
+        sc.thr = scal + 8 * count;
+        int *ints = nullptr;
+        SCE_TRY(alloc(&ints, (size_t)count * 4 + 4));
+        sc.act_out = ints;
+        sc.act_in = ints + count;
+        sc.iters = ints + 2 * count;
+        sc.ppar = ints + 3 * count;
+        misc = ints + 4 * count;
+        sc.counter = misc;
+        return CE_OK;
+    }
+
     // launches of the tiled kernels of window height SH
     unsigned tile_attr_mask = 0;
     template <int SH>
@@ -889,49 +1003,127 @@ struct Solver {
     }
 };
 
+// ---- idle solvers of earlier calls, with their captured CG iterations
+// (SCE_GRAPHS=1).  A solve takes an idle solver of the same plan (samples,
+// grid, window heights) or builds one; a successful solve puts it back, a
+// failed one destroys it.  At most kPoolMax idle solvers are kept (the least
+// recently used is freed); darcy_solver_cache_clear frees them all.
+constexpr int kPoolMax = 16;
+
+static bool solver_graphs_on(cudaStream_t st) {
+    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread || sce_prof_on())
+        return false;
+    const char *e = getenv("SCE_GRAPHS");
+    if (!(e && atoi(e) != 0)) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+
+template <typename T>
+struct SolverPool {
+    std::mutex mu;
+    std::vector<std::pair<int, Solver<T> *>> idle;   // (device, solver), most recent last
+
+    Solver<T> *take(const std::vector<int> &sig) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t i = idle.size(); i-- > 0;) {
+            if (idle[i].first == dev && idle[i].second->signature() == sig) {
+                Solver<T> *s = idle[i].second;
+                idle.erase(idle.begin() + (long)i);
+                return s;
+            }
+        }
+        return nullptr;
+    }
+    void give(Solver<T> *s, cudaStream_t st) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::vector<Solver<T> *> victims;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            idle.emplace_back(dev, s);
+            while ((int)idle.size() > kPoolMax) {
+                victims.push_back(idle.front().second);
+                idle.erase(idle.begin());
+            }
+        }
+        for (Solver<T> *v : victims) {   // their last solve has finished (solves synchronise)
+            v->st = st;
+            delete v;
+        }
+    }
+    int clear(cudaStream_t st) {
+        std::vector<std::pair<int, Solver<T> *>> all;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            all.swap(idle);
+        }
+        int cur = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess) return CE_ERR_CUDA;
+        for (auto &pr : all) {
+            cudaSetDevice(pr.first);
+            pr.second->st = pr.first == cur ? st : nullptr;
+            delete pr.second;
+        }
+        cudaSetDevice(cur);
+        return CE_OK;
+    }
+};
+
+template <typename T>
+SolverPool<T> &solver_pool() {
+    static SolverPool<T> pool;
+    return pool;
+}
+
+// Owns the solver of one solve: back to the pool on success (cached mode),
+// destroyed otherwise.
+template <typename T>
+struct SolverLease {
+    bool cached;
+    cudaStream_t st;
+    Solver<T> *s = nullptr;
+    bool ok = false;
+    SolverLease(bool c, cudaStream_t stream) : cached(c), st(stream) {}
+    ~SolverLease() {
+        if (!s) return;
+        if (cached && ok) solver_pool<T>().give(s, st);
+        else delete s;
+    }
+};
+
 template <typename T, typename Tk>
 static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
                          int *n_failed_out, int qmask, const double *u_init) {
-    Solver<T> S;
+    // the solver's buffers, and with cached graphs the captured iterations,
+    // come from the pool of idle solvers of the same plan when there is one
+    const bool cached = solver_graphs_on(st);
+    SolverLease<T> lease(cached, st);
+    {
+        auto fresh = std::make_unique<Solver<T>>();
+        fresh->st = st;
+        fresh->init_plan(p->n, count);
+        Solver<T> *hit = cached ? solver_pool<T>().take(fresh->signature()) : nullptr;
+        if (hit) {
+            lease.s = hit;
+        } else {
+            SCE_TRY(fresh->alloc_all());
+            lease.s = fresh.release();
+        }
+    }
+    Solver<T> &S = *lease.s;
     S.st = st;
-    S.count = count;
     const int n0 = p->n;
-    int lv = 0;
-    for (int nn = n0; nn >= 2; nn /= 2) {
-        S.n[lv] = nn;
-        S.ln[lv] = launch_for(nn);
-        ++lv;
-    }
-    S.nlev = lv;
     const long long V0 = S.ln[0].V;
-    for (int L = 0; L < S.nlev; ++L) {
-        const size_t cnt = (size_t)count * S.ln[L].V;
-        SCE_TRY(S.alloc(&S.cx[L], cnt));
-        SCE_TRY(S.alloc(&S.cy[L], cnt));
-        SCE_TRY(S.alloc(&S.b[L], cnt));
-        SCE_TRY(S.alloc(&S.z[L], cnt));
-    }
     const size_t c0 = (size_t)count * V0;
-    SCE_TRY(S.alloc(&S.d, c0));
-    SCE_TRY(S.alloc(&S.p, c0));
-    SCE_TRY(S.alloc(&S.p2, c0));
-    // both p arrays start finite (the first fused pass multiplies p_in by 0)
-    SCE_CUDA(cudaMemsetAsync(S.p, 0, c0 * sizeof(T), st));
-    SCE_CUDA(cudaMemsetAsync(S.p2, 0, c0 * sizeof(T), st));
-    SCE_TRY(S.alloc(&S.q, c0));
     constexpr bool mixed = sizeof(T) == 4;
     using O = std::conditional_t<mixed, OuterF, OuterD>;
     O o{};
-    if constexpr (mixed) {
-        SCE_TRY(S.alloc(&S.uff, c0));
-        SCE_TRY(S.alloc(&S.cxl, c0));
-        SCE_TRY(S.alloc(&S.cyl, c0));
-        o = OuterF{S.uff, S.cx[0], S.cy[0], S.cxl, S.cyl};
-    } else {
-        SCE_TRY(S.alloc(&S.u64, c0));
-        o = OuterD{S.u64, S.cx[0], S.cy[0]};
-    }
+    if constexpr (mixed) o = OuterF{S.uff, S.cx[0], S.cy[0], S.cxl, S.cyl};
+    else o = OuterD{S.u64, S.cx[0], S.cy[0]};
     Load F{};
     {
         const double h2_6 = p->f / (6.0 * (double)n0 * (double)n0);
@@ -942,36 +1134,10 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
             F.Ff[r].lo = (float)(F.Fd[r] - (double)F.Ff[r].hi);
         }
     }
-    {
-        const char *e = getenv("SCE_MG_FUSED");
-        S.fused = !(e && atoi(e) == 0);
-    }
-    S.plan_fused();
-    if (S.fused)
-        for (int L = 0; L < S.Lt; ++L) SCE_TRY(S.alloc(&S.zpre[L], (size_t)count * S.ln[L].V));
-    const int nblk_part = std::max(S.ln[0].nblk, S.rz_blocks());
-    SCE_TRY(S.alloc(&S.part, (size_t)count * nblk_part));
-    SCE_TRY(S.alloc(&S.part2, (size_t)count * nblk_part));
-    double *scal = nullptr;
-    SCE_TRY(S.alloc(&scal, (size_t)count * 9));
-    S.sc.rz = scal;
-    S.sc.pq = scal + count;
-    S.sc.rr = scal + 2 * count;
-    S.sc.rr0 = scal + 3 * count;
-    S.sc.alpha = scal + 4 * count;
-    S.sc.beta = scal + 5 * count;
-    S.sc.orr = scal + 6 * count;
-    S.sc.orr0 = scal + 7 * count;
-    S.sc.thr = scal + 8 * count;
-    int *ints = nullptr;
-    SCE_TRY(S.alloc(&ints, (size_t)count * 4 + 4));
-    S.sc.act_out = ints;
-    S.sc.act_in = ints + count;
-    S.sc.iters = ints + 2 * count;
-    S.sc.ppar = ints + 3 * count;
-    S.misc = ints + 4 * count;
-    S.sc.counter = S.misc;
-    SCE_CUDA(cudaMemsetAsync(ints, 0, ((size_t)count * 4 + 4) * sizeof(int), st));
+    // both p arrays start finite (the first fused pass multiplies p_in by 0)
+    SCE_CUDA(cudaMemsetAsync(S.p, 0, c0 * sizeof(T), st));
+    SCE_CUDA(cudaMemsetAsync(S.p2, 0, c0 * sizeof(T), st));
+    SCE_CUDA(cudaMemsetAsync(S.sc.act_out, 0, ((size_t)count * 4 + 4) * sizeof(int), st));
 
     const Launch &l0 = S.ln[0];
     const dim3 g0 = S.grid(0);
@@ -1011,11 +1177,16 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     // a given first iterate: the stopping rule stays relative to the lifting's
     // residual (orr0 above); refinement starts from u_init's residual
     if (u_init) {
-        set_u_kernel<<<g0, l0.tpb, 0, st>>>(o, u_init, n0, l0.vpt);
+        if (l0.vpt == 8) set_u_kernel<O, 8><<<g0, l0.tpb, 0, st>>>(o, u_init, n0, 8);
+        else set_u_kernel<O><<<g0, l0.tpb, 0, st>>>(o, u_init, n0, l0.vpt);
         {
             SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 24.0));
-            outer_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(o, F, n0, l0.vpt, S.b[0], S.part,
-                                                            l0.nblk, S.sc.act_out);
+            if (l0.vpt == 8)
+                outer_residual_kernel<T, O, 8><<<g0, l0.tpb, 0, st>>>(
+                    o, F, n0, 8, S.b[0], S.part, l0.nblk, S.sc.act_out);
+            else
+                outer_residual_kernel<T, O><<<g0, l0.tpb, 0, st>>>(
+                    o, F, n0, l0.vpt, S.b[0], S.part, l0.nblk, S.sc.act_out);
         }
         SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
         S.reduce(RED_ORR, S.sc.act_out, rtol2, in_rel2);
@@ -1070,23 +1241,12 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         S.par ^= 1;
         return CE_OK;
     };
-    // CUDA graph of check_every iterations (head + tail each), replayed, when
-    // SCE_GRAPHS=1: not on the legacy default stream or with the launch
-    // profiler on.  Off by default: each solve captures and instantiates its
-    // own graph, and on the oscillatory workload that costs more than the
-    // launches it saves (461K vs 478K samples/s).  A failed capture falls back
-    // to stream launches.
-    bool use_graph = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread &&
-                     !sce_prof_on();
-    {
-        const char *e = getenv("SCE_GRAPHS");
-        use_graph = use_graph && e && atoi(e) != 0;
-    }
-    if (use_graph) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
-            use_graph = false;
-    }
+    // CUDA graph of check_every iterations (head + tail each), captured once
+    // per cached solver and replayed by every later solve of the same plan
+    // (SCE_GRAPHS=1: not on the legacy default stream, during a capture or
+    // with the launch profiler on).  A failed capture falls back to stream
+    // launches.
+    bool use_graph = cached;
     auto capture_graph = [&]() -> int {
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
@@ -1158,14 +1318,22 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         {
             // reads d, p and u, writes u (the last deferred CG update folded in)
             SceProf pr(KP_OUTER_UPD, st, S.vb(0, 2.0, 16.0));
-            outer_update_kernel<T><<<g0, l0.tpb, 0, st>>>(o, S.d, S.p, S.p2, S.sc.alpha,
-                                                          S.sc.ppar, n0, l0.vpt, S.sc.act_out);
+            if (l0.vpt == 8)
+                outer_update_kernel<T, O, 8><<<g0, l0.tpb, 0, st>>>(
+                    o, S.d, S.p, S.p2, S.sc.alpha, S.sc.ppar, n0, 8, S.sc.act_out);
+            else
+                outer_update_kernel<T, O><<<g0, l0.tpb, 0, st>>>(
+                    o, S.d, S.p, S.p2, S.sc.alpha, S.sc.ppar, n0, l0.vpt, S.sc.act_out);
         }
         {
             // reads u (8 B) and both conductances (16 B: FP64, or FP32 hi + lo), writes rin
             SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 24.0));
-            outer_residual_kernel<T><<<g0, l0.tpb, 0, st>>>(o, F, n0, l0.vpt, S.b[0], S.part,
-                                                            l0.nblk, S.sc.act_out);
+            if (l0.vpt == 8)
+                outer_residual_kernel<T, O, 8><<<g0, l0.tpb, 0, st>>>(
+                    o, F, n0, 8, S.b[0], S.part, l0.nblk, S.sc.act_out);
+            else
+                outer_residual_kernel<T, O><<<g0, l0.tpb, 0, st>>>(
+                    o, F, n0, l0.vpt, S.b[0], S.part, l0.nblk, S.sc.act_out);
         }
         SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
         S.reduce(RED_ORR, S.sc.act_out, rtol2, in_rel2);
@@ -1201,10 +1369,19 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         max_iters_out[0] = hm[1];
         max_iters_out[1] = hm[2];
     }
+    lease.ok = true;
     return hm[0] > 0 ? CE_ERR_NOT_CONVERGED : CE_OK;
 }
 
 }  // namespace
+
+extern "C" int darcy_solver_cache_clear(void *stream) {
+    const cudaStream_t st = as_stream(stream);
+    const int a = solver_pool<float>().clear(st);
+    const int b = solver_pool<double>().clear(st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CE_ERR_CUDA;
+    return a != CE_OK ? a : b;
+}
 
 int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,

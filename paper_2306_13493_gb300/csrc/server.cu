@@ -70,6 +70,10 @@ struct Job {
 };
 
 constexpr int kMaxHeadSkips = 8;
+// queued or running slices of one request: with every slot open to them, a
+// large request's slices held all slots and small requests waited a slice
+// (measured p99 of small requests 172 ms against 56 ms with two)
+constexpr int kSlicesInFlight = 2;
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -379,10 +383,9 @@ extern "C" int sce_server_submit(sce_server_t S, const sce_request *r, uint64_t 
         j.res.t_submit = S->now();
         S->jobs.emplace(id, j);
         if (sliced) {
-            // up to `slots` slices queued or running: an idle server gives a large
-            // request every slot, and each finished slice queues the next one
-            // behind the requests that arrived meanwhile
-            for (int k = 0; k < std::min(S->cfg.slots, j.nslices); ++k) S->enqueue_slice(id);
+            // each finished slice queues the next one behind the requests that
+            // arrived meanwhile
+            for (int k = 0; k < std::min(kSlicesInFlight, j.nslices); ++k) S->enqueue_slice(id);
         } else {
             S->queue.push_back(id);
         }

@@ -197,6 +197,7 @@ _SIGS = {
     "darcy_autotune_tiles": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int)]),
     "sce_test_fail_allocs": (None, [ctypes.c_int]),
+    "darcy_solver_cache_clear": (ctypes.c_int, [_P]),
     "sce_peak_fma": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "sce_peak_l2": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _P, _P]),
     "sce_profile_enable": (None, [ctypes.c_int]),
@@ -681,3 +682,8 @@ def sce_peak_l2(buf, reps, blocks, out, stream=None):
 def sce_test_fail_allocs(count):
     """Test hook: the next `count` library allocations fail with CE_ERR_OOM."""
     load().sce_test_fail_allocs(int(count))
+
+
+def darcy_solver_cache_clear(stream=None):
+    """Frees the idle solvers (and their graphs) kept under SCE_GRAPHS=1."""
+    _check(load().darcy_solver_cache_clear(_stream(stream)), "darcy_solver_cache_clear")

@@ -159,7 +159,8 @@ def test_graph_replay_matches_stream_launches(sce, precision, maxit, monkeypatch
     n, count = 128, 5
     k_np = _oracle_k(n, count, lam=0.05, seed=4, precision=precision)
     out = []
-    for graphs in ("1", "0"):
+    # the second graph solve takes over the first one's cached solver and graph
+    for graphs in ("1", "1", "0"):
         monkeypatch.setenv("SCE_GRAPHS", graphs)
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
@@ -172,11 +173,49 @@ def test_graph_replay_matches_stream_launches(sce, precision, maxit, monkeypatch
                                        stream=s.cuda_stream, allow_not_converged=True)
         s.synchronize()
         out.append((rc, qoi.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()))
-    (rc1, q1, i1, s1), (rc0, q0, i0, s0) = out
-    assert rc1 == rc0
-    assert np.array_equal(q1, q0) and np.array_equal(i1, i0) and np.array_equal(s1, s0)
-    if maxit == 6:
-        assert rc1 == sce.CE_ERR_NOT_CONVERGED and np.all(i1 <= 6)
+    sce.darcy_solver_cache_clear()
+    (rc0, q0, i0, s0) = out[-1]
+    for rc1, q1, i1, s1 in out[:-1]:
+        assert rc1 == rc0
+        assert np.array_equal(q1, q0) and np.array_equal(i1, i0) and np.array_equal(s1, s0)
+        if maxit == 6:
+            assert rc1 == sce.CE_ERR_NOT_CONVERGED and np.all(i1 <= 6)
+
+
+def test_cached_graphs_give_the_same_mlmc_step(sce, monkeypatch):
+    """Two all-levels MLMC calls with SCE_GRAPHS=1 (the second reusing every
+    level's cached solver and graph) give the per-sample Y and level sums of
+    plain stream launches bit for bit."""
+    import torch
+    import workloads
+    w = workloads.OSCILLATORY
+    embs = []
+    for l, n in ((2, 64), (3, 128), (4, 256)):
+        e0 = sce.ce_setup_embedding(0, w.nu, w.lam, w.sigma2, n, pad_mode=w.pad_mode)
+        kf, kc = workloads.keep_counts(e0.P, l == 4, True)
+        e0.close()
+        embs.append((l, sce.ce_setup_embedding(0, w.nu, w.lam, w.sigma2, n, pad_mode=w.pad_mode,
+                                               keep_fine=kf, keep_coarse=kc)))
+    runs = []
+    for graphs in ("1", "1", "0"):
+        monkeypatch.setenv("SCE_GRAPHS", graphs)
+        s = torch.cuda.Stream()
+        tasks = [{"emb": e, "level": l, "first_sample": 4, "count": c,
+                  "Y": torch.full((c,), float("nan"), dtype=torch.float64, device="cuda")}
+                 for (l, e), c in zip(embs, (9, 5, 3))]
+        sums, stats, st = sce.mlmc_estimate_levels(tasks, 3, qoi_index=1, f=1.0, rtol=1e-10,
+                                                   precision=32, max_concurrency=3,
+                                                   stream=s.cuda_stream)
+        s.synchronize()
+        assert st == 0
+        runs.append(([t["Y"].clone() for t in tasks],
+                     [(o.N, o.sumY, o.sumY2, o.sumQf, o.sumQf2, o.total_iters) for o in sums]))
+    sce.darcy_solver_cache_clear()
+    for Ys, sm in runs[:-1]:
+        assert sm == runs[-1][1]
+        assert all(torch.equal(a, b) for a, b in zip(Ys, runs[-1][0]))
+    for _, e in embs:
+        e.close()
 
 
 @pytest.mark.parametrize("precision", [32, 64])

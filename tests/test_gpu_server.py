@@ -134,8 +134,8 @@ def test_tau_rule_equals_explicit_keep_counts(sce):
 
 
 def test_sliced_request_is_the_same_alone_and_in_the_mix(sce):
-    """A request above slice_vertices runs as sample slices (at most `slots`
-    in flight, each finished slice queueing the next behind newer requests):
+    """A request above slice_vertices runs as sample slices (at most two in
+    flight, each finished slice queueing the next behind newer requests):
     its per-sample Y equals mlmc_level_estimate's, its sums equal the
     slice-order sum of the slices' own level estimates, and both are the
     same alone and among other requests."""
