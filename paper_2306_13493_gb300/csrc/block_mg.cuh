@@ -11,6 +11,15 @@
 namespace sce {
 
 constexpr int mg_levels(int n) { return n <= 2 ? 1 : 1 + mg_levels(n / 2); }
+
+// Barrier of an NT-thread block: a single-warp block (NT == 32) only needs
+// the warp's own synchronisation, which also orders its shared-memory
+// accesses.
+template <int NT>
+__device__ __forceinline__ void block_sync() {
+    if constexpr (NT == 32) __syncwarp();
+    else __syncthreads();
+}
 constexpr int mg_vof(int n) { return (n + 1) * (n + 1); }
 
 // Array k (0 cx, 1 cy, 2 b, 3 z) of level L of an N-cell hierarchy, all levels
@@ -38,7 +47,23 @@ __device__ __forceinline__ void block_half_sweep(const T *cx, const T *cy, const
     }
 }
 
-template <typename T, int N, int NT, class Lay, int L>
+template <typename T, int N, int NT, class Lay, int L, int WARP_N = 0>
+__device__ __forceinline__ void block_vcycle_level(T *base);
+
+// The V-cycle from level L down and back up: with WARP_N > 0 in a block of
+// more than one warp, the levels of at most WARP_N cells run on warp 0 alone
+// (warp synchronisation) while the other warps wait at one block barrier.
+template <typename T, int N, int NT, class Lay, int L, int WARP_N>
+__device__ __forceinline__ void block_vcycle_from(T *base) {
+    if constexpr (NT > 32 && WARP_N > 0 && (N >> L) <= WARP_N) {
+        if (threadIdx.x < 32) block_vcycle_level<T, N, 32, Lay, L, 0>(base);
+        __syncthreads();
+    } else {
+        block_vcycle_level<T, N, NT, Lay, L, WARP_N>(base);
+    }
+}
+
+template <typename T, int N, int NT, class Lay, int L, int WARP_N>
 __device__ __forceinline__ void block_vcycle_level(T *base) {
     constexpr int NL = mg_levels(N);
     constexpr int nL = N >> L;
@@ -46,30 +71,30 @@ __device__ __forceinline__ void block_vcycle_level(T *base) {
     T *b = base + Lay::off(L, 2), *z = base + Lay::off(L, 3);
     if constexpr (L == NL - 1) {
         if (threadIdx.x == 0) coarsest_solve(cx, cy, b, z);
-        __syncthreads();
+        block_sync<NT>();
     } else {
         constexpr int nc = nL / 2, wc = nc + 1, Vc = wc * wc, wL = nL + 1, VL = wL * wL;
         T *bc = base + Lay::off(L + 1, 2), *zc = base + Lay::off(L + 1, 3);
         block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
-        __syncthreads();
+        block_sync<NT>();
         block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
-        __syncthreads();
+        block_sync<NT>();
         for (int v = threadIdx.x; v < Vc; v += NT) {
             const int J = v / wc, I = v - J * wc;
             bc[v] = (I > 0 && I < nc) ? restrict_at(cx, cy, b, z, nL, I, J) : T(0);
             zc[v] = T(0);
         }
-        __syncthreads();
-        block_vcycle_level<T, N, NT, Lay, L + 1>(base);
+        block_sync<NT>();
+        block_vcycle_from<T, N, NT, Lay, L + 1, WARP_N>(base);
         for (int v = threadIdx.x; v < VL; v += NT) {
             const int j = v / wL, i = v - j * wL;
             if (i > 0 && i < nL) z[v] += prolong_at(zc, nc, i, j);
         }
-        __syncthreads();
+        block_sync<NT>();
         block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
-        __syncthreads();
+        block_sync<NT>();
         block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
-        __syncthreads();
+        block_sync<NT>();
     }
 }
 
@@ -87,7 +112,7 @@ __device__ __forceinline__ void block_coarsen(T *base) {
             cx[v] = gx;
             cy[v] = gy;
         }
-        __syncthreads();
+        block_sync<NT>();
         block_coarsen<T, N, NT, Lay, L + 1>(base);
     }
 }
@@ -95,12 +120,12 @@ __device__ __forceinline__ void block_coarsen(T *base) {
 // z = M^{-1} b on level 0 of the hierarchy laid out by Lay from `base`.
 // Symmetric: red-black Gauss-Seidel before the restriction, black-red after
 // the prolongation, exact solve on 2 cells.  All NT threads must call it.
-template <typename T, int N, int NT, class Lay>
+template <typename T, int N, int NT, class Lay, int WARP_N = 0>
 __device__ __forceinline__ void block_vcycle(T *base) {
     T *z = base + Lay::off(0, 3);
     for (int v = threadIdx.x; v < mg_vof(N); v += NT) z[v] = T(0);
-    __syncthreads();
-    block_vcycle_level<T, N, NT, Lay, 0>(base);
+    block_sync<NT>();
+    block_vcycle_from<T, N, NT, Lay, 0, WARP_N>(base);
 }
 
 }  // namespace sce

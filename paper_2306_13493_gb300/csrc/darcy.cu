@@ -935,6 +935,7 @@ struct Solver {
     }
 
     bool v64_attr_set = false;
+    int v64_warp_n = 0;   // SCE_V64_WARP_N: levels of at most 8 or 16 cells on one warp
     void v64_launch(bool want_rz) {
         if constexpr (sizeof(T) == 4) {
             TailPtrs tp{};
@@ -944,16 +945,27 @@ struct Solver {
             }
             constexpr size_t smem = v64_smem_bytes<T>();
             if (!v64_attr_set) {   // outside any stream capture (the first cycle is not captured)
-                sce_raise_smem_limit((const void *)mg_v64_kernel<T>, smem);
+                sce_raise_smem_limit((const void *)mg_v64_kernel<T, 0>, smem);
+                sce_raise_smem_limit((const void *)mg_v64_kernel<T, 8>, smem);
+                sce_raise_smem_limit((const void *)mg_v64_kernel<T, 16>, smem);
                 v64_attr_set = true;
+                const char *e = getenv("SCE_V64_WARP_N");
+                v64_warp_n = e ? atoi(e) : 0;
             }
             // b, cx, cy in, z out on the level; the conductances of the levels below in
             double tail_v = 0.0;
             for (int L = Lt + 1; L < nlev; ++L) tail_v += (double)ln[L].V;
             SceProf pr(KP_MG_V64, st, vb(Lt, 4.0) + (double)count * tail_v * 2.0 * sizeof(T));
-            mg_v64_kernel<T><<<count, V64_THREADS, smem, st>>>(cx[Lt], cy[Lt], b[Lt], z[Lt], tp,
-                                                              sc.act_in,
-                                                              want_rz ? part : nullptr);
+            double *pr_rz = want_rz ? part : nullptr;
+            if (v64_warp_n == 8)
+                mg_v64_kernel<T, 8><<<count, V64_THREADS, smem, st>>>(cx[Lt], cy[Lt], b[Lt], z[Lt],
+                                                                     tp, sc.act_in, pr_rz);
+            else if (v64_warp_n == 16)
+                mg_v64_kernel<T, 16><<<count, V64_THREADS, smem, st>>>(cx[Lt], cy[Lt], b[Lt],
+                                                                      z[Lt], tp, sc.act_in, pr_rz);
+            else
+                mg_v64_kernel<T, 0><<<count, V64_THREADS, smem, st>>>(cx[Lt], cy[Lt], b[Lt], z[Lt],
+                                                                     tp, sc.act_in, pr_rz);
         }
     }
 

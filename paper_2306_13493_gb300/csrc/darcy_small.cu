@@ -39,6 +39,9 @@ template <int N> struct SmallLayout {
 template <int NT, typename R>
 __device__ __forceinline__ R bsum1(R v, R *sh, int &par) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if constexpr (NT == 32) {   // one warp: the tree's result, from lane 0 to every lane
+        return __shfl_sync(0xffffffffu, v, 0);
+    }
     R *buf = sh + (par ? 16 : 0);
     par ^= 1;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
         cyl[v] = gy.lo;
         u[v] = make_float2(i == 0 ? 1.0f : 0.0f, 0.0f);
     }
-    __syncthreads();
+    block_sync<NT>();
     block_coarsen<float, N, NT, MG, 1>(mg);
 
     // load F = f h^2/6 x (triangles at the vertex): 3 on the rows j = 0, N, 6 inside
@@ -183,13 +186,13 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             const float beta = rz > 0.f ? rzn / rz : 0.f;
             rz = rzn;
             for (int v = tid; v < V; v += NT) p[v] = z[v] + beta * p[v];
-            __syncthreads();
+            block_sync<NT>();
         }
         for (int v = tid; v < V; v += NT) {
             const ff t = ff_add_f(ff{u[v].x, u[v].y}, d[v]);
             u[v] = make_float2(t.hi, t.lo);
         }
-        __syncthreads();
+        block_sync<NT>();
         orr = outer_residual();
     }
 
@@ -254,6 +257,13 @@ int launch_small(const darcy_problem *p, const float *k, int count, double *qoi,
 
 }  // namespace
 
+// n = 16: two warps per sample; SCE_SMALL16_NT=32 runs one warp per sample with
+// warp synchronisation only (measured slower: 7.89 vs 7.31 ms per sweep)
+static int small16_threads() {
+    const char *e = getenv("SCE_SMALL16_NT");
+    return e && atoi(e) == 32 ? 32 : 64;
+}
+
 // Largest n solved one block per sample (SCE_SMALL_MAX_N overrides; 0 = never).
 int sce_small_max_n() {
     const char *e = getenv("SCE_SMALL_MAX_N");
@@ -272,10 +282,10 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
     switch (p->n) {
         case 4: SCE_SMALL(4, 32); break;
         case 8: SCE_SMALL(8, 64); break;
-#ifndef SCE_SMALL_NT16
-#define SCE_SMALL_NT16 64
-#endif
-        case 16: SCE_SMALL(16, SCE_SMALL_NT16); break;
+        case 16:
+            if (small16_threads() == 32) SCE_SMALL(16, 32);
+            else SCE_SMALL(16, 64);
+            break;
         case 32: SCE_SMALL(32, 256); break;
         case 64: SCE_SMALL(64, 512); break;
         default: break;

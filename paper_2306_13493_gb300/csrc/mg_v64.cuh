@@ -40,8 +40,9 @@ constexpr size_t v64_smem_bytes() {
 }
 
 // tp.cx[i], tp.cy[i]: conductances of level 32 >> i (i = 0..4), per sample
-// contiguous.  part_rz: one slot per sample, or NULL.
-template <typename T>
+// contiguous.  part_rz: one slot per sample, or NULL.  WARP_N > 0: the levels
+// of at most WARP_N cells run on warp 0 alone (see block_vcycle_from).
+template <typename T, int WARP_N = 0>
 __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ z, TailPtrs tp, const int *__restrict__ act, double *__restrict__ part_rz) {
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     if (threadIdx.x <= NC) bc[threadIdx.x * WC + NC] = T(0);   // Dirichlet column I = 32
 
     // levels 32..2 (block_vcycle zeroes z of level 32 and synchronises first)
-    block_vcycle<T, NC, V64_THREADS, V64Lay>(base);
+    block_vcycle<T, NC, V64_THREADS, V64Lay, WARP_N>(base);
 
     // z += P zc: coarse columns lane, lane + 1 and rows 2 warp + {0, 1, 2}
     // (rows beyond 32 only feed elements outside the grid: read as 0)

@@ -255,3 +255,20 @@ def test_tile_autotuner_picks_a_height(sce, monkeypatch):
     assert np.max(np.abs(before[4] - after[4])) < 1e-11
     with pytest.raises(sce.SceError):
         sce.darcy_autotune_tiles(64, 32)
+
+
+@pytest.mark.parametrize("warp_n", ["8", "16"])
+def test_v64_coarse_levels_on_one_warp_give_identical_solves(sce, warp_n, monkeypatch):
+    """The fused n = 64 V-cycle with its levels of at most 8 or 16 cells run by
+    one warp (SCE_V64_WARP_N) computes every vertex as the block-wide version:
+    bit-identical solves on n = 64 and n = 128 (where the n = 64 level is a
+    coarse level of the hierarchy)."""
+    for n in (64, 128):
+        k = _oracle_k(n, 3, lam=0.05, seed=6, precision=32)
+        monkeypatch.setenv("SCE_V64_WARP_N", "0")
+        ref = _solve(sce, k, 32, f=1.0)
+        monkeypatch.setenv("SCE_V64_WARP_N", warp_n)
+        got = _solve(sce, k, 32, f=1.0)
+        assert ref[0] == got[0] == 0
+        assert np.array_equal(ref[1], got[1]) and np.array_equal(ref[2], got[2])
+        assert np.array_equal(ref[4], got[4])
