@@ -128,7 +128,7 @@ __device__ __forceinline__ T block_sum(T val, T *sh) {
 // Conductances of the fine grid.  FP64 path (T = double): FP64.  Mixed path
 // (T = float): float-float, hi to cx/cy (the operator of the FP32 inner
 // solve and of the hierarchy), lo to cxl/cyl.
-template <typename Tk, typename T>
+template <typename Tk, typename T, int VPT = 0>
 __global__ void cond_kernel(const Tk *__restrict__ k, int n, int vpt, T *__restrict__ cx,
                             T *__restrict__ cy, float *__restrict__ cxl,
                             float *__restrict__ cyl) {
@@ -136,7 +136,7 @@ __global__ void cond_kernel(const Tk *__restrict__ k, int n, int vpt, T *__restr
     const long long V = (long long)(n + 1) * (n + 1);
     const Tk *ks = k + s * V;
     const int w = n + 1;
-    FOR_VERT(V, vpt) {
+    FOR_VERT_C(V, VPT, vpt) {
         const int j = v / w, i = v - j * w;
         if constexpr (sizeof(T) == 4 && sizeof(Tk) == 4) {
             ff gx, gy;
@@ -154,7 +154,7 @@ __global__ void cond_kernel(const Tk *__restrict__ k, int n, int vpt, T *__restr
     }
 }
 
-template <typename T>
+template <typename T, int VPT = 0>
 __global__ void coarsen_kernel(const T *__restrict__ cxf, const T *__restrict__ cyf, int nf,
                                int vpt, T *__restrict__ cxc, T *__restrict__ cyc) {
     const int s = blockIdx.y;
@@ -162,7 +162,7 @@ __global__ void coarsen_kernel(const T *__restrict__ cxf, const T *__restrict__ 
     const long long Vf = (long long)(nf + 1) * (nf + 1), Vc = (long long)(nc + 1) * (nc + 1);
     const T *ax = cxf + s * Vf, *ay = cyf + s * Vf;
     const int wc = nc + 1;
-    FOR_VERT(Vc, vpt) {
+    FOR_VERT_C(Vc, VPT, vpt) {
         const int J = v / wc, I = v - J * wc;
         T gx, gy;
         coarsen_at(ax, ay, nf, I, J, &gx, &gy);
@@ -1056,9 +1056,18 @@ struct SolverPool {
         {
             std::lock_guard<std::mutex> lk(mu);
             idle.emplace_back(dev, s);
-            while ((int)idle.size() > kPoolMax) {
-                victims.push_back(idle.front().second);
-                idle.erase(idle.begin());
+            // at most kPoolMax idle solvers of this device: the least recently
+            // used of them are freed (on this device, stream-ordered on st)
+            int mine = 0;
+            for (auto &pr : idle) mine += pr.first == dev;
+            for (size_t i = 0; i < idle.size() && mine > kPoolMax;) {
+                if (idle[i].first == dev) {
+                    victims.push_back(idle[i].second);
+                    idle.erase(idle.begin() + (long)i);
+                    --mine;
+                } else {
+                    ++i;
+                }
             }
         }
         for (Solver<T> *v : victims) {   // their last solve has finished (solves synchronise)
@@ -1156,13 +1165,21 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     // operator and hierarchy
     {
         SceProf pr(KP_COND, st, S.vb(0, 2.0, sizeof(Tk) + (mixed ? 8.0 : 0.0)));
-        cond_kernel<Tk, T><<<g0, l0.tpb, 0, st>>>(k, n0, l0.vpt, S.cx[0], S.cy[0], S.cxl, S.cyl);
+        if (l0.vpt == 8)
+            cond_kernel<Tk, T, 8><<<g0, l0.tpb, 0, st>>>(k, n0, 8, S.cx[0], S.cy[0], S.cxl, S.cyl);
+        else
+            cond_kernel<Tk, T><<<g0, l0.tpb, 0, st>>>(k, n0, l0.vpt, S.cx[0], S.cy[0], S.cxl,
+                                                      S.cyl);
     }
     SCE_CUDA(cudaGetLastError());
     for (int L = 1; L < S.nlev; ++L) {
         SceProf pr(KP_COARSEN, st, S.vb(L - 1, 2.0) + S.vb(L, 2.0));
-        coarsen_kernel<T><<<S.grid(L), S.ln[L].tpb, 0, st>>>(S.cx[L - 1], S.cy[L - 1], S.n[L - 1],
-                                                             S.ln[L].vpt, S.cx[L], S.cy[L]);
+        if (S.ln[L].vpt == 8)
+            coarsen_kernel<T, 8><<<S.grid(L), S.ln[L].tpb, 0, st>>>(
+                S.cx[L - 1], S.cy[L - 1], S.n[L - 1], 8, S.cx[L], S.cy[L]);
+        else
+            coarsen_kernel<T><<<S.grid(L), S.ln[L].tpb, 0, st>>>(
+                S.cx[L - 1], S.cy[L - 1], S.n[L - 1], S.ln[L].vpt, S.cx[L], S.cy[L]);
     }
     SCE_CUDA(cudaGetLastError());
     {

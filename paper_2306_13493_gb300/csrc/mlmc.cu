@@ -295,16 +295,6 @@ static int estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
         release();
         return CE_ERR_CUDA;
     }
-    for (int i = 0; i < ntasks; ++i) {
-        for (int k = 0; k < (tasks[i].level > 0 ? 2 : 1); ++k) {
-            cudaStream_t &s = ss[2 * (size_t)i + k];
-            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaStreamWaitEvent(s, ev0, 0) != cudaSuccess) {
-                release();
-                return CE_ERR_CUDA;
-            }
-        }
-    }
     // largest levels first: they bound the makespan
     std::vector<int> order(ntasks);
     for (int i = 0; i < ntasks; ++i) order[i] = i;
@@ -313,6 +303,25 @@ static int estimate_levels(const darcy_problem *p, uint64_t seed, int qoi_index,
         return (double)tasks[i].count * (double)((n + 1) * (n + 1)) * (tasks[i].level ? 1.25 : 1.0);
     };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+    // SCE_LEVEL_PRIORITY=1: the levels' streams get priorities by rank of work
+    // (the largest the highest), so the other levels fill the gaps of the largest
+    int lo_prio = 0, hi_prio = 0;
+    std::vector<int> prio(ntasks, 0);
+    {
+        const char *e = getenv("SCE_LEVEL_PRIORITY");
+        if (e && atoi(e) != 0 && cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess)
+            for (int k = 0; k < ntasks; ++k) prio[order[k]] = std::min(lo_prio, hi_prio + k);
+    }
+    for (int i = 0; i < ntasks; ++i) {
+        for (int k = 0; k < (tasks[i].level > 0 ? 2 : 1); ++k) {
+            cudaStream_t &s = ss[2 * (size_t)i + k];
+            if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(s, ev0, 0) != cudaSuccess) {
+                release();
+                return CE_ERR_CUDA;
+            }
+        }
+    }
     std::atomic<int> next{0};
     // a failing task's error text (the workers' sce_last_error is thread-local)
     std::mutex err_mu;
