@@ -1066,12 +1066,24 @@ def mixed_launch_bench(args, sce, stream):
 
         f1, _ = timed(fields_one)
         fe, _ = timed(fields_each)
+        # the persistent field launch together with cached solver graphs
+        os.environ["SCE_GRAPHS"] = "1"
+        try:
+            gms, _ = timed(lambda i: launch(i, persistent=True))
+        finally:
+            os.environ.pop("SCE_GRAPHS", None)
+            sce.darcy_solver_cache_clear(stream=stream.cuda_stream)
         out["persistent"] = {
             "ms_per_launch": round(pms, 2), "samples_per_s": round(nsamp / (pms / 1e3), 1),
             "note": "every bucket's fields in one persistent launch (ce_sample_levels: device "
                     "work queue over all row and column blocks, bounded per-sample waits), "
                     "then the solves as in the streams path; bit-identical results",
-            "fields_one_launch_ms": round(f1, 3), "fields_per_bucket_calls_ms": round(fe, 3)}
+            "fields_one_launch_ms": round(f1, 3), "fields_per_bucket_calls_ms": round(fe, 3),
+            "with_cached_graphs": {"ms_per_launch": round(gms, 2),
+                                   "samples_per_s": round(nsamp / (gms / 1e3), 1),
+                                   "note": "the persistent path with SCE_GRAPHS=1: every "
+                                           "solve shape keeps its buffers and a captured "
+                                           "graph of four CG iterations, replayed"}}
         del ks
     for e in embs:
         e.close()

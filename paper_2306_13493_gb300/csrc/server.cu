@@ -104,6 +104,7 @@ struct sce_server_s {
     std::mutex mu;
     std::condition_variable cv_work, cv_done, cv_emb;
     std::deque<unsigned long long> queue;
+    std::deque<unsigned long long> sliced;   // sliced requests, oldest first
     std::unordered_map<unsigned long long, Job> jobs;
     unsigned long long next_id = 1;
     long long budget = 0, reserved = 0, peak_reserved = 0;
@@ -176,7 +177,11 @@ struct sce_server_s {
         return true;
     }
 
-    // Next admissible job (caller holds mu); 0 if none.
+    // Next admissible job (caller holds mu); 0 if none.  With nothing
+    // admissible queued, another slice of the oldest sliced request with
+    // slices left is started -- while at least one slot stays free for the
+    // requests that arrive meanwhile -- so that an otherwise idle server gives
+    // a large request more of the GPU.
     unsigned long long pick() {
         for (size_t i = 0; i < queue.size(); ++i) {
             const unsigned long long id = queue[i];
@@ -188,6 +193,20 @@ struct sce_server_s {
                 head_skips = 0;
             }
             queue.erase(queue.begin() + (long)i);
+            return id;
+        }
+        if (!queue.empty() || in_flight + 1 >= cfg.slots) return 0;
+        while (!sliced.empty()) {
+            const unsigned long long pid = sliced.front();
+            auto it = jobs.find(pid);
+            if (it == jobs.end() || it->second.next_slice >= it->second.nslices) {
+                sliced.pop_front();
+                continue;
+            }
+            enqueue_slice(pid);
+            const unsigned long long id = queue.back();
+            if (jobs.at(id).fp > budget - reserved) return 0;   // stays queued
+            queue.pop_back();
             return id;
         }
         return 0;
@@ -386,6 +405,7 @@ extern "C" int sce_server_submit(sce_server_t S, const sce_request *r, uint64_t 
             // each finished slice queues the next one behind the requests that
             // arrived meanwhile
             for (int k = 0; k < std::min(kSlicesInFlight, j.nslices); ++k) S->enqueue_slice(id);
+            S->sliced.push_back(id);
         } else {
             S->queue.push_back(id);
         }
