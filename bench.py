@@ -1388,7 +1388,12 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else None
+    # the roofline of the HBM-bound family with the largest share of device time
+    # (families bound by issue, barriers or launch latency have no HBM fraction)
+    hbm_fams = [kv for kv in prof.items()
+                if KERNEL_BOUND.get(kv[0], "hbm") == "hbm" and kv[1][2] > 0]
+    top = max(hbm_fams, key=lambda kv: kv[1][0]) if hbm_fams else None
+    top_all = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
     roof = None
     kernels = {}
     prof_total = sum(v[0] for v in prof.values()) if prof else 0.0
@@ -1416,6 +1421,7 @@ def run_ours(args):
                 "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": round(by / nl),
                 "peak_source": peak_src, "avg_launch_us": round(1000 * ms / nl, 2),
+                "dominant_family_overall": top_all,
                 "timed": "one extra step after the timed ones, levels one after another, "
                          "CUDA events around every launch on its stream"}
 
