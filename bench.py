@@ -629,10 +629,11 @@ def three_d_study(args):
         var = (a[2] - a[0] * mean * mean) / (a[0] - 1)
         per_level.append({"level": l, "n": n, "P": embs[l].P, "N": N, "mean_Y": mean,
                           "var_Y": var, "failed": a[3], "max_iters": a[4]})
-    line = {"study": "3d", "metric": "fine-level samples/s (3D field+Darcy solve)",
-            "value": total / (ms_step / 1000.0), "unit": "samples/s", "n_gpus": 1,
+    line = {"study": "3d", "metric": "MLMC level-samples/s, all levels of one 3D sweep (each: "
+                                     "field + fine and coarse Darcy solves + QoI + Y_l)",
+            "value": total / (ms_step / 1000.0), "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "higher_is_better": True, "dtype": DTYPE_MIXED, "data": "synthetic",
             "config": {"workload": wl.describe(), "levels_in_flight": conc,
                        "l2": "flushed before every timed step (258 MB write)"},
             "setup_seconds": round(setup_s, 3), "clocks": clk, "per_level": per_level,
@@ -659,7 +660,7 @@ def three_d_study(args):
         lv = range(len(wl.cpu_samples))
         sec = sum(wl.N[l] * mean[l] for l in lv) / sum(wl.N[l] for l in lv)
         line["cpu_baseline"] = {
-            "value": cores / sec, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "value": cores / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": (f"oracle (numpy/scipy FP64, direct sparse solves) on {cores} host cores, "
                        f"{'/'.join(map(str, wl.cpu_samples))} samples on levels "
                        f"0..{len(wl.cpu_samples) - 1} (n = "
