@@ -83,10 +83,16 @@ __device__ __forceinline__ ff apply_at_ff(const float *cx, const float *cxl, con
     return a;
 }
 
+// Series conductance a b / (a + b) of two edges.  It only enters the
+// coarse operators of the multigrid preconditioner, which has to be a fixed
+// symmetric operation, not an exact one (the refinement removes its
+// rounding): FP32 uses the fast single-precision division, as the smoothers
+// do; FP64 keeps the exact division.
 template <typename T>
 __device__ __forceinline__ T series_cond(T a, T b) {
     const T t = a + b;
-    return t > T(0) ? a * b / t : T(0);
+    if constexpr (sizeof(T) == 4) return t > T(0) ? __fdividef(a * b, t) : T(0);
+    else return t > T(0) ? a * b / t : T(0);
 }
 
 // Coarse conductances at coarse vertex (I, J): a coarse edge spans two fine

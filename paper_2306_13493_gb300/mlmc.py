@@ -20,6 +20,8 @@ formulas of the paper's §3.3-3.6 and §4:
   algorithm of Giles, which §3.4 builds on);
 * rates alpha, beta, gamma by least squares on log2 |E Y_l|, log2 V[Y_l],
   log2 C_l against l (§4);
+* checkpoint / resume of the level state (``save_checkpoint``,
+  ``load_checkpoint``, ``resume_runners``; ``run_to_rmse(checkpoint=...)``);
 * the smoothing rules of §3.6 (``mlmc_tau_exponential`` and
   ``mlmc_tau_matern`` of the C ABI) give a real tau_l; ``keep_for_tau`` turns
   it into the keep count ce_setup_embedding takes (s = P^2 is known once the
@@ -29,8 +31,10 @@ formulas of the paper's §3.3-3.6 and §4:
 The cost of a sample on level l is the GPU time of its level estimate
 divided by its sample count (CUDA events on the launching stream).
 """
+import json
 import math
-from dataclasses import dataclass, field
+import os
+from dataclasses import asdict, dataclass, field
 from typing import Callable, List, Optional
 
 import numpy as np
@@ -181,6 +185,50 @@ def _run_levels(runners, counts):
         r.collect(t)
 
 
+# ---- checkpoint / resume of the level state.  The state of an MLMC run is
+# its per-level sums, counts, next sample indices and measured seconds; the
+# normals of sample i of level l depend only on (seed, l, i) (counter-based
+# Philox), so a run resumed from a checkpoint draws exactly the samples the
+# interrupted run would have drawn next.
+
+CHECKPOINT_VERSION = 1
+
+
+def save_checkpoint(path, runners, meta=None):
+    """Writes the level state of `runners` to `path` (JSON; floats round-trip
+    exactly), atomically: a crash while writing leaves the previous file."""
+    doc = {"version": CHECKPOINT_VERSION, "meta": meta or {},
+           "levels": [asdict(r.stats) for r in runners]}
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(doc, fh)
+        fh.flush()
+        os.fsync(fh.fileno())
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path):
+    """(list of LevelStats, meta) from a file written by save_checkpoint."""
+    with open(path) as fh:
+        doc = json.load(fh)
+    if doc.get("version") != CHECKPOINT_VERSION:
+        raise ValueError("unsupported checkpoint version %r" % doc.get("version"))
+    return [LevelStats(**d) for d in doc["levels"]], doc.get("meta", {})
+
+
+def resume_runners(runners, stats):
+    """Puts checkpointed level state into fresh runners (same levels and
+    grids, in order); raises if they do not match."""
+    if len(stats) > len(runners):
+        raise ValueError("checkpoint has more levels than runners")
+    for r, st in zip(runners, stats):
+        if (r.stats.level, r.stats.n) != (st.level, st.n):
+            raise ValueError("checkpoint level %d (n = %d) does not match runner level %d "
+                             "(n = %d)" % (st.level, st.n, r.stats.level, r.stats.n))
+        r.stats = LevelStats(**asdict(st))
+    return runners
+
+
 def coarsest_cells(kind, nu, lam):
     """Cells per side n0 = 1/h0 of the coarsest level of plain MLMC: the
     smallest power of two with 1/n0 <= lambda (separable exponential
@@ -315,18 +363,28 @@ def fit_alpha(stats: List[LevelStats], finest=None, alpha_max=None):
 
 
 def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rounds=10,
-                ratio=1.0, var_share=0.5, alpha_levels=None, alpha_max=None, bias_levels=1):
+                ratio=1.0, var_share=0.5, alpha_levels=None, alpha_max=None, bias_levels=1,
+                checkpoint=None):
     """MLMC with the fixed level set of `runners` to a root-mean-square error eps:
     pilot samples, then the optimal N_l from the measured V_l and C_l for the
     variance target var_share * eps^2 (Eq. (3.6) as printed: var_share = 1/2),
     topped up until no level needs more than 1 % extra samples.  alpha (given,
     or fitted on the `alpha_levels` finest levels, all levels l >= 1 if None)
     enters the Richardson bias.  Returns the estimate, the estimated RMSE
-    (statistical error and bias) and the GPU seconds spent."""
+    (statistical error and bias) and the GPU seconds spent.
+
+    checkpoint: a file path; if it exists, the runners resume from the level
+    state in it (``resume_runners``), and the state is saved there after the
+    pilot and after every round, so that an interrupted run can be restarted
+    with the same arguments and continues where it stopped."""
     if not 0.0 < var_share <= 1.0:
         raise ValueError("var_share must be in (0, 1]")
+    if checkpoint and os.path.exists(checkpoint):
+        resume_runners(runners, load_checkpoint(checkpoint)[0])
     pilot = pilot or [100] * len(runners)
     _run_levels(runners, [p - r.stats.N for r, p in zip(runners, pilot)])
+    if checkpoint:
+        save_checkpoint(checkpoint, runners, {"eps": eps})
     N_opt = None
     # Eq. (3.6) sizes for the variance target eps_v^2 / 2 = var_share eps^2
     eps_v = eps * math.sqrt(2.0 * var_share)
@@ -338,6 +396,8 @@ def run_to_rmse(runners: List[LevelRunner], eps, pilot=None, alpha=None, max_rou
         if all(e <= 0.01 * r.stats.N for e, r in zip(extra, runners)):
             break
         _run_levels(runners, extra)
+        if checkpoint:
+            save_checkpoint(checkpoint, runners, {"eps": eps})
     stats = [r.stats for r in runners]
     est = sum(s.mean for s in stats)
     stat_err = math.sqrt(sum(s.var / s.N for s in stats))

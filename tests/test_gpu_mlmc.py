@@ -213,3 +213,30 @@ def test_estimate_levels_batched_levels_match_oracle(sce, nested, monkeypatch):
         assert s.N == t["count"] and s.n_failed == 0
     for e in embs:
         e.close()
+
+
+def test_level_runner_resumes_from_a_checkpoint(sce, tmp_path):
+    """A LevelRunner that ran 40 then 25 samples, and one that ran 40, was
+    checkpointed, and whose state a fresh runner took over for the other 25,
+    hold the same level sums bit for bit (counter-based normals: the resumed
+    runner draws samples 40..64)."""
+    from paper_2306_13493_gb300 import mlmc as gm
+    embs = _level_setup(sce, [0, 1])
+    a = [gm.LevelRunner(embs[l], l, 9, qoi=1, f=1.0) for l in (0, 1)]
+    for r in a:
+        r.run(40)
+        r.run(25)
+    b = [gm.LevelRunner(embs[l], l, 9, qoi=1, f=1.0) for l in (0, 1)]
+    for r in b:
+        r.run(40)
+    ck = str(tmp_path / "levels.json")
+    gm.save_checkpoint(ck, b)
+    c = gm.resume_runners([gm.LevelRunner(embs[l], l, 9, qoi=1, f=1.0) for l in (0, 1)],
+                          gm.load_checkpoint(ck)[0])
+    for r in c:
+        r.run(25)
+    for ra, rc in zip(a, c):
+        assert (ra.stats.N, ra.stats.sumY, ra.stats.sumY2, ra.stats.sumQ, ra.stats.next_sample) == \
+            (rc.stats.N, rc.stats.sumY, rc.stats.sumY2, rc.stats.sumQ, rc.stats.next_sample)
+    for e in embs:
+        e.close()

@@ -306,3 +306,59 @@ def test_run_adaptive_respects_the_minimum_finest_level(drv):
     res = drv.run_adaptive(make_runner, eps, L0=2, L_max=6, pilot=50, alpha=1.0, bias_levels=1,
                            restart_previous_finest=False, L_min=5)
     assert len(res.levels) == 6 and res.bias == pytest.approx(0.001, rel=1e-3)
+
+
+class CounterRunner:
+    """Level l's sample i is a fixed function of (l, i) -- like the
+    counter-based normals -- at cost C_l per sample; raises once `fail_at`
+    run() calls have been made (an interruption)."""
+
+    calls = 0
+    fail_at = None
+
+    def __init__(self, level):
+        from paper_2306_13493_gb300.mlmc import LevelStats
+        self.stats = LevelStats(level=level, n=16 << level)
+
+    def run(self, count):
+        if CounterRunner.fail_at is not None and CounterRunner.calls >= CounterRunner.fail_at:
+            raise RuntimeError("interrupted")
+        CounterRunner.calls += 1
+        st = self.stats
+        i = np.arange(st.next_sample, st.next_sample + count, dtype=np.float64)
+        y = 0.05 * 2.0 ** -st.level + 0.02 * 2.0 ** (-st.level) * np.sin(1.7 * i + st.level)
+        st.N += count
+        st.sumY += float(y.sum())
+        st.sumY2 += float((y * y).sum())
+        st.sumQ += float(y.sum())
+        st.sumQ2 += float((y * y).sum())
+        st.seconds += 1e-6 * 4.0 ** st.level * count
+        st.next_sample += count
+        return st
+
+
+def test_checkpoint_resume_continues_the_same_run(drv, tmp_path):
+    """A run to an RMSE interrupted after its pilot and resumed from its
+    checkpoint ends with exactly the level sums, sample counts and estimate
+    of the uninterrupted run; the checkpoint file round-trips the state."""
+    eps = 2e-3
+    CounterRunner.calls, CounterRunner.fail_at = 0, None
+    full = drv.run_to_rmse([CounterRunner(l) for l in range(4)], eps, pilot=[50] * 4, alpha=1.0)
+    ck = str(tmp_path / "state.json")
+    CounterRunner.calls, CounterRunner.fail_at = 0, 4       # dies in the first top-up round
+    with pytest.raises(RuntimeError):
+        drv.run_to_rmse([CounterRunner(l) for l in range(4)], eps, pilot=[50] * 4, alpha=1.0,
+                        checkpoint=ck)
+    stats, meta = drv.load_checkpoint(ck)
+    assert [s.N for s in stats] == [50] * 4 and meta["eps"] == eps
+    CounterRunner.calls, CounterRunner.fail_at = 0, None
+    res = drv.run_to_rmse([CounterRunner(l) for l in range(4)], eps, pilot=[50] * 4, alpha=1.0,
+                          checkpoint=ck)
+    assert [s.N for s in res.levels] == [s.N for s in full.levels]
+    assert [(s.sumY, s.sumY2, s.next_sample) for s in res.levels] == \
+        [(s.sumY, s.sumY2, s.next_sample) for s in full.levels]
+    assert res.estimate == full.estimate
+    again, _ = drv.load_checkpoint(ck)
+    assert [s.N for s in again] == [s.N for s in res.levels]
+    with pytest.raises(ValueError):
+        drv.resume_runners([CounterRunner(1)], again)
