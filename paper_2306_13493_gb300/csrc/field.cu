@@ -499,8 +499,8 @@ __device__ __forceinline__ void ce_row_block(
     }
 }
 
-template <typename R, int MAXB, bool QMC = false>
-__global__ void __launch_bounds__(256, 4) ce_row_kernel(
+template <typename R, int MAXB, bool QMC = false, int MINB = 4>
+__global__ void __launch_bounds__(256, MINB) ce_row_kernel(
     const R *__restrict__ sq_f, const R *__restrict__ sq_c, const typename C2<R>::T *__restrict__ tw,
     int P, int logP, int m, uint64_t seed, uint32_t level, uint64_t first_sample, int F, int tpf,
     typename C2<R>::T *__restrict__ Yf, typename C2<R>::T *__restrict__ Yc, QmcArgs qa) {
@@ -577,8 +577,8 @@ __device__ __forceinline__ void ce_col_block(
     }
 }
 
-template <typename R, int MAXB>
-__global__ void __launch_bounds__(256, 4) ce_col_kernel(
+template <typename R, int MAXB, int MINB = 4>
+__global__ void __launch_bounds__(256, MINB) ce_col_kernel(
     const typename C2<R>::T *__restrict__ Y, int ncols, int P, int logP, int m, int F, int tpf,
     const typename C2<R>::T *__restrict__ tw, int coarse, R *__restrict__ kout,
     R *__restrict__ kc_plain) {
@@ -638,6 +638,14 @@ static LineCfg line_cfg_tuned(int P, int units, int pass) {
     return c;
 }
 
+// Blocks per SM the FP32 FFT passes are compiled for (64 registers at 4; 5 and
+// 6 trade registers for occupancy): SCE_ROW_MINB / SCE_COL_MINB, default 4.
+static int fft_minb(const char *name) {
+    const char *e = getenv(name);
+    const int v = e ? atoi(e) : 4;
+    return (v == 5 || v == 6) ? v : 4;
+}
+
 template <typename R, int MAXB>
 static int launch_row(const ce_embedding_s *e, bool masked, const typename C2<R>::T *tw,
                       uint64_t seed, uint32_t level, uint64_t first, int count,
@@ -661,11 +669,22 @@ static int launch_row(const ce_embedding_s *e, bool masked, const typename C2<R>
                (double)e->s * sizeof(R) * (masked ? 2 : 1) +
                    (double)count * (m + 1) * e->P * 2 * sizeof(R) * (masked ? 1.5 : 1.0));
     const QmcArgs q = qa ? *qa : QmcArgs{nullptr, 1u, 0};
+    const int minb = (sizeof(R) == 4 && MAXB == 4 && !qa) ? fft_minb("SCE_ROW_MINB") : 4;
     if (qa)
         ce_row_kernel<R, MAXB, true><<<grid, c.F * c.tpf, c.smem, st>>>(
             sqf, masked ? sqc : nullptr, tw, e->P, ilog2(e->P), e->n, seed, level, first, c.F,
             c.tpf, Yf, Yc, q);
-    else
+    else if (minb == 5) {
+        SCE_TRY(sce_raise_smem_limit((const void *)ce_row_kernel<R, MAXB, false, 5>, c.smem));
+        ce_row_kernel<R, MAXB, false, 5><<<grid, c.F * c.tpf, c.smem, st>>>(
+            sqf, masked ? sqc : nullptr, tw, e->P, ilog2(e->P), e->n, seed, level, first, c.F,
+            c.tpf, Yf, Yc, q);
+    } else if (minb == 6) {
+        SCE_TRY(sce_raise_smem_limit((const void *)ce_row_kernel<R, MAXB, false, 6>, c.smem));
+        ce_row_kernel<R, MAXB, false, 6><<<grid, c.F * c.tpf, c.smem, st>>>(
+            sqf, masked ? sqc : nullptr, tw, e->P, ilog2(e->P), e->n, seed, level, first, c.F,
+            c.tpf, Yf, Yc, q);
+    } else
         ce_row_kernel<R, MAXB, false><<<grid, c.F * c.tpf, c.smem, st>>>(
             sqf, masked ? sqc : nullptr, tw, e->P, ilog2(e->P), e->n, seed, level, first, c.F,
             c.tpf, Yf, Yc, q);
@@ -683,9 +702,19 @@ static int launch_col(const ce_embedding_s *e, const typename C2<R>::T *Y, int n
     SceProf pr(KP_COL, st,
                (double)count * ncols * e->P * 2 * sizeof(R) +
                    (double)count * ncols * rows_out * sizeof(R) * (kc_plain ? 1.25 : 1.0));
-    ce_col_kernel<R, MAXB><<<grid, c.F * c.tpf, c.smem, st>>>(Y, ncols, e->P, ilog2(e->P), e->n,
-                                                               c.F, c.tpf, tw, coarse, kout,
-                                                               kc_plain);
+    const int minb = (sizeof(R) == 4 && MAXB == 4) ? fft_minb("SCE_COL_MINB") : 4;
+    if (minb == 5) {
+        SCE_TRY(sce_raise_smem_limit((const void *)ce_col_kernel<R, MAXB, 5>, c.smem));
+        ce_col_kernel<R, MAXB, 5><<<grid, c.F * c.tpf, c.smem, st>>>(
+            Y, ncols, e->P, ilog2(e->P), e->n, c.F, c.tpf, tw, coarse, kout, kc_plain);
+    } else if (minb == 6) {
+        SCE_TRY(sce_raise_smem_limit((const void *)ce_col_kernel<R, MAXB, 6>, c.smem));
+        ce_col_kernel<R, MAXB, 6><<<grid, c.F * c.tpf, c.smem, st>>>(
+            Y, ncols, e->P, ilog2(e->P), e->n, c.F, c.tpf, tw, coarse, kout, kc_plain);
+    } else
+        ce_col_kernel<R, MAXB><<<grid, c.F * c.tpf, c.smem, st>>>(Y, ncols, e->P, ilog2(e->P),
+                                                                   e->n, c.F, c.tpf, tw, coarse,
+                                                                   kout, kc_plain);
     SCE_CUDA(cudaGetLastError());
     return CE_OK;
 }
