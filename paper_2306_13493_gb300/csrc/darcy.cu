@@ -57,8 +57,8 @@ constexpr int TAIL_N = SCE_TAIL_N;   // levels with n <= TAIL_N run in one block
 // Window heights of the tiled multigrid kernels, per (precision, grid size),
 // chosen by darcy_autotune_tiles; MG_SH where absent (SCE_TILE_SH forces one
 // for every level).  Every height computes each vertex of a V-cycle
-// identically; the per-tile r . z partial sums follow the tiling, so results
-// agree to rounding across heights.
+// identically; the per-tile r . z partial sums follow the tiling, so the
+// solves take different rounding paths to the same stopping tolerance.
 constexpr int kTileHeights[] = {16, 24, 32, 48};
 std::mutex g_tile_mu;
 std::map<std::pair<int, int>, int> g_tile_sh;   // (sizeof T, n) -> window height
@@ -108,6 +108,14 @@ static Launch launch_for(int n) {
          ++e_, v += blockDim.x)                                                        \
         if (v < (V))
 
+// Row index of vertex v on a grid of width w without an integer division:
+// floor(v / w) = (v * ceil(2^40 / w)) >> 40, exact whenever v w < 2^40 (every
+// grid up to n = 4096; checked exhaustively for all widths on the host).
+inline unsigned long long row_magic(int w) { return ((1ull << 40) + (unsigned)w - 1) / (unsigned)w; }
+__device__ __forceinline__ int vrow(int v, unsigned long long m) {
+    return (int)(((unsigned long long)(unsigned)v * m) >> 40);
+}
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T val, T *sh) {
     // fixed-order tree: warp shuffles then warp partials in order
@@ -131,13 +139,13 @@ __device__ __forceinline__ T block_sum(T val, T *sh) {
 template <typename Tk, typename T, int VPT = 0>
 __global__ void cond_kernel(const Tk *__restrict__ k, int n, int vpt, T *__restrict__ cx,
                             T *__restrict__ cy, float *__restrict__ cxl,
-                            float *__restrict__ cyl) {
+                            float *__restrict__ cyl, unsigned long long rdm) {
     const int s = blockIdx.y;
     const long long V = (long long)(n + 1) * (n + 1);
     const Tk *ks = k + s * V;
     const int w = n + 1;
     FOR_VERT_C(V, VPT, vpt) {
-        const int j = v / w, i = v - j * w;
+        const int j = vrow(v, rdm), i = v - j * w;
         if constexpr (sizeof(T) == 4 && sizeof(Tk) == 4) {
             ff gx, gy;
             cond_at_ff(ks, i, j, n, &gx, &gy);
@@ -156,14 +164,15 @@ __global__ void cond_kernel(const Tk *__restrict__ k, int n, int vpt, T *__restr
 
 template <typename T, int VPT = 0>
 __global__ void coarsen_kernel(const T *__restrict__ cxf, const T *__restrict__ cyf, int nf,
-                               int vpt, T *__restrict__ cxc, T *__restrict__ cyc) {
+                               int vpt, T *__restrict__ cxc, T *__restrict__ cyc,
+                               unsigned long long rdm) {
     const int s = blockIdx.y;
     const int nc = nf / 2;
     const long long Vf = (long long)(nf + 1) * (nf + 1), Vc = (long long)(nc + 1) * (nc + 1);
     const T *ax = cxf + s * Vf, *ay = cyf + s * Vf;
     const int wc = nc + 1;
     FOR_VERT_C(Vc, VPT, vpt) {
-        const int J = v / wc, I = v - J * wc;
+        const int J = vrow(v, rdm), I = v - J * wc;
         T gx, gy;
         coarsen_at(ax, ay, nf, I, J, &gx, &gy);
         cxc[s * Vc + v] = gx;
@@ -172,6 +181,51 @@ __global__ void coarsen_kernel(const T *__restrict__ cxf, const T *__restrict__ 
 }
 
 // ---------------------------------------------------------------- multigrid
+// Conductances of the levels nf/2, nf/4, ..., nf >> nout (all of them at most
+// 64 cells wide) from those of the nf-cell level above them: one block per
+// sample, each level into global memory (out.cx[l], out.cy[l], per sample
+// contiguous) and into shared memory, from which the next level is coarsened.
+// Vertex for vertex the arithmetic of coarsen_kernel: one launch per solve
+// instead of one per level.
+template <typename T>
+__global__ void __launch_bounds__(256) coarsen_tail_kernel(const T *__restrict__ cxf,
+                                                           const T *__restrict__ cyf, int nf,
+                                                           TailPtrs out, int nout) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int s = blockIdx.x;
+    const long long Vf = (long long)(nf + 1) * (nf + 1);
+    const T *ax = cxf + s * Vf, *ay = cyf + s * Vf;
+    int nin = nf;
+    for (int l = 0; l < nout; ++l) {
+        const int nc = nin / 2, wc = nc + 1, Vc = wc * wc;
+        T *sx = sm, *sy = sm + Vc;
+        T *gx = reinterpret_cast<T *>(out.cx[l]) + (long long)s * Vc;
+        T *gy = reinterpret_cast<T *>(out.cy[l]) + (long long)s * Vc;
+        for (int v = threadIdx.x; v < Vc; v += blockDim.x) {
+            const int J = v / wc, I = v - J * wc;
+            T x, y;
+            coarsen_at(ax, ay, nin, I, J, &x, &y);
+            sx[v] = x;
+            sy[v] = y;
+            gx[v] = x;
+            gy[v] = y;
+        }
+        __syncthreads();
+        ax = sx;
+        ay = sy;
+        sm += 2 * Vc;
+        nin = nc;
+    }
+}
+
+template <typename T>
+constexpr size_t coarsen_tail_smem(int nf) {
+    size_t t = 0;
+    for (int nc = nf / 2; nc >= 2; nc /= 2) t += 2 * (size_t)(nc + 1) * (nc + 1);
+    return t * sizeof(T);
+}
+
 template <typename T>
 __global__ void smooth_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
                               const T *__restrict__ b, T *__restrict__ z, int n, int vpt,
@@ -277,24 +331,105 @@ __global__ void dot_kernel(const T *__restrict__ a, const T *__restrict__ b, int
 
 
 
-// Fused CG pass of iteration k (one read of p_{k-1}): p_k = z + beta p_{k-1}
-// (beta = 0 at the start of an inner solve, so p_0 = z), the deferred update
-// d += alpha_{k-1} p_{k-1} of iteration k-1 (alpha = 0 at the start), q = A p_k
-// and the p_k.q partials.  p ping-pongs: p_in holds p_{k-1}, p_out gets p_k;
-// the neighbours' p_k are formed from z and p_in, so no block reads what
-// another writes.  On the Dirichlet columns z = p = 0, so p_k stays 0 there.
+// Per-sample scalar state.  ppar: the p array of the pending update (alpha, p).
+// rz: two slots per sample (r.z of the iterations of even and odd parity;
+// the reduction launches use the first).  rzf, alphaf: the FP32 path's folded
+// r.z (float-float, two slots) and alpha.
+struct Scal {
+    double *rz, *pq, *rr, *rr0, *alpha, *beta, *orr, *orr0, *thr;
+    float2 *rzf;
+    float *alphaf;
+    int *act_out, *act_in, *iters, *counter, *ppar;
+};
+
+// Fixed-order sum of one sample's nb block partials by one warp: lane-strided
+// sums, then a shuffle tree; lane 0 gets the total.  Every caller (reduce_kernel
+// and the blocks of the CG kernels below) adds in this order, so all of them
+// obtain the same value bit for bit.
+__device__ __forceinline__ double warp_sum_parts(const double *__restrict__ p, int nb, int lane) {
+    double v = 0.0;
+    for (int i = lane; i < nb; i += 32) v += p[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The same fixed-order warp sum in float-float, for partials that hold FP32
+// values (the block sums of the FP32 kernels): FP32 operations only, the
+// result within 2^-47 of the exact sum.
+template <typename P>
+__device__ __forceinline__ ff warp_sum_parts_ff(const P *__restrict__ p, int nb, int lane) {
+    ff v = {0.0f, 0.0f};
+    for (int i = lane; i < nb; i += 32) v = ff_add_f(v, (float)p[i]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const ff t = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+        v = ff_add(v, t);
+    }
+    return v;
+}
+
+// Where CG's scalars alpha and beta are formed (SCE_CG_FOLD): 0 = by reduction
+// launches between the CG kernels; 1 = alpha inside rupdate_kernel, beta by a
+// launch; 2 = both inside the CG kernels (the default).  Folded, every block
+// of the consuming kernel sums the producing kernel's partials itself, in the
+// fixed order of reduce_kernel; FP32 (T = float) in float-float with the
+// quotient in FP32 (the kernels use alpha and beta as FP32 values), FP64 in
+// FP64 (bit-identical to the launches).
+enum { FOLD_NONE = 0, FOLD_ALPHA = 1, FOLD_BOTH = 2 };
+
+// Fused CG pass of iteration k (one read of p_{k-1}): beta, p_k = z + beta
+// p_{k-1}, the deferred update d += alpha_{k-1} p_{k-1} of iteration k-1
+// (alpha = 0 at the start), q = A p_k and the p_k.q partials (FP32 values for
+// a folded alpha on the FP32 path, else doubles).
+// beta: FOLD_BOTH: from the preconditioner's r.z partials rz_part, beta =
+// r.z_k / r.z_{k-1} (0 when r.z_{k-1} = 0, as at the start of an inner solve);
+// r.z alternates between two slots by the parity of k: r.z_{k-1} is read from
+// slot par ^ 1, block 0 stores r.z_k in slot par (no block reads that slot in
+// this launch); FP32 keeps them as float-float (rzf), FP64 as doubles (rz).
+// Otherwise beta[s], set by a reduction launch.  p ping-pongs: p_in holds
+// p_{k-1}, p_out gets p_k; the neighbours' p_k are formed from z and p_in, so
+// no block reads what another writes.  On the Dirichlet columns z = p = 0, so
+// p_k stays 0 there.
 template <typename T, int VPT = 0>
 __global__ void pspmv_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
                              const T *__restrict__ z, const T *__restrict__ p_in,
                              T *__restrict__ p_out, T *__restrict__ q, T *__restrict__ d,
-                             const double *__restrict__ beta, const double *__restrict__ alpha,
-                             int n, int vpt, double *__restrict__ part, int nblk,
-                             const int *__restrict__ act) {
+                             const double *__restrict__ rz_part, int rz_nblk, Scal sc, int count,
+                             int par, int fold, int n, int vpt, double *__restrict__ part,
+                             int nblk, const int *__restrict__ act) {
     __shared__ T sh[32];
+    __shared__ T sbeta;
     const int s = blockIdx.y;
+    constexpr bool F32 = sizeof(T) == 4;
     // the per-sample scalars are loaded together with the flag (one latency)
-    const T bt = (T)beta[s], al = (T)alpha[s];
+    const T al = (F32 && fold != FOLD_NONE) ? (T)sc.alphaf[s] : (T)sc.alpha[s];
+    T pre_b = T(0);
+    float2 old_f = {0.0f, 0.0f};
+    double old_d = 0.0;
+    if (fold != FOLD_BOTH) pre_b = (T)sc.beta[s];
+    else if constexpr (F32) old_f = sc.rzf[(par ^ 1) * count + s];
+    else old_d = sc.rz[(par ^ 1) * count + s];
     if (!act[s]) return;
+    T bt = pre_b;
+    if (fold == FOLD_BOTH) {
+        if (threadIdx.x < 32) {
+            const double *pp = rz_part + (long long)s * rz_nblk;
+            if constexpr (F32) {
+                const ff v = warp_sum_parts_ff(pp, rz_nblk, threadIdx.x);
+                if (threadIdx.x == 0) {
+                    sbeta = old_f.x > 0.0f ? __fdiv_rn(v.hi, old_f.x) : 0.0f;
+                    if (blockIdx.x == 0) sc.rzf[par * count + s] = make_float2(v.hi, v.lo);
+                }
+            } else {
+                const double v = warp_sum_parts(pp, rz_nblk, threadIdx.x);
+                if (threadIdx.x == 0) {
+                    sbeta = old_d > 0.0 ? v / old_d : 0.0;
+                    if (blockIdx.x == 0) sc.rz[par * count + s] = v;
+                }
+            }
+        }
+        __syncthreads();
+        bt = sbeta;
+    }
     const long long V = (long long)(n + 1) * (n + 1);
     const int w = n + 1;
     const T *ax = cx + s * V, *ay = cy + s * V, *zs = z + s * V, *pi = p_in + s * V;
@@ -317,23 +452,81 @@ __global__ void pspmv_kernel(const T *__restrict__ cx, const T *__restrict__ cy,
         qs[v] = val;
     }
     const T tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = (double)tot;
+    if (threadIdx.x == 0) {
+        if (F32 && fold != FOLD_NONE)
+            reinterpret_cast<float *>(part)[(long long)s * nblk + blockIdx.x] = tot;
+        else
+            part[(long long)s * nblk + blockIdx.x] = (double)tot;
+    }
 }
 
-// r -= alpha q and the r.r partials (the d update is deferred to pspmv_kernel)
+// alpha, r -= alpha q and the r.r partials.  alpha: folded (fold != 0), every
+// block sums the p.q partials of the CG pass (FP32 values on the FP32 path) in
+// the same order, alpha = r.z / p.q (0 when p.q <= 0), with r.z from slot par
+// of the folded state (FOLD_BOTH) or from the reduction launches' rz[s]; block
+// 0 records alpha (and its FP32 copy) and the parity of the p array for the
+// deferred update d += alpha p (next CG pass, or the outer update).  Not
+// folded: alpha[s] from a reduction launch.  The d update itself is deferred to
+// pspmv_kernel.
 template <typename T, int VPT = 0>
-__global__ void rupdate_kernel(T *__restrict__ r, const T *__restrict__ q,
-                               const double *__restrict__ alpha, int n, int vpt,
-                               double *__restrict__ part, int nblk, const int *__restrict__ act) {
+__global__ void __launch_bounds__(256, VPT > 0 ? (sizeof(T) == 4 ? 4 : 3) : 1) rupdate_kernel(
+    T *__restrict__ r, const T *__restrict__ q, const double *__restrict__ pq_part, int pq_nblk,
+    Scal sc, int count, int par, int fold, int n, int vpt, double *__restrict__ part, int nblk,
+    const int *__restrict__ act) {
     __shared__ T sh[32];
+    __shared__ T salpha;
     const int s = blockIdx.y;
-    const T a = (T)alpha[s];   // loaded together with the flag (one latency)
+    constexpr bool F32 = sizeof(T) == 4;
+    // loaded together with the flag (one latency)
+    T pre_a = T(0);
+    float rz_f = 0.0f;
+    double rz_d = 0.0;
+    if (fold == FOLD_NONE) pre_a = (T)sc.alpha[s];
+    else if (fold == FOLD_BOTH) {
+        if constexpr (F32) rz_f = sc.rzf[par * count + s].x;
+        else rz_d = sc.rz[par * count + s];
+    } else {
+        if constexpr (F32) rz_f = (float)sc.rz[s];
+        else rz_d = sc.rz[s];
+    }
     if (!act[s]) return;
     const long long V = (long long)(n + 1) * (n + 1);
+    auto alpha_of_sample = [&]() -> T {
+        if (fold == FOLD_NONE) return pre_a;
+        if (threadIdx.x < 32) {
+            if constexpr (F32) {
+                const float *pf = reinterpret_cast<const float *>(pq_part) + (long long)s * pq_nblk;
+                const ff v = warp_sum_parts_ff(pf, pq_nblk, threadIdx.x);
+                if (threadIdx.x == 0) {
+                    const float a = v.hi > 0.0f ? __fdiv_rn(rz_f, v.hi) : 0.0f;
+                    salpha = a;
+                    if (blockIdx.x == 0) {
+                        sc.alphaf[s] = a;
+                        sc.alpha[s] = (double)a;
+                        sc.ppar[s] = par;
+                    }
+                }
+            } else {
+                const double v =
+                    warp_sum_parts(pq_part + (long long)s * pq_nblk, pq_nblk, threadIdx.x);
+                if (threadIdx.x == 0) {
+                    const double a = v > 0.0 ? rz_d / v : 0.0;
+                    salpha = a;
+                    if (blockIdx.x == 0) {
+                        sc.alpha[s] = a;
+                        sc.ppar[s] = par;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        return salpha;
+    };
     T acc = T(0);
     if constexpr (VPT > 0) {
-        // every load of the thread first (all in flight together), then the
-        // updates and stores in the same order as the run-time loop
+        // every load of the thread first (all in flight together, and while
+        // alpha is formed), then the updates and stores in the same order as
+        // the run-time loop
         T rv[VPT], qv[VPT];
         const long long v0 = (long long)blockIdx.x * (blockDim.x * VPT) + threadIdx.x;
 #pragma unroll
@@ -342,6 +535,7 @@ __global__ void rupdate_kernel(T *__restrict__ r, const T *__restrict__ q,
             rv[e] = v < V ? r[s * V + v] : T(0);
             qv[e] = v < V ? q[s * V + v] : T(0);
         }
+        const T a = alpha_of_sample();
 #pragma unroll
         for (int e = 0; e < VPT; ++e) {
             const long long v = v0 + (long long)e * blockDim.x;
@@ -352,6 +546,7 @@ __global__ void rupdate_kernel(T *__restrict__ r, const T *__restrict__ q,
             }
         }
     } else {
+        const T a = alpha_of_sample();
         FOR_VERT_C(V, VPT, vpt) {
             const long long g = s * V + v;
             const T rv = r[g] - a * q[g];
@@ -364,12 +559,6 @@ __global__ void rupdate_kernel(T *__restrict__ r, const T *__restrict__ q,
 }
 
 
-// Per-sample scalar state.  ppar: the p array of the pending update (alpha, p).
-struct Scal {
-    double *rz, *pq, *rr, *rr0, *alpha, *beta, *orr, *orr0, *thr;
-    int *act_out, *act_in, *iters, *counter, *ppar;
-};
-
 enum { RED_ALPHA = 0, RED_RR = 1, RED_BETA = 2, RED_RZ0 = 3, RED_ORR = 4, RED_ORR0 = 5 };
 
 // one warp per sample: fixed-order sum of the block partials, then the
@@ -381,9 +570,7 @@ __global__ void reduce_kernel(const double *__restrict__ part, int nblk, int cou
     if (warp >= count) return;
     const int s = warp;
     if (act && !act[s]) return;
-    double v = 0.0;
-    for (int i = lane; i < nblk; i += 32) v += part[(long long)s * nblk + i];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const double v = warp_sum_parts(part + (long long)s * nblk, nblk, lane);
     if (lane != 0) return;
     switch (mode) {
         case RED_ALPHA:
@@ -469,6 +656,39 @@ __global__ void set_u_kernel(O o, const double *__restrict__ uc, int n, int vpt)
     }
 }
 
+// set_u_kernel for a float-float coarse solution (the mixed path's nested
+// iteration): the mean of the one, two or four coarse values by float-float
+// additions, the halving exact, so no FP64 operation per vertex.
+template <int VPT = 0>
+__global__ void set_u_ff_kernel(OuterF o, const float2 *__restrict__ uc, int n, int vpt,
+                                unsigned long long rdm) {
+    const int s = blockIdx.y;
+    const long long V = (long long)(n + 1) * (n + 1);
+    const int w = n + 1, nc = n / 2, wc = nc + 1;
+    const float2 *c = uc + (long long)s * wc * wc;
+    auto U = [&](int jj, int ii) {
+        const float2 t = c[jj * wc + ii];
+        return ff{t.x, t.y};
+    };
+    FOR_VERT_C(V, VPT, vpt) {
+        const int j = vrow(v, rdm), i = v - j * w;
+        const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
+        ff a = U(j0, i0);
+        float sc = 1.0f;
+        if (i1 != i0) {
+            a = ff_add(a, U(j0, i1));
+            sc = 0.5f;
+        }
+        if (j1 != j0) {
+            ff b = U(j1, i0);
+            if (i1 != i0) b = ff_add(b, U(j1, i1));
+            a = ff_add(a, b);
+            sc *= 0.5f;
+        }
+        o.u[s * V + v] = make_float2(a.hi * sc, a.lo * sc);
+    }
+}
+
 template <class O>
 __global__ void lift_kernel(O o, int n, int vpt) {
     const int s = blockIdx.y;
@@ -494,7 +714,7 @@ struct Load {
 template <typename T, class O, int VPT = 0>
 __global__ void outer_residual_kernel(O o, Load F, int n, int vpt, T *__restrict__ rin,
                                       double *__restrict__ part, int nblk,
-                                      const int *__restrict__ act) {
+                                      const int *__restrict__ act, unsigned long long rdm) {
     __shared__ T sh[32];
     const int s = blockIdx.y;
     if (act && !act[s]) return;
@@ -502,16 +722,15 @@ __global__ void outer_residual_kernel(O o, Load F, int n, int vpt, T *__restrict
     const int w = n + 1;
     T acc = T(0);
     FOR_VERT_C(V, VPT, vpt) {
-        const int j = v / w, i = v - j * w;
+        const int j = vrow(v, rdm), i = v - j * w;
         const long long g = s * V + v;
         T rv = T(0);
         if (i > 0 && i < n) {
             const int inner = (j > 0 && j < n) ? 1 : 0;
             if constexpr (std::is_same<O, OuterF>::value) {
                 const long long b0 = s * V;
-                const ff Au = apply_at_ff(o.cx + b0, o.cxl + b0, o.cy + b0, o.cyl + b0, o.u + b0,
-                                          i, j, n);
-                rv = ff_sub(F.Ff[inner], Au).hi;
+                rv = resid_at_ff(inner ? F.Ff[1] : F.Ff[0], o.cx + b0, o.cxl + b0, o.cy + b0,
+                                 o.cyl + b0, o.u + b0, i, j, n);
             } else {
                 const double uc = o.u[g];
                 double Au = o.cx[g - 1] * (uc - o.u[g - 1]) + o.cx[g] * (uc - o.u[g + 1]);
@@ -652,6 +871,8 @@ __global__ void qoi_final_kernel(const double *__restrict__ part_out,
                                  const Scal sc, double rtol2, double *__restrict__ qoi,
                                  int *__restrict__ iters_out, int *__restrict__ status_out,
                                  int *__restrict__ nfail, int qmask) {
+    // nfail[0]: samples that failed; nfail[1], nfail[2]: the largest and the
+    // total iteration count (integer atomics: order-independent)
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= count) return;
     const int s = warp;
@@ -691,37 +912,11 @@ __global__ void qoi_final_kernel(const double *__restrict__ part_out,
         st = CE_ERR_NONFINITE;
     else if (!(sc.orr[s] <= rtol2 * sc.orr0[s])) st = CE_ERR_NOT_CONVERGED;
     if (status_out) status_out[s] = st;
-    if (iters_out) iters_out[s] = sc.iters[s];
+    const int its = sc.iters[s];
+    if (iters_out) iters_out[s] = its;
     if (st != 0) atomicAdd(nfail, 1);
-}
-
-// out[0] = max, out[1] = sum of a[0..count)
-__global__ void max_int_kernel(const int *__restrict__ a, int count, int *__restrict__ out) {
-    int m = 0, t = 0;
-    for (int i = threadIdx.x; i < count; i += blockDim.x) {
-        m = max(m, a[i]);
-        t += a[i];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        m = max(m, __shfl_down_sync(0xffffffffu, m, o));
-        t += __shfl_down_sync(0xffffffffu, t, o);
-    }
-    __shared__ int sh[32], sh2[32];
-    if ((threadIdx.x & 31) == 0) {
-        sh[threadIdx.x >> 5] = m;
-        sh2[threadIdx.x >> 5] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        m = 0;
-        t = 0;
-        for (int i = 0; i < (blockDim.x + 31) / 32; ++i) {
-            m = max(m, sh[i]);
-            t += sh2[i];
-        }
-        out[0] = m;
-        out[1] = t;
-    }
+    atomicMax(nfail + 1, its);
+    atomicAdd(nfail + 2, its);
 }
 
 // ---------------------------------------------------------------- host driver
@@ -740,7 +935,7 @@ struct Solver {
     float *cxl = nullptr, *cyl = nullptr;   // mixed path: lo parts of the conductances
     double *part = nullptr, *part2 = nullptr;
     Scal sc{};
-    int *misc = nullptr;   // [0] counter, [1] nfail, [2] max iters
+    int *misc = nullptr;   // [0] counter, [1] nfail, [2] max iters, [3] total iters
     std::vector<void *> owned;
     cudaStream_t st = nullptr;
     cudaGraphExec_t graph = nullptr;   // four captured CG iterations, replayed
@@ -868,16 +1063,18 @@ struct Solver {
         SCE_TRY(alloc(&part, (size_t)count * nblk_part));
         SCE_TRY(alloc(&part2, (size_t)count * nblk_part));
         double *scal = nullptr;
-        SCE_TRY(alloc(&scal, (size_t)count * 9));
-        sc.rz = scal;
-        sc.pq = scal + count;
-        sc.rr = scal + 2 * count;
-        sc.rr0 = scal + 3 * count;
-        sc.alpha = scal + 4 * count;
-        sc.beta = scal + 5 * count;
-        sc.orr = scal + 6 * count;
-        sc.orr0 = scal + 7 * count;
-        sc.thr = scal + 8 * count;
+        SCE_TRY(alloc(&scal, (size_t)count * 10));
+        sc.rz = scal;   // two slots
+        sc.pq = scal + 2 * count;
+        sc.rr = scal + 3 * count;
+        sc.rr0 = scal + 4 * count;
+        sc.alpha = scal + 5 * count;
+        sc.beta = scal + 6 * count;
+        sc.orr = scal + 7 * count;
+        sc.orr0 = scal + 8 * count;
+        sc.thr = scal + 9 * count;
+        SCE_TRY(alloc(&sc.rzf, (size_t)count * 2));
+        SCE_TRY(alloc(&sc.alphaf, (size_t)count));
         int *ints = nullptr;
         SCE_TRY(alloc(&ints, (size_t)count * 4 + 4));
         sc.act_out = ints;
@@ -917,6 +1114,7 @@ struct Solver {
     int rz_blocks() const { return Lt == 0 ? 1 : tiles_n[0]; }
 
     bool tail_attr_set = false;
+    bool ctail_attr_set = false;   // shared-memory limit of coarsen_tail_kernel raised
     template <int NTN, int NTHR>
     void tail_launch(bool want_rz) {
         TailPtrs tp{};
@@ -998,14 +1196,14 @@ struct Solver {
         }
     }
 
-    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0, int nblk = -1,
-                int rpar = 0) {
+    void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0,
+                int nblk = -1, int rpar = 0, const double *src = nullptr) {
         const int threads = 256;
         const int blocks = (count * 32 + threads - 1) / threads;
         if (nblk < 0) nblk = ln[0].nblk;
         SceProf pr(KP_REDUCE, st, (double)count * nblk * 8.0);
-        reduce_kernel<<<blocks, threads, 0, st>>>(part, nblk, count, mode, sc, act, rtol2,
-                                                  in_rel2, rpar);
+        reduce_kernel<<<blocks, threads, 0, st>>>(src ? src : part, nblk, count, mode, sc, act,
+                                                  rtol2, in_rel2, rpar);
     }
 
     int read_counter(int *host) {
@@ -1022,7 +1220,16 @@ struct Solver {
 // recently used is freed); darcy_solver_cache_clear frees them all.
 constexpr int kPoolMax = 16;
 
-static bool solver_graphs_on(cudaStream_t st) {
+static // Where CG's alpha and beta are formed: SCE_CG_FOLD = 0 (reduction launches),
+// 1 (alpha folded into the r update) or 2 (both folded; the default).
+int cg_fold_mode() {
+    const char *e = getenv("SCE_CG_FOLD");
+    if (!e) return FOLD_BOTH;
+    const int v = atoi(e);
+    return (v == FOLD_NONE || v == FOLD_ALPHA) ? v : FOLD_BOTH;
+}
+
+bool solver_graphs_on(cudaStream_t st) {
     if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread || sce_prof_on())
         return false;
     const char *e = getenv("SCE_GRAPHS");
@@ -1118,7 +1325,7 @@ struct SolverLease {
 template <typename T, typename Tk>
 static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                         int *n_failed_out, int qmask, const double *u_init) {
+                         int *n_failed_out, int qmask, const double *u_init, bool u_ff) {
     // the solver's buffers, and with cached graphs the captured iterations,
     // come from the pool of idle solvers of the same plan when there is one
     const bool cached = solver_graphs_on(st);
@@ -1166,23 +1373,50 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     {
         SceProf pr(KP_COND, st, S.vb(0, 2.0, sizeof(Tk) + (mixed ? 8.0 : 0.0)));
         if (l0.vpt == 8)
-            cond_kernel<Tk, T, 8><<<g0, l0.tpb, 0, st>>>(k, n0, 8, S.cx[0], S.cy[0], S.cxl, S.cyl);
+            cond_kernel<Tk, T, 8><<<g0, l0.tpb, 0, st>>>(k, n0, 8, S.cx[0], S.cy[0], S.cxl, S.cyl,
+                                                         row_magic(n0 + 1));
         else
             cond_kernel<Tk, T><<<g0, l0.tpb, 0, st>>>(k, n0, l0.vpt, S.cx[0], S.cy[0], S.cxl,
-                                                      S.cyl);
+                                                      S.cyl, row_magic(n0 + 1));
     }
     SCE_CUDA(cudaGetLastError());
-    for (int L = 1; L < S.nlev; ++L) {
+    // levels wider than 64 cells one launch each, then every narrower level
+    // in one launch
+    int Lc = 1;
+    for (; Lc < S.nlev && S.n[Lc] > 64; ++Lc) {
+        const int L = Lc;
         SceProf pr(KP_COARSEN, st, S.vb(L - 1, 2.0) + S.vb(L, 2.0));
         if (S.ln[L].vpt == 8)
             coarsen_kernel<T, 8><<<S.grid(L), S.ln[L].tpb, 0, st>>>(
-                S.cx[L - 1], S.cy[L - 1], S.n[L - 1], 8, S.cx[L], S.cy[L]);
+                S.cx[L - 1], S.cy[L - 1], S.n[L - 1], 8, S.cx[L], S.cy[L], row_magic(S.n[L] + 1));
         else
             coarsen_kernel<T><<<S.grid(L), S.ln[L].tpb, 0, st>>>(
-                S.cx[L - 1], S.cy[L - 1], S.n[L - 1], S.ln[L].vpt, S.cx[L], S.cy[L]);
+                S.cx[L - 1], S.cy[L - 1], S.n[L - 1], S.ln[L].vpt, S.cx[L], S.cy[L],
+                row_magic(S.n[L] + 1));
+    }
+    if (Lc < S.nlev) {
+        const int nout = S.nlev - Lc;
+        double bytes = S.vb(Lc - 1, 2.0);
+        TailPtrs outp{};
+        for (int l = 0; l < nout; ++l) {
+            outp.cx[l] = S.cx[Lc + l];
+            outp.cy[l] = S.cy[Lc + l];
+            bytes += S.vb(Lc + l, 2.0);
+        }
+        const size_t smem = coarsen_tail_smem<T>(S.n[Lc - 1]);
+        if (!S.ctail_attr_set) {   // the largest tail (from a 128-cell level)
+            SCE_TRY(sce_raise_smem_limit((const void *)coarsen_tail_kernel<T>,
+                                         coarsen_tail_smem<T>(128)));
+            S.ctail_attr_set = true;
+        }
+        SceProf pr(KP_COARSEN, st, bytes);
+        coarsen_tail_kernel<T><<<count, 256, smem, st>>>(S.cx[Lc - 1], S.cy[Lc - 1],
+                                                         S.n[Lc - 1], outp, nout);
     }
     SCE_CUDA(cudaGetLastError());
-    {
+    // u = the lifting of the Dirichlet data, unless a first iterate is given
+    // (set_u_kernel below then writes every vertex of u)
+    if (!u_init) {
         SceProf pr(KP_OUTER_UPD, st, S.vb(0, 0.0, 8.0));
         lift_kernel<<<g0, l0.tpb, 0, st>>>(o, n0, l0.vpt);
     }
@@ -1206,16 +1440,33 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     // a given first iterate: the stopping rule stays relative to the lifting's
     // residual (orr0 above); refinement starts from u_init's residual
     if (u_init) {
-        if (l0.vpt == 8) set_u_kernel<O, 8><<<g0, l0.tpb, 0, st>>>(o, u_init, n0, 8);
-        else set_u_kernel<O><<<g0, l0.tpb, 0, st>>>(o, u_init, n0, l0.vpt);
+        {
+            // reads the coarse solution (8 B per coarse vertex), writes u (8 B)
+            SceProf pr(KP_OUTER_UPD, st, S.vb(0, 0.0, 10.0));
+            if constexpr (mixed) {
+                if (u_ff) {
+                    const float2 *uf = reinterpret_cast<const float2 *>(u_init);
+                    if (l0.vpt == 8)
+                        set_u_ff_kernel<8><<<g0, l0.tpb, 0, st>>>(o, uf, n0, 8, row_magic(n0 + 1));
+                    else
+                        set_u_ff_kernel<><<<g0, l0.tpb, 0, st>>>(o, uf, n0, l0.vpt,
+                                                                 row_magic(n0 + 1));
+                }
+            }
+            if (!(mixed && u_ff)) {
+                if (l0.vpt == 8) set_u_kernel<O, 8><<<g0, l0.tpb, 0, st>>>(o, u_init, n0, 8);
+                else set_u_kernel<O><<<g0, l0.tpb, 0, st>>>(o, u_init, n0, l0.vpt);
+            }
+        }
         {
             SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 24.0));
             if (l0.vpt == 8)
                 outer_residual_kernel<T, O, 8><<<g0, l0.tpb, 0, st>>>(
-                    o, F, n0, 8, S.b[0], S.part, l0.nblk, S.sc.act_out);
+                    o, F, n0, 8, S.b[0], S.part, l0.nblk, S.sc.act_out, row_magic(n0 + 1));
             else
                 outer_residual_kernel<T, O><<<g0, l0.tpb, 0, st>>>(
-                    o, F, n0, l0.vpt, S.b[0], S.part, l0.nblk, S.sc.act_out);
+                    o, F, n0, l0.vpt, S.b[0], S.part, l0.nblk, S.sc.act_out,
+                    row_magic(n0 + 1));
         }
         SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
         S.reduce(RED_ORR, S.sc.act_out, rtol2, in_rel2);
@@ -1225,37 +1476,45 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     SCE_TRY(S.read_counter(&n_act));
     int total_inner = 0;
 
-    // one CG iteration: p = z + beta p, the deferred d += alpha p, q = A p,
-    // alpha, r -= alpha q, |r|^2 ...
+    // one CG iteration: beta from the preconditioner's r.z partials, p = z +
+    // beta p, the deferred d += alpha p, q = A p (partials of p.q in part2);
+    // alpha from them, r -= alpha q (partials of r.r in part), |r|^2 ...
+    const int rz_nblk = S.fused ? S.rz_blocks() : l0.nblk;
+    const int fold = cg_fold_mode();
     auto iter_head = [&]() -> int {
         T *pin = S.par ? S.p : S.p2, *pout = S.par ? S.p2 : S.p;
         {
             // reads cx, cy, z, p_in, d; writes p_out, d, q
             SceProf pr(KP_SPMV, st, S.vb(0, 8.0));
             if (l0.vpt == 8)
-                pspmv_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.z[0], pin, pout, S.q,
-                                                          S.d, S.sc.beta, S.sc.alpha, n0, 8,
-                                                          S.part, l0.nblk, S.sc.act_in);
+                pspmv_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.z[0], pin, pout,
+                                                          S.q, S.d, S.part, rz_nblk, S.sc, count,
+                                                          S.par, fold, n0, 8, S.part2, l0.nblk,
+                                                          S.sc.act_in);
             else
                 pspmv_kernel<T><<<g0, l0.tpb, 0, st>>>(S.cx[0], S.cy[0], S.z[0], pin, pout, S.q,
-                                                       S.d, S.sc.beta, S.sc.alpha, n0, l0.vpt,
-                                                       S.part, l0.nblk, S.sc.act_in);
+                                                       S.d, S.part, rz_nblk, S.sc, count, S.par,
+                                                       fold, n0, l0.vpt, S.part2, l0.nblk,
+                                                       S.sc.act_in);
         }
-        S.reduce(RED_ALPHA, S.sc.act_in, 0.0, 0.0, -1, S.par);
+        if (fold == FOLD_NONE) S.reduce(RED_ALPHA, S.sc.act_in, 0.0, 0.0, -1, S.par, S.part2);
         {
             SceProf pr(KP_AXPY, st, S.vb(0, 3.0));
             if (l0.vpt == 8)
-                rupdate_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.b[0], S.q, S.sc.alpha, n0, 8, S.part,
+                rupdate_kernel<T, 8><<<g0, l0.tpb, 0, st>>>(S.b[0], S.q, S.part2, l0.nblk, S.sc,
+                                                            count, S.par, fold, n0, 8, S.part,
                                                             l0.nblk, S.sc.act_in);
             else
-                rupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.q, S.sc.alpha, n0, l0.vpt,
-                                                         S.part, l0.nblk, S.sc.act_in);
+                rupdate_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.q, S.part2, l0.nblk, S.sc,
+                                                         count, S.par, fold, n0, l0.vpt, S.part,
+                                                         l0.nblk, S.sc.act_in);
         }
         SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
         S.reduce(RED_RR, S.sc.act_in);
         return CE_OK;
     };
-    // ... and z = M^-1 r, beta (the p update is the next iteration's fused pass)
+    // ... and z = M^-1 r with its r.z partials, then beta (FOLD_BOTH: formed by
+    // the next CG pass; the p update is part of it)
     auto iter_tail = [&]() -> int {
         if (S.fused) {
             S.vcycle_fused(true);
@@ -1266,7 +1525,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
             dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.z[0], n0, l0.vpt, S.part, l0.nblk,
                                                  S.sc.act_in);
         }
-        S.reduce(RED_BETA, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
+        if (fold != FOLD_BOTH) S.reduce(RED_BETA, S.sc.act_in, 0.0, 0.0, rz_nblk);
         S.par ^= 1;
         return CE_OK;
     };
@@ -1304,10 +1563,18 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     };
     for (int outer = 0; outer < 64 && n_act > 0 && total_inner < maxit; ++outer) {
         // inner PCG on the correction equation, samples with act_in set; no
-        // pending d update and p_0 = z (alpha = beta = 0)
+        // pending d update (alpha = 0) and p_0 = z (beta = 0; folded: the r.z
+        // slot of iteration -1 holds 0)
         SCE_CUDA(cudaMemsetAsync(S.d, 0, c0 * sizeof(T), st));
         SCE_CUDA(cudaMemsetAsync(S.sc.alpha, 0, (size_t)count * sizeof(double), st));
-        SCE_CUDA(cudaMemsetAsync(S.sc.beta, 0, (size_t)count * sizeof(double), st));
+        if (sizeof(T) == 4 && fold != FOLD_NONE)
+            SCE_CUDA(cudaMemsetAsync(S.sc.alphaf, 0, (size_t)count * sizeof(float), st));
+        if (fold != FOLD_BOTH)
+            SCE_CUDA(cudaMemsetAsync(S.sc.beta, 0, (size_t)count * sizeof(double), st));
+        else if (sizeof(T) == 4)
+            SCE_CUDA(cudaMemsetAsync(S.sc.rzf + count, 0, (size_t)count * sizeof(float2), st));
+        else
+            SCE_CUDA(cudaMemsetAsync(S.sc.rz + count, 0, (size_t)count * sizeof(double), st));
         S.par = 0;
         if (S.fused) {
             S.vcycle_fused(true);
@@ -1318,7 +1585,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
             dot_kernel<T><<<g0, l0.tpb, 0, st>>>(S.b[0], S.z[0], n0, l0.vpt, S.part, l0.nblk,
                                                  S.sc.act_in);
         }
-        S.reduce(RED_RZ0, S.sc.act_in, 0.0, 0.0, S.fused ? S.rz_blocks() : -1);
+        if (fold != FOLD_BOTH) S.reduce(RED_RZ0, S.sc.act_in, 0.0, 0.0, rz_nblk);
         int in_act = n_act;
         for (int it = 0; it < inner_max && in_act > 0 && total_inner < maxit;) {
             // four iterations as one graph launch when they fit the budgets (the
@@ -1359,10 +1626,11 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
             SceProf pr(KP_OUTER_RES, st, S.vb(0, 1.0, 24.0));
             if (l0.vpt == 8)
                 outer_residual_kernel<T, O, 8><<<g0, l0.tpb, 0, st>>>(
-                    o, F, n0, 8, S.b[0], S.part, l0.nblk, S.sc.act_out);
+                    o, F, n0, 8, S.b[0], S.part, l0.nblk, S.sc.act_out, row_magic(n0 + 1));
             else
                 outer_residual_kernel<T, O><<<g0, l0.tpb, 0, st>>>(
-                    o, F, n0, l0.vpt, S.b[0], S.part, l0.nblk, S.sc.act_out);
+                    o, F, n0, l0.vpt, S.b[0], S.part, l0.nblk, S.sc.act_out,
+                    row_magic(n0 + 1));
         }
         SCE_CUDA(cudaMemsetAsync(S.sc.counter, 0, sizeof(int), st));
         S.reduce(RED_ORR, S.sc.act_out, rtol2, in_rel2);
@@ -1377,15 +1645,24 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         qoi_partial_kernel<<<g0, l0.tpb, 0, st>>>(o, n0, l0.vpt, S.part, S.part2, l0.nblk,
                                                   qmask);
     }
-    SCE_CUDA(cudaMemsetAsync(S.misc + 1, 0, sizeof(int), st));
-    qoi_final_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(
-        grid_qoi ? S.part : nullptr, grid_qoi ? S.part2 : nullptr, l0.nblk, count, o, n0,
-        p->f, S.sc, rtol2, qoi, iters, status, S.misc + 1, qmask);
-    max_int_kernel<<<1, 256, 0, st>>>(S.sc.iters, count, S.misc + 2);
+    SCE_CUDA(cudaMemsetAsync(S.misc + 1, 0, 3 * sizeof(int), st));
+    {
+        // one warp per sample (launch-latency bound, like the level sums)
+        SceProf pr(KP_LEVEL, st, (double)count * 64.0);
+        qoi_final_kernel<<<(count * 32 + 255) / 256, 256, 0, st>>>(
+            grid_qoi ? S.part : nullptr, grid_qoi ? S.part2 : nullptr, l0.nblk, count, o, n0,
+            p->f, S.sc, rtol2, qoi, iters, status, S.misc + 1, qmask);
+    }
     SCE_CUDA(cudaGetLastError());
     if (u_out) {
         if constexpr (mixed) {
-            u_to_double_kernel<<<g0, l0.tpb, 0, st>>>(o, n0, l0.vpt, u_out);
+            if (u_ff) {   // the float-float pairs as they are
+                SCE_CUDA(cudaMemcpyAsync(u_out, S.uff, c0 * sizeof(float2),
+                                         cudaMemcpyDeviceToDevice, st));
+            } else {
+                SceProf pr(KP_COPY, st, S.vb(0, 0.0, 16.0));
+                u_to_double_kernel<<<g0, l0.tpb, 0, st>>>(o, n0, l0.vpt, u_out);
+            }
         } else {
             SCE_CUDA(cudaMemcpyAsync(u_out, S.u64, c0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
         }
@@ -1414,22 +1691,23 @@ extern "C" int darcy_solver_cache_clear(void *stream) {
 
 int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                         int *n_failed_out, int qmask, const double *u_init) {
+                         int *n_failed_out, int qmask, const double *u_init, bool u_ff) {
     if (!p || !k || !qoi || count < 0) return CE_ERR_INVALID_ARG;
     if (!is_pow2(p->n) || p->n < 4 || p->n > 4096) return CE_ERR_INVALID_ARG;
     if (p->precision != 32 && p->precision != 64) return CE_ERR_INVALID_ARG;
     if (!(p->rtol > 0) || count > 65535) return CE_ERR_INVALID_ARG;
     if (count == 0) return CE_OK;
     qmask &= 7;
+    if (u_ff && p->precision != 32) return CE_ERR_INVALID_ARG;
     if (p->precision == 32 && p->n <= sce_small_max_n() && p->n <= 64)
         return sce_darcy_small(p, (const float *)k, count, qoi, iters, status, u_out, st,
-                               max_iters_out, n_failed_out, qmask);
+                               max_iters_out, n_failed_out, qmask | (u_ff ? 8 : 0));
     if (p->precision == 64)
         return darcy_solve_t<double, double>(p, (const double *)k, count, qoi, iters, status,
                                              u_out, st, max_iters_out, n_failed_out, qmask,
-                                             u_init);
+                                             u_init, false);
     return darcy_solve_t<float, float>(p, (const float *)k, count, qoi, iters, status, u_out, st,
-                                       max_iters_out, n_failed_out, qmask, u_init);
+                                       max_iters_out, n_failed_out, qmask, u_init, u_ff);
 }
 
 extern "C" int darcy_solve_batch(const darcy_problem *p, const void *k, int count, double *qoi,

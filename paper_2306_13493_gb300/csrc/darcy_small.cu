@@ -103,8 +103,7 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             const int j = v / W, i = v - j * W;
             float rv = 0.f;
             if (i > 0 && i < N) {
-                rv = ff_sub(Fv[(j > 0 && j < N) ? 1 : 0],
-                            apply_at_ff(cx0, cxl, cy0, cyl, u, i, j, N)).hi;
+                rv = resid_at_ff((j > 0 && j < N) ? Fv[1] : Fv[0], cx0, cxl, cy0, cyl, u, i, j, N);
                 acc += rv * rv;
             }
             r[v] = rv;
@@ -124,7 +123,7 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             const int j = v / W, i = v - j * W;
             float rv = 0.f;
             if (i > 0 && i < N) {
-                ff rf = Fv[(j > 0 && j < N) ? 1 : 0];
+                ff rf = (j > 0 && j < N) ? Fv[1] : Fv[0];
                 if (i == 1) rf = ff_add(rf, ff{cx0[v - 1], cxl[v - 1]});
                 rv = rf.hi;
                 acc += rv * rv;
@@ -210,7 +209,10 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
                 const double s1 = a + b + c, s2 = a + e + c;
                 l2 += s1 * s1 + a * a + b * b + c * c + s2 * s2 + a * a + e * e + c * c;
             }
-            if (u_out) u_out[(size_t)s * V + v] = ud(v);
+            if (u_out) {
+                if (qmask & 8) reinterpret_cast<float2 *>(u_out)[(size_t)s * V + v] = u[v];
+                else u_out[(size_t)s * V + v] = ud(v);
+            }
         }
         qo = bsum1<NT>(qo, sh, pard);
         l2 = bsum1<NT>(l2, sh, pard);

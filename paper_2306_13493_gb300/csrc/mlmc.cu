@@ -100,6 +100,8 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
     void *kf = nullptr, *kc = nullptr;
     double *qf = nullptr, *qc = nullptr, *Yd = nullptr, *sums = nullptr;
     double *ucs = nullptr;   // nested iteration: the coarse solution
+    // FP32 problems hand it over as float-float pairs (8 bytes per vertex, as a double)
+    const bool ff_hand = p->precision == 32;
     cudaEvent_t ev_field = nullptr, ev_coarse = nullptr;
     std::vector<void *> owned;
     auto cleanup = [&]() {
@@ -181,12 +183,12 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
         int mi[2] = {0, 0}, nf = 0;
         if (nested) {
             rc = sce_darcy_solve_impl(&pc, kc, cn, qc_c, nullptr, nullptr, ucs, st, mi_c, &nf_c,
-                                      qmask_c);
+                                      qmask_c, nullptr, ff_hand);
             if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
             account(rc, mi_c, nf_c);
         }
         rc = sce_darcy_solve_impl(&pf, kf, cn, qf_c, nullptr, nullptr, nullptr, st, mi, &nf,
-                                  qmask_f, nested ? ucs : nullptr);
+                                  qmask_f, nested ? ucs : nullptr, ff_hand);
         const int rc_c = split ? fut.get() : CE_OK;
         if (split && rc_c != CE_OK && rc_c != CE_ERR_NOT_CONVERGED) sce_set_last_error_text(coarse_err);
         if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
@@ -201,8 +203,14 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
             if (rc != CE_OK && rc != CE_ERR_NOT_CONVERGED) { cleanup(); return rc; }
             account(rc, mi, nf);
         }
-        level_diff_kernel<<<(cn + 255) / 256, 256, 0, st>>>(qf_c, qc_c, cn, qoi_index, Y_c);
-        level_sums_kernel<<<1, 256, 0, st>>>(Y_c, qf_c, cn, qoi_index, sums);
+        {
+            SceProf pr(KP_LEVEL, st, (double)cn * 32.0);
+            level_diff_kernel<<<(cn + 255) / 256, 256, 0, st>>>(qf_c, qc_c, cn, qoi_index, Y_c);
+        }
+        {
+            SceProf pr(KP_LEVEL, st, (double)cn * 16.0);
+            level_sums_kernel<<<1, 256, 0, st>>>(Y_c, qf_c, cn, qoi_index, sums);
+        }
         if (cudaGetLastError() != cudaSuccess) { cleanup(); return CE_ERR_CUDA; }
         double h[4];
         if (cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

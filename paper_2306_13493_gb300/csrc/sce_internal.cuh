@@ -125,7 +125,8 @@ int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
                           int count, int precision, void *k_fine, void *k_coarse, cudaStream_t st,
                           const QmcArgs *qa = nullptr);
 
-// One-block-per-sample solver for small grids (mixed precision).
+// One-block-per-sample solver for small grids (mixed precision).  qmask bit 3:
+// u_out holds float-float pairs (float2) instead of doubles.
 int sce_small_max_n();
 int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
                     int *status, double *u_out, cudaStream_t st, int *max_iters_out,
@@ -138,7 +139,11 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
 // NULL = the lifting): the solution of the same field on the n/2-cell grid,
 // whose bilinear prolongation is the batched solver's first iterate; the
 // convergence test stays relative to the lifting's residual.  The one-block
-// solver (small n) ignores it.
+// solver (small n) ignores it.  u_ff (FP32 problems only): u_out and u_init
+// hold float-float pairs (float2, hi + lo) instead of doubles -- the mixed
+// path's own representation, so the hand-over between the coarse and the fine
+// solve of a level needs no FP64 arithmetic.
 int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, double *qoi, int *iters,
                          int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                         int *n_failed_out, int qmask, const double *u_init = nullptr);
+                         int *n_failed_out, int qmask, const double *u_init = nullptr,
+                         bool u_ff = false);

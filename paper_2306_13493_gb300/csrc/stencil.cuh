@@ -43,44 +43,69 @@ __device__ __forceinline__ void cond_at(const Tk *ks, int i, int j, int n, doubl
 __device__ __forceinline__ ff ff_sixth() { return {0x1.555556p-3f, -0x1.555556p-28f}; }
 
 // cond_at in float-float from FP32 k: the same sums of at most six vertex
-// values and one scaling by 1/6.
+// values and one scaling by 1/6.  The two triangles of an edge share the two
+// vertex values a, b of the edge itself, so an interior edge sums to
+// 2 (a + b) + c + d: TwoSum(a, b), an exact doubling, and two float-float +
+// float additions (positive terms: no cancellation, relative error ~2^-47).
 __device__ __forceinline__ void cond_at_ff(const float *ks, int i, int j, int n, ff *gx, ff *gy) {
     const int w = n + 1, v = j * w + i;
     const float a = ks[v];
-    const float b = i < n ? ks[v + 1] : 0.0f;
-    const float e = j < n ? ks[v + w] : 0.0f;
-    const float c = (i < n && j < n) ? ks[v + w + 1] : 0.0f;
     ff x = {0.0f, 0.0f}, y = {0.0f, 0.0f};
     if (i < n) {
-        const ff ab = two_sum(a, b);
-        if (j < n) x = ff_add_f(ab, c);
-        if (j > 0) x = ff_add(x, ff_add_f(ab, ks[v - w]));
+        const float b = ks[v + 1];                       // k(i+1, j)
+        x = two_sum(a, b);
+        if (j > 0 && j < n) x = {2.0f * x.hi, 2.0f * x.lo};
+        if (j < n) x = ff_add_f(x, ks[v + w + 1]);      // T1(i, j): k(i+1, j+1)
+        if (j > 0) x = ff_add_f(x, ks[v - w]);          // T2(i, j-1): k(i, j-1)
         x = ff_mul(x, ff_sixth());
     }
     if (j < n) {
-        const ff ae = two_sum(a, e);
-        if (i < n) y = ff_add_f(ae, c);
-        if (i > 0) y = ff_add(y, ff_add_f(ae, ks[v - 1]));
+        const float e = ks[v + w];                       // k(i, j+1)
+        y = two_sum(a, e);
+        if (i > 0 && i < n) y = {2.0f * y.hi, 2.0f * y.lo};
+        if (i < n) y = ff_add_f(y, ks[v + w + 1]);      // T2(i, j): k(i+1, j+1)
+        if (i > 0) y = ff_add_f(y, ks[v - 1]);          // T1(i-1, j): k(i-1, j)
         y = ff_mul(y, ff_sixth());
     }
     *gx = x;
     *gy = y;
 }
 
-// (A u)(i, j) of an unknown vertex in float-float: u as (hi, lo) pairs,
-// conductances hi (cx, cy) + lo (cxl, cyl); differences of u are formed
-// before the products (both exact-ish in float-float).
-__device__ __forceinline__ ff apply_at_ff(const float *cx, const float *cxl, const float *cy,
-                                          const float *cyl, const float2 *u, int i, int j,
-                                          int n) {
+// F - (A u)(i, j) at an unknown vertex, rounded once to FP32: the residual of
+// the float-float refinement.  u as (hi, lo) pairs, conductances hi (cx, cy) +
+// lo (cxl, cyl), F a float-float.  For every edge to a neighbour nb:
+//   u_c - u_nb = TwoSum of the hi parts (exact) + the difference of the lo
+//                parts (two FP32 roundings of terms below ulp(u));
+//   c (u_c - u_nb) = TwoProduct of the hi parts (exact) + the cross terms
+//                c_hi * d_lo + c_lo * d_hi (fused, the c_lo * d_lo term is
+//                below 2^-48 of the product and dropped);
+// F.hi minus the four product hi parts is summed by a cascade of TwoSums, and
+// their rounding errors together with every low-order term in plain FP32
+// (Algorithm Sum2 of Ogita, Rump and Oishi, "Accurate sum and dot product",
+// 2005); the two sums are added once at the end.  The error stays of the
+// order 2^-48 of |u| and of the products, the resolution of the float-float
+// operands themselves, at about 80 FP32 operations against ~190 for composing
+// float-float subtractions, products and sums.
+__device__ __forceinline__ float resid_at_ff(ff F, const float *cx, const float *cxl,
+                                             const float *cy, const float *cyl, const float2 *u,
+                                             int i, int j, int n) {
     const int w = n + 1, v = j * w + i;
-    auto U = [&](int q) { const float2 t = u[q]; return ff{t.x, t.y}; };
-    const ff uc = U(v);
-    ff a = ff_mul(ff{cx[v - 1], cxl[v - 1]}, ff_sub(uc, U(v - 1)));
-    a = ff_add(a, ff_mul(ff{cx[v], cxl[v]}, ff_sub(uc, U(v + 1))));
-    if (j > 0) a = ff_add(a, ff_mul(ff{cy[v - w], cyl[v - w]}, ff_sub(uc, U(v - w))));
-    if (j < n) a = ff_add(a, ff_mul(ff{cy[v], cyl[v]}, ff_sub(uc, U(v + w))));
-    return a;
+    const float2 uc = u[v];
+    float p = F.hi, sig = F.lo;
+    auto edge = [&](float ch, float cl, float2 un) {
+        const ff d = two_sum(uc.x, -un.x);
+        const float dl = __fadd_rn(d.lo, __fsub_rn(uc.y, un.y));
+        const ff pr = two_prod(ch, d.hi);
+        const float pl = __fmaf_rn(cl, d.hi, __fmaf_rn(ch, dl, pr.lo));
+        const ff t = two_sum(p, -pr.hi);
+        p = t.hi;
+        sig = __fadd_rn(sig, __fsub_rn(t.lo, pl));
+    };
+    edge(cx[v - 1], cxl[v - 1], u[v - 1]);
+    edge(cx[v], cxl[v], u[v + 1]);
+    if (j > 0) edge(cy[v - w], cyl[v - w], u[v - w]);
+    if (j < n) edge(cy[v], cyl[v], u[v + w]);
+    return __fadd_rn(p, sig);
 }
 
 // Series conductance a b / (a + b) of two edges.  It only enters the

@@ -182,6 +182,48 @@ def test_graph_replay_matches_stream_launches(sce, precision, maxit, monkeypatch
             assert rc1 == sce.CE_ERR_NOT_CONVERGED and np.all(i1 <= 6)
 
 
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("graphs", ["0", "1"])
+def test_folded_cg_scalars_match_reduction_launches(sce, precision, graphs, monkeypatch):
+    """CG's alpha (SCE_CG_FOLD=1, the default) or alpha and beta (2) formed
+    inside the CG kernels (every block sums the partials in the fixed order)
+    against the separate reduction launches (0), on the tiled (n = 256) and
+    the fused n = 64 V-cycle.  FP64: all three sum in FP64 in the same order,
+    so QoIs, iteration counts and statuses agree bit for bit.  FP32: the
+    folded scalars are formed in float-float and FP32 (the launches in FP64),
+    so the solves take slightly different rounding paths to the same
+    tolerance: QoIs within 10 rtol |Q|, iteration counts within one."""
+    import torch
+    for n in (256, 64):
+        count = 3
+        k_np = _oracle_k(n, count, lam=0.05, seed=9, precision=precision)
+        out = []
+        for fold in ("0", "1", "2"):
+            monkeypatch.setenv("SCE_CG_FOLD", fold)
+            monkeypatch.setenv("SCE_GRAPHS", graphs)
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                k = torch.tensor(k_np, dtype=torch_dtype(precision), device="cuda")
+                qoi = torch.empty(count, 3, dtype=torch.float64, device="cuda")
+                iters = torch.empty(count, dtype=torch.int32, device="cuda")
+                status = torch.empty(count, dtype=torch.int32, device="cuda")
+                rc = sce.darcy_solve_batch(n, k, count, qoi, f=1.0, rtol=1e-12,
+                                           precision=precision, iters=iters, status=status,
+                                           stream=s.cuda_stream)
+            s.synchronize()
+            sce.darcy_solver_cache_clear()
+            out.append((rc, qoi.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()))
+        rc0, q0, i0, s0 = out[0]
+        assert rc0 == 0 and np.all(s0 == 0)
+        for rc1, q1, i1, s1 in out[1:]:
+            assert rc1 == 0 and np.all(s1 == 0)
+            if precision == 64:
+                assert np.array_equal(q0, q1) and np.array_equal(i0, i1)
+            else:
+                assert np.max(np.abs(q0 - q1)) < 10 * 1e-12 * max(1.0, np.max(np.abs(q0)))
+                assert np.max(np.abs(i0 - i1)) <= 1
+
+
 def test_cached_graphs_give_the_same_mlmc_step(sce, monkeypatch):
     """Two all-levels MLMC calls with SCE_GRAPHS=1 (the second reusing every
     level's cached solver and graph) give the per-sample Y and level sums of
@@ -224,8 +266,10 @@ def test_tile_heights_give_the_same_solves(sce, precision, monkeypatch):
     rows) computes each vertex of a V-cycle identically; only the order in
     which the per-tile partial sums of r . z are added follows the tiling.
     The solutions and QoIs of a random field on n = 256 (tiled levels 256
-    and 128, ragged tiles at the grid's edges) agree to rounding across
-    heights, and match the oracle's direct solve."""
+    and 128, ragged tiles at the grid's edges) match the oracle's direct
+    solve, and agree across heights to the accuracy of two solves stopped at
+    rtol = 1e-12 on different rounding paths: QoIs within 10 rtol |Q|, u
+    within 1e-10, iteration counts within one."""
     n, count = 256, 3
     k = _oracle_k(n, count, lam=0.05, seed=4, precision=precision)
     ref = None
@@ -238,9 +282,9 @@ def test_tile_heights_give_the_same_solves(sce, precision, monkeypatch):
             Q = np.array([odarcy.solve_qois(k[i].astype(np.float64), 1.0) for i in range(count)])
             assert np.max(np.abs(q - Q)) < QOI_TOL
         else:
-            assert np.max(np.abs(q - ref[0])) < 1e-12, h
+            assert np.max(np.abs(q - ref[0])) < 10 * 1e-12 * max(1.0, np.max(np.abs(ref[0]))), h
             assert np.max(np.abs(it - ref[1])) <= 1, h
-            assert np.max(np.abs(u - ref[2])) < 1e-11, h
+            assert np.max(np.abs(u - ref[2])) < 1e-10, h
 
 
 def test_tile_autotuner_picks_a_height(sce, monkeypatch):
@@ -251,8 +295,9 @@ def test_tile_autotuner_picks_a_height(sce, monkeypatch):
     h = sce.darcy_autotune_tiles(n, 32, count=64, reps=1)
     assert h in (16, 24, 32, 48)
     after = _solve(sce, k, 32, f=1.0)
-    assert np.max(np.abs(before[1] - after[1])) < 1e-12
-    assert np.max(np.abs(before[4] - after[4])) < 1e-11
+    # another window height: the same solve up to the stopping tolerance (rtol 1e-12)
+    assert np.max(np.abs(before[1] - after[1])) < 10 * 1e-12 * max(1.0, np.max(np.abs(before[1])))
+    assert np.max(np.abs(before[4] - after[4])) < 1e-10
     with pytest.raises(sce.SceError):
         sce.darcy_autotune_tiles(64, 32)
 
