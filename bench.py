@@ -751,11 +751,12 @@ def precision_study(args):
 # bandwidth); the row pass (Philox, Box-Muller, butterflies), the one-block
 # solver (whole solve in shared memory) and the fused n = 64 V-cycle (one
 # level in registers, the levels below in shared memory) are bound by
-# instruction issue and barriers; the
-# reductions (one warp per sample over a few partials) by launch latency.  The
+# instruction issue and barriers; the reductions and the level sums (one warp
+# per sample over a few partials) and the coarsening of the levels of at most
+# 64 cells (one block per sample, a few microseconds) by launch latency.  The
 # rest are HBM-bound.
 KERNEL_BOUND = {"mg_tail": "l2", "ce_row": "issue", "darcy_small": "issue", "mg_v64": "issue",
-                "reduce": "latency", "level_sums": "latency"}
+                "reduce": "latency", "level_sums": "latency", "coarsen_tail": "latency"}
 
 
 def measure_peaks(sce, stream, reps=10):

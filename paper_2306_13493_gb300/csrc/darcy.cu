@@ -1409,7 +1409,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
                                          coarsen_tail_smem<T>(128)));
             S.ctail_attr_set = true;
         }
-        SceProf pr(KP_COARSEN, st, bytes);
+        SceProf pr(KP_COARSEN_TAIL, st, bytes);
         coarsen_tail_kernel<T><<<count, 256, smem, st>>>(S.cx[Lc - 1], S.cy[Lc - 1],
                                                          S.n[Lc - 1], outp, nout);
     }
@@ -1422,7 +1422,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     }
 
     const double rtol2 = p->rtol * p->rtol;
-    const double in_rel = sizeof(T) == 4 ? 1e-5 : 0.0;
+    const double in_rel = sizeof(T) == 4 ? sce_inner_rel_f32() : 0.0;
     const double in_rel2 = in_rel * in_rel;
     const int maxit = p->maxit > 0 ? p->maxit : 1000;
     const int inner_max = sizeof(T) == 4 ? 40 : maxit;

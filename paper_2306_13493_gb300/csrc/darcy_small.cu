@@ -248,7 +248,7 @@ int launch_small(const darcy_problem *p, const float *k, int count, double *qoi,
                  int *status, double *u_out, int *misc, int qmask, cudaStream_t st) {
     const size_t smem = SmallLayout<N>::bytes;
     SCE_TRY(sce_raise_smem_limit((const void *)small_solve_kernel<N, NT>, smem));
-    const double in_rel = 1e-5;
+    const double in_rel = sce_inner_rel_f32();
     SceProf pr(KP_SMALL, st, (double)count * SmallLayout<N>::V * (sizeof(float) + 0.0) + 24.0 * count);
     small_solve_kernel<N, NT><<<count, NT, smem, st>>>(k, p->f, p->rtol * p->rtol, in_rel * in_rel,
                                                        p->maxit > 0 ? p->maxit : 1000, qoi, iters,

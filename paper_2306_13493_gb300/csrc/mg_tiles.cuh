@@ -46,28 +46,30 @@ constexpr int MG_SW = 64;                  // window width: 32 lanes x 2 columns
 #define SCE_MG_SH 32
 #endif
 constexpr int MG_SH = SCE_MG_SH;           // window height: MG_SH / 4 warps x 4 rows
+#ifndef SCE_TILE_WARPS_PER_SM
+#define SCE_TILE_WARPS_PER_SM 40
+#endif
 constexpr int MG_NW = MG_SH / 4;           // warps per block
 constexpr int MG_CW = (MG_SW - 6) / 2;     // 29 coarse vertices per tile in x
 constexpr int MG_CH = (MG_SH - 6) / 2;     // 13 coarse vertices per tile in y
 constexpr int MG_THREADS = 32 * MG_NW;
-constexpr int MG_BLOCKS_PER_SM = 5 * 256 / MG_THREADS;   // 48 registers per thread (a few bytes spill)
 static_assert(MG_SH % 4 == 0 && MG_NW <= 32, "tile height");
 constexpr int MG_CCW = MG_CW + 3;          // coarse window of mg_up: 32 x 16 (+1 row)
 constexpr int MG_CCH = MG_CH + 3;
 constexpr unsigned MG_FULL = 0xffffffffu;
 
 // Window shape of the tiled kernels by window height SH (the width is always
-// 64): SH / 4 warps, CH coarse vertices per tile in y, and blocks per SM
-// such that a thread keeps 48 registers (each of the four schedulers of an SM
-// has 16384: at most 10 warps of 48 registers, so 40 warps per SM; twice
-// fewer blocks in FP64).  The solver
-// picks SH per grid size (table set by darcy_autotune_tiles; MG_SH otherwise).
+// 64): SH / 4 warps, CH coarse vertices per tile in y, and blocks per SM for
+// SCE_TILE_WARPS_PER_SM resident warps (40: a thread keeps 48 registers,
+// each of the four schedulers of an SM having 16384; 48: 40 registers, a few
+// dozen bytes spilled; twice fewer blocks in FP64).  The solver picks SH per
+// grid size (table set by darcy_autotune_tiles; MG_SH otherwise).
 template <int SH>
 struct MGTile {
     static_assert(SH % 4 == 0 && SH >= 16 && SH <= 64, "tile height");
     static constexpr int H = SH, NW = SH / 4, CH = (SH - 6) / 2, THREADS = 32 * NW;
     static constexpr int CCH = CH + 3;
-    static constexpr int BPS = 40 / NW;
+    static constexpr int BPS = SCE_TILE_WARPS_PER_SM / NW;
 };
 
 // shared memory: z of rows 0 and 3 of every warp (2 buffers), one row per
@@ -100,11 +102,27 @@ template <> __device__ __forceinline__ double recip<double>(double d) { return 1
 // (2 lane + c, 4 warp + r).  Conductances: cxe = cx at the element (edge to
 // the east), cyn = cy (edge to the north); cxw0[r] = west edge of the c = 0
 // column (from lane - 1), cys0[c] = south edge of row 0 (from warp - 1).
+// unk: bitmask of the elements that are unknowns.  1/diag is not stored: each
+// element uses it once per kernel (one half-sweep of its colour, or the first
+// red update from z = 0), so it is formed where it is used (tile_inv), which
+// keeps eight registers free.
 template <typename T>
 struct TileBlock {
-    T b[8], z[8], cxe[8], cyn[8], inv[8], cxw0[4], cys0[2];
+    T b[8], z[8], cxe[8], cyn[8], cxw0[4], cys0[2];
     T zs[2], zn[2];   // z of the rows below (r = -1) and above (r = 4) the strip
+    unsigned unk;
 };
+
+// 1/diag of element (c, r): 1 / (sum of its four edge conductances); 0 where
+// the element is not an unknown (Dirichlet column, outside the grid), so its
+// z stays 0.  c and r are compile-time constants after unrolling.
+template <typename T>
+__device__ __forceinline__ T tile_inv(const TileBlock<T> &t, int c, int r) {
+    const int e = 2 * r + c;
+    const T cw = c == 0 ? t.cxw0[r] : t.cxe[2 * r];
+    const T cs = r == 0 ? t.cys0[c] : t.cyn[2 * (r - 1) + c];
+    return ((t.unk >> e) & 1) ? recip(cw + t.cxe[e] + cs + t.cyn[e]) : T(0);
+}
 
 // Loads b, cx, cy of the block (zero outside the grid); returns the bitmask
 // of elements that are unknowns (1 <= gi <= n-1, 0 <= gj <= n).  inside: the
@@ -149,8 +167,8 @@ __device__ __forceinline__ unsigned tile_load(TileBlock<T> &t, const T *bs, cons
 }
 
 // West/south edge conductances from the neighbouring lane / warp (xrow: one
-// shared row per warp), then 1/diag (0 where not an unknown).  Contains a
-// barrier.  NW: warps of the block.
+// shared row per warp); records the unknowns' mask.  Contains a barrier.
+// NW: warps of the block.
 template <typename T, int NW = MG_NW>
 __device__ __forceinline__ void tile_diag(TileBlock<T> &t, T *xrow, int lane, int warp,
                                           unsigned unk) {
@@ -162,16 +180,7 @@ __device__ __forceinline__ void tile_diag(TileBlock<T> &t, T *xrow, int lane, in
 #pragma unroll
     for (int c = 0; c < 2; ++c)
         t.cys0[c] = warp > 0 ? xrow[(warp - 1) * MG_SW + 2 * lane + c] : T(0);
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int e = 2 * r + c;
-            const T cw = c == 0 ? t.cxw0[r] : t.cxe[2 * r];
-            const T cs = r == 0 ? t.cys0[c] : t.cyn[2 * (r - 1) + c];
-            t.inv[e] = ((unk >> e) & 1) ? recip(cw + t.cxe[e] + cs + t.cyn[e]) : T(0);
-        }
-    }
+    t.unk = unk;
 }
 
 // Publishes rows 0 and 3 of z in buffer buf, waits, and reads the rows below
@@ -224,7 +233,7 @@ __device__ __forceinline__ void tile_half_sweep(TileBlock<T> &t) {
         constexpr int C = (COL + R) & 1, e = 2 * R + C;
         T zw, ze, zsv, znv, cw, cs;
         tile_nbrs<T, C, R, EAST0>(t, &zw, &ze, &zsv, &znv, &cw, &cs);
-        t.z[e] = (t.b[e] + cw * zw + t.cxe[e] * ze + cs * zsv + t.cyn[e] * znv) * t.inv[e];
+        t.z[e] = (t.b[e] + cw * zw + t.cxe[e] * ze + cs * zsv + t.cyn[e] * znv) * tile_inv(t, C, R);
         tile_half_sweep<T, COL, R + 1, EAST0>(t);
     }
 }
@@ -269,7 +278,7 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int e = 2 * r + c;
-            t.z[e] = ((c + r) & 1) == 0 ? t.b[e] * t.inv[e] : T(0);
+            t.z[e] = ((c + r) & 1) == 0 ? t.b[e] * tile_inv(t, c, r) : T(0);
         }
     }
     tile_exchange<T, MG_NW>(t, xz, 0, lane, warp);

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int e = 2 * r + c;
-            t.z[e] = ((c + r) & 1) == 0 ? t.b[e] * t.inv[e] : T(0);
+            t.z[e] = ((c + r) & 1) == 0 ? t.b[e] * tile_inv(t, c, r) : T(0);
         }
     }
     tile_exchange<T, V64_NW>(t, xz, 0, lane, warp);

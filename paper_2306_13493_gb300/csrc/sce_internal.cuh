@@ -88,7 +88,7 @@ enum SceKernel {
     KP_SETUP, KP_NORMALS, KP_LEVEL, KP_SMALL, KP_MG_DOWN, KP_MG_UP, KP_MG_TAIL,
     // three-dimensional path
     KP_X3, KP_Y3, KP_Z3, KP_COND3, KP_SMOOTH3, KP_RESID3, KP_RESTRICT3, KP_PROLONG3, KP_SPMV3,
-    KP_VEC3, KP_OUTER3, KP_MG_V64, KP_LEVELS, KP_COUNT_
+    KP_VEC3, KP_OUTER3, KP_MG_V64, KP_LEVELS, KP_COARSEN_TAIL, KP_COUNT_
 };
 
 bool sce_prof_on();
@@ -124,6 +124,11 @@ struct ce_qmc_s {
 int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint64_t first_sample,
                           int count, int precision, void *k_fine, void *k_coarse, cudaStream_t st,
                           const QmcArgs *qa = nullptr);
+
+// Relative residual drop each inner FP32 PCG solve of the mixed path aims
+// for before the float-float refinement recomputes the residual
+// (SCE_INNER_REL, default 1e-5).
+double sce_inner_rel_f32();
 
 // One-block-per-sample solver for small grids (mixed precision).  qmask bit 3:
 // u_out holds float-float pairs (float2) instead of doubles.
