@@ -46,7 +46,7 @@ TRAFFIC_PER_ALG = {
                     "paper_2306_13493_gb300/csrc/darcy.cu", "pspmv_kernel",
                     "9a76b841323f6d80ce7b0bc9ee4c5a1f56e55f9e4fc43749a2e76bd639234e5b"),
     # n = 512 launch of the tile kernel (profiles/mg_up_n512x32.md)
-    "mg_up": ((143.218432 + 19.509760) / 176.882432,
+    "mg_up": ((143.220224 + 18.703616) / 176.882432,
               "paper_2306_13493_gb300/csrc/mg_tiles.cuh", "mg_up_kernel",
               "6f61a474e9d4bb26e8ddf599ca63a9ee17763655decf7ccee56e53a2a50bfcec"),
 }
