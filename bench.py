@@ -45,10 +45,10 @@ TRAFFIC_PER_ALG = {
     "cg_spmv_dot": ((168.580608 + 63.755776) / 269.485056,
                     "paper_2306_13493_gb300/csrc/darcy.cu", "pspmv_kernel",
                     "9a76b841323f6d80ce7b0bc9ee4c5a1f56e55f9e4fc43749a2e76bd639234e5b"),
-    # n = 512 launch of the tile kernel (profiles/mg_up_n512x32.md)
-    "mg_up": ((143.220224 + 18.703616) / 176.882432,
+    # n = 512 launch of the tile kernel, 48-row windows (profiles/mg_up_n512x32.md)
+    "mg_up": ((143.225856 + 19.805184) / 176.882432,
               "paper_2306_13493_gb300/csrc/mg_tiles.cuh", "mg_up_kernel",
-              "6f61a474e9d4bb26e8ddf599ca63a9ee17763655decf7ccee56e53a2a50bfcec"),
+              "3e1d5f0881eaad1e1963cf2dfe9c59df44e8e21f59a62938ebfc471610ecf5cd"),
 }
 
 

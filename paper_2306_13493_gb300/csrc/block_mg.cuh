@@ -1,4 +1,4 @@
-// Multigrid V(1,1) cycle executed by one thread block on one sample whose
+// Multigrid V(nu, nu) cycle executed by one thread block on one sample whose
 // level arrays are in shared memory (levels N, N/2, ..., 2).  Shared by the
 // one-block-per-sample solver and by the coarse-level tail of the batched
 // solver.  Level sizes and array offsets are compile-time constants (the
@@ -11,6 +11,24 @@
 namespace sce {
 
 constexpr int mg_levels(int n) { return n <= 2 ? 1 : 1 + mg_levels(n / 2); }
+
+// Red-black Gauss-Seidel sweeps before and after each coarse-grid correction,
+// on every level and in every kernel of the batched FP32 solver's cycle:
+// SCE_MG_NU = 2, a V(2,2) cycle (the default: ~27 % fewer CG iterations for
+// ~1.3-1.45 times the work of a cycle), or 1, a V(1,1) cycle.
+#ifndef SCE_MG_NU
+#define SCE_MG_NU 2
+#endif
+constexpr int MG_NU = SCE_MG_NU;
+static_assert(MG_NU == 1 || MG_NU == 2, "sweeps per side of the cycle");
+
+// Sweeps per side for element type T: the FP32 path takes MG_NU; the FP64
+// path keeps V(1,1), since its smoothing runs on GB300's FP64 pipe (~1/64 of
+// the FP32 rate), where V(2,2) measured 10 % slower over a whole sweep.
+template <typename T>
+constexpr int mg_nu() {
+    return sizeof(T) == 4 ? MG_NU : 1;
+}
 
 // Barrier of an NT-thread block: a single-warp block (NT == 32) only needs
 // the warp's own synchronisation, which also orders its shared-memory
@@ -47,23 +65,23 @@ __device__ __forceinline__ void block_half_sweep(const T *cx, const T *cy, const
     }
 }
 
-template <typename T, int N, int NT, class Lay, int L, int WARP_N = 0>
+template <typename T, int N, int NT, class Lay, int L, int WARP_N, int NU>
 __device__ __forceinline__ void block_vcycle_level(T *base);
 
 // The V-cycle from level L down and back up: with WARP_N > 0 in a block of
 // more than one warp, the levels of at most WARP_N cells run on warp 0 alone
 // (warp synchronisation) while the other warps wait at one block barrier.
-template <typename T, int N, int NT, class Lay, int L, int WARP_N>
+template <typename T, int N, int NT, class Lay, int L, int WARP_N, int NU>
 __device__ __forceinline__ void block_vcycle_from(T *base) {
     if constexpr (NT > 32 && WARP_N > 0 && (N >> L) <= WARP_N) {
-        if (threadIdx.x < 32) block_vcycle_level<T, N, 32, Lay, L, 0>(base);
+        if (threadIdx.x < 32) block_vcycle_level<T, N, 32, Lay, L, 0, NU>(base);
         __syncthreads();
     } else {
-        block_vcycle_level<T, N, NT, Lay, L, WARP_N>(base);
+        block_vcycle_level<T, N, NT, Lay, L, WARP_N, NU>(base);
     }
 }
 
-template <typename T, int N, int NT, class Lay, int L, int WARP_N>
+template <typename T, int N, int NT, class Lay, int L, int WARP_N, int NU>
 __device__ __forceinline__ void block_vcycle_level(T *base) {
     constexpr int NL = mg_levels(N);
     constexpr int nL = N >> L;
@@ -75,26 +93,32 @@ __device__ __forceinline__ void block_vcycle_level(T *base) {
     } else {
         constexpr int nc = nL / 2, wc = nc + 1, Vc = wc * wc, wL = nL + 1, VL = wL * wL;
         T *bc = base + Lay::off(L + 1, 2), *zc = base + Lay::off(L + 1, 3);
-        block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
-        block_sync<NT>();
-        block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
-        block_sync<NT>();
+#pragma unroll
+        for (int k = 0; k < NU; ++k) {
+            block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
+            block_sync<NT>();
+            block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
+            block_sync<NT>();
+        }
         for (int v = threadIdx.x; v < Vc; v += NT) {
             const int J = v / wc, I = v - J * wc;
             bc[v] = (I > 0 && I < nc) ? restrict_at(cx, cy, b, z, nL, I, J) : T(0);
             zc[v] = T(0);
         }
         block_sync<NT>();
-        block_vcycle_from<T, N, NT, Lay, L + 1, WARP_N>(base);
+        block_vcycle_from<T, N, NT, Lay, L + 1, WARP_N, NU>(base);
         for (int v = threadIdx.x; v < VL; v += NT) {
             const int j = v / wL, i = v - j * wL;
             if (i > 0 && i < nL) z[v] += prolong_at(zc, nc, i, j);
         }
         block_sync<NT>();
-        block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
-        block_sync<NT>();
-        block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
-        block_sync<NT>();
+#pragma unroll
+        for (int k = 0; k < NU; ++k) {
+            block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
+            block_sync<NT>();
+            block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
+            block_sync<NT>();
+        }
     }
 }
 
@@ -118,14 +142,15 @@ __device__ __forceinline__ void block_coarsen(T *base) {
 }
 
 // z = M^{-1} b on level 0 of the hierarchy laid out by Lay from `base`.
-// Symmetric: red-black Gauss-Seidel before the restriction, black-red after
-// the prolongation, exact solve on 2 cells.  All NT threads must call it.
-template <typename T, int N, int NT, class Lay, int WARP_N = 0>
+// Symmetric: NU red-black Gauss-Seidel sweeps before the restriction, NU
+// black-red sweeps after the prolongation, exact solve on 2 cells.  All NT
+// threads must call it.
+template <typename T, int N, int NT, class Lay, int WARP_N = 0, int NU = mg_nu<T>()>
 __device__ __forceinline__ void block_vcycle(T *base) {
     T *z = base + Lay::off(0, 3);
     for (int v = threadIdx.x; v < mg_vof(N); v += NT) z[v] = T(0);
     block_sync<NT>();
-    block_vcycle_from<T, N, NT, Lay, 0, WARP_N>(base);
+    block_vcycle_from<T, N, NT, Lay, 0, WARP_N, NU>(base);
 }
 
 }  // namespace sce

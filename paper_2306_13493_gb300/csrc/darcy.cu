@@ -14,8 +14,10 @@
 //
 // Solver.  u (nodal, Dirichlet values included) is improved by iterative
 // refinement: r = F - A u in high precision; the correction equation A d = r
-// is solved by CG preconditioned with one symmetric multigrid V(1,1) cycle
-// (red-black Gauss-Seidel, full-weighting restriction = transpose of bilinear
+// is solved by CG preconditioned with one symmetric multigrid cycle, V(2,2)
+// in FP32 and V(1,1) in FP64 (mg_nu<T>() red-black Gauss-Seidel sweeps before
+// and black-red sweeps after each coarse correction, full-weighting
+// restriction = transpose of bilinear
 // prolongation, coarse conductances by series/parallel edge averaging, exact
 // tridiagonal solve on the 2-cell grid), in FP32 (precision 32) or FP64
 // (precision 64); u += d.  High precision is FP64 on the FP64 path and
@@ -970,8 +972,10 @@ struct Solver {
                                                                     sc.act_in);
             return;
         }
-        smooth(L, 0);
-        smooth(L, 1);
+        for (int k = 0; k < mg_nu<T>(); ++k) {
+            smooth(L, 0);
+            smooth(L, 1);
+        }
         {
             SceProf pr(KP_RESTRICT, st, vb(L, 4.0) + vb(L + 1, 2.0));
             restrict_kernel<T><<<grid(L + 1), ln[L + 1].tpb, 0, st>>>(
@@ -983,8 +987,10 @@ struct Solver {
             prolong_kernel<T><<<grid(L), ln[L].tpb, 0, st>>>(z[L + 1], n[L + 1], z[L], ln[L].vpt,
                                                              sc.act_in);
         }
-        smooth(L, 1);
-        smooth(L, 0);
+        for (int k = 0; k < mg_nu<T>(); ++k) {
+            smooth(L, 1);
+            smooth(L, 0);
+        }
     }
 
     // ---- fused cycle: tiled down/up kernels above the tail, one block per
@@ -1009,8 +1015,8 @@ struct Solver {
         for (int L = 0; L < Lt; ++L) {
             const int nc1 = n[L] / 2 + 1;
             sh[L] = tile_height_for((int)sizeof(T), n[L]);
-            const int ch = (sh[L] - 6) / 2;
-            tiles_x[L] = (nc1 + MG_CW - 1) / MG_CW;
+            const int ch = MGGeom<T>::ch(sh[L]), cw = MGGeom<T>::CW;
+            tiles_x[L] = (nc1 + cw - 1) / cw;
             tiles_n[L] = tiles_x[L] * ((nc1 + ch - 1) / ch);
         }
     }
@@ -1426,7 +1432,15 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     const double in_rel2 = in_rel * in_rel;
     const int maxit = p->maxit > 0 ? p->maxit : 1000;
     const int inner_max = sizeof(T) == 4 ? 40 : maxit;
-    const int check_every = 4;
+    // iterations between host reads of the active-sample count (the per-sample
+    // flags stop converged samples in between, but their blocks still launch):
+    // SCE_CHECK_EVERY, default 2 (V(2,2) inner solves take ~5 iterations, so
+    // checking every 4 launched ~8)
+    const int check_every = [] {
+        const char *e = getenv("SCE_CHECK_EVERY");
+        const int v = e ? atoi(e) : 2;
+        return (v >= 1 && v <= 8) ? v : 2;
+    }();
 
     // initial residual (of the lifting, in closed form)
     {
@@ -1473,6 +1487,10 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         SCE_CUDA(cudaGetLastError());
     }
     int n_act = 0;
+    // launch profiler (when on): the CG loop's kernels are charged for all
+    // samples at launch; the passes that ran are counted at the end
+    const SceProfMark prof_mark = sce_prof_on() ? sce_prof_mark() : SceProfMark{};
+    long long n_head = 0, n_vc = 0;   // CG-pass launches, V-cycle invocations
     SCE_TRY(S.read_counter(&n_act));
     int total_inner = 0;
 
@@ -1482,6 +1500,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     const int rz_nblk = S.fused ? S.rz_blocks() : l0.nblk;
     const int fold = cg_fold_mode();
     auto iter_head = [&]() -> int {
+        ++n_head;
         T *pin = S.par ? S.p : S.p2, *pout = S.par ? S.p2 : S.p;
         {
             // reads cx, cy, z, p_in, d; writes p_out, d, q
@@ -1516,6 +1535,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     // ... and z = M^-1 r with its r.z partials, then beta (FOLD_BOTH: formed by
     // the next CG pass; the p update is part of it)
     auto iter_tail = [&]() -> int {
+        ++n_vc;
         if (S.fused) {
             S.vcycle_fused(true);
         } else {
@@ -1534,7 +1554,9 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     // (SCE_GRAPHS=1: not on the legacy default stream, during a capture or
     // with the launch profiler on).  A failed capture falls back to stream
     // launches.
-    bool use_graph = cached;
+    // (an even number of iterations per graph: each toggles the p array, and
+    // every replay must start from the parity it was captured with)
+    bool use_graph = cached && check_every % 2 == 0;
     auto capture_graph = [&]() -> int {
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
@@ -1576,6 +1598,7 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         else
             SCE_CUDA(cudaMemsetAsync(S.sc.rz + count, 0, (size_t)count * sizeof(double), st));
         S.par = 0;
+        ++n_vc;
         if (S.fused) {
             S.vcycle_fused(true);
         } else {
@@ -1674,6 +1697,21 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
     if (max_iters_out) {
         max_iters_out[0] = hm[1];
         max_iters_out[1] = hm[2];
+    }
+    if (sce_prof_on() && count > 0) {
+        // an active sample runs one CG pass, one r update and one V-cycle per
+        // iteration (the V-cycle at an inner solve's start stands in for the
+        // one its last iteration skips), so the passes that ran are the
+        // samples' total iteration count hm[2]
+        static const int cg_ids[] = {KP_SPMV, KP_AXPY};
+        static const int vc_ids[] = {KP_MG_DOWN, KP_MG_UP, KP_MG_V64, KP_MG_TAIL, KP_SMOOTH,
+                                     KP_RESTRICT, KP_PROLONG, KP_COARSEST, KP_DOT};
+        if (n_head > 0)
+            sce_prof_scale(prof_mark, st, cg_ids, 2,
+                           std::min(1.0, (double)hm[2] / ((double)n_head * count)));
+        if (n_vc > 0)
+            sce_prof_scale(prof_mark, st, vc_ids, 9,
+                           std::min(1.0, (double)hm[2] / ((double)n_vc * count)));
     }
     lease.ok = true;
     return hm[0] > 0 ? CE_ERR_NOT_CONVERGED : CE_OK;

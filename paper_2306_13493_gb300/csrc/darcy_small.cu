@@ -2,7 +2,7 @@
 //
 // The same discrete problem and the same algorithm as the batched solver in
 // darcy.cu (float-float iterative refinement around FP32 CG preconditioned
-// with one symmetric multigrid V(1,1) cycle), but the whole solve of one sample --
+// with one symmetric multigrid cycle, here V(1,1)), but the whole solve of one sample --
 // conductances, hierarchy, every CG iteration and V-cycle, the QoIs -- runs in
 // one thread block with all state in shared memory: the coefficient field is
 // read from HBM once and three doubles per sample are written back.  Many
@@ -111,9 +111,11 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
         return bsum1<NT>((double)acc, sh, pard);
     };
 
-    // one symmetric V(1,1) cycle: z[0] = M^-1 r
+    // one symmetric V(1,1) cycle: z[0] = M^-1 r (one sweep per side: every
+    // half-sweep of this solver is a block barrier, and V(2,2) measured slower
+    // here than the iterations it saves)
     static_assert(NL == mg_levels(N), "level count");
-    auto vcycle = [&]() { block_vcycle<float, N, NT, MG>(mg); };
+    auto vcycle = [&]() { block_vcycle<float, N, NT, MG, 0, 1>(mg); };
 
     // residual of the lifting in closed form: r0 = F + [i = 1] cx(0, j)
     double orr;

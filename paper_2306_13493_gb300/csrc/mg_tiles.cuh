@@ -17,23 +17,24 @@
 // indices.  Elements outside the grid hold zero data; at Dirichlet columns and
 // outside the grid 1/diag is 0, so their z stays 0.
 //
-//   mg_down: pre-smoothing from a zero guess (red then black Gauss-Seidel),
-//            fine residual, full-weighting restriction -> zpre (fine), b (coarse).
+//   mg_down: pre-smoothing from a zero guess (mg_nu<T>() sweeps of red then black
+//            Gauss-Seidel), fine residual, full-weighting restriction -> zpre
+//            (fine), b (coarse).
 //            After the black half-sweep the residual vanishes at the black
 //            vertices (each was just solved for with its red neighbours
 //            fixed), so it is formed at the red vertices only and the
 //            restriction sums the coarse vertex and its four diagonal
 //            neighbours (the red ones of its 3 x 3 stencil).
 //   mg_up  : z = zpre + bilinear prolongation of the coarse correction, then
-//            post-smoothing (black then red) -> z (fine); optionally the
+//            post-smoothing (mg_nu<T>() sweeps of black then red) -> z (fine); optionally the
 //            partial sums of r . z (level 0, for CG's beta).  zpre and z are
 //            distinct arrays: a tile reads zpre in its halo, which other
 //            tiles of the same launch own and write to z.
 //   mg_tail: the whole V-cycle of the coarse levels n <= NT_N of one sample in
 //            one thread block (shared memory)
-// Together with the exact coarsest solve this is the same symmetric V(1,1)
-// cycle as the level-by-level kernels (up to rounding: 1/diag is applied as a
-// reciprocal multiply).
+// Together with the exact coarsest solve this is the same symmetric
+// V(nu, nu) cycle as the level-by-level kernels (up to rounding: 1/diag
+// is applied as a reciprocal multiply).
 #pragma once
 
 #include "block_mg.cuh"
@@ -50,12 +51,24 @@ constexpr int MG_SH = SCE_MG_SH;           // window height: MG_SH / 4 warps x 4
 #define SCE_TILE_WARPS_PER_SM 40
 #endif
 constexpr int MG_NW = MG_SH / 4;           // warps per block
-constexpr int MG_CW = (MG_SW - 6) / 2;     // 29 coarse vertices per tile in x
-constexpr int MG_CH = (MG_SH - 6) / 2;     // 13 coarse vertices per tile in y
+// Halo of the windows.  In a window, every half-sweep after the first makes
+// one more ring at its edges invalid (the values beyond the window are not
+// there), and so do the residual and the restriction's diagonal neighbours:
+// with NU sweeps per side, mg_down's window starts 2 NU + 2 fine vertices below
+// and left of its owned region, mg_up's 2 NU; the owned region is 2 CW x 2 CH
+// fine vertices with CW = 32 - 2 NU - 1 (29 for V(1,1), 27 for V(2,2)) and
+// CH = SH / 2 - 2 NU - 1 for a window of SH rows.
+template <typename T>
+struct MGGeom {
+    static constexpr int NU = mg_nu<T>();
+    static constexpr int OD = 2 * NU + 2;            // mg_down window origin: 2 I0 - OD
+    static constexpr int OU = 2 * NU;                // mg_up window origin: 2 I0 - OU
+    static constexpr int CW = MG_SW / 2 - 2 * NU - 1;
+    static constexpr int ch(int sh) { return sh / 2 - 2 * NU - 1; }
+};
 constexpr int MG_THREADS = 32 * MG_NW;
 static_assert(MG_SH % 4 == 0 && MG_NW <= 32, "tile height");
-constexpr int MG_CCW = MG_CW + 3;          // coarse window of mg_up: 32 x 16 (+1 row)
-constexpr int MG_CCH = MG_CH + 3;
+constexpr int MG_CCW = MG_SW / 2 + 1;      // coarse window of mg_up: 33 columns
 constexpr unsigned MG_FULL = 0xffffffffu;
 
 // Window shape of the tiled kernels by window height SH (the width is always
@@ -67,8 +80,8 @@ constexpr unsigned MG_FULL = 0xffffffffu;
 template <int SH>
 struct MGTile {
     static_assert(SH % 4 == 0 && SH >= 16 && SH <= 64, "tile height");
-    static constexpr int H = SH, NW = SH / 4, CH = (SH - 6) / 2, THREADS = 32 * NW;
-    static constexpr int CCH = CH + 3;
+    static constexpr int H = SH, NW = SH / 4, THREADS = 32 * NW;
+    static constexpr int CCH = SH / 2;   // coarse rows of mg_up's window (+ a zero row)
     static constexpr int BPS = SCE_TILE_WARPS_PER_SM / NW;
 };
 
@@ -255,7 +268,8 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ zpre, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
     using G = MGTile<SH>;
-    constexpr int MG_SH = SH, MG_NW = G::NW, MG_CH = G::CH;
+    using GM = MGGeom<T>;
+    constexpr int MG_SH = SH, MG_NW = G::NW, MG_CH = GM::ch(SH), MG_CW = GM::CW, MG_OD = GM::OD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xz = reinterpret_cast<T *>(smem_raw);
     T *xrow = xz + 2 * 2 * MG_NW * MG_SW;
@@ -266,9 +280,9 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     const long long V = (long long)w * w, Vc = (long long)wc * wc;
     const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
     const int I0 = tx * MG_CW, J0 = ty * MG_CH;
-    const int gi0 = 2 * I0 - 4 + 2 * lane, gj0 = 2 * J0 - 4 + 4 * warp;
-    const bool inside = 2 * I0 - 4 >= 0 && 2 * I0 - 4 + MG_SW - 1 <= n && 2 * J0 - 4 >= 0 &&
-                        2 * J0 - 4 + MG_SH - 1 <= n;
+    const int gi0 = 2 * I0 - MG_OD + 2 * lane, gj0 = 2 * J0 - MG_OD + 4 * warp;
+    const bool inside = 2 * I0 - MG_OD >= 0 && 2 * I0 - MG_OD + MG_SW - 1 <= n &&
+                        2 * J0 - MG_OD >= 0 && 2 * J0 - MG_OD + MG_SH - 1 <= n;
     TileBlock<T> t;
     const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n, inside);
     tile_diag<T, MG_NW>(t, xrow, lane, warp, unk);
@@ -284,6 +298,12 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     tile_exchange<T, MG_NW>(t, xz, 0, lane, warp);
     tile_half_sweep<T, 1>(t);
     tile_exchange<T, MG_NW>(t, xz, 1, lane, warp);
+    if constexpr (GM::NU == 2) {   // the second sweep: red, black
+        tile_half_sweep<T, 0>(t);
+        tile_exchange<T, MG_NW>(t, xz, 0, lane, warp);
+        tile_half_sweep<T, 1>(t);
+        tile_exchange<T, MG_NW>(t, xz, 1, lane, warp);
+    }
     // red residuals of rows 0..3 (c = r % 2)
     const T r0 = tile_red_residual<T, 0>(t, unk), r1 = tile_red_residual<T, 1>(t, unk);
     const T r2 = tile_red_residual<T, 2>(t, unk), r3 = tile_red_residual<T, 3>(t, unk);
@@ -295,7 +315,7 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     const T lm = __shfl_up_sync(MG_FULL, rm, 1);
     // coarse vertices at (c = 0, r = 0) and (c = 0, r = 2): centre + 1/4 x the
     // four diagonal (red) neighbours, in the order SW, SE, NW, NE
-    const int I = I0 - 2 + lane, Jb = J0 - 2 + 2 * warp;
+    const int I = I0 - MG_OD / 2 + lane, Jb = J0 - MG_OD / 2 + 2 * warp;
     const T acc[2] = {T(0.25) * (lm + rm + l1 + r1) + r0, T(0.25) * (l1 + r1 + l3 + r3) + r2};
     T *bcs = bc + s * Vc;
 #pragma unroll
@@ -304,7 +324,7 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
         if (I - I0 >= 0 && I - I0 < MG_CW && J - J0 >= 0 && J - J0 < MG_CH && I <= nc && J <= nc)
             bcs[(long long)J * wc + I] = (I > 0 && I < nc) ? acc[k] : T(0);
     }
-    // owned fine vertices: window [4, 4 + 2 CW) x [4, 4 + 2 CH)
+    // owned fine vertices: window [OD, OD + 2 CW) x [OD, OD + 2 CH)
     T *zs = zpre + s * V;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -312,7 +332,8 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
         for (int c = 0; c < 2; ++c) {
             const int li = 2 * lane + c, lj = 4 * warp + r;
             const int gi = gi0 + c, gj = gj0 + r;
-            if (li >= 4 && li < 4 + 2 * MG_CW && lj >= 4 && lj < 4 + 2 * MG_CH && gi <= n && gj <= n)
+            if (li >= MG_OD && li < MG_OD + 2 * MG_CW && lj >= MG_OD &&
+                lj < MG_OD + 2 * MG_CH && gi <= n && gj <= n)
                 zs[(long long)gj * w + gi] = t.z[2 * r + c];
         }
     }
@@ -324,7 +345,9 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     const T *__restrict__ zpre, T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x,
     const int *__restrict__ act, double *__restrict__ part_rz, int nblk) {
     using G = MGTile<SH>;
-    constexpr int MG_SH = SH, MG_NW = G::NW, MG_CH = G::CH, MG_CCH = G::CCH;
+    using GM = MGGeom<T>;
+    constexpr int MG_SH = SH, MG_NW = G::NW, MG_CH = GM::ch(SH), MG_CCH = G::CCH;
+    constexpr int MG_CW = GM::CW, MG_OU = GM::OU;
     constexpr int MG_THREADS = G::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T sred[32];
@@ -338,8 +361,8 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     const long long V = (long long)w * w, Vc = (long long)wc * wc;
     const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
     const int I0 = tx * MG_CW, J0 = ty * MG_CH;
-    const int gi0 = 2 * I0 - 2 + 2 * lane, gj0 = 2 * J0 - 2 + 4 * warp;
-    const int cox = I0 - 1, coy = J0 - 1;
+    const int gi0 = 2 * I0 - MG_OU + 2 * lane, gj0 = 2 * J0 - MG_OU + 4 * warp;
+    const int cox = I0 - MG_OU / 2, coy = J0 - MG_OU / 2;
     const T *zcs = zc + s * Vc;
     for (int q = threadIdx.x; q < (MG_CCH + 1) * MG_CCW + 1; q += MG_THREADS) {
         const int ci = q % MG_CCW, cj = q / MG_CCW;
@@ -347,8 +370,8 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
         szc[q] = (cj < MG_CCH && I >= 0 && I <= nc && J >= 0 && J <= nc)
                      ? zcs[(long long)J * wc + I] : T(0);
     }
-    const bool inside = 2 * I0 - 2 >= 0 && 2 * I0 - 2 + MG_SW - 1 <= n && 2 * J0 - 2 >= 0 &&
-                        2 * J0 - 2 + MG_SH - 1 <= n;
+    const bool inside = 2 * I0 - MG_OU >= 0 && 2 * I0 - MG_OU + MG_SW - 1 <= n &&
+                        2 * J0 - MG_OU >= 0 && 2 * J0 - MG_OU + MG_SH - 1 <= n;
     TileBlock<T> t;
     const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n, inside);
     const T *zps = zpre + s * V;
@@ -391,7 +414,13 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     tile_half_sweep<T, 1>(t);
     tile_exchange<T, MG_NW>(t, xz, 1, lane, warp);
     tile_half_sweep<T, 0>(t);
-    // owned fine vertices: window [2, 2 + 2 CW) x [2, 2 + 2 CH)
+    if constexpr (GM::NU == 2) {   // the second sweep: black, red
+        tile_exchange<T, MG_NW>(t, xz, 0, lane, warp);
+        tile_half_sweep<T, 1>(t);
+        tile_exchange<T, MG_NW>(t, xz, 1, lane, warp);
+        tile_half_sweep<T, 0>(t);
+    }
+    // owned fine vertices: window [OU, OU + 2 CW) x [OU, OU + 2 CH)
     T *zs = z + s * V;
     T rz = T(0);
 #pragma unroll
@@ -400,7 +429,8 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
         for (int c = 0; c < 2; ++c) {
             const int li = 2 * lane + c, lj = 4 * warp + r;
             const int gi = gi0 + c, gj = gj0 + r;
-            if (li >= 2 && li < 2 + 2 * MG_CW && lj >= 2 && lj < 2 + 2 * MG_CH && gi <= n && gj <= n) {
+            if (li >= MG_OU && li < MG_OU + 2 * MG_CW && lj >= MG_OU &&
+                lj < MG_OU + 2 * MG_CH && gi <= n && gj <= n) {
                 zs[(long long)gj * w + gi] = t.z[2 * r + c];
                 rz += t.b[2 * r + c] * t.z[2 * r + c];
             }

@@ -1,5 +1,5 @@
-// One multigrid V(1,1) cycle of a whole n = 64 grid and of the levels below
-// it, one sample per thread block.
+// One multigrid V(MG_NU, MG_NU) cycle of a whole n = 64 grid and of the
+// levels below it, one sample per thread block.
 //
 // The 65 x 65 fine grid has 63 unknown columns (1..63) between its two
 // Dirichlet columns, so its columns 0..63 fit one 64-wide register window
@@ -11,15 +11,15 @@
 // and 1/diag = 0, as in the tiles.
 //
 //   load b, cx, cy of the level and the conductances of levels 32..2
-//   pre-smoothing from z = 0 (red, then black), red residuals, full-weighting
+//   pre-smoothing from z = 0 (MG_NU sweeps: red, then black), red residuals, full-weighting
 //   restriction into the b of level 32 in shared memory
 //   V-cycle of levels 32..2 in shared memory (block_vcycle)
-//   bilinear prolongation of the level-32 correction, post-smoothing (black,
-//   then red), z of the level to global memory, optionally the block's
+//   bilinear prolongation of the level-32 correction, post-smoothing (MG_NU
+//   sweeps: black, then red), z of the level to global memory, optionally the block's
 //   partial sum of b . z (CG's beta when the level is the finest)
 //
 // The arithmetic per vertex is that of mg_down / mg_tail / mg_up, so this is
-// the same symmetric V(1,1) cycle; it replaces their three launches on this
+// the same symmetric V(MG_NU, MG_NU) cycle; it replaces their three launches on this
 // level by one and the 2.8-fold window overlap of 64 x 32 tiles on a 65 x 65
 // grid by none.
 #pragma once
@@ -103,6 +103,12 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     tile_exchange<T, V64_NW>(t, xz, 0, lane, warp);
     tile_half_sweep<T, 1, 0, true>(t);
     tile_exchange<T, V64_NW>(t, xz, 1, lane, warp);
+    if constexpr (mg_nu<T>() == 2) {   // the second sweep: red, black
+        tile_half_sweep<T, 0, 0, true>(t);
+        tile_exchange<T, V64_NW>(t, xz, 0, lane, warp);
+        tile_half_sweep<T, 1, 0, true>(t);
+        tile_exchange<T, V64_NW>(t, xz, 1, lane, warp);
+    }
 
     // red residuals (the black ones vanish) and full weighting: coarse vertex
     // (lane, 2 warp + k) sits at (c = 0, r = 2 k); its diagonal neighbours are
@@ -148,11 +154,14 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
         t.z[k] += pv;
     }
 
-    // post-smoothing: black, then red
-    tile_exchange<T, V64_NW>(t, xz, 0, lane, warp);
-    tile_half_sweep<T, 1, 0, true>(t);
-    tile_exchange<T, V64_NW>(t, xz, 1, lane, warp);
-    tile_half_sweep<T, 0, 0, true>(t);
+    // post-smoothing: black, then red (MG_NU times)
+#pragma unroll
+    for (int k = 0; k < mg_nu<T>(); ++k) {
+        tile_exchange<T, V64_NW>(t, xz, 0, lane, warp);
+        tile_half_sweep<T, 1, 0, true>(t);
+        tile_exchange<T, V64_NW>(t, xz, 1, lane, warp);
+        tile_half_sweep<T, 0, 0, true>(t);
+    }
 
     // z of the level (column 64, the Dirichlet column, is 0) and b . z
     T *zs = z + (long long)s * V;

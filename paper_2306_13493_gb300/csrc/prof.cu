@@ -13,9 +13,11 @@ struct Rec {
     int id;
     cudaEvent_t a, b;
     double bytes;
+    cudaStream_t st;
 };
 std::mutex g_mu;
 bool g_on = false;
+long long g_gen = 0;   // bumped whenever the records are folded into the totals
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_free;
 double g_ms[KP_COUNT_], g_bytes[KP_COUNT_];
@@ -45,6 +47,7 @@ void resolve_locked() {
         if (r.b) g_free.push_back(r.b);
     }
     g_recs.clear();
+    ++g_gen;
 }
 
 const char *kNames[KP_COUNT_] = {
@@ -62,7 +65,7 @@ SceProf::SceProf(int kernel, cudaStream_t s, double bytes) {
     std::lock_guard<std::mutex> lk(g_mu);
     id = kernel;
     st = s;
-    Rec r{kernel, get_event(), nullptr, bytes};
+    Rec r{kernel, get_event(), nullptr, bytes, s};
     cudaEventRecord(r.a, s);
     g_recs.push_back(r);
     slot = (int)g_recs.size() - 1;
@@ -74,6 +77,26 @@ SceProf::~SceProf() {
     if (slot < (int)g_recs.size() && g_recs[slot].id == id && g_recs[slot].b == nullptr) {
         g_recs[slot].b = get_event();
         cudaEventRecord(g_recs[slot].b, st);
+    }
+}
+
+SceProfMark sce_prof_mark() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return SceProfMark{g_gen, (long long)g_recs.size()};
+}
+
+void sce_prof_scale(const SceProfMark &m, cudaStream_t st, const int *ids, int nids, double f) {
+    if (!g_on || !(f >= 0.0)) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (m.gen != g_gen) return;   // the records were folded in since the mark
+    for (size_t i = (size_t)m.idx; i < g_recs.size(); ++i) {
+        Rec &r = g_recs[i];
+        if (r.st != st) continue;
+        for (int k = 0; k < nids; ++k)
+            if (r.id == ids[k]) {
+                r.bytes *= f;
+                break;
+            }
     }
 }
 

@@ -102,6 +102,19 @@ struct SceProf {
     ~SceProf();
 };
 
+// A position in the launch records, and the correction of the bytes that the
+// launches after it on stream st, of the families ids[0..nids), attributed to
+// themselves: multiplied by f.  A kernel whose launch covers every sample but
+// skips the converged ones (per-sample flags on the device) is charged the
+// bytes of all samples when it is launched; the solver, which knows at its end
+// how many sample-passes actually ran, scales them to those.  No effect while
+// the profiler is off, or once the records were read since the mark.
+struct SceProfMark {
+    long long gen = -1, idx = 0;
+};
+SceProfMark sce_prof_mark();
+void sce_prof_scale(const SceProfMark &m, cudaStream_t st, const int *ids, int nids, double f);
+
 // Field path entry used by mlmc_level_estimate (same as ce_sample_batch).
 // Lattice normals of the quasi-Monte Carlo sampler (ce_qmc_setup): for point i
 // and grid index j, y = frac((i zr[j] mod N)/N + Delta_j), xi = Phi^-1(y), with
