@@ -746,7 +746,9 @@ def precision_study(args):
     return 0
 
 
-# bound of each kernel family that HBM bandwidth does not bound: the coarse
+# bound of each kernel family that HBM bandwidth does not bound (the V(2,2)
+# multigrid tiles: 65 % issue active and 34 % of DRAM bandwidth in their n = 512
+# capture, the second sweep having doubled their instructions per byte); the coarse
 # multigrid tail reads its levels from L2 (judged against the measured L2 read
 # bandwidth); the row pass (Philox, Box-Muller, butterflies), the one-block
 # solver (whole solve in shared memory) and the fused n = 64 V-cycle (one
@@ -756,7 +758,21 @@ def precision_study(args):
 # 64 cells (one block per sample, a few microseconds) by launch latency.  The
 # rest are HBM-bound.
 KERNEL_BOUND = {"mg_tail": "l2", "ce_row": "issue", "darcy_small": "issue", "mg_v64": "issue",
+                "mg_up": "issue", "mg_down": "issue",
                 "reduce": "latency", "level_sums": "latency", "coarsen_tail": "latency"}
+
+# Warp instructions per algorithmic byte of issue-bound families, from one ncu
+# capture of the kernel (smsp__inst_executed.sum / the launch's algorithmic
+# bytes), with the file, kernel and sha256 of the captured source text: the
+# bench's issue fraction = its algorithmic bytes x this ratio / time / the
+# measured FMA issue rate, reported only while the source is the captured one.
+INSTR_PER_ALG = {
+    # n = 512 x 32 launches with 48-row windows, V(2,2) (profiles/mg_up_n512x32.md)
+    "mg_up": (45090048 / 176882432, "paper_2306_13493_gb300/csrc/mg_tiles.cuh", "mg_up_kernel",
+              "3e1d5f0881eaad1e1963cf2dfe9c59df44e8e21f59a62938ebfc471610ecf5cd"),
+    "mg_down": (39403648 / 143196800, "paper_2306_13493_gb300/csrc/mg_tiles.cuh",
+                "mg_down_kernel", "be286ab6497d33794a845c565701359b7c621d2da6dbb8c43440a60c79ddf222"),
+}
 
 
 def measure_peaks(sce, stream, reps=10):
@@ -1408,6 +1424,10 @@ def run_ours(args):
             frac = round(gbs / hbm, 4)
         elif gbs is not None and bound == "l2":
             frac = round(gbs / mpk["l2_read_gbs"], 4)
+        elif gbs is not None and bound == "issue" and name in INSTR_PER_ALG:
+            ipb, src, kname, digest = INSTR_PER_ALG[name]
+            if kernel_source_digest(src, kname) == digest:
+                frac = round(by * ipb / (ms * 1e-3) / mpk["fma_warp_inst_per_s"], 4)
         kernels[name] = {"ms": round(ms, 3), "launches": nl, "share": round(ms / prof_total, 4),
                          "GBps": round(gbs, 1) if gbs is not None else None, "bound": bound,
                          "frac": frac}

@@ -455,7 +455,7 @@ int mlmc_level_estimate_qmc(ce_qmc_t q, const darcy_problem *p, uint64_t seed, u
 int darcy_solver_cache_clear(void *stream);
 
 /*
- * darcy_autotune_tiles -- picks the window height (16, 24, 32 or 48 rows; the
+ * darcy_autotune_tiles -- picks the window height (16, 24, 32, 48 or 64 rows; the
  * width is 64 columns) of the tiled multigrid kernels for grids of n cells
  * (n >= 128, a power of two) in `precision` by timing `reps` solves of
  * `count` samples of a smooth synthetic coefficient for every height (CUDA

@@ -61,7 +61,7 @@ constexpr int TAIL_N = SCE_TAIL_N;   // levels with n <= TAIL_N run in one block
 // for every level).  Every height computes each vertex of a V-cycle
 // identically; the per-tile r . z partial sums follow the tiling, so the
 // solves take different rounding paths to the same stopping tolerance.
-constexpr int kTileHeights[] = {16, 24, 32, 48};
+constexpr int kTileHeights[] = {16, 24, 32, 48, 64};
 std::mutex g_tile_mu;
 std::map<std::pair<int, int>, int> g_tile_sh;   // (sizeof T, n) -> window height
 
@@ -1180,6 +1180,7 @@ struct Solver {
                 case 16: tile_down<16>(L); break;
                 case 24: tile_down<24>(L); break;
                 case 48: tile_down<48>(L); break;
+                case 64: tile_down<64>(L); break;
                 default: tile_down<32>(L); break;
             }
         }
@@ -1197,6 +1198,7 @@ struct Solver {
                 case 16: tile_up<16>(L, want_rz); break;
                 case 24: tile_up<24>(L, want_rz); break;
                 case 48: tile_up<48>(L, want_rz); break;
+                case 64: tile_up<64>(L, want_rz); break;
                 default: tile_up<32>(L, want_rz); break;
             }
         }

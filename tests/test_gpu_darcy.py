@@ -293,7 +293,7 @@ def test_tile_autotuner_picks_a_height(sce, monkeypatch):
     k = _oracle_k(n, count, lam=0.05, seed=5, precision=32)
     before = _solve(sce, k, 32, f=1.0)
     h = sce.darcy_autotune_tiles(n, 32, count=64, reps=1)
-    assert h in (16, 24, 32, 48)
+    assert h in (16, 24, 32, 48, 64)
     after = _solve(sce, k, 32, f=1.0)
     # another window height: the same solve up to the stopping tolerance (rtol 1e-12)
     assert np.max(np.abs(before[1] - after[1])) < 10 * 1e-12 * max(1.0, np.max(np.abs(before[1])))

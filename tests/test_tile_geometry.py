@@ -61,7 +61,7 @@ def writes(n, sh, nu):
 
 
 @pytest.mark.parametrize("nu", [1, 2])
-@pytest.mark.parametrize("sh", [16, 24, 32, 48])
+@pytest.mark.parametrize("sh", [16, 24, 32, 48, 64])
 @pytest.mark.parametrize("n", [128, 256])
 def test_every_vertex_written_once(nu, sh, n):
     fine_down, fine_up, coarse = writes(n, sh, nu)
@@ -71,7 +71,7 @@ def test_every_vertex_written_once(nu, sh, n):
 
 
 @pytest.mark.parametrize("nu", [1, 2])
-@pytest.mark.parametrize("sh", [16, 24, 32, 48])
+@pytest.mark.parametrize("sh", [16, 24, 32, 48, 64])
 def test_coarse_window_reads_stay_in_the_buffer(nu, sh):
     """mg_up loads SH/2 coarse rows of CCW entries plus a zero row; lane x of
     warp w reads rows 2w .. 2w + 2, columns x and x + 1."""
@@ -88,7 +88,7 @@ def test_coarse_window_reads_stay_in_the_buffer(nu, sh):
 
 
 @pytest.mark.parametrize("nu", [1, 2])
-@pytest.mark.parametrize("sh", [16, 24, 32, 48])
+@pytest.mark.parametrize("sh", [16, 24, 32, 48, 64])
 def test_owned_region_inside_the_valid_part_of_the_window(nu, sh):
     """Ring bookkeeping of a window with last index E (63 across, SH - 1 up).
     mg_down: the first red update from z = 0 is exact except at index 0 (no
