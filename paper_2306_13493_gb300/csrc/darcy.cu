@@ -263,19 +263,7 @@ __global__ void restrict_kernel(const T *__restrict__ cxf, const T *__restrict__
     const int wc = nc + 1;
     FOR_VERT(Vc, vpt) {
         const int J = v / wc, I = v - J * wc;
-        T acc = T(0);
-        if (I > 0 && I < nc) {
-            for (int dj = -1; dj <= 1; ++dj) {
-                const int j = 2 * J + dj;
-                if (j < 0 || j > nf) continue;
-                const T wy = dj == 0 ? T(1) : T(0.5);
-                for (int di = -1; di <= 1; ++di) {
-                    const T wx = di == 0 ? T(1) : T(0.5);
-                    acc += wx * wy * resid_at(ax, ay, bs, zs, 2 * I + di, j, nf);
-                }
-            }
-        }
-        bc[s * Vc + v] = acc;
+        bc[s * Vc + v] = (I > 0 && I < nc) ? restrict_at(ax, ay, bs, zs, nf, I, J) : T(0);
         zc[s * Vc + v] = T(0);
     }
 }

@@ -268,6 +268,12 @@ static int small16_threads() {
     return e && atoi(e) == 32 ? 32 : 64;
 }
 
+// Threads per block of the n = 32 solver (SCE_SMALL32_NT: 128 or 256).
+static int small32_threads() {
+    const char *e = getenv("SCE_SMALL32_NT");
+    return e && atoi(e) == 128 ? 128 : 256;
+}
+
 // Largest n solved one block per sample (SCE_SMALL_MAX_N overrides; 0 = never).
 int sce_small_max_n() {
     const char *e = getenv("SCE_SMALL_MAX_N");
@@ -290,7 +296,10 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
             if (small16_threads() == 32) SCE_SMALL(16, 32);
             else SCE_SMALL(16, 64);
             break;
-        case 32: SCE_SMALL(32, 256); break;
+        case 32:
+            if (small32_threads() == 128) SCE_SMALL(32, 128);
+            else SCE_SMALL(32, 256);
+            break;
         case 64: SCE_SMALL(64, 512); break;
         default: break;
     }

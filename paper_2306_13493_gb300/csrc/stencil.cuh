@@ -182,21 +182,22 @@ __device__ __forceinline__ void smooth_at(const T *ax, const T *ay, const T *b, 
 }
 
 // Full-weighting restriction (transpose of bilinear prolongation) of the
-// fine residual to coarse unknown (I, J), 1 <= I <= nc-1.
+// fine residual to coarse unknown (I, J), 1 <= I <= nc-1, right after a
+// black half-sweep: the residual then vanishes at the black vertices (each was
+// just solved for with its red neighbours fixed), so of the 3 x 3 stencil
+// only the red ones count -- the coarse vertex itself (weight 1) and its four
+// diagonal neighbours (weight 1/4), as in the tiled kernels.
 template <typename T>
 __device__ __forceinline__ T restrict_at(const T *ax, const T *ay, const T *b, const T *z, int nf,
                                          int I, int J) {
-    T acc = T(0);
-    for (int dj = -1; dj <= 1; ++dj) {
+    T acc = resid_at(ax, ay, b, z, 2 * I, 2 * J, nf);
+    T d = T(0);
+    for (int dj = -1; dj <= 1; dj += 2) {
         const int j = 2 * J + dj;
         if (j < 0 || j > nf) continue;
-        const T wy = dj == 0 ? T(1) : T(0.5);
-        for (int di = -1; di <= 1; ++di) {
-            const T wx = di == 0 ? T(1) : T(0.5);
-            acc += wx * wy * resid_at(ax, ay, b, z, 2 * I + di, j, nf);
-        }
+        d += resid_at(ax, ay, b, z, 2 * I - 1, j, nf) + resid_at(ax, ay, b, z, 2 * I + 1, j, nf);
     }
-    return acc;
+    return acc + T(0.25) * d;
 }
 
 // Bilinear prolongation of the coarse correction to fine vertex (i, j).
