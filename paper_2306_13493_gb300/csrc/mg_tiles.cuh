@@ -85,13 +85,18 @@ struct MGTile {
     static constexpr int BPS = SCE_TILE_WARPS_PER_SM / NW;
 };
 
+// shared-memory values per block for the 1/diag slices of NW warps (eight
+// per thread, see TileBlock)
+constexpr int tile_inv_slots(int nw) { return nw * 8 * 32; }
+
 // shared memory: z of rows 0 and 3 of every warp (2 buffers), one row per
-// warp for cy / residual exchange, the coarse window of mg_up with a spare row
+// warp for cy / residual exchange, the coarse window of mg_up with a spare row,
+// the threads' 1/diag slices
 template <typename T, int SH = MG_SH>
 constexpr size_t mg_tile_smem_bytes() {
     using G = MGTile<SH>;
     return sizeof(T) * (2 * 2 * G::NW * (size_t)MG_SW + G::NW * (size_t)MG_SW +
-                        (size_t)(G::CCH + 1) * MG_CCW + 1);
+                        (size_t)(G::CCH + 1) * MG_CCW + 1 + tile_inv_slots(G::NW));
 }
 
 template <typename T>
@@ -115,26 +120,23 @@ template <> __device__ __forceinline__ double recip<double>(double d) { return 1
 // (2 lane + c, 4 warp + r).  Conductances: cxe = cx at the element (edge to
 // the east), cyn = cy (edge to the north); cxw0[r] = west edge of the c = 0
 // column (from lane - 1), cys0[c] = south edge of row 0 (from warp - 1).
-// unk: bitmask of the elements that are unknowns.  1/diag is not stored: each
-// element uses it once per kernel (one half-sweep of its colour, or the first
-// red update from z = 0), so it is formed where it is used (tile_inv), which
-// keeps eight registers free.
+// inv: the lane's 1/diag values in shared memory (element e at inv[32 e]),
+// written once by tile_diag and read back by the half-sweeps: each element
+// uses its 1/diag once per sweep of its colour, and keeping the eight values in
+// registers spilled, so they live in a per-thread slice of shared memory
+// (element-major across the lanes, so the accesses are free of bank
+// conflicts; only the owning thread reads them, so no barrier is needed).
 template <typename T>
 struct TileBlock {
     T b[8], z[8], cxe[8], cyn[8], cxw0[4], cys0[2];
     T zs[2], zn[2];   // z of the rows below (r = -1) and above (r = 4) the strip
-    unsigned unk;
+    T *inv;
 };
 
-// 1/diag of element (c, r): 1 / (sum of its four edge conductances); 0 where
-// the element is not an unknown (Dirichlet column, outside the grid), so its
-// z stays 0.  c and r are compile-time constants after unrolling.
+// 1/diag of element (c, r); c and r are compile-time constants after unrolling
 template <typename T>
 __device__ __forceinline__ T tile_inv(const TileBlock<T> &t, int c, int r) {
-    const int e = 2 * r + c;
-    const T cw = c == 0 ? t.cxw0[r] : t.cxe[2 * r];
-    const T cs = r == 0 ? t.cys0[c] : t.cyn[2 * (r - 1) + c];
-    return ((t.unk >> e) & 1) ? recip(cw + t.cxe[e] + cs + t.cyn[e]) : T(0);
+    return t.inv[32 * (2 * r + c)];
 }
 
 // Loads b, cx, cy of the block (zero outside the grid); returns the bitmask
@@ -180,11 +182,13 @@ __device__ __forceinline__ unsigned tile_load(TileBlock<T> &t, const T *bs, cons
 }
 
 // West/south edge conductances from the neighbouring lane / warp (xrow: one
-// shared row per warp); records the unknowns' mask.  Contains a barrier.
-// NW: warps of the block.
+// shared row per warp), then 1/diag of the lane's elements (0 where not an
+// unknown: Dirichlet column, outside the grid, so their z stays 0) into its
+// slice of sinv (tile_inv_slots(NW) values).  Contains a barrier.  NW: warps
+// of the block.
 template <typename T, int NW = MG_NW>
 __device__ __forceinline__ void tile_diag(TileBlock<T> &t, T *xrow, int lane, int warp,
-                                          unsigned unk) {
+                                          unsigned unk, T *sinv) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) t.cxw0[r] = __shfl_up_sync(MG_FULL, t.cxe[2 * r + 1], 1);
     xrow[warp * MG_SW + 2 * lane] = t.cyn[6];
@@ -193,7 +197,17 @@ __device__ __forceinline__ void tile_diag(TileBlock<T> &t, T *xrow, int lane, in
 #pragma unroll
     for (int c = 0; c < 2; ++c)
         t.cys0[c] = warp > 0 ? xrow[(warp - 1) * MG_SW + 2 * lane + c] : T(0);
-    t.unk = unk;
+    t.inv = sinv + warp * 8 * 32 + lane;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int e = 2 * r + c;
+            const T cw = c == 0 ? t.cxw0[r] : t.cxe[2 * r];
+            const T cs = r == 0 ? t.cys0[c] : t.cyn[2 * (r - 1) + c];
+            t.inv[32 * e] = ((unk >> e) & 1) ? recip(cw + t.cxe[e] + cs + t.cyn[e]) : T(0);
+        }
+    }
 }
 
 // Publishes rows 0 and 3 of z in buffer buf, waits, and reads the rows below
@@ -273,6 +287,7 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xz = reinterpret_cast<T *>(smem_raw);
     T *xrow = xz + 2 * 2 * MG_NW * MG_SW;
+    T *sinv = xrow + MG_NW * MG_SW;
     const int s = blockIdx.y;
     if (!act[s]) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -285,7 +300,7 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
                         2 * J0 - MG_OD >= 0 && 2 * J0 - MG_OD + MG_SH - 1 <= n;
     TileBlock<T> t;
     const unsigned unk = tile_load(t, b + s * V, cx + s * V, cy + s * V, gi0, gj0, n, inside);
-    tile_diag<T, MG_NW>(t, xrow, lane, warp, unk);
+    tile_diag<T, MG_NW>(t, xrow, lane, warp, unk, sinv);
     // red from z = 0: z = b / diag at red elements ((c + r) even), 0 at black
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -354,6 +369,7 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     T *xz = reinterpret_cast<T *>(smem_raw);
     T *xrow = xz + 2 * 2 * MG_NW * MG_SW;
     T *szc = xrow + MG_NW * MG_SW;   // coarse window, row stride MG_CCW, MG_CCH + 1 rows
+    T *sinv = szc + (MG_CCH + 1) * MG_CCW + 1;
     const int s = blockIdx.y;
     if (!act[s]) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -392,7 +408,7 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
             }
         }
     }
-    tile_diag<T, MG_NW>(t, xrow, lane, warp, unk);   // its barrier also covers szc
+    tile_diag<T, MG_NW>(t, xrow, lane, warp, unk, sinv);   // its barrier also covers szc
     // z += P zc: coarse column lane (and lane + 1), rows 2 warp + {0, 1, 2};
     // weights (1, 0) at even fine indices, (1/2, 1/2) at odd ones
     const T *q0 = szc + (2 * warp) * MG_CCW + lane;

@@ -36,7 +36,7 @@ using V64Lay = MGPackedLayout<V64_N / 2>;       // levels 32..2 in shared memory
 template <typename T>
 constexpr size_t v64_smem_bytes() {
     return sizeof(T) * ((size_t)V64Lay::total() + 2 * 2 * V64_NW * (size_t)MG_SW +
-                        V64_NW * (size_t)MG_SW + 32);
+                        V64_NW * (size_t)MG_SW + 32 + tile_inv_slots(V64_NW));
 }
 
 // tp.cx[i], tp.cy[i]: conductances of level 32 >> i (i = 0..4), per sample
@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     T *xz = base + V64Lay::total();
     T *xrow = xz + 2 * 2 * V64_NW * MG_SW;
     T *sred = xrow + V64_NW * MG_SW;
+    T *sinv = sred + 32;   // the threads' 1/diag slices
     const int s = blockIdx.x;
     if (!act[s]) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
             if (in && gi >= 1) unk |= 1u << e;
         }
     }
-    tile_diag<T, V64_NW>(t, xrow, lane, warp, unk);
+    tile_diag<T, V64_NW>(t, xrow, lane, warp, unk, sinv);
 
     // pre-smoothing: red from z = 0, then black
 #pragma unroll
