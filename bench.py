@@ -37,18 +37,19 @@ UNIT = "level-samples/s"
 DTYPE_MIXED = "f32+ff(fp32x2)+f64 eig/QoI"
 L2_BYTES = 129 * 1024 * 1024
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of
-# the dominant kernel family, from a capture of its n = 256 launch (profiles/ summary of
-# the same name); scaled to the bench's launches by their algorithmic bytes, and reported
-# only while the kernel source is the one that was captured (sha256 below).
+# a kernel family, from one capture of its n = 512 x 32 launch (profiles/ summary named
+# below); scaled to the bench's launches by their algorithmic bytes for the roofline
+# family, and reported only while the kernel source is the one that was captured
+# (sha256 below).
 TRAFFIC_PER_ALG = {
     # fused CG pass, n = 512 x 32 samples (profiles/cg_pass_n512x32.md)
     "cg_spmv_dot": ((168.580608 + 63.755776) / 269.485056,
                     "paper_2306_13493_gb300/csrc/darcy.cu", "pspmv_kernel",
                     "9a76b841323f6d80ce7b0bc9ee4c5a1f56e55f9e4fc43749a2e76bd639234e5b"),
     # n = 512 launch of the tile kernel, 48-row windows (profiles/mg_up_n512x32.md)
-    "mg_up": ((143.225856 + 19.805184) / 176.882432,
+    "mg_up": ((143.224064 + 19.643136) / 176.882432,
               "paper_2306_13493_gb300/csrc/mg_tiles.cuh", "mg_up_kernel",
-              "3e1d5f0881eaad1e1963cf2dfe9c59df44e8e21f59a62938ebfc471610ecf5cd"),
+              "03378b11ee42316507e0de0419a19074477b337e3214572363991afb8f39df0b"),
 }
 
 
@@ -767,11 +768,12 @@ KERNEL_BOUND = {"mg_tail": "l2", "ce_row": "issue", "darcy_small": "issue", "mg_
 # bench's issue fraction = its algorithmic bytes x this ratio / time / the
 # measured FMA issue rate, reported only while the source is the captured one.
 INSTR_PER_ALG = {
-    # n = 512 x 32 launches with 48-row windows, V(2,2) (profiles/mg_up_n512x32.md)
-    "mg_up": (45090048 / 176882432, "paper_2306_13493_gb300/csrc/mg_tiles.cuh", "mg_up_kernel",
-              "3e1d5f0881eaad1e1963cf2dfe9c59df44e8e21f59a62938ebfc471610ecf5cd"),
-    "mg_down": (39403648 / 143196800, "paper_2306_13493_gb300/csrc/mg_tiles.cuh",
-                "mg_down_kernel", "be286ab6497d33794a845c565701359b7c621d2da6dbb8c43440a60c79ddf222"),
+    # n = 512 x 32 launches with 48-row windows, V(2,2) (profiles/mg_up_n512x32.md,
+    # profiles/mg_down_n512x32.md)
+    "mg_up": (40920192 / 176882432, "paper_2306_13493_gb300/csrc/mg_tiles.cuh", "mg_up_kernel",
+              "03378b11ee42316507e0de0419a19074477b337e3214572363991afb8f39df0b"),
+    "mg_down": (34649984 / 143196800, "paper_2306_13493_gb300/csrc/mg_tiles.cuh",
+                "mg_down_kernel", "7e4e5ffd8a16cddc3599ab83cf44c53c804d063fcc45229a39f72a7ec30967f1"),
 }
 
 
