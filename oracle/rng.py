@@ -23,8 +23,10 @@ definitions produces the same bits:
           argument-reduction + atanh series, e.g. Cody & Waite 1980, ch. 5);
     sin/cos(pi t): t reduced by multiples of 1/2 (exact), then truncated
           Taylor series in x = pi r, |x| <= pi/4, in nested (Horner) form.
-  Term counts: FP64 ln to s^10, sin to x^19, cos to x^18;
-               FP32 ln to s^5,  sin to x^11, cos to x^12.
+  Term counts: FP64 ln to s^10, sin to x^19, cos to x^18 (nested);
+               FP32 ln to s^4,  sin to x^9,  cos to x^10 (Horner, with the
+               coefficients rounded to float32 once; the next terms are
+               below 2e-9, far under float32 resolution).
 """
 import numpy as np
 
@@ -140,6 +142,12 @@ _F32 = np.float32
 _SQRT_HALF_32 = _F32(0.70710677)
 _LN2_32 = _F32(0.6931472)
 _PI_32 = _F32(3.1415927)
+# (-1)^k / (2k+1)!, k = 0..4, and (-1)^k / (2k)!, k = 0..5, as float32
+_SIN32 = [_F32(float.fromhex(h)) for h in
+          ("0x1p0", "-0x1.555556p-3", "0x1.111112p-7", "-0x1.a01a02p-13", "0x1.71de3ap-19")]
+_COS32 = [_F32(float.fromhex(h)) for h in
+          ("0x1p0", "-0x1p-1", "0x1.555556p-5", "-0x1.6c16c2p-10", "0x1.a01a02p-16",
+           "-0x1.27e4fcp-22")]
 
 
 def log32(x):
@@ -153,8 +161,8 @@ def log32(x):
     e = np.where(low, e - _F32(1.0), e).astype(_F32)
     f = (m - _F32(1.0)) / (m + _F32(1.0))
     s = f * f
-    p = _F32(1.0) / _F32(11.0)
-    for k in range(4, -1, -1):
+    p = _F32(1.0) / _F32(9.0)
+    for k in range(3, -1, -1):
         p = _F32(1.0) / _F32(2 * k + 1) + s * p
     t = f * p
     return (e * _LN2_32 + (t + t)).astype(_F32)
@@ -167,12 +175,14 @@ def sincospi32(t):
     r = r.astype(_F32)
     x = _PI_32 * r
     x2 = x * x
-    S = np.ones_like(x2)
-    for k in range(5, 0, -1):
-        S = _F32(1.0) - (x2 * S) * (_F32(1.0) / _F32((2 * k) * (2 * k + 1)))
-    C = np.ones_like(x2)
-    for k in range(6, 0, -1):
-        C = _F32(1.0) - (x2 * C) * (_F32(1.0) / _F32((2 * k - 1) * (2 * k)))
+    # Horner form, coefficients (-1)^k/(2k+1)! (sin, to x^9) and (-1)^k/(2k)!
+    # (cos, to x^10) rounded to float32 once
+    S = np.full_like(x2, _SIN32[-1])
+    for c in _SIN32[-2::-1]:
+        S = c + x2 * S
+    C = np.full_like(x2, _COS32[-1])
+    for c in _COS32[-2::-1]:
+        C = c + x2 * C
     S = x * S
     sin = np.choose(q, [S, C, -S, -C]).astype(_F32)
     cos = np.choose(q, [C, -S, -C, S]).astype(_F32)

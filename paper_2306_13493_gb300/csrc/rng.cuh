@@ -12,9 +12,10 @@
 // explicit round-to-nearest intrinsics (no contraction into FMA), so the bits
 // equal those of any other IEEE implementation of the same steps:
 //   ln x : x = m 2^e, m in [sqrt(1/2), sqrt(2)), f = (m-1)/(m+1), s = f^2,
-//          ln x = e ln2 + 2 f sum_k s^k/(2k+1)   (k <= 10 FP64, k <= 5 FP32)
+//          ln x = e ln2 + 2 f sum_k s^k/(2k+1)   (k <= 10 FP64, k <= 4 FP32)
 //   sincos(pi t): q = rint(2t), r = t - q/2 (exact), x = pi r, Taylor series
-//          of sin to x^19 / cos to x^18 (FP64), x^11 / x^12 (FP32), nested.
+//          of sin to x^19 / cos to x^18 (FP64, nested), x^9 / x^10 (FP32,
+//          Horner form with the coefficients rounded to float32 once).
 #pragma once
 
 #include <stdint.h>
@@ -134,11 +135,12 @@ __device__ __forceinline__ float ln_f32(float x) {
     }
     const float f = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
     const float s = __fmul_rn(f, f);
-    float p = 1.0f / 11.0f;
-    p = __fadd_rn(1.0f / 9.0f, __fmul_rn(s, p));
-    p = __fadd_rn(1.0f / 7.0f, __fmul_rn(s, p));
-    p = __fadd_rn(1.0f / 5.0f, __fmul_rn(s, p));
-    p = __fadd_rn(1.0f / 3.0f, __fmul_rn(s, p));
+    // atanh(f)/f = 1 + s/3 + s^2/5 + s^3/7 + s^4/9 (the s^5/11 term is below
+    // 2^-30 of the result for |f| <= 0.1716), float32 coefficients
+    float p = 0x1.c71c72p-4f;                          // 1/9
+    p = __fadd_rn(0x1.24924ap-3f, __fmul_rn(s, p));    // 1/7
+    p = __fadd_rn(0x1.99999ap-3f, __fmul_rn(s, p));    // 1/5
+    p = __fadd_rn(0x1.555556p-2f, __fmul_rn(s, p));    // 1/3
     p = __fadd_rn(1.0f, __fmul_rn(s, p));
     const float t = __fmul_rn(f, p);
     return __fadd_rn(__fmul_rn(e, 0.6931472f), __fadd_rn(t, t));
@@ -150,19 +152,20 @@ __device__ __forceinline__ void sincospi_f32(float t, float *sn, float *cs) {
     const int qi = ((int)q) & 3;
     const float x = __fmul_rn(3.1415927f, r);
     const float x2 = __fmul_rn(x, x);
-    float S = 1.0f;
-    S = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, S), 1.0f / 110.0f));
-    S = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, S), 1.0f / 72.0f));
-    S = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, S), 1.0f / 42.0f));
-    S = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, S), 1.0f / 20.0f));
-    S = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, S), 1.0f / 6.0f));
-    float C = 1.0f;
-    C = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, C), 1.0f / 132.0f));
-    C = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, C), 1.0f / 90.0f));
-    C = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, C), 1.0f / 56.0f));
-    C = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, C), 1.0f / 30.0f));
-    C = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, C), 1.0f / 12.0f));
-    C = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(x2, C), 1.0f / 2.0f));
+    // Taylor polynomials for |x| <= pi/4 in Horner form with float32
+    // coefficients (-1)^k/(2k+1)! and (-1)^k/(2k)!: sin to x^9, cos to x^10
+    // (the next terms are below 2e-9)
+    float S = 0x1.71de3ap-19f;                          // 1/9!
+    S = __fadd_rn(-0x1.a01a02p-13f, __fmul_rn(x2, S));  // -1/7!
+    S = __fadd_rn(0x1.111112p-7f, __fmul_rn(x2, S));    // 1/5!
+    S = __fadd_rn(-0x1.555556p-3f, __fmul_rn(x2, S));   // -1/3!
+    S = __fadd_rn(1.0f, __fmul_rn(x2, S));
+    float C = -0x1.27e4fcp-22f;                         // -1/10!
+    C = __fadd_rn(0x1.a01a02p-16f, __fmul_rn(x2, C));   // 1/8!
+    C = __fadd_rn(-0x1.6c16c2p-10f, __fmul_rn(x2, C));  // -1/6!
+    C = __fadd_rn(0x1.555556p-5f, __fmul_rn(x2, C));    // 1/4!
+    C = __fadd_rn(-0.5f, __fmul_rn(x2, C));             // -1/2!
+    C = __fadd_rn(1.0f, __fmul_rn(x2, C));
     S = __fmul_rn(x, S);
     switch (qi) {
         case 0: *sn = S; *cs = C; break;
