@@ -24,6 +24,7 @@
 #include <cstring>
 #include <vector>
 
+#include "bulk.cuh"
 #include "fft.cuh"
 #include "rng.cuh"
 #include "sce_internal.cuh"
@@ -587,6 +588,126 @@ __global__ void __launch_bounds__(256, MINB) ce_col_kernel(
                           blockIdx.y, smem_raw);
 }
 
+// ------------------------------------------------------- column pass, staged
+// The FP32 column pass for P = 16..2048 with its lines brought in by bulk
+// copies.  Lines are numbered across the launch's samples, line l = sl *
+// ncols + x, and lie one after the other in Y, so CB_G = 2048 / P consecutive
+// lines are one contiguous 16 KB chunk.  A persistent block of CB_THREADS
+// threads (P/16 per line, CB_G lines at once) takes chunks blockIdx.x,
+// blockIdx.x + gridDim.x, ...; two stages of shared memory alternate, and the
+// copy of the next chunk is in flight while the current one is transformed,
+// in place: each thread reads its 16 first-pass inputs from the copied
+// (unpadded) lines, and after a block barrier the radix-16 passes run on the
+// same memory in the padded line layout.  The butterflies, twiddles and the
+// exp epilogue are the per-block kernel's, so both give the same bits.  A
+// chunk whose copy does not land within wait_cycles gets NaN outputs (and so
+// does every later chunk of the block; *err is set), which the solver turns
+// into CE_ERR_NONFINITE.
+constexpr int CB_THREADS = 128;
+constexpr int CB_ELEMS = CB_THREADS * 16;   // complex values per chunk
+
+__host__ __device__ constexpr size_t col_bulk_stage_len(int P) {
+    return (size_t)(CB_ELEMS / P) * fft_line_pitch(P);   // float2 per stage
+}
+__host__ __device__ constexpr size_t col_bulk_smem(int P) {
+    return 2 * col_bulk_stage_len(P) * sizeof(float2) + 2 * sizeof(uint64_t);
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(CB_THREADS, MINB) ce_col_bulk_kernel(
+    const float2 *__restrict__ Y, int nlines, int ncols, int P, int logP, int m,
+    const float2 *__restrict__ tw, int coarse, float *__restrict__ kout,
+    float *__restrict__ kc_plain, long long wait_cycles, int *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tpf = P >> 4, G = CB_ELEMS / P, SL = (int)col_bulk_stage_len(P);
+    float2 *stg = reinterpret_cast<float2 *>(smem_raw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(stg + 2 * SL);
+    const int nchunks = (nlines + G - 1) / G;
+    const int tid = threadIdx.x, g = tid / tpf, t = tid - g * tpf;
+    if (tid == 0) {
+        mbar_init(bar);
+        mbar_init(bar + 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // thread 0: copy chunk c into stage s
+    auto issue = [&](int c, int s) {
+        const int l0 = c * G, nl = min(G, nlines - l0);
+        const uint32_t bytes = (uint32_t)nl * (uint32_t)P * (uint32_t)sizeof(float2);
+        mbar_arrive_expect(bar + s, bytes);
+        bulk_copy_g2s(stg + (size_t)s * SL, Y + (size_t)l0 * P, bytes, bar + s);
+    };
+    int c = blockIdx.x;
+    bool broken = false;
+    unsigned pend = 0;    // bit s: a copy into stage s not yet waited for
+    int uses0 = 0, uses1 = 0;   // completed phases of the two stages' barriers
+    if (c < nchunks) {
+        if (tid == 0) issue(c, 0);
+        pend = 1u;
+    }
+    const float invP = 1.0f / (float)P;
+    const int mc = m / 2, nout = coarse ? mc + 1 : m + 1;
+    // the outputs of a chunk are (y, line) pairs with the line fastest: since
+    // G divides CB_THREADS, each thread keeps one line of every chunk
+    const int gq = tid & (G - 1), ystep = CB_THREADS / G;
+    for (int k = 0; c < nchunks; c += gridDim.x, ++k) {
+        const int s = k & 1;
+        const int cn = c + gridDim.x;
+        if (!broken && cn < nchunks) {
+            // stage s ^ 1 was last touched before the barrier that ended the previous chunk
+            if (tid == 0) issue(cn, s ^ 1);
+            pend |= 2u >> s;
+        }
+        const int par = (s ? uses1 : uses0) & 1;
+        const bool ok = broken || mbar_wait(bar + s, (uint32_t)par, wait_cycles);
+        if (__syncthreads_or(!ok)) {
+            if (!broken && tid == 0) atomicExch(err, 1);
+            broken = true;
+        } else if (!broken) {
+            pend &= ~(1u << s);
+            if (s) ++uses1;
+            else ++uses0;
+        }
+        float2 *buf = stg + (size_t)s * SL;
+        const int l0 = c * G, nl = min(G, nlines - l0);
+        if (!broken) {
+            float2 v[16];
+            const float2 *raw = buf + (size_t)g * P;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = raw[t + r * tpf];
+            __syncthreads();   // every copied value read before the padded layout overwrites it
+            smem_fft16_regs<float>(buf + (size_t)g * fft_line_pitch(P), v, logP, tw, t, tpf);
+        }
+        if (gq < nl) {
+            const int l = l0 + gq, sl = l / ncols, x = l - sl * ncols;
+            const float2 *line = buf + (size_t)gq * fft_line_pitch(P);
+            for (int y = tid / G; y < nout; y += ystep) {
+                float kv = __int_as_float(0x7fc00000);
+                if (!broken) {
+                    const float2 w = line[fft_pad(coarse ? 2 * y : y)];
+                    kv = exp_r<float>((w.x + w.y) * invP);
+                }
+                if (!coarse) {
+                    kout[((size_t)sl * (m + 1) + y) * (m + 1) + x] = kv;
+                    if (kc_plain && ((x | y) & 1) == 0)
+                        kc_plain[((size_t)sl * (mc + 1) + (y >> 1)) * (mc + 1) + (x >> 1)] = kv;
+                } else {
+                    kout[((size_t)sl * (mc + 1) + y) * (mc + 1) + x] = kv;
+                }
+            }
+        }
+        // stage s consumed, and this thread's stores to it ordered before the
+        // bulk copy that will reuse it
+        fence_proxy_async_smem();
+        __syncthreads();
+    }
+    // a wait that gave up: give the copies still in flight a bounded chance to land
+    if (broken && tid == 0) {
+        if (pend & 1u) mbar_wait(bar, (uint32_t)(uses0 & 1), wait_cycles);
+        if (pend & 2u) mbar_wait(bar + 1, (uint32_t)(uses1 & 1), wait_cycles);
+    }
+}
+
 struct LineCfg {
     int tpf, F, maxb;
     size_t smem;
@@ -692,10 +813,68 @@ static int launch_row(const ce_embedding_s *e, bool masked, const typename C2<R>
     return CE_OK;
 }
 
+// The staged column pass (SCE_COL_BULK=0: the per-block kernel instead).
+__device__ int g_col_bulk_err;   // set by a staged block whose copy never landed
+
+static bool col_bulk_on() {
+    const char *e = getenv("SCE_COL_BULK");
+    return !(e && atoi(e) == 0);
+}
+
+// Blocks per SM the staged column pass is compiled for (SCE_COLB_MINB: 4, 5
+// or 6; 6 caps it at 80 registers, with a little spilling).
+static int colb_minb() {
+    const char *e = getenv("SCE_COLB_MINB");
+    const int v = e ? atoi(e) : 6;
+    return (v == 4 || v == 5) ? v : 6;
+}
+
+template <int MINB>
+static int launch_col_bulk(const ce_embedding_s *e, const float2 *Y, int ncols, int coarse,
+                           const float2 *tw, int count, float *kout, float *kc_plain,
+                           cudaStream_t st) {
+    const int P = e->P;
+    const size_t smem = col_bulk_smem(P);
+    int dev = 0, sms = 0, bps = 0;
+    SCE_CUDA(cudaGetDevice(&dev));
+    SCE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SCE_TRY(sce_raise_smem_limit((const void *)ce_col_bulk_kernel<MINB>, smem));
+    SCE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ce_col_bulk_kernel<MINB>,
+                                                           CB_THREADS, smem));
+    int *err = nullptr;
+    SCE_CUDA(cudaGetSymbolAddress((void **)&err, g_col_bulk_err));
+    const long long nlines = (long long)count * ncols;
+    if (nlines > INT32_MAX / 2) return CE_ERR_INVALID_ARG;
+    const int G = CB_ELEMS / P;
+    const long long nchunks = (nlines + G - 1) / G;
+    const long long grid = std::min<long long>(nchunks, (long long)sms * std::max(1, bps));
+    const double rows_out = coarse ? (e->n / 2 + 1) : (e->n + 1);
+    SceProf pr(KP_COL, st,
+               (double)count * ncols * P * 2 * sizeof(float) +
+                   (double)count * ncols * rows_out * sizeof(float) * (kc_plain ? 1.25 : 1.0));
+    ce_col_bulk_kernel<MINB><<<(unsigned)grid, CB_THREADS, smem, st>>>(
+        Y, (int)nlines, ncols, P, ilog2(P), e->n, tw, coarse, kout, kc_plain, 1LL << 31, err);
+    SCE_CUDA(cudaGetLastError());
+    return CE_OK;
+}
+
 template <typename R, int MAXB>
 static int launch_col(const ce_embedding_s *e, const typename C2<R>::T *Y, int ncols, int coarse,
                       const typename C2<R>::T *tw, int count, R *kout, R *kc_plain,
                       const LineCfg &c, cudaStream_t st) {
+    // staged form: FP32, the radix-16 line shape, lines of 16..2048 values whose
+    // 16 KB chunks start on 16-byte boundaries (bulk-copy alignment)
+    if constexpr (sizeof(R) == 4) {
+        if (col_bulk_on() && c.tpf * 16 == e->P && e->P >= 16 && e->P <= CB_ELEMS &&
+            ((uintptr_t)Y & 15) == 0) {
+            const int mb = colb_minb();
+            if (mb == 4)
+                return launch_col_bulk<4>(e, Y, ncols, coarse, tw, count, kout, kc_plain, st);
+            if (mb == 5)
+                return launch_col_bulk<5>(e, Y, ncols, coarse, tw, count, kout, kc_plain, st);
+            return launch_col_bulk<6>(e, Y, ncols, coarse, tw, count, kout, kc_plain, st);
+        }
+    }
     SCE_TRY(sce_raise_smem_limit((const void *)ce_col_kernel<R, MAXB>, c.smem));
     dim3 grid((ncols + c.F - 1) / c.F, count);
     const double rows_out = coarse ? (e->n / 2 + 1) : (e->n + 1);

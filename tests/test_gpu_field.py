@@ -222,3 +222,45 @@ def test_fft_autotune_changes_time_not_fields():
             out.append((k.clone(), kc_t.clone()))
         assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
         emb.close()
+
+
+@pytest.mark.parametrize("n,pad,masked,count", [
+    (4, oem.PAD_DOUBLING, False, 5),     # short lines: 64 or more lines per staged chunk
+    (16, oem.PAD_SMOOTH, True, 37),      # ragged last chunk, coarse-masked pass
+    (32, oem.PAD_DOUBLING, False, 3),    # plain coarse field taken from the fine pass
+    (64, oem.PAD_SMOOTH, True, 9),
+    (512, oem.PAD_SMOOTH, True, 2),      # P = 2048: one line per chunk
+])
+def test_staged_column_pass_bit_identical(monkeypatch, n, pad, masked, count):
+    """The column pass with its lines staged by bulk copies (the default in
+    FP32) gives the same bits as the per-block column kernel
+    (SCE_COL_BULK=0), for every register budget it can be built for."""
+    import torch
+    from tests.gpu_common import lib
+    sce = lib()
+    emb = sce.ce_setup_embedding(ocv.MATERN, 0.5, 0.05, 1.0, n, pad_mode=pad)
+    if masked:
+        s, P = emb.info.s, emb.P
+        emb.close()
+        emb = sce.ce_setup_embedding(ocv.MATERN, 0.5, 0.05, 1.0, n, pad_mode=pad,
+                                     keep_fine=s - P, keep_coarse=s // 4)
+    out = {}
+    for mode in ("0", "4", "5", "6"):
+        if mode == "0":
+            monkeypatch.setenv("SCE_COL_BULK", "0")
+        else:
+            monkeypatch.delenv("SCE_COL_BULK", raising=False)
+            monkeypatch.setenv("SCE_COLB_MINB", mode)
+        k = torch.full((count, n + 1, n + 1), -1.0, dtype=torch.float32, device="cuda")
+        kc = torch.full((count, n // 2 + 1, n // 2 + 1), -1.0, dtype=torch.float32, device="cuda")
+        sce.ce_sample_batch(emb, 11, 3, 1000, count, 32, k_fine=k, k_coarse=kc)
+        torch.cuda.synchronize()
+        out[mode] = (k.clone(), kc.clone())
+    monkeypatch.delenv("SCE_COLB_MINB", raising=False)
+    emb.close()
+    k0, kc0 = out["0"]
+    assert bool(torch.isfinite(k0).all()) and float(k0.min()) > 0.0
+    assert bool(torch.isfinite(kc0).all()) and float(kc0.min()) > 0.0
+    for mode in ("4", "5", "6"):
+        assert torch.equal(out[mode][0], k0), mode
+        assert torch.equal(out[mode][1], kc0), mode
