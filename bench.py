@@ -47,9 +47,9 @@ TRAFFIC_PER_ALG = {
                     "paper_2306_13493_gb300/csrc/darcy.cu", "pspmv_kernel",
                     "9a76b841323f6d80ce7b0bc9ee4c5a1f56e55f9e4fc43749a2e76bd639234e5b"),
     # n = 512 launch of the tile kernel, 48-row windows (profiles/mg_up_n512x32.md)
-    "mg_up": ((143.224064 + 19.643136) / 176.882432,
+    "mg_up": ((143.223296 + 20.216576) / 176.882432,
               "paper_2306_13493_gb300/csrc/mg_tiles.cuh", "mg_up_kernel",
-              "03378b11ee42316507e0de0419a19074477b337e3214572363991afb8f39df0b"),
+              "1e6c3d6b2ae324929df37ce45854077b49df36df7edd57bdbf3e5778ac9dd6b9"),
 }
 
 
@@ -759,7 +759,7 @@ def precision_study(args):
 # 64 cells (one block per sample, a few microseconds) by launch latency.  The
 # rest are HBM-bound.
 KERNEL_BOUND = {"mg_tail": "l2", "ce_row": "issue", "darcy_small": "issue", "mg_v64": "issue",
-                "mg_up": "issue", "mg_down": "issue",
+                "mg_up": "issue", "mg_down": "issue", "mg_up3": "issue", "mg_down3": "issue",
                 "reduce": "latency", "level_sums": "latency", "coarsen_tail": "latency"}
 
 # Warp instructions per algorithmic byte of issue-bound families, from one ncu
@@ -768,12 +768,17 @@ KERNEL_BOUND = {"mg_tail": "l2", "ce_row": "issue", "darcy_small": "issue", "mg_
 # bench's issue fraction = its algorithmic bytes x this ratio / time / the
 # measured FMA issue rate, reported only while the source is the captured one.
 INSTR_PER_ALG = {
-    # n = 512 x 32 launches with 48-row windows, V(2,2) (profiles/mg_up_n512x32.md,
+    # n = 512 x 32 launches with 48-row windows and two sweeps per side; the
+    # n = 128 launches of the same capture with three (profiles/mg_up_n512x32.md,
     # profiles/mg_down_n512x32.md)
     "mg_up": (40920192 / 176882432, "paper_2306_13493_gb300/csrc/mg_tiles.cuh", "mg_up_kernel",
-              "03378b11ee42316507e0de0419a19074477b337e3214572363991afb8f39df0b"),
+              "1e6c3d6b2ae324929df37ce45854077b49df36df7edd57bdbf3e5778ac9dd6b9"),
     "mg_down": (34649984 / 143196800, "paper_2306_13493_gb300/csrc/mg_tiles.cuh",
-                "mg_down_kernel", "7e4e5ffd8a16cddc3599ab83cf44c53c804d063fcc45229a39f72a7ec30967f1"),
+                "mg_down_kernel", "0ce6fbf16c0c0370eaa26537be930a5a137567ada777dd6f46508928316588f9"),
+    "mg_up3": (3979584 / 11191040, "paper_2306_13493_gb300/csrc/mg_tiles.cuh", "mg_up_kernel",
+               "1e6c3d6b2ae324929df37ce45854077b49df36df7edd57bdbf3e5778ac9dd6b9"),
+    "mg_down3": (3466176 / 9060992, "paper_2306_13493_gb300/csrc/mg_tiles.cuh",
+                 "mg_down_kernel", "0ce6fbf16c0c0370eaa26537be930a5a137567ada777dd6f46508928316588f9"),
 }
 
 

@@ -12,10 +12,11 @@ namespace sce {
 
 constexpr int mg_levels(int n) { return n <= 2 ? 1 : 1 + mg_levels(n / 2); }
 
-// Red-black Gauss-Seidel sweeps before and after each coarse-grid correction,
-// on every level and in every kernel of the batched FP32 solver's cycle:
-// SCE_MG_NU = 2, a V(2,2) cycle (the default: ~27 % fewer CG iterations for
-// ~1.3-1.45 times the work of a cycle), or 1, a V(1,1) cycle.
+// Red-black Gauss-Seidel sweeps before and after each coarse-grid correction
+// on the finest level of the batched FP32 solver's cycle and on its levels
+// wider than 128 cells (the coarser levels take three by default):
+// SCE_MG_NU = 2 (the default: ~27 % fewer CG iterations than one sweep for
+// ~1.3-1.45 times the work of a cycle), or 1.
 #ifndef SCE_MG_NU
 #define SCE_MG_NU 2
 #endif
@@ -66,23 +67,25 @@ __device__ __forceinline__ void block_half_sweep(const T *cx, const T *cy, const
 }
 
 template <typename T, int N, int NT, class Lay, int L, int WARP_N, int NU>
-__device__ __forceinline__ void block_vcycle_level(T *base);
+__device__ __forceinline__ void block_vcycle_level(T *base, int nu0, int nuc);
 
 // The V-cycle from level L down and back up: with WARP_N > 0 in a block of
 // more than one warp, the levels of at most WARP_N cells run on warp 0 alone
 // (warp synchronisation) while the other warps wait at one block barrier.
+// nu0: sweeps per side on level 0, nuc on the others (compile-time constants
+// where the caller passes them so, and the sweep loops unroll).
 template <typename T, int N, int NT, class Lay, int L, int WARP_N, int NU>
-__device__ __forceinline__ void block_vcycle_from(T *base) {
+__device__ __forceinline__ void block_vcycle_from(T *base, int nu0, int nuc) {
     if constexpr (NT > 32 && WARP_N > 0 && (N >> L) <= WARP_N) {
-        if (threadIdx.x < 32) block_vcycle_level<T, N, 32, Lay, L, 0, NU>(base);
+        if (threadIdx.x < 32) block_vcycle_level<T, N, 32, Lay, L, 0, NU>(base, nu0, nuc);
         __syncthreads();
     } else {
-        block_vcycle_level<T, N, NT, Lay, L, WARP_N, NU>(base);
+        block_vcycle_level<T, N, NT, Lay, L, WARP_N, NU>(base, nu0, nuc);
     }
 }
 
 template <typename T, int N, int NT, class Lay, int L, int WARP_N, int NU>
-__device__ __forceinline__ void block_vcycle_level(T *base) {
+__device__ __forceinline__ void block_vcycle_level(T *base, int nu0, int nuc) {
     constexpr int NL = mg_levels(N);
     constexpr int nL = N >> L;
     T *cx = base + Lay::off(L, 0), *cy = base + Lay::off(L, 1);
@@ -93,8 +96,9 @@ __device__ __forceinline__ void block_vcycle_level(T *base) {
     } else {
         constexpr int nc = nL / 2, wc = nc + 1, Vc = wc * wc, wL = nL + 1, VL = wL * wL;
         T *bc = base + Lay::off(L + 1, 2), *zc = base + Lay::off(L + 1, 3);
+        const int nu = L == 0 ? nu0 : nuc;
 #pragma unroll
-        for (int k = 0; k < NU; ++k) {
+        for (int k = 0; k < nu; ++k) {
             block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
             block_sync<NT>();
             block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
@@ -106,14 +110,14 @@ __device__ __forceinline__ void block_vcycle_level(T *base) {
             zc[v] = T(0);
         }
         block_sync<NT>();
-        block_vcycle_from<T, N, NT, Lay, L + 1, WARP_N, NU>(base);
+        block_vcycle_from<T, N, NT, Lay, L + 1, WARP_N, NU>(base, nu0, nuc);
         for (int v = threadIdx.x; v < VL; v += NT) {
             const int j = v / wL, i = v - j * wL;
             if (i > 0 && i < nL) z[v] += prolong_at(zc, nc, i, j);
         }
         block_sync<NT>();
 #pragma unroll
-        for (int k = 0; k < NU; ++k) {
+        for (int k = 0; k < nu; ++k) {
             block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
             block_sync<NT>();
             block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
@@ -142,15 +146,16 @@ __device__ __forceinline__ void block_coarsen(T *base) {
 }
 
 // z = M^{-1} b on level 0 of the hierarchy laid out by Lay from `base`.
-// Symmetric: NU red-black Gauss-Seidel sweeps before the restriction, NU
-// black-red sweeps after the prolongation, exact solve on 2 cells.  All NT
+// Symmetric: on each level, nu red-black Gauss-Seidel sweeps before the
+// restriction and nu black-red sweeps after the prolongation (nu = nu0 on
+// level 0, nuc below it; both NU by default), exact solve on 2 cells.  All NT
 // threads must call it.
 template <typename T, int N, int NT, class Lay, int WARP_N = 0, int NU = mg_nu<T>()>
-__device__ __forceinline__ void block_vcycle(T *base) {
+__device__ __forceinline__ void block_vcycle(T *base, int nu0 = NU, int nuc = NU) {
     T *z = base + Lay::off(0, 3);
     for (int v = threadIdx.x; v < mg_vof(N); v += NT) z[v] = T(0);
     block_sync<NT>();
-    block_vcycle_from<T, N, NT, Lay, 0, WARP_N, NU>(base);
+    block_vcycle_from<T, N, NT, Lay, 0, WARP_N, NU>(base, nu0, nuc);
 }
 
 }  // namespace sce

@@ -14,9 +14,11 @@
 //
 // Solver.  u (nodal, Dirichlet values included) is improved by iterative
 // refinement: r = F - A u in high precision; the correction equation A d = r
-// is solved by CG preconditioned with one symmetric multigrid cycle, V(2,2)
-// in FP32 and V(1,1) in FP64 (mg_nu<T>() red-black Gauss-Seidel sweeps before
-// and black-red sweeps after each coarse correction, full-weighting
+// is solved by CG preconditioned with one symmetric multigrid cycle: in FP32
+// two red-black Gauss-Seidel sweeps before and two black-red sweeps after each
+// coarse correction on the finest level and on the levels wider than 128
+// cells, three on the coarser levels (the per-level counts keep the cycle
+// symmetric); V(1,1) in FP64; full-weighting
 // restriction = transpose of bilinear
 // prolongation, coarse conductances by series/parallel edge averaging, exact
 // tridiagonal solve on the 2-cell grid), in FP32 (precision 32) or FP64
@@ -55,6 +57,20 @@ constexpr int MAXLEV = 14;
 #define SCE_TAIL_N 32
 #endif
 constexpr int TAIL_N = SCE_TAIL_N;   // levels with n <= TAIL_N run in one block per sample
+
+// Sweeps per side on the coarse levels of the FP32 cycle: on grids of 128
+// cells or more, every level below the finest of at most MG_NU_COARSE_MAX cells takes
+// SCE_MG_NU_COARSE sweeps (3 by default; 2 gives the uniform V(2,2) cycle).
+// On the oscillatory fields the third sweep on those levels (all of them: on
+// a subset it gains nothing) takes a solve at n = 128..512 from ~9.3 to ~8.4
+// CG iterations for a few percent more work per cycle; on n = 64 grids it
+// saved too little to pay for the extra barrier-bound sweeps of the fused
+// n = 64 cycle's shared-memory levels.
+constexpr int MG_NU_COARSE_MAX = 128;
+int mg_nu_coarse() {
+    const char *e = getenv("SCE_MG_NU_COARSE");
+    return (e && atoi(e) == 2) ? 2 : 3;
+}
 
 // Window heights of the tiled multigrid kernels, per (precision, grid size),
 // chosen by darcy_autotune_tiles; MG_SH where absent (SCE_TILE_SH forces one
@@ -960,7 +976,7 @@ struct Solver {
                                                                     sc.act_in);
             return;
         }
-        for (int k = 0; k < mg_nu<T>(); ++k) {
+        for (int k = 0; k < lnu(L); ++k) {
             smooth(L, 0);
             smooth(L, 1);
         }
@@ -975,7 +991,7 @@ struct Solver {
             prolong_kernel<T><<<grid(L), ln[L].tpb, 0, st>>>(z[L + 1], n[L + 1], z[L], ln[L].vpt,
                                                              sc.act_in);
         }
-        for (int k = 0; k < mg_nu<T>(); ++k) {
+        for (int k = 0; k < lnu(L); ++k) {
             smooth(L, 1);
             smooth(L, 0);
         }
@@ -986,6 +1002,16 @@ struct Solver {
     bool fused = true;
     int Lt = 0;                 // first level of the tail
     int tiles_x[MAXLEV], tiles_n[MAXLEV], sh[MAXLEV];
+    int nu[MAXLEV];             // sweeps per side of each tiled level
+    int nu_c = 0;               // sweeps per side of the coarse levels (FP32)
+    int v64_nut = 0, v64_nus = 0;
+    // sweeps per side on level L, the same rule on every path of the cycle
+    // (tiles, fused n = 64 cycle, one-block tail, level-by-level kernels)
+    int lnu(int L) const {
+        return (n[0] >= 2 * V64_N && L > 0 && L < nlev && n[L] <= MG_NU_COARSE_MAX)
+                   ? nu_c
+                   : mg_nu<T>();
+    }
 
     // FP32: an n = 64 level and everything below it run as one fused kernel
     // per sample (mg_v64_kernel; SCE_V64=0 keeps the tiled kernels for it)
@@ -1000,10 +1026,17 @@ struct Solver {
         Lt = 0;
         while (n[Lt] > tail_n) ++Lt;
         v64 = sizeof(T) == 4 && tail_n == V64_N && n[Lt] == V64_N;
+        nu_c = sizeof(T) == 4 ? mg_nu_coarse() : mg_nu<T>();
+        v64_nut = lnu(Lt);
+        v64_nus = lnu(Lt + 1);
         for (int L = 0; L < Lt; ++L) {
             const int nc1 = n[L] / 2 + 1;
+            nu[L] = lnu(L);
             sh[L] = tile_height_for((int)sizeof(T), n[L]);
-            const int ch = MGGeom<T>::ch(sh[L]), cw = MGGeom<T>::CW;
+            // three sweeps: windows of 48 rows at least (CH = SH / 2 - 7)
+            if (nu[L] == 3 && sh[L] < 48) sh[L] = 48;
+            const int ch = nu[L] == 3 ? MGGeom<T, 3>::ch(sh[L]) : MGGeom<T>::ch(sh[L]);
+            const int cw = nu[L] == 3 ? MGGeom<T, 3>::CW : MGGeom<T>::CW;
             tiles_x[L] = (nc1 + cw - 1) / cw;
             tiles_n[L] = tiles_x[L] * ((nc1 + ch - 1) / ch);
         }
@@ -1026,7 +1059,7 @@ struct Solver {
 
     // what a cached solver must match to be reused: samples, grid and plan
     std::vector<int> signature() const {
-        std::vector<int> sg{count, n[0], fused ? 1 : 0, Lt, v64 ? 1 : 0};
+        std::vector<int> sg{count, n[0], fused ? 1 : 0, Lt, v64 ? 1 : 0, nu_c};
         for (int L = 0; L < Lt; ++L) sg.push_back(sh[L]);
         return sg;
     }
@@ -1080,28 +1113,59 @@ struct Solver {
         return CE_OK;
     }
 
-    // launches of the tiled kernels of window height SH
+    // launches of the tiled kernels of window height SH and NU sweeps per side
     unsigned tile_attr_mask = 0;
-    template <int SH>
+    template <int SH, int NU>
     void tile_down(int L) {
         constexpr size_t smem = mg_tile_smem_bytes<T, SH>();
-        constexpr unsigned bit = 1u << (SH / 8);
+        constexpr unsigned bit = 1u << (SH / 8 + 9 * (NU - 1));
         if (!(tile_attr_mask & bit)) {   // outside any capture (the first cycle is not captured)
-            sce_raise_smem_limit((const void *)mg_down_kernel<T, SH>, smem);
-            sce_raise_smem_limit((const void *)mg_up_kernel<T, SH>, smem);
+            sce_raise_smem_limit((const void *)mg_down_kernel<T, SH, NU>, smem);
+            sce_raise_smem_limit((const void *)mg_up_kernel<T, SH, NU>, smem);
             tile_attr_mask |= bit;
         }
-        SceProf pr(KP_MG_DOWN, st, vb(L, 4.0) + vb(L + 1, 1.0));
-        mg_down_kernel<T, SH><<<dim3(tiles_n[L], count), MGTile<SH>::THREADS, smem, st>>>(
+        SceProf pr(NU == 3 ? KP_MG_DOWN3 : KP_MG_DOWN, st, vb(L, 4.0) + vb(L + 1, 1.0));
+        mg_down_kernel<T, SH, NU><<<dim3(tiles_n[L], count), MGTile<SH>::THREADS, smem, st>>>(
             cx[L], cy[L], b[L], zpre[L], n[L], b[L + 1], tiles_x[L], sc.act_in);
     }
-    template <int SH>
+    template <int SH, int NU>
     void tile_up(int L, bool want_rz) {
         constexpr size_t smem = mg_tile_smem_bytes<T, SH>();
-        SceProf pr(KP_MG_UP, st, vb(L, 5.0) + vb(L + 1, 1.0));
-        mg_up_kernel<T, SH><<<dim3(tiles_n[L], count), MGTile<SH>::THREADS, smem, st>>>(
+        SceProf pr(NU == 3 ? KP_MG_UP3 : KP_MG_UP, st, vb(L, 5.0) + vb(L + 1, 1.0));
+        mg_up_kernel<T, SH, NU><<<dim3(tiles_n[L], count), MGTile<SH>::THREADS, smem, st>>>(
             cx[L], cy[L], b[L], zpre[L], z[L], n[L], z[L + 1], tiles_x[L], sc.act_in,
             (want_rz && L == 0) ? part : nullptr, tiles_n[0]);
+    }
+    // by the level's window height and sweep count (three sweeps: FP32, 48 or
+    // 64 rows)
+    template <int NU>
+    void tile_pass(int L, bool up, bool want_rz) {
+        auto go = [&](auto shc) {
+            constexpr int SH = decltype(shc)::value;
+            if (up) tile_up<SH, NU>(L, want_rz);
+            else tile_down<SH, NU>(L);
+        };
+        if constexpr (NU == 3) {
+            if (sh[L] == 64) go(std::integral_constant<int, 64>{});
+            else go(std::integral_constant<int, 48>{});
+        } else {
+            switch (sh[L]) {
+                case 16: go(std::integral_constant<int, 16>{}); break;
+                case 24: go(std::integral_constant<int, 24>{}); break;
+                case 48: go(std::integral_constant<int, 48>{}); break;
+                case 64: go(std::integral_constant<int, 64>{}); break;
+                default: go(std::integral_constant<int, 32>{}); break;
+            }
+        }
+    }
+    void tile_level(int L, bool up, bool want_rz) {
+        if constexpr (sizeof(T) == 4) {
+            if (nu[L] == 3) {
+                tile_pass<3>(L, up, want_rz);
+                return;
+            }
+        }
+        tile_pass<mg_nu<T>()>(L, up, want_rz);
     }
 
     // partial-sum slots per sample written by vcycle_fused(want_rz = true)
@@ -1123,11 +1187,22 @@ struct Solver {
         }
         SceProf pr(KP_MG_TAIL, st, (double)count * (smem + 2 * sizeof(T) * ln[Lt].V));
         mg_tail_kernel<T, NTN, NTHR><<<count, NTHR, smem, st>>>(tp, b[Lt], z[Lt], sc.act_in,
-                                                                want_rz ? part : nullptr);
+                                                                want_rz ? part : nullptr,
+                                                                lnu(Lt), lnu(Lt + 1));
     }
 
-    bool v64_attr_set = false;
-    int v64_warp_n = 0;   // SCE_V64_WARP_N: levels of at most 8 or 16 cells on one warp
+    unsigned v64_attr_mask = 0;
+    template <int NUT, int NUS>
+    void v64_go(const TailPtrs &tp, double *pr_rz) {
+        constexpr size_t smem = v64_smem_bytes<T>();
+        constexpr unsigned bit = 1u << (NUT * 4 + NUS);
+        if (!(v64_attr_mask & bit)) {   // outside any stream capture (the first cycle is not captured)
+            sce_raise_smem_limit((const void *)mg_v64_kernel<T, 0, NUT, NUS>, smem);
+            v64_attr_mask |= bit;
+        }
+        mg_v64_kernel<T, 0, NUT, NUS><<<count, V64_THREADS, smem, st>>>(
+            cx[Lt], cy[Lt], b[Lt], z[Lt], tp, sc.act_in, pr_rz);
+    }
     void v64_launch(bool want_rz) {
         if constexpr (sizeof(T) == 4) {
             TailPtrs tp{};
@@ -1135,43 +1210,21 @@ struct Solver {
                 tp.cx[i] = cx[Lt + 1 + i];
                 tp.cy[i] = cy[Lt + 1 + i];
             }
-            constexpr size_t smem = v64_smem_bytes<T>();
-            if (!v64_attr_set) {   // outside any stream capture (the first cycle is not captured)
-                sce_raise_smem_limit((const void *)mg_v64_kernel<T, 0>, smem);
-                sce_raise_smem_limit((const void *)mg_v64_kernel<T, 8>, smem);
-                sce_raise_smem_limit((const void *)mg_v64_kernel<T, 16>, smem);
-                v64_attr_set = true;
-                const char *e = getenv("SCE_V64_WARP_N");
-                v64_warp_n = e ? atoi(e) : 0;
-            }
             // b, cx, cy in, z out on the level; the conductances of the levels below in
             double tail_v = 0.0;
             for (int L = Lt + 1; L < nlev; ++L) tail_v += (double)ln[L].V;
             SceProf pr(KP_MG_V64, st, vb(Lt, 4.0) + (double)count * tail_v * 2.0 * sizeof(T));
             double *pr_rz = want_rz ? part : nullptr;
-            if (v64_warp_n == 8)
-                mg_v64_kernel<T, 8><<<count, V64_THREADS, smem, st>>>(cx[Lt], cy[Lt], b[Lt], z[Lt],
-                                                                     tp, sc.act_in, pr_rz);
-            else if (v64_warp_n == 16)
-                mg_v64_kernel<T, 16><<<count, V64_THREADS, smem, st>>>(cx[Lt], cy[Lt], b[Lt],
-                                                                      z[Lt], tp, sc.act_in, pr_rz);
-            else
-                mg_v64_kernel<T, 0><<<count, V64_THREADS, smem, st>>>(cx[Lt], cy[Lt], b[Lt], z[Lt],
-                                                                     tp, sc.act_in, pr_rz);
+            // three sweeps on the n = 64 level and below when it is a coarse
+            // level of a wider grid, else the default
+            if (v64_nut == 3 && v64_nus == 3) v64_go<3, 3>(tp, pr_rz);
+            else v64_go<mg_nu<T>(), mg_nu<T>()>(tp, pr_rz);
         }
     }
 
     // z[0] = M^{-1} b[0]; with want_rz the partial sums of b[0] . z[0] go to part
     void vcycle_fused(bool want_rz) {
-        for (int L = 0; L < Lt; ++L) {
-            switch (sh[L]) {
-                case 16: tile_down<16>(L); break;
-                case 24: tile_down<24>(L); break;
-                case 48: tile_down<48>(L); break;
-                case 64: tile_down<64>(L); break;
-                default: tile_down<32>(L); break;
-            }
-        }
+        for (int L = 0; L < Lt; ++L) tile_level(L, false, false);
         const bool rz_tail = want_rz && Lt == 0;
         if (v64) v64_launch(rz_tail);
         else switch (n[Lt]) {
@@ -1181,15 +1234,7 @@ struct Solver {
             case 8: tail_launch<8, 64>(rz_tail); break;
             default: tail_launch<4, 32>(rz_tail); break;
         }
-        for (int L = Lt - 1; L >= 0; --L) {
-            switch (sh[L]) {
-                case 16: tile_up<16>(L, want_rz); break;
-                case 24: tile_up<24>(L, want_rz); break;
-                case 48: tile_up<48>(L, want_rz); break;
-                case 64: tile_up<64>(L, want_rz); break;
-                default: tile_up<32>(L, want_rz); break;
-            }
-        }
+        for (int L = Lt - 1; L >= 0; --L) tile_level(L, true, want_rz);
     }
 
     void reduce(int mode, const int *act, double rtol2 = 0.0, double in_rel2 = 0.0,
@@ -1694,13 +1739,14 @@ static int darcy_solve_t(const darcy_problem *p, const Tk *k, int count, double 
         // one its last iteration skips), so the passes that ran are the
         // samples' total iteration count hm[2]
         static const int cg_ids[] = {KP_SPMV, KP_AXPY};
-        static const int vc_ids[] = {KP_MG_DOWN, KP_MG_UP, KP_MG_V64, KP_MG_TAIL, KP_SMOOTH,
-                                     KP_RESTRICT, KP_PROLONG, KP_COARSEST, KP_DOT};
+        static const int vc_ids[] = {KP_MG_DOWN, KP_MG_UP, KP_MG_DOWN3, KP_MG_UP3, KP_MG_V64,
+                                     KP_MG_TAIL, KP_SMOOTH, KP_RESTRICT, KP_PROLONG,
+                                     KP_COARSEST, KP_DOT};
         if (n_head > 0)
             sce_prof_scale(prof_mark, st, cg_ids, 2,
                            std::min(1.0, (double)hm[2] / ((double)n_head * count)));
         if (n_vc > 0)
-            sce_prof_scale(prof_mark, st, vc_ids, 9,
+            sce_prof_scale(prof_mark, st, vc_ids, (int)(sizeof(vc_ids) / sizeof(vc_ids[0])),
                            std::min(1.0, (double)hm[2] / ((double)n_vc * count)));
     }
     lease.ok = true;
@@ -1729,7 +1775,8 @@ int sce_darcy_solve_impl(const darcy_problem *p, const void *k, int count, doubl
     if (u_ff && p->precision != 32) return CE_ERR_INVALID_ARG;
     if (p->precision == 32 && p->n <= sce_small_max_n() && p->n <= 64)
         return sce_darcy_small(p, (const float *)k, count, qoi, iters, status, u_out, st,
-                               max_iters_out, n_failed_out, qmask | (u_ff ? 8 : 0));
+                               max_iters_out, n_failed_out, qmask | (u_ff ? 8 : 0), u_init,
+                               u_ff);
     if (p->precision == 64)
         return darcy_solve_t<double, double>(p, (const double *)k, count, qoi, iters, status,
                                              u_out, st, max_iters_out, n_failed_out, qmask,

@@ -57,7 +57,8 @@ template <int N, int NT>
 __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kernel(
     const float *__restrict__ kin, double f, double rtol2, double in_rel2, int maxit,
     double *__restrict__ qoi, int *__restrict__ iters_out, int *__restrict__ status_out,
-    double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits, int qmask) {
+    double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits, int qmask,
+    const float2 *__restrict__ u0f, const double *__restrict__ u0d) {
     using Lay = SmallLayout<N>;
     using MG = MGPackedLayout<N>;
     constexpr int W = Lay::W, V = Lay::V, NL = Lay::NL;
@@ -135,6 +136,39 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
         orr = bsum1<NT>((double)acc, sh, pard);
     }
     const double orr0 = orr;
+    // a first iterate from the n/2 solution (nested iteration): u = P u_c with
+    // float-float additions and exact halvings, then its float-float residual
+    if (u0f || u0d) {
+        constexpr int NCc = N / 2, WCc = NCc + 1;
+        const size_t cb = (size_t)s * WCc * WCc;
+        auto U = [&](int jj, int ii) {
+            const size_t q = cb + (size_t)jj * WCc + ii;
+            if (u0f) {
+                const float2 t = u0f[q];
+                return ff{t.x, t.y};
+            }
+            return ff_from_double(u0d[q]);
+        };
+        for (int v = tid; v < V; v += NT) {
+            const int j = v / W, i = v - j * W;
+            const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
+            ff a = U(j0, i0);
+            float sc = 1.0f;
+            if (i1 != i0) {
+                a = ff_add(a, U(j0, i1));
+                sc = 0.5f;
+            }
+            if (j1 != j0) {
+                ff b = U(j1, i0);
+                if (i1 != i0) b = ff_add(b, U(j1, i1));
+                a = ff_add(a, b);
+                sc *= 0.5f;
+            }
+            u[v] = make_float2(a.hi * sc, a.lo * sc);
+        }
+        block_sync<NT>();
+        orr = outer_residual();
+    }
     float *shf = reinterpret_cast<float *>(sh + 40);
     int its = 0;
     for (int outer = 0; outer < 64 && orr > rtol2 * orr0 && its < maxit; ++outer) {
@@ -247,14 +281,16 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
 
 template <int N, int NT>
 int launch_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
-                 int *status, double *u_out, int *misc, int qmask, cudaStream_t st) {
+                 int *status, double *u_out, int *misc, int qmask, const float2 *u0f,
+                 const double *u0d, cudaStream_t st) {
     const size_t smem = SmallLayout<N>::bytes;
     SCE_TRY(sce_raise_smem_limit((const void *)small_solve_kernel<N, NT>, smem));
     const double in_rel = sce_inner_rel_f32();
     SceProf pr(KP_SMALL, st, (double)count * SmallLayout<N>::V * (sizeof(float) + 0.0) + 24.0 * count);
     small_solve_kernel<N, NT><<<count, NT, smem, st>>>(k, p->f, p->rtol * p->rtol, in_rel * in_rel,
                                                        p->maxit > 0 ? p->maxit : 1000, qoi, iters,
-                                                       status, u_out, misc, misc + 1, qmask);
+                                                       status, u_out, misc, misc + 1, qmask,
+                                                       u0f, u0d);
     SCE_CUDA(cudaGetLastError());
     return CE_OK;
 }
@@ -282,13 +318,15 @@ int sce_small_max_n() {
 
 int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
                     int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                    int *n_failed_out, int qmask) {
+                    int *n_failed_out, int qmask, const void *u_init, bool u_init_ff) {
+    const float2 *u0f = u_init_ff ? static_cast<const float2 *>(u_init) : nullptr;
+    const double *u0d = u_init_ff ? nullptr : static_cast<const double *>(u_init);
     int *misc = nullptr;   // [0] failed samples, [1] max iterations, [2] total iterations
     SCE_TRY(sce_alloc_t(&misc, 3, st));
     SCE_CUDA(cudaMemsetAsync(misc, 0, 3 * sizeof(int), st));
     int rc = CE_ERR_INVALID_ARG;
 #define SCE_SMALL(NN, TT) \
-    rc = launch_small<NN, TT>(p, k, count, qoi, iters, status, u_out, misc, qmask, st)
+    rc = launch_small<NN, TT>(p, k, count, qoi, iters, status, u_out, misc, qmask, u0f, u0d, st)
     switch (p->n) {
         case 4: SCE_SMALL(4, 32); break;
         case 8: SCE_SMALL(8, 64); break;

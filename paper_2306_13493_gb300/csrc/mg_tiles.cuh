@@ -17,7 +17,7 @@
 // indices.  Elements outside the grid hold zero data; at Dirichlet columns and
 // outside the grid 1/diag is 0, so their z stays 0.
 //
-//   mg_down: pre-smoothing from a zero guess (mg_nu<T>() sweeps of red then black
+//   mg_down: pre-smoothing from a zero guess (NU sweeps of red then black
 //            Gauss-Seidel), fine residual, full-weighting restriction -> zpre
 //            (fine), b (coarse).
 //            After the black half-sweep the residual vanishes at the black
@@ -26,7 +26,7 @@
 //            restriction sums the coarse vertex and its four diagonal
 //            neighbours (the red ones of its 3 x 3 stencil).
 //   mg_up  : z = zpre + bilinear prolongation of the coarse correction, then
-//            post-smoothing (mg_nu<T>() sweeps of black then red) -> z (fine); optionally the
+//            post-smoothing (NU sweeps of black then red) -> z (fine); optionally the
 //            partial sums of r . z (level 0, for CG's beta).  zpre and z are
 //            distinct arrays: a tile reads zpre in its halo, which other
 //            tiles of the same launch own and write to z.
@@ -56,11 +56,13 @@ constexpr int MG_NW = MG_SH / 4;           // warps per block
 // there), and so do the residual and the restriction's diagonal neighbours:
 // with NU sweeps per side, mg_down's window starts 2 NU + 2 fine vertices below
 // and left of its owned region, mg_up's 2 NU; the owned region is 2 CW x 2 CH
-// fine vertices with CW = 32 - 2 NU - 1 (29 for V(1,1), 27 for V(2,2)) and
-// CH = SH / 2 - 2 NU - 1 for a window of SH rows.
-template <typename T>
+// fine vertices with CW = 32 - 2 NU - 1 (29 for V(1,1), 27 for V(2,2), 25 for
+// V(3,3)) and CH = SH / 2 - 2 NU - 1 for a window of SH rows.  NU is chosen per
+// level by the solver (sweeps of the level's cycle), mg_nu<T>() by default.
+template <typename T, int NU_ = mg_nu<T>()>
 struct MGGeom {
-    static constexpr int NU = mg_nu<T>();
+    static_assert(NU_ >= 1 && NU_ <= 3, "sweeps per side");
+    static constexpr int NU = NU_;
     static constexpr int OD = 2 * NU + 2;            // mg_down window origin: 2 I0 - OD
     static constexpr int OU = 2 * NU;                // mg_up window origin: 2 I0 - OU
     static constexpr int CW = MG_SW / 2 - 2 * NU - 1;
@@ -277,12 +279,12 @@ __device__ __forceinline__ T tile_red_residual(const TileBlock<T> &t, unsigned u
     return ((unk >> e) & 1) ? rv : T(0);
 }
 
-template <typename T, int SH = MG_SH>
+template <typename T, int SH = MG_SH, int NU = mg_nu<T>()>
 __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<SH>::BPS : MGTile<SH>::BPS / 2) mg_down_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ zpre, int n, T *__restrict__ bc, int tiles_x, const int *__restrict__ act) {
     using G = MGTile<SH>;
-    using GM = MGGeom<T>;
+    using GM = MGGeom<T, NU>;
     constexpr int MG_SH = SH, MG_NW = G::NW, MG_CH = GM::ch(SH), MG_CW = GM::CW, MG_OD = GM::OD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xz = reinterpret_cast<T *>(smem_raw);
@@ -313,7 +315,8 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     tile_exchange<T, MG_NW>(t, xz, 0, lane, warp);
     tile_half_sweep<T, 1>(t);
     tile_exchange<T, MG_NW>(t, xz, 1, lane, warp);
-    if constexpr (GM::NU == 2) {   // the second sweep: red, black
+#pragma unroll
+    for (int k = 1; k < NU; ++k) {   // the further sweeps: red, black
         tile_half_sweep<T, 0>(t);
         tile_exchange<T, MG_NW>(t, xz, 0, lane, warp);
         tile_half_sweep<T, 1>(t);
@@ -354,13 +357,13 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     }
 }
 
-template <typename T, int SH = MG_SH>
+template <typename T, int SH = MG_SH, int NU = mg_nu<T>()>
 __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<SH>::BPS : MGTile<SH>::BPS / 2) mg_up_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     const T *__restrict__ zpre, T *__restrict__ z, int n, const T *__restrict__ zc, int tiles_x,
     const int *__restrict__ act, double *__restrict__ part_rz, int nblk) {
     using G = MGTile<SH>;
-    using GM = MGGeom<T>;
+    using GM = MGGeom<T, NU>;
     constexpr int MG_SH = SH, MG_NW = G::NW, MG_CH = GM::ch(SH), MG_CCH = G::CCH;
     constexpr int MG_CW = GM::CW, MG_OU = GM::OU;
     constexpr int MG_THREADS = G::THREADS;
@@ -430,7 +433,8 @@ __global__ void __launch_bounds__(MGTile<SH>::THREADS, sizeof(T) == 4 ? MGTile<S
     tile_half_sweep<T, 1>(t);
     tile_exchange<T, MG_NW>(t, xz, 1, lane, warp);
     tile_half_sweep<T, 0>(t);
-    if constexpr (GM::NU == 2) {   // the second sweep: black, red
+#pragma unroll
+    for (int k = 1; k < NU; ++k) {   // the further sweeps: black, red
         tile_exchange<T, MG_NW>(t, xz, 0, lane, warp);
         tile_half_sweep<T, 1>(t);
         tile_exchange<T, MG_NW>(t, xz, 1, lane, warp);
@@ -462,12 +466,14 @@ struct TailPtrs {
     void *cx[8], *cy[8];
 };
 
-// V-cycle of levels NT_N, NT_N/2, ..., 2 of one sample per block.
+// V-cycle of levels NT_N, NT_N/2, ..., 2 of one sample per block: nu0 sweeps
+// per side on level NT_N, nuc on the levels below.
 template <typename T, int NT_N, int NTHR>
 __global__ void __launch_bounds__(NTHR) mg_tail_kernel(TailPtrs tp, const T *__restrict__ b,
                                                        T *__restrict__ z,
                                                        const int *__restrict__ act,
-                                                       double *__restrict__ part_rz) {
+                                                       double *__restrict__ part_rz, int nu0,
+                                                       int nuc) {
     using Lay = MGPackedLayout<NT_N>;
     constexpr int NL = mg_levels(NT_N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(NTHR) mg_tail_kernel(TailPtrs tp, const T *__r
     T *b0 = base + Lay::off(0, 2), *z0 = base + Lay::off(0, 3);
     for (int v = threadIdx.x; v < V0; v += NTHR) b0[v] = bs[v];
     __syncthreads();
-    block_vcycle<T, NT_N, NTHR, Lay>(base);
+    block_vcycle<T, NT_N, NTHR, Lay>(base, nu0, nuc);
     T *zs = z + (long long)s * V0;
     T rz = T(0);
     for (int v = threadIdx.x; v < V0; v += NTHR) {

@@ -1,5 +1,6 @@
-// One multigrid V(MG_NU, MG_NU) cycle of a whole n = 64 grid and of the
-// levels below it, one sample per thread block.
+// One multigrid V-cycle of a whole n = 64 grid and of the levels below it, one
+// sample per thread block: NUT sweeps per side on the n = 64 level, NUS on each
+// level below it.
 //
 // The 65 x 65 fine grid has 63 unknown columns (1..63) between its two
 // Dirichlet columns, so its columns 0..63 fit one 64-wide register window
@@ -11,17 +12,17 @@
 // and 1/diag = 0, as in the tiles.
 //
 //   load b, cx, cy of the level and the conductances of levels 32..2
-//   pre-smoothing from z = 0 (MG_NU sweeps: red, then black), red residuals, full-weighting
+//   pre-smoothing from z = 0 (NUT sweeps: red, then black), red residuals, full-weighting
 //   restriction into the b of level 32 in shared memory
-//   V-cycle of levels 32..2 in shared memory (block_vcycle)
-//   bilinear prolongation of the level-32 correction, post-smoothing (MG_NU
+//   V-cycle of levels 32..2 in shared memory (block_vcycle, NUS sweeps per side)
+//   bilinear prolongation of the level-32 correction, post-smoothing (NUT
 //   sweeps: black, then red), z of the level to global memory, optionally the block's
 //   partial sum of b . z (CG's beta when the level is the finest)
 //
 // The arithmetic per vertex is that of mg_down / mg_tail / mg_up, so this is
-// the same symmetric V(MG_NU, MG_NU) cycle; it replaces their three launches on this
-// level by one and the 2.8-fold window overlap of 64 x 32 tiles on a 65 x 65
-// grid by none.
+// the same symmetric cycle; it replaces their three launches on this level by
+// one and the 2.8-fold window overlap of 64 x 32 tiles on a 65 x 65 grid by
+// none.
 #pragma once
 
 #include "mg_tiles.cuh"
@@ -42,7 +43,9 @@ constexpr size_t v64_smem_bytes() {
 // tp.cx[i], tp.cy[i]: conductances of level 32 >> i (i = 0..4), per sample
 // contiguous.  part_rz: one slot per sample, or NULL.  WARP_N > 0: the levels
 // of at most WARP_N cells run on warp 0 alone (see block_vcycle_from).
-template <typename T, int WARP_N = 0>
+// NUT: sweeps per side on the n = 64 level, NUS on the levels 32..2 in shared
+// memory.
+template <typename T, int WARP_N = 0, int NUT = mg_nu<T>(), int NUS = mg_nu<T>()>
 __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ z, TailPtrs tp, const int *__restrict__ act, double *__restrict__ part_rz) {
@@ -104,7 +107,8 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     tile_exchange<T, V64_NW>(t, xz, 0, lane, warp);
     tile_half_sweep<T, 1, 0, true>(t);
     tile_exchange<T, V64_NW>(t, xz, 1, lane, warp);
-    if constexpr (mg_nu<T>() == 2) {   // the second sweep: red, black
+#pragma unroll
+    for (int k = 1; k < NUT; ++k) {   // the further sweeps: red, black
         tile_half_sweep<T, 0, 0, true>(t);
         tile_exchange<T, V64_NW>(t, xz, 0, lane, warp);
         tile_half_sweep<T, 1, 0, true>(t);
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     if (threadIdx.x <= NC) bc[threadIdx.x * WC + NC] = T(0);   // Dirichlet column I = 32
 
     // levels 32..2 (block_vcycle zeroes z of level 32 and synchronises first)
-    block_vcycle<T, NC, V64_THREADS, V64Lay, WARP_N>(base);
+    block_vcycle<T, NC, V64_THREADS, V64Lay, WARP_N, NUS>(base);
 
     // z += P zc: coarse columns lane, lane + 1 and rows 2 warp + {0, 1, 2}
     // (rows beyond 32 only feed elements outside the grid: read as 0)
@@ -155,9 +159,9 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
         t.z[k] += pv;
     }
 
-    // post-smoothing: black, then red (MG_NU times)
+    // post-smoothing: black, then red (NUT times)
 #pragma unroll
-    for (int k = 0; k < mg_nu<T>(); ++k) {
+    for (int k = 0; k < NUT; ++k) {
         tile_exchange<T, V64_NW>(t, xz, 0, lane, warp);
         tile_half_sweep<T, 1, 0, true>(t);
         tile_exchange<T, V64_NW>(t, xz, 1, lane, warp);

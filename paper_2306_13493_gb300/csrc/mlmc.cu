@@ -77,12 +77,15 @@ static int level_run(const LevelArgs &a, const darcy_problem *p, uint64_t seed, 
     if (count == 0) return CE_OK;
     const int n = e->n, nc = n / 2;
     const bool coarse = a.level > 0;
-    // nested iteration: on levels with a coarse grid whose fine solve is the
-    // batched solver, the coarse solve runs first and its prolonged solution
-    // is the fine solve's first iterate (SCE_NESTED=0: both start from the
-    // lifting, the coarse solve on a second stream)
+    // nested iteration: on levels with a coarse grid the coarse solve runs
+    // first and its prolonged solution is the fine solve's first iterate
+    // (SCE_NESTED=0: both start from the lifting, the coarse solve on a second
+    // stream; SCE_NESTED_SMALL=0: only where the fine solve is the batched
+    // solver, not the one-block solver of the small grids)
     const bool fine_batched = !(p->precision == 32 && n <= sce_small_max_n() && n <= 64);
-    bool nested = coarse && fine_batched;
+    bool nested = coarse;
+    if (!fine_batched)
+        if (const char *ev = getenv("SCE_NESTED_SMALL")) nested = nested && atoi(ev) != 0;
     if (const char *ev = getenv("SCE_NESTED")) nested = nested && atoi(ev) != 0;
     const bool split = coarse && stc != st && !nested;
     const size_t es = p->precision == 64 ? sizeof(double) : sizeof(float);

@@ -55,7 +55,8 @@ const char *kNames[KP_COUNT_] = {
     "mg_coarsest", "cg_spmv_dot", "cg_axpy", "cg_dot", "cg_pupdate", "cg_copy", "reduce",
     "ir_residual", "ir_update", "qoi", "setup", "normals", "level_sums", "darcy_small", "mg_down", "mg_up", "mg_tail",
     "ce3_x", "ce3_y", "ce3_z", "cond3", "mg3_smooth", "mg3_resid", "mg3_restrict", "mg3_prolong",
-    "cg3_spmv_dot", "cg3_vec", "ir3", "mg_v64", "ce_levels", "coarsen_tail"};
+    "cg3_spmv_dot", "cg3_vec", "ir3", "mg_v64", "ce_levels", "coarsen_tail", "mg_down3",
+    "mg_up3"};
 }  // namespace
 
 bool sce_prof_on() { return g_on; }

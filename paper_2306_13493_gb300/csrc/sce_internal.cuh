@@ -88,7 +88,8 @@ enum SceKernel {
     KP_SETUP, KP_NORMALS, KP_LEVEL, KP_SMALL, KP_MG_DOWN, KP_MG_UP, KP_MG_TAIL,
     // three-dimensional path
     KP_X3, KP_Y3, KP_Z3, KP_COND3, KP_SMOOTH3, KP_RESID3, KP_RESTRICT3, KP_PROLONG3, KP_SPMV3,
-    KP_VEC3, KP_OUTER3, KP_MG_V64, KP_LEVELS, KP_COARSEN_TAIL, KP_COUNT_
+    KP_VEC3, KP_OUTER3, KP_MG_V64, KP_LEVELS, KP_COARSEN_TAIL, KP_MG_DOWN3, KP_MG_UP3,
+    KP_COUNT_
 };
 
 bool sce_prof_on();
@@ -144,11 +145,15 @@ int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
 double sce_inner_rel_f32();
 
 // One-block-per-sample solver for small grids (mixed precision).  qmask bit 3:
-// u_out holds float-float pairs (float2) instead of doubles.
+// u_out holds float-float pairs (float2) instead of doubles.  u_init: NULL, or
+// the solutions of the samples on the n/2 grid ((n/2+1)^2 per sample; float2
+// pairs when u_init_ff, else doubles), prolonged bilinearly into the first
+// iterate; the stopping rule stays relative to the lifting's residual.
 int sce_small_max_n();
 int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
                     int *status, double *u_out, cudaStream_t st, int *max_iters_out,
-                    int *n_failed_out, int qmask);
+                    int *n_failed_out, int qmask, const void *u_init = nullptr,
+                    bool u_init_ff = false);
 
 // Darcy solver entry used by mlmc_level_estimate.  max_iters_out, if not
 // NULL, points at int[2]: {max iterations over the samples, total iterations}.

@@ -176,6 +176,42 @@ def test_batched_level_estimate_matches_oracle(sce, level, finest, nested, preci
     assert abs(out.sumY2 - (Yg * Yg).sum()) < 1e-12 * max(1.0, out.sumY2)
 
 
+# Level 1 of the oscillatory workload (n = 32 fine, 16 coarse): both solves
+# run in the one-block solver; by default the fine one starts from the
+# prolonged coarse solution (SCE_NESTED_SMALL=0: from the lifting).
+def test_small_grid_level_estimate_nested_matches_oracle(sce, monkeypatch):
+    """Algorithm 2 step 4 and Eq. (3.5) on the one-block path of the small
+    levels: per-sample Y against the oracle at 1e-5, and the nested start never
+    needs more CG iterations in total than the start from the lifting."""
+    import torch
+    import workloads
+    w = workloads.OSCILLATORY
+    level = 1
+    n = w.n0 << level
+    oe = oem.setup_embedding(ocv.MATERN, w.nu, w.lam, w.sigma2, n, oem.PAD_SMOOTH)
+    mf, mc = omlmc.default_masks(oe, True, False)
+    keep_f, keep_c = workloads.keep_counts(oe.P, False, True)
+    emb = sce.ce_setup_embedding(ocv.MATERN, w.nu, w.lam, w.sigma2, n, pad_mode=oem.PAD_SMOOTH,
+                                 keep_fine=keep_f, keep_coarse=keep_c)
+    count, first = 23, 7
+    outs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SCE_NESTED_SMALL", flag)
+        Y = torch.full((count,), float("nan"), dtype=torch.float64, device="cuda")
+        out, st = sce.mlmc_level_estimate(emb, w.seed, level, first, count, qoi_index=w.qoi,
+                                          f=w.f, rtol=1e-12, precision=32, Y=Y)
+        torch.cuda.synchronize()
+        assert st == 0 and out.N == count and out.n_failed == 0
+        outs[flag] = (out, Y.cpu().numpy())
+    emb.close()
+    (N, s1, s2, f1, f2), oY = omlmc.level_estimate(oe, mf, mc, w.seed, level, first, count,
+                                                   qoi_index=w.qoi, f=w.f, precision=32)
+    for out, Yg in outs.values():
+        assert np.max(np.abs(Yg - oY)) < 1e-5
+        assert abs(out.sumQf - f1) < 1e-5 * abs(f1)
+    assert outs["1"][0].total_iters <= outs["0"][0].total_iters
+
+
 @pytest.mark.parametrize("nested", [True, False])
 def test_estimate_levels_batched_levels_match_oracle(sce, nested, monkeypatch):
     """The all-levels call on levels 2 and 3 of the oscillatory workload

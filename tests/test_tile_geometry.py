@@ -60,7 +60,7 @@ def writes(n, sh, nu):
     return fine_down, fine_up, coarse
 
 
-@pytest.mark.parametrize("nu", [1, 2])
+@pytest.mark.parametrize("nu", [1, 2, 3])
 @pytest.mark.parametrize("sh", [16, 24, 32, 48, 64])
 @pytest.mark.parametrize("n", [128, 256])
 def test_every_vertex_written_once(nu, sh, n):
@@ -70,7 +70,7 @@ def test_every_vertex_written_once(nu, sh, n):
     assert np.all(coarse == 1)
 
 
-@pytest.mark.parametrize("nu", [1, 2])
+@pytest.mark.parametrize("nu", [1, 2, 3])
 @pytest.mark.parametrize("sh", [16, 24, 32, 48, 64])
 def test_coarse_window_reads_stay_in_the_buffer(nu, sh):
     """mg_up loads SH/2 coarse rows of CCW entries plus a zero row; lane x of
@@ -87,7 +87,7 @@ def test_coarse_window_reads_stay_in_the_buffer(nu, sh):
     assert (ou + 2 * cw - 1 + 1) // 2 < CCW - 1
 
 
-@pytest.mark.parametrize("nu", [1, 2])
+@pytest.mark.parametrize("nu", [1, 2, 3])
 @pytest.mark.parametrize("sh", [16, 24, 32, 48, 64])
 def test_owned_region_inside_the_valid_part_of_the_window(nu, sh):
     """Ring bookkeeping of a window with last index E (63 across, SH - 1 up).
