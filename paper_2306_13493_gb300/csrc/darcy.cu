@@ -1033,8 +1033,12 @@ struct Solver {
             const int nc1 = n[L] / 2 + 1;
             nu[L] = lnu(L);
             sh[L] = tile_height_for((int)sizeof(T), n[L]);
-            // three sweeps: windows of 48 rows at least (CH = SH / 2 - 7)
-            if (nu[L] == 3 && sh[L] < 48) sh[L] = 48;
+            // three sweeps: windows of 48 rows (CH = SH / 2 - 7), or 64 where the
+            // table or SCE_TILE_SH3=64 asks for them
+            if (nu[L] == 3) {
+                const char *e3 = getenv("SCE_TILE_SH3");
+                sh[L] = (sh[L] == 64 || (e3 && atoi(e3) == 64)) ? 64 : 48;
+            }
             const int ch = nu[L] == 3 ? MGGeom<T, 3>::ch(sh[L]) : MGGeom<T>::ch(sh[L]);
             const int cw = nu[L] == 3 ? MGGeom<T, 3>::CW : MGGeom<T>::CW;
             tiles_x[L] = (nc1 + cw - 1) / cw;
