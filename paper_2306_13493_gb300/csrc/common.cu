@@ -257,5 +257,5 @@ extern "C" int mlmc_tau_matern(double h, double J, double nu, double alpha, doub
 double sce_inner_rel_f32() {
     const char *e = getenv("SCE_INNER_REL");
     const double v = e ? atof(e) : 0.0;
-    return (v >= 1e-8 && v <= 1e-2) ? v : 1e-5;
+    return (v >= 1e-8 && v <= 1e-2) ? v : 2e-5;
 }

@@ -141,7 +141,7 @@ int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
 
 // Relative residual drop each inner FP32 PCG solve of the mixed path aims
 // for before the float-float refinement recomputes the residual
-// (SCE_INNER_REL, default 1e-5).
+// (SCE_INNER_REL, default 2e-5).
 double sce_inner_rel_f32();
 
 // One-block-per-sample solver for small grids (mixed precision).  qmask bit 3:
