@@ -53,7 +53,7 @@ __device__ __forceinline__ R bsum1(R v, R *sh, int &par) {
     return t;
 }
 
-template <int N, int NT>
+template <int N, int NT, int NU = 1>
 __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kernel(
     const float *__restrict__ kin, double f, double rtol2, double in_rel2, int maxit,
     double *__restrict__ qoi, int *__restrict__ iters_out, int *__restrict__ status_out,
@@ -112,11 +112,11 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
         return bsum1<NT>((double)acc, sh, pard);
     };
 
-    // one symmetric V(1,1) cycle: z[0] = M^-1 r (one sweep per side: every
-    // half-sweep of this solver is a block barrier, and V(2,2) measured slower
-    // here than the iterations it saves)
+    // one symmetric V(NU,NU) cycle: z[0] = M^-1 r (one sweep per side by
+    // default: every half-sweep of this solver is a block barrier, and V(2,2)
+    // measured slower here than the iterations it saves)
     static_assert(NL == mg_levels(N), "level count");
-    auto vcycle = [&]() { block_vcycle<float, N, NT, MG, 0, 1>(mg); };
+    auto vcycle = [&]() { block_vcycle<float, N, NT, MG, 0, NU>(mg); };
 
     // residual of the lifting in closed form: r0 = F + [i = 1] cx(0, j)
     double orr;
@@ -279,15 +279,15 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
     }
 }
 
-template <int N, int NT>
+template <int N, int NT, int NU = 1>
 int launch_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
                  int *status, double *u_out, int *misc, int qmask, const float2 *u0f,
                  const double *u0d, cudaStream_t st) {
     const size_t smem = SmallLayout<N>::bytes;
-    SCE_TRY(sce_raise_smem_limit((const void *)small_solve_kernel<N, NT>, smem));
+    SCE_TRY(sce_raise_smem_limit((const void *)small_solve_kernel<N, NT, NU>, smem));
     const double in_rel = sce_inner_rel_f32();
     SceProf pr(KP_SMALL, st, (double)count * SmallLayout<N>::V * (sizeof(float) + 0.0) + 24.0 * count);
-    small_solve_kernel<N, NT><<<count, NT, smem, st>>>(k, p->f, p->rtol * p->rtol, in_rel * in_rel,
+    small_solve_kernel<N, NT, NU><<<count, NT, smem, st>>>(k, p->f, p->rtol * p->rtol, in_rel * in_rel,
                                                        p->maxit > 0 ? p->maxit : 1000, qoi, iters,
                                                        status, u_out, misc, misc + 1, qmask,
                                                        u0f, u0d);
@@ -302,6 +302,13 @@ int launch_small(const darcy_problem *p, const float *k, int count, double *qoi,
 static int small16_threads() {
     const char *e = getenv("SCE_SMALL16_NT");
     return e && atoi(e) == 32 ? 32 : 64;
+}
+
+// Sweeps per side of the n = 16 solver's cycle (SCE_SMALL16_NU: 1 or 2; its
+// two-warp blocks make a barrier cheap).
+static int small16_nu() {
+    const char *e = getenv("SCE_SMALL16_NU");
+    return e && atoi(e) == 2 ? 2 : 1;
 }
 
 // Threads per block of the n = 32 solver (SCE_SMALL32_NT: 128 or 256).
@@ -332,6 +339,9 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
         case 8: SCE_SMALL(8, 64); break;
         case 16:
             if (small16_threads() == 32) SCE_SMALL(16, 32);
+            else if (small16_nu() == 2)
+                rc = launch_small<16, 64, 2>(p, k, count, qoi, iters, status, u_out, misc, qmask,
+                                             u0f, u0d, st);
             else SCE_SMALL(16, 64);
             break;
         case 32:

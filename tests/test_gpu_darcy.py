@@ -302,6 +302,26 @@ def test_tile_autotuner_picks_a_height(sce, monkeypatch):
         sce.darcy_autotune_tiles(64, 32)
 
 
+def test_small16_solver_sweeps(sce, monkeypatch):
+    """The n = 16 one-block solver with V(2,2) (SCE_SMALL16_NU=2) against its
+    V(1,1) default: both match the oracle's direct solves and agree to the
+    stopping tolerance; V(2,2) takes fewer CG iterations in total."""
+    n, count = 16, 24
+    k = _oracle_k(n, count, lam=0.02, seed=12, precision=32)
+    out = {}
+    for nu in ("1", "2"):
+        monkeypatch.setenv("SCE_SMALL16_NU", nu)
+        out[nu] = _solve(sce, k, 32, f=1.0)
+    monkeypatch.delenv("SCE_SMALL16_NU", raising=False)
+    for nu in ("1", "2"):
+        assert out[nu][0] == 0 and np.all(out[nu][3] == 0)
+        for i in range(0, count, 5):
+            u, _ = odarcy.solve(k[i].astype(np.float64), f=1.0)[:2]
+            assert np.max(np.abs(out[nu][4][i] - u)) < 1e-8
+    assert np.max(np.abs(out["1"][1] - out["2"][1])) < 10 * 1e-12 * max(1.0, np.max(np.abs(out["1"][1])))
+    assert out["2"][2].sum() < out["1"][2].sum(), (out["1"][2], out["2"][2])
+
+
 @pytest.mark.parametrize("n", [64, 128, 256, 512])
 def test_coarse_level_sweeps_same_solution_fewer_iterations(sce, n, monkeypatch):
     """Three sweeps per side on the coarse levels of at most 128 cells of a
