@@ -41,20 +41,31 @@ __device__ __forceinline__ void block_sync() {
 }
 constexpr int mg_vof(int n) { return (n + 1) * (n + 1); }
 
+// Row pitch of a level of n cells in a shared-memory hierarchy: n + 1, or
+// n + 2 with PAD on the levels of at least 32 cells.  With the odd pitch n + 1
+// every vertex of one colour sits at an address of one parity, so a warp's
+// red-black half-sweep reaches only half of the 32 banks (two accesses per
+// bank); the even pitch alternates the parity from row to row, and the rows
+// of one colour a warp covers fill all the banks.
+constexpr int mg_pitch(int n, bool pad) { return n + 1 + ((pad && n >= 32) ? 1 : 0); }
+
 // Array k (0 cx, 1 cy, 2 b, 3 z) of level L of an N-cell hierarchy, all levels
-// stored one after the other, each as [cx | cy | b | z].
-template <int N> struct MGPackedLayout {
+// stored one after the other, each as [cx | cy | b | z], rows of pitch(L)
+// values (the padding column is never read).
+template <int N, bool PAD = false> struct MGPackedLayout {
+    static constexpr int pitch(int L) { return mg_pitch(N >> L, PAD); }
+    static constexpr int size(int L) { return ((N >> L) + 1) * pitch(L); }
     static constexpr int off(int L, int k) {
         int o = 0;
-        for (int l = 0; l < L; ++l) o += 4 * mg_vof(N >> l);
-        return o + k * mg_vof(N >> L);
+        for (int l = 0; l < L; ++l) o += 4 * size(l);
+        return o + k * size(L);
     }
     static constexpr int total() { return off(mg_levels(N), 0); }
 };
 
-// One red-black half-sweep of colour c on level nL: vertex (i, j) with
-// (i + j) % 2 == c, 1 <= i <= nL-1.
-template <typename T, int nL, int NT>
+// One red-black half-sweep of colour c on level nL (row pitch PW): vertex
+// (i, j) with (i + j) % 2 == c, 1 <= i <= nL-1.
+template <typename T, int nL, int NT, int PW = nL + 1>
 __device__ __forceinline__ void block_half_sweep(const T *cx, const T *cy, const T *b, T *z,
                                                  int c) {
     constexpr int W = nL + 1;
@@ -62,7 +73,7 @@ __device__ __forceinline__ void block_half_sweep(const T *cx, const T *cy, const
     for (int k = threadIdx.x; k < W * HW; k += NT) {
         const int j = k / HW;
         const int i = 2 * (k - j * HW) + ((j + c) & 1);
-        if (i >= 1 && i <= nL - 1) smooth_at(cx, cy, b, z, i, j, nL);
+        if (i >= 1 && i <= nL - 1) smooth_at(cx, cy, b, z, i, j, nL, PW);
     }
 }
 
@@ -91,36 +102,38 @@ __device__ __forceinline__ void block_vcycle_level(T *base, int nu0, int nuc) {
     T *cx = base + Lay::off(L, 0), *cy = base + Lay::off(L, 1);
     T *b = base + Lay::off(L, 2), *z = base + Lay::off(L, 3);
     if constexpr (L == NL - 1) {
+        static_assert(Lay::pitch(L) == 3, "the coarsest level is dense");
         if (threadIdx.x == 0) coarsest_solve(cx, cy, b, z);
         block_sync<NT>();
     } else {
         constexpr int nc = nL / 2, wc = nc + 1, Vc = wc * wc, wL = nL + 1, VL = wL * wL;
+        constexpr int PL = Lay::pitch(L), PC = Lay::pitch(L + 1);
         T *bc = base + Lay::off(L + 1, 2), *zc = base + Lay::off(L + 1, 3);
         const int nu = L == 0 ? nu0 : nuc;
 #pragma unroll
         for (int k = 0; k < nu; ++k) {
-            block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
+            block_half_sweep<T, nL, NT, PL>(cx, cy, b, z, 0);
             block_sync<NT>();
-            block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
+            block_half_sweep<T, nL, NT, PL>(cx, cy, b, z, 1);
             block_sync<NT>();
         }
         for (int v = threadIdx.x; v < Vc; v += NT) {
-            const int J = v / wc, I = v - J * wc;
-            bc[v] = (I > 0 && I < nc) ? restrict_at(cx, cy, b, z, nL, I, J) : T(0);
-            zc[v] = T(0);
+            const int J = v / wc, I = v - J * wc, q = J * PC + I;
+            bc[q] = (I > 0 && I < nc) ? restrict_at(cx, cy, b, z, nL, I, J, PL) : T(0);
+            zc[q] = T(0);
         }
         block_sync<NT>();
         block_vcycle_from<T, N, NT, Lay, L + 1, WARP_N, NU>(base, nu0, nuc);
         for (int v = threadIdx.x; v < VL; v += NT) {
             const int j = v / wL, i = v - j * wL;
-            if (i > 0 && i < nL) z[v] += prolong_at(zc, nc, i, j);
+            if (i > 0 && i < nL) z[j * PL + i] += prolong_at(zc, nc, i, j, PC);
         }
         block_sync<NT>();
 #pragma unroll
         for (int k = 0; k < nu; ++k) {
-            block_half_sweep<T, nL, NT>(cx, cy, b, z, 1);
+            block_half_sweep<T, nL, NT, PL>(cx, cy, b, z, 1);
             block_sync<NT>();
-            block_half_sweep<T, nL, NT>(cx, cy, b, z, 0);
+            block_half_sweep<T, nL, NT, PL>(cx, cy, b, z, 0);
             block_sync<NT>();
         }
     }
@@ -131,14 +144,15 @@ template <typename T, int N, int NT, class Lay, int L>
 __device__ __forceinline__ void block_coarsen(T *base) {
     if constexpr (L < mg_levels(N)) {
         constexpr int nL = N >> L, wL = nL + 1, VL = wL * wL;
+        constexpr int PF = Lay::pitch(L - 1), PL = Lay::pitch(L);
         const T *fx = base + Lay::off(L - 1, 0), *fy = base + Lay::off(L - 1, 1);
         T *cx = base + Lay::off(L, 0), *cy = base + Lay::off(L, 1);
         for (int v = threadIdx.x; v < VL; v += NT) {
             const int J = v / wL, I = v - J * wL;
             T gx, gy;
-            coarsen_at(fx, fy, 2 * nL, I, J, &gx, &gy);
-            cx[v] = gx;
-            cy[v] = gy;
+            coarsen_at(fx, fy, 2 * nL, I, J, &gx, &gy, PF);
+            cx[J * PL + I] = gx;
+            cy[J * PL + I] = gy;
         }
         block_sync<NT>();
         block_coarsen<T, N, NT, Lay, L + 1>(base);
@@ -153,7 +167,7 @@ __device__ __forceinline__ void block_coarsen(T *base) {
 template <typename T, int N, int NT, class Lay, int WARP_N = 0, int NU = mg_nu<T>()>
 __device__ __forceinline__ void block_vcycle(T *base, int nu0 = NU, int nuc = NU) {
     T *z = base + Lay::off(0, 3);
-    for (int v = threadIdx.x; v < mg_vof(N); v += NT) z[v] = T(0);
+    for (int v = threadIdx.x; v < Lay::size(0); v += NT) z[v] = T(0);
     block_sync<NT>();
     block_vcycle_from<T, N, NT, Lay, 0, WARP_N, NU>(base, nu0, nuc);
 }

@@ -254,6 +254,11 @@ extern "C" int mlmc_tau_matern(double h, double J, double nu, double alpha, doub
     return CE_OK;
 }
 
+bool sce_smem_pad() {
+    const char *e = getenv("SCE_SMEM_PAD");
+    return !(e && atoi(e) == 0);
+}
+
 double sce_inner_rel_f32() {
     const char *e = getenv("SCE_INNER_REL");
     const double v = e ? atof(e) : 0.0;

@@ -1196,16 +1196,21 @@ struct Solver {
     }
 
     unsigned v64_attr_mask = 0;
-    template <int NUT, int NUS>
+    template <int NUT, int NUS, bool PAD>
     void v64_go(const TailPtrs &tp, double *pr_rz) {
-        constexpr size_t smem = v64_smem_bytes<T>();
-        constexpr unsigned bit = 1u << (NUT * 4 + NUS);
+        constexpr size_t smem = v64_smem_bytes<T, PAD>();
+        constexpr unsigned bit = 1u << (NUT * 4 + NUS + (PAD ? 16 : 0));
         if (!(v64_attr_mask & bit)) {   // outside any stream capture (the first cycle is not captured)
-            sce_raise_smem_limit((const void *)mg_v64_kernel<T, 0, NUT, NUS>, smem);
+            sce_raise_smem_limit((const void *)mg_v64_kernel<T, 0, NUT, NUS, PAD>, smem);
             v64_attr_mask |= bit;
         }
-        mg_v64_kernel<T, 0, NUT, NUS><<<count, V64_THREADS, smem, st>>>(
+        mg_v64_kernel<T, 0, NUT, NUS, PAD><<<count, V64_THREADS, smem, st>>>(
             cx[Lt], cy[Lt], b[Lt], z[Lt], tp, sc.act_in, pr_rz);
+    }
+    template <int NUT, int NUS>
+    void v64_go(const TailPtrs &tp, double *pr_rz) {
+        if (sce_smem_pad()) v64_go<NUT, NUS, true>(tp, pr_rz);
+        else v64_go<NUT, NUS, false>(tp, pr_rz);
     }
     void v64_launch(bool want_rz) {
         if constexpr (sizeof(T) == 4) {

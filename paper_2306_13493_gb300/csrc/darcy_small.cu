@@ -19,16 +19,21 @@ namespace {
 
 constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
 
-template <int N> struct SmallLayout {
+// Shared-memory layout of one sample: every level-0 array in rows of PW
+// values (N + 2 with PAD on grids of at least 32 cells, see mg_pitch), V
+// vertices, VP values per array.
+template <int N, bool PAD> struct SmallLayout {
+    using MG = MGPackedLayout<N, PAD>;
     static constexpr int W = N + 1;
+    static constexpr int PW = MG::pitch(0);
     static constexpr int V = W * W;
+    static constexpr int VP = W * PW;
     static constexpr int NL = ilog2c(N);            // levels N, N/2, ..., 2
-    static constexpr int vof(int L) { return ((N >> L) + 1) * ((N >> L) + 1); }
     // float2: u as float-float; doubles: reduction scratch (64); floats: the
     // multigrid hierarchy (level 0 holds the conductances' hi parts), their lo
     // parts, d, p
-    static constexpr size_t bytes = sizeof(float2) * (size_t)V + sizeof(double) * 64 +
-                                    sizeof(float) * (MGPackedLayout<N>::total() + 4 * (size_t)V);
+    static constexpr size_t bytes = sizeof(float2) * (size_t)VP + sizeof(double) * 64 +
+                                    sizeof(float) * (MG::total() + 4 * (size_t)VP);
 };
 
 // Sum over the block, returned to every thread (fixed order: warp trees,
@@ -53,42 +58,44 @@ __device__ __forceinline__ R bsum1(R v, R *sh, int &par) {
     return t;
 }
 
-template <int N, int NT, int NU = 1>
+template <int N, int NT, int NU = 1, bool PAD = false>
 __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kernel(
     const float *__restrict__ kin, double f, double rtol2, double in_rel2, int maxit,
     double *__restrict__ qoi, int *__restrict__ iters_out, int *__restrict__ status_out,
     double *__restrict__ u_out, int *__restrict__ nfail, int *__restrict__ maxits, int qmask,
     const float2 *__restrict__ u0f, const double *__restrict__ u0d) {
-    using Lay = SmallLayout<N>;
-    using MG = MGPackedLayout<N>;
-    constexpr int W = Lay::W, V = Lay::V, NL = Lay::NL;
+    using Lay = SmallLayout<N, PAD>;
+    using MG = typename Lay::MG;
+    constexpr int W = Lay::W, PW = Lay::PW, V = Lay::V, VP = Lay::VP, NL = Lay::NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *u = reinterpret_cast<float2 *>(smem_raw);
-    double *sh = reinterpret_cast<double *>(u + V);
+    double *sh = reinterpret_cast<double *>(u + VP);
     // FP32 region: the multigrid hierarchy (level 0 = [cx | cy | r | z]), then
     // the lo parts of the level-0 conductances, d, p
     float *mg = reinterpret_cast<float *>(sh + 64);
     float *cx0 = mg + MG::off(0, 0), *cy0 = mg + MG::off(0, 1);
     float *r = mg + MG::off(0, 2), *z = mg + MG::off(0, 3);
     float *cxl = mg + MG::total();
-    float *cyl = cxl + V;
-    float *d = cyl + V;
-    float *p = d + V;
+    float *cyl = cxl + VP;
+    float *d = cyl + VP;
+    float *p = d + VP;
     const int s = blockIdx.x;
     const int tid = threadIdx.x;
     const float *ks = kin + (size_t)s * V;
     int pard = 0, parf = 0;   // buffer parity of the FP64 and FP32 block sums
 
     // operator: float-float conductances, hi = the FP32 operator of the inner solve
+    // (v: the vertex in the dense layout of k and of the outputs; q: its slot
+    // in the shared-memory arrays of row pitch PW)
     for (int v = tid; v < V; v += NT) {
-        const int j = v / W, i = v - j * W;
+        const int j = v / W, i = v - j * W, q = j * PW + i;
         ff gx, gy;
         cond_at_ff(ks, i, j, N, &gx, &gy);
-        cx0[v] = gx.hi;
-        cy0[v] = gy.hi;
-        cxl[v] = gx.lo;
-        cyl[v] = gy.lo;
-        u[v] = make_float2(i == 0 ? 1.0f : 0.0f, 0.0f);
+        cx0[q] = gx.hi;
+        cy0[q] = gy.hi;
+        cxl[q] = gx.lo;
+        cyl[q] = gy.lo;
+        u[q] = make_float2(i == 0 ? 1.0f : 0.0f, 0.0f);
     }
     block_sync<NT>();
     block_coarsen<float, N, NT, MG, 1>(mg);
@@ -104,10 +111,11 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             const int j = v / W, i = v - j * W;
             float rv = 0.f;
             if (i > 0 && i < N) {
-                rv = resid_at_ff((j > 0 && j < N) ? Fv[1] : Fv[0], cx0, cxl, cy0, cyl, u, i, j, N);
+                rv = resid_at_ff((j > 0 && j < N) ? Fv[1] : Fv[0], cx0, cxl, cy0, cyl, u, i, j, N,
+                                 PW);
                 acc += rv * rv;
             }
-            r[v] = rv;
+            r[j * PW + i] = rv;
         }
         return bsum1<NT>((double)acc, sh, pard);
     };
@@ -123,15 +131,15 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
     {
         float acc = 0.f;
         for (int v = tid; v < V; v += NT) {
-            const int j = v / W, i = v - j * W;
+            const int j = v / W, i = v - j * W, q = j * PW + i;
             float rv = 0.f;
             if (i > 0 && i < N) {
                 ff rf = (j > 0 && j < N) ? Fv[1] : Fv[0];
-                if (i == 1) rf = ff_add(rf, ff{cx0[v - 1], cxl[v - 1]});
+                if (i == 1) rf = ff_add(rf, ff{cx0[q - 1], cxl[q - 1]});
                 rv = rf.hi;
                 acc += rv * rv;
             }
-            r[v] = rv;
+            r[q] = rv;
         }
         orr = bsum1<NT>((double)acc, sh, pard);
     }
@@ -164,7 +172,7 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
                 a = ff_add(a, b);
                 sc *= 0.5f;
             }
-            u[v] = make_float2(a.hi * sc, a.lo * sc);
+            u[j * PW + i] = make_float2(a.hi * sc, a.lo * sc);
         }
         block_sync<NT>();
         orr = outer_residual();
@@ -175,39 +183,41 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
         // inner CG on A d = r, entirely in FP32 (dot products included)
         float rr0 = 0.f;
         for (int v = tid; v < V; v += NT) {
-            d[v] = 0.f;
-            rr0 += r[v] * r[v];
+            const int j = v / W, q = j * PW + (v - j * W);
+            d[q] = 0.f;
+            rr0 += r[q] * r[q];
         }
         rr0 = bsum1<NT>(rr0, shf, parf);
         const float thr = (float)fmax(in_rel2 * (double)rr0, 0.0625 * rtol2 * orr0);
         vcycle();
         float rz = 0.f;
         for (int v = tid; v < V; v += NT) {
-            p[v] = z[v];
-            rz += r[v] * z[v];
+            const int j = v / W, q = j * PW + (v - j * W);
+            p[q] = z[q];
+            rz += r[q] * z[q];
         }
         rz = bsum1<NT>(rz, shf, parf);
         for (int it = 0; it < 40 && its < maxit; ++it) {
             // q = A p, kept in the multigrid z array (free until the next cycle)
             float pq = 0.f;
             for (int v = tid; v < V; v += NT) {
-                const int j = v / W, i = v - j * W;
+                const int j = v / W, i = v - j * W, q = j * PW + i;
                 if (i > 0 && i < N) {
-                    const float ap = apply_at(cx0, cy0, p, i, j, N);
-                    z[v] = ap;
-                    pq += p[v] * ap;
+                    const float ap = apply_at(cx0, cy0, p, i, j, N, PW);
+                    z[q] = ap;
+                    pq += p[q] * ap;
                 }
             }
             pq = bsum1<NT>(pq, shf, parf);
             const float alpha = pq > 0.f ? rz / pq : 0.f;
             float rr = 0.f;
             for (int v = tid; v < V; v += NT) {
-                const int j = v / W, i = v - j * W;
+                const int j = v / W, i = v - j * W, q = j * PW + i;
                 if (i > 0 && i < N) {
-                    const float ap = z[v];
-                    d[v] += alpha * p[v];
-                    const float rv = r[v] - alpha * ap;
-                    r[v] = rv;
+                    const float ap = z[q];
+                    d[q] += alpha * p[q];
+                    const float rv = r[q] - alpha * ap;
+                    r[q] = rv;
                     rr += rv * rv;
                 }
             }
@@ -216,16 +226,23 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
             if (rr <= thr) break;
             vcycle();
             float rzn = 0.f;
-            for (int v = tid; v < V; v += NT) rzn += r[v] * z[v];
+            for (int v = tid; v < V; v += NT) {
+                const int j = v / W, q = j * PW + (v - j * W);
+                rzn += r[q] * z[q];
+            }
             rzn = bsum1<NT>(rzn, shf, parf);
             const float beta = rz > 0.f ? rzn / rz : 0.f;
             rz = rzn;
-            for (int v = tid; v < V; v += NT) p[v] = z[v] + beta * p[v];
+            for (int v = tid; v < V; v += NT) {
+                const int j = v / W, q = j * PW + (v - j * W);
+                p[q] = z[q] + beta * p[q];
+            }
             block_sync<NT>();
         }
         for (int v = tid; v < V; v += NT) {
-            const ff t = ff_add_f(ff{u[v].x, u[v].y}, d[v]);
-            u[v] = make_float2(t.hi, t.lo);
+            const int j = v / W, q = j * PW + (v - j * W);
+            const ff t = ff_add_f(ff{u[q].x, u[q].y}, d[q]);
+            u[q] = make_float2(t.hi, t.lo);
         }
         block_sync<NT>();
         orr = outer_residual();
@@ -238,16 +255,16 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
     auto ud = [&](int q) { return (double)u[q].x + (double)u[q].y; };
     if (want_out || want_l2 || u_out) {
         for (int v = tid; v < V; v += NT) {
-            const int j = v / W, i = v - j * W;
-            if (want_out && i == N - 1) qo += ((double)cx0[v] + (double)cxl[v]) * ud(v);
+            const int j = v / W, i = v - j * W, q = j * PW + i;
+            if (want_out && i == N - 1) qo += ((double)cx0[q] + (double)cxl[q]) * ud(q);
             if (want_l2 && i < N && j < N) {
-                const double a = ud(v), b = ud(v + 1), c = ud(v + W + 1), e = ud(v + W);
+                const double a = ud(q), b = ud(q + 1), c = ud(q + PW + 1), e = ud(q + PW);
                 const double s1 = a + b + c, s2 = a + e + c;
                 l2 += s1 * s1 + a * a + b * b + c * c + s2 * s2 + a * a + e * e + c * c;
             }
             if (u_out) {
-                if (qmask & 8) reinterpret_cast<float2 *>(u_out)[(size_t)s * V + v] = u[v];
-                else u_out[(size_t)s * V + v] = ud(v);
+                if (qmask & 8) reinterpret_cast<float2 *>(u_out)[(size_t)s * V + v] = u[q];
+                else u_out[(size_t)s * V + v] = ud(q);
             }
         }
         qo = bsum1<NT>(qo, sh, pard);
@@ -260,8 +277,8 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
         const double xs = 7.0 / 15.0 * (double)N, ys = 7.0 / 15.0 * (double)N;
         const int ca = min((int)floor(xs), N - 1), cb = min((int)floor(ys), N - 1);
         const double xi = xs - ca, et = ys - cb;
-        const double uab = ud(cb * W + ca), ua1b = ud(cb * W + ca + 1);
-        const double uab1 = ud((cb + 1) * W + ca), ua1b1 = ud((cb + 1) * W + ca + 1);
+        const double uab = ud(cb * PW + ca), ua1b = ud(cb * PW + ca + 1);
+        const double uab1 = ud((cb + 1) * PW + ca), ua1b1 = ud((cb + 1) * PW + ca + 1);
         const double q_pt = !(qmask & 2) ? 0.0
                             : xi >= et ? uab + xi * (ua1b - uab) + et * (ua1b1 - ua1b)
                                        : uab + et * (uab1 - uab) + xi * (ua1b1 - uab1);
@@ -279,18 +296,18 @@ __global__ void __launch_bounds__(NT, N >= 16 ? 1024 / NT : 1) small_solve_kerne
     }
 }
 
-template <int N, int NT, int NU = 1>
+template <int N, int NT, int NU = 1, bool PAD = false>
 int launch_small(const darcy_problem *p, const float *k, int count, double *qoi, int *iters,
                  int *status, double *u_out, int *misc, int qmask, const float2 *u0f,
                  const double *u0d, cudaStream_t st) {
-    const size_t smem = SmallLayout<N>::bytes;
-    SCE_TRY(sce_raise_smem_limit((const void *)small_solve_kernel<N, NT, NU>, smem));
+    using Lay = SmallLayout<N, PAD>;
+    const size_t smem = Lay::bytes;
+    SCE_TRY(sce_raise_smem_limit((const void *)small_solve_kernel<N, NT, NU, PAD>, smem));
     const double in_rel = sce_inner_rel_f32();
-    SceProf pr(KP_SMALL, st, (double)count * SmallLayout<N>::V * (sizeof(float) + 0.0) + 24.0 * count);
-    small_solve_kernel<N, NT, NU><<<count, NT, smem, st>>>(k, p->f, p->rtol * p->rtol, in_rel * in_rel,
-                                                       p->maxit > 0 ? p->maxit : 1000, qoi, iters,
-                                                       status, u_out, misc, misc + 1, qmask,
-                                                       u0f, u0d);
+    SceProf pr(KP_SMALL, st, (double)count * Lay::V * (sizeof(float) + 0.0) + 24.0 * count);
+    small_solve_kernel<N, NT, NU, PAD><<<count, NT, smem, st>>>(
+        k, p->f, p->rtol * p->rtol, in_rel * in_rel, p->maxit > 0 ? p->maxit : 1000, qoi, iters,
+        status, u_out, misc, misc + 1, qmask, u0f, u0d);
     SCE_CUDA(cudaGetLastError());
     return CE_OK;
 }
@@ -346,9 +363,17 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
             break;
         case 32:
             if (small32_threads() == 128) SCE_SMALL(32, 128);
+            else if (sce_smem_pad())
+                rc = launch_small<32, 256, 1, true>(p, k, count, qoi, iters, status, u_out, misc,
+                                                    qmask, u0f, u0d, st);
             else SCE_SMALL(32, 256);
             break;
-        case 64: SCE_SMALL(64, 512); break;
+        case 64:
+            if (sce_smem_pad())
+                rc = launch_small<64, 512, 1, true>(p, k, count, qoi, iters, status, u_out, misc,
+                                                    qmask, u0f, u0d, st);
+            else SCE_SMALL(64, 512);
+            break;
         default: break;
     }
 #undef SCE_SMALL

@@ -32,11 +32,13 @@ namespace sce {
 constexpr int V64_N = 64;
 constexpr int V64_NW = 17;                      // 68 rows >= 65
 constexpr int V64_THREADS = 32 * V64_NW;        // 544
-using V64Lay = MGPackedLayout<V64_N / 2>;       // levels 32..2 in shared memory
+// levels 32..2 in shared memory (PAD: level 32 in rows of 34, see mg_pitch)
+template <bool PAD>
+using V64Lay = MGPackedLayout<V64_N / 2, PAD>;
 
-template <typename T>
+template <typename T, bool PAD = false>
 constexpr size_t v64_smem_bytes() {
-    return sizeof(T) * ((size_t)V64Lay::total() + 2 * 2 * V64_NW * (size_t)MG_SW +
+    return sizeof(T) * ((size_t)V64Lay<PAD>::total() + 2 * 2 * V64_NW * (size_t)MG_SW +
                         V64_NW * (size_t)MG_SW + 32 + tile_inv_slots(V64_NW));
 }
 
@@ -44,17 +46,19 @@ constexpr size_t v64_smem_bytes() {
 // contiguous.  part_rz: one slot per sample, or NULL.  WARP_N > 0: the levels
 // of at most WARP_N cells run on warp 0 alone (see block_vcycle_from).
 // NUT: sweeps per side on the n = 64 level, NUS on the levels 32..2 in shared
-// memory.
-template <typename T, int WARP_N = 0, int NUT = mg_nu<T>(), int NUS = mg_nu<T>()>
+// memory; PAD: their layout.
+template <typename T, int WARP_N = 0, int NUT = mg_nu<T>(), int NUS = mg_nu<T>(),
+          bool PAD = false>
 __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     const T *__restrict__ cx, const T *__restrict__ cy, const T *__restrict__ b,
     T *__restrict__ z, TailPtrs tp, const int *__restrict__ act, double *__restrict__ part_rz) {
-    constexpr int NC = V64_N / 2, W = V64_N + 1, WC = NC + 1;
+    using Lay = V64Lay<PAD>;
+    constexpr int NC = V64_N / 2, W = V64_N + 1, PC = Lay::pitch(0);   // PC: level 32's row pitch
     constexpr int V = W * W;
     constexpr int NL = mg_levels(NC);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *base = reinterpret_cast<T *>(smem_raw);
-    T *xz = base + V64Lay::total();
+    T *xz = base + Lay::total();
     T *xrow = xz + 2 * 2 * V64_NW * MG_SW;
     T *sred = xrow + V64_NW * MG_SW;
     T *sinv = sred + 32;   // the threads' 1/diag slices
@@ -65,13 +69,14 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     // conductances of the coarse levels (read by block_vcycle after the barriers below)
 #pragma unroll
     for (int L = 0; L < NL; ++L) {
-        const int VL = mg_vof(NC >> L);
-        T *sx = base + V64Lay::off(L, 0), *sy = base + V64Lay::off(L, 1);
+        const int VL = mg_vof(NC >> L), wl = (NC >> L) + 1, pl = Lay::pitch(L);
+        T *sx = base + Lay::off(L, 0), *sy = base + Lay::off(L, 1);
         const T *gx = reinterpret_cast<const T *>(tp.cx[L]) + (long long)s * VL;
         const T *gy = reinterpret_cast<const T *>(tp.cy[L]) + (long long)s * VL;
         for (int v = threadIdx.x; v < VL; v += V64_THREADS) {
-            sx[v] = gx[v];
-            sy[v] = gy[v];
+            const int J = v / wl, q = J * pl + (v - J * wl);
+            sx[q] = gx[v];
+            sy[q] = gy[v];
         }
     }
 
@@ -126,26 +131,26 @@ __global__ void __launch_bounds__(V64_THREADS, 2) mg_v64_kernel(
     const T l1 = __shfl_up_sync(MG_FULL, r1, 1), l3 = __shfl_up_sync(MG_FULL, r3, 1);
     const T lm = __shfl_up_sync(MG_FULL, rm, 1);
     const T acc[2] = {T(0.25) * (lm + rm + l1 + r1) + r0, T(0.25) * (l1 + r1 + l3 + r3) + r2};
-    T *bc = base + V64Lay::off(0, 2);
+    T *bc = base + Lay::off(0, 2);
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int J = 2 * warp + k;
-        if (J <= NC) bc[J * WC + lane] = lane > 0 ? acc[k] : T(0);
+        if (J <= NC) bc[J * PC + lane] = lane > 0 ? acc[k] : T(0);
     }
-    if (threadIdx.x <= NC) bc[threadIdx.x * WC + NC] = T(0);   // Dirichlet column I = 32
+    if (threadIdx.x <= NC) bc[threadIdx.x * PC + NC] = T(0);   // Dirichlet column I = 32
 
     // levels 32..2 (block_vcycle zeroes z of level 32 and synchronises first)
-    block_vcycle<T, NC, V64_THREADS, V64Lay, WARP_N, NUS>(base);
+    block_vcycle<T, NC, V64_THREADS, Lay, WARP_N, NUS>(base);
 
     // z += P zc: coarse columns lane, lane + 1 and rows 2 warp + {0, 1, 2}
     // (rows beyond 32 only feed elements outside the grid: read as 0)
-    const T *zc = base + V64Lay::off(0, 3);
+    const T *zc = base + Lay::off(0, 3);
     const int J0 = 2 * warp;
-    const T a0 = zc[J0 * WC + lane], a1 = zc[J0 * WC + lane + 1];
-    const T b0 = J0 + 1 <= NC ? zc[(J0 + 1) * WC + lane] : T(0);
-    const T b1 = J0 + 1 <= NC ? zc[(J0 + 1) * WC + lane + 1] : T(0);
-    const T c0 = J0 + 2 <= NC ? zc[(J0 + 2) * WC + lane] : T(0);
-    const T c1 = J0 + 2 <= NC ? zc[(J0 + 2) * WC + lane + 1] : T(0);
+    const T a0 = zc[J0 * PC + lane], a1 = zc[J0 * PC + lane + 1];
+    const T b0 = J0 + 1 <= NC ? zc[(J0 + 1) * PC + lane] : T(0);
+    const T b1 = J0 + 1 <= NC ? zc[(J0 + 1) * PC + lane + 1] : T(0);
+    const T c0 = J0 + 2 <= NC ? zc[(J0 + 2) * PC + lane] : T(0);
+    const T c1 = J0 + 2 <= NC ? zc[(J0 + 2) * PC + lane + 1] : T(0);
     const T h = T(0.5), qq = T(0.25);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {

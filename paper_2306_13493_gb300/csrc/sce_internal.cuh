@@ -144,6 +144,10 @@ int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
 // (SCE_INNER_REL, default 2e-5).
 double sce_inner_rel_f32();
 
+// Padded rows (pitch n + 2) for the shared-memory levels of at least 32 cells
+// in the one-block solvers and the fused n = 64 cycle (SCE_SMEM_PAD=0: n + 1).
+bool sce_smem_pad();
+
 // One-block-per-sample solver for small grids (mixed precision).  qmask bit 3:
 // u_out holds float-float pairs (float2) instead of doubles.  u_init: NULL, or
 // the solutions of the samples on the n/2 grid ((n/2+1)^2 per sample; float2

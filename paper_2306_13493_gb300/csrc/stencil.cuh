@@ -1,7 +1,9 @@
 // Per-vertex pieces of the five-point P1 operator and of the multigrid cycle,
 // shared by the grid-wide batched kernels and the one-block-per-sample solver.
 // All functions take the base pointer of one sample's array on an n-cell grid
-// (row-major, x-fastest, width n+1); they work on global or shared memory.
+// (row-major, x-fastest, n+1 vertices per row); they work on global or shared
+// memory.  w (or wf / wc for the fine / coarse grid): the arrays' row pitch,
+// 0 for the dense layout (n + 1); padded shared-memory levels pass n + 2.
 #pragma once
 
 #include "ff.cuh"
@@ -88,8 +90,9 @@ __device__ __forceinline__ void cond_at_ff(const float *ks, int i, int j, int n,
 // float-float subtractions, products and sums.
 __device__ __forceinline__ float resid_at_ff(ff F, const float *cx, const float *cxl,
                                              const float *cy, const float *cyl, const float2 *u,
-                                             int i, int j, int n) {
-    const int w = n + 1, v = j * w + i;
+                                             int i, int j, int n, int w = 0) {
+    if (w <= 0) w = n + 1;
+    const int v = j * w + i;
     const float2 uc = u[v];
     float p = F.hi, sig = F.lo;
     auto edge = [&](float ch, float cl, float2 un) {
@@ -125,8 +128,9 @@ __device__ __forceinline__ T series_cond(T a, T b) {
 // Computed in the working precision T of the hierarchy.
 template <typename T>
 __device__ __forceinline__ void coarsen_at(const T *ax, const T *ay, int nf, int I, int J, T *gx,
-                                           T *gy) {
-    const int nc = nf / 2, wf = nf + 1;
+                                           T *gy, int wf = 0) {
+    const int nc = nf / 2;
+    if (wf <= 0) wf = nf + 1;
     T x = T(0), y = T(0);
     if (I < nc) {
         auto S = [&](int j) { return series_cond(ax[j * wf + 2 * I], ax[j * wf + 2 * I + 1]); };
@@ -146,8 +150,10 @@ __device__ __forceinline__ void coarsen_at(const T *ax, const T *ay, int nf, int
 
 // (A p)(i,j) at an unknown vertex (1 <= i <= n-1).
 template <typename T>
-__device__ __forceinline__ T apply_at(const T *ax, const T *ay, const T *p, int i, int j, int n) {
-    const int w = n + 1, v = j * w + i;
+__device__ __forceinline__ T apply_at(const T *ax, const T *ay, const T *p, int i, int j, int n,
+                                      int w = 0) {
+    if (w <= 0) w = n + 1;
+    const int v = j * w + i;
     const T pc = p[v];
     T a = ax[v - 1] * (pc - p[v - 1]) + ax[v] * (pc - p[v + 1]);
     if (j > 0) a += ay[v - w] * (pc - p[v - w]);
@@ -158,8 +164,9 @@ __device__ __forceinline__ T apply_at(const T *ax, const T *ay, const T *p, int 
 // b - A z at an unknown vertex.
 template <typename T>
 __device__ __forceinline__ T resid_at(const T *ax, const T *ay, const T *b, const T *z, int i,
-                                      int j, int n) {
-    return b[j * (n + 1) + i] - apply_at(ax, ay, z, i, j, n);
+                                      int j, int n, int w = 0) {
+    if (w <= 0) w = n + 1;
+    return b[j * w + i] - apply_at(ax, ay, z, i, j, n, w);
 }
 
 // Division in the smoothers: the fast single-precision form in FP32 (a
@@ -171,8 +178,9 @@ __device__ __forceinline__ double smooth_div(double a, double b) { return a / b;
 // Gauss-Seidel update of one unknown vertex.
 template <typename T>
 __device__ __forceinline__ void smooth_at(const T *ax, const T *ay, const T *b, T *z, int i, int j,
-                                          int n) {
-    const int w = n + 1, v = j * w + i;
+                                          int n, int w = 0) {
+    if (w <= 0) w = n + 1;
+    const int v = j * w + i;
     const T cw = ax[v - 1], ce = ax[v];
     const T cs = j > 0 ? ay[v - w] : T(0), cn = j < n ? ay[v] : T(0);
     T acc = b[v] + cw * z[v - 1] + ce * z[v + 1];
@@ -189,21 +197,22 @@ __device__ __forceinline__ void smooth_at(const T *ax, const T *ay, const T *b, 
 // diagonal neighbours (weight 1/4), as in the tiled kernels.
 template <typename T>
 __device__ __forceinline__ T restrict_at(const T *ax, const T *ay, const T *b, const T *z, int nf,
-                                         int I, int J) {
-    T acc = resid_at(ax, ay, b, z, 2 * I, 2 * J, nf);
+                                         int I, int J, int wf = 0) {
+    T acc = resid_at(ax, ay, b, z, 2 * I, 2 * J, nf, wf);
     T d = T(0);
     for (int dj = -1; dj <= 1; dj += 2) {
         const int j = 2 * J + dj;
         if (j < 0 || j > nf) continue;
-        d += resid_at(ax, ay, b, z, 2 * I - 1, j, nf) + resid_at(ax, ay, b, z, 2 * I + 1, j, nf);
+        d += resid_at(ax, ay, b, z, 2 * I - 1, j, nf, wf) +
+             resid_at(ax, ay, b, z, 2 * I + 1, j, nf, wf);
     }
     return acc + T(0.25) * d;
 }
 
 // Bilinear prolongation of the coarse correction to fine vertex (i, j).
 template <typename T>
-__device__ __forceinline__ T prolong_at(const T *c, int nc, int i, int j) {
-    const int wc = nc + 1;
+__device__ __forceinline__ T prolong_at(const T *c, int nc, int i, int j, int wc = 0) {
+    if (wc <= 0) wc = nc + 1;
     const int I = i >> 1, J = j >> 1;
     if (!(i & 1) && !(j & 1)) return c[J * wc + I];
     if ((i & 1) && !(j & 1)) return T(0.5) * (c[J * wc + I] + c[J * wc + I + 1]);
