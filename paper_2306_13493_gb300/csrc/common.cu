@@ -259,6 +259,11 @@ bool sce_smem_pad() {
     return !(e && atoi(e) == 0);
 }
 
+bool sce_small_pad() {
+    const char *e = getenv("SCE_SMALL_PAD");
+    return e && atoi(e) == 1;
+}
+
 double sce_inner_rel_f32() {
     const char *e = getenv("SCE_INNER_REL");
     const double v = e ? atof(e) : 0.0;

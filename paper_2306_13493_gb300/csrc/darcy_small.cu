@@ -363,13 +363,13 @@ int sce_darcy_small(const darcy_problem *p, const float *k, int count, double *q
             break;
         case 32:
             if (small32_threads() == 128) SCE_SMALL(32, 128);
-            else if (sce_smem_pad())
+            else if (sce_small_pad())
                 rc = launch_small<32, 256, 1, true>(p, k, count, qoi, iters, status, u_out, misc,
                                                     qmask, u0f, u0d, st);
             else SCE_SMALL(32, 256);
             break;
         case 64:
-            if (sce_smem_pad())
+            if (sce_small_pad())
                 rc = launch_small<64, 512, 1, true>(p, k, count, qoi, iters, status, u_out, misc,
                                                     qmask, u0f, u0d, st);
             else SCE_SMALL(64, 512);

@@ -144,9 +144,12 @@ int sce_sample_batch_impl(ce_embedding_t e, uint64_t seed, uint32_t level, uint6
 // (SCE_INNER_REL, default 2e-5).
 double sce_inner_rel_f32();
 
-// Padded rows (pitch n + 2) for the shared-memory levels of at least 32 cells
-// in the one-block solvers and the fused n = 64 cycle (SCE_SMEM_PAD=0: n + 1).
+// Padded rows (pitch n + 2) for the shared-memory levels of at least 32 cells:
+// in the fused n = 64 cycle by default (SCE_SMEM_PAD=0: n + 1), in the
+// one-block solvers with SCE_SMALL_PAD=1 (their CG loops then compute a row
+// index per vertex, which measured slower than the bank conflicts it removes).
 bool sce_smem_pad();
+bool sce_small_pad();
 
 // One-block-per-sample solver for small grids (mixed precision).  qmask bit 3:
 // u_out holds float-float pairs (float2) instead of doubles.  u_init: NULL, or

@@ -353,16 +353,18 @@ def test_coarse_level_sweeps_same_solution_fewer_iterations(sce, n, monkeypatch)
 @pytest.mark.parametrize("n,small", [(32, "32"), (64, "64"), (64, "0"), (128, "0")])
 def test_padded_shared_memory_rows_are_bit_identical(sce, n, small, monkeypatch):
     """Rows of n + 2 values for the shared-memory levels of at least 32 cells
-    (the default, against SCE_SMEM_PAD=0) change addresses only: the one-block
-    solvers (n = 32, 64) and the fused n = 64 cycle (as the finest level at
-    n = 64, as a coarse level at n = 128) give bit-identical solutions, QoIs
-    and iteration counts."""
+    change addresses only: the fused n = 64 cycle (padded by default, against
+    SCE_SMEM_PAD=0; as the finest level at n = 64, as a coarse level at
+    n = 128) and the one-block solvers (n = 32, 64; padded with
+    SCE_SMALL_PAD=1) give bit-identical solutions, QoIs and iteration counts."""
     monkeypatch.setenv("SCE_SMALL_MAX_N", small)
     k = _oracle_k(n, 5, lam=0.03, seed=21, precision=32)
     out = {}
     for pad in ("0", "1"):
         monkeypatch.setenv("SCE_SMEM_PAD", pad)
+        monkeypatch.setenv("SCE_SMALL_PAD", pad)
         out[pad] = _solve(sce, k, 32, f=1.0)
+    monkeypatch.delenv("SCE_SMALL_PAD", raising=False)
     assert out["1"][0] == 0 and np.all(out["1"][3] == 0)
     for i in (1, 2, 4):
         assert np.array_equal(out["0"][i], out["1"][i]), i
